@@ -1,0 +1,744 @@
+/*
+ * hj_oracle.c -- plain, slow, FP64 CPU oracle for the generalized Lax/Hopf
+ * method of Chow, Darbon, Osher and Yin (arXiv 1704.02524).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this file's library.
+ * The CUDA path shares no code, header, table or helper with it.
+ *
+ * Everything is double precision and written as directly as possible:
+ * straight loops over coordinates, full storage of every RK4 stage for the
+ * adjoint, one pair at a time.  Each function names the passage it follows.
+ *
+ * What it computes, per (query x, time t, initial guess v):
+ *   - the bi-characteristics (Sec. 4.1, final value problem):
+ *         d gamma/ds = dH/dp,  dp/ds = -dH/dx,  gamma(t) = x,  p(t) = v,
+ *     integrated backward from s = t to s = 0 with N classical RK4 steps
+ *     (the paper suggests forward Euler "for illustration" and allows better
+ *     solvers, Sec. 4.2);
+ *   - the functional F^1 (Lax, eq. lax_formula / Sec. 4.1) or G (Hopf,
+ *     eq. hopf_formula / Sec. 4.1) with the running-cost integral taken
+ *     either by RK4 on an augmented quadrature state (default) or by the
+ *     rectangular rule of eq. num_int;
+ *   - derivatives by the finite differences of eq. num_diff (forward) or
+ *     the central form, and the exact gradient of the discretised
+ *     functional by the discrete adjoint of the RK4 map;
+ *   - cyclic coordinate descent (Algorithm 1) and gradient descent;
+ *   - the certificate p(0) in dg(gamma(0)) (Sec. 4.3), reseeding of failed
+ *     starts and best-of-guesses (Sec. 5: multiple random initial guesses).
+ *
+ * Random initial guesses come from Philox4x32-10 (Salmon, Moraes, Dror,
+ * Shaw, "Parallel Random Numbers: As Easy as 1, 2, 3", SC'11), written here
+ * from that paper's definition.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Largest dimension and control width the oracle accepts (stack buffers). */
+#define ORC_DMAX 128
+#define ORC_MMAX 64
+
+/* ------------------------------------------------------------------------ */
+/* Problem description                                                       */
+/* ------------------------------------------------------------------------ */
+
+enum { FAM_QUAD_ISO = 0, FAM_SPEED_QUAD = 1, FAM_SMOOTH_NONCONVEX = 2, FAM_LINEAR_QUAD = 3 };
+enum { LAX = 0, HOPF = 1 };
+enum { G_QUAD_SHIFT = 0, G_DIAG_QUAD = 1 };
+enum { QUAD_RK4 = 0, QUAD_RECT = 1 };
+enum { GRAD_FD_CENTRAL = 0, GRAD_FD_FORWARD = 1, GRAD_ADJOINT = 2 };
+enum { DESC_CD = 0, DESC_GD = 1 };
+
+/* Per-query status bits (same meaning as the library's, defined separately). */
+#define ST_CERTIFIED 1
+#define ST_MAX_ITERS 2
+#define ST_NONFINITE 4
+#define ST_RESEEDED 8
+
+typedef struct {
+    int d;            /* dimension of x, p, v                                   */
+    int family;       /* FAM_*                                                  */
+    int principle;    /* LAX or HOPF                                            */
+    int g_kind;       /* G_*                                                    */
+    int m;            /* columns of B (linear-quadratic family)                 */
+    int n_neg;        /* smooth non-convex family: first n_neg signs negative   */
+    double s_eps;     /* smooth non-convex family: s(q) = sqrt(q^2 + s_eps)     */
+    const double *w;  /* [d]   speed c(x) = 1 + sin(<w,x>)/2                    */
+    const double *A;  /* [d*d] row-major drift matrix                           */
+    const double *B;  /* [d*m] row-major control matrix                         */
+    const double *ga; /* [d]   shift a of g = |x-a|^2/2                         */
+    const double *gs; /* [d]   sigma of g = sum x_i^2/(2 sigma_i^2)             */
+} orc_problem;
+
+typedef struct {
+    int quad;            /* QUAD_RK4 / QUAD_RECT                                 */
+    int descent;         /* DESC_CD / DESC_GD                                    */
+    int grad;            /* GRAD_FD_CENTRAL / GRAD_FD_FORWARD / GRAD_ADJOINT     */
+    double fd_h;         /* finite-difference step sigma of eq. num_diff         */
+    double step;         /* alpha = 1/L of Algorithm 1                           */
+    int max_iters;       /* iteration cap (CD: coordinate iterations; GD: steps) */
+    int halving_period;  /* M of Algorithm 1 (0: never halve)                    */
+    double eps;          /* stopping tolerance epsilon of Algorithm 1            */
+    int adapt;           /* GD only: per-coordinate sign-change step control     */
+    double grow;         /* GD adapt: factor applied when the sign is kept       */
+    double shrink;       /* GD adapt: factor applied when the sign flips         */
+    double step_max;     /* GD adapt: upper bound on a coordinate's step         */
+    int n_guesses;       /* initial guesses per query                            */
+    int max_trials;      /* total trials per query (guesses + reseeds)           */
+    int max_rounds;      /* reseed rounds after round 0                          */
+    uint64_t seed;       /* Philox key                                           */
+    int guess_dist;      /* 0: U[-2,2]^d, 1: Irwin-Hall(12) approximate N(0,1)   */
+    double cert_tol;     /* certificate tolerance tau                            */
+} orc_opts;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (SC'11, Sec. 4): ten rounds of two 32x32->64 multiplies with */
+/* the published multipliers, key bumped by the published Weyl constants.   */
+/* ------------------------------------------------------------------------ */
+
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t prod0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t prod1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += W0; k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Word number `j` of the stream for (query q, guess slot g, round r).
+ * Counter = (j / 4, g | r << 16, q low word, q high word); key = seed. */
+static uint32_t guess_word(uint64_t seed, int64_t q, int g, int r, int j)
+{
+    uint32_t ctr[4] = { (uint32_t)(j / 4), (uint32_t)g | ((uint32_t)r << 16),
+                        (uint32_t)((uint64_t)q & 0xffffffffu), (uint32_t)((uint64_t)q >> 32) };
+    uint32_t key[2] = { (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) };
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[j % 4];
+}
+
+/* Initial guess (Sec. 5: random starting points uniform in [-2,2]^d).
+ * dist 0: v_j = 4 u - 2 with u = (word >> 8) 2^-24, exact in binary32.
+ * dist 1: Irwin-Hall(12): sum of twelve 24-bit uniforms minus 6, summed as an
+ *         integer so the value is exact in binary64. */
+void orc_guess(uint64_t seed, int64_t q, int g, int r, int d, int dist, double *v)
+{
+    for (int j = 0; j < d; ++j) {
+        if (dist == 0) {
+            uint32_t wd = guess_word(seed, q, g, r, j);
+            v[j] = 4.0 * ((double)(wd >> 8) * 0x1p-24) - 2.0;
+        } else {
+            uint64_t s = 0;
+            for (int k = 0; k < 12; ++k) s += guess_word(seed, q, g, r, 12 * j + k) >> 8;
+            v[j] = (double)s * 0x1p-24 - 6.0;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hamiltonian families: right-hand side of the characteristic system and the */
+/* running cost of the functional (Sec. 4.1; per family in the comments).    */
+/* ------------------------------------------------------------------------ */
+
+static double dot(const double *a, const double *b, int d)
+{
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) s += a[i] * b[i];
+    return s;
+}
+
+static double sgn_of(const orc_problem *P, int i) { return i < P->n_neg ? -1.0 : 1.0; }
+
+/* Speed c(x) = 1 + sin(u)/2, u = <w,x>, with c' = cos(u)/2, c'' = -sin(u)/2
+ * along w (so grad c = c' w). */
+static void speed(const orc_problem *P, const double *gam, double *u, double *c, double *c1, double *c2)
+{
+    *u = dot(P->w, gam, P->d);
+    *c = 1.0 + 0.5 * sin(*u);
+    *c1 = 0.5 * cos(*u);
+    *c2 = -0.5 * sin(*u);
+}
+
+/* Hamiltonian value H(gamma, p). */
+static double ham(const orc_problem *P, const double *gam, const double *p)
+{
+    int d = P->d;
+    double u, c, c1, c2;
+    switch (P->family) {
+    case FAM_QUAD_ISO:
+        return 0.5 * dot(p, p, d);
+    case FAM_SPEED_QUAD:
+        speed(P, gam, &u, &c, &c1, &c2);
+        return 0.5 * c * c * dot(p, p, d);
+    case FAM_SMOOTH_NONCONVEX: {
+        speed(P, gam, &u, &c, &c1, &c2);
+        double phi = 0.0;
+        for (int i = 0; i < d; ++i) phi += sgn_of(P, i) * sqrt(p[i] * p[i] + P->s_eps);
+        return c * phi;
+    }
+    case FAM_LINEAR_QUAD: {
+        double h = 0.0;
+        for (int i = 0; i < d; ++i) {
+            double ax = 0.0;
+            for (int j = 0; j < d; ++j) ax += P->A[i * d + j] * gam[j];
+            h += ax * p[i];
+        }
+        for (int k = 0; k < P->m; ++k) {
+            double btp = 0.0;
+            for (int i = 0; i < d; ++i) btp += P->B[i * P->m + k] * p[i];
+            h += 0.5 * btp * btp;
+        }
+        return h;
+    }
+    }
+    return NAN;
+}
+
+/* dH/dp and dH/dx at (gamma, p). */
+static void ham_grads(const orc_problem *P, const double *gam, const double *p, double *Hp, double *Hx)
+{
+    int d = P->d;
+    double u, c, c1, c2;
+    switch (P->family) {
+    case FAM_QUAD_ISO:
+        for (int i = 0; i < d; ++i) { Hp[i] = p[i]; Hx[i] = 0.0; }
+        return;
+    case FAM_SPEED_QUAD: {
+        speed(P, gam, &u, &c, &c1, &c2);
+        double pp = dot(p, p, d);
+        for (int i = 0; i < d; ++i) {
+            Hp[i] = c * c * p[i];
+            Hx[i] = c * c1 * pp * P->w[i];
+        }
+        return;
+    }
+    case FAM_SMOOTH_NONCONVEX: {
+        speed(P, gam, &u, &c, &c1, &c2);
+        double phi = 0.0;
+        for (int i = 0; i < d; ++i) {
+            double s = sqrt(p[i] * p[i] + P->s_eps);
+            phi += sgn_of(P, i) * s;
+            Hp[i] = c * sgn_of(P, i) * p[i] / s;
+        }
+        for (int i = 0; i < d; ++i) Hx[i] = phi * c1 * P->w[i];
+        return;
+    }
+    case FAM_LINEAR_QUAD: {
+        double btp[ORC_MMAX];
+        for (int k = 0; k < P->m; ++k) {
+            btp[k] = 0.0;
+            for (int i = 0; i < d; ++i) btp[k] += P->B[i * P->m + k] * p[i];
+        }
+        for (int i = 0; i < d; ++i) {
+            double ax = 0.0, atp = 0.0, bbtp = 0.0;
+            for (int j = 0; j < d; ++j) {
+                ax += P->A[i * d + j] * gam[j];
+                atp += P->A[j * d + i] * p[j];
+            }
+            for (int k = 0; k < P->m; ++k) bbtp += P->B[i * P->m + k] * btp[k];
+            Hp[i] = ax + bbtp;
+            Hx[i] = atp;
+        }
+        return;
+    }
+    }
+}
+
+/* Running cost inside the integral: Lax <p, dH/dp> - H (eq. lax_formula),
+ * Hopf H - <dH/dx, gamma> (eq. hopf_formula). */
+static double running_cost(const orc_problem *P, const double *gam, const double *p)
+{
+    int d = P->d;
+    double Hp[ORC_DMAX], Hx[ORC_DMAX];
+    ham_grads(P, gam, p, Hp, Hx);
+    double H = ham(P, gam, p);
+    return (P->principle == LAX) ? dot(p, Hp, d) - H : H - dot(Hx, gam, d);
+}
+
+/* Right-hand side in reversed time tau = t - s: the state z = (gamma, p)
+ * moves by dz/dtau = (-dH/dp, +dH/dx) and the quadrature state by the
+ * running cost.  out has 2d + 1 entries. */
+static void field(const orc_problem *P, const double *z, double *out)
+{
+    int d = P->d;
+    const double *gam = z, *p = z + d;
+    double Hp[ORC_DMAX], Hx[ORC_DMAX];
+    ham_grads(P, gam, p, Hp, Hx);
+    for (int i = 0; i < d; ++i) {
+        out[i] = -Hp[i];
+        out[d + i] = Hx[i];
+    }
+    out[2 * d] = running_cost(P, gam, p);
+}
+
+/* Vector-Jacobian product of `field`: given weights a (2d entries, on the
+ * state rows) and b (on the quadrature row), return
+ *     r = a^T d(field_z)/dz + b d(field_Q)/dz     (2d entries).
+ * The Jacobians are written out per family from the formulas above. */
+static void field_vjp(const orc_problem *P, const double *z, const double *a, double b, double *r)
+{
+    int d = P->d;
+    const double *gam = z, *p = z + d;
+    const double *ag = a, *ap = a + d;
+    double *rg = r, *rp = r + d;
+    switch (P->family) {
+    case FAM_QUAD_ISO:
+        /* field = (-p, 0, |p|^2/2) for both principles */
+        for (int i = 0; i < d; ++i) { rg[i] = 0.0; rp[i] = -ag[i] + b * p[i]; }
+        return;
+    case FAM_SPEED_QUAD: {
+        double u, c, c1, c2;
+        speed(P, gam, &u, &c, &c1, &c2);
+        double A = dot(ag, p, d), Bw = dot(ap, P->w, d), pp = dot(p, p, d);
+        /* field_gamma = -c^2 p, field_p = c c' |p|^2 w
+         * Lax L = c^2 |p|^2 / 2 ; Hopf L = c^2|p|^2/2 - c c' |p|^2 u */
+        double dE_du = -2.0 * c * c1 * A + (c1 * c1 + c * c2) * pp * Bw;
+        if (P->principle == LAX) dE_du += b * c * c1 * pp;
+        else dE_du += b * (-(c1 * c1 + c * c2) * pp * u);
+        for (int i = 0; i < d; ++i) {
+            rg[i] = dE_du * P->w[i];
+            double dLdp = (P->principle == LAX) ? c * c * p[i] : (c * c - 2.0 * c * c1 * u) * p[i];
+            rp[i] = -c * c * ag[i] + 2.0 * c * c1 * Bw * p[i] + b * dLdp;
+        }
+        return;
+    }
+    case FAM_SMOOTH_NONCONVEX: {
+        double u, c, c1, c2;
+        speed(P, gam, &u, &c, &c1, &c2);
+        double phi = 0.0, A = 0.0, pdphi = 0.0;
+        for (int i = 0; i < d; ++i) {
+            double s = sqrt(p[i] * p[i] + P->s_eps);
+            double dphi = sgn_of(P, i) * p[i] / s;
+            phi += sgn_of(P, i) * s;
+            A += ag[i] * dphi;
+            pdphi += p[i] * dphi;
+        }
+        double Bw = dot(ap, P->w, d);
+        /* field_gamma = -c Phi'(p), field_p = Phi c' w
+         * Lax L = c (<p,Phi'> - Phi) ; Hopf L = Phi (c - c' u) */
+        double dE_du = -c1 * A + phi * c2 * Bw;
+        if (P->principle == LAX) dE_du += b * c1 * (pdphi - phi);
+        else dE_du += b * (-phi * c2 * u);
+        for (int i = 0; i < d; ++i) {
+            double s = sqrt(p[i] * p[i] + P->s_eps);
+            double dphi = sgn_of(P, i) * p[i] / s;
+            double ddphi = sgn_of(P, i) * P->s_eps / (s * s * s);
+            double dLdp = (P->principle == LAX) ? c * p[i] * ddphi : dphi * (c - c1 * u);
+            rg[i] = dE_du * P->w[i];
+            rp[i] = -c * ag[i] * ddphi + dphi * c1 * Bw + b * dLdp;
+        }
+        return;
+    }
+    case FAM_LINEAR_QUAD: {
+        /* field_gamma = -(A gamma + B B^T p), field_p = A^T p, L = |B^T p|^2/2 */
+        int m = P->m;
+        double btag[ORC_MMAX], btp[ORC_MMAX];
+        for (int k = 0; k < m; ++k) {
+            btag[k] = 0.0; btp[k] = 0.0;
+            for (int i = 0; i < d; ++i) {
+                btag[k] += P->B[i * m + k] * ag[i];
+                btp[k] += P->B[i * m + k] * p[i];
+            }
+        }
+        for (int i = 0; i < d; ++i) {
+            double atag = 0.0, aap = 0.0, bb = 0.0;
+            for (int j = 0; j < d; ++j) {
+                atag += P->A[j * d + i] * ag[j];
+                aap += P->A[i * d + j] * ap[j];
+            }
+            for (int k = 0; k < m; ++k) bb += P->B[i * m + k] * (-btag[k] + b * btp[k]);
+            rg[i] = -atag;
+            rp[i] = aap + bb;
+        }
+        return;
+    }
+    }
+}
+
+/* Initial data g, its gradient, its Legendre transform g* and grad g*. */
+static double g_val(const orc_problem *P, const double *x)
+{
+    double s = 0.0;
+    for (int i = 0; i < P->d; ++i) {
+        if (P->g_kind == G_QUAD_SHIFT) {
+            double a = P->ga ? P->ga[i] : 0.0;
+            s += 0.5 * (x[i] - a) * (x[i] - a);
+        } else {
+            s += 0.5 * x[i] * x[i] / (P->gs[i] * P->gs[i]);
+        }
+    }
+    return s;
+}
+static void g_grad(const orc_problem *P, const double *x, double *out)
+{
+    for (int i = 0; i < P->d; ++i)
+        out[i] = (P->g_kind == G_QUAD_SHIFT) ? x[i] - (P->ga ? P->ga[i] : 0.0) : x[i] / (P->gs[i] * P->gs[i]);
+}
+static double gstar_val(const orc_problem *P, const double *p)
+{
+    double s = 0.0;
+    for (int i = 0; i < P->d; ++i) {
+        if (P->g_kind == G_QUAD_SHIFT) s += 0.5 * p[i] * p[i] + (P->ga ? P->ga[i] : 0.0) * p[i];
+        else s += 0.5 * P->gs[i] * P->gs[i] * p[i] * p[i];
+    }
+    return s;
+}
+static void gstar_grad(const orc_problem *P, const double *p, double *out)
+{
+    for (int i = 0; i < P->d; ++i)
+        out[i] = (P->g_kind == G_QUAD_SHIFT) ? p[i] + (P->ga ? P->ga[i] : 0.0) : P->gs[i] * P->gs[i] * p[i];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Functional evaluation (Sec. 4.1 functionals F^1 and G; Sec. 4.2 solver and */
+/* quadrature).                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Integrate from s = t (tau = 0) to s = 0 (tau = t) in N RK4 steps.  The
+ * trajectory z_n (n = 0..N, tau_n = n t/N) and, for the adjoint, the four
+ * stage inputs of every step are written when the buffers are non-NULL.
+ * Returns the quadrature of the running cost over [0, t]. */
+static double integrate(const orc_problem *P, int quad, const double *x, double t, int N, const double *v,
+                        double *traj /* [(N+1)*2d] */, double *stages /* [N*4*2d] */)
+{
+    int d = P->d, n2 = 2 * d;
+    double h = t / N;
+    double z[2 * ORC_DMAX + 1], zs[2 * ORC_DMAX + 1];
+    double k1[2 * ORC_DMAX + 1], k2[2 * ORC_DMAX + 1], k3[2 * ORC_DMAX + 1], k4[2 * ORC_DMAX + 1];
+    for (int i = 0; i < d; ++i) { z[i] = x[i]; z[d + i] = v[i]; }
+    double Q = 0.0;
+    if (traj) memcpy(traj, z, sizeof(double) * n2);
+    for (int n = 0; n < N; ++n) {
+        if (stages) memcpy(stages + (size_t)(4 * n + 0) * n2, z, sizeof(double) * n2);
+        field(P, z, k1);
+        for (int i = 0; i < n2; ++i) zs[i] = z[i] + 0.5 * h * k1[i];
+        if (stages) memcpy(stages + (size_t)(4 * n + 1) * n2, zs, sizeof(double) * n2);
+        field(P, zs, k2);
+        for (int i = 0; i < n2; ++i) zs[i] = z[i] + 0.5 * h * k2[i];
+        if (stages) memcpy(stages + (size_t)(4 * n + 2) * n2, zs, sizeof(double) * n2);
+        field(P, zs, k3);
+        for (int i = 0; i < n2; ++i) zs[i] = z[i] + h * k3[i];
+        if (stages) memcpy(stages + (size_t)(4 * n + 3) * n2, zs, sizeof(double) * n2);
+        field(P, zs, k4);
+        for (int i = 0; i < n2; ++i) z[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+        if (quad == QUAD_RK4) {
+            /* RK4 on the augmented quadrature state */
+            Q += h / 6.0 * (k1[n2] + 2.0 * k2[n2] + 2.0 * k3[n2] + k4[n2]);
+        } else {
+            /* eq. num_int: rectangle rule on the solver's mesh.  The node
+             * s_i = i ds (i = 0..N-1) is the state after N - i steps of
+             * reversed time, i.e. the states z_1..z_N reached here. */
+            Q += h * running_cost(P, z, z + d);
+        }
+        if (traj) memcpy(traj + (size_t)(n + 1) * n2, z, sizeof(double) * n2);
+    }
+    return Q;
+}
+
+/* F^1 (Lax) = g(gamma(0)) + int_0^t (<p, H_p> - H) ds;
+ * G (Hopf)  = g*(p(0)) + int_0^t (H - <H_x, gamma>) ds - <x, v>.
+ * gamma0, p0 may be NULL. */
+double orc_functional(const orc_problem *P, int quad, const double *x, double t, int N, const double *v,
+                      double *gamma0, double *p0)
+{
+    int d = P->d, n2 = 2 * d;
+    double *traj = (double *)malloc(sizeof(double) * (size_t)(N + 1) * n2);
+    double Q = integrate(P, quad, x, t, N, v, traj, NULL);
+    const double *zN = traj + (size_t)N * n2; /* (gamma(0), p(0)) */
+    double F = (P->principle == LAX) ? g_val(P, zN) + Q : gstar_val(P, zN + d) + Q - dot(x, v, d);
+    if (gamma0) memcpy(gamma0, zN, sizeof(double) * d);
+    if (p0) memcpy(p0, zN + d, sizeof(double) * d);
+    free(traj);
+    return F;
+}
+
+/* Exact gradient of the discretised functional with respect to v: the
+ * discrete adjoint of the RK4 map (reverse accumulation through the four
+ * stages of every step; all stage inputs are stored).  Returns F. */
+double orc_gradient(const orc_problem *P, int quad, const double *x, double t, int N, const double *v,
+                    double *grad)
+{
+    int d = P->d, n2 = 2 * d;
+    double h = t / N;
+    double *traj = (double *)malloc(sizeof(double) * (size_t)(N + 1) * n2);
+    double *stages = (double *)malloc(sizeof(double) * (size_t)N * 4 * n2);
+    double lam[2 * ORC_DMAX], a1[2 * ORC_DMAX], a2[2 * ORC_DMAX], a3[2 * ORC_DMAX], a4[2 * ORC_DMAX];
+    double w[2 * ORC_DMAX];
+    double Q = integrate(P, quad, x, t, N, v, traj, stages);
+    const double *zN = traj + (size_t)N * n2;
+    double F;
+    /* adjoint of the terminal term */
+    for (int i = 0; i < n2; ++i) lam[i] = 0.0;
+    if (P->principle == LAX) {
+        F = g_val(P, zN) + Q;
+        g_grad(P, zN, lam);
+    } else {
+        F = gstar_val(P, zN + d) + Q - dot(x, v, d);
+        gstar_grad(P, zN + d, lam + d);
+    }
+    double beta_q = (quad == QUAD_RK4) ? 1.0 : 0.0; /* dF/dQ flows through the stages only for RK4 quadrature */
+    for (int n = N - 1; n >= 0; --n) {
+        const double *Z1 = stages + (size_t)(4 * n + 0) * n2, *Z2 = Z1 + n2, *Z3 = Z2 + n2, *Z4 = Z3 + n2;
+        if (quad == QUAD_RECT) {
+            /* rectangle node at the state after step n, weight h: add h grad L */
+            double gl[2 * ORC_DMAX], zero[2 * ORC_DMAX];
+            for (int i = 0; i < n2; ++i) zero[i] = 0.0;
+            field_vjp(P, traj + (size_t)(n + 1) * n2, zero, 1.0, gl);
+            for (int i = 0; i < n2; ++i) lam[i] += h * gl[i];
+        }
+        /* z_{n+1} = z_n + h/6 (k1 + 2k2 + 2k3 + k4), Q likewise; reverse: */
+        for (int i = 0; i < n2; ++i) w[i] = h / 6.0 * lam[i];
+        field_vjp(P, Z4, w, beta_q * h / 6.0, a4);
+        for (int i = 0; i < n2; ++i) w[i] = h / 3.0 * lam[i] + h * a4[i];
+        field_vjp(P, Z3, w, beta_q * h / 3.0, a3);
+        for (int i = 0; i < n2; ++i) w[i] = h / 3.0 * lam[i] + 0.5 * h * a3[i];
+        field_vjp(P, Z2, w, beta_q * h / 3.0, a2);
+        for (int i = 0; i < n2; ++i) w[i] = h / 6.0 * lam[i] + 0.5 * h * a2[i];
+        field_vjp(P, Z1, w, beta_q * h / 6.0, a1);
+        for (int i = 0; i < n2; ++i) lam[i] += a1[i] + a2[i] + a3[i] + a4[i];
+    }
+    for (int i = 0; i < d; ++i) grad[i] = lam[d + i] - (P->principle == HOPF ? x[i] : 0.0);
+    free(traj);
+    free(stages);
+    return F;
+}
+
+/* Finite-difference partial derivative along e_j (eq. num_diff; central form
+ * when central != 0).  F0 is F(v), used by the forward form. */
+static double fd_partial(const orc_problem *P, int quad, const double *x, double t, int N, double *v, int j,
+                         double h, int central, double F0)
+{
+    double vj = v[j];
+    v[j] = vj + h;
+    double Fp = orc_functional(P, quad, x, t, N, v, NULL, NULL);
+    double deriv;
+    if (central) {
+        v[j] = vj - h;
+        double Fm = orc_functional(P, quad, x, t, N, v, NULL, NULL);
+        deriv = (Fp - Fm) / (2.0 * h);
+    } else {
+        deriv = (Fp - F0) / h;
+    }
+    v[j] = vj;
+    return deriv;
+}
+
+/* Central-difference full gradient (the plain definition of the derivative,
+ * used to check the adjoint). */
+void orc_gradient_fd(const orc_problem *P, int quad, const double *x, double t, int N, const double *v, double h,
+                     double *grad)
+{
+    double *vv = (double *)malloc(sizeof(double) * (size_t)P->d);
+    memcpy(vv, v, sizeof(double) * P->d);
+    for (int j = 0; j < P->d; ++j) grad[j] = fd_partial(P, quad, x, t, N, vv, j, h, 1, 0.0);
+    free(vv);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Descent (Sec. 4.1, Algorithm 1, and its gradient form).                  */
+/* ------------------------------------------------------------------------ */
+
+/* Algorithm 1, cyclic coordinate descent, read as follows.  alpha = step;
+ * at iteration k the coordinate j_k = k mod d moves by alpha * dF/dv_j; the
+ * counter of consecutive steps with |dv_j| <= eps resets on a larger step,
+ * and the descent stops when it reaches d (a full sweep of small steps);
+ * every `halving_period` iterations alpha is halved; max_iters caps k.
+ * Gradient form: every iteration moves all coordinates by alpha_i dF/dv_i
+ * with the adjoint gradient; it stops after one iteration whose largest
+ * move is <= eps.
+ * Per-coordinate step control (`adapt`, both forms): each coordinate keeps
+ * its own alpha_i.  When its derivative changes sign between two
+ * consecutive visits (an overshoot) alpha_i is multiplied by `shrink`; when
+ * the sign is kept, by `grow` (capped at step_max).  This is a per-
+ * coordinate trigger for Algorithm 1's "alpha := alpha/2"; the global
+ * halving every `halving_period` iterations still applies on top.
+ * Returns the number of iterations; *hit_cap is set when the cap stopped it. */
+int orc_descend(const orc_problem *P, const orc_opts *O, const double *x, double t, int N, double *v, int *hit_cap,
+                int *nonfinite)
+{
+    int d = P->d;
+    *hit_cap = 0;
+    *nonfinite = 0;
+    if (O->descent == DESC_CD) {
+        double alpha[ORC_DMAX], dprev[ORC_DMAX];
+        for (int i = 0; i < d; ++i) { alpha[i] = O->step; dprev[i] = 0.0; }
+        int count = 0, k_in_period = 0, it;
+        for (it = 0; it < O->max_iters; ++it) {
+            int j = it % d;
+            double F0 = 0.0;
+            if (O->grad == GRAD_FD_FORWARD) F0 = orc_functional(P, O->quad, x, t, N, v, NULL, NULL);
+            double dj = fd_partial(P, O->quad, x, t, N, v, j, O->fd_h, O->grad != GRAD_FD_FORWARD, F0);
+            if (O->adapt) {
+                double prod = dj * dprev[j];
+                if (prod < 0.0) alpha[j] *= O->shrink;
+                else if (prod > 0.0) alpha[j] = fmin(alpha[j] * O->grow, O->step_max);
+                dprev[j] = dj;
+            }
+            double step = alpha[j] * dj;
+            if (!isfinite(step)) { *nonfinite = 1; return it + 1; }
+            v[j] -= step;
+            if (fabs(step) > O->eps) count = 0; else count += 1;
+            if (O->halving_period > 0 && ++k_in_period == O->halving_period) {
+                k_in_period = 0;
+                for (int i = 0; i < d; ++i) alpha[i] *= 0.5;
+            }
+            if (count >= d) return it + 1;
+        }
+        *hit_cap = 1;
+        return it;
+    } else {
+        double *g = (double *)malloc(sizeof(double) * 3 * (size_t)d), *gprev = g + d, *alpha = gprev + d;
+        for (int i = 0; i < d; ++i) { alpha[i] = O->step; gprev[i] = 0.0; }
+        int it;
+        for (it = 0; it < O->max_iters; ++it) {
+            if (O->grad == GRAD_ADJOINT) orc_gradient(P, O->quad, x, t, N, v, g);
+            else orc_gradient_fd(P, O->quad, x, t, N, v, O->fd_h, g);
+            double big = 0.0;
+            for (int i = 0; i < d; ++i) {
+                if (O->adapt) {
+                    double prod = g[i] * gprev[i];
+                    if (prod < 0.0) alpha[i] *= O->shrink;
+                    else if (prod > 0.0) alpha[i] = fmin(alpha[i] * O->grow, O->step_max);
+                }
+                double step = alpha[i] * g[i];
+                if (!isfinite(step)) { *nonfinite = 1; free(g); return it + 1; }
+                v[i] -= step;
+                if (fabs(step) > big) big = fabs(step);
+                gprev[i] = g[i];
+            }
+            if (O->halving_period > 0 && (it + 1) % O->halving_period == 0)
+                for (int i = 0; i < d; ++i) alpha[i] *= 0.5;
+            if (big <= O->eps) { free(g); return it + 1; }
+        }
+        free(g);
+        *hit_cap = 1;
+        return it;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Certificate (Sec. 4.3): p(0) in dg(gamma(0)).  Lax: residual             */
+/* |p(0) - grad g(gamma(0))| / (1 + |p(0)|); Hopf (g convex, so the inclusion */
+/* is gamma(0) = grad g*(p(0))): |gamma(0) - grad g*(p(0))| / (1 + |gamma(0)|). */
+/* Also returns the FP64 functional value at v.                              */
+/* ------------------------------------------------------------------------ */
+double orc_certify(const orc_problem *P, int quad, const double *x, double t, int N, const double *v,
+                   double *residual)
+{
+    int d = P->d;
+    double *g0 = (double *)malloc(sizeof(double) * 3 * (size_t)d), *p0 = g0 + d, *gr = p0 + d;
+    double F = orc_functional(P, quad, x, t, N, v, g0, p0);
+    double num = 0.0, den = 0.0;
+    if (P->principle == LAX) {
+        g_grad(P, g0, gr);
+        for (int i = 0; i < d; ++i) { num += (p0[i] - gr[i]) * (p0[i] - gr[i]); den += p0[i] * p0[i]; }
+    } else {
+        gstar_grad(P, p0, gr);
+        for (int i = 0; i < d; ++i) { num += (g0[i] - gr[i]) * (g0[i] - gr[i]); den += g0[i] * g0[i]; }
+    }
+    *residual = sqrt(num) / (1.0 + sqrt(den));
+    free(g0);
+    return F;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One query: guesses, descent, certificate, reseeding of failed starts and  */
+/* best-of-guesses (Sec. 4.3 and Sec. 5).                                    */
+/*                                                                          */
+/* Round 0 runs n_guesses slots from Philox draws (q, g, 0).  In round r >= 1 */
+/* every slot whose certificate failed is restarted from draw (q, g, r), in  */
+/* slot order, while the query's trial budget max_trials lasts.  The answer  */
+/* is the certified slot with the smallest FP64 functional value (ties: the  */
+/* lowest slot); with no certified slot, the smallest over all slots.  Lax:  */
+/* phi = F^1; Hopf: phi = -G.                                                */
+/*                                                                          */
+/* Per-slot diagnostics (may be NULL), each [n_guesses]: final functional,   */
+/* residual, pass flag, iterations of the last attempt, round of the last    */
+/* attempt, and the final v of every slot ([n_guesses * d]).                 */
+/* ------------------------------------------------------------------------ */
+int orc_solve_query(const orc_problem *P, const orc_opts *O, int64_t q, const double *x, double t, int N,
+                    double *phi, double *vstar, double *slot_F, double *slot_res, int *slot_pass, int *slot_iters,
+                    int *slot_round, double *slot_v)
+{
+    int d = P->d, G = O->n_guesses;
+    double *V = (double *)malloc(sizeof(double) * (size_t)G * d);
+    double *F = (double *)malloc(sizeof(double) * (size_t)G * 2), *R = F + G;
+    int *pass = (int *)malloc(sizeof(int) * (size_t)G * 4), *iters = pass + G, *round = iters + G, *cap = round + G;
+    int any_nonfinite = 0, reseeded = 0;
+    int trials = 0;
+    for (int g = 0; g < G; ++g) {
+        double *v = V + (size_t)g * d;
+        orc_guess(O->seed, q, g, 0, d, O->guess_dist, v);
+        int nf;
+        iters[g] = orc_descend(P, O, x, t, N, v, &cap[g], &nf);
+        any_nonfinite |= nf;
+        F[g] = orc_certify(P, O->quad, x, t, N, v, &R[g]);
+        pass[g] = (R[g] <= O->cert_tol) && isfinite(F[g]);
+        round[g] = 0;
+        trials++;
+    }
+    for (int r = 1; r <= O->max_rounds; ++r) {
+        int launched = 0;
+        for (int g = 0; g < G && trials < O->max_trials; ++g) {
+            if (pass[g]) continue;
+            double *v = V + (size_t)g * d;
+            orc_guess(O->seed, q, g, r, d, O->guess_dist, v);
+            int nf;
+            iters[g] = orc_descend(P, O, x, t, N, v, &cap[g], &nf);
+            any_nonfinite |= nf;
+            F[g] = orc_certify(P, O->quad, x, t, N, v, &R[g]);
+            pass[g] = (R[g] <= O->cert_tol) && isfinite(F[g]);
+            round[g] = r;
+            trials++;
+            launched++;
+            reseeded = 1;
+        }
+        if (!launched) break;
+    }
+    int best = -1, best_cert = 0;
+    for (int g = 0; g < G; ++g) {
+        if (!isfinite(F[g])) continue;
+        if (pass[g] && !best_cert) { best = g; best_cert = 1; continue; }
+        if (pass[g] != best_cert) continue;
+        if (best < 0 || F[g] < F[best]) best = g;
+    }
+    int status = 0;
+    if (best >= 0) {
+        *phi = (P->principle == LAX) ? F[best] : -F[best];
+        memcpy(vstar, V + (size_t)best * d, sizeof(double) * d);
+        if (best_cert) status |= ST_CERTIFIED;
+        if (cap[best]) status |= ST_MAX_ITERS;
+    } else {
+        *phi = NAN;
+        for (int i = 0; i < d; ++i) vstar[i] = NAN;
+        status |= ST_NONFINITE;
+    }
+    if (any_nonfinite) status |= ST_NONFINITE;
+    if (reseeded) status |= ST_RESEEDED;
+    for (int g = 0; g < G; ++g) {
+        if (slot_F) slot_F[g] = F[g];
+        if (slot_res) slot_res[g] = R[g];
+        if (slot_pass) slot_pass[g] = pass[g];
+        if (slot_iters) slot_iters[g] = iters[g];
+        if (slot_round) slot_round[g] = round[g];
+        if (slot_v) memcpy(slot_v + (size_t)g * d, V + (size_t)g * d, sizeof(double) * d);
+    }
+    free(V);
+    free(F);
+    free(pass);
+    return status;
+}

@@ -1,0 +1,239 @@
+"""Seeded synthetic workloads for the generalized Lax/Hopf solver.
+
+This module only draws inputs: query points, times, step counts and the
+parameters of each Hamiltonian family, rounded to binary32 and returned as
+float64 arrays, so the GPU (which computes in fp32) and the FP64 oracle
+solve exactly the same problem.  It holds none of the method's arithmetic
+and imports neither the CUDA library nor the oracle; tests and bench.py
+feed its arrays to both sides.
+
+The paper (arXiv 1704.02524, Sec. 5) evaluates analytic examples only, on
+2-D cross-sections of [-3,3]^d with random initial guesses in [-2,2]^d; it
+uses no dataset.  The five workloads below are synthetic in the same
+spirit, with the sizes listed in each docstring.  Every draw comes from
+numpy's Philox bit generator keyed by 0x170402524 + workload number, in a
+fixed order (family parameters first, then queries), so the first n rows
+of a workload do not depend on how many rows are drawn.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional
+
+import numpy as np
+
+FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD = 0, 1, 2, 3
+LAX, HOPF = 0, 1
+G_QUAD_SHIFT, G_DIAG_QUAD = 0, 1
+
+HARNESS_SEED = 0x170402524
+
+
+def f32(a) -> np.ndarray:
+    """Round to binary32, return as float64 (the values both sides receive)."""
+    return np.asarray(a, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def rng_for(index: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=HARNESS_SEED + index))
+
+
+@dataclass
+class ProblemSpec:
+    """A Hamiltonian family instance and its initial data g."""
+    d: int
+    family: int
+    principle: int
+    g_kind: int
+    w: Optional[np.ndarray] = None       # [d]   speed c(x) = 1 + sin(<w,x>)/2
+    A: Optional[np.ndarray] = None       # [d,d] drift
+    B: Optional[np.ndarray] = None       # [d,m] control
+    a: Optional[np.ndarray] = None       # [d]   g = |x-a|^2/2
+    sigma: Optional[np.ndarray] = None   # [d]   g = sum x_i^2/(2 sigma_i^2)
+    n_neg: int = 1
+    s_eps: float = 1e-6
+    n_guesses: int = 1
+
+    def params(self) -> np.ndarray:
+        """Flat parameter vector in the library's documented order:
+        family block (w | A row-major then B row-major), then g block (a | sigma)."""
+        parts: List[np.ndarray] = []
+        if self.family in (FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX):
+            parts.append(self.w)
+        if self.family == FAM_LINEAR_QUAD:
+            parts += [self.A.reshape(-1), self.B.reshape(-1)]
+        parts.append(self.a if self.g_kind == G_QUAD_SHIFT else self.sigma)
+        return np.concatenate([np.asarray(p, dtype=np.float64).reshape(-1) for p in parts])
+
+    @property
+    def m(self) -> int:
+        return 0 if self.B is None else int(self.B.shape[1])
+
+
+@dataclass
+class Workload:
+    name: str
+    problems: List[ProblemSpec]
+    x: np.ndarray            # [nq, ld] float64 (binary32 values), zero padded past each row's d
+    t: np.ndarray            # [nq]
+    n_steps: np.ndarray      # [nq] int32
+    problem_idx: np.ndarray  # [nq] int32
+    solver: Dict             # solver constants (see solver_constants)
+    precision: str           # "fp32" or "fp64"
+    note: str = ""
+
+    @property
+    def nq(self) -> int:
+        return int(self.x.shape[0])
+
+    @property
+    def n_pairs(self) -> int:
+        return int(sum(self.problems[int(i)].n_guesses for i in self.problem_idx))
+
+    def head(self, n: int) -> "Workload":
+        """The first n queries (same problems and constants)."""
+        return Workload(self.name, self.problems, self.x[:n].copy(), self.t[:n].copy(), self.n_steps[:n].copy(),
+                        self.problem_idx[:n].copy(), dict(self.solver), self.precision, self.note)
+
+    def take(self, idx) -> "Workload":
+        idx = np.asarray(idx)
+        return Workload(self.name, self.problems, self.x[idx].copy(), self.t[idx].copy(),
+                        self.n_steps[idx].copy(), self.problem_idx[idx].copy(), dict(self.solver),
+                        self.precision, self.note)
+
+
+def solver_constants(**over) -> Dict:
+    """Default solver constants (names follow Algorithm 1 of the paper)."""
+    c = dict(grad="adjoint", quad="rk4", fd_h=2.0 ** -10, step=0.05, max_iters=200, halving_period=0,
+             eps=1e-6, adapt=1, grow=1.2, shrink=0.5, step_max=1.0, n_guesses=1, max_trials=20,
+             max_rounds=4, seed=0x5EED1704, guess_dist=0, cert_tol=1e-3)
+    c.update(over)
+    return c
+
+
+def _speed_w(rng, d):
+    return f32(rng.normal(size=d) / math.sqrt(d))
+
+
+def c1_quad_iso(nq: Optional[int] = None) -> Workload:
+    """d=2 Lax, H=|p|^2/2, g=|x|^2/2, t=1: 64 queries on the 8x8 grid over
+    [-2,2]^2 (endpoints included), RK4 N=20, coordinate descent with central
+    differences (h=1e-4, alpha=0.1, exactly 200 sweeps), 4 Irwin-Hall
+    guesses, all in FP64.  Closed form phi = |x|^2 / (2 (1 + t))."""
+    g = -2.0 + 4.0 * np.arange(8) / 7.0
+    X = np.array([[a, b] for a in g for b in g])
+    P = ProblemSpec(d=2, family=FAM_QUAD_ISO, principle=LAX, g_kind=G_QUAD_SHIFT, a=np.zeros(2), n_guesses=4)
+    nq = 64 if nq is None else nq
+    X = X[:nq]
+    solver = solver_constants(grad="fd_central", fd_h=1e-4, step=0.1, max_iters=200 * 2, eps=0.0, adapt=0,
+                              n_guesses=4, max_trials=4, max_rounds=0, guess_dist=1, cert_tol=1e-6)
+    return Workload("quad_iso_d2_lax", [P], X, np.ones(nq), np.full(nq, 20, np.int32), np.zeros(nq, np.int32),
+                    solver, "fp64")
+
+
+def c2_speed_quad(nq_x: int = 16384) -> Workload:
+    """d=10 Lax, H = c(x)^2 |p|^2 / 2 with c = 1 + sin(<w,x>)/2, w ~ N(0, I/d);
+    g = |x-a|^2/2, a ~ U[-1,1]^d; x ~ U[-2,2]^d, each at t in {0.25, 0.5, 1}
+    (query 3i+k is point i at time k); RK4 N=50; 8 uniform guesses."""
+    rng = rng_for(2)
+    d = 10
+    w = _speed_w(rng, d)
+    a = f32(rng.uniform(-1, 1, d))
+    X = f32(rng.uniform(-2, 2, (nq_x, d)))
+    T = np.array([0.25, 0.5, 1.0])
+    P = ProblemSpec(d=d, family=FAM_SPEED_QUAD, principle=LAX, g_kind=G_QUAD_SHIFT, w=w, a=a, n_guesses=8)
+    x = np.repeat(X, 3, axis=0)
+    t = np.tile(T, nq_x)
+    nq = x.shape[0]
+    return Workload("speed_quad_d10_lax", [P], x, t, np.full(nq, 50, np.int32), np.zeros(nq, np.int32),
+                    solver_constants(n_guesses=8), "fp32")
+
+
+def c3_smooth_nonconvex(nq: int = 65536) -> Workload:
+    """d=20 Hopf, H = c(x) (-s(p_1) + sum_{i>=2} s(p_i)), s(q) = sqrt(q^2+1e-6),
+    c as in the d=10 workload (its own w); g = sum x_i^2/(2 sigma_i^2),
+    sigma ~ U[0.5,2]; x ~ U[-1,1]^d; t = 0.5; RK4 N=64; 16 uniform guesses,
+    certificate and reseeding (at most 20 trials per query)."""
+    rng = rng_for(3)
+    d = 20
+    w = _speed_w(rng, d)
+    sigma = f32(rng.uniform(0.5, 2.0, d))
+    X = f32(rng.uniform(-1, 1, (nq, d)))
+    P = ProblemSpec(d=d, family=FAM_SMOOTH_NONCONVEX, principle=HOPF, g_kind=G_DIAG_QUAD, w=w, sigma=sigma,
+                    n_neg=1, s_eps=1e-6, n_guesses=16)
+    return Workload("smooth_nonconvex_d20_hopf", [P], X, np.full(nq, 0.5), np.full(nq, 64, np.int32),
+                    np.zeros(nq, np.int32), solver_constants(n_guesses=16), "fp32")
+
+
+def _lq_matrices(rng, d, m=32):
+    G0 = rng.normal(size=(d, d))
+    A = f32(G0 / (2.0 * np.linalg.norm(G0, 2)))
+    B = f32(rng.normal(size=(d, m)) / math.sqrt(d))
+    return A, B
+
+
+def c4_linear_quad(nq: int = 32768) -> Workload:
+    """d=64 Lax, H = <Ax,p> + |B^T p|^2/2 with A = G/(2||G||_2), G a standard
+    Gaussian d x d, B a d x 32 Gaussian scaled by 1/sqrt(d); g = |x|^2/2;
+    x ~ N(0, I); t = 1; RK4 N=100; one guess.  The exact solution is
+    x^T P(t) x / 2 with the Riccati matrix P."""
+    rng = rng_for(4)
+    d = 64
+    A, B = _lq_matrices(rng, d)
+    X = f32(rng.normal(size=(nq, d)))
+    P = ProblemSpec(d=d, family=FAM_LINEAR_QUAD, principle=LAX, g_kind=G_QUAD_SHIFT, A=A, B=B, a=np.zeros(d),
+                    n_guesses=1)
+    return Workload("linear_quad_d64_lax", [P], X, np.ones(nq), np.full(nq, 100, np.int32), np.zeros(nq, np.int32),
+                    solver_constants(n_guesses=1, max_iters=300), "fp32")
+
+
+def c5_mixed(n_pairs: int = 1 << 20) -> Workload:
+    """Uneven batch of (query, guess) pairs: a third of the pairs each from
+    the d=10-style speed-quadratic Lax family (8 guesses), the d=20-style
+    non-convex Hopf family (16 guesses) and the linear-quadratic Lax family
+    (1 guess).  Each query draws d from {8, 16, 32, 100}, t ~ U[0.1, 2] and
+    N = ceil(64 t).  Family parameters are drawn per (family, d)."""
+    rng = rng_for(5)
+    dims = [8, 16, 32, 100]
+    probs: List[ProblemSpec] = []
+    for d in dims:
+        probs.append(ProblemSpec(d=d, family=FAM_SPEED_QUAD, principle=LAX, g_kind=G_QUAD_SHIFT,
+                                 w=_speed_w(rng, d), a=f32(rng.uniform(-1, 1, d)), n_guesses=8))
+    for d in dims:
+        probs.append(ProblemSpec(d=d, family=FAM_SMOOTH_NONCONVEX, principle=HOPF, g_kind=G_DIAG_QUAD,
+                                 w=_speed_w(rng, d), sigma=f32(rng.uniform(0.5, 2.0, d)), n_guesses=16))
+    for d in dims:
+        A, B = _lq_matrices(rng, d)
+        probs.append(ProblemSpec(d=d, family=FAM_LINEAR_QUAD, principle=LAX, g_kind=G_QUAD_SHIFT, A=A, B=B,
+                                 a=np.zeros(d), n_guesses=1))
+    per_fam = n_pairs // 3
+    n_q = [per_fam // 8, per_fam // 16]
+    n_q.append(n_pairs - 8 * n_q[0] - 16 * n_q[1])
+    ld = max(dims)
+    xs, ts, idx = [], [], []
+    for f, nqf in enumerate(n_q):
+        dsel = rng.integers(0, len(dims), nqf)
+        tt = f32(rng.uniform(0.1, 2.0, nqf))
+        X = np.zeros((nqf, ld))
+        raw = rng.uniform(-1, 1, (nqf, ld)) if f != 2 else rng.normal(size=(nqf, ld))
+        for k, d in enumerate(dims):
+            rows = dsel == k
+            X[rows, :d] = f32(raw[rows, :d])
+        xs.append(X)
+        ts.append(tt)
+        idx.append(4 * f + dsel)
+    x = np.concatenate(xs)
+    t = np.concatenate(ts)
+    pidx = np.concatenate(idx).astype(np.int32)
+    N = np.ceil(64.0 * t).astype(np.int32)
+    return Workload("mixed_persistent", probs, x, t, N, pidx, solver_constants(max_iters=300), "fp32")
+
+
+WORKLOADS = {
+    "quad_iso_d2_lax": c1_quad_iso,
+    "speed_quad_d10_lax": c2_speed_quad,
+    "smooth_nonconvex_d20_hopf": c3_smooth_nonconvex,
+    "linear_quad_d64_lax": c4_linear_quad,
+    "mixed_persistent": c5_mixed,
+}

@@ -1,0 +1,32 @@
+"""Test-side glue: workload specs -> oracle objects, and tolerances."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+from paper_1704_02524_gb300 import workloads as W
+
+GRAD_CODES = {"fd_central": O.GRAD_FD_CENTRAL, "fd_forward": O.GRAD_FD_FORWARD, "adjoint": O.GRAD_ADJOINT}
+QUAD_CODES = {"rk4": O.QUAD_RK4, "rect": O.QUAD_RECT}
+
+
+def oracle_problem(spec: W.ProblemSpec) -> O.Problem:
+    return O.Problem(d=spec.d, family=spec.family, principle=spec.principle, g_kind=spec.g_kind, w=spec.w,
+                     A=spec.A, B=spec.B, a=spec.a, sigma=spec.sigma, n_neg=spec.n_neg, s_eps=spec.s_eps)
+
+
+def oracle_opts(solver: dict, n_guesses: int) -> O.Opts:
+    g = GRAD_CODES[solver["grad"]]
+    return O.Opts(quad=QUAD_CODES[solver["quad"]], descent=O.DESC_GD if g == O.GRAD_ADJOINT else O.DESC_CD,
+                  grad=g, fd_h=solver["fd_h"] if g != O.GRAD_ADJOINT else 1e-6, step=solver["step"],
+                  max_iters=solver["max_iters"], halving_period=solver["halving_period"], eps=solver["eps"],
+                  adapt=solver["adapt"], grow=solver["grow"], shrink=solver["shrink"],
+                  step_max=solver["step_max"], n_guesses=n_guesses, max_trials=solver["max_trials"],
+                  max_rounds=solver["max_rounds"], seed=solver["seed"], guess_dist=solver["guess_dist"],
+                  cert_tol=solver["cert_tol"])
+
+
+def rel_err(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.abs(a - b) / (1.0 + np.abs(b))

@@ -1,0 +1,507 @@
+"""Pins of the FP64 oracle against facts outside it (CPU only).
+
+Each test checks one oracle function against something the paper or the
+mathematics fixes: published known-answer vectors, closed forms, the
+classical Hopf formula, the Riccati solution, a Lax-Friedrichs grid solve,
+the HJ equation itself, or convergence orders.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.integrate
+
+import oracle as O
+from paper_1704_02524_gb300 import workloads as W
+from tests import pins
+from tests.helpers import oracle_opts, oracle_problem, rel_err
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10 and the initial guesses (Sec. 5: random starts in [-2,2]^d)
+# --------------------------------------------------------------------------
+
+def _kat_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                w = [int(x, 16) for x in line.split()]
+                rows.append((w[0:4], w[4:6], w[6:10]))
+    return rows
+
+
+@pytest.mark.parametrize("ctr,key,expect", _kat_rows())
+def test_philox_known_answers(ctr, key, expect):
+    assert list(O.philox4x32_10(ctr, key)) == expect
+
+
+def test_uniform_guess_is_exact_binary32_and_uniform():
+    d = 20
+    draws = np.array([O.guess(0xABCDEF, q, g, 0, d, 0) for q in range(200) for g in range(16)]).ravel()
+    assert draws.min() >= -2.0 and draws.max() < 2.0
+    assert np.array_equal(draws.astype(np.float32).astype(np.float64), draws)
+    # each value is 4 k 2^-24 - 2 for an integer k < 2^24
+    k = (draws + 2.0) / 4.0 * 2 ** 24
+    assert np.array_equal(k, np.round(k))
+    # chi-square over 40 bins (64000 draws; 99.9% quantile of chi2(39) ~ 72)
+    counts, _ = np.histogram(draws, bins=40, range=(-2, 2))
+    exp = draws.size / 40
+    assert ((counts - exp) ** 2 / exp).sum() < 72.0
+
+
+def test_guess_streams_differ_by_query_slot_round_and_seed():
+    a = O.guess(1, 5, 3, 0, 8)
+    assert not np.array_equal(a, O.guess(1, 6, 3, 0, 8))
+    assert not np.array_equal(a, O.guess(1, 5, 4, 0, 8))
+    assert not np.array_equal(a, O.guess(1, 5, 3, 1, 8))
+    assert not np.array_equal(a, O.guess(2, 5, 3, 0, 8))
+    assert np.array_equal(a, O.guess(1, 5, 3, 0, 8))
+
+
+def test_irwin_hall_guess_moments():
+    v = np.array([O.guess(77, q, 0, 0, 10, 1) for q in range(3000)]).ravel()
+    assert abs(v.mean()) < 0.03 and abs(v.var() - 1.0) < 0.04
+    assert np.abs(v).max() <= 6.0
+    k = (v + 6.0) * 2 ** 24
+    assert np.array_equal(k, np.round(k))
+
+
+# --------------------------------------------------------------------------
+# Functional evaluation (Sec. 4.1), closed forms
+# --------------------------------------------------------------------------
+
+def _p_quad_iso(principle=O.LAX, d=2):
+    return O.Problem(d=d, family=O.FAM_QUAD_ISO, principle=principle, g_kind=O.G_QUAD_SHIFT, a=np.zeros(d))
+
+
+@pytest.mark.parametrize("N", [1, 7, 20])
+def test_quad_iso_lax_functional_closed_form(N):
+    # H = |p|^2/2: p is constant, gamma(0) = x - t v, integrand |p|^2/2,
+    # so F^1(v) = |x - t v|^2/2 + t|v|^2/2 exactly (RK4 is exact here).
+    rng = np.random.default_rng(0)
+    P = _p_quad_iso()
+    for _ in range(10):
+        x, v, t = rng.normal(size=2), rng.normal(size=2), rng.uniform(0.1, 2)
+        F = O.functional(P, x, t, N, v)
+        assert abs(F - (0.5 * np.sum((x - t * v) ** 2) + 0.5 * t * np.sum(v ** 2))) < 1e-13
+
+
+def test_quad_iso_hopf_functional_closed_form():
+    # G(v) = g*(v) + t|v|^2/2 - <x,v> with g* = |p|^2/2 (Sec. 3.4, Example 1).
+    rng = np.random.default_rng(1)
+    P = _p_quad_iso(O.HOPF, d=3)
+    for _ in range(10):
+        x, v, t = rng.normal(size=3), rng.normal(size=3), rng.uniform(0.1, 2)
+        G = O.functional(P, x, t, 9, v)
+        assert abs(G - (0.5 * (1 + t) * np.sum(v ** 2) - x @ v)) < 1e-13
+
+
+def test_rect_rule_equals_rk4_when_integrand_is_constant():
+    # for H = |p|^2/2 the integrand is constant along characteristics, so the
+    # rectangle rule of eq. num_int is exact as well
+    P = _p_quad_iso()
+    x, v = np.array([0.3, -1.0]), np.array([1.1, 0.4])
+    assert abs(O.functional(P, x, 0.8, 13, v, quad=O.QUAD_RECT) - O.functional(P, x, 0.8, 13, v)) < 1e-13
+
+
+def test_state_independent_nonconvex_matches_classical_hopf_formula():
+    # w = 0 makes c = 1 and H = Phi(p) state independent: p is constant,
+    # G(v) = sum_i sigma_i^2 v_i^2/2 + t Phi(v) - <x,v> (Sec. 3.4, Example 1)
+    rng = np.random.default_rng(2)
+    d = 20
+    sig = rng.uniform(0.5, 2, d)
+    P = O.Problem(d=d, family=O.FAM_SMOOTH_NONCONVEX, principle=O.HOPF, g_kind=O.G_DIAG_QUAD, w=np.zeros(d),
+                  sigma=sig, n_neg=1, s_eps=1e-6)
+    e = np.ones(d)
+    e[0] = -1
+    for _ in range(5):
+        x, v = rng.uniform(-1, 1, d), rng.uniform(-2, 2, d)
+        s = np.sqrt(v * v + 1e-6)
+        expect = np.sum(0.5 * sig ** 2 * v ** 2) + 0.5 * np.sum(e * s) - x @ v
+        assert abs(O.functional(P, x, 0.5, 64, v) - expect) < 1e-12
+
+
+def test_speed_quad_with_zero_w_matches_hopf_lax_closed_form():
+    # w = 0: H = |p|^2/2, g = |x-a|^2/2, so phi = |x-a|^2 / (2(1+t)) and the
+    # minimiser is v = (x-a)/(1+t); F^1 at the minimiser equals phi.
+    rng = np.random.default_rng(3)
+    d = 10
+    a = rng.uniform(-1, 1, d)
+    for principle in (O.LAX, O.HOPF):
+        P = O.Problem(d=d, family=O.FAM_SPEED_QUAD, principle=principle, g_kind=O.G_QUAD_SHIFT, w=np.zeros(d), a=a)
+        for t in (0.25, 1.0):
+            x = rng.uniform(-2, 2, d)
+            vstar = (x - a) / (1 + t)
+            F = O.functional(P, x, t, 50, vstar)
+            phi = np.sum((x - a) ** 2) / (2 * (1 + t))
+            assert abs((F if principle == O.LAX else -F) - phi) < 1e-12
+
+
+def test_linear_quadratic_functional_at_riccati_optimum():
+    # At v = grad phi(x,t) = P(t) x the Lax functional equals phi = x^T P x/2,
+    # up to the O(h^4) RK4 error; its gradient vanishes there.
+    wl = W.c4_linear_quad(nq=4)
+    spec = wl.problems[0]
+    P = oracle_problem(spec)
+    Pt = pins.riccati_P(spec.A, spec.B, 1.0)
+    for q in range(2):
+        x = wl.x[q]
+        vstar = Pt @ x
+        F, g = O.gradient(P, x, 1.0, 100, vstar)
+        phi = 0.5 * x @ Pt @ x
+        assert rel_err(F, phi) < 1e-8
+        assert np.abs(g).max() < 1e-6
+
+
+def test_riccati_pin_itself_matches_ode_integration():
+    rng = np.random.default_rng(4)
+    d = 6
+    A = rng.normal(size=(d, d)) * 0.3
+    B = rng.normal(size=(d, 3)) / math.sqrt(d)
+    rhs = lambda s, y: (-(A.T @ y.reshape(d, d) + y.reshape(d, d) @ A)
+                        - y.reshape(d, d) @ B @ B.T @ y.reshape(d, d)).ravel()
+    sol = scipy.integrate.solve_ivp(rhs, (0, 1.0), np.eye(d).ravel(), rtol=1e-12, atol=1e-12)
+    assert np.abs(sol.y[:, -1].reshape(d, d) - pins.riccati_P(A, B, 1.0)).max() < 1e-9
+
+
+def test_rk4_fourth_order_convergence_state_dependent():
+    # state-dependent family: |F_N - F_2N| shrinks by ~16 per halving of h
+    rng = np.random.default_rng(5)
+    d = 10
+    P = O.Problem(d=d, family=O.FAM_SPEED_QUAD, principle=O.LAX, g_kind=O.G_QUAD_SHIFT,
+                  w=rng.normal(size=d) / math.sqrt(d), a=rng.uniform(-1, 1, d))
+    x, v = rng.uniform(-2, 2, d), rng.uniform(-1, 1, d)
+    Fs = [O.functional(P, x, 1.0, N, v) for N in (8, 16, 32, 64)]
+    diffs = np.abs(np.diff(Fs))
+    ratios = diffs[:-1] / diffs[1:]
+    assert np.all(ratios > 12) and np.all(ratios < 20)
+
+
+def test_rect_rule_first_order_convergence():
+    # Hopf integrand H - <H_x, gamma> varies along the path (the Lax one of
+    # this family equals H, a constant of motion, so the rule would be exact)
+    rng = np.random.default_rng(6)
+    d = 4
+    P = O.Problem(d=d, family=O.FAM_SPEED_QUAD, principle=O.HOPF, g_kind=O.G_QUAD_SHIFT,
+                  w=rng.normal(size=d), a=rng.uniform(-1, 1, d))
+    x, v = rng.uniform(-1, 1, d), rng.uniform(-1, 1, d)
+    ref = O.functional(P, x, 1.0, 4096, v)
+    e = [abs(O.functional(P, x, 1.0, N, v, quad=O.QUAD_RECT) - ref) for N in (64, 128, 256)]
+    assert 1.7 < e[0] / e[1] < 2.3 and 1.7 < e[1] / e[2] < 2.3
+
+
+# --------------------------------------------------------------------------
+# Gradients: the adjoint against the plain derivative
+# --------------------------------------------------------------------------
+
+def test_adjoint_gradient_closed_form_quad_iso():
+    P = _p_quad_iso()
+    x, v, t = np.array([0.7, -1.3]), np.array([0.2, 0.5]), 1.0
+    F, g = O.gradient(P, x, t, 20, v)
+    assert np.abs(g - (-t * (x - t * v) + t * v)).max() < 1e-13
+
+
+@pytest.mark.parametrize("family,principle,g_kind", [
+    (O.FAM_SPEED_QUAD, O.LAX, O.G_QUAD_SHIFT), (O.FAM_SPEED_QUAD, O.HOPF, O.G_QUAD_SHIFT),
+    (O.FAM_SMOOTH_NONCONVEX, O.HOPF, O.G_DIAG_QUAD), (O.FAM_SMOOTH_NONCONVEX, O.LAX, O.G_DIAG_QUAD),
+    (O.FAM_LINEAR_QUAD, O.LAX, O.G_QUAD_SHIFT), (O.FAM_LINEAR_QUAD, O.HOPF, O.G_QUAD_SHIFT)])
+@pytest.mark.parametrize("quad", [O.QUAD_RK4, O.QUAD_RECT])
+def test_adjoint_gradient_matches_central_differences(family, principle, g_kind, quad):
+    rng = np.random.default_rng(7 + family + 3 * principle)
+    d = 6
+    P = O.Problem(d=d, family=family, principle=principle, g_kind=g_kind, w=rng.normal(size=d) / math.sqrt(d),
+                  a=rng.uniform(-1, 1, d), sigma=rng.uniform(0.5, 2, d), A=rng.normal(size=(d, d)) * 0.2,
+                  B=rng.normal(size=(d, 4)) / math.sqrt(d), n_neg=2, s_eps=1e-2)
+    for _ in range(3):
+        x, v = rng.uniform(-1, 1, d), rng.uniform(-1, 1, d)
+        F, g = O.gradient(P, x, 0.5, 16, v, quad=quad)
+        assert abs(F - O.functional(P, x, 0.5, 16, v, quad=quad)) < 1e-13
+        gfd = O.gradient_fd(P, x, 0.5, 16, v, h=1e-5, quad=quad)
+        assert np.abs(g - gfd).max() <= 1e-7 * (1 + np.abs(gfd).max())
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1 and the gradient form
+# --------------------------------------------------------------------------
+
+def test_cyclic_cd_contracts_exactly_on_quadratic():
+    # F^1 = |x - t v|^2/2 + t|v|^2/2 is separable with curvature t^2 + t, so
+    # each visit of coordinate j maps v_j - v*_j to (1 - alpha (t^2+t)) (v_j - v*_j)
+    P = _p_quad_iso()
+    x, t, alpha = np.array([1.5, -0.5]), 1.0, 0.1
+    v0 = np.array([-1.0, 2.0])
+    vstar = x / (1 + t)
+    O_ = O.Opts(descent=O.DESC_CD, grad=O.GRAD_FD_CENTRAL, fd_h=1e-4, step=alpha, max_iters=2 * 7, eps=0.0)
+    v, it, cap, nf = O.descend(P, O_, x, t, 20, v0)
+    expect = vstar + (1 - alpha * (t * t + t)) ** 7 * (v0 - vstar)
+    assert it == 14 and cap and not nf
+    assert np.abs(v - expect).max() < 1e-9
+
+
+def test_cd_halving_period_halves_alpha():
+    P = _p_quad_iso()
+    x, t = np.array([1.5, -0.5]), 1.0
+    v0 = np.array([-1.0, 2.0])
+    vstar = x / (1 + t)
+    # M = 2 iterations = one sweep per halving; sweep k uses alpha/2^k
+    O_ = O.Opts(descent=O.DESC_CD, grad=O.GRAD_FD_CENTRAL, fd_h=1e-4, step=0.4, max_iters=2 * 4,
+                halving_period=2, eps=0.0)
+    v, *_ = O.descend(P, O_, x, t, 20, v0)
+    fac = np.prod([1 - 0.4 / 2 ** k * 2.0 for k in range(4)])
+    assert np.abs(v - (vstar + fac * (v0 - vstar))).max() < 1e-9
+
+
+def test_cd_stops_after_d_small_steps():
+    P = _p_quad_iso()
+    x = np.array([1.0, 1.0])
+    O_ = O.Opts(descent=O.DESC_CD, grad=O.GRAD_FD_CENTRAL, fd_h=1e-4, step=0.5, max_iters=10000, eps=1e-9)
+    v, it, cap, _ = O.descend(P, O_, x, 1.0, 20, np.zeros(2))
+    # alpha (t^2+t) = 1: exact in one visit per coordinate, then d small steps
+    assert not cap and it == 4
+    assert np.abs(v - x / 2).max() < 1e-9
+
+
+def _gd_rule_reference(grad, v0, O_):
+    """The per-coordinate sign-change step rule stepped by hand."""
+    v = v0.copy()
+    alpha = np.full(v.size, O_.step)
+    gprev = np.zeros(v.size)
+    for it in range(O_.max_iters):
+        g = grad(v)
+        prod = g * gprev
+        alpha = np.where(prod < 0, alpha * O_.shrink, np.where(prod > 0, np.minimum(alpha * O_.grow, O_.step_max), alpha))
+        step = alpha * g
+        v = v - step
+        gprev = g
+        if np.abs(step).max() <= O_.eps:
+            return v, it + 1
+    return v, O_.max_iters
+
+
+def test_gradient_descent_rule_on_closed_form():
+    P = _p_quad_iso(d=2)
+    x, t = np.array([1.2, -0.7]), 0.5
+    O_ = O.Opts(descent=O.DESC_GD, grad=O.GRAD_ADJOINT, step=0.9, max_iters=60, eps=1e-12, adapt=1, grow=1.3,
+                shrink=0.5, step_max=3.0)
+    v0 = np.array([2.0, -2.0])
+    v, it, cap, _ = O.descend(P, O_, x, t, 11, v0)
+    vr, itr = _gd_rule_reference(lambda v: -t * (x - t * v) + t * v, v0, O_)
+    assert it == itr
+    assert np.abs(v - vr).max() < 1e-10
+
+
+# --------------------------------------------------------------------------
+# Certificate (Sec. 4.3)
+# --------------------------------------------------------------------------
+
+def test_certificate_residual_closed_form():
+    P = _p_quad_iso()
+    x, t = np.array([0.4, -1.2]), 1.0
+    v = np.array([0.3, 0.1])
+    F, r, ok = O.certify(P, x, t, 20, v, 1e-3)
+    g0, p0 = x - t * v, v
+    assert abs(r - np.linalg.norm(p0 - g0) / (1 + np.linalg.norm(p0))) < 1e-14 and not ok
+    F, r, ok = O.certify(P, x, t, 20, x / (1 + t), 1e-3)
+    assert r < 1e-14 and ok
+
+
+def test_certificate_hopf_residual_is_minus_gradient_when_state_independent():
+    # with c = 1, gamma(0) - grad g*(p(0)) = x - t Phi'(v) - sigma^2 v = -grad G
+    rng = np.random.default_rng(8)
+    d = 5
+    P = O.Problem(d=d, family=O.FAM_SMOOTH_NONCONVEX, principle=O.HOPF, g_kind=O.G_DIAG_QUAD, w=np.zeros(d),
+                  sigma=rng.uniform(0.5, 2, d))
+    x, v = rng.uniform(-1, 1, d), rng.uniform(-1, 1, d)
+    F, g = O.gradient(P, x, 0.5, 8, v)
+    F2, g0, p0 = O.functional(P, x, 0.5, 8, v, with_ends=True)
+    _, r, _ = O.certify(P, x, 0.5, 8, v, 1e-3)
+    assert abs(r - np.linalg.norm(g) / (1 + np.linalg.norm(g0))) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Whole solve against closed forms
+# --------------------------------------------------------------------------
+
+def test_solve_quad_iso_workload_closed_form():
+    wl = W.c1_quad_iso()
+    P = oracle_problem(wl.problems[0])
+    res = O.solve(P, oracle_opts(wl.solver, 4), wl.x, wl.t, wl.n_steps)
+    phi = np.sum(wl.x ** 2, axis=1) / 4.0
+    assert np.abs(res["phi"] - phi).max() < 1e-12
+    assert np.abs(res["v"] - wl.x / 2.0).max() < 1e-10
+    assert np.all(res["status"] & O.ST_CERTIFIED)
+
+
+def test_solve_state_independent_d20_hopf_matches_brute_force():
+    # the d=20 non-convex Hopf workload with w = 0 separates into 1-D problems
+    # (classical Hopf formula, Sec. 3.4 Example 1); -s(v_1) makes a double well
+    wl = W.c3_smooth_nonconvex(nq=6)
+    spec = wl.problems[0]
+    spec0 = W.ProblemSpec(d=20, family=spec.family, principle=spec.principle, g_kind=spec.g_kind,
+                          w=np.zeros(20), sigma=spec.sigma, n_neg=1, s_eps=1e-6, n_guesses=16)
+    P = oracle_problem(spec0)
+    opts = oracle_opts(dict(wl.solver, eps=1e-10, max_iters=2000), 16)
+    res = O.solve(P, opts, wl.x, wl.t, wl.n_steps)
+    e = np.ones(20)
+    e[0] = -1
+    for q in range(wl.nq):
+        mins = [pins.separable_hopf_min(spec.sigma[i] ** 2, e[i], 0.5, wl.x[q, i], 1e-6) for i in range(20)]
+        assert abs(res["phi"][q] - (-sum(mins))) < 1e-8
+    assert np.all(res["status"] & O.ST_CERTIFIED)
+
+
+def test_solve_linear_quadratic_matches_riccati():
+    # full-rank B keeps the quadratic functional well conditioned, so the
+    # descent converges and the discrete optimum is within O(h^4) of the
+    # Riccati value (rank-deficient B gives condition numbers ~1e4)
+    rng = np.random.default_rng(9)
+    d = 8
+    G0 = rng.normal(size=(d, d))
+    A = G0 / (2 * np.linalg.norm(G0, 2))
+    B = np.eye(d) + rng.normal(size=(d, d)) / (2 * math.sqrt(d))
+    P = O.Problem(d=d, family=O.FAM_LINEAR_QUAD, principle=O.LAX, g_kind=O.G_QUAD_SHIFT, A=A, B=B, a=np.zeros(d))
+    X = rng.normal(size=(4, d))
+    opts = oracle_opts(W.solver_constants(eps=1e-11, max_iters=3000, n_guesses=1), 1)
+    res = O.solve(P, opts, X, 1.0, 100)
+    Pt = pins.riccati_P(A, B, 1.0)
+    phi = 0.5 * np.einsum("qi,ij,qj->q", X, Pt, X)
+    assert np.all(rel_err(res["phi"], phi) < 1e-7)
+
+
+def test_lax_and_hopf_agree_for_convex_state_dependent_problem():
+    # both principles represent the same viscosity solution when H is convex
+    # in p and g is convex (Sec. 1): the d=10 speed-quadratic family
+    wl = W.c2_speed_quad(nq_x=3)
+    spec = wl.problems[0]
+    res = {}
+    for principle in (O.LAX, O.HOPF):
+        sp = W.ProblemSpec(**{**spec.__dict__, "principle": principle})
+        opts = oracle_opts(dict(wl.solver, eps=1e-10, max_iters=3000), 8)
+        res[principle] = O.solve(oracle_problem(sp), opts, wl.x, wl.t, wl.n_steps)["phi"]
+    assert np.all(rel_err(res[O.HOPF], res[O.LAX]) < 1e-7)
+
+
+# --------------------------------------------------------------------------
+# Best-of-guesses and reseeding (Sec. 4.3, Sec. 5)
+# --------------------------------------------------------------------------
+
+def test_failed_certificates_spend_exactly_the_trial_budget():
+    wl = W.c3_smooth_nonconvex(nq=2)
+    P = oracle_problem(wl.problems[0])
+    opts = oracle_opts(dict(wl.solver, cert_tol=0.0, max_iters=5, max_trials=20, max_rounds=3), 16)
+    res = O.solve(P, opts, wl.x, wl.t, wl.n_steps)
+    # 16 slots in round 0, then slots 0..3 reseeded once in round 1; none passes
+    for q in range(2):
+        assert list(res["slot_round"][q]) == [1] * 4 + [0] * 12
+        assert not np.any(res["slot_pass"][q])
+        assert res["status"][q] & O.ST_RESEEDED and not res["status"][q] & O.ST_CERTIFIED
+    opts2 = oracle_opts(dict(wl.solver, cert_tol=0.0, max_iters=5, max_trials=40, max_rounds=3), 16)
+    res2 = O.solve(P, opts2, wl.x, wl.t, wl.n_steps)
+    assert list(res2["slot_round"][0]) == [2] * 8 + [1] * 8
+
+
+def test_best_of_guesses_picks_global_minimum_of_double_well():
+    # 1-D, w = 0: G(v) = sigma^2 v^2/2 - t s(v) - x v has minima near
+    # (x +- t)/sigma^2; the deeper one has the sign of x.  Guesses from
+    # both wells must resolve to the deeper well's value.
+    P = O.Problem(d=1, family=O.FAM_SMOOTH_NONCONVEX, principle=O.HOPF, g_kind=O.G_DIAG_QUAD, w=np.zeros(1),
+                  sigma=np.array([1.0]), n_neg=1, s_eps=1e-6)
+    opts = O.Opts(descent=O.DESC_GD, grad=O.GRAD_ADJOINT, step=0.05, max_iters=2000, eps=1e-12, adapt=1,
+                  grow=1.2, shrink=0.5, step_max=1.0, n_guesses=16, max_trials=16, seed=3, cert_tol=1e-3)
+    x = np.array([[0.3]])
+    res = O.solve(P, opts, x, 0.5, 32)
+    wells = {round(float(v), 3) for v in res["slot_v"][0, :, 0]}
+    assert len(wells) == 2  # both wells were reached by some guess
+    brute = pins.separable_hopf_min(1.0, -1.0, 0.5, 0.3, 1e-6)
+    assert abs(res["phi"][0] + brute) < 1e-10
+
+
+# --------------------------------------------------------------------------
+# Truth checks for state-dependent problems: Lax-Friedrichs (Sec. 5) and the
+# HJ equation itself
+# --------------------------------------------------------------------------
+
+def _lf_speed_quad_1d(w, a, t, dx):
+    H = lambda X, P: 0.5 * (1 + 0.5 * np.sin(w * X[0])) ** 2 * P[0] ** 2
+    g = lambda X: 0.5 * (X[0] - a) ** 2
+    # |dH/dp| = c^2 |p| <= 2.25 * 3.2 on the box
+    return pins.lax_friedrichs(H, 7.5, g, -3.0, 3.0, dx, t, 1)
+
+
+def test_state_dependent_1d_lax_matches_lax_friedrichs_first_order():
+    # LF is first order: its error halves with dx, and the Richardson
+    # extrapolation 2 LF(dx/2) - LF(dx) must land on the oracle's value
+    w, a, t = 1.3, 0.2, 0.5
+    P = O.Problem(d=1, family=O.FAM_SPEED_QUAD, principle=O.LAX, g_kind=O.G_QUAD_SHIFT, w=np.array([w]),
+                  a=np.array([a]))
+    opts = O.Opts(descent=O.DESC_GD, grad=O.GRAD_ADJOINT, step=0.05, max_iters=3000, eps=1e-12, adapt=1,
+                  grow=1.2, shrink=0.5, step_max=1.0, n_guesses=4, max_trials=4, seed=1, cert_tol=1e-3)
+    xq = np.linspace(-1.0, 1.0, 9)
+    phi = O.solve(P, opts, xq[:, None], t, 200)["phi"]
+    lf = {}
+    for dx in (0.01, 0.005, 0.0025):
+        xs, sol = _lf_speed_quad_1d(w, a, t, dx)
+        lf[dx] = np.interp(xq, xs, sol)
+    e = {dx: np.abs(lf[dx] - phi).max() for dx in lf}
+    assert 1.8 < e[0.01] / e[0.005] < 2.2 and 1.8 < e[0.005] / e[0.0025] < 2.2
+    assert np.abs(2 * lf[0.0025] - lf[0.005] - phi).max() < 5e-4
+
+
+def test_state_dependent_2d_nonconvex_hopf_matches_lax_friedrichs():
+    # d = 2, H = c(x)(-s(p_1) + s(p_2)), g = sum x_i^2/(2 sigma_i^2) (the
+    # d=20 workload's family at d = 2), against the monotone scheme
+    w = np.array([0.8, -0.5])
+    sig = np.array([1.2, 0.8])
+    t = 0.3
+    P = O.Problem(d=2, family=O.FAM_SMOOTH_NONCONVEX, principle=O.HOPF, g_kind=O.G_DIAG_QUAD, w=w, sigma=sig,
+                  n_neg=1, s_eps=1e-6)
+    opts = O.Opts(descent=O.DESC_GD, grad=O.GRAD_ADJOINT, step=0.05, max_iters=3000, eps=1e-12, adapt=1,
+                  grow=1.2, shrink=0.5, step_max=1.0, n_guesses=16, max_trials=20, max_rounds=2, seed=2,
+                  cert_tol=1e-3)
+    rng = np.random.default_rng(10)
+    xq = rng.uniform(-0.8, 0.8, (8, 2))
+    phi = O.solve(P, opts, xq, t, 60)["phi"]
+
+    def H(X, Pg):
+        c = 1 + 0.5 * np.sin(w[0] * X[0] + w[1] * X[1])
+        return c * (-np.sqrt(Pg[0] ** 2 + 1e-6) + np.sqrt(Pg[1] ** 2 + 1e-6))
+
+    g = lambda X: 0.5 * (X[0] ** 2 / sig[0] ** 2 + X[1] ** 2 / sig[1] ** 2)
+    from scipy.interpolate import RegularGridInterpolator
+    lf = {}
+    for dx in (0.04, 0.02):
+        xs, sol = pins.lax_friedrichs(H, 1.5, g, -2.5, 2.5, dx, t, 2)
+        lf[dx] = RegularGridInterpolator((xs, xs), sol)(xq)
+    e = {dx: np.abs(lf[dx] - phi).max() for dx in lf}
+    assert 1.5 < e[0.04] / e[0.02] < 2.5
+    assert np.abs(2 * lf[0.02] - lf[0.04] - phi).max() < 0.25 * e[0.02]
+
+
+def test_d20_nonconvex_solution_satisfies_hj_equation():
+    # where phi is smooth, phi_t + H(x, grad phi) = 0 and the returned v
+    # equals grad phi (Sec. 1, the arg-optimum is grad phi); checked with
+    # central differences of the oracle's phi in (x, t) on the d=20 workload
+    wl = W.c3_smooth_nonconvex(nq=2)
+    spec = wl.problems[0]
+    P = oracle_problem(spec)
+    opts = oracle_opts(dict(wl.solver, eps=1e-12, max_iters=3000), 16)
+    d, h = 20, 1e-3
+    for q in range(wl.nq):
+        x = wl.x[q]
+        base = O.solve(P, opts, x[None], 0.5, 64)
+        v = base["v"][0]
+        pts = [x + h * np.eye(d)[i] for i in range(d)] + [x - h * np.eye(d)[i] for i in range(d)]
+        ph = O.solve(P, opts, np.array(pts), 0.5, 64)["phi"]
+        grad = (ph[:d] - ph[d:]) / (2 * h)
+        pt = O.solve(P, opts, np.array([x, x]), np.array([0.5 + h, 0.5 - h]), 64)["phi"]
+        phit = (pt[0] - pt[1]) / (2 * h)
+        c = 1 + 0.5 * np.sin(spec.w @ x)
+        e = np.ones(d)
+        e[0] = -1
+        Hval = c * np.sum(e * np.sqrt(grad ** 2 + 1e-6))
+        assert abs(phit + Hval) < 2e-3 * (1 + abs(phit))
+        assert np.abs(grad - v).max() < 2e-3
