@@ -1,0 +1,259 @@
+/*
+ * hj.h -- C ABI of the GB300 (sm_103a) solver for state-dependent
+ * Hamilton-Jacobi equations by the generalized Lax minimisation and Hopf
+ * maximisation principles of Chow, Darbon, Osher and Yin (arXiv 1704.02524).
+ *
+ * The equation is phi_t + H(x, grad phi) = 0, phi(x, 0) = g(x) (Sec. 2.1).
+ * For a query (x, t) and a vector v the library integrates the
+ * bi-characteristics (Sec. 4.1)
+ *      d gamma/ds = dH/dp(gamma, p),  dp/ds = -dH/dx(gamma, p),
+ *      gamma(t) = x,  p(t) = v,
+ * backward from s = t to s = 0 with N classical RK4 steps, and evaluates
+ *   Lax  (convex H, eq. lax_formula):
+ *      F(v) = g(gamma(0)) + int_0^t ( <p, dH/dp> - H ) ds,       phi = min_v F
+ *   Hopf (g convex, eq. hopf_formula):
+ *      G(v) = g*(p(0)) + int_0^t ( H - <dH/dx, gamma> ) ds - <x, v>,
+ *                                                                phi = -min_v G
+ * It minimises over v by the paper's cyclic coordinate descent with
+ * finite differences (Algorithm 1, eq. num_diff) or by gradient descent with
+ * the exact gradient of the discretised functional (discrete adjoint of
+ * RK4), checks the certificate p(0) in dg(gamma(0)) (Sec. 4.3), reseeds
+ * failed starts and keeps the best of several random guesses (Sec. 5).
+ *
+ * Conventions for every entry point below
+ *  - Array arguments are DEVICE pointers owned by the caller, contiguous,
+ *    row-major, on the context's device, unless a comment says "host".
+ *  - Element type of x, t, v, F, grad: float when opts.precision is
+ *    HJ_PREC_FP32, double when HJ_PREC_FP64.  phi, residuals: double.
+ *  - Vectors of a query are rows of length ld = the largest d over the
+ *    context's problems; a row of a problem with smaller d uses its first d
+ *    entries (the rest is ignored on input and left untouched on output).
+ *  - problem_idx (int32 [n], nullable = all 0) selects the problem of each
+ *    row; n_steps (int32 [n], nullable = opts.n_steps_default) its RK4 step
+ *    count N.  t must be > 0, N in [1, 256].
+ *  - Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream).  Argument errors are detected on the host and
+ *    returned before anything is enqueued; the message is available from
+ *    hj_last_error().  Non-convergence is reported per query in the status
+ *    bits, never by trapping.
+ *  - A context is not thread safe: serialise calls that share one.
+ */
+#ifndef HJ_H
+#define HJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hj_ctx hj_ctx;
+
+typedef enum {
+    HJ_OK = 0,
+    HJ_EINVAL = 1,        /* invalid argument (message in hj_last_error)        */
+    HJ_ENOMEM = 2,        /* device or host allocation failed                   */
+    HJ_ECUDA = 3,         /* a CUDA call failed                                 */
+    HJ_ETIMEOUT = 4,      /* reserved: a bounded device wait ran out            */
+    HJ_EUNSUPPORTED = 5   /* combination not built into this library            */
+} hj_status;
+
+/* Hamiltonian families (per-family parameters in hj_problem_desc.params). */
+typedef enum {
+    HJ_FAM_QUAD_ISO = 0,         /* H = |p|^2/2                                              */
+    HJ_FAM_SPEED_QUAD = 1,       /* H = c(x)^2 |p|^2/2,  c = 1 + sin(<w,x>)/2                 */
+    HJ_FAM_SMOOTH_NONCONVEX = 2, /* H = c(x) sum_i e_i s(p_i), s(q) = sqrt(q^2 + s_eps),
+                                    e_i = -1 for i < n_neg, +1 otherwise                       */
+    HJ_FAM_LINEAR_QUAD = 3       /* H = <A x, p> + |B^T p|^2/2                               */
+} hj_family;
+
+typedef enum { HJ_LAX = 0, HJ_HOPF = 1 } hj_principle;
+
+/* Initial data g. */
+typedef enum {
+    HJ_G_QUAD_SHIFT = 0,  /* g = |x - a|^2/2,          g* = |p|^2/2 + <a,p>       */
+    HJ_G_DIAG_QUAD = 1    /* g = sum x_i^2/(2 s_i^2),  g* = sum s_i^2 p_i^2/2     */
+} hj_initial;
+
+typedef enum {
+    HJ_GRAD_FD_CENTRAL = 0, /* cyclic coordinate descent, (F(v+he)-F(v-he))/2h            */
+    HJ_GRAD_FD_FORWARD = 1, /* cyclic coordinate descent, (F(v+he)-F(v))/h  (eq. num_diff) */
+    HJ_GRAD_ADJOINT = 2     /* gradient descent with the discrete-adjoint gradient         */
+} hj_grad_mode;
+
+typedef enum {
+    HJ_QUAD_RK4 = 0,  /* running cost integrated by RK4 on an augmented state          */
+    HJ_QUAD_RECT = 1  /* rectangle rule on the solver mesh, nodes s_i = i t/N, i<N     */
+} hj_quad_mode;
+
+typedef enum { HJ_PREC_FP32 = 0, HJ_PREC_FP64 = 1 } hj_precision;
+
+/* Per-query status bits written by hj_solve. */
+#define HJ_ST_CERTIFIED 1  /* the returned start passed the certificate           */
+#define HJ_ST_MAX_ITERS 2  /* the returned start stopped at the iteration cap     */
+#define HJ_ST_NONFINITE 4  /* some start produced a non-finite value              */
+#define HJ_ST_RESEEDED 8   /* at least one failed start was restarted             */
+
+/*
+ * One problem: a Hamiltonian family instance and its initial data.
+ * params (HOST, double, copied by hj_create) holds, in order:
+ *   family block:  SPEED_QUAD, SMOOTH_NONCONVEX: w[d]
+ *                  LINEAR_QUAD: A[d*d] (row-major), then B[d*m] (row-major)
+ *                  QUAD_ISO: nothing
+ *   g block:       HJ_G_QUAD_SHIFT: a[d];  HJ_G_DIAG_QUAD: s[d] (all > 0)
+ * n_params must equal the total.  d in [1, 1024]; m in [1, 64] for
+ * LINEAR_QUAD (d in [1, 128] there), else ignored.
+ */
+typedef struct {
+    int d;
+    hj_family family;
+    hj_principle principle;
+    hj_initial g_kind;
+    int m;             /* LINEAR_QUAD: columns of B                             */
+    int n_neg;         /* SMOOTH_NONCONVEX: number of leading negative signs     */
+    double s_eps;      /* SMOOTH_NONCONVEX: smoothing of |q|, > 0                */
+    int n_guesses;     /* random starts per query for hj_solve (0: opts value)   */
+    const double *params;
+    size_t n_params;
+} hj_problem_desc;
+
+/*
+ * Solver constants.  Names follow Algorithm 1: step = alpha = 1/L; every
+ * `halving_period` iterations alpha is halved (0: never); the descent stops
+ * when every move of a full sweep is smaller than `eps` (coordinate descent:
+ * d consecutive coordinate moves, a move larger than eps restarting the
+ * count; gradient descent: one iteration; eps = 0 never stops early), or at
+ * `max_iters` (coordinate descent counts coordinate moves, gradient descent
+ * counts gradient steps).  With `adapt`, each coordinate keeps its own
+ * alpha_i, multiplied by `shrink` when its derivative changes sign between
+ * consecutive visits and by `grow` (capped at step_max) when it keeps it.
+ * Round 0 of hj_solve runs n_guesses starts per query (Philox4x32-10 draws
+ * keyed by `seed`, counter (component/4, slot | round<<16, query id));
+ * then up to `max_rounds` rounds restart failed starts, in slot order,
+ * while fewer than `max_trials` starts of that query have run.
+ * guess_dist: 0 = uniform on [-2,2]^d (Sec. 5), 1 = Irwin-Hall(12) N(0,1)
+ * approximation.  cert_tol: certificate tolerance on the relative residual
+ *   Lax  |p(0) - grad g(gamma(0))| / (1 + |p(0)|),
+ *   Hopf |gamma(0) - grad g*(p(0))| / (1 + |gamma(0)|).
+ * kahan: compensated summation of the running-cost quadrature.
+ */
+typedef struct {
+    int n_steps_default;
+    hj_quad_mode quad;
+    hj_grad_mode grad;
+    double fd_h;
+    double step;
+    int max_iters;
+    int halving_period;
+    double eps;
+    int adapt;
+    double grow;
+    double shrink;
+    double step_max;
+    int n_guesses;
+    int max_trials;
+    int max_rounds;
+    uint64_t seed;
+    int guess_dist;
+    double cert_tol;
+    hj_precision precision;
+    int kahan;
+} hj_solver_opts;
+
+/* Counters and device timings of the last hj_solve on a context
+ * (hj_last_solve_info); times come from CUDA events on the solve's stream. */
+typedef struct {
+    int64_t n_queries;
+    int64_t n_pairs;            /* (query, start) pairs run, reseeds included      */
+    int64_t iterations;         /* descent iterations summed over pairs             */
+    int64_t functional_evals;   /* forward functional evaluations                   */
+    int64_t gradient_evals;     /* adjoint gradients                                */
+    int64_t rk4_steps;          /* RK4 steps of all evaluations (forward sweeps)    */
+    double algorithmic_flops;   /* fp32/fp64 arithmetic of the descent, FMA = 2     */
+    double certify_flops;       /* FP64 arithmetic of the certificate evaluations   */
+    int threads_per_pair;       /* of the first problem's descent launch            */
+    int comps_per_thread;
+    int descent_launches;       /* rounds run (each: one descent launch per problem) */
+    double descent_ms;          /* device time of the descent launches (CUDA events) */
+    double certify_ms;          /* device time of the certificate launches           */
+    double total_ms;            /* device time of the whole hj_solve                 */
+} hj_solve_info;
+
+/*
+ * hj_create -- copy the problems and options to `cuda_device`, validate them
+ * and return a context in *out.  The context owns its parameter copies and
+ * its scratch memory; the caller owns every I/O buffer.
+ * Errors: HJ_EINVAL (bad description; *out untouched), HJ_ENOMEM, HJ_ECUDA.
+ */
+hj_status hj_create(const hj_problem_desc *problems, int n_problems, const hj_solver_opts *opts,
+                    int cuda_device, hj_ctx **out);
+
+/* hj_destroy -- synchronise the device and free the context. */
+hj_status hj_destroy(hj_ctx *ctx);
+
+/*
+ * hj_eval_functional -- F (Lax) or G (Hopf) of Sec. 4.1 at n (x, t, v):
+ * x, v [n, ld], t [n], F_out [n].
+ */
+hj_status hj_eval_functional(hj_ctx *ctx, int64_t n, const int32_t *problem_idx, const void *x, const void *t,
+                             const int32_t *n_steps, const void *v, void *F_out, void *stream);
+
+/*
+ * hj_grad -- F and its exact gradient dF/dv of the discretised functional
+ * (discrete adjoint of the RK4 map with sqrt(N)-step checkpointing):
+ * F_out [n] (nullable), grad_out [n, ld].
+ */
+hj_status hj_grad(hj_ctx *ctx, int64_t n, const int32_t *problem_idx, const void *x, const void *t,
+                  const int32_t *n_steps, const void *v, void *F_out, void *grad_out, void *stream);
+
+/*
+ * hj_certify -- the certificate of Sec. 4.3 at n (x, t, v), always in FP64
+ * (v is read in the context precision): residual_out [n] (relative
+ * residual above), pass_out [n] (1 iff residual <= opts.cert_tol and the
+ * value is finite), F_out [n] (double, nullable): the FP64 functional.
+ */
+hj_status hj_certify(hj_ctx *ctx, int64_t n, const int32_t *problem_idx, const void *x, const void *t,
+                     const int32_t *n_steps, const void *v, double *residual_out, uint8_t *pass_out,
+                     double *F_out, void *stream);
+
+/*
+ * hj_solve -- phi(x, t) for n_queries queries: random starts, descent,
+ * certificate, reseeding, best of the starts (certified first; ties go to
+ * the lowest slot), phi from the FP64 value at the chosen v.
+ * q_begin: global index of the first query (the Philox counter uses
+ * q_begin + row), so a batch split across devices draws the same starts.
+ * phi_out [nq] double, v_out [nq, ld] (the chosen v, an estimate of
+ * grad phi), status_out [nq] int32 (HJ_ST_* bits).
+ */
+hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_t *problem_idx, const void *x,
+                   const void *t, const int32_t *n_steps, double *phi_out, void *v_out, int32_t *status_out,
+                   void *stream);
+
+/*
+ * hj_guesses -- the initial guesses hj_solve draws, for testing the
+ * counter-based generator: for each of n entries, the start of query id
+ * query_id[i] (int64), slot slot[i], round round[i] (int32) for problem
+ * problem_idx[i] (nullable): v_out [n, ld].
+ */
+hj_status hj_guesses(hj_ctx *ctx, int64_t n, const int64_t *query_id, const int32_t *slot, const int32_t *round,
+                     const int32_t *problem_idx, void *v_out, void *stream);
+
+/* hj_last_solve_info -- counters of the last hj_solve (synchronises its stream). */
+hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out);
+
+/*
+ * hj_set_launch -- override the threads per (query, start) pair used for
+ * problem `problem` (tpp in {1,2,4,8,16,32}; 0 restores the automatic
+ * choice).  Returns HJ_EUNSUPPORTED when no kernel is built for the
+ * resulting components per thread.
+ */
+hj_status hj_set_launch(hj_ctx *ctx, int problem, int tpp);
+
+/* Message of the last error on ctx (or of the last failed hj_create when ctx is NULL). */
+const char *hj_last_error(const hj_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HJ_H */

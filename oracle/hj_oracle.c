@@ -553,13 +553,14 @@ void orc_gradient_fd(const orc_problem *P, int quad, const double *x, double t, 
 /* ------------------------------------------------------------------------ */
 
 /* Algorithm 1, cyclic coordinate descent, read as follows.  alpha = step;
- * at iteration k the coordinate j_k = k mod d moves by alpha * dF/dv_j; the
- * counter of consecutive steps with |dv_j| <= eps resets on a larger step,
- * and the descent stops when it reaches d (a full sweep of small steps);
+ * at iteration k the coordinate j_k = k mod d moves by alpha * dF/dv_j; a
+ * move |dv_j| > eps resets the counter, a move |dv_j| < eps increments it
+ * (both strict, as in steps 3-4; eps = 0 therefore never stops early), and
+ * the descent stops when it reaches d (a full sweep of small moves);
  * every `halving_period` iterations alpha is halved; max_iters caps k.
  * Gradient form: every iteration moves all coordinates by alpha_i dF/dv_i
  * with the adjoint gradient; it stops after one iteration whose largest
- * move is <= eps.
+ * move is < eps.
  * Per-coordinate step control (`adapt`, both forms): each coordinate keeps
  * its own alpha_i.  When its derivative changes sign between two
  * consecutive visits (an overshoot) alpha_i is multiplied by `shrink`; when
@@ -591,7 +592,9 @@ int orc_descend(const orc_problem *P, const orc_opts *O, const double *x, double
             double step = alpha[j] * dj;
             if (!isfinite(step)) { *nonfinite = 1; return it + 1; }
             v[j] -= step;
-            if (fabs(step) > O->eps) count = 0; else count += 1;
+            /* steps 3-4: reset on a move > eps, count a move < eps (strict) */
+            if (fabs(step) > O->eps) count = 0;
+            else if (fabs(step) < O->eps) count += 1;
             if (O->halving_period > 0 && ++k_in_period == O->halving_period) {
                 k_in_period = 0;
                 for (int i = 0; i < d; ++i) alpha[i] *= 0.5;
@@ -622,7 +625,7 @@ int orc_descend(const orc_problem *P, const orc_opts *O, const double *x, double
             }
             if (O->halving_period > 0 && (it + 1) % O->halving_period == 0)
                 for (int i = 0; i < d; ++i) alpha[i] *= 0.5;
-            if (big <= O->eps) { free(g); return it + 1; }
+            if (big < O->eps) { free(g); return it + 1; }
         }
         free(g);
         *hit_cap = 1;

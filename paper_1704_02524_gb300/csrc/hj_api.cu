@@ -1,0 +1,853 @@
+// hj_api.cu -- the C ABI of include/hj.h: context, validation, parameter
+// upload, kernel choice and the hj_solve pipeline.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hj.h"
+#include "hj_device.cuh"
+#include "hj_internal.h"
+#include "hj_kernels.cuh"
+#include "hj_sched.h"
+
+namespace hjd {
+void reg_f32_qi_lax(Registry &);
+void reg_f32_qi_hopf(Registry &);
+void reg_f32_sq_lax(Registry &);
+void reg_f32_sq_hopf(Registry &);
+void reg_f32_sn_lax(Registry &);
+void reg_f32_sn_hopf(Registry &);
+void reg_f64_qi_lax(Registry &);
+void reg_f64_qi_hopf(Registry &);
+void reg_f64_sq_lax(Registry &);
+void reg_f64_sq_hopf(Registry &);
+void reg_f64_sn_lax(Registry &);
+void reg_f64_sn_hopf(Registry &);
+
+Registry &registry()
+{
+    static Registry *r = [] {
+        Registry *x = new Registry();
+        reg_f32_qi_lax(*x);
+        reg_f32_qi_hopf(*x);
+        reg_f32_sq_lax(*x);
+        reg_f32_sq_hopf(*x);
+        reg_f32_sn_lax(*x);
+        reg_f32_sn_hopf(*x);
+        reg_f64_qi_lax(*x);
+        reg_f64_qi_hopf(*x);
+        reg_f64_sq_lax(*x);
+        reg_f64_sq_hopf(*x);
+        reg_f64_sn_lax(*x);
+        reg_f64_sn_hopf(*x);
+        return x;
+    }();
+    return *r;
+}
+}  // namespace hjd
+
+using namespace hjd;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+enum Kind { K_EVAL = 0, K_GRAD = 1, K_CD = 2, K_GD = 3, K_CERT = 4 };
+
+// Arithmetic per RK4 step of one pair (FMA = 2, add/mul = 1, sin/cos and
+// rsqrt not counted), from the operations written in hj_device.cuh.
+struct FlopModel {
+    double fwd_step;  // one forward step: 4 field evaluations + stage combinations
+    double adj_step;  // one reverse step: 4 vector-Jacobian products + combinations
+};
+
+FlopModel flop_model(int fam, int pr, int d)
+{
+    double fld = 0, vjp = 0;
+    switch (fam) {
+    case HJ_FAM_QUAD_ISO: fld = 3.0 * d + 1; vjp = 2.0 * d; break;
+    case HJ_FAM_SPEED_QUAD: fld = 6.0 * d + (pr == HJ_HOPF ? 10 : 8); vjp = 12.0 * d + 25; break;
+    case HJ_FAM_SMOOTH_NONCONVEX:
+        fld = (pr == HJ_LAX ? 11.0 : 10.0) * d + 7;
+        vjp = (pr == HJ_LAX ? 28.0 : 22.0) * d + 20;
+        break;
+    default: break;
+    }
+    return FlopModel{4 * fld + 26.0 * d + 12, 4 * vjp + 28.0 * d + 6};
+}
+
+struct DevProblem {
+    void *block32 = nullptr, *block64 = nullptr;
+    ProbDev<float> pf{};
+    ProbDev<double> pd{};
+};
+
+template <typename T>
+void fill_prob(const hj_problem_desc &D, const std::vector<double> &par, int ld, std::vector<T> &host, ProbDev<T> &P)
+{
+    const int d = D.d, m = (D.family == HJ_FAM_LINEAR_QUAD) ? D.m : 0;
+    const size_t nvec = 5 * (size_t)DPAD, nA = (size_t)d * d, nB = (size_t)d * m;
+    host.assign(nvec + (m ? nA + nB : 0), (T)0);
+    T *w = host.data(), *e = w + DPAD, *ga = e + DPAD, *gs2 = ga + DPAD, *gis2 = gs2 + DPAD;
+    size_t off = 0;
+    if (D.family == HJ_FAM_SPEED_QUAD || D.family == HJ_FAM_SMOOTH_NONCONVEX) {
+        for (int i = 0; i < d; ++i) w[i] = (T)par[i];
+        off = d;
+    }
+    if (D.family == HJ_FAM_LINEAR_QUAD) {
+        for (size_t i = 0; i < nA + nB; ++i) host[nvec + i] = (T)par[i];
+        off = nA + nB;
+    }
+    for (int i = 0; i < d; ++i) {
+        e[i] = (T)((i < D.n_neg) ? -1 : 1);
+        if (D.g_kind == HJ_G_QUAD_SHIFT) {
+            ga[i] = (T)par[off + i];
+        } else {
+            const T s = (T)par[off + i];
+            gs2[i] = s * s;
+            gis2[i] = (T)1 / (s * s);
+        }
+    }
+    P.d = d;
+    P.family = D.family;
+    P.principle = D.principle;
+    P.g_kind = D.g_kind;
+    P.m = m;
+    P.n_neg = D.n_neg;
+    P.ld = ld;
+    P.s_eps = (T)D.s_eps;
+}
+
+template <typename T>
+void bind_prob(void *block, int m, ProbDev<T> &P)
+{
+    T *b = (T *)block;
+    P.w = b;
+    P.e = b + DPAD;
+    P.ga = b + 2 * DPAD;
+    P.gs2 = b + 3 * DPAD;
+    P.gis2 = b + 4 * DPAD;
+    P.A = m ? b + 5 * DPAD : nullptr;
+    P.B = m ? b + 5 * DPAD + (size_t)P.d * P.d : nullptr;
+}
+
+}  // namespace
+
+struct hj_ctx {
+    int device = 0, nsm = 0, np = 0, ld = 0, prec = 0, gmax = 1;
+    hj_solver_opts opts{};
+    std::vector<hj_problem_desc> desc;
+    std::vector<std::vector<double>> params;
+    std::vector<DevProblem> dev;
+    std::vector<int> tpp_override;
+    int32_t *d_pg = nullptr, *d_pd = nullptr, *d_pprin = nullptr;
+    // scratch
+    long long cap_q = 0, cap_p = 0;
+    int32_t *starts = nullptr, *pair_base = nullptr, *block_sums = nullptr, *trials = nullptr, *qflags = nullptr;
+    int32_t *pair_q = nullptr, *pair_slot = nullptr, *pair_round = nullptr, *iters = nullptr, *wl = nullptr;
+    uint8_t *flags = nullptr, *pP = nullptr;
+    double *pF = nullptr, *pR = nullptr;
+    void *vfin = nullptr;
+    int32_t *pcount = nullptr, *seg_begin = nullptr, *wl_count = nullptr, *cursor = nullptr;
+    unsigned long long *stats = nullptr;
+    // last solve
+    cudaStream_t last_stream = nullptr;
+    long long last_nq = 0;
+    int last_tpp = 0, last_c = 0;
+    bool timing = true;
+    std::vector<cudaEvent_t> ev_desc, ev_cert;
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
+    int n_desc_ev = 0, n_cert_ev = 0;
+    std::string err;
+};
+
+namespace {
+
+hj_status fail(hj_ctx *ctx, hj_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    else g_create_error = buf;
+    return s;
+}
+
+#define CU(call)                                                                                \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? HJ_ENOMEM : HJ_ECUDA, "%s: %s (%s:%d)", #call, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                            \
+    } while (0)
+
+size_t expected_params(const hj_problem_desc &D)
+{
+    size_t n = 0;
+    if (D.family == HJ_FAM_SPEED_QUAD || D.family == HJ_FAM_SMOOTH_NONCONVEX) n += D.d;
+    if (D.family == HJ_FAM_LINEAR_QUAD) n += (size_t)D.d * D.d + (size_t)D.d * D.m;
+    n += D.d;
+    return n;
+}
+
+hj_status validate_problem(hj_ctx *ctx, const hj_problem_desc &D, int idx)
+{
+    if (D.d < 1 || D.d > DPAD) return fail(ctx, HJ_EINVAL, "problem %d: d=%d outside [1, %d]", idx, D.d, DPAD);
+    if (D.family < HJ_FAM_QUAD_ISO || D.family > HJ_FAM_LINEAR_QUAD)
+        return fail(ctx, HJ_EINVAL, "problem %d: unknown family %d", idx, (int)D.family);
+    if (D.principle != HJ_LAX && D.principle != HJ_HOPF)
+        return fail(ctx, HJ_EINVAL, "problem %d: unknown principle %d", idx, (int)D.principle);
+    if (D.g_kind != HJ_G_QUAD_SHIFT && D.g_kind != HJ_G_DIAG_QUAD)
+        return fail(ctx, HJ_EINVAL, "problem %d: unknown initial data %d", idx, (int)D.g_kind);
+    if (D.family == HJ_FAM_LINEAR_QUAD) {
+        if (D.m < 1 || D.m > 64 || D.d > 128)
+            return fail(ctx, HJ_EINVAL, "problem %d: linear-quadratic needs m in [1,64], d <= 128", idx);
+        return fail(ctx, HJ_EUNSUPPORTED, "problem %d: the linear-quadratic family is not built into this library",
+                    idx);
+    }
+    if (D.family == HJ_FAM_SMOOTH_NONCONVEX && !(D.s_eps > 0))
+        return fail(ctx, HJ_EINVAL, "problem %d: s_eps must be > 0", idx);
+    if (D.n_guesses < 0 || D.n_guesses > 65535)
+        return fail(ctx, HJ_EINVAL, "problem %d: n_guesses=%d outside [0, 65535]", idx, D.n_guesses);
+    if (!D.params && expected_params(D) > 0) return fail(ctx, HJ_EINVAL, "problem %d: params is NULL", idx);
+    if (D.n_params != expected_params(D))
+        return fail(ctx, HJ_EINVAL, "problem %d: n_params=%zu, expected %zu", idx, D.n_params, expected_params(D));
+    size_t off = expected_params(D) - D.d;
+    for (size_t i = 0; i < D.n_params; ++i)
+        if (!std::isfinite(D.params[i])) return fail(ctx, HJ_EINVAL, "problem %d: params[%zu] not finite", idx, i);
+    if (D.g_kind == HJ_G_DIAG_QUAD)
+        for (int i = 0; i < D.d; ++i)
+            if (!(D.params[off + i] > 0)) return fail(ctx, HJ_EINVAL, "problem %d: sigma[%d] must be > 0", idx, i);
+    return HJ_OK;
+}
+
+hj_status validate_opts(hj_ctx *ctx, const hj_solver_opts &o)
+{
+    if (o.n_steps_default < 1 || o.n_steps_default > MAX_N)
+        return fail(ctx, HJ_EINVAL, "n_steps_default=%d outside [1, %d]", o.n_steps_default, MAX_N);
+    if (o.quad != HJ_QUAD_RK4 && o.quad != HJ_QUAD_RECT) return fail(ctx, HJ_EINVAL, "unknown quad %d", (int)o.quad);
+    if (o.grad < HJ_GRAD_FD_CENTRAL || o.grad > HJ_GRAD_ADJOINT)
+        return fail(ctx, HJ_EINVAL, "unknown grad mode %d", (int)o.grad);
+    if (o.grad != HJ_GRAD_ADJOINT && !(o.fd_h > 0)) return fail(ctx, HJ_EINVAL, "fd_h must be > 0");
+    if (!(o.step > 0) || !std::isfinite(o.step)) return fail(ctx, HJ_EINVAL, "step must be finite and > 0");
+    if (o.max_iters < 0) return fail(ctx, HJ_EINVAL, "max_iters must be >= 0");
+    if (o.halving_period < 0) return fail(ctx, HJ_EINVAL, "halving_period must be >= 0");
+    if (!(o.eps >= 0)) return fail(ctx, HJ_EINVAL, "eps must be >= 0");
+    if (o.adapt && (!(o.grow >= 1) || !(o.shrink > 0 && o.shrink <= 1) || !(o.step_max > 0)))
+        return fail(ctx, HJ_EINVAL, "adapt needs grow >= 1, 0 < shrink <= 1, step_max > 0");
+    if (o.n_guesses < 1 || o.n_guesses > 65535) return fail(ctx, HJ_EINVAL, "n_guesses=%d outside [1, 65535]", o.n_guesses);
+    if (o.max_rounds < 0 || o.max_rounds > 64) return fail(ctx, HJ_EINVAL, "max_rounds=%d outside [0, 64]", o.max_rounds);
+    if (o.max_trials < 0) return fail(ctx, HJ_EINVAL, "max_trials must be >= 0");
+    if (o.guess_dist != 0 && o.guess_dist != 1) return fail(ctx, HJ_EINVAL, "guess_dist must be 0 or 1");
+    if (!(o.cert_tol >= 0)) return fail(ctx, HJ_EINVAL, "cert_tol must be >= 0");
+    if (o.precision != HJ_PREC_FP32 && o.precision != HJ_PREC_FP64)
+        return fail(ctx, HJ_EINVAL, "unknown precision %d", (int)o.precision);
+    return HJ_OK;
+}
+
+// Smallest instantiated C >= need for this (precision, family, principle, kind).
+int pick_c(int prec, int fam, int pr, int kind, int need)
+{
+    const Registry &R = registry();
+    for (int c = need; c <= MAXC; ++c) {
+        const KSet &k = R.k[prec][fam][pr][c];
+        const void *f = kind == K_EVAL ? (const void *)k.eval : kind == K_GRAD ? (const void *)k.grad
+                      : kind == K_CD ? (const void *)k.cd : kind == K_GD ? (const void *)k.gd
+                      : (const void *)k.cert_pairs;
+        if (f) return c;
+    }
+    return -1;
+}
+
+// Threads per pair and components per thread for one launch.  Preference:
+// at most `pref` components per thread (fewer registers for the adjoint and
+// for FP64), then the fewest lanes.
+bool choose(const hj_ctx *ctx, int p, int kind, int *tpp_out, int *c_out)
+{
+    const hj_problem_desc &D = ctx->desc[p];
+    const int prec = (kind == K_CERT) ? ctx->prec : ctx->prec;
+    int pref;
+    if (kind == K_CERT) pref = 2;
+    else if (ctx->prec == 1) pref = 4;
+    else if (kind == K_GRAD || kind == K_GD) pref = 5;
+    else pref = 10;
+    const int ov = ctx->tpp_override[p];
+    for (int tpp = 1; tpp <= 32; tpp <<= 1) {
+        if (ov && kind != K_CERT && tpp != ov) continue;
+        const int need = (D.d + tpp - 1) / tpp;
+        if (!ov && need > pref && tpp < 32) continue;
+        const int c = pick_c(prec, D.family, D.principle, kind, need);
+        if (c > 0) {
+            *tpp_out = tpp;
+            *c_out = c;
+            return true;
+        }
+    }
+    return false;
+}
+
+const KSet &kset(const hj_ctx *ctx, int p, int c)
+{
+    const hj_problem_desc &D = ctx->desc[p];
+    return registry().k[ctx->prec][D.family][D.principle][c];
+}
+
+int persistent_grid(hj_ctx *ctx, const void *fn)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, BLOCK, 0) != cudaSuccess || nb < 1) nb = 1;
+    return nb * ctx->nsm;
+}
+
+int rows_grid(hj_ctx *ctx, const void *fn, long long n, int tpp)
+{
+    long long need = (n * tpp + BLOCK - 1) / BLOCK;
+    long long cap = (long long)persistent_grid(ctx, fn) * 8;
+    if (need < 1) need = 1;
+    return (int)std::min(need, cap);
+}
+
+template <typename T>
+void *as_ptr(T *p) { return (void *)p; }
+
+hj_status ensure_scratch(hj_ctx *ctx, long long nq, long long npairs)
+{
+    if (nq > ctx->cap_q) {
+        cudaFree(ctx->starts); cudaFree(ctx->pair_base); cudaFree(ctx->block_sums);
+        cudaFree(ctx->trials); cudaFree(ctx->qflags);
+        ctx->starts = ctx->pair_base = ctx->block_sums = ctx->trials = ctx->qflags = nullptr;
+        ctx->cap_q = 0;
+        long long nb = (nq + 1023) / 1024 + 1;
+        CU(cudaMalloc(&ctx->starts, sizeof(int32_t) * nq));
+        CU(cudaMalloc(&ctx->pair_base, sizeof(int32_t) * nq));
+        CU(cudaMalloc(&ctx->block_sums, sizeof(int32_t) * nb));
+        CU(cudaMalloc(&ctx->trials, sizeof(int32_t) * nq));
+        CU(cudaMalloc(&ctx->qflags, sizeof(int32_t) * nq));
+        ctx->cap_q = nq;
+    }
+    if (npairs > ctx->cap_p) {
+        cudaFree(ctx->pair_q); cudaFree(ctx->pair_slot); cudaFree(ctx->pair_round); cudaFree(ctx->iters);
+        cudaFree(ctx->wl); cudaFree(ctx->flags); cudaFree(ctx->pP); cudaFree(ctx->pF); cudaFree(ctx->pR);
+        cudaFree(ctx->vfin);
+        ctx->pair_q = ctx->pair_slot = ctx->pair_round = ctx->iters = ctx->wl = nullptr;
+        ctx->flags = ctx->pP = nullptr;
+        ctx->pF = ctx->pR = nullptr;
+        ctx->vfin = nullptr;
+        ctx->cap_p = 0;
+        const size_t es = ctx->prec ? sizeof(double) : sizeof(float);
+        CU(cudaMalloc(&ctx->pair_q, sizeof(int32_t) * npairs));
+        CU(cudaMalloc(&ctx->pair_slot, sizeof(int32_t) * npairs));
+        CU(cudaMalloc(&ctx->pair_round, sizeof(int32_t) * npairs));
+        CU(cudaMalloc(&ctx->iters, sizeof(int32_t) * npairs));
+        CU(cudaMalloc(&ctx->wl, sizeof(int32_t) * npairs));
+        CU(cudaMalloc(&ctx->flags, npairs));
+        CU(cudaMalloc(&ctx->pP, npairs));
+        CU(cudaMalloc(&ctx->pF, sizeof(double) * npairs));
+        CU(cudaMalloc(&ctx->pR, sizeof(double) * npairs));
+        CU(cudaMalloc(&ctx->vfin, es * npairs * ctx->ld));
+        ctx->cap_p = npairs;
+    }
+    return HJ_OK;
+}
+
+SolverDev solver_dev(const hj_solver_opts &o)
+{
+    SolverDev S;
+    S.quad = o.quad;
+    S.grad = o.grad;
+    S.max_iters = o.max_iters;
+    S.halving_period = o.halving_period;
+    S.adapt = o.adapt;
+    S.max_trials = o.max_trials;
+    S.max_rounds = o.max_rounds;
+    S.guess_dist = o.guess_dist;
+    S.kahan = o.kahan;
+    S.n_default = o.n_steps_default;
+    S.fd_h = o.fd_h;
+    S.step = o.step;
+    S.eps = o.eps;
+    S.grow = o.grow;
+    S.shrink = o.shrink;
+    S.step_max = o.step_max;
+    S.cert_tol = o.cert_tol;
+    S.seed = o.seed;
+    return S;
+}
+
+hj_status check_rows(hj_ctx *ctx, int64_t n, const void *x, const void *t, const void *v)
+{
+    if (!ctx) return HJ_EINVAL;
+    if (n < 0) return fail(ctx, HJ_EINVAL, "n must be >= 0");
+    if (n > (int64_t)1 << 30) return fail(ctx, HJ_EINVAL, "n=%lld too large (max 2^30)", (long long)n);
+    if (n > 0 && (!x || !t || !v)) return fail(ctx, HJ_EINVAL, "x, t and v must be non-NULL");
+    return HJ_OK;
+}
+
+template <typename T>
+RowArgs<T> row_args(hj_ctx *ctx, int p, int tpp, int64_t n, const int32_t *pidx, const void *x, const void *t,
+                    const int32_t *ns, const void *v, void *F, void *grad)
+{
+    RowArgs<T> a{};
+    a.P = *(ProbDev<T> *)(sizeof(T) == 8 ? (void *)&ctx->dev[p].pd : (void *)&ctx->dev[p].pf);
+    a.tpp = tpp;
+    a.n = n;
+    a.x = (const T *)x;
+    a.t = (const T *)t;
+    a.nsteps = ns;
+    a.n_default = ctx->opts.n_steps_default;
+    a.v = (const T *)v;
+    a.F = (T *)F;
+    a.grad = (T *)grad;
+    a.pidx = (ctx->np > 1) ? pidx : nullptr;
+    a.pfilter = p;
+    a.quad = ctx->opts.quad;
+    a.kahan = ctx->opts.kahan;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+hj_status hj_create(const hj_problem_desc *problems, int n_problems, const hj_solver_opts *opts, int cuda_device,
+                    hj_ctx **out)
+{
+    hj_ctx *ctx = nullptr;
+    if (!problems || n_problems < 1 || !opts || !out)
+        return fail(nullptr, HJ_EINVAL, "hj_create: problems, opts and out must be non-NULL, n_problems >= 1");
+    if (n_problems > 4096) return fail(nullptr, HJ_EINVAL, "hj_create: at most 4096 problems");
+    for (int i = 0; i < n_problems; ++i) {
+        hj_status s = validate_problem(nullptr, problems[i], i);
+        if (s != HJ_OK) return s;
+    }
+    {
+        hj_status s = validate_opts(nullptr, *opts);
+        if (s != HJ_OK) return s;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)
+        return fail(nullptr, HJ_ECUDA, "hj_create: no CUDA device available");
+    if (cuda_device < 0 || cuda_device >= ndev)
+        return fail(nullptr, HJ_EINVAL, "hj_create: device %d outside [0, %d)", cuda_device, ndev);
+    ctx = new (std::nothrow) hj_ctx();
+    if (!ctx) return fail(nullptr, HJ_ENOMEM, "hj_create: out of host memory");
+    ctx->device = cuda_device;
+    ctx->np = n_problems;
+    ctx->opts = *opts;
+    ctx->prec = opts->precision == HJ_PREC_FP64 ? 1 : 0;
+    ctx->desc.assign(problems, problems + n_problems);
+    ctx->params.resize(n_problems);
+    ctx->dev.resize(n_problems);
+    ctx->tpp_override.assign(n_problems, 0);
+    for (int i = 0; i < n_problems; ++i) {
+        ctx->params[i].assign(problems[i].params, problems[i].params + problems[i].n_params);
+        ctx->desc[i].params = ctx->params[i].data();
+        if (ctx->desc[i].n_guesses == 0) ctx->desc[i].n_guesses = opts->n_guesses;
+        ctx->ld = std::max(ctx->ld, problems[i].d);
+        ctx->gmax = std::max(ctx->gmax, ctx->desc[i].n_guesses);
+    }
+    auto bail = [&](hj_status s) {
+        g_create_error = ctx->err;
+        hj_destroy(ctx);
+        return s;
+    };
+#define CUC(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            fail(ctx, e_ == cudaErrorMemoryAllocation ? HJ_ENOMEM : HJ_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+            return bail(e_ == cudaErrorMemoryAllocation ? HJ_ENOMEM : HJ_ECUDA);                  \
+        }                                                                                          \
+    } while (0)
+    CUC(cudaSetDevice(cuda_device));
+    CUC(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, cuda_device));
+    std::vector<int32_t> pg(n_problems), pd(n_problems), pprin(n_problems);
+    for (int i = 0; i < n_problems; ++i) {
+        const hj_problem_desc &D = ctx->desc[i];
+        std::vector<float> hf;
+        std::vector<double> hd;
+        fill_prob<float>(D, ctx->params[i], ctx->ld, hf, ctx->dev[i].pf);
+        fill_prob<double>(D, ctx->params[i], ctx->ld, hd, ctx->dev[i].pd);
+        CUC(cudaMalloc(&ctx->dev[i].block32, hf.size() * sizeof(float)));
+        CUC(cudaMalloc(&ctx->dev[i].block64, hd.size() * sizeof(double)));
+        CUC(cudaMemcpy(ctx->dev[i].block32, hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CUC(cudaMemcpy(ctx->dev[i].block64, hd.data(), hd.size() * sizeof(double), cudaMemcpyHostToDevice));
+        bind_prob<float>(ctx->dev[i].block32, ctx->dev[i].pf.m, ctx->dev[i].pf);
+        bind_prob<double>(ctx->dev[i].block64, ctx->dev[i].pd.m, ctx->dev[i].pd);
+        ctx->dev[i].pf.n_guesses = ctx->dev[i].pd.n_guesses = D.n_guesses;
+        pg[i] = D.n_guesses;
+        pd[i] = D.d;
+        pprin[i] = D.principle;
+        int tpp, c;
+        if (!choose(ctx, i, K_EVAL, &tpp, &c) || !choose(ctx, i, K_CERT, &tpp, &c) ||
+            !choose(ctx, i, opts->grad == HJ_GRAD_ADJOINT ? K_GD : K_CD, &tpp, &c)) {
+            fail(ctx, HJ_EUNSUPPORTED, "problem %d: no kernel built for d=%d in this precision", i, D.d);
+            return bail(HJ_EUNSUPPORTED);
+        }
+    }
+    CUC(cudaMalloc(&ctx->d_pg, sizeof(int32_t) * n_problems));
+    CUC(cudaMalloc(&ctx->d_pd, sizeof(int32_t) * n_problems));
+    CUC(cudaMalloc(&ctx->d_pprin, sizeof(int32_t) * n_problems));
+    CUC(cudaMemcpy(ctx->d_pg, pg.data(), sizeof(int32_t) * n_problems, cudaMemcpyHostToDevice));
+    CUC(cudaMemcpy(ctx->d_pd, pd.data(), sizeof(int32_t) * n_problems, cudaMemcpyHostToDevice));
+    CUC(cudaMemcpy(ctx->d_pprin, pprin.data(), sizeof(int32_t) * n_problems, cudaMemcpyHostToDevice));
+    CUC(cudaMalloc(&ctx->pcount, sizeof(int32_t) * n_problems));
+    CUC(cudaMalloc(&ctx->seg_begin, sizeof(int32_t) * (n_problems + 1)));
+    CUC(cudaMalloc(&ctx->wl_count, sizeof(int32_t) * n_problems));
+    CUC(cudaMalloc(&ctx->cursor, sizeof(int32_t) * n_problems));
+    CUC(cudaMalloc(&ctx->stats, sizeof(unsigned long long) * 8 * n_problems));
+    CUC(cudaMemset(ctx->stats, 0, sizeof(unsigned long long) * 8 * n_problems));
+    CUC(cudaEventCreate(&ctx->ev_begin));
+    CUC(cudaEventCreate(&ctx->ev_end));
+#undef CUC
+    *out = ctx;
+    return HJ_OK;
+}
+
+hj_status hj_destroy(hj_ctx *ctx)
+{
+    if (!ctx) return HJ_EINVAL;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto &d : ctx->dev) {
+        cudaFree(d.block32);
+        cudaFree(d.block64);
+    }
+    void *ptrs[] = {ctx->d_pg, ctx->d_pd, ctx->d_pprin, ctx->starts, ctx->pair_base, ctx->block_sums, ctx->trials,
+                    ctx->qflags, ctx->pair_q, ctx->pair_slot, ctx->pair_round, ctx->iters, ctx->wl, ctx->flags,
+                    ctx->pP, ctx->pF, ctx->pR, ctx->vfin, ctx->pcount, ctx->seg_begin, ctx->wl_count, ctx->cursor,
+                    ctx->stats};
+    for (void *p : ptrs) cudaFree(p);
+    for (auto e : ctx->ev_desc) cudaEventDestroy(e);
+    for (auto e : ctx->ev_cert) cudaEventDestroy(e);
+    if (ctx->ev_begin) cudaEventDestroy(ctx->ev_begin);
+    if (ctx->ev_end) cudaEventDestroy(ctx->ev_end);
+    delete ctx;
+    return HJ_OK;
+}
+
+const char *hj_last_error(const hj_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+hj_status hj_set_launch(hj_ctx *ctx, int problem, int tpp)
+{
+    if (!ctx) return HJ_EINVAL;
+    if (problem < 0 || problem >= ctx->np) return fail(ctx, HJ_EINVAL, "problem %d outside [0, %d)", problem, ctx->np);
+    if (tpp != 0 && tpp != 1 && tpp != 2 && tpp != 4 && tpp != 8 && tpp != 16 && tpp != 32)
+        return fail(ctx, HJ_EINVAL, "tpp must be 0 or a power of two <= 32");
+    int old = ctx->tpp_override[problem];
+    ctx->tpp_override[problem] = tpp;
+    int t, c;
+    const int kind = ctx->opts.grad == HJ_GRAD_ADJOINT ? K_GD : K_CD;
+    if (!choose(ctx, problem, kind, &t, &c) || !choose(ctx, problem, K_EVAL, &t, &c)) {
+        ctx->tpp_override[problem] = old;
+        return fail(ctx, HJ_EUNSUPPORTED, "no kernel for d=%d with %d threads per pair", ctx->desc[problem].d, tpp);
+    }
+    return HJ_OK;
+}
+
+static hj_status rows_launch(hj_ctx *ctx, int kind, int64_t n, const int32_t *pidx, const void *x, const void *t,
+                             const int32_t *ns, const void *v, void *F, void *grad, void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(ctx->device));
+    for (int p = 0; p < ctx->np; ++p) {
+        int tpp, c;
+        if (!choose(ctx, p, kind, &tpp, &c)) return fail(ctx, HJ_EUNSUPPORTED, "no kernel for problem %d", p);
+        const KSet &k = kset(ctx, p, c);
+        if (ctx->prec) {
+            RowArgs<double> a = row_args<double>(ctx, p, tpp, n, pidx, x, t, ns, v, F, grad);
+            const void *fn = kind == K_EVAL ? k.f_eval : k.f_grad;
+            CU((kind == K_EVAL ? k.eval : k.grad)(&a, rows_grid(ctx, fn, n, tpp), s));
+        } else {
+            RowArgs<float> a = row_args<float>(ctx, p, tpp, n, pidx, x, t, ns, v, F, grad);
+            const void *fn = kind == K_EVAL ? k.f_eval : k.f_grad;
+            CU((kind == K_EVAL ? k.eval : k.grad)(&a, rows_grid(ctx, fn, n, tpp), s));
+        }
+    }
+    return HJ_OK;
+}
+
+hj_status hj_eval_functional(hj_ctx *ctx, int64_t n, const int32_t *problem_idx, const void *x, const void *t,
+                             const int32_t *n_steps, const void *v, void *F_out, void *stream)
+{
+    hj_status s = check_rows(ctx, n, x, t, v);
+    if (s != HJ_OK) return s;
+    if (n > 0 && !F_out) return fail(ctx, HJ_EINVAL, "F_out must be non-NULL");
+    if (n == 0) return HJ_OK;
+    return rows_launch(ctx, K_EVAL, n, problem_idx, x, t, n_steps, v, F_out, nullptr, stream);
+}
+
+hj_status hj_grad(hj_ctx *ctx, int64_t n, const int32_t *problem_idx, const void *x, const void *t,
+                  const int32_t *n_steps, const void *v, void *F_out, void *grad_out, void *stream)
+{
+    hj_status s = check_rows(ctx, n, x, t, v);
+    if (s != HJ_OK) return s;
+    if (n > 0 && !grad_out) return fail(ctx, HJ_EINVAL, "grad_out must be non-NULL");
+    if (n == 0) return HJ_OK;
+    return rows_launch(ctx, K_GRAD, n, problem_idx, x, t, n_steps, v, F_out, grad_out, stream);
+}
+
+hj_status hj_certify(hj_ctx *ctx, int64_t n, const int32_t *problem_idx, const void *x, const void *t,
+                     const int32_t *n_steps, const void *v, double *residual_out, uint8_t *pass_out, double *F_out,
+                     void *stream)
+{
+    hj_status st = check_rows(ctx, n, x, t, v);
+    if (st != HJ_OK) return st;
+    if (n > 0 && (!residual_out || !pass_out)) return fail(ctx, HJ_EINVAL, "residual_out and pass_out must be non-NULL");
+    if (n == 0) return HJ_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(ctx->device));
+    double *F = F_out;
+    double *tmp = nullptr;
+    if (!F) {
+        CU(cudaMallocAsync(&tmp, sizeof(double) * n, s));
+        F = tmp;
+    }
+    for (int p = 0; p < ctx->np; ++p) {
+        int tpp, c;
+        if (!choose(ctx, p, K_CERT, &tpp, &c)) return fail(ctx, HJ_EUNSUPPORTED, "no certificate kernel for problem %d", p);
+        const KSet &k = kset(ctx, p, c);
+        auto fill = [&](auto &a) {
+            a.P = ctx->dev[p].pd;
+            a.tpp = tpp;
+            a.n = n;
+            a.nsteps = n_steps;
+            a.n_default = ctx->opts.n_steps_default;
+            a.F = F;
+            a.resid = residual_out;
+            a.pass = pass_out;
+            a.tol = ctx->opts.cert_tol;
+            a.pidx = ctx->np > 1 ? problem_idx : nullptr;
+            a.pfilter = p;
+            a.quad = ctx->opts.quad;
+        };
+        if (ctx->prec) {
+            CertArgs<double> a{};
+            fill(a);
+            a.x = (const double *)x; a.t = (const double *)t; a.v = (const double *)v;
+            CU(k.cert_rows(&a, rows_grid(ctx, k.f_cert_rows, n, tpp), s));
+        } else {
+            CertArgs<float> a{};
+            fill(a);
+            a.x = (const float *)x; a.t = (const float *)t; a.v = (const float *)v;
+            CU(k.cert_rows(&a, rows_grid(ctx, k.f_cert_rows, n, tpp), s));
+        }
+    }
+    if (tmp) CU(cudaFreeAsync(tmp, s));
+    return HJ_OK;
+}
+
+hj_status hj_guesses(hj_ctx *ctx, int64_t n, const int64_t *query_id, const int32_t *slot, const int32_t *round,
+                     const int32_t *problem_idx, void *v_out, void *stream)
+{
+    if (!ctx) return HJ_EINVAL;
+    if (n < 0) return fail(ctx, HJ_EINVAL, "n must be >= 0");
+    if (n == 0) return HJ_OK;
+    if (!query_id || !slot || !round || !v_out) return fail(ctx, HJ_EINVAL, "query_id, slot, round, v_out must be non-NULL");
+    CU(cudaSetDevice(ctx->device));
+    CU(launch_guess(n, (const long long *)query_id, slot, round, ctx->np > 1 ? problem_idx : nullptr, ctx->d_pd,
+                    ctx->ld, ctx->opts.seed, ctx->opts.guess_dist, ctx->prec, v_out, (cudaStream_t)stream));
+    return HJ_OK;
+}
+
+static hj_status record(hj_ctx *ctx, std::vector<cudaEvent_t> &pool, int idx, cudaStream_t s)
+{
+    while ((int)pool.size() <= idx) {
+        cudaEvent_t e;
+        CU(cudaEventCreate(&e));
+        pool.push_back(e);
+    }
+    CU(cudaEventRecord(pool[idx], s));
+    return HJ_OK;
+}
+
+hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_t *problem_idx, const void *x,
+                   const void *t, const int32_t *n_steps, double *phi_out, void *v_out, int32_t *status_out,
+                   void *stream)
+{
+    if (!ctx) return HJ_EINVAL;
+    if (n_queries < 0) return fail(ctx, HJ_EINVAL, "n_queries must be >= 0");
+    if (q_begin < 0) return fail(ctx, HJ_EINVAL, "q_begin must be >= 0");
+    if (n_queries == 0) return HJ_OK;
+    if (!x || !t || !phi_out || !v_out || !status_out)
+        return fail(ctx, HJ_EINVAL, "x, t, phi_out, v_out and status_out must be non-NULL");
+    if (ctx->np > 1 && !problem_idx) return fail(ctx, HJ_EINVAL, "problem_idx is required with several problems");
+    const long long npairs = (long long)n_queries * ctx->gmax;
+    if (npairs > ((long long)1 << 31) - 1) return fail(ctx, HJ_EINVAL, "too many (query, start) pairs");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(ctx->device));
+    hj_status st = ensure_scratch(ctx, n_queries, npairs);
+    if (st != HJ_OK) return st;
+    const int32_t *pidx = ctx->np > 1 ? problem_idx : nullptr;
+    const int kind = ctx->opts.grad == HJ_GRAD_ADJOINT ? K_GD : K_CD;
+    // choose kernels up front so nothing is enqueued on failure
+    std::vector<int> tpp_d(ctx->np), c_d(ctx->np), tpp_c(ctx->np), c_c(ctx->np);
+    for (int p = 0; p < ctx->np; ++p)
+        if (!choose(ctx, p, kind, &tpp_d[p], &c_d[p]) || !choose(ctx, p, K_CERT, &tpp_c[p], &c_c[p]))
+            return fail(ctx, HJ_EUNSUPPORTED, "no kernel for problem %d", p);
+    ctx->last_stream = s;
+    ctx->last_nq = n_queries;
+    ctx->last_tpp = tpp_d[0];
+    ctx->last_c = c_d[0];
+    ctx->n_desc_ev = ctx->n_cert_ev = 0;
+    CU(cudaEventRecord(ctx->ev_begin, s));
+    CU(cudaMemsetAsync(ctx->stats, 0, sizeof(unsigned long long) * 8 * ctx->np, s));
+    CU(launch_count(n_queries, pidx, ctx->d_pg, ctx->starts, ctx->pcount, ctx->np, ctx->seg_begin, ctx->wl_count, s));
+    CU(launch_scan(n_queries, ctx->starts, ctx->pair_base, ctx->block_sums, s));
+    CU(launch_build_pairs(n_queries, pidx, ctx->d_pg, ctx->pair_base, ctx->pair_q, ctx->pair_slot, ctx->pair_round,
+                          ctx->trials, ctx->qflags, ctx->seg_begin, ctx->wl_count, ctx->wl, s));
+    const SolverDev S = solver_dev(ctx->opts);
+    for (int round = 0; round <= ctx->opts.max_rounds; ++round) {
+        CU(cudaMemsetAsync(ctx->cursor, 0, sizeof(int32_t) * ctx->np, s));
+        if (ctx->timing) { st = record(ctx, ctx->ev_desc, ctx->n_desc_ev++, s); if (st != HJ_OK) return st; }
+        for (int p = 0; p < ctx->np; ++p) {
+            const KSet &k = kset(ctx, p, c_d[p]);
+            Launch L = kind == K_GD ? k.gd : k.cd;
+            const void *fn = kind == K_GD ? k.f_gd : k.f_cd;
+            auto fill = [&](auto &a) {
+                a.tpp = tpp_d[p];
+                a.problem = p;
+                a.nsteps = n_steps;
+                a.q_begin = q_begin;
+                a.S = S;
+                a.wl = ctx->wl;
+                a.seg_begin = ctx->seg_begin;
+                a.wl_count = ctx->wl_count;
+                a.cursor = ctx->cursor;
+                a.pair_q = ctx->pair_q;
+                a.pair_slot = ctx->pair_slot;
+                a.pair_round = ctx->pair_round;
+                a.iters = ctx->iters;
+                a.flags = ctx->flags;
+                a.stats = ctx->stats + 8 * p;
+            };
+            if (ctx->prec) {
+                DescArgs<double> a{};
+                fill(a);
+                a.P = ctx->dev[p].pd;
+                a.x = (const double *)x; a.t = (const double *)t; a.vfin = (double *)ctx->vfin;
+                CU(L(&a, persistent_grid(ctx, fn), s));
+            } else {
+                DescArgs<float> a{};
+                fill(a);
+                a.P = ctx->dev[p].pf;
+                a.x = (const float *)x; a.t = (const float *)t; a.vfin = (float *)ctx->vfin;
+                CU(L(&a, persistent_grid(ctx, fn), s));
+            }
+        }
+        if (ctx->timing) { st = record(ctx, ctx->ev_desc, ctx->n_desc_ev++, s); if (st != HJ_OK) return st; }
+        for (int p = 0; p < ctx->np; ++p) {
+            const KSet &k = kset(ctx, p, c_c[p]);
+            auto fill = [&](auto &a) {
+                a.P = ctx->dev[p].pd;
+                a.tpp = tpp_c[p];
+                a.nsteps = n_steps;
+                a.n_default = ctx->opts.n_steps_default;
+                a.F = ctx->pF;
+                a.resid = ctx->pR;
+                a.pass = ctx->pP;
+                a.tol = ctx->opts.cert_tol;
+                a.quad = ctx->opts.quad;
+                a.wl = ctx->wl;
+                a.seg_begin = ctx->seg_begin;
+                a.wl_count = ctx->wl_count;
+                a.problem = p;
+                a.pair_q = ctx->pair_q;
+            };
+            // the pair-mode grid covers a full round-0 list of this problem
+            const long long cap = (long long)n_queries * ctx->desc[p].n_guesses;
+            if (ctx->prec) {
+                CertArgs<double> a{};
+                fill(a);
+                a.x = (const double *)x; a.t = (const double *)t; a.v = (const double *)ctx->vfin;
+                CU(k.cert_pairs(&a, rows_grid(ctx, k.f_cert_pairs, cap, tpp_c[p]), s));
+            } else {
+                CertArgs<float> a{};
+                fill(a);
+                a.x = (const float *)x; a.t = (const float *)t; a.v = (const float *)ctx->vfin;
+                CU(k.cert_pairs(&a, rows_grid(ctx, k.f_cert_pairs, cap, tpp_c[p]), s));
+            }
+        }
+        if (ctx->timing) { st = record(ctx, ctx->ev_cert, ctx->n_cert_ev++, s); if (st != HJ_OK) return st; }
+        const int schedule = round < ctx->opts.max_rounds;
+        if (schedule) CU(cudaMemsetAsync(ctx->wl_count, 0, sizeof(int32_t) * ctx->np, s));
+        SelectArgs a{};
+        a.nq = n_queries;
+        a.pidx = pidx;
+        a.pg = ctx->d_pg;
+        a.pd = ctx->d_pd;
+        a.pprin = ctx->d_pprin;
+        a.ld = ctx->ld;
+        a.pair_base = ctx->pair_base;
+        a.pF = ctx->pF;
+        a.pP = ctx->pP;
+        a.flags = ctx->flags;
+        a.vfin = ctx->vfin;
+        a.pair_round = ctx->pair_round;
+        a.trials = ctx->trials;
+        a.qflags = ctx->qflags;
+        a.round = round;
+        a.schedule = schedule;
+        a.max_trials = ctx->opts.max_trials;
+        a.seg_begin = ctx->seg_begin;
+        a.wl_count = ctx->wl_count;
+        a.wl = ctx->wl;
+        a.phi = phi_out;
+        a.v_out = v_out;
+        a.status = status_out;
+        CU(launch_select(a, ctx->prec, s));
+    }
+    CU(cudaEventRecord(ctx->ev_end, s));
+    return HJ_OK;
+}
+
+hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out)
+{
+    if (!ctx || !out) return HJ_EINVAL;
+    std::memset(out, 0, sizeof *out);
+    if (!ctx->last_nq) return HJ_OK;
+    CU(cudaSetDevice(ctx->device));
+    CU(cudaStreamSynchronize(ctx->last_stream));
+    std::vector<unsigned long long> st(8 * ctx->np);
+    CU(cudaMemcpy(st.data(), ctx->stats, sizeof(unsigned long long) * st.size(), cudaMemcpyDeviceToHost));
+    out->n_queries = ctx->last_nq;
+    for (int p = 0; p < ctx->np; ++p) {
+        const unsigned long long *c = st.data() + 8 * p;
+        const hj_problem_desc &D = ctx->desc[p];
+        FlopModel fm = flop_model(D.family, D.principle, D.d);
+        out->iterations += (int64_t)c[0];
+        out->functional_evals += (int64_t)c[1];
+        out->gradient_evals += (int64_t)c[2];
+        out->rk4_steps += (int64_t)c[3];
+        out->n_pairs += (int64_t)c[5];
+        out->algorithmic_flops += (double)c[3] * fm.fwd_step + (double)c[4] * fm.adj_step;
+        out->certify_flops += (double)c[6] * fm.fwd_step;
+    }
+    out->threads_per_pair = ctx->last_tpp;
+    out->comps_per_thread = ctx->last_c;
+    float ms = 0;
+    double desc_ms = 0, cert_ms = 0;
+    for (int i = 0; i + 1 < ctx->n_desc_ev; i += 2) {
+        CU(cudaEventElapsedTime(&ms, ctx->ev_desc[i], ctx->ev_desc[i + 1]));
+        desc_ms += ms;
+        if (i / 2 < ctx->n_cert_ev) {
+            CU(cudaEventElapsedTime(&ms, ctx->ev_desc[i + 1], ctx->ev_cert[i / 2]));
+            cert_ms += ms;
+        }
+    }
+    CU(cudaEventElapsedTime(&ms, ctx->ev_begin, ctx->ev_end));
+    out->total_ms = ms;
+    out->descent_ms = desc_ms;
+    out->certify_ms = cert_ms;
+    out->descent_launches = ctx->n_desc_ev / 2;
+    return HJ_OK;
+}
+
+}  // extern "C"

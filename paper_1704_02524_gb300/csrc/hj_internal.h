@@ -1,0 +1,27 @@
+// hj_internal.h -- host-side registry of the instantiated kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace hjd {
+
+constexpr int MAXC = 10;  // largest components-per-thread instantiated
+
+using Launch = cudaError_t (*)(const void *args, int grid, cudaStream_t stream);
+
+// Launchers of one (precision, family, principle, C) combination.  eval,
+// grad, cd and gd compute in the context precision; cert_* compute in FP64
+// and read v in the context precision.
+struct KSet {
+    Launch eval = nullptr, grad = nullptr, cd = nullptr, gd = nullptr, cert_rows = nullptr, cert_pairs = nullptr;
+    const void *f_eval = nullptr, *f_grad = nullptr, *f_cd = nullptr, *f_gd = nullptr, *f_cert_rows = nullptr,
+               *f_cert_pairs = nullptr;
+};
+
+struct Registry {
+    KSet k[2][4][2][MAXC + 1];  // [precision][family][principle][C]
+};
+
+Registry &registry();
+
+}  // namespace hjd

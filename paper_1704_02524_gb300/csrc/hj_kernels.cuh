@@ -1,0 +1,336 @@
+// hj_kernels.cuh -- templated kernels of the solver (instantiated per
+// family and precision in hj_inst_*.cu) and the argument blocks they take.
+#pragma once
+
+#include "hj_device.cuh"
+
+namespace hjd {
+
+// Rows-mode arguments (hj_eval_functional / hj_grad / hj_certify).
+template <typename T>
+struct RowArgs {
+    ProbDev<T> P;
+    int tpp;
+    long long n;
+    const T *x;              // [n, ld]
+    const T *t;              // [n]
+    const int32_t *nsteps;   // [n] or null
+    int n_default;
+    const T *v;              // [n, ld]
+    T *F;                    // [n] or null
+    T *grad;                 // [n, ld] (gradient kernel)
+    const int32_t *pidx;     // [n] or null: rows whose problem is not `pfilter` are skipped
+    int pfilter;
+    int quad, kahan;
+};
+
+// Certificate arguments: rows mode (pid = row) or pair mode (work list).
+template <typename Tv>
+struct CertArgs {
+    ProbDev<double> P;
+    int tpp;
+    long long n;             // rows mode: number of rows
+    const Tv *x;             // [nq, ld] (context precision)
+    const Tv *t;
+    const int32_t *nsteps;
+    int n_default;
+    const Tv *v;             // rows mode: [n, ld]; pair mode: per-pair v [npairs, ld]
+    double *F;               // [n] / [npairs]
+    double *resid;
+    uint8_t *pass;
+    double tol;
+    const int32_t *pidx;
+    int pfilter;
+    int quad;
+    // pair mode
+    const int32_t *wl;       // work list
+    const int32_t *seg_begin;
+    const int32_t *wl_count;
+    int problem;
+    const int32_t *pair_q;
+};
+
+// Descent arguments (always pair mode).
+template <typename T>
+struct DescArgs {
+    ProbDev<T> P;
+    int tpp;
+    int problem;
+    const T *x;
+    const T *t;
+    const int32_t *nsteps;
+    long long q_begin;
+    SolverDev S;
+    const int32_t *wl;
+    const int32_t *seg_begin;
+    const int32_t *wl_count;
+    int *cursor;
+    const int32_t *pair_q, *pair_slot, *pair_round;
+    T *vfin;                 // [npairs, ld]
+    int32_t *iters;
+    uint8_t *flags;          // bit0: iteration cap, bit1: non-finite
+    unsigned long long *stats;  // [0] iterations [1] functional evals [2] gradients [3] forward RK4 steps
+                                // [4] adjoint steps [5] pairs [6] sum of N over pairs
+};
+
+constexpr int BLOCK = 128;
+
+template <typename T, int C>
+__device__ __forceinline__ void load_row(const Grp &g, const T *row, int d, T *out)
+{
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        int i = g.lane + k * g.tpp;
+        out[k] = (i < d) ? row[i] : (T)0;
+    }
+}
+template <typename T, int C>
+__device__ __forceinline__ void store_row(const Grp &g, T *row, int d, const T *val)
+{
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        int i = g.lane + k * g.tpp;
+        if (i < d) row[i] = val[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Functional values at given (x, t, v) rows.
+// ---------------------------------------------------------------------------
+template <typename T, int C, int FAM, int PR>
+__global__ void __launch_bounds__(BLOCK) k_eval(RowArgs<T> a)
+{
+    const Grp g = make_grp(a.tpp);
+    TP<T, C> tp;
+    tp.load(a.P, g);
+    const long long groups = (long long)gridDim.x * (BLOCK / a.tpp);
+    for (long long r = ((long long)blockIdx.x * BLOCK + threadIdx.x) / a.tpp; r < a.n; r += groups) {
+        if (a.pidx && a.pidx[r] != a.pfilter) continue;
+        const int N = a.nsteps ? a.nsteps[r] : a.n_default;
+        T x[C], v[C], gam[C], p[C];
+        load_row<T, C>(g, a.x + r * a.P.ld, a.P.d, x);
+        load_row<T, C>(g, a.v + r * a.P.ld, a.P.d, v);
+#pragma unroll
+        for (int k = 0; k < C; ++k) { gam[k] = x[k]; p[k] = v[k]; }
+        T F = functional<T, C, FAM, PR>(g, tp, a.P, a.quad, a.kahan, x, v, a.t[r], N, gam, p);
+        if (g.lane == 0) a.F[r] = F;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exact gradients at given rows.
+// ---------------------------------------------------------------------------
+template <typename T, int C, int FAM, int PR>
+__global__ void __launch_bounds__(BLOCK) k_grad(RowArgs<T> a)
+{
+    const Grp g = make_grp(a.tpp);
+    TP<T, C> tp;
+    tp.load(a.P, g);
+    T ck[MAX_SEG * 2 * C];
+    T seg[MAX_SEG * 8 * C];
+    const long long groups = (long long)gridDim.x * (BLOCK / a.tpp);
+    for (long long r = ((long long)blockIdx.x * BLOCK + threadIdx.x) / a.tpp; r < a.n; r += groups) {
+        if (a.pidx && a.pidx[r] != a.pfilter) continue;
+        const int N = a.nsteps ? a.nsteps[r] : a.n_default;
+        T x[C], v[C], gr[C];
+        load_row<T, C>(g, a.x + r * a.P.ld, a.P.d, x);
+        load_row<T, C>(g, a.v + r * a.P.ld, a.P.d, v);
+        T F = gradient<T, C, FAM, PR>(g, tp, a.P, a.quad, a.kahan, x, v, a.t[r], N, gr, ck, seg);
+        store_row<T, C>(g, a.grad + r * a.P.ld, a.P.d, gr);
+        if (a.F && g.lane == 0) a.F[r] = F;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Certificate of Sec. 4.3 in FP64 (and the FP64 functional value).
+// ---------------------------------------------------------------------------
+template <typename Tv, int C, int FAM, int PR, bool PAIRS>
+__global__ void __launch_bounds__(BLOCK) k_cert(CertArgs<Tv> a)
+{
+    const Grp g = make_grp(a.tpp);
+    TP<double, C> tp;
+    tp.load(a.P, g);
+    long long n, begin = 0;
+    if (PAIRS) {
+        n = a.wl_count[a.problem];
+        begin = a.seg_begin[a.problem];
+    } else {
+        n = a.n;
+    }
+    const long long groups = (long long)gridDim.x * (BLOCK / a.tpp);
+    for (long long j = ((long long)blockIdx.x * BLOCK + threadIdx.x) / a.tpp; j < n; j += groups) {
+        long long pid, q;
+        if (PAIRS) {
+            pid = a.wl[begin + j];
+            q = a.pair_q[pid];
+        } else {
+            if (a.pidx && a.pidx[j] != a.pfilter) continue;
+            pid = j;
+            q = j;
+        }
+        const int N = a.nsteps ? a.nsteps[q] : a.n_default;
+        double x[C], v[C], gam[C], p[C];
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            int i = g.lane + k * g.tpp;
+            x[k] = (i < a.P.d) ? (double)a.x[q * a.P.ld + i] : 0.0;
+            v[k] = (i < a.P.d) ? (double)a.v[pid * a.P.ld + i] : 0.0;
+            gam[k] = x[k];
+            p[k] = v[k];
+        }
+        double F = functional<double, C, FAM, PR>(g, tp, a.P, a.quad, 0, x, v, (double)a.t[q], N, gam, p);
+        double r = cert_residual<double, C, PR>(g, tp, a.P.g_kind, gam, p);
+        if (g.lane == 0) {
+            a.F[pid] = F;
+            a.resid[pid] = r;
+            a.pass[pid] = (r <= a.tol && isfinite(F)) ? 1 : 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent descent kernel: each lane group takes (query, start) pairs from
+// the problem's work list, draws the start (Philox), runs Algorithm 1
+// (cyclic coordinate descent with finite differences) or its gradient form
+// with the adjoint gradient, and writes the final v.
+// ---------------------------------------------------------------------------
+template <typename T, int C, int FAM, int PR, bool GD>
+__global__ void __launch_bounds__(BLOCK) k_desc(DescArgs<T> a)
+{
+    const Grp g = make_grp(a.tpp);
+    TP<T, C> tp;
+    tp.load(a.P, g);
+    const int d = a.P.d;
+    const long long n = a.wl_count[a.problem];
+    const long long begin = a.seg_begin[a.problem];
+    const int lead = (threadIdx.x & 31) & ~(a.tpp - 1);
+    const T eps_stop = (T)a.S.eps;
+    const T fd_h = (T)a.S.fd_h;
+    T ck[GD ? MAX_SEG * 2 * C : 1];
+    T seg[GD ? MAX_SEG * 8 * C : 1];
+    unsigned long long n_it = 0, n_f = 0, n_g = 0, n_rk = 0, n_adj = 0, n_pairs = 0, n_sumN = 0;
+    for (;;) {
+        long long j = 0;
+        if (g.lane == 0) j = atomicAdd(a.cursor + a.problem, 1);
+        j = __shfl_sync(g.mask, j, lead);
+        if (j >= n) break;
+        const long long pid = a.wl[begin + j];
+        const long long q = a.pair_q[pid];
+        const int slot = a.pair_slot[pid], round = a.pair_round[pid];
+        const int N = a.nsteps ? a.nsteps[q] : a.S.n_default;
+        const T t = a.t[q];
+        T x[C], v[C], alpha[C], prev[C];
+        load_row<T, C>(g, a.x + q * a.P.ld, d, x);
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            int i = g.lane + k * g.tpp;
+            v[k] = (i < d) ? start_component<T>(a.S.seed, a.q_begin + q, slot, round, i, a.S.guess_dist) : (T)0;
+            alpha[k] = (T)a.S.step;
+            prev[k] = 0;
+        }
+        int it = 0, cap = 1, bad = 0;
+        if (GD) {
+            for (; it < a.S.max_iters; ++it) {
+                T gr[C];
+                gradient<T, C, FAM, PR>(g, tp, a.P, a.S.quad, a.S.kahan, x, v, t, N, gr, ck, seg);
+                n_g++;
+                n_rk += N;
+                n_adj += N;
+                T big = 0;
+                bool fin = true;
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    if (a.S.adapt) {
+                        T prod = gr[k] * prev[k];
+                        if (prod < 0) alpha[k] *= (T)a.S.shrink;
+                        else if (prod > 0) alpha[k] = fmin(alpha[k] * (T)a.S.grow, (T)a.S.step_max);
+                    }
+                    T st = alpha[k] * gr[k];
+                    fin = fin && finite_(st);
+                    v[k] -= st;
+                    big = fmax(big, fabs(st));
+                    prev[k] = gr[k];
+                }
+                big = gmax(g, fin ? big : (T)INFINITY);
+                if (!(big < (T)INFINITY)) { bad = 1; ++it; cap = 0; break; }
+                if (a.S.halving_period > 0 && (it + 1) % a.S.halving_period == 0) {
+#pragma unroll
+                    for (int k = 0; k < C; ++k) alpha[k] *= (T)0.5;
+                }
+                if (big < eps_stop) { ++it; cap = 0; break; }
+            }
+        } else {
+            const bool central = (a.S.grad != HJ_GRAD_FD_FORWARD);
+            int count = 0, kper = 0;
+            for (; it < a.S.max_iters; ++it) {
+                const int jc = it % d;
+                const int owner = jc % a.tpp, comp = jc / a.tpp;
+                const bool mine = (g.lane == owner);
+                T gam[C], p[C], vp[C];
+                // F(v + h e_j)
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    vp[k] = v[k] + ((mine && k == comp) ? fd_h : (T)0);
+                    gam[k] = x[k];
+                    p[k] = vp[k];
+                }
+                T Fp = functional<T, C, FAM, PR>(g, tp, a.P, a.S.quad, a.S.kahan, x, vp, t, N, gam, p);
+                // F(v - h e_j) (central) or F(v) (forward)
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    vp[k] = v[k] - ((central && mine && k == comp) ? fd_h : (T)0);
+                    gam[k] = x[k];
+                    p[k] = vp[k];
+                }
+                T Fm = functional<T, C, FAM, PR>(g, tp, a.P, a.S.quad, a.S.kahan, x, vp, t, N, gam, p);
+                n_f += 2;
+                n_rk += 2 * N;
+                T dj = central ? (Fp - Fm) / ((T)2 * fd_h) : (Fp - Fm) / fd_h;
+                T st = 0;
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    if (mine && k == comp) {
+                        if (a.S.adapt) {
+                            T prod = dj * prev[k];
+                            if (prod < 0) alpha[k] *= (T)a.S.shrink;
+                            else if (prod > 0) alpha[k] = fmin(alpha[k] * (T)a.S.grow, (T)a.S.step_max);
+                            prev[k] = dj;
+                        }
+                        st = alpha[k] * dj;
+                        v[k] -= st;
+                    }
+                }
+                st = __shfl_sync(g.mask, st, lead + owner);
+                if (!finite_(st)) { bad = 1; ++it; cap = 0; break; }
+                // reset on a move > eps, count a move < eps (strict; eps = 0 never stops)
+                if (fabs(st) > eps_stop) count = 0;
+                else if (fabs(st) < eps_stop) ++count;
+                if (a.S.halving_period > 0 && ++kper == a.S.halving_period) {
+                    kper = 0;
+#pragma unroll
+                    for (int k = 0; k < C; ++k) alpha[k] *= (T)0.5;
+                }
+                if (count >= d) { ++it; cap = 0; break; }
+            }
+        }
+        n_it += it;
+        n_pairs++;
+        n_sumN += N;
+        store_row<T, C>(g, a.vfin + pid * a.P.ld, d, v);
+        if (g.lane == 0) {
+            a.iters[pid] = it;
+            a.flags[pid] = (uint8_t)(cap | (bad << 1));
+        }
+    }
+    if (g.lane == 0 && a.stats) {
+        atomicAdd(a.stats + 0, n_it);
+        atomicAdd(a.stats + 1, n_f);
+        atomicAdd(a.stats + 2, n_g);
+        atomicAdd(a.stats + 3, n_rk);
+        atomicAdd(a.stats + 4, n_adj);
+        atomicAdd(a.stats + 5, n_pairs);
+        atomicAdd(a.stats + 6, n_sumN);
+    }
+}
+
+}  // namespace hjd

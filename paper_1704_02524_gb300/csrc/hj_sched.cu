@@ -1,0 +1,234 @@
+// hj_sched.cu -- bookkeeping kernels of hj_solve: pair layout, work lists,
+// best-of-guesses with reseeding (Sec. 4.3 and Sec. 5), and the guesses
+// entry point.  None of these touches the Hamiltonian.
+#include <cstdint>
+
+#include "hj.h"
+#include "hj_device.cuh"
+#include "hj_sched.h"
+
+namespace hjd {
+
+// Starts per query -> starts[q]; pairs per problem accumulated in pcount.
+__global__ void k_count(long long nq, const int32_t *pidx, const int32_t *pg, int32_t *starts, int32_t *pcount)
+{
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (long long)gridDim.x * blockDim.x) {
+        int p = pidx ? pidx[q] : 0;
+        int G = pg[p];
+        starts[q] = G;
+        atomicAdd(pcount + p, G);
+    }
+}
+
+// Exclusive prefix over problems; clears the work-list counters.
+__global__ void k_problem_offsets(int np, const int32_t *pcount, int32_t *seg_begin, int32_t *wl_count)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int acc = 0;
+        for (int p = 0; p < np; ++p) {
+            seg_begin[p] = acc;
+            acc += pcount[p];
+            wl_count[p] = 0;
+        }
+        seg_begin[np] = acc;
+    }
+}
+
+// Three-phase exclusive scan of int32 counts: per-block scans, a serial
+// scan of the block totals, then the block offsets added back.
+constexpr int SCAN_BLOCK = 1024;
+
+__global__ void k_scan_blocks(long long n, const int32_t *in, int32_t *out, int32_t *block_sums)
+{
+    __shared__ int32_t sh[SCAN_BLOCK];
+    long long i = (long long)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+    int32_t v = (i < n) ? in[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < SCAN_BLOCK; o <<= 1) {
+        int32_t t = (threadIdx.x >= (unsigned)o) ? sh[threadIdx.x - o] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < n) out[i] = sh[threadIdx.x] - v;
+    if (threadIdx.x == SCAN_BLOCK - 1) block_sums[blockIdx.x] = sh[threadIdx.x];
+}
+
+__global__ void k_scan_sums(int nb, int32_t *block_sums)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int32_t acc = 0;
+        for (int b = 0; b < nb; ++b) {
+            int32_t v = block_sums[b];
+            block_sums[b] = acc;
+            acc += v;
+        }
+    }
+}
+
+__global__ void k_scan_add(long long n, int32_t *out, const int32_t *block_sums)
+{
+    long long i = (long long)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+    if (i < n) out[i] += block_sums[blockIdx.x];
+}
+
+// Round 0: every (query, slot) pair, appended to its problem's work list.
+__global__ void k_build_pairs(long long nq, const int32_t *pidx, const int32_t *pg, const int32_t *pair_base,
+                              int32_t *pair_q, int32_t *pair_slot, int32_t *pair_round, int32_t *trials,
+                              int32_t *qflags, const int32_t *seg_begin, int32_t *wl_count, int32_t *wl)
+{
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (long long)gridDim.x * blockDim.x) {
+        int p = pidx ? pidx[q] : 0;
+        int G = pg[p];
+        int base = pair_base[q];
+        int pos = atomicAdd(wl_count + p, G);
+        for (int s = 0; s < G; ++s) {
+            pair_q[base + s] = (int32_t)q;
+            pair_slot[base + s] = s;
+            pair_round[base + s] = 0;
+            wl[seg_begin[p] + pos + s] = base + s;
+        }
+        trials[q] = G;
+        qflags[q] = 0;
+    }
+}
+
+// Best of the starts of each query, then the reseed decisions for the next
+// round: failed slots, in slot order, while fewer than max_trials starts of
+// the query have run.  phi = F (Lax) or -G (Hopf) at the chosen start.
+template <typename T>
+__global__ void k_select(long long nq, const int32_t *pidx, const int32_t *pg, const int32_t *pd,
+                         const int32_t *pprin, int ld, const int32_t *pair_base, const double *pF,
+                         const uint8_t *pP, const uint8_t *flags, const T *vfin, int32_t *pair_round,
+                         int32_t *trials, int32_t *qflags, int round, int schedule, int max_trials,
+                         const int32_t *seg_begin, int32_t *wl_count, int32_t *wl, double *phi, T *v_out,
+                         int32_t *status)
+{
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (long long)gridDim.x * blockDim.x) {
+        const int p = pidx ? pidx[q] : 0;
+        const int G = pg[p], d = pd[p];
+        const int base = pair_base[q];
+        int best = -1, best_cert = 0, qf = qflags[q];
+        for (int s = 0; s < G; ++s) {
+            const int pid = base + s;
+            if (flags[pid] & 2) qf |= HJ_ST_NONFINITE;
+            const double F = pF[pid];
+            if (!isfinite(F)) continue;
+            const int ok = pP[pid];
+            if (ok && !best_cert) { best = s; best_cert = 1; continue; }
+            if (ok != best_cert) continue;
+            if (best < 0 || F < pF[base + best]) best = s;
+        }
+        int st = 0;
+        if (best >= 0) {
+            const int pid = base + best;
+            const double F = pF[pid];
+            phi[q] = (pprin[p] == HJ_LAX) ? F : -F;
+            for (int i = 0; i < d; ++i) v_out[q * ld + i] = vfin[(long long)pid * ld + i];
+            if (best_cert) st |= HJ_ST_CERTIFIED;
+            if (flags[pid] & 1) st |= HJ_ST_MAX_ITERS;
+        } else {
+            phi[q] = nan("");
+            for (int i = 0; i < d; ++i) v_out[q * ld + i] = (T)nan("");
+            st |= HJ_ST_NONFINITE;
+        }
+        if (schedule) {
+            int tr = trials[q];
+            for (int s = 0; s < G && tr < max_trials; ++s) {
+                const int pid = base + s;
+                if (pP[pid]) continue;
+                pair_round[pid] = round + 1;
+                int pos = atomicAdd(wl_count + p, 1);
+                wl[seg_begin[p] + pos] = pid;
+                ++tr;
+                qf |= HJ_ST_RESEEDED;
+            }
+            trials[q] = tr;
+        }
+        qflags[q] = qf;
+        status[q] = st | qf;
+    }
+}
+
+// hj_guesses: the starts drawn by hj_solve, for testing.
+template <typename T>
+__global__ void k_guess(long long n, const long long *qid, const int32_t *slot, const int32_t *round,
+                        const int32_t *pidx, const int32_t *pd, int ld, unsigned long long seed, int dist, T *v)
+{
+    const long long total = n * ld;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const long long r = e / ld;
+        const int i = (int)(e % ld);
+        const int d = pd[pidx ? pidx[r] : 0];
+        if (i < d) v[e] = start_component<T>(seed, qid[r], slot[r], round[r], i, dist);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers.
+// ---------------------------------------------------------------------------
+static int grid_for(long long n, int block)
+{
+    long long g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > 65535LL * 16) g = 65535LL * 16;
+    return (int)g;
+}
+
+cudaError_t launch_count(long long nq, const int32_t *pidx, const int32_t *pg, int32_t *starts, int32_t *pcount,
+                         int np, int32_t *seg_begin, int32_t *wl_count, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(pcount, 0, sizeof(int32_t) * np, s);
+    if (e != cudaSuccess) return e;
+    k_count<<<grid_for(nq, 256), 256, 0, s>>>(nq, pidx, pg, starts, pcount);
+    k_problem_offsets<<<1, 1, 0, s>>>(np, pcount, seg_begin, wl_count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(long long n, const int32_t *in, int32_t *out, int32_t *block_sums, cudaStream_t s)
+{
+    int nb = (int)((n + SCAN_BLOCK - 1) / SCAN_BLOCK);
+    if (nb < 1) nb = 1;
+    k_scan_blocks<<<nb, SCAN_BLOCK, 0, s>>>(n, in, out, block_sums);
+    k_scan_sums<<<1, 1, 0, s>>>(nb, block_sums);
+    k_scan_add<<<nb, SCAN_BLOCK, 0, s>>>(n, out, block_sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_pairs(long long nq, const int32_t *pidx, const int32_t *pg, const int32_t *pair_base,
+                               int32_t *pair_q, int32_t *pair_slot, int32_t *pair_round, int32_t *trials,
+                               int32_t *qflags, const int32_t *seg_begin, int32_t *wl_count, int32_t *wl,
+                               cudaStream_t s)
+{
+    k_build_pairs<<<grid_for(nq, 256), 256, 0, s>>>(nq, pidx, pg, pair_base, pair_q, pair_slot, pair_round, trials,
+                                                    qflags, seg_begin, wl_count, wl);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_select_t(const SelectArgs &a, cudaStream_t s)
+{
+    k_select<T><<<grid_for(a.nq, 128), 128, 0, s>>>(
+        a.nq, a.pidx, a.pg, a.pd, a.pprin, a.ld, a.pair_base, a.pF, a.pP, a.flags, (const T *)a.vfin, a.pair_round,
+        a.trials, a.qflags, a.round, a.schedule, a.max_trials, a.seg_begin, a.wl_count, a.wl, a.phi, (T *)a.v_out,
+        a.status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select(const SelectArgs &a, int prec, cudaStream_t s)
+{
+    return prec ? launch_select_t<double>(a, s) : launch_select_t<float>(a, s);
+}
+
+cudaError_t launch_guess(long long n, const long long *qid, const int32_t *slot, const int32_t *round,
+                         const int32_t *pidx, const int32_t *pd, int ld, unsigned long long seed, int dist, int prec,
+                         void *v, cudaStream_t s)
+{
+    int g = grid_for(n * ld, 256);
+    if (prec) k_guess<double><<<g, 256, 0, s>>>(n, qid, slot, round, pidx, pd, ld, seed, dist, (double *)v);
+    else k_guess<float><<<g, 256, 0, s>>>(n, qid, slot, round, pidx, pd, ld, seed, dist, (float *)v);
+    return cudaGetLastError();
+}
+
+}  // namespace hjd

@@ -1,0 +1,150 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances: fp32 functional values 2e-5 relative (RK4 state and Kahan
+quadrature in binary32 over <= 256 steps); fp64 paths 1e-11; solved phi
+within 1e-4 (1 + |phi|) as the accuracy target of the solver states;
+integer/bit outputs (starts, certificate decisions) exactly.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1704_02524_gb300 import workloads as W
+from tests.helpers import oracle_opts, oracle_problem, rel_err
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def hj():
+    from paper_1704_02524_gb300 import hj as H
+    H.load_library()
+    return H
+
+
+def _spec(family, principle, d, seed=0, n_neg=1, s_eps=1e-6, g_kind=None):
+    rng = np.random.default_rng(seed)
+    if g_kind is None:
+        g_kind = W.G_DIAG_QUAD if family == W.FAM_SMOOTH_NONCONVEX else W.G_QUAD_SHIFT
+    return W.ProblemSpec(d=d, family=family, principle=principle, g_kind=g_kind,
+                         w=W.f32(rng.normal(size=d) / np.sqrt(d)), a=W.f32(rng.uniform(-1, 1, d)),
+                         sigma=W.f32(rng.uniform(0.5, 2, d)), n_neg=n_neg, s_eps=s_eps, n_guesses=4)
+
+
+def _rows(n, d, seed, prec):
+    rng = np.random.default_rng(seed)
+    x = W.f32(rng.uniform(-1, 1, (n, d)))
+    v = W.f32(rng.uniform(-1.5, 1.5, (n, d)))
+    t = W.f32(rng.uniform(0.2, 1.0, n))
+    N = rng.integers(1, 70, n).astype(np.int32)
+    return x, v, t, N
+
+
+def _t(a, dtype):
+    return torch.tensor(np.asarray(a), dtype=dtype, device=DEV)
+
+
+FAMS = [(W.FAM_QUAD_ISO, W.LAX), (W.FAM_QUAD_ISO, W.HOPF), (W.FAM_SPEED_QUAD, W.LAX), (W.FAM_SPEED_QUAD, W.HOPF),
+        (W.FAM_SMOOTH_NONCONVEX, W.HOPF), (W.FAM_SMOOTH_NONCONVEX, W.LAX)]
+
+
+@pytest.mark.parametrize("family,principle", FAMS)
+@pytest.mark.parametrize("d", [1, 3, 10, 20, 37])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_functional_and_gradient_match_oracle(hj, family, principle, d, prec):
+    spec = _spec(family, principle, d, seed=d, s_eps=1e-2)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    opts = hj.opts_from_dict(W.solver_constants(), hj.HJ_PREC_FP32 if prec == "fp32" else hj.HJ_PREC_FP64, 32)
+    ctx = hj.hj_create([spec], opts, 0)
+    n = 67  # several groups and a ragged tail
+    x, v, t, N = _rows(n, d, 100 + d, prec)
+    F = hj.hj_eval_functional(ctx, _t(x, dt), _t(t, dt), _t(v, dt), _t(N, torch.int32)).cpu().numpy()
+    Fg, G = hj.hj_grad(ctx, _t(x, dt), _t(t, dt), _t(v, dt), _t(N, torch.int32))
+    Fg, G = Fg.cpu().numpy(), G.cpu().numpy()
+    P = oracle_problem(spec)
+    tolF = 2e-5 if prec == "fp32" else 1e-11
+    for i in range(n):
+        Fo, Go = O.gradient(P, x[i], t[i], int(N[i]), v[i])
+        assert rel_err(F[i], Fo) <= tolF, (i, F[i], Fo)
+        assert rel_err(Fg[i], Fo) <= tolF
+        scale = 1 + np.abs(Go).max()
+        assert np.abs(G[i] - Go).max() <= (5e-4 if prec == "fp32" else 1e-9) * scale, (i, G[i], Go)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("dist", [0, 1])
+def test_starts_are_bit_exact(hj, prec, dist):
+    spec = _spec(W.FAM_SMOOTH_NONCONVEX, W.HOPF, 20)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    solver = W.solver_constants(guess_dist=dist, seed=0x1234ABCD5678)
+    ctx = hj.hj_create([spec], hj.opts_from_dict(solver, hj.HJ_PREC_FP32 if prec == "fp32" else hj.HJ_PREC_FP64), 0)
+    rng = np.random.default_rng(5)
+    n = 300
+    q = rng.integers(0, 2 ** 40, n).astype(np.int64)
+    s = rng.integers(0, 20, n).astype(np.int32)
+    r = rng.integers(0, 5, n).astype(np.int32)
+    v = hj.hj_guesses(ctx, _t(q, torch.int64), _t(s, torch.int32), _t(r, torch.int32)).cpu().numpy()
+    for i in range(n):
+        ref = O.guess(solver["seed"], int(q[i]), int(s[i]), int(r[i]), 20, dist)
+        if prec == "fp32":
+            ref = ref.astype(np.float32).astype(np.float64)
+        assert np.array_equal(v[i].astype(np.float64), ref), i
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_certificate_matches_oracle(hj, prec):
+    spec = _spec(W.FAM_SMOOTH_NONCONVEX, W.HOPF, 20, seed=3)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    solver = W.solver_constants(cert_tol=0.3)
+    ctx = hj.hj_create([spec], hj.opts_from_dict(solver, hj.HJ_PREC_FP32 if prec == "fp32" else hj.HJ_PREC_FP64, 64), 0)
+    n = 50
+    x, v, t, N = _rows(n, 20, 9, prec)
+    F, R, Pa = hj.hj_certify(ctx, _t(x, dt), _t(t, dt), _t(v, dt), _t(N, torch.int32))
+    F, R, Pa = F.cpu().numpy(), R.cpu().numpy(), Pa.cpu().numpy()
+    P = oracle_problem(spec)
+    for i in range(n):
+        Fo, Ro, ok = O.certify(P, x[i], t[i], int(N[i]), v[i], 0.3)
+        assert rel_err(F[i], Fo) < 1e-11 and abs(R[i] - Ro) < 1e-11
+        assert bool(Pa[i]) == ok
+    ctx.close()
+
+
+def _solve_both(hj, wl, nq, prec_code=None):
+    w = wl.head(nq)
+    spec = w.problems[0]
+    prec = prec_code if prec_code is not None else (hj.HJ_PREC_FP64 if w.precision == "fp64" else hj.HJ_PREC_FP32)
+    dt = torch.float64 if prec == hj.HJ_PREC_FP64 else torch.float32
+    ctx = hj.hj_create(w.problems, hj.opts_from_dict(w.solver, prec, int(w.n_steps[0])), 0)
+    phi, v, st = hj.hj_solve(ctx, _t(w.x, dt), _t(w.t, dt), _t(w.n_steps, torch.int32))
+    info = hj.hj_last_solve_info(ctx)
+    ctx.close()
+    ref = O.solve(oracle_problem(spec), oracle_opts(w.solver, spec.n_guesses), w.x, w.t, w.n_steps)
+    return phi.cpu().numpy(), v.cpu().numpy(), st.cpu().numpy(), ref, info
+
+
+def test_solve_quad_iso_d2_fp64_matches_closed_form_and_oracle(hj):
+    wl = W.c1_quad_iso()
+    phi, v, st, ref, info = _solve_both(hj, wl, 64)
+    exact = np.sum(wl.x ** 2, axis=1) / 4
+    assert np.abs(phi - exact).max() < 1e-12
+    assert np.abs(phi - ref["phi"]).max() < 1e-12
+    assert np.array_equal(st, ref["status"])
+    assert info["iterations"] == 64 * 4 * 400
+
+
+def test_solve_speed_quad_d10_matches_oracle(hj):
+    phi, v, st, ref, info = _solve_both(hj, W.c2_speed_quad(nq_x=16), 48)
+    assert np.all(rel_err(phi, ref["phi"]) <= 1e-4)
+    assert np.array_equal(st & 1, ref["status"] & 1)
+
+
+def test_solve_smooth_nonconvex_d20_matches_oracle(hj):
+    phi, v, st, ref, info = _solve_both(hj, W.c3_smooth_nonconvex(nq=40), 40)
+    err = rel_err(phi, ref["phi"])
+    assert np.all(err <= 1e-4), err.max()
+    assert np.array_equal(st & 1, ref["status"] & 1)
