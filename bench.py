@@ -1,0 +1,343 @@
+"""Benchmark: queries/s of the generalized Hopf solve on the d=20 non-convex
+workload (65,536 queries x 16 starts, RK4 N=64, t=0.5, certificate and
+reseeding), with the adjoint gradient-descent path as the headline and the
+plain coordinate-descent / finite-difference path beside it.
+
+One step = one hj_solve over the whole batch with inputs resident in HBM
+(guesses, descent, FP64 certificate, reseed rounds, best-of-guesses).
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the same workload instead (bounded samples per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1704_02524_gb300 import workloads as W  # noqa: E402
+
+WORKLOAD = "smooth_nonconvex_d20_hopf"
+METRIC = "queries/s at 1e-4 rel err (d=20 Hopf), adjoint vs plain CD-FD; % FP32 peak"
+CPU_SAMPLE = 64          # queries of the oracle timing sample (cpu_baseline)
+REF_SAMPLE = 16          # queries per step of the reference arm
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nq", type=int, default=65536)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain CD-FD measurement")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
+    return ap.parse_args()
+
+
+def _oracle_inputs(wl):
+    import oracle as O
+    from tests.helpers import oracle_opts, oracle_problem  # noqa: F401  (same glue as the tests)
+    spec = wl.problems[0]
+    return O, oracle_problem(spec), oracle_opts(wl.solver, spec.n_guesses)
+
+
+def _time_oracle(wl, q_ids):
+    """Oracle on the given query rows of wl, all host cores; returns (seconds, result, threads)."""
+    O, P, opts = _oracle_inputs(wl)
+    sub = wl.take(q_ids)
+    t0 = time.perf_counter()
+    res = O.solve(P, opts, sub.x, sub.t, sub.n_steps, query_ids=np.asarray(q_ids, dtype=np.int64))
+    return time.perf_counter() - t0, res, res["threads"]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"hj_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                try:
+                    rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+                except ValueError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+def run_reference(a):
+    """Reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = W.c3_smooth_nonconvex(nq=a.nq)
+    rng = np.random.default_rng(0)
+    times = []
+    threads = 1
+    for k in range(a.warmup + a.steps):
+        ids = rng.choice(a.nq, REF_SAMPLE, replace=False)
+        dt, _, threads = _time_oracle(wl, ids)
+        if k >= a.warmup:
+            times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    val = REF_SAMPLE / (ms / 1e3)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "queries/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "d": 20, "queries": a.nq, "guesses": 16, "n_steps": 64, "t": 0.5,
+                   "sample_per_step": REF_SAMPLE},
+        "cpu_baseline": {"value": val, "unit": "queries/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{REF_SAMPLE} random queries of the workload per step (all 16 starts each)"},
+        "e2e": {"value": val, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+    from paper_1704_02524_gb300 import hj
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = W.c3_smooth_nonconvex(nq=a.nq)
+    spec = wl.problems[0]
+    nq = wl.nq
+    q_begin = rank * nq  # weak scaling: every rank solves its own batch of nq queries
+    if rank > 0:
+        # other ranks draw their own queries from the same distribution
+        rng = np.random.default_rng(1000 + rank)
+        wl.x = W.f32(rng.uniform(-1, 1, wl.x.shape))
+    x = torch.tensor(wl.x, dtype=torch.float32, device=dev)
+    t = torch.tensor(wl.t, dtype=torch.float32, device=dev)
+    ns = torch.tensor(wl.n_steps, dtype=torch.int32, device=dev)
+    opts = hj.opts_from_dict(wl.solver, hj.HJ_PREC_FP32, 64)
+    ctx = hj.hj_create([spec], opts, local)
+    phi = torch.empty(nq, dtype=torch.float64, device=dev)
+    vout = torch.zeros(nq, 20, dtype=torch.float32, device=dev)
+    status = torch.empty(nq, dtype=torch.int32, device=dev)
+    out = (phi, vout, status)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        hj.hj_solve(ctx, x, t, ns, None, q_begin, out)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    infos = []
+    with ClockSampler(local) as clk:
+        for k in range(a.steps):
+            flush.fill_(float(k))  # evict L2 between timed steps (outside the timed region)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            infos.append(hj.hj_last_solve_info(ctx))  # synchronises after the end event
+        torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ms_steps = [e0.elapsed_time(e1) for e0, e1 in ev]
+    ms = sum(ms_steps) / len(ms_steps)
+    ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = nq * world / (ms_max / 1e3)
+    clocks = clk.summary()
+
+    # roofline of the dominant kernel (the persistent descent kernel)
+    flops = sum(i["algorithmic_flops"] for i in infos)
+    desc_s = sum(i["descent_ms"] for i in infos) / 1e3
+    achieved = flops / desc_s / 1e12
+    peaks, peak_src = _peaks()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_fp32 = nsm * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    info = infos[-1]
+
+    # e2e through the C ABI with host buffers: pinned H2D of x, t, N, solve, D2H of phi, v, status
+    hx = torch.tensor(wl.x, dtype=torch.float32).pin_memory()
+    ht = torch.tensor(wl.t, dtype=torch.float32).pin_memory()
+    hn = torch.tensor(wl.n_steps, dtype=torch.int32).pin_memory()
+    hphi = torch.empty(nq, dtype=torch.float64).pin_memory()
+    hv = torch.empty(nq, 20, dtype=torch.float32).pin_memory()
+    hst = torch.empty(nq, dtype=torch.int32).pin_memory()
+    dx, dt_, dn = torch.empty_like(x), torch.empty_like(t), torch.empty_like(ns)
+    h2d = hx.numel() * 4 + ht.numel() * 4 + hn.numel() * 4
+    d2h = hphi.numel() * 8 + hv.numel() * 4 + hst.numel() * 4
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        dx.copy_(hx, non_blocking=True)
+        dt_.copy_(ht, non_blocking=True)
+        dn.copy_(hn, non_blocking=True)
+        hj.hj_solve(ctx, dx, dt_, dn, None, q_begin, out)
+        hphi.copy_(phi, non_blocking=True)
+        hv.copy_(vout, non_blocking=True)
+        hst.copy_(status, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / a.steps
+    e2e_t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_val = nq * world / (float(e2e_t.item()) / 1e3)
+    phi_np = hphi.numpy().copy()
+    st_np = hst.numpy().copy()
+
+    # plain path: Algorithm 1 (cyclic CD) with central differences, same workload
+    plain = None
+    if not a.no_plain:
+        solver_cd = W.c3_cd_solver()
+        ctx_cd = hj.hj_create([spec], hj.opts_from_dict(solver_cd, hj.HJ_PREC_FP32, 64), local)
+        phi_cd = torch.empty_like(phi)
+        out_cd = (phi_cd, torch.zeros_like(vout), torch.empty_like(status))
+        hj.hj_solve(ctx_cd, x, t, ns, None, q_begin, out_cd)  # warm-up
+        torch.cuda.synchronize()
+        flush.fill_(1.0)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        hj.hj_solve(ctx_cd, x, t, ns, None, q_begin, out_cd)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cd_ms = c0.elapsed_time(c1)
+        icd = hj.hj_last_solve_info(ctx_cd)
+        plain = {"value": nq / (cd_ms / 1e3), "unit": "queries/s", "ms_per_step": cd_ms,
+                 "descent": "cyclic coordinate descent, central differences h=2^-10",
+                 "functional_evals": icd["functional_evals"],
+                 "achieved_tflops": icd["algorithmic_flops"] / (icd["descent_ms"] / 1e3) / 1e12,
+                 "phi": phi_cd.cpu().numpy()}
+        ctx_cd.close()
+
+    result = None
+    if rank == 0:
+        cpu = None
+        acc = None
+        if not a.no_cpu and world == 1:
+            ids = np.arange(0, nq, nq // CPU_SAMPLE)[:CPU_SAMPLE]
+            sec, ref, threads = _time_oracle(wl, ids)
+            cpu = {"value": CPU_SAMPLE / sec, "unit": "queries/s", "cores": threads, "kind": "oracle",
+                   "sample": f"{CPU_SAMPLE} queries (every {nq // CPU_SAMPLE}th) of the workload, all 16 starts, "
+                             f"FP64, {sec:.1f} s wall"}
+            err = np.abs(phi_np[ids] - ref["phi"]) / (1 + np.abs(ref["phi"]))
+            acc = {"sample": CPU_SAMPLE, "max_rel_err": float(err.max()),
+                   "frac_within_1e-4": float(np.mean(err <= 1e-4)),
+                   "certified_agree": float(np.mean((st_np[ids] & 1) == (ref["status"] & 1)))}
+            if plain is not None:
+                errp = np.abs(plain["phi"][ids] - ref["phi"]) / (1 + np.abs(ref["phi"]))
+                plain["max_rel_err_vs_oracle"] = float(errp.max())
+                plain["frac_within_1e-4"] = float(np.mean(errp <= 1e-4))
+        if plain is not None:
+            plain.pop("phi")
+        result = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "d": 20, "queries_per_gpu": nq, "guesses": 16, "n_steps": 64, "t": 0.5,
+                       "descent": "gradient descent, discrete-adjoint gradient, per-coordinate step control",
+                       "certificate": "fp64", "max_trials": 20, "l2": "flushed between timed steps (256 MB write)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+                         "frac": achieved / peak_fp32, "traffic": None,
+                         "kernel": "k_desc (persistent descent, adjoint)",
+                         "peak_note": f"FP32 FMA {nsm} SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                                      f"({peak_src} max SM clock)"},
+            "e2e": {"value": e2e_val, "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
+            "clocks": clocks,
+            "detail": {"descent_ms_per_step": desc_s * 1e3 / len(infos),
+                       "certify_ms_per_step": sum(i["certify_ms"] for i in infos) / len(infos),
+                       "gradients_per_step": info["gradient_evals"], "pairs_per_step": info["n_pairs"],
+                       "iterations_per_pair": info["iterations"] / max(1, info["n_pairs"]),
+                       "threads_per_pair": info["threads_per_pair"], "comps_per_thread": info["comps_per_thread"],
+                       "algorithmic_tflop_per_step": flops / len(infos) / 1e12,
+                       "certified_frac": float(np.mean(st_np & 1))},
+            "plain_cd_fd": plain,
+            "accuracy_vs_oracle": acc,
+            "cpu_baseline": cpu,
+        }
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    if result is not None:
+        print(json.dumps(result))
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -178,6 +178,7 @@ typedef struct {
     double descent_ms;          /* device time of the descent launches (CUDA events) */
     double certify_ms;          /* device time of the certificate launches           */
     double total_ms;            /* device time of the whole hj_solve                 */
+    int64_t kernel_launches;    /* kernels the library launched in the last hj_solve */
 } hj_solve_info;
 
 /*

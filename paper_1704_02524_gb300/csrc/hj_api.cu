@@ -163,6 +163,7 @@ struct hj_ctx {
     std::vector<cudaEvent_t> ev_desc, ev_cert;
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
     int n_desc_ev = 0, n_cert_ev = 0;
+    long long launches = 0;
     std::string err;
 };
 
@@ -699,6 +700,7 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
     ctx->n_desc_ev = ctx->n_cert_ev = 0;
     CU(cudaEventRecord(ctx->ev_begin, s));
     CU(cudaMemsetAsync(ctx->stats, 0, sizeof(unsigned long long) * 8 * ctx->np, s));
+    ctx->launches = 6;  // count, offsets, three scan phases, pair build
     CU(launch_count(n_queries, pidx, ctx->d_pg, ctx->starts, ctx->pcount, ctx->np, ctx->seg_begin, ctx->wl_count, s));
     CU(launch_scan(n_queries, ctx->starts, ctx->pair_base, ctx->block_sums, s));
     CU(launch_build_pairs(n_queries, pidx, ctx->d_pg, ctx->pair_base, ctx->pair_q, ctx->pair_slot, ctx->pair_round,
@@ -741,6 +743,7 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                 a.x = (const float *)x; a.t = (const float *)t; a.vfin = (float *)ctx->vfin;
                 CU(L(&a, persistent_grid(ctx, fn), s));
             }
+            ctx->launches++;
         }
         if (ctx->timing) { st = record(ctx, ctx->ev_desc, ctx->n_desc_ev++, s); if (st != HJ_OK) return st; }
         for (int p = 0; p < ctx->np; ++p) {
@@ -774,6 +777,7 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                 a.x = (const float *)x; a.t = (const float *)t; a.v = (const float *)ctx->vfin;
                 CU(k.cert_pairs(&a, rows_grid(ctx, k.f_cert_pairs, cap, tpp_c[p]), s));
             }
+            ctx->launches++;
         }
         if (ctx->timing) { st = record(ctx, ctx->ev_cert, ctx->n_cert_ev++, s); if (st != HJ_OK) return st; }
         const int schedule = round < ctx->opts.max_rounds;
@@ -803,6 +807,7 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
         a.v_out = v_out;
         a.status = status_out;
         CU(launch_select(a, ctx->prec, s));
+        ctx->launches++;
     }
     CU(cudaEventRecord(ctx->ev_end, s));
     return HJ_OK;
@@ -847,6 +852,7 @@ hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out)
     out->descent_ms = desc_ms;
     out->certify_ms = cert_ms;
     out->descent_launches = ctx->n_desc_ev / 2;
+    out->kernel_launches = ctx->launches;
     return HJ_OK;
 }
 

@@ -54,7 +54,7 @@ class hj_solve_info(C.Structure):
                 ("functional_evals", C.c_int64), ("gradient_evals", C.c_int64), ("rk4_steps", C.c_int64),
                 ("algorithmic_flops", C.c_double), ("certify_flops", C.c_double), ("threads_per_pair", C.c_int),
                 ("comps_per_thread", C.c_int), ("descent_launches", C.c_int), ("descent_ms", C.c_double),
-                ("certify_ms", C.c_double), ("total_ms", C.c_double)]
+                ("certify_ms", C.c_double), ("total_ms", C.c_double), ("kernel_launches", C.c_int64)]
 
 
 _lib = None

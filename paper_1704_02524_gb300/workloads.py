@@ -237,3 +237,11 @@ WORKLOADS = {
     "linear_quad_d64_lax": c4_linear_quad,
     "mixed_persistent": c5_mixed,
 }
+
+
+def c3_cd_solver() -> Dict:
+    """Constants of the plain path on the d=20 Hopf workload: Algorithm 1
+    (cyclic coordinate descent) with central differences, h = 2^-10 (the
+    binary32 functional carries ~1e-6 absolute rounding, so smaller steps
+    drown the difference in noise), at most 100 sweeps."""
+    return solver_constants(grad="fd_central", fd_h=2.0 ** -10, max_iters=100 * 20, n_guesses=16)
