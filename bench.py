@@ -42,6 +42,8 @@ def _args():
     ap.add_argument("--nq", type=int, default=65536)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain CD-FD measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
+    ap.add_argument("--tpp", type=int, default=0, help="threads per pair of the descent (0: library choice)")
+    ap.add_argument("--ck", type=int, default=0, help="adjoint checkpoint interval (0: library choice)")
     return ap.parse_args()
 
 
@@ -177,6 +179,8 @@ def run_ours(a):
     ns = torch.tensor(wl.n_steps, dtype=torch.int32, device=dev)
     opts = hj.opts_from_dict(wl.solver, hj.HJ_PREC_FP32, 64)
     ctx = hj.hj_create([spec], opts, local)
+    if a.tpp or a.ck:
+        hj.hj_set_tuning(ctx, 0, a.tpp, a.ck)
     phi = torch.empty(nq, dtype=torch.float64, device=dev)
     vout = torch.zeros(nq, 20, dtype=torch.float32, device=dev)
     status = torch.empty(nq, dtype=torch.int32, device=dev)
@@ -314,6 +318,7 @@ def run_ours(a):
             "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
             "clocks": clocks,
             "detail": {"descent_ms_per_step": desc_s * 1e3 / len(infos),
+                       "descent_round0_ms_per_step": sum(i["descent_ms_round0"] for i in infos) / len(infos),
                        "certify_ms_per_step": sum(i["certify_ms"] for i in infos) / len(infos),
                        "gradients_per_step": info["gradient_evals"], "pairs_per_step": info["n_pairs"],
                        "iterations_per_pair": info["iterations"] / max(1, info["n_pairs"]),

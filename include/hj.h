@@ -171,7 +171,7 @@ typedef struct {
     int64_t gradient_evals;     /* adjoint gradients                                */
     int64_t rk4_steps;          /* RK4 steps of all evaluations (forward sweeps)    */
     double algorithmic_flops;   /* fp32/fp64 arithmetic of the descent, FMA = 2     */
-    double certify_flops;       /* FP64 arithmetic of the certificate evaluations   */
+    double certify_flops;       /* arithmetic of the in-kernel certificate passes   */
     int threads_per_pair;       /* of the first problem's descent launch            */
     int comps_per_thread;
     int descent_launches;       /* rounds run (each: one descent launch per problem) */
@@ -179,6 +179,7 @@ typedef struct {
     double certify_ms;          /* device time of the certificate launches           */
     double total_ms;            /* device time of the whole hj_solve                 */
     int64_t kernel_launches;    /* kernels the library launched in the last hj_solve */
+    double descent_ms_round0;   /* device time of the first round's descent launches */
 } hj_solve_info;
 
 /*
@@ -221,7 +222,10 @@ hj_status hj_certify(hj_ctx *ctx, int64_t n, const int32_t *problem_idx, const v
 /*
  * hj_solve -- phi(x, t) for n_queries queries: random starts, descent,
  * certificate, reseeding, best of the starts (certified first; ties go to
- * the lowest slot), phi from the FP64 value at the chosen v.
+ * the lowest slot), phi from the FP64 value at the chosen v.  The
+ * certificate of each start is evaluated in the context precision at the
+ * end of its descent; in FP32 a residual inside [0.75, 1.34] x cert_tol is
+ * re-evaluated in FP64 before the pass/fail decision.
  * q_begin: global index of the first query (the Philox counter uses
  * q_begin + row), so a batch split across devices draws the same starts.
  * phi_out [nq] double, v_out [nq, ld] (the chosen v, an estimate of
@@ -244,12 +248,15 @@ hj_status hj_guesses(hj_ctx *ctx, int64_t n, const int64_t *query_id, const int3
 hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out);
 
 /*
- * hj_set_launch -- override the threads per (query, start) pair used for
- * problem `problem` (tpp in {1,2,4,8,16,32}; 0 restores the automatic
- * choice).  Returns HJ_EUNSUPPORTED when no kernel is built for the
- * resulting components per thread.
+ * hj_set_tuning -- launch parameters of problem `problem` (used by the
+ * autotuner and for experiments): tpp = threads per (query, start) pair of
+ * the descent and gradient kernels, in {1,2,4,8,16,32} (0: automatic);
+ * ck_interval = RK4 steps between checkpoints of the adjoint, in [1, 16]
+ * (0: automatic, the smallest interval whose checkpoint storage fits a
+ * fixed per-thread budget).  Returns HJ_EUNSUPPORTED when no kernel is built
+ * for the resulting components per thread.
  */
-hj_status hj_set_launch(hj_ctx *ctx, int problem, int tpp);
+hj_status hj_set_tuning(hj_ctx *ctx, int problem, int tpp, int ck_interval);
 
 /* Message of the last error on ctx (or of the last failed hj_create when ctx is NULL). */
 const char *hj_last_error(const hj_ctx *ctx);

@@ -60,7 +60,10 @@ thread_local std::string g_create_error;
 enum Kind { K_EVAL = 0, K_GRAD = 1, K_CD = 2, K_GD = 3, K_CERT = 4 };
 
 // Arithmetic per RK4 step of one pair (FMA = 2, add/mul = 1, sin/cos and
-// rsqrt not counted), from the operations written in hj_device.cuh.
+// rsqrt not counted), from the operations written in hj_device.cuh.  The
+// reverse step counts only the vector-Jacobian products (the stage
+// intermediates they reuse and the recomputation of stage inputs from
+// checkpoints are not counted).
 struct FlopModel {
     double fwd_step;  // one forward step: 4 field evaluations + stage combinations
     double adj_step;  // one reverse step: 4 vector-Jacobian products + combinations
@@ -71,10 +74,10 @@ FlopModel flop_model(int fam, int pr, int d)
     double fld = 0, vjp = 0;
     switch (fam) {
     case HJ_FAM_QUAD_ISO: fld = 3.0 * d + 1; vjp = 2.0 * d; break;
-    case HJ_FAM_SPEED_QUAD: fld = 6.0 * d + (pr == HJ_HOPF ? 10 : 8); vjp = 12.0 * d + 25; break;
+    case HJ_FAM_SPEED_QUAD: fld = 6.0 * d + (pr == HJ_HOPF ? 10 : 8); vjp = 8.0 * d + 25; break;
     case HJ_FAM_SMOOTH_NONCONVEX:
         fld = (pr == HJ_LAX ? 11.0 : 10.0) * d + 7;
-        vjp = (pr == HJ_LAX ? 28.0 : 22.0) * d + 20;
+        vjp = (pr == HJ_LAX ? 13.0 : 11.0) * d + 20;
         break;
     default: break;
     }
@@ -144,16 +147,18 @@ struct hj_ctx {
     std::vector<hj_problem_desc> desc;
     std::vector<std::vector<double>> params;
     std::vector<DevProblem> dev;
-    std::vector<int> tpp_override;
+    std::vector<int> tpp_override, ck_interval;
     int32_t *d_pg = nullptr, *d_pd = nullptr, *d_pprin = nullptr;
     // scratch
     long long cap_q = 0, cap_p = 0;
-    int32_t *starts = nullptr, *pair_base = nullptr, *block_sums = nullptr, *trials = nullptr, *qflags = nullptr;
-    int32_t *pair_q = nullptr, *pair_slot = nullptr, *pair_round = nullptr, *iters = nullptr, *wl = nullptr;
+    int32_t *starts = nullptr, *pair_base = nullptr, *block_sums = nullptr, *trials = nullptr, *qflags = nullptr,
+            *best_pid = nullptr;
+    int32_t *pair_q = nullptr, *pair_slot = nullptr, *pair_round = nullptr, *iters = nullptr, *wl = nullptr,
+            *amb_wl = nullptr;
     uint8_t *flags = nullptr, *pP = nullptr;
     double *pF = nullptr, *pR = nullptr;
     void *vfin = nullptr;
-    int32_t *pcount = nullptr, *seg_begin = nullptr, *wl_count = nullptr, *cursor = nullptr;
+    int32_t *pcount = nullptr, *seg_begin = nullptr, *wl_count = nullptr, *cursor = nullptr, *amb_count = nullptr;
     unsigned long long *stats = nullptr;
     // last solve
     cudaStream_t last_stream = nullptr;
@@ -322,8 +327,8 @@ hj_status ensure_scratch(hj_ctx *ctx, long long nq, long long npairs)
 {
     if (nq > ctx->cap_q) {
         cudaFree(ctx->starts); cudaFree(ctx->pair_base); cudaFree(ctx->block_sums);
-        cudaFree(ctx->trials); cudaFree(ctx->qflags);
-        ctx->starts = ctx->pair_base = ctx->block_sums = ctx->trials = ctx->qflags = nullptr;
+        cudaFree(ctx->trials); cudaFree(ctx->qflags); cudaFree(ctx->best_pid);
+        ctx->starts = ctx->pair_base = ctx->block_sums = ctx->trials = ctx->qflags = ctx->best_pid = nullptr;
         ctx->cap_q = 0;
         long long nb = (nq + 1023) / 1024 + 1;
         CU(cudaMalloc(&ctx->starts, sizeof(int32_t) * nq));
@@ -331,13 +336,14 @@ hj_status ensure_scratch(hj_ctx *ctx, long long nq, long long npairs)
         CU(cudaMalloc(&ctx->block_sums, sizeof(int32_t) * nb));
         CU(cudaMalloc(&ctx->trials, sizeof(int32_t) * nq));
         CU(cudaMalloc(&ctx->qflags, sizeof(int32_t) * nq));
+        CU(cudaMalloc(&ctx->best_pid, sizeof(int32_t) * nq));
         ctx->cap_q = nq;
     }
     if (npairs > ctx->cap_p) {
         cudaFree(ctx->pair_q); cudaFree(ctx->pair_slot); cudaFree(ctx->pair_round); cudaFree(ctx->iters);
         cudaFree(ctx->wl); cudaFree(ctx->flags); cudaFree(ctx->pP); cudaFree(ctx->pF); cudaFree(ctx->pR);
-        cudaFree(ctx->vfin);
-        ctx->pair_q = ctx->pair_slot = ctx->pair_round = ctx->iters = ctx->wl = nullptr;
+        cudaFree(ctx->vfin); cudaFree(ctx->amb_wl);
+        ctx->pair_q = ctx->pair_slot = ctx->pair_round = ctx->iters = ctx->wl = ctx->amb_wl = nullptr;
         ctx->flags = ctx->pP = nullptr;
         ctx->pF = ctx->pR = nullptr;
         ctx->vfin = nullptr;
@@ -348,6 +354,7 @@ hj_status ensure_scratch(hj_ctx *ctx, long long nq, long long npairs)
         CU(cudaMalloc(&ctx->pair_round, sizeof(int32_t) * npairs));
         CU(cudaMalloc(&ctx->iters, sizeof(int32_t) * npairs));
         CU(cudaMalloc(&ctx->wl, sizeof(int32_t) * npairs));
+        CU(cudaMalloc(&ctx->amb_wl, sizeof(int32_t) * npairs));
         CU(cudaMalloc(&ctx->flags, npairs));
         CU(cudaMalloc(&ctx->pP, npairs));
         CU(cudaMalloc(&ctx->pF, sizeof(double) * npairs));
@@ -410,6 +417,7 @@ RowArgs<T> row_args(hj_ctx *ctx, int p, int tpp, int64_t n, const int32_t *pidx,
     a.pfilter = p;
     a.quad = ctx->opts.quad;
     a.kahan = ctx->opts.kahan;
+    a.ck_interval = ctx->ck_interval[p];
     return a;
 }
 
@@ -447,6 +455,7 @@ hj_status hj_create(const hj_problem_desc *problems, int n_problems, const hj_so
     ctx->params.resize(n_problems);
     ctx->dev.resize(n_problems);
     ctx->tpp_override.assign(n_problems, 0);
+    ctx->ck_interval.assign(n_problems, 0);
     for (int i = 0; i < n_problems; ++i) {
         ctx->params[i].assign(problems[i].params, problems[i].params + problems[i].n_params);
         ctx->desc[i].params = ctx->params[i].data();
@@ -503,6 +512,7 @@ hj_status hj_create(const hj_problem_desc *problems, int n_problems, const hj_so
     CUC(cudaMalloc(&ctx->seg_begin, sizeof(int32_t) * (n_problems + 1)));
     CUC(cudaMalloc(&ctx->wl_count, sizeof(int32_t) * n_problems));
     CUC(cudaMalloc(&ctx->cursor, sizeof(int32_t) * n_problems));
+    CUC(cudaMalloc(&ctx->amb_count, sizeof(int32_t) * n_problems));
     CUC(cudaMalloc(&ctx->stats, sizeof(unsigned long long) * 8 * n_problems));
     CUC(cudaMemset(ctx->stats, 0, sizeof(unsigned long long) * 8 * n_problems));
     CUC(cudaEventCreate(&ctx->ev_begin));
@@ -524,7 +534,7 @@ hj_status hj_destroy(hj_ctx *ctx)
     void *ptrs[] = {ctx->d_pg, ctx->d_pd, ctx->d_pprin, ctx->starts, ctx->pair_base, ctx->block_sums, ctx->trials,
                     ctx->qflags, ctx->pair_q, ctx->pair_slot, ctx->pair_round, ctx->iters, ctx->wl, ctx->flags,
                     ctx->pP, ctx->pF, ctx->pR, ctx->vfin, ctx->pcount, ctx->seg_begin, ctx->wl_count, ctx->cursor,
-                    ctx->stats};
+                    ctx->stats, ctx->amb_wl, ctx->amb_count, ctx->best_pid};
     for (void *p : ptrs) cudaFree(p);
     for (auto e : ctx->ev_desc) cudaEventDestroy(e);
     for (auto e : ctx->ev_cert) cudaEventDestroy(e);
@@ -536,20 +546,24 @@ hj_status hj_destroy(hj_ctx *ctx)
 
 const char *hj_last_error(const hj_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
-hj_status hj_set_launch(hj_ctx *ctx, int problem, int tpp)
+hj_status hj_set_tuning(hj_ctx *ctx, int problem, int tpp, int ck_interval)
 {
     if (!ctx) return HJ_EINVAL;
     if (problem < 0 || problem >= ctx->np) return fail(ctx, HJ_EINVAL, "problem %d outside [0, %d)", problem, ctx->np);
     if (tpp != 0 && tpp != 1 && tpp != 2 && tpp != 4 && tpp != 8 && tpp != 16 && tpp != 32)
         return fail(ctx, HJ_EINVAL, "tpp must be 0 or a power of two <= 32");
+    if (ck_interval < 0 || ck_interval > MAX_SEG)
+        return fail(ctx, HJ_EINVAL, "ck_interval must be in [0, %d]", MAX_SEG);
     int old = ctx->tpp_override[problem];
     ctx->tpp_override[problem] = tpp;
     int t, c;
     const int kind = ctx->opts.grad == HJ_GRAD_ADJOINT ? K_GD : K_CD;
-    if (!choose(ctx, problem, kind, &t, &c) || !choose(ctx, problem, K_EVAL, &t, &c)) {
+    if (!choose(ctx, problem, kind, &t, &c) || !choose(ctx, problem, K_EVAL, &t, &c) ||
+        !choose(ctx, problem, K_GRAD, &t, &c)) {
         ctx->tpp_override[problem] = old;
         return fail(ctx, HJ_EUNSUPPORTED, "no kernel for d=%d with %d threads per pair", ctx->desc[problem].d, tpp);
     }
+    ctx->ck_interval[problem] = ck_interval;
     return HJ_OK;
 }
 
@@ -708,6 +722,7 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
     const SolverDev S = solver_dev(ctx->opts);
     for (int round = 0; round <= ctx->opts.max_rounds; ++round) {
         CU(cudaMemsetAsync(ctx->cursor, 0, sizeof(int32_t) * ctx->np, s));
+        CU(cudaMemsetAsync(ctx->amb_count, 0, sizeof(int32_t) * ctx->np, s));
         if (ctx->timing) { st = record(ctx, ctx->ev_desc, ctx->n_desc_ev++, s); if (st != HJ_OK) return st; }
         for (int p = 0; p < ctx->np; ++p) {
             const KSet &k = kset(ctx, p, c_d[p]);
@@ -719,6 +734,7 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                 a.nsteps = n_steps;
                 a.q_begin = q_begin;
                 a.S = S;
+                a.S.ck_interval = ctx->ck_interval[p];
                 a.wl = ctx->wl;
                 a.seg_begin = ctx->seg_begin;
                 a.wl_count = ctx->wl_count;
@@ -729,6 +745,12 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                 a.iters = ctx->iters;
                 a.flags = ctx->flags;
                 a.stats = ctx->stats + 8 * p;
+                a.pF = ctx->pF;
+                a.pR = ctx->pR;
+                a.pP = ctx->pP;
+                a.amb_wl = ctx->amb_wl;
+                a.amb_count = ctx->amb_count;
+                a.tol = ctx->opts.cert_tol;
             };
             if (ctx->prec) {
                 DescArgs<double> a{};
@@ -758,14 +780,15 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                 a.pass = ctx->pP;
                 a.tol = ctx->opts.cert_tol;
                 a.quad = ctx->opts.quad;
-                a.wl = ctx->wl;
+                a.wl = ctx->amb_wl;
                 a.seg_begin = ctx->seg_begin;
-                a.wl_count = ctx->wl_count;
+                a.wl_count = ctx->amb_count;
                 a.problem = p;
                 a.pair_q = ctx->pair_q;
             };
-            // the pair-mode grid covers a full round-0 list of this problem
-            const long long cap = (long long)n_queries * ctx->desc[p].n_guesses;
+            // FP64 certificate of the starts whose binary32 residual fell in
+            // the band around the tolerance (few): a small grid suffices
+            const long long cap = std::min<long long>((long long)n_queries * ctx->desc[p].n_guesses, 1 << 16);
             if (ctx->prec) {
                 CertArgs<double> a{};
                 fill(a);
@@ -806,9 +829,39 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
         a.phi = phi_out;
         a.v_out = v_out;
         a.status = status_out;
+        a.best_pid = ctx->best_pid;
         CU(launch_select(a, ctx->prec, s));
         ctx->launches++;
     }
+    // phi in FP64 at each query's chosen start
+    for (int p = 0; p < ctx->np; ++p) {
+        const KSet &k = kset(ctx, p, c_c[p]);
+        auto fill = [&](auto &a) {
+            a.P = ctx->dev[p].pd;
+            a.tpp = tpp_c[p];
+            a.n = n_queries;
+            a.nsteps = n_steps;
+            a.n_default = ctx->opts.n_steps_default;
+            a.quad = ctx->opts.quad;
+            a.pidx = pidx;
+            a.pfilter = p;
+            a.best_pid = ctx->best_pid;
+            a.phi = phi_out;
+        };
+        if (ctx->prec) {
+            CertArgs<double> a{};
+            fill(a);
+            a.x = (const double *)x; a.t = (const double *)t; a.v = (const double *)ctx->vfin;
+            CU(k.cert_final(&a, rows_grid(ctx, k.f_cert_final, n_queries, tpp_c[p]), s));
+        } else {
+            CertArgs<float> a{};
+            fill(a);
+            a.x = (const float *)x; a.t = (const float *)t; a.v = (const float *)ctx->vfin;
+            CU(k.cert_final(&a, rows_grid(ctx, k.f_cert_final, n_queries, tpp_c[p]), s));
+        }
+        ctx->launches++;
+    }
+    if (ctx->timing) { st = record(ctx, ctx->ev_cert, ctx->n_cert_ev++, s); if (st != HJ_OK) return st; }
     CU(cudaEventRecord(ctx->ev_end, s));
     return HJ_OK;
 }
@@ -833,20 +886,28 @@ hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out)
         out->rk4_steps += (int64_t)c[3];
         out->n_pairs += (int64_t)c[5];
         out->algorithmic_flops += (double)c[3] * fm.fwd_step + (double)c[4] * fm.adj_step;
-        out->certify_flops += (double)c[6] * fm.fwd_step;
+        out->certify_flops += (double)c[7] * fm.fwd_step;
     }
     out->threads_per_pair = ctx->last_tpp;
     out->comps_per_thread = ctx->last_c;
     float ms = 0;
     double desc_ms = 0, cert_ms = 0;
+    double round0_ms = 0;
     for (int i = 0; i + 1 < ctx->n_desc_ev; i += 2) {
         CU(cudaEventElapsedTime(&ms, ctx->ev_desc[i], ctx->ev_desc[i + 1]));
         desc_ms += ms;
+        if (i == 0) round0_ms = ms;
         if (i / 2 < ctx->n_cert_ev) {
             CU(cudaEventElapsedTime(&ms, ctx->ev_desc[i + 1], ctx->ev_cert[i / 2]));
             cert_ms += ms;
         }
     }
+    if (ctx->n_cert_ev > ctx->n_desc_ev / 2 && ctx->n_cert_ev >= 2) {
+        // final FP64 evaluation of phi: from the last select to the last event
+        CU(cudaEventElapsedTime(&ms, ctx->ev_cert[ctx->n_cert_ev - 2], ctx->ev_cert[ctx->n_cert_ev - 1]));
+        cert_ms += ms;
+    }
+    out->descent_ms_round0 = round0_ms;
     CU(cudaEventElapsedTime(&ms, ctx->ev_begin, ctx->ev_end));
     out->total_ms = ms;
     out->descent_ms = desc_ms;

@@ -22,7 +22,9 @@ namespace hjd {
 
 constexpr int DPAD = 1024;   // parameter vectors are zero padded to this length
 constexpr int MAX_N = 256;   // RK4 steps supported by the adjoint buffers
-constexpr int MAX_SEG = 16;  // checkpoint segment length cap (ceil(sqrt(MAX_N)))
+constexpr int MAX_CK = 128;  // checkpoints per gradient (so N <= MAX_CK * interval)
+constexpr int MAX_SEG = 16;  // checkpoint interval cap
+constexpr int CK_BUDGET = 3072;  // bytes of checkpoint + segment storage per thread (automatic interval)
 
 // ---------------------------------------------------------------------------
 // Problem parameters on the device (one problem per launch).
@@ -43,6 +45,7 @@ struct ProbDev {
 // Solver constants on the device.
 struct SolverDev {
     int quad, grad, max_iters, halving_period, adapt, max_trials, max_rounds, guess_dist, kahan, n_default;
+    int ck_interval;  // adjoint checkpoint interval K (0: automatic)
     double fd_h, step, eps, grow, shrink, step_max, cert_tol;
     unsigned long long seed;
 };
@@ -164,11 +167,12 @@ __device__ __forceinline__ T start_component(unsigned long long seed, long long 
 }
 
 // ---------------------------------------------------------------------------
-// Per-thread copies of the per-component parameters.
+// Per-thread copies of the per-component parameters the field needs (the
+// initial-data parameters are read from memory at the terminal term).
 // ---------------------------------------------------------------------------
 template <typename T, int C>
 struct TP {
-    T w[C], e[C], ga[C], gs2[C], gis2[C];
+    T w[C], e[C];
     __device__ void load(const ProbDev<T> &P, const Grp &g)
     {
 #pragma unroll
@@ -176,212 +180,229 @@ struct TP {
             int i = g.lane + k * g.tpp;
             w[k] = P.w[i];
             e[k] = P.e[i];
-            ga[k] = P.ga[i];
-            gs2[k] = P.gs2[i];
-            gis2[k] = P.gis2[i];
         }
     }
 };
 
 // ---------------------------------------------------------------------------
-// Families.  field(): dz/dtau = (-dH/dp, +dH/dx) and the running cost L
-// (Lax: <p, dH/dp> - H;  Hopf: H - <dH/dx, gamma>).  vjp(): for weights
-// (ag, ap) on the state rows and b on the cost row, the products
-//   rg = ag.d(-H_p)/dgamma + ap.d(H_x)/dgamma + b dL/dgamma, and the same in p.
+// Families.  Each family splits its work at a stage input Z = (gamma, p):
+//   prep()     the quantities that need reductions or special functions
+//              (dot products, sin/cos, rsqrt), gathered in an FI record;
+//   field_fi() dZ/dtau = (-dH/dp, +dH/dx) and the running cost L
+//              (Lax: <p, dH/dp> - H;  Hopf: H - <dH/dx, gamma>) from FI;
+//   vjp_fi()   for weights (ag, ap) on the state rows and b on the cost row,
+//              rg = ag.d(-H_p)/dgamma + ap.d(H_x)/dgamma + b dL/dgamma and
+//              the same in p, from FI (one reduction round).
+// The adjoint reuses the FI of a stage for its vector-Jacobian product.
 // Speed c(gamma) = 1 + sin(u)/2, u = <w, gamma>, c' = cos(u)/2, c'' = -sin(u)/2.
 // ---------------------------------------------------------------------------
 template <typename T, int C, int FAM, int PR>
 struct Family;
 
-// H = |p|^2/2: dz/dtau = (-p, 0), L = |p|^2/2 for both principles.
+// H = |p|^2/2: dZ/dtau = (-p, 0), L = |p|^2/2 for both principles.
 template <typename T, int C, int PR>
 struct Family<T, C, HJ_FAM_QUAD_ISO, PR> {
-    __device__ static __forceinline__ void field(const Grp &g, const TP<T, C> &tp, const T *gam, const T *p, T *dg,
-                                                 T *dp, T &L)
+    struct FI {
+        T pp;
+        T p[C];
+    };
+    __device__ static __forceinline__ void prep(const Grp &g, const TP<T, C> &, T, const T *, const T *p, FI &f)
     {
         T pp = 0;
 #pragma unroll
         for (int k = 0; k < C; ++k) {
-            dg[k] = -p[k];
-            dp[k] = 0;
+            f.p[k] = p[k];
             pp = fma(p[k], p[k], pp);
         }
-        L = (T)0.5 * gsum(g, pp);
+        f.pp = gsum(g, pp);
     }
-    __device__ static __forceinline__ void vjp(const Grp &, const TP<T, C> &, const T *, const T *p, const T *ag,
-                                               const T *, T b, T *rg, T *rp)
+    __device__ static __forceinline__ void field_fi(const TP<T, C> &, const FI &f, T, T *dg, T *dp, T &L)
+    {
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            dg[k] = -f.p[k];
+            dp[k] = 0;
+        }
+        L = (T)0.5 * f.pp;
+    }
+    __device__ static __forceinline__ void vjp_fi(const Grp &, const TP<T, C> &, const FI &f, T, const T *ag,
+                                                  const T *, T b, T *rg, T *rp)
     {
 #pragma unroll
         for (int k = 0; k < C; ++k) {
             rg[k] = 0;
-            rp[k] = fma(b, p[k], -ag[k]);
+            rp[k] = fma(b, f.p[k], -ag[k]);
         }
     }
-    static constexpr int field_flops_per_comp = 3, field_flops_fixed = 2, vjp_flops_per_comp = 2,
-                         vjp_flops_fixed = 0;
 };
 
-// H = c^2 |p|^2/2: dz/dtau = (-c^2 p, c c' |p|^2 w),
+// H = c^2 |p|^2/2: dZ/dtau = (-c^2 p, c c' |p|^2 w),
 // L_Lax = c^2|p|^2/2, L_Hopf = c^2|p|^2/2 - c c' |p|^2 u.
 template <typename T, int C, int PR>
 struct Family<T, C, HJ_FAM_SPEED_QUAD, PR> {
-    __device__ static __forceinline__ void field(const Grp &g, const TP<T, C> &tp, const T *gam, const T *p, T *dg,
-                                                 T *dp, T &L)
+    struct FI {
+        T u, pp, c, c1, c2;
+        T p[C];
+    };
+    __device__ static __forceinline__ void prep(const Grp &g, const TP<T, C> &tp, T, const T *gam, const T *p, FI &f)
     {
         T u = 0, pp = 0;
 #pragma unroll
         for (int k = 0; k < C; ++k) {
             u = fma(tp.w[k], gam[k], u);
             pp = fma(p[k], p[k], pp);
+            f.p[k] = p[k];
         }
         gsum2(g, u, pp);
         T su, cu;
         sin_cos(u, &su, &cu);
-        T c = fma((T)0.5, su, (T)1), c1 = (T)0.5 * cu;
-        T c2 = c * c, fx = c * c1 * pp;
+        f.u = u;
+        f.pp = pp;
+        f.c = fma((T)0.5, su, (T)1);
+        f.c1 = (T)0.5 * cu;
+        f.c2 = (T)-0.5 * su;
+    }
+    __device__ static __forceinline__ void field_fi(const TP<T, C> &tp, const FI &f, T, T *dg, T *dp, T &L)
+    {
+        const T cc = f.c * f.c, fx = f.c * f.c1 * f.pp;
 #pragma unroll
         for (int k = 0; k < C; ++k) {
-            dg[k] = -c2 * p[k];
+            dg[k] = -cc * f.p[k];
             dp[k] = fx * tp.w[k];
         }
-        L = (T)0.5 * c2 * pp;
-        if (PR == HJ_HOPF) L -= fx * u;
+        L = (T)0.5 * cc * f.pp;
+        if (PR == HJ_HOPF) L -= fx * f.u;
     }
-    __device__ static __forceinline__ void vjp(const Grp &g, const TP<T, C> &tp, const T *gam, const T *p,
-                                               const T *ag, const T *ap, T b, T *rg, T *rp)
+    __device__ static __forceinline__ void vjp_fi(const Grp &g, const TP<T, C> &tp, const FI &f, T, const T *ag,
+                                                  const T *ap, T b, T *rg, T *rp)
     {
-        T u = 0, pp = 0, A = 0, Bw = 0;
+        T A = 0, Bw = 0;
 #pragma unroll
         for (int k = 0; k < C; ++k) {
-            u = fma(tp.w[k], gam[k], u);
-            pp = fma(p[k], p[k], pp);
-            A = fma(ag[k], p[k], A);
+            A = fma(ag[k], f.p[k], A);
             Bw = fma(ap[k], tp.w[k], Bw);
         }
-        gsum4(g, u, pp, A, Bw);
-        T su, cu;
-        sin_cos(u, &su, &cu);
-        T c = fma((T)0.5, su, (T)1), c1 = (T)0.5 * cu, cc2 = (T)-0.5 * su;
-        T q = fma(c1, c1, c * cc2);  // d(c c')/du
-        T dEdu = (T)-2 * c * c1 * A + q * pp * Bw;
+        gsum2(g, A, Bw);
+        const T c = f.c, c1 = f.c1;
+        const T q = fma(c1, c1, c * f.c2);  // d(c c')/du
+        T dEdu = (T)-2 * c * c1 * A + q * f.pp * Bw;
         T dLp;
         if (PR == HJ_LAX) {
-            dEdu += b * c * c1 * pp;
+            dEdu += b * c * c1 * f.pp;
             dLp = c * c;
         } else {
-            dEdu -= b * q * pp * u;
-            dLp = c * c - (T)2 * c * c1 * u;
+            dEdu -= b * q * f.pp * f.u;
+            dLp = c * c - (T)2 * c * c1 * f.u;
         }
-        T kp = (T)2 * c * c1 * Bw + b * dLp;
-        T mc2 = -c * c;
+        const T kp = (T)2 * c * c1 * Bw + b * dLp;
+        const T mc2 = -c * c;
 #pragma unroll
         for (int k = 0; k < C; ++k) {
             rg[k] = dEdu * tp.w[k];
-            rp[k] = fma(mc2, ag[k], kp * p[k]);
+            rp[k] = fma(mc2, ag[k], kp * f.p[k]);
         }
     }
-    static constexpr int field_flops_per_comp = 6, field_flops_fixed = 12, vjp_flops_per_comp = 11,
-                         vjp_flops_fixed = 26;
 };
 
 // H = c Phi(p), Phi = sum_i e_i s(p_i), s = sqrt(p^2 + eps):
-// dz/dtau = (-c Phi', Phi c' w), Phi'_i = e_i p_i / s_i,
+// dZ/dtau = (-c Phi', Phi c' w), Phi'_i = e_i p_i / s_i, Phi''_i = e_i eps / s_i^3,
 // L_Lax = c (<p, Phi'> - Phi) = -c eps sum_i e_i / s_i, L_Hopf = Phi (c - c' u).
+// FI keeps er_i = e_i / s_i and Phi'_i = er_i p_i (e_i^2 = 1 on real
+// components, so Phi''_i = eps er_i^3; both are 0 on padding).
 template <typename T, int C, int PR>
 struct Family<T, C, HJ_FAM_SMOOTH_NONCONVEX, PR> {
-    __device__ static __forceinline__ void field(const Grp &g, const TP<T, C> &tp, const T *gam, const T *p, T *dg,
-                                                 T *dp, T &L, T eps)
+    struct FI {
+        T u, c, c1, c2, phi, lax;
+        T er[C], dphi[C];
+        T pl[PR == HJ_LAX ? C : 1];  // p_i, kept for the Lax running cost only
+    };
+    __device__ static __forceinline__ void prep(const Grp &g, const TP<T, C> &tp, T eps, const T *gam, const T *p,
+                                                FI &f)
     {
-        T u = 0;
-#pragma unroll
-        for (int k = 0; k < C; ++k) u = fma(tp.w[k], gam[k], u);
-        u = gsum(g, u);
-        T su, cu;
-        sin_cos(u, &su, &cu);
-        T c = fma((T)0.5, su, (T)1), c1 = (T)0.5 * cu;
-        T phi = 0, lax = 0;
-#pragma unroll
-        for (int k = 0; k < C; ++k) {
-            T q = fma(p[k], p[k], eps);
-            T r = rsq(q);
-            T er = tp.e[k] * r;
-            phi = fma(er, q, phi);   // e s
-            if (PR == HJ_LAX) lax += er;
-            dg[k] = -c * er * p[k];
-        }
-        if (PR == HJ_LAX) gsum2(g, phi, lax);
-        else phi = gsum(g, phi);
-        T fx = phi * c1;
-#pragma unroll
-        for (int k = 0; k < C; ++k) dp[k] = fx * tp.w[k];
-        if (PR == HJ_LAX) L = -c * eps * lax;
-        else L = phi * (c - c1 * u);
-    }
-    __device__ static __forceinline__ void vjp(const Grp &g, const TP<T, C> &tp, const T *gam, const T *p,
-                                               const T *ag, const T *ap, T b, T *rg, T *rp, T eps)
-    {
-        T u = 0, Bw = 0;
+        T u = 0, phi = 0, lax = 0;
 #pragma unroll
         for (int k = 0; k < C; ++k) {
             u = fma(tp.w[k], gam[k], u);
-            Bw = fma(ap[k], tp.w[k], Bw);
+            const T q = fma(p[k], p[k], eps);
+            const T er = tp.e[k] * rsq(q);
+            f.er[k] = er;
+            f.dphi[k] = er * p[k];
+            if constexpr (PR == HJ_LAX) f.pl[k] = p[k];
+            phi = fma(er, q, phi);  // e s
+            if (PR == HJ_LAX) lax += er;
         }
-        gsum2(g, u, Bw);
+        if (PR == HJ_LAX) gsum3(g, u, phi, lax);
+        else gsum2(g, u, phi);
         T su, cu;
         sin_cos(u, &su, &cu);
-        T c = fma((T)0.5, su, (T)1), c1 = (T)0.5 * cu, cc2 = (T)-0.5 * su;
-        T phi = 0, A = 0, pdphi = 0;
-        T r[C];
+        f.u = u;
+        f.phi = phi;
+        f.lax = lax;
+        f.c = fma((T)0.5, su, (T)1);
+        f.c1 = (T)0.5 * cu;
+        f.c2 = (T)-0.5 * su;
+    }
+    __device__ static __forceinline__ void field_fi(const TP<T, C> &tp, const FI &f, T eps, T *dg, T *dp, T &L)
+    {
+        const T fx = f.phi * f.c1, mc = -f.c;
 #pragma unroll
         for (int k = 0; k < C; ++k) {
-            T q = fma(p[k], p[k], eps);
-            r[k] = rsq(q);
-            T er = tp.e[k] * r[k];
-            phi = fma(er, q, phi);
-            T dphi = er * p[k];
-            A = fma(ag[k], dphi, A);
-            if (PR == HJ_LAX) pdphi = fma(p[k], dphi, pdphi);
+            dg[k] = mc * f.dphi[k];
+            dp[k] = fx * tp.w[k];
         }
-        if (PR == HJ_LAX) gsum3(g, phi, A, pdphi);
-        else gsum2(g, phi, A);
-        T dEdu = -c1 * A + phi * cc2 * Bw;
+        if (PR == HJ_LAX) L = mc * eps * f.lax;
+        else L = f.phi * (f.c - f.c1 * f.u);
+    }
+    __device__ static __forceinline__ void vjp_fi(const Grp &g, const TP<T, C> &tp, const FI &f, T eps, const T *ag,
+                                                  const T *ap, T b, T *rg, T *rp)
+    {
+        T A = 0, Bw = 0;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            A = fma(ag[k], f.dphi[k], A);
+            Bw = fma(ap[k], tp.w[k], Bw);
+        }
+        gsum2(g, A, Bw);
+        const T c = f.c, c1 = f.c1;
+        T dEdu = -c1 * A + f.phi * f.c2 * Bw;
         T kd;  // coefficient of Phi'_i in rp
         if (PR == HJ_LAX) {
-            dEdu += b * c1 * (pdphi - phi);
+            // <p, Phi'> - Phi = -eps sum e/s
+            dEdu -= b * c1 * eps * f.lax;
             kd = c1 * Bw;
         } else {
-            dEdu -= b * phi * cc2 * u;
-            kd = c1 * Bw + b * (c - c1 * u);
+            dEdu -= b * f.phi * f.c2 * f.u;
+            kd = c1 * Bw + b * (c - c1 * f.u);
         }
+        // rp_i = Phi''_i (-c ag_i [+ b c p_i for Lax]) + kd Phi'_i, Phi''_i = eps er_i^3
+        const T ce = c * eps;
 #pragma unroll
         for (int k = 0; k < C; ++k) {
-            T er = tp.e[k] * r[k];
-            T dphi = er * p[k];
-            T ddphi = eps * er * r[k] * r[k];  // e eps / s^3
+            T a = -ag[k];
+            if constexpr (PR == HJ_LAX) a = fma(b, f.pl[k], a);
+            const T er = f.er[k];
             rg[k] = dEdu * tp.w[k];
-            T v = fma(-c * ag[k], ddphi, kd * dphi);
-            if (PR == HJ_LAX) v = fma(b * c * p[k], ddphi, v);
-            rp[k] = v;
+            rp[k] = fma(ce * a * er * er, er, kd * f.dphi[k]);
         }
     }
-    static constexpr int field_flops_per_comp = 9, field_flops_fixed = 10, vjp_flops_per_comp = 20,
-                         vjp_flops_fixed = 24;
 };
 
-// Dispatch helpers so every family shares one call form.
+// Whole-stage helpers.
 template <typename T, int C, int FAM, int PR>
 __device__ __forceinline__ void field(const Grp &g, const TP<T, C> &tp, T eps, const T *gam, const T *p, T *dg,
                                       T *dp, T &L)
 {
-    if constexpr (FAM == HJ_FAM_SMOOTH_NONCONVEX) Family<T, C, FAM, PR>::field(g, tp, gam, p, dg, dp, L, eps);
-    else Family<T, C, FAM, PR>::field(g, tp, gam, p, dg, dp, L);
+    typename Family<T, C, FAM, PR>::FI f;
+    Family<T, C, FAM, PR>::prep(g, tp, eps, gam, p, f);
+    Family<T, C, FAM, PR>::field_fi(tp, f, eps, dg, dp, L);
 }
 template <typename T, int C, int FAM, int PR>
 __device__ __forceinline__ void vjp(const Grp &g, const TP<T, C> &tp, T eps, const T *gam, const T *p, const T *ag,
                                     const T *ap, T b, T *rg, T *rp)
 {
-    if constexpr (FAM == HJ_FAM_SMOOTH_NONCONVEX) Family<T, C, FAM, PR>::vjp(g, tp, gam, p, ag, ap, b, rg, rp, eps);
-    else Family<T, C, FAM, PR>::vjp(g, tp, gam, p, ag, ap, b, rg, rp);
+    typename Family<T, C, FAM, PR>::FI f;
+    Family<T, C, FAM, PR>::prep(g, tp, eps, gam, p, f);
+    Family<T, C, FAM, PR>::vjp_fi(g, tp, f, eps, ag, ap, b, rg, rp);
 }
 
 // ---------------------------------------------------------------------------
@@ -391,19 +412,27 @@ __device__ __forceinline__ void vjp(const Grp &g, const TP<T, C> &tp, T eps, con
 //   Hopf term g*(p0) - <x, v>, seed (0, grad g*(p0))
 // ---------------------------------------------------------------------------
 template <typename T, int C, int PR>
-__device__ __forceinline__ T terminal(const Grp &g, const TP<T, C> &tp, int g_kind, const T *x, const T *v,
-                                      const T *gam, const T *p, T *sg, T *sp)
+__device__ __forceinline__ T terminal(const Grp &g, const ProbDev<T> &P, const T *x, const T *v, const T *gam,
+                                      const T *p, T *sg, T *sp)
 {
     T acc = 0;
 #pragma unroll
     for (int k = 0; k < C; ++k) {
+        const int i = g.lane + k * g.tpp;
         if (PR == HJ_LAX) {
-            T gr = (g_kind == HJ_G_QUAD_SHIFT) ? gam[k] - tp.ga[k] : gam[k] * tp.gis2[k];
-            acc = fma((T)0.5 * gr, (g_kind == HJ_G_QUAD_SHIFT) ? gr : gam[k], acc);
+            T gr = (P.g_kind == HJ_G_QUAD_SHIFT) ? gam[k] - __ldg(P.ga + i) : gam[k] * __ldg(P.gis2 + i);
+            acc = fma((T)0.5 * gr, (P.g_kind == HJ_G_QUAD_SHIFT) ? gr : gam[k], acc);
             if (sg) { sg[k] = gr; sp[k] = 0; }
         } else {
-            T gr = (g_kind == HJ_G_QUAD_SHIFT) ? p[k] + tp.ga[k] : tp.gs2[k] * p[k];
-            T val = (g_kind == HJ_G_QUAD_SHIFT) ? p[k] * fma((T)0.5, p[k], tp.ga[k]) : (T)0.5 * gr * p[k];
+            T gr, val;
+            if (P.g_kind == HJ_G_QUAD_SHIFT) {
+                const T a = __ldg(P.ga + i);
+                gr = p[k] + a;
+                val = p[k] * fma((T)0.5, p[k], a);
+            } else {
+                gr = __ldg(P.gs2 + i) * p[k];
+                val = (T)0.5 * gr * p[k];
+            }
             acc += val - x[k] * v[k];
             if (sg) { sg[k] = 0; sp[k] = gr; }
         }
@@ -413,18 +442,19 @@ __device__ __forceinline__ T terminal(const Grp &g, const TP<T, C> &tp, int g_ki
 
 // Relative certificate residual (Sec. 4.3) from (gamma(0), p(0)).
 template <typename T, int C, int PR>
-__device__ __forceinline__ T cert_residual(const Grp &g, const TP<T, C> &tp, int g_kind, const T *gam, const T *p)
+__device__ __forceinline__ T cert_residual(const Grp &g, const ProbDev<T> &P, const T *gam, const T *p)
 {
     T num = 0, den = 0;
 #pragma unroll
     for (int k = 0; k < C; ++k) {
+        const int i = g.lane + k * g.tpp;
         T diff, base;
         if (PR == HJ_LAX) {
-            T gr = (g_kind == HJ_G_QUAD_SHIFT) ? gam[k] - tp.ga[k] : gam[k] * tp.gis2[k];
+            T gr = (P.g_kind == HJ_G_QUAD_SHIFT) ? gam[k] - __ldg(P.ga + i) : gam[k] * __ldg(P.gis2 + i);
             diff = p[k] - gr;
             base = p[k];
         } else {
-            T gr = (g_kind == HJ_G_QUAD_SHIFT) ? p[k] + tp.ga[k] : tp.gs2[k] * p[k];
+            T gr = (P.g_kind == HJ_G_QUAD_SHIFT) ? p[k] + __ldg(P.ga + i) : __ldg(P.gs2 + i) * p[k];
             diff = gam[k] - gr;
             base = gam[k];
         }
@@ -509,15 +539,16 @@ __device__ __forceinline__ T functional(const Grp &g, const TP<T, C> &tp, const 
     const T h = t / (T)N;
     T Q = 0, Qc = 0;
     for (int n = 0; n < N; ++n) rk4_step<T, C, FAM, PR>(g, tp, P.s_eps, h, quad, kahan, gam, p, Q, Qc);
-    return terminal<T, C, PR>(g, tp, P.g_kind, x, v, gam, p, (T *)nullptr, (T *)nullptr) + Q;
+    return terminal<T, C, PR>(g, P, x, v, gam, p, (T *)nullptr, (T *)nullptr) + Q;
 }
 
 // ---------------------------------------------------------------------------
 // Discrete adjoint of the RK4 map (exact gradient of the discretised
 // functional).  Forward: checkpoints of z every K = ceil(sqrt(N)) steps.
-// Reverse, segment by segment: recompute the segment's steps from its
-// checkpoint storing the four stage inputs of every step, then run the
-// adjoint of each step backward:
+// Reverse, segment by segment: recompute the segment's states z_n from its
+// checkpoint (stored, 2C values per step), then for each step backward
+// rebuild its stage inputs Z1 = z_n, Z2 = z_n + h/2 k1, Z3 = z_n + h/2 k2,
+// Z4 = z_n + h k3 and run the adjoint of the step:
 //   a4 = J(Z4)^T(h/6 lam, h/6 b)
 //   a3 = J(Z3)^T(h/3 lam + h a4, h/3 b)
 //   a2 = J(Z2)^T(h/3 lam + h/2 a3, h/3 b)
@@ -526,78 +557,58 @@ __device__ __forceinline__ T functional(const Grp &g, const TP<T, C> &tp, const 
 // with b = 1 for the RK4 quadrature (0 for the rectangle rule, whose nodes
 // add h grad L(z_{n+1}) to lam directly).  The seed lam(tau=t) comes from
 // the terminal term; dF/dv = lam_p(tau=0) (minus x for Hopf).
-// Buffers (per thread, local memory) are sized for N <= MAX_N.
+// Per-thread scratch (local memory): ck >= ceil(N/K)*2C, seg >= K*2C values,
+// both sized for N <= MAX_N.
 // ---------------------------------------------------------------------------
 template <typename T, int C, int FAM, int PR>
-__device__ __forceinline__ void stage_inputs(const Grp &g, const TP<T, C> &tp, T eps, T h, const T *zg, const T *zp,
-                                             T *st /* [4][2C] */, T *ng, T *np)
+__device__ __forceinline__ void adjoint_step(const Grp &g, const TP<T, C> &tp, T eps, T h, T b, const T *zg,
+                                             const T *zp, T *lg, T *lp)
 {
-    // Computes one RK4 step from (zg, zp), storing its four stage inputs and
-    // returning the new state in (ng, np).
-    T ag[C], ap[C], kg[C], kp[C], sg[C], sp[C], L;
-    const T h2 = (T)0.5 * h, h6 = h / (T)6;
-#pragma unroll
-    for (int k = 0; k < C; ++k) { st[k] = zg[k]; st[C + k] = zp[k]; }
-    field<T, C, FAM, PR>(g, tp, eps, zg, zp, kg, kp, L);
-#pragma unroll
-    for (int k = 0; k < C; ++k) {
-        ag[k] = kg[k]; ap[k] = kp[k];
-        sg[k] = fma(h2, kg[k], zg[k]); sp[k] = fma(h2, kp[k], zp[k]);
-        st[2 * C + k] = sg[k]; st[3 * C + k] = sp[k];
-    }
-    field<T, C, FAM, PR>(g, tp, eps, sg, sp, kg, kp, L);
-#pragma unroll
-    for (int k = 0; k < C; ++k) {
-        ag[k] = fma((T)2, kg[k], ag[k]); ap[k] = fma((T)2, kp[k], ap[k]);
-        sg[k] = fma(h2, kg[k], zg[k]); sp[k] = fma(h2, kp[k], zp[k]);
-        st[4 * C + k] = sg[k]; st[5 * C + k] = sp[k];
-    }
-    field<T, C, FAM, PR>(g, tp, eps, sg, sp, kg, kp, L);
-#pragma unroll
-    for (int k = 0; k < C; ++k) {
-        ag[k] = fma((T)2, kg[k], ag[k]); ap[k] = fma((T)2, kp[k], ap[k]);
-        sg[k] = fma(h, kg[k], zg[k]); sp[k] = fma(h, kp[k], zp[k]);
-        st[6 * C + k] = sg[k]; st[7 * C + k] = sp[k];
-    }
-    field<T, C, FAM, PR>(g, tp, eps, sg, sp, kg, kp, L);
-#pragma unroll
-    for (int k = 0; k < C; ++k) {
-        ng[k] = fma(h6, ag[k] + kg[k], zg[k]);
-        np[k] = fma(h6, ap[k] + kp[k], zp[k]);
-    }
-}
-
-template <typename T, int C, int FAM, int PR>
-__device__ __forceinline__ void adjoint_step(const Grp &g, const TP<T, C> &tp, T eps, T h, T b, const T *st,
-                                             T *lg, T *lp)
-{
-    T wg[C], wp[C], rg[C], rp[C], sumg[C], sump[C];
+    using Fam = Family<T, C, FAM, PR>;
+    typename Fam::FI f1, f2, f3, f4;
+    T kg[C], kp[C], sg[C], sp[C], L;
     const T h6 = h / (T)6, h3 = h / (T)3, h2 = (T)0.5 * h;
+    // rebuild the stage inputs of the step from z_n, keeping each stage's FI
+    Fam::prep(g, tp, eps, zg, zp, f1);
+    Fam::field_fi(tp, f1, eps, kg, kp, L);
+#pragma unroll
+    for (int k = 0; k < C; ++k) { sg[k] = fma(h2, kg[k], zg[k]); sp[k] = fma(h2, kp[k], zp[k]); }
+    Fam::prep(g, tp, eps, sg, sp, f2);
+    Fam::field_fi(tp, f2, eps, kg, kp, L);
+#pragma unroll
+    for (int k = 0; k < C; ++k) { sg[k] = fma(h2, kg[k], zg[k]); sp[k] = fma(h2, kp[k], zp[k]); }
+    Fam::prep(g, tp, eps, sg, sp, f3);
+    Fam::field_fi(tp, f3, eps, kg, kp, L);
+#pragma unroll
+    for (int k = 0; k < C; ++k) { sg[k] = fma(h, kg[k], zg[k]); sp[k] = fma(h, kp[k], zp[k]); }
+    Fam::prep(g, tp, eps, sg, sp, f4);
+
+    T wg[C], wp[C], rg[C], rp[C], sumg[C], sump[C];
     // stage 4
 #pragma unroll
     for (int k = 0; k < C; ++k) { wg[k] = h6 * lg[k]; wp[k] = h6 * lp[k]; }
-    vjp<T, C, FAM, PR>(g, tp, eps, st + 6 * C, st + 7 * C, wg, wp, h6 * b, rg, rp);
+    Fam::vjp_fi(g, tp, f4, eps, wg, wp, h6 * b, rg, rp);
 #pragma unroll
     for (int k = 0; k < C; ++k) {
         sumg[k] = rg[k]; sump[k] = rp[k];
         wg[k] = fma(h3, lg[k], h * rg[k]); wp[k] = fma(h3, lp[k], h * rp[k]);
     }
     // stage 3
-    vjp<T, C, FAM, PR>(g, tp, eps, st + 4 * C, st + 5 * C, wg, wp, h3 * b, rg, rp);
+    Fam::vjp_fi(g, tp, f3, eps, wg, wp, h3 * b, rg, rp);
 #pragma unroll
     for (int k = 0; k < C; ++k) {
         sumg[k] += rg[k]; sump[k] += rp[k];
         wg[k] = fma(h3, lg[k], h2 * rg[k]); wp[k] = fma(h3, lp[k], h2 * rp[k]);
     }
     // stage 2
-    vjp<T, C, FAM, PR>(g, tp, eps, st + 2 * C, st + 3 * C, wg, wp, h3 * b, rg, rp);
+    Fam::vjp_fi(g, tp, f2, eps, wg, wp, h3 * b, rg, rp);
 #pragma unroll
     for (int k = 0; k < C; ++k) {
         sumg[k] += rg[k]; sump[k] += rp[k];
         wg[k] = fma(h6, lg[k], h2 * rg[k]); wp[k] = fma(h6, lp[k], h2 * rp[k]);
     }
     // stage 1
-    vjp<T, C, FAM, PR>(g, tp, eps, st, st + C, wg, wp, h6 * b, rg, rp);
+    Fam::vjp_fi(g, tp, f1, eps, wg, wp, h6 * b, rg, rp);
 #pragma unroll
     for (int k = 0; k < C; ++k) {
         lg[k] += sumg[k] + rg[k];
@@ -605,13 +616,28 @@ __device__ __forceinline__ void adjoint_step(const Grp &g, const TP<T, C> &tp, T
     }
 }
 
-// Gradient of F with respect to v.  ck: >= ceil(N/K)*2C entries, seg: >= K*8C
-// entries of thread-private scratch.  Returns F; grad gets dF/dv.
+// Checkpoint interval: the given K, or the smallest K whose checkpoint and
+// segment storage, (ceil(N/K) + K) states of 2C values, fits CK_BUDGET bytes.
+template <typename T, int C>
+__device__ __forceinline__ int ck_interval(int N, int fixed)
+{
+    int K = fixed;
+    if (K <= 0) {
+        K = 1;
+        while (K < MAX_SEG && ((N + K - 1) / K + K) * 2 * C * (int)sizeof(T) > CK_BUDGET) ++K;
+    }
+    K = max(K, (N + MAX_CK - 1) / MAX_CK);
+    return min(K, MAX_SEG);
+}
+
+// Gradient of F with respect to v.  Returns F; grad gets dF/dv.  ck holds
+// MAX_CK states, seg MAX_SEG states (2C values each, thread-private).
 template <typename T, int C, int FAM, int PR>
 __device__ __forceinline__ T gradient(const Grp &g, const TP<T, C> &tp, const ProbDev<T> &P, int quad, int kahan,
-                                   const T *x, const T *v, T t, int N, T *grad, T *ck, T *seg)
+                                      int ck_fixed, const T *x, const T *v, T t, int N, T *grad, T *ck, T *seg)
 {
-    if (N < 1 || N > MAX_N) {
+    const int K = ck_interval<T, C>(N, ck_fixed);
+    if (N < 1 || N > MAX_N || (N + K - 1) / K > MAX_CK) {
         // the checkpoint buffers hold MAX_N steps: reject other step counts
 #pragma unroll
         for (int k = 0; k < C; ++k) grad[k] = (T)NAN;
@@ -619,53 +645,61 @@ __device__ __forceinline__ T gradient(const Grp &g, const TP<T, C> &tp, const Pr
     }
     const T h = t / (T)N;
     const T eps = P.s_eps;
-    int K = 1;
-    while (K * K < N) ++K;
     T gam[C], p[C], Q = 0, Qc = 0;
 #pragma unroll
     for (int k = 0; k < C; ++k) { gam[k] = x[k]; p[k] = v[k]; }
-    for (int n = 0; n < N; ++n) {
-        if (n % K == 0) {
-            T *c = ck + (n / K) * 2 * C;
+    T *c = ck;
+    for (int n = 0, kk = 0; n < N; ++n) {
+        if (kk == 0) {
 #pragma unroll
             for (int k = 0; k < C; ++k) { c[k] = gam[k]; c[C + k] = p[k]; }
+            c += 2 * C;
         }
+        if (++kk == K) kk = 0;
         rk4_step<T, C, FAM, PR>(g, tp, eps, h, quad, kahan, gam, p, Q, Qc);
     }
+    // gam, p hold z_N
     T lg[C], lp[C];
-    T F = terminal<T, C, PR>(g, tp, P.g_kind, x, v, gam, p, lg, lp) + Q;
+    T F = terminal<T, C, PR>(g, P, x, v, gam, p, lg, lp) + Q;
     const T b = (quad == HJ_QUAD_RK4) ? (T)1 : (T)0;
     const int nseg = (N + K - 1) / K;
     for (int s = nseg - 1; s >= 0; --s) {
         const int n0 = s * K, n1 = min(N, n0 + K);
+        // states z_{n0 .. n1-1}: the checkpoint and K-1 recomputed steps
         T zg[C], zp[C];
         const T *c = ck + s * 2 * C;
 #pragma unroll
         for (int k = 0; k < C; ++k) { zg[k] = c[k]; zp[k] = c[C + k]; }
         for (int n = n0; n < n1; ++n) {
-            T ng[C], np[C];
-            stage_inputs<T, C, FAM, PR>(g, tp, eps, h, zg, zp, seg + (n - n0) * 8 * C, ng, np);
+            T *st = seg + (n - n0) * 2 * C;
 #pragma unroll
-            for (int k = 0; k < C; ++k) { zg[k] = ng[k]; zp[k] = np[k]; }
+            for (int k = 0; k < C; ++k) { st[k] = zg[k]; st[C + k] = zp[k]; }
+            if (n + 1 < n1) {
+                T Qd = 0, Qcd = 0;
+                rk4_step<T, C, FAM, PR>(g, tp, eps, h, HJ_QUAD_RK4, 0, zg, zp, Qd, Qcd);
+            }
         }
-        // zg, zp now hold z_{n1}
         for (int n = n1 - 1; n >= n0; --n) {
+            const T *st = seg + (n - n0) * 2 * C;
+            T ug[C], up[C];
+#pragma unroll
+            for (int k = 0; k < C; ++k) { ug[k] = st[k]; up[k] = st[C + k]; }
             if (quad == HJ_QUAD_RECT) {
-                // rectangle node at z_{n+1}: lam += h grad L(z_{n+1})
-                T zeros[C], rg[C], rp[C];
-                const T *sn = (n + 1 < n1) ? seg + (n + 1 - n0) * 8 * C : nullptr;
-                T ug[C], up[C];
+                // rectangle node at z_{n+1}: lam += h grad L(z_{n+1}); z_{n+1} is the
+                // next stored state, the next checkpoint, or z_N
+                T zeros[C], rg[C], rp[C], ng[C], np[C];
+                const T *sn = (n + 1 < n1) ? seg + (n + 1 - n0) * 2 * C : (s + 1 < nseg ? ck + (s + 1) * 2 * C : nullptr);
 #pragma unroll
                 for (int k = 0; k < C; ++k) {
                     zeros[k] = 0;
-                    ug[k] = sn ? sn[k] : zg[k];
-                    up[k] = sn ? sn[C + k] : zp[k];
+                    ng[k] = sn ? sn[k] : gam[k];
+                    np[k] = sn ? sn[C + k] : p[k];
                 }
-                vjp<T, C, FAM, PR>(g, tp, eps, ug, up, zeros, zeros, (T)1, rg, rp);
+                vjp<T, C, FAM, PR>(g, tp, eps, ng, np, zeros, zeros, (T)1, rg, rp);
 #pragma unroll
                 for (int k = 0; k < C; ++k) { lg[k] = fma(h, rg[k], lg[k]); lp[k] = fma(h, rp[k], lp[k]); }
             }
-            adjoint_step<T, C, FAM, PR>(g, tp, eps, h, b, seg + (n - n0) * 8 * C, lg, lp);
+            adjoint_step<T, C, FAM, PR>(g, tp, eps, h, b, ug, up, lg, lp);
         }
     }
 #pragma unroll

@@ -26,10 +26,10 @@ cudaError_t launch_desc(const void *a, int grid, cudaStream_t s)
     k_desc<T, C, FAM, PR, GD><<<grid, BLOCK, 0, s>>>(*(const DescArgs<T> *)a);
     return cudaGetLastError();
 }
-template <typename Tv, int C, int FAM, int PR, bool PAIRS>
+template <typename Tv, int C, int FAM, int PR, int MODE>
 cudaError_t launch_cert(const void *a, int grid, cudaStream_t s)
 {
-    k_cert<Tv, C, FAM, PR, PAIRS><<<grid, BLOCK, 0, s>>>(*(const CertArgs<Tv> *)a);
+    k_cert<Tv, C, FAM, PR, MODE><<<grid, BLOCK, 0, s>>>(*(const CertArgs<Tv> *)a);
     return cudaGetLastError();
 }
 
@@ -55,10 +55,12 @@ void register_compute(Registry &r)
 template <typename Tv, int FAM, int PR, int... Cs>
 void register_cert(Registry &r)
 {
-    ((r.k[prec_index<Tv>()][FAM][PR][Cs].cert_rows = &launch_cert<Tv, Cs, FAM, PR, false>,
-      r.k[prec_index<Tv>()][FAM][PR][Cs].f_cert_rows = (const void *)&k_cert<Tv, Cs, FAM, PR, false>,
-      r.k[prec_index<Tv>()][FAM][PR][Cs].cert_pairs = &launch_cert<Tv, Cs, FAM, PR, true>,
-      r.k[prec_index<Tv>()][FAM][PR][Cs].f_cert_pairs = (const void *)&k_cert<Tv, Cs, FAM, PR, true>),
+    ((r.k[prec_index<Tv>()][FAM][PR][Cs].cert_rows = &launch_cert<Tv, Cs, FAM, PR, 0>,
+      r.k[prec_index<Tv>()][FAM][PR][Cs].f_cert_rows = (const void *)&k_cert<Tv, Cs, FAM, PR, 0>,
+      r.k[prec_index<Tv>()][FAM][PR][Cs].cert_pairs = &launch_cert<Tv, Cs, FAM, PR, 1>,
+      r.k[prec_index<Tv>()][FAM][PR][Cs].f_cert_pairs = (const void *)&k_cert<Tv, Cs, FAM, PR, 1>,
+      r.k[prec_index<Tv>()][FAM][PR][Cs].cert_final = &launch_cert<Tv, Cs, FAM, PR, 2>,
+      r.k[prec_index<Tv>()][FAM][PR][Cs].f_cert_final = (const void *)&k_cert<Tv, Cs, FAM, PR, 2>),
      ...);
 }
 

@@ -21,7 +21,7 @@ struct RowArgs {
     T *grad;                 // [n, ld] (gradient kernel)
     const int32_t *pidx;     // [n] or null: rows whose problem is not `pfilter` are skipped
     int pfilter;
-    int quad, kahan;
+    int quad, kahan, ck_interval;
 };
 
 // Certificate arguments: rows mode (pid = row) or pair mode (work list).
@@ -48,6 +48,9 @@ struct CertArgs {
     const int32_t *wl_count;
     int problem;
     const int32_t *pair_q;
+    // final mode: FP64 value at each query's chosen start
+    const int32_t *best_pid;   // [nq], -1 when no start is usable
+    double *phi;               // [nq]
 };
 
 // Descent arguments (always pair mode).
@@ -69,11 +72,23 @@ struct DescArgs {
     T *vfin;                 // [npairs, ld]
     int32_t *iters;
     uint8_t *flags;          // bit0: iteration cap, bit1: non-finite
+    // certificate at the final v in the kernel precision: F, residual and
+    // pass (0/1), or pass = 2 with the pair appended to the FP64 list when
+    // a binary32 residual falls inside [CERT_BAND_LO, CERT_BAND_HI] * tol
+    double *pF, *pR;
+    uint8_t *pP;
+    int32_t *amb_wl, *amb_count;
+    double tol;
     unsigned long long *stats;  // [0] iterations [1] functional evals [2] gradients [3] forward RK4 steps
                                 // [4] adjoint steps [5] pairs [6] sum of N over pairs
+                                // [7] RK4 steps of the in-kernel certificate
 };
 
 constexpr int BLOCK = 128;
+// Band around the certificate tolerance inside which a binary32 residual is
+// re-checked in FP64 (binary32 rounding moves the residual by ~1e-6, far
+// less than these margins for tolerances >= 1e-4).
+constexpr double CERT_BAND_LO = 0.75, CERT_BAND_HI = 1.34;
 
 template <typename T, int C>
 __device__ __forceinline__ void load_row(const Grp &g, const T *row, int d, T *out)
@@ -126,8 +141,8 @@ __global__ void __launch_bounds__(BLOCK) k_grad(RowArgs<T> a)
     const Grp g = make_grp(a.tpp);
     TP<T, C> tp;
     tp.load(a.P, g);
-    T ck[MAX_SEG * 2 * C];
-    T seg[MAX_SEG * 8 * C];
+    T ck[MAX_CK * 2 * C];
+    T seg[MAX_SEG * 2 * C];
     const long long groups = (long long)gridDim.x * (BLOCK / a.tpp);
     for (long long r = ((long long)blockIdx.x * BLOCK + threadIdx.x) / a.tpp; r < a.n; r += groups) {
         if (a.pidx && a.pidx[r] != a.pfilter) continue;
@@ -135,7 +150,7 @@ __global__ void __launch_bounds__(BLOCK) k_grad(RowArgs<T> a)
         T x[C], v[C], gr[C];
         load_row<T, C>(g, a.x + r * a.P.ld, a.P.d, x);
         load_row<T, C>(g, a.v + r * a.P.ld, a.P.d, v);
-        T F = gradient<T, C, FAM, PR>(g, tp, a.P, a.quad, a.kahan, x, v, a.t[r], N, gr, ck, seg);
+        T F = gradient<T, C, FAM, PR>(g, tp, a.P, a.quad, a.kahan, a.ck_interval, x, v, a.t[r], N, gr, ck, seg);
         store_row<T, C>(g, a.grad + r * a.P.ld, a.P.d, gr);
         if (a.F && g.lane == 0) a.F[r] = F;
     }
@@ -144,14 +159,17 @@ __global__ void __launch_bounds__(BLOCK) k_grad(RowArgs<T> a)
 // ---------------------------------------------------------------------------
 // Certificate of Sec. 4.3 in FP64 (and the FP64 functional value).
 // ---------------------------------------------------------------------------
-template <typename Tv, int C, int FAM, int PR, bool PAIRS>
+// MODE 0: rows (hj_certify); MODE 1: the pairs of a work list (starts whose
+// binary32 residual was too close to the tolerance); MODE 2: the chosen
+// start of every query, writing phi = F (Lax) or -G (Hopf).
+template <typename Tv, int C, int FAM, int PR, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_cert(CertArgs<Tv> a)
 {
     const Grp g = make_grp(a.tpp);
     TP<double, C> tp;
     tp.load(a.P, g);
     long long n, begin = 0;
-    if (PAIRS) {
+    if (MODE == 1) {
         n = a.wl_count[a.problem];
         begin = a.seg_begin[a.problem];
     } else {
@@ -160,9 +178,14 @@ __global__ void __launch_bounds__(BLOCK) k_cert(CertArgs<Tv> a)
     const long long groups = (long long)gridDim.x * (BLOCK / a.tpp);
     for (long long j = ((long long)blockIdx.x * BLOCK + threadIdx.x) / a.tpp; j < n; j += groups) {
         long long pid, q;
-        if (PAIRS) {
+        if (MODE == 1) {
             pid = a.wl[begin + j];
             q = a.pair_q[pid];
+        } else if (MODE == 2) {
+            if (a.pidx && a.pidx[j] != a.pfilter) continue;
+            q = j;
+            pid = a.best_pid[j];
+            if (pid < 0) continue;
         } else {
             if (a.pidx && a.pidx[j] != a.pfilter) continue;
             pid = j;
@@ -179,7 +202,11 @@ __global__ void __launch_bounds__(BLOCK) k_cert(CertArgs<Tv> a)
             p[k] = v[k];
         }
         double F = functional<double, C, FAM, PR>(g, tp, a.P, a.quad, 0, x, v, (double)a.t[q], N, gam, p);
-        double r = cert_residual<double, C, PR>(g, tp, a.P.g_kind, gam, p);
+        if (MODE == 2) {
+            if (g.lane == 0) a.phi[q] = (PR == HJ_LAX) ? F : -F;
+            continue;
+        }
+        double r = cert_residual<double, C, PR>(g, a.P, gam, p);
         if (g.lane == 0) {
             a.F[pid] = F;
             a.resid[pid] = r;
@@ -189,13 +216,17 @@ __global__ void __launch_bounds__(BLOCK) k_cert(CertArgs<Tv> a)
 }
 
 // ---------------------------------------------------------------------------
-// Persistent descent kernel: each lane group takes (query, start) pairs from
-// the problem's work list, draws the start (Philox), runs Algorithm 1
-// (cyclic coordinate descent with finite differences) or its gradient form
-// with the adjoint gradient, and writes the final v.
+// Persistent descent kernel.  Each lane group owns one (query, start) pair at
+// a time: it draws the start (Philox), runs Algorithm 1 (cyclic coordinate
+// descent with finite differences) or its gradient form with the adjoint
+// gradient, and writes the final v.  The loop is organised per iteration so
+// that every group of a warp executes the same iteration body together
+// (the body has no data-dependent branches besides the RK4 step count); a
+// group whose pair has finished takes the next pair from the problem's work
+// list between iterations, so lanes never wait for a whole warp to drain.
 // ---------------------------------------------------------------------------
 template <typename T, int C, int FAM, int PR, bool GD>
-__global__ void __launch_bounds__(BLOCK) k_desc(DescArgs<T> a)
+__global__ void __launch_bounds__(BLOCK, GD ? 3 : 4) k_desc(DescArgs<T> a)
 {
     const Grp g = make_grp(a.tpp);
     TP<T, C> tp;
@@ -206,33 +237,55 @@ __global__ void __launch_bounds__(BLOCK) k_desc(DescArgs<T> a)
     const int lead = (threadIdx.x & 31) & ~(a.tpp - 1);
     const T eps_stop = (T)a.S.eps;
     const T fd_h = (T)a.S.fd_h;
-    T ck[GD ? MAX_SEG * 2 * C : 1];
-    T seg[GD ? MAX_SEG * 8 * C : 1];
-    unsigned long long n_it = 0, n_f = 0, n_g = 0, n_rk = 0, n_adj = 0, n_pairs = 0, n_sumN = 0;
-    for (;;) {
-        long long j = 0;
-        if (g.lane == 0) j = atomicAdd(a.cursor + a.problem, 1);
-        j = __shfl_sync(g.mask, j, lead);
-        if (j >= n) break;
-        const long long pid = a.wl[begin + j];
-        const long long q = a.pair_q[pid];
-        const int slot = a.pair_slot[pid], round = a.pair_round[pid];
-        const int N = a.nsteps ? a.nsteps[q] : a.S.n_default;
-        const T t = a.t[q];
-        T x[C], v[C], alpha[C], prev[C];
-        load_row<T, C>(g, a.x + q * a.P.ld, d, x);
+    const bool central = (a.S.grad != HJ_GRAD_FD_FORWARD);
+    T ck[GD ? MAX_CK * 2 * C : 1];
+    T seg[GD ? MAX_SEG * 2 * C : 1];
+    unsigned long long n_it = 0, n_f = 0, n_g = 0, n_rk = 0, n_adj = 0, n_pairs = 0, n_sumN = 0, n_cert = 0;
+
+    bool active = false, exhausted = false;
+    long long pid = 0, q = 0;
+    int N = 1, it = 0, count = 0, kper = 0, bad = 0;
+    T t = 0;
+    T x[C], v[C], alpha[C], prev[C];
 #pragma unroll
-        for (int k = 0; k < C; ++k) {
-            int i = g.lane + k * g.tpp;
-            v[k] = (i < d) ? start_component<T>(a.S.seed, a.q_begin + q, slot, round, i, a.S.guess_dist) : (T)0;
-            alpha[k] = (T)a.S.step;
-            prev[k] = 0;
+    for (int k = 0; k < C; ++k) { x[k] = 0; v[k] = 0; alpha[k] = 0; prev[k] = 0; }
+
+    for (;;) {
+        // ---- refill: groups without a pair take the next one ----------------
+        if (!active && !exhausted) {
+            long long j = 0;
+            if (g.lane == 0) j = atomicAdd(a.cursor + a.problem, 1);
+            j = __shfl_sync(g.mask, j, lead);
+            if (j >= n) {
+                exhausted = true;
+            } else {
+                pid = a.wl[begin + j];
+                q = a.pair_q[pid];
+                const int slot = a.pair_slot[pid], round = a.pair_round[pid];
+                N = a.nsteps ? a.nsteps[q] : a.S.n_default;
+                t = a.t[q];
+                load_row<T, C>(g, a.x + q * a.P.ld, d, x);
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    int i = g.lane + k * g.tpp;
+                    v[k] = (i < d) ? start_component<T>(a.S.seed, a.q_begin + q, slot, round, i, a.S.guess_dist)
+                                   : (T)0;
+                    alpha[k] = (T)a.S.step;
+                    prev[k] = 0;
+                }
+                it = count = kper = bad = 0;
+                active = true;
+            }
         }
-        int it = 0, cap = 1, bad = 0;
-        if (GD) {
-            for (; it < a.S.max_iters; ++it) {
+        if (!__any_sync(0xffffffffu, active)) break;
+        if (!active) continue;
+
+        // ---- one iteration ----------------------------------------------------
+        bool stop = (it >= a.S.max_iters), conv = false;
+        if (!stop) {
+            if (GD) {
                 T gr[C];
-                gradient<T, C, FAM, PR>(g, tp, a.P, a.S.quad, a.S.kahan, x, v, t, N, gr, ck, seg);
+                gradient<T, C, FAM, PR>(g, tp, a.P, a.S.quad, a.S.kahan, a.S.ck_interval, x, v, t, N, gr, ck, seg);
                 n_g++;
                 n_rk += N;
                 n_adj += N;
@@ -252,17 +305,14 @@ __global__ void __launch_bounds__(BLOCK) k_desc(DescArgs<T> a)
                     prev[k] = gr[k];
                 }
                 big = gmax(g, fin ? big : (T)INFINITY);
-                if (!(big < (T)INFINITY)) { bad = 1; ++it; cap = 0; break; }
-                if (a.S.halving_period > 0 && (it + 1) % a.S.halving_period == 0) {
+                ++it;
+                if (!(big < (T)INFINITY)) { bad = 1; stop = true; }
+                if (a.S.halving_period > 0 && it % a.S.halving_period == 0) {
 #pragma unroll
                     for (int k = 0; k < C; ++k) alpha[k] *= (T)0.5;
                 }
-                if (big < eps_stop) { ++it; cap = 0; break; }
-            }
-        } else {
-            const bool central = (a.S.grad != HJ_GRAD_FD_FORWARD);
-            int count = 0, kper = 0;
-            for (; it < a.S.max_iters; ++it) {
+                if (big < eps_stop) conv = stop = true;
+            } else {
                 const int jc = it % d;
                 const int owner = jc % a.tpp, comp = jc / a.tpp;
                 const bool mine = (g.lane == owner);
@@ -301,8 +351,9 @@ __global__ void __launch_bounds__(BLOCK) k_desc(DescArgs<T> a)
                     }
                 }
                 st = __shfl_sync(g.mask, st, lead + owner);
-                if (!finite_(st)) { bad = 1; ++it; cap = 0; break; }
-                // reset on a move > eps, count a move < eps (strict; eps = 0 never stops)
+                ++it;
+                if (!finite_(st)) { bad = 1; stop = true; }
+                // steps 3-4 of Algorithm 1: reset on a move > eps, count a move < eps
                 if (fabs(st) > eps_stop) count = 0;
                 else if (fabs(st) < eps_stop) ++count;
                 if (a.S.halving_period > 0 && ++kper == a.S.halving_period) {
@@ -310,16 +361,42 @@ __global__ void __launch_bounds__(BLOCK) k_desc(DescArgs<T> a)
 #pragma unroll
                     for (int k = 0; k < C; ++k) alpha[k] *= (T)0.5;
                 }
-                if (count >= d) { ++it; cap = 0; break; }
+                if (count >= d) conv = stop = true;
             }
+            if (it >= a.S.max_iters) stop = true;
         }
-        n_it += it;
-        n_pairs++;
-        n_sumN += N;
-        store_row<T, C>(g, a.vfin + pid * a.P.ld, d, v);
-        if (g.lane == 0) {
-            a.iters[pid] = it;
-            a.flags[pid] = (uint8_t)(cap | (bad << 1));
+        // ---- finished pair: certificate at the final v, then write it out -----
+        if (stop) {
+            const int cap = (!conv && !bad) ? 1 : 0;
+            n_it += it;
+            n_pairs++;
+            n_sumN += N;
+            T gam[C], p[C];
+#pragma unroll
+            for (int k = 0; k < C; ++k) { gam[k] = x[k]; p[k] = v[k]; }
+            const T F = functional<T, C, FAM, PR>(g, tp, a.P, a.S.quad, a.S.kahan, x, v, t, N, gam, p);
+            const T r = cert_residual<T, C, PR>(g, a.P, gam, p);
+            n_cert += N;
+            store_row<T, C>(g, a.vfin + pid * a.P.ld, d, v);
+            if (g.lane == 0) {
+                a.iters[pid] = it;
+                a.flags[pid] = (uint8_t)(cap | (bad << 1));
+                const bool fin = finite_(F) && finite_(r);
+                uint8_t pass;
+                if (!fin) pass = 0;
+                else if (sizeof(T) == 8) pass = ((double)r <= a.tol) ? 1 : 0;
+                else if ((double)r < CERT_BAND_LO * a.tol) pass = 1;
+                else if ((double)r > CERT_BAND_HI * a.tol) pass = 0;
+                else pass = 2;
+                a.pF[pid] = (double)F;
+                a.pR[pid] = (double)r;
+                a.pP[pid] = pass;
+                if (pass == 2) {
+                    const int pos = atomicAdd(a.amb_count + a.problem, 1);
+                    a.amb_wl[begin + pos] = (int32_t)pid;
+                }
+            }
+            active = false;
         }
     }
     if (g.lane == 0 && a.stats) {
@@ -330,6 +407,7 @@ __global__ void __launch_bounds__(BLOCK) k_desc(DescArgs<T> a)
         atomicAdd(a.stats + 4, n_adj);
         atomicAdd(a.stats + 5, n_pairs);
         atomicAdd(a.stats + 6, n_sumN);
+        atomicAdd(a.stats + 7, n_cert);
     }
 }
 

@@ -21,6 +21,7 @@ struct SelectArgs {
     double *phi;
     void *v_out;
     int32_t *status;
+    int32_t *best_pid;
 };
 
 cudaError_t launch_count(long long nq, const int32_t *pidx, const int32_t *pg, int32_t *starts, int32_t *pcount,

@@ -32,7 +32,7 @@ HJ_PREC_FP32, HJ_PREC_FP64 = 0, 1
 HJ_ST_CERTIFIED, HJ_ST_MAX_ITERS, HJ_ST_NONFINITE, HJ_ST_RESEEDED = 1, 2, 4, 8
 
 EXPORTED = ("hj_create", "hj_destroy", "hj_eval_functional", "hj_grad", "hj_certify", "hj_solve", "hj_guesses",
-            "hj_last_solve_info", "hj_set_launch", "hj_last_error")
+            "hj_last_solve_info", "hj_set_tuning", "hj_last_error")
 
 
 class hj_problem_desc(C.Structure):
@@ -54,7 +54,8 @@ class hj_solve_info(C.Structure):
                 ("functional_evals", C.c_int64), ("gradient_evals", C.c_int64), ("rk4_steps", C.c_int64),
                 ("algorithmic_flops", C.c_double), ("certify_flops", C.c_double), ("threads_per_pair", C.c_int),
                 ("comps_per_thread", C.c_int), ("descent_launches", C.c_int), ("descent_ms", C.c_double),
-                ("certify_ms", C.c_double), ("total_ms", C.c_double), ("kernel_launches", C.c_int64)]
+                ("certify_ms", C.c_double), ("total_ms", C.c_double), ("kernel_launches", C.c_int64),
+                ("descent_ms_round0", C.c_double)]
 
 
 _lib = None
@@ -79,7 +80,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.hj_solve.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.hj_guesses.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
     lib.hj_last_solve_info.argtypes = [vp, C.POINTER(hj_solve_info)]
-    lib.hj_set_launch.argtypes = [vp, C.c_int, C.c_int]
+    lib.hj_set_tuning.argtypes = [vp, C.c_int, C.c_int, C.c_int]
     lib.hj_last_error.argtypes = [vp]
     lib.hj_last_error.restype = C.c_char_p
     for name in EXPORTED:
@@ -254,8 +255,8 @@ def hj_last_solve_info(ctx: Context) -> Dict:
     return {name: getattr(info, name) for name, _ in hj_solve_info._fields_}
 
 
-def hj_set_launch(ctx: Context, problem: int, tpp: int):
-    _check(ctx, load_library().hj_set_launch(ctx.handle, problem, tpp))
+def hj_set_tuning(ctx: Context, problem: int, tpp: int = 0, ck_interval: int = 0):
+    _check(ctx, load_library().hj_set_tuning(ctx.handle, problem, tpp, ck_interval))
 
 
 class Functional(torch.autograd.Function):

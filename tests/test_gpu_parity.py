@@ -148,3 +148,39 @@ def test_solve_smooth_nonconvex_d20_matches_oracle(hj):
     err = rel_err(phi, ref["phi"])
     assert np.all(err <= 1e-4), err.max()
     assert np.array_equal(st & 1, ref["status"] & 1)
+
+
+@pytest.mark.parametrize("ck", [1, 2, 3, 8, 16])
+@pytest.mark.parametrize("quad", ["rk4", "rect"])
+def test_gradient_checkpoint_intervals_and_quadrature(hj, ck, quad):
+    # every checkpoint interval (including ones that do not divide N) and
+    # both quadratures give the oracle's exact gradient of the discretised functional
+    spec = _spec(W.FAM_SMOOTH_NONCONVEX, W.HOPF, 20, seed=11, s_eps=1e-2)
+    solver = W.solver_constants(quad=quad)
+    ctx = hj.hj_create([spec], hj.opts_from_dict(solver, hj.HJ_PREC_FP32, 64), 0)
+    hj.hj_set_tuning(ctx, 0, 4, ck)
+    n = 33
+    x, v, t, N = _rows(n, 20, 21, "fp32")
+    N = np.array([1, 2, 5, 17, 64, 100, 255, 256] * 5)[:n].astype(np.int32)
+    F, G = hj.hj_grad(ctx, _t(x, torch.float32), _t(t, torch.float32), _t(v, torch.float32), _t(N, torch.int32))
+    F, G = F.cpu().numpy(), G.cpu().numpy()
+    P = oracle_problem(spec)
+    q = O.QUAD_RK4 if quad == "rk4" else O.QUAD_RECT
+    for i in range(n):
+        Fo, Go = O.gradient(P, x[i], t[i], int(N[i]), v[i], quad=q)
+        assert rel_err(F[i], Fo) <= 2e-5
+        assert np.abs(G[i] - Go).max() <= 5e-4 * (1 + np.abs(Go).max()), (i, N[i])
+    ctx.close()
+
+
+def test_step_counts_outside_range_give_nan_not_memory_errors(hj):
+    spec = _spec(W.FAM_SMOOTH_NONCONVEX, W.HOPF, 20)
+    ctx = hj.hj_create([spec], hj.opts_from_dict(W.solver_constants(), hj.HJ_PREC_FP32, 64), 0)
+    x, v, t, _ = _rows(4, 20, 3, "fp32")
+    N = np.array([0, 257, -5, 1000], dtype=np.int32)
+    F, G = hj.hj_grad(ctx, _t(x, torch.float32), _t(t, torch.float32), _t(v, torch.float32), _t(N, torch.int32))
+    assert np.all(np.isnan(F.cpu().numpy())) and np.all(np.isnan(G.cpu().numpy()))
+    E = hj.hj_eval_functional(ctx, _t(x, torch.float32), _t(t, torch.float32), _t(v, torch.float32),
+                              _t(N, torch.int32))
+    assert np.all(np.isnan(E.cpu().numpy()))
+    ctx.close()
