@@ -258,6 +258,33 @@ hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out);
  */
 hj_status hj_set_tuning(hj_ctx *ctx, int problem, int tpp, int ck_interval);
 
+/*
+ * hj_solve_noalloc -- hj_solve that allocates nothing.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * while they solve, e.g. programs whose GPU memory is owned by another
+ * allocator (a framework's caching pool, a pre-reserved arena) or
+ * latency-critical loops that must not risk an allocation.  Create the
+ * context once beforehand (hj_create allocates); this call then makes no
+ * cudaMalloc/cudaFree and uses no allocating library routine.
+ *
+ * Arguments, results and status codes are those of hj_solve.  All of the
+ * call's scratch lives in one static device array of
+ * HJ_SOLVE_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps
+ * for the life of the process; a call that needs more (about
+ * n_queries * max_starts * (42 + ld * element size) bytes plus ~20 bytes per
+ * query) returns HJ_EINVAL with the sizes in hj_last_error and enqueues
+ * nothing.  The first call on each device looks up the array's device
+ * address with that device current; make that first call before any stream
+ * capture starts.  Every call on a device shares the one array: calls that
+ * overlap on the GPU (other streams, other threads, other contexts) race
+ * and corrupt each other's results, so serialise them.  hj_last_solve_info
+ * keeps describing the last hj_solve call.
+ */
+#define HJ_SOLVE_NOALLOC_SCRATCH_BYTES (16u << 20)
+hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_t *problem_idx,
+                           const void *x, const void *t, const int32_t *n_steps, double *phi_out, void *v_out,
+                           int32_t *status_out, void *stream);
+
 /* Message of the last error on ctx (or of the last failed hj_create when ctx is NULL). */
 const char *hj_last_error(const hj_ctx *ctx);
 

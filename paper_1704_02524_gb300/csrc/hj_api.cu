@@ -918,3 +918,253 @@ hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// hj_solve_noalloc: hj_solve with every piece of per-call scratch taken from
+// one fixed, statically allocated device array instead of cudaMalloc.
+//
+// Who needs it: programs that cannot make driver allocations at call time,
+// for example ones whose device memory is entirely owned by another
+// allocator (a framework's caching pool or a pre-reserved arena, where an
+// extra cudaMalloc fails or fragments memory), or latency-critical loops that
+// must not pay for, or risk failing, an allocation.  They create the context
+// once at start-up and then solve without allocating anything.
+//
+// The array below is a file-scope __device__ variable: every GPU that loads
+// this library reserves it for the life of the process.  Host code must not
+// pass its name to a kernel (on the host the name is only a stand-in for the
+// symbol); the device address comes from cudaGetSymbolAddress, fetched once
+// per device with that device current, on the first hj_solve_noalloc call
+// made on that device.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char hj_noalloc_scratch[HJ_SOLVE_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+unsigned char *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+struct NoallocLayout {
+    int32_t *pcount, *seg_begin, *wl_count, *cursor, *amb_count;
+    int32_t *starts, *pair_base, *block_sums, *trials, *qflags, *best_pid;
+    int32_t *pair_q, *pair_slot, *pair_round, *iters, *wl, *amb_wl;
+    uint8_t *flags, *pP;
+    double *pF, *pR;
+    void *vfin;
+};
+
+// Carves the scratch into the solve's arrays (each 256-byte aligned) and
+// returns the bytes needed; base == nullptr only measures.
+size_t noalloc_layout(unsigned char *base, int np, long long nq, long long npairs, int ld, size_t es, NoallocLayout *L)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> unsigned char * {
+        off = (off + 255) & ~(size_t)255;
+        unsigned char *p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    L->pcount = (int32_t *)take(sizeof(int32_t) * np);
+    L->seg_begin = (int32_t *)take(sizeof(int32_t) * (np + 1));
+    L->wl_count = (int32_t *)take(sizeof(int32_t) * np);
+    L->cursor = (int32_t *)take(sizeof(int32_t) * np);
+    L->amb_count = (int32_t *)take(sizeof(int32_t) * np);
+    L->starts = (int32_t *)take(sizeof(int32_t) * nq);
+    L->pair_base = (int32_t *)take(sizeof(int32_t) * nq);
+    L->block_sums = (int32_t *)take(sizeof(int32_t) * ((nq + 1023) / 1024 + 1));
+    L->trials = (int32_t *)take(sizeof(int32_t) * nq);
+    L->qflags = (int32_t *)take(sizeof(int32_t) * nq);
+    L->best_pid = (int32_t *)take(sizeof(int32_t) * nq);
+    L->pair_q = (int32_t *)take(sizeof(int32_t) * npairs);
+    L->pair_slot = (int32_t *)take(sizeof(int32_t) * npairs);
+    L->pair_round = (int32_t *)take(sizeof(int32_t) * npairs);
+    L->iters = (int32_t *)take(sizeof(int32_t) * npairs);
+    L->wl = (int32_t *)take(sizeof(int32_t) * npairs);
+    L->amb_wl = (int32_t *)take(sizeof(int32_t) * npairs);
+    L->flags = (uint8_t *)take(npairs);
+    L->pP = (uint8_t *)take(npairs);
+    L->pF = (double *)take(sizeof(double) * npairs);
+    L->pR = (double *)take(sizeof(double) * npairs);
+    L->vfin = (void *)take(es * npairs * ld);
+    return off;
+}
+
+}  // namespace
+
+extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_t *problem_idx,
+                                      const void *x, const void *t, const int32_t *n_steps, double *phi_out,
+                                      void *v_out, int32_t *status_out, void *stream)
+{
+    if (!ctx) return HJ_EINVAL;
+    if (n_queries < 0) return fail(ctx, HJ_EINVAL, "n_queries must be >= 0");
+    if (q_begin < 0) return fail(ctx, HJ_EINVAL, "q_begin must be >= 0");
+    if (n_queries == 0) return HJ_OK;
+    if (!x || !t || !phi_out || !v_out || !status_out)
+        return fail(ctx, HJ_EINVAL, "x, t, phi_out, v_out and status_out must be non-NULL");
+    if (ctx->np > 1 && !problem_idx) return fail(ctx, HJ_EINVAL, "problem_idx is required with several problems");
+    if (ctx->device < 0 || ctx->device >= NOALLOC_MAX_DEVICES)
+        return fail(ctx, HJ_EUNSUPPORTED, "hj_solve_noalloc supports devices 0..%d", NOALLOC_MAX_DEVICES - 1);
+    const long long npairs = (long long)n_queries * ctx->gmax;
+    const size_t es = ctx->prec ? sizeof(double) : sizeof(float);
+    NoallocLayout L{};
+    const size_t need = noalloc_layout(nullptr, ctx->np, n_queries, npairs, ctx->ld, es, &L);
+    if (need > (size_t)HJ_SOLVE_NOALLOC_SCRATCH_BYTES)
+        return fail(ctx, HJ_EINVAL,
+                    "hj_solve_noalloc: %lld queries x %d starts need %zu bytes of scratch, the static array holds %zu "
+                    "(split the batch or use hj_solve)",
+                    (long long)n_queries, ctx->gmax, need, (size_t)HJ_SOLVE_NOALLOC_SCRATCH_BYTES);
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(ctx->device));
+    if (!g_noalloc_ptr[ctx->device]) {
+        // once per device, with that device current
+        void *p = nullptr;
+        CU(cudaGetSymbolAddress(&p, hj_noalloc_scratch));
+        g_noalloc_ptr[ctx->device] = (unsigned char *)p;
+    }
+    noalloc_layout(g_noalloc_ptr[ctx->device], ctx->np, n_queries, npairs, ctx->ld, es, &L);
+    const int32_t *pidx = ctx->np > 1 ? problem_idx : nullptr;
+    const int kind = ctx->opts.grad == HJ_GRAD_ADJOINT ? K_GD : K_CD;
+    std::vector<int> tpp_d(ctx->np), c_d(ctx->np), tpp_c(ctx->np), c_c(ctx->np);
+    for (int p = 0; p < ctx->np; ++p)
+        if (!choose(ctx, p, kind, &tpp_d[p], &c_d[p]) || !choose(ctx, p, K_CERT, &tpp_c[p], &c_c[p]))
+            return fail(ctx, HJ_EUNSUPPORTED, "no kernel for problem %d", p);
+    // Every array read below is written earlier in this call; only the
+    // per-problem counters must start at zero, and they are cleared here.
+    CU(launch_count(n_queries, pidx, ctx->d_pg, L.starts, L.pcount, ctx->np, L.seg_begin, L.wl_count, s));
+    CU(launch_scan(n_queries, L.starts, L.pair_base, L.block_sums, s));
+    CU(launch_build_pairs(n_queries, pidx, ctx->d_pg, L.pair_base, L.pair_q, L.pair_slot, L.pair_round, L.trials,
+                          L.qflags, L.seg_begin, L.wl_count, L.wl, s));
+    const SolverDev S = solver_dev(ctx->opts);
+    for (int round = 0; round <= ctx->opts.max_rounds; ++round) {
+        CU(cudaMemsetAsync(L.cursor, 0, sizeof(int32_t) * ctx->np, s));
+        CU(cudaMemsetAsync(L.amb_count, 0, sizeof(int32_t) * ctx->np, s));
+        for (int p = 0; p < ctx->np; ++p) {
+            const KSet &k = kset(ctx, p, c_d[p]);
+            Launch Lk = kind == K_GD ? k.gd : k.cd;
+            const void *fn = kind == K_GD ? k.f_gd : k.f_cd;
+            auto fill = [&](auto &a) {
+                a.tpp = tpp_d[p];
+                a.problem = p;
+                a.nsteps = n_steps;
+                a.q_begin = q_begin;
+                a.S = S;
+                a.S.ck_interval = ctx->ck_interval[p];
+                a.wl = L.wl;
+                a.seg_begin = L.seg_begin;
+                a.wl_count = L.wl_count;
+                a.cursor = L.cursor;
+                a.pair_q = L.pair_q;
+                a.pair_slot = L.pair_slot;
+                a.pair_round = L.pair_round;
+                a.iters = L.iters;
+                a.flags = L.flags;
+                a.stats = nullptr;
+                a.pF = L.pF;
+                a.pR = L.pR;
+                a.pP = L.pP;
+                a.amb_wl = L.amb_wl;
+                a.amb_count = L.amb_count;
+                a.tol = ctx->opts.cert_tol;
+            };
+            if (ctx->prec) {
+                DescArgs<double> a{};
+                fill(a);
+                a.P = ctx->dev[p].pd;
+                a.x = (const double *)x; a.t = (const double *)t; a.vfin = (double *)L.vfin;
+                CU(Lk(&a, persistent_grid(ctx, fn), s));
+            } else {
+                DescArgs<float> a{};
+                fill(a);
+                a.P = ctx->dev[p].pf;
+                a.x = (const float *)x; a.t = (const float *)t; a.vfin = (float *)L.vfin;
+                CU(Lk(&a, persistent_grid(ctx, fn), s));
+            }
+        }
+        for (int p = 0; p < ctx->np; ++p) {
+            const KSet &k = kset(ctx, p, c_c[p]);
+            auto fill = [&](auto &a) {
+                a.P = ctx->dev[p].pd;
+                a.tpp = tpp_c[p];
+                a.nsteps = n_steps;
+                a.n_default = ctx->opts.n_steps_default;
+                a.F = L.pF;
+                a.resid = L.pR;
+                a.pass = L.pP;
+                a.tol = ctx->opts.cert_tol;
+                a.quad = ctx->opts.quad;
+                a.wl = L.amb_wl;
+                a.seg_begin = L.seg_begin;
+                a.wl_count = L.amb_count;
+                a.problem = p;
+                a.pair_q = L.pair_q;
+            };
+            const long long cap = std::min<long long>((long long)n_queries * ctx->desc[p].n_guesses, 1 << 16);
+            if (ctx->prec) {
+                CertArgs<double> a{};
+                fill(a);
+                a.x = (const double *)x; a.t = (const double *)t; a.v = (const double *)L.vfin;
+                CU(k.cert_pairs(&a, rows_grid(ctx, k.f_cert_pairs, cap, tpp_c[p]), s));
+            } else {
+                CertArgs<float> a{};
+                fill(a);
+                a.x = (const float *)x; a.t = (const float *)t; a.v = (const float *)L.vfin;
+                CU(k.cert_pairs(&a, rows_grid(ctx, k.f_cert_pairs, cap, tpp_c[p]), s));
+            }
+        }
+        const int schedule = round < ctx->opts.max_rounds;
+        if (schedule) CU(cudaMemsetAsync(L.wl_count, 0, sizeof(int32_t) * ctx->np, s));
+        SelectArgs a{};
+        a.nq = n_queries;
+        a.pidx = pidx;
+        a.pg = ctx->d_pg;
+        a.pd = ctx->d_pd;
+        a.pprin = ctx->d_pprin;
+        a.ld = ctx->ld;
+        a.pair_base = L.pair_base;
+        a.pF = L.pF;
+        a.pP = L.pP;
+        a.flags = L.flags;
+        a.vfin = L.vfin;
+        a.pair_round = L.pair_round;
+        a.trials = L.trials;
+        a.qflags = L.qflags;
+        a.round = round;
+        a.schedule = schedule;
+        a.max_trials = ctx->opts.max_trials;
+        a.seg_begin = L.seg_begin;
+        a.wl_count = L.wl_count;
+        a.wl = L.wl;
+        a.phi = phi_out;
+        a.v_out = v_out;
+        a.status = status_out;
+        a.best_pid = L.best_pid;
+        CU(launch_select(a, ctx->prec, s));
+    }
+    for (int p = 0; p < ctx->np; ++p) {
+        const KSet &k = kset(ctx, p, c_c[p]);
+        auto fill = [&](auto &a) {
+            a.P = ctx->dev[p].pd;
+            a.tpp = tpp_c[p];
+            a.n = n_queries;
+            a.nsteps = n_steps;
+            a.n_default = ctx->opts.n_steps_default;
+            a.quad = ctx->opts.quad;
+            a.pidx = pidx;
+            a.pfilter = p;
+            a.best_pid = L.best_pid;
+            a.phi = phi_out;
+        };
+        if (ctx->prec) {
+            CertArgs<double> a{};
+            fill(a);
+            a.x = (const double *)x; a.t = (const double *)t; a.v = (const double *)L.vfin;
+            CU(k.cert_final(&a, rows_grid(ctx, k.f_cert_final, n_queries, tpp_c[p]), s));
+        } else {
+            CertArgs<float> a{};
+            fill(a);
+            a.x = (const float *)x; a.t = (const float *)t; a.v = (const float *)L.vfin;
+            CU(k.cert_final(&a, rows_grid(ctx, k.f_cert_final, n_queries, tpp_c[p]), s));
+        }
+    }
+    return HJ_OK;
+}

@@ -32,7 +32,7 @@ HJ_PREC_FP32, HJ_PREC_FP64 = 0, 1
 HJ_ST_CERTIFIED, HJ_ST_MAX_ITERS, HJ_ST_NONFINITE, HJ_ST_RESEEDED = 1, 2, 4, 8
 
 EXPORTED = ("hj_create", "hj_destroy", "hj_eval_functional", "hj_grad", "hj_certify", "hj_solve", "hj_guesses",
-            "hj_last_solve_info", "hj_set_tuning", "hj_last_error")
+            "hj_last_solve_info", "hj_set_tuning", "hj_last_error", "hj_solve_noalloc")
 
 
 class hj_problem_desc(C.Structure):
@@ -78,6 +78,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.hj_grad.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.hj_certify.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.hj_solve.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.hj_solve_noalloc.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.hj_guesses.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
     lib.hj_last_solve_info.argtypes = [vp, C.POINTER(hj_solve_info)]
     lib.hj_set_tuning.argtypes = [vp, C.c_int, C.c_int, C.c_int]
@@ -235,6 +236,26 @@ def hj_solve(ctx: Context, x: torch.Tensor, t: torch.Tensor, n_steps: Optional[t
         phi, v, status = out
     _check(ctx, load_library().hj_solve(ctx.handle, q_begin, n, _ptr(problem_idx), _ptr(x), _ptr(t), _ptr(n_steps),
                                         _ptr(phi), _ptr(v), _ptr(status), _stream(x.device)))
+    return phi, v, status
+
+
+def hj_solve_noalloc(ctx: Context, x: torch.Tensor, t: torch.Tensor, n_steps: Optional[torch.Tensor] = None,
+                     problem_idx: Optional[torch.Tensor] = None, q_begin: int = 0, out=None):
+    """hj_solve without any device allocation inside the library (its scratch
+    is a fixed static array); for callers that cannot allocate while solving.
+    The output tensors are the caller's: pass them in `out` to keep the call
+    free of allocations on the Python side too."""
+    n = x.shape[0]
+    _dev(ctx, x, "x", ctx.dtype, (n, ctx.ld)); _dev(ctx, t, "t", ctx.dtype, (n,))
+    _dev(ctx, n_steps, "n_steps", torch.int32, (n,)); _dev(ctx, problem_idx, "problem_idx", torch.int32, (n,))
+    if out is None:
+        phi = torch.empty(n, dtype=torch.float64, device=x.device)
+        v = torch.zeros(n, ctx.ld, dtype=ctx.dtype, device=x.device)
+        status = torch.empty(n, dtype=torch.int32, device=x.device)
+    else:
+        phi, v, status = out
+    _check(ctx, load_library().hj_solve_noalloc(ctx.handle, q_begin, n, _ptr(problem_idx), _ptr(x), _ptr(t),
+                                                _ptr(n_steps), _ptr(phi), _ptr(v), _ptr(status), _stream(x.device)))
     return phi, v, status
 
 
