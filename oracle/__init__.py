@@ -17,7 +17,9 @@ Paper passages followed (all in arXiv 1704.02524):
     illustration), eq. num_int (rectangle rule), eq. num_diff (finite
     differences).
   * Sec. 4.3 -- the certificate p(0) in dg(gamma(0)) and restart on failure.
-  * Sec. 5 -- random initial guesses in [-2,2]^d, at most 20 trials.
+  * Sec. 5 -- random initial guesses in [-2,2]^d, at most 20 trials; the
+    remark that momentum helps descents that drag along flat trenches
+    (conjugate-gradient descent, DESC_CG).
 """
 from __future__ import annotations
 
@@ -42,7 +44,7 @@ LAX, HOPF = 0, 1
 G_QUAD_SHIFT, G_DIAG_QUAD = 0, 1
 QUAD_RK4, QUAD_RECT = 0, 1
 GRAD_FD_CENTRAL, GRAD_FD_FORWARD, GRAD_ADJOINT = 0, 1, 2
-DESC_CD, DESC_GD = 0, 1
+DESC_CD, DESC_GD, DESC_CG = 0, 1, 2
 ST_CERTIFIED, ST_MAX_ITERS, ST_NONFINITE, ST_RESEEDED = 1, 2, 4, 8
 
 

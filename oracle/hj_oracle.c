@@ -23,7 +23,9 @@
  *   - derivatives by the finite differences of eq. num_diff (forward) or
  *     the central form, and the exact gradient of the discretised
  *     functional by the discrete adjoint of the RK4 map;
- *   - cyclic coordinate descent (Algorithm 1) and gradient descent;
+ *   - cyclic coordinate descent (Algorithm 1), gradient descent, and a
+ *     conjugate-gradient (momentum) descent for ill-conditioned functionals
+ *     (Sec. 5 points to momentum methods when plain descent drags);
  *   - the certificate p(0) in dg(gamma(0)) (Sec. 4.3), reseeding of failed
  *     starts and best-of-guesses (Sec. 5: multiple random initial guesses).
  *
@@ -49,7 +51,7 @@ enum { LAX = 0, HOPF = 1 };
 enum { G_QUAD_SHIFT = 0, G_DIAG_QUAD = 1 };
 enum { QUAD_RK4 = 0, QUAD_RECT = 1 };
 enum { GRAD_FD_CENTRAL = 0, GRAD_FD_FORWARD = 1, GRAD_ADJOINT = 2 };
-enum { DESC_CD = 0, DESC_GD = 1 };
+enum { DESC_CD = 0, DESC_GD = 1, DESC_CG = 2 };
 
 /* Per-query status bits (same meaning as the library's, defined separately). */
 #define ST_CERTIFIED 1
@@ -74,7 +76,7 @@ typedef struct {
 
 typedef struct {
     int quad;            /* QUAD_RK4 / QUAD_RECT                                 */
-    int descent;         /* DESC_CD / DESC_GD                                    */
+    int descent;         /* DESC_CD / DESC_GD / DESC_CG                          */
     int grad;            /* GRAD_FD_CENTRAL / GRAD_FD_FORWARD / GRAD_ADJOINT     */
     double fd_h;         /* finite-difference step sigma of eq. num_diff         */
     double step;         /* alpha = 1/L of Algorithm 1                           */
@@ -568,12 +570,16 @@ void orc_gradient_fd(const orc_problem *P, int quad, const double *x, double t, 
  * coordinate trigger for Algorithm 1's "alpha := alpha/2"; the global
  * halving every `halving_period` iterations still applies on top.
  * Returns the number of iterations; *hit_cap is set when the cap stopped it. */
+static int descend_cg(const orc_problem *P, const orc_opts *O, const double *x, double t, int N, double *v,
+                      int *hit_cap, int *nonfinite);
+
 int orc_descend(const orc_problem *P, const orc_opts *O, const double *x, double t, int N, double *v, int *hit_cap,
                 int *nonfinite)
 {
     int d = P->d;
     *hit_cap = 0;
     *nonfinite = 0;
+    if (O->descent == DESC_CG) return descend_cg(P, O, x, t, N, v, hit_cap, nonfinite);
     if (O->descent == DESC_CD) {
         double alpha[ORC_DMAX], dprev[ORC_DMAX];
         for (int i = 0; i < d; ++i) { alpha[i] = O->step; dprev[i] = 0.0; }
@@ -631,6 +637,62 @@ int orc_descend(const orc_problem *P, const orc_opts *O, const double *x, double
         *hit_cap = 1;
         return it;
     }
+}
+
+/* Conjugate-gradient descent with the adjoint gradient (Sec. 5 remarks that
+ * descent along long, flat trenches needs momentum; conjugate directions are
+ * the momentum that is exact for quadratic functionals, such as the
+ * linear-quadratic family's, where plain descent needs ~condition-number
+ * iterations).  Polak-Ribiere+ directions with one secant line search per
+ * iteration:
+ *   g = grad F(v); dir = -g
+ *   repeat (one iteration):
+ *     n = max_i |dir_i|;  sigma = step / n           (probe: largest move = step)
+ *     gp = grad F(v + sigma dir)
+ *     s0 = <g, dir>, s1 = <gp, dir>, curv = (s1 - s0) / sigma
+ *     alpha = -s0 / curv if curv > 0, else sigma;  alpha <= step_max / n
+ *     v += alpha dir;  stop if alpha n < eps, or at max_iters
+ *     gn = grad F(v);  beta = max(0, <gn, gn - g> / <g, g>)
+ *     dir = -gn + beta dir;  dir = -gn if <gn, dir> >= 0;  g = gn
+ * On a quadratic the secant slope is its exact curvature along dir, so this
+ * is linear CG with exact line searches.  Returns the iteration count. */
+static int descend_cg(const orc_problem *P, const orc_opts *O, const double *x, double t, int N, double *v,
+                      int *hit_cap, int *nonfinite)
+{
+    int d = P->d;
+    double *g = (double *)malloc(sizeof(double) * 4 * (size_t)d), *dir = g + d, *gp = dir + d, *u = gp + d;
+    orc_gradient(P, O->quad, x, t, N, v, g);
+    for (int i = 0; i < d; ++i) dir[i] = -g[i];
+    int it = 0;
+    while (it < O->max_iters) {
+        double n = 0.0;
+        for (int i = 0; i < d; ++i) n = fmax(n, fabs(dir[i]));
+        if (!isfinite(n)) { *nonfinite = 1; free(g); return it; }
+        if (n == 0.0) { free(g); return it; }
+        double sigma = O->step / n;
+        for (int i = 0; i < d; ++i) u[i] = v[i] + sigma * dir[i];
+        orc_gradient(P, O->quad, x, t, N, u, gp);
+        double s0 = dot(g, dir, d), s1 = dot(gp, dir, d);
+        double curv = (s1 - s0) / sigma;
+        double alpha = (curv > 0.0) ? -s0 / curv : sigma;
+        if (alpha > O->step_max / n) alpha = O->step_max / n;
+        if (!isfinite(alpha)) { *nonfinite = 1; free(g); return it + 1; }
+        for (int i = 0; i < d; ++i) v[i] += alpha * dir[i];
+        ++it;
+        if (alpha * n < O->eps) { free(g); return it; }
+        if (it >= O->max_iters) break;
+        orc_gradient(P, O->quad, x, t, N, v, gp);
+        double gg = dot(g, g, d), gy = 0.0;
+        for (int i = 0; i < d; ++i) gy += gp[i] * (gp[i] - g[i]);
+        double beta = (gg > 0.0) ? fmax(0.0, gy / gg) : 0.0;
+        for (int i = 0; i < d; ++i) dir[i] = -gp[i] + beta * dir[i];
+        if (dot(gp, dir, d) >= 0.0)
+            for (int i = 0; i < d; ++i) dir[i] = -gp[i];
+        memcpy(g, gp, sizeof(double) * d);
+    }
+    free(g);
+    *hit_cap = 1;
+    return it;
 }
 
 /* ------------------------------------------------------------------------ */

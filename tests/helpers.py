@@ -6,7 +6,9 @@ import numpy as np
 import oracle as O
 from paper_1704_02524_gb300 import workloads as W
 
-GRAD_CODES = {"fd_central": O.GRAD_FD_CENTRAL, "fd_forward": O.GRAD_FD_FORWARD, "adjoint": O.GRAD_ADJOINT}
+GRAD_CODES = {"fd_central": O.GRAD_FD_CENTRAL, "fd_forward": O.GRAD_FD_FORWARD, "adjoint": O.GRAD_ADJOINT,
+              "adjoint_cg": O.GRAD_ADJOINT}
+DESCENT_CODES = {"fd_central": O.DESC_CD, "fd_forward": O.DESC_CD, "adjoint": O.DESC_GD, "adjoint_cg": O.DESC_CG}
 QUAD_CODES = {"rk4": O.QUAD_RK4, "rect": O.QUAD_RECT}
 
 
@@ -17,7 +19,7 @@ def oracle_problem(spec: W.ProblemSpec) -> O.Problem:
 
 def oracle_opts(solver: dict, n_guesses: int) -> O.Opts:
     g = GRAD_CODES[solver["grad"]]
-    return O.Opts(quad=QUAD_CODES[solver["quad"]], descent=O.DESC_GD if g == O.GRAD_ADJOINT else O.DESC_CD,
+    return O.Opts(quad=QUAD_CODES[solver["quad"]], descent=DESCENT_CODES[solver["grad"]],
                   grad=g, fd_h=solver["fd_h"] if g != O.GRAD_ADJOINT else 1e-6, step=solver["step"],
                   max_iters=solver["max_iters"], halving_period=solver["halving_period"], eps=solver["eps"],
                   adapt=solver["adapt"], grow=solver["grow"], shrink=solver["shrink"],

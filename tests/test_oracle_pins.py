@@ -294,6 +294,85 @@ def test_gradient_descent_rule_on_closed_form():
     assert np.abs(v - vr).max() < 1e-10
 
 
+def _cg_rule_reference(grad, v0, step, step_max, iters):
+    """Polak-Ribiere+ conjugate gradients with one secant line search per
+    iteration, stepped by hand (the rule the oracle's DESC_CG states)."""
+    v = v0.copy()
+    g = grad(v)
+    dr = -g
+    for _ in range(iters):
+        n = np.abs(dr).max()
+        sig = step / n
+        gp = grad(v + sig * dr)
+        curv = (gp @ dr - g @ dr) / sig
+        a = -(g @ dr) / curv if curv > 0 else sig
+        a = min(a, step_max / n)
+        v = v + a * dr
+        gn = grad(v)
+        beta = max(0.0, gn @ (gn - g) / (g @ g))
+        dr = -gn + beta * dr
+        if gn @ dr >= 0:
+            dr = -gn
+        g = gn
+    return v
+
+
+def _p_hopf_diag(sig):
+    d = sig.size
+    return O.Problem(d=d, family=O.FAM_QUAD_ISO, principle=O.HOPF, g_kind=O.G_DIAG_QUAD, sigma=sig)
+
+
+def test_cg_rule_on_anisotropic_closed_form():
+    # Hopf with H = |p|^2/2 and g = sum x^2/(2 s^2): p is constant along the
+    # characteristics, so G(v) = sum (s_i^2 + t) v_i^2 / 2 - <x, v> exactly
+    # (any N); its gradient (s^2 + t) v - x is a diagonal quadratic's
+    sig = np.array([0.5, 0.8, 1.3, 2.0])
+    x, t = np.array([0.9, -1.1, 0.4, 1.7]), 0.6
+    v0 = np.array([1.5, -2.0, 0.3, -0.7])
+    lam = sig ** 2 + t
+    grad = lambda v: lam * v - x
+    P = _p_hopf_diag(sig)
+    for k in (1, 2, 3):
+        O_ = O.Opts(descent=O.DESC_CG, grad=O.GRAD_ADJOINT, step=0.25, step_max=50.0, max_iters=k, eps=0.0)
+        v, it, cap, nf = O.descend(P, O_, x, t, 9, v0)
+        assert it == k and cap and not nf
+        assert np.abs(v - _cg_rule_reference(grad, v0, 0.25, 50.0, k)).max() < 1e-10
+    # exact line searches on a quadratic with d distinct curvatures: d steps
+    O_ = O.Opts(descent=O.DESC_CG, grad=O.GRAD_ADJOINT, step=0.25, step_max=50.0, max_iters=4, eps=0.0)
+    v, *_ = O.descend(P, O_, x, t, 9, v0)
+    assert np.abs(v - x / lam).max() < 1e-9
+
+
+def test_cg_isotropic_quadratic_in_one_iteration():
+    P = _p_quad_iso(d=3)
+    x, t = np.array([1.5, -0.5, 0.25]), 0.7
+    O_ = O.Opts(descent=O.DESC_CG, grad=O.GRAD_ADJOINT, step=0.1, step_max=100.0, max_iters=1, eps=0.0)
+    v, it, cap, _ = O.descend(P, O_, x, t, 13, np.array([-1.0, 2.0, 0.5]))
+    assert it == 1 and np.abs(v - x / (1 + t)).max() < 1e-12
+
+
+def test_cg_solves_rank_deficient_linear_quadratic_where_gd_stalls():
+    # B of rank d/2 leaves directions of tiny curvature (condition ~1e5 here):
+    # conjugate directions reach the Riccati value in a few d iterations,
+    # plain gradient steps with the same number of gradients do not
+    rng = np.random.default_rng(21)
+    d, m = 16, 8
+    G0 = rng.normal(size=(d, d))
+    A = G0 / (2 * np.linalg.norm(G0, 2))
+    B = rng.normal(size=(d, m)) / math.sqrt(d)
+    P = O.Problem(d=d, family=O.FAM_LINEAR_QUAD, principle=O.LAX, g_kind=O.G_QUAD_SHIFT, A=A, B=B, a=np.zeros(d))
+    X = rng.normal(size=(3, d))
+    Pt = pins.riccati_P(A, B, 1.0)
+    phi = 0.5 * np.einsum("qi,ij,qj->q", X, Pt, X)
+    cg = oracle_opts(W.solver_constants(grad="adjoint_cg", step=1.0, step_max=100.0, eps=0.0, max_iters=4 * d,
+                                        max_trials=1, max_rounds=0), 1)
+    gd = oracle_opts(W.solver_constants(eps=0.0, max_iters=8 * d, max_trials=1, max_rounds=0), 1)
+    r_cg = O.solve(P, cg, X, 1.0, 50)
+    r_gd = O.solve(P, gd, X, 1.0, 50)
+    assert np.all(rel_err(r_cg["phi"], phi) < 1e-7)
+    assert np.any(rel_err(r_gd["phi"], phi) > 1e-4)
+
+
 # --------------------------------------------------------------------------
 # Certificate (Sec. 4.3)
 # --------------------------------------------------------------------------
