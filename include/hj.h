@@ -79,7 +79,10 @@ typedef enum {
 typedef enum {
     HJ_GRAD_FD_CENTRAL = 0, /* cyclic coordinate descent, (F(v+he)-F(v-he))/2h            */
     HJ_GRAD_FD_FORWARD = 1, /* cyclic coordinate descent, (F(v+he)-F(v))/h  (eq. num_diff) */
-    HJ_GRAD_ADJOINT = 2     /* gradient descent with the discrete-adjoint gradient         */
+    HJ_GRAD_ADJOINT = 2,    /* gradient descent with the discrete-adjoint gradient         */
+    HJ_GRAD_ADJOINT_CG = 3  /* conjugate-gradient descent with the discrete-adjoint
+                               gradient (the momentum Sec. 5 recommends when descent drags
+                               along flat trenches; see hj_solver_opts)                     */
 } hj_grad_mode;
 
 typedef enum {
@@ -103,7 +106,10 @@ typedef enum { HJ_PREC_FP32 = 0, HJ_PREC_FP64 = 1 } hj_precision;
  *                  QUAD_ISO: nothing
  *   g block:       HJ_G_QUAD_SHIFT: a[d];  HJ_G_DIAG_QUAD: s[d] (all > 0)
  * n_params must equal the total.  d in [1, 1024]; m in [1, 64] for
- * LINEAR_QUAD (d in [1, 128] there), else ignored.
+ * LINEAR_QUAD (d in [1, 128] there), else ignored.  LINEAR_QUAD computes
+ * B B^T once in double precision at hj_create and integrates
+ * d gamma/ds = A gamma + (B B^T) p, dp/ds = -A^T p with running cost
+ * p^T (B B^T) p / 2 (the same for both principles).
  */
 typedef struct {
     int d;
@@ -128,6 +134,16 @@ typedef struct {
  * counts gradient steps).  With `adapt`, each coordinate keeps its own
  * alpha_i, multiplied by `shrink` when its derivative changes sign between
  * consecutive visits and by `grow` (capped at step_max) when it keeps it.
+ * HJ_GRAD_ADJOINT_CG: Polak-Ribiere+ conjugate directions with one secant
+ * line search per iteration: from the gradient g at v and dir (first
+ * dir = -g), probe the gradient gp at v + sigma dir with sigma = step /
+ * max|dir|, move v by alpha dir with alpha = -<g,dir> / ((<gp,dir> -
+ * <g,dir>) / sigma) when that curvature is positive (else sigma), capped at
+ * step_max / max|dir|; stop when alpha max|dir| < eps or at max_iters
+ * (iterations, each two gradients); then dir = -gn + beta dir with
+ * beta = max(0, <gn, gn - g> / <g, g>), restarted at -gn when it is not a
+ * descent direction.  Exact line searches on quadratic functionals (the
+ * linear-quadratic family), whose conditioning defeats plain gradient steps.
  * Round 0 of hj_solve runs n_guesses starts per query (Philox4x32-10 draws
  * keyed by `seed`, counter (component/4, slot | round<<16, query id));
  * then up to `max_rounds` rounds restart failed starts, in slot order,

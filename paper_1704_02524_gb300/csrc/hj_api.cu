@@ -28,6 +28,10 @@ void reg_f64_sq_lax(Registry &);
 void reg_f64_sq_hopf(Registry &);
 void reg_f64_sn_lax(Registry &);
 void reg_f64_sn_hopf(Registry &);
+void reg_f32_lq_lax(Registry &);
+void reg_f32_lq_hopf(Registry &);
+void reg_f64_lq_lax(Registry &);
+void reg_f64_lq_hopf(Registry &);
 
 Registry &registry()
 {
@@ -45,6 +49,10 @@ Registry &registry()
         reg_f64_sq_hopf(*x);
         reg_f64_sn_lax(*x);
         reg_f64_sn_hopf(*x);
+        reg_f32_lq_lax(*x);
+        reg_f32_lq_hopf(*x);
+        reg_f64_lq_lax(*x);
+        reg_f64_lq_hopf(*x);
         return x;
     }();
     return *r;
@@ -57,7 +65,10 @@ namespace {
 
 thread_local std::string g_create_error;
 
-enum Kind { K_EVAL = 0, K_GRAD = 1, K_CD = 2, K_GD = 3, K_CERT = 4 };
+enum Kind { K_EVAL = 0, K_GRAD = 1, K_CD = 2, K_GD = 3, K_CERT = 4, K_CG = 5 };
+
+// Descent kernel kind of a gradient mode.
+int desc_kind(int grad) { return grad == HJ_GRAD_ADJOINT ? K_GD : grad == HJ_GRAD_ADJOINT_CG ? K_CG : K_CD; }
 
 // Arithmetic per RK4 step of one pair (FMA = 2, add/mul = 1, sin/cos and
 // rsqrt not counted), from the operations written in hj_device.cuh.  The
@@ -79,6 +90,12 @@ FlopModel flop_model(int fam, int pr, int d)
         fld = (pr == HJ_LAX ? 11.0 : 10.0) * d + 7;
         vjp = (pr == HJ_LAX ? 13.0 : 11.0) * d + 20;
         break;
+    case HJ_FAM_LINEAR_QUAD:
+        // three d x d products (A gamma, Cm p, A^T p) per field and per
+        // vector-Jacobian product (A^T ag, A ap, Cm ag)
+        fld = 6.0 * d * d + 3.0 * d + 1;
+        vjp = 6.0 * d * d + 2.0 * d;
+        break;
     default: break;
     }
     return FlopModel{4 * fld + 26.0 * d + 12, 4 * vjp + 28.0 * d + 6};
@@ -95,7 +112,7 @@ void fill_prob(const hj_problem_desc &D, const std::vector<double> &par, int ld,
 {
     const int d = D.d, m = (D.family == HJ_FAM_LINEAR_QUAD) ? D.m : 0;
     const size_t nvec = 5 * (size_t)DPAD, nA = (size_t)d * d, nB = (size_t)d * m;
-    host.assign(nvec + (m ? nA + nB : 0), (T)0);
+    host.assign(nvec + (m ? 3 * nA : 0), (T)0);
     T *w = host.data(), *e = w + DPAD, *ga = e + DPAD, *gs2 = ga + DPAD, *gis2 = gs2 + DPAD;
     size_t off = 0;
     if (D.family == HJ_FAM_SPEED_QUAD || D.family == HJ_FAM_SMOOTH_NONCONVEX) {
@@ -103,7 +120,17 @@ void fill_prob(const hj_problem_desc &D, const std::vector<double> &par, int ld,
         off = d;
     }
     if (D.family == HJ_FAM_LINEAR_QUAD) {
-        for (size_t i = 0; i < nA + nB; ++i) host[nvec + i] = (T)par[i];
+        // At[j][i] = A[i][j], A[j][i], Cm = B B^T (double sums, then rounded)
+        T *At = host.data() + nvec, *A = At + nA, *Cm = A + nA;
+        const double *pA = par.data(), *pB = par.data() + nA;
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) {
+                At[(size_t)j * d + i] = (T)pA[(size_t)i * d + j];
+                A[(size_t)j * d + i] = (T)pA[(size_t)j * d + i];
+                double c = 0;
+                for (int k = 0; k < m; ++k) c += pB[(size_t)i * m + k] * pB[(size_t)j * m + k];
+                Cm[(size_t)j * d + i] = (T)c;
+            }
         off = nA + nB;
     }
     for (int i = 0; i < d; ++i) {
@@ -135,8 +162,9 @@ void bind_prob(void *block, int m, ProbDev<T> &P)
     P.ga = b + 2 * DPAD;
     P.gs2 = b + 3 * DPAD;
     P.gis2 = b + 4 * DPAD;
-    P.A = m ? b + 5 * DPAD : nullptr;
-    P.B = m ? b + 5 * DPAD + (size_t)P.d * P.d : nullptr;
+    P.At = m ? b + 5 * DPAD : nullptr;
+    P.A = m ? b + 5 * DPAD + (size_t)P.d * P.d : nullptr;
+    P.Cm = m ? b + 5 * DPAD + 2 * (size_t)P.d * P.d : nullptr;
 }
 
 }  // namespace
@@ -215,8 +243,6 @@ hj_status validate_problem(hj_ctx *ctx, const hj_problem_desc &D, int idx)
     if (D.family == HJ_FAM_LINEAR_QUAD) {
         if (D.m < 1 || D.m > 64 || D.d > 128)
             return fail(ctx, HJ_EINVAL, "problem %d: linear-quadratic needs m in [1,64], d <= 128", idx);
-        return fail(ctx, HJ_EUNSUPPORTED, "problem %d: the linear-quadratic family is not built into this library",
-                    idx);
     }
     if (D.family == HJ_FAM_SMOOTH_NONCONVEX && !(D.s_eps > 0))
         return fail(ctx, HJ_EINVAL, "problem %d: s_eps must be > 0", idx);
@@ -239,9 +265,12 @@ hj_status validate_opts(hj_ctx *ctx, const hj_solver_opts &o)
     if (o.n_steps_default < 1 || o.n_steps_default > MAX_N)
         return fail(ctx, HJ_EINVAL, "n_steps_default=%d outside [1, %d]", o.n_steps_default, MAX_N);
     if (o.quad != HJ_QUAD_RK4 && o.quad != HJ_QUAD_RECT) return fail(ctx, HJ_EINVAL, "unknown quad %d", (int)o.quad);
-    if (o.grad < HJ_GRAD_FD_CENTRAL || o.grad > HJ_GRAD_ADJOINT)
+    if (o.grad < HJ_GRAD_FD_CENTRAL || o.grad > HJ_GRAD_ADJOINT_CG)
         return fail(ctx, HJ_EINVAL, "unknown grad mode %d", (int)o.grad);
-    if (o.grad != HJ_GRAD_ADJOINT && !(o.fd_h > 0)) return fail(ctx, HJ_EINVAL, "fd_h must be > 0");
+    if ((o.grad == HJ_GRAD_FD_CENTRAL || o.grad == HJ_GRAD_FD_FORWARD) && !(o.fd_h > 0))
+        return fail(ctx, HJ_EINVAL, "fd_h must be > 0");
+    if (o.grad == HJ_GRAD_ADJOINT_CG && !(o.step_max > 0))
+        return fail(ctx, HJ_EINVAL, "conjugate gradients need step_max > 0");
     if (!(o.step > 0) || !std::isfinite(o.step)) return fail(ctx, HJ_EINVAL, "step must be finite and > 0");
     if (o.max_iters < 0) return fail(ctx, HJ_EINVAL, "max_iters must be >= 0");
     if (o.halving_period < 0) return fail(ctx, HJ_EINVAL, "halving_period must be >= 0");
@@ -266,7 +295,7 @@ int pick_c(int prec, int fam, int pr, int kind, int need)
         const KSet &k = R.k[prec][fam][pr][c];
         const void *f = kind == K_EVAL ? (const void *)k.eval : kind == K_GRAD ? (const void *)k.grad
                       : kind == K_CD ? (const void *)k.cd : kind == K_GD ? (const void *)k.gd
-                      : (const void *)k.cert_pairs;
+                      : kind == K_CG ? (const void *)k.cg : (const void *)k.cert_pairs;
         if (f) return c;
     }
     return -1;
@@ -282,7 +311,7 @@ bool choose(const hj_ctx *ctx, int p, int kind, int *tpp_out, int *c_out)
     int pref;
     if (kind == K_CERT) pref = 2;
     else if (ctx->prec == 1) pref = 4;
-    else if (kind == K_GRAD || kind == K_GD) pref = 5;
+    else if (kind == K_GRAD || kind == K_GD || kind == K_CG) pref = 5;
     else pref = 10;
     const int ov = ctx->tpp_override[p];
     for (int tpp = 1; tpp <= 32; tpp <<= 1) {
@@ -497,7 +526,7 @@ hj_status hj_create(const hj_problem_desc *problems, int n_problems, const hj_so
         pprin[i] = D.principle;
         int tpp, c;
         if (!choose(ctx, i, K_EVAL, &tpp, &c) || !choose(ctx, i, K_CERT, &tpp, &c) ||
-            !choose(ctx, i, opts->grad == HJ_GRAD_ADJOINT ? K_GD : K_CD, &tpp, &c)) {
+            !choose(ctx, i, desc_kind(opts->grad), &tpp, &c)) {
             fail(ctx, HJ_EUNSUPPORTED, "problem %d: no kernel built for d=%d in this precision", i, D.d);
             return bail(HJ_EUNSUPPORTED);
         }
@@ -557,7 +586,7 @@ hj_status hj_set_tuning(hj_ctx *ctx, int problem, int tpp, int ck_interval)
     int old = ctx->tpp_override[problem];
     ctx->tpp_override[problem] = tpp;
     int t, c;
-    const int kind = ctx->opts.grad == HJ_GRAD_ADJOINT ? K_GD : K_CD;
+    const int kind = desc_kind(ctx->opts.grad);
     if (!choose(ctx, problem, kind, &t, &c) || !choose(ctx, problem, K_EVAL, &t, &c) ||
         !choose(ctx, problem, K_GRAD, &t, &c)) {
         ctx->tpp_override[problem] = old;
@@ -701,7 +730,7 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
     hj_status st = ensure_scratch(ctx, n_queries, npairs);
     if (st != HJ_OK) return st;
     const int32_t *pidx = ctx->np > 1 ? problem_idx : nullptr;
-    const int kind = ctx->opts.grad == HJ_GRAD_ADJOINT ? K_GD : K_CD;
+    const int kind = desc_kind(ctx->opts.grad);
     // choose kernels up front so nothing is enqueued on failure
     std::vector<int> tpp_d(ctx->np), c_d(ctx->np), tpp_c(ctx->np), c_c(ctx->np);
     for (int p = 0; p < ctx->np; ++p)
@@ -726,8 +755,8 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
         if (ctx->timing) { st = record(ctx, ctx->ev_desc, ctx->n_desc_ev++, s); if (st != HJ_OK) return st; }
         for (int p = 0; p < ctx->np; ++p) {
             const KSet &k = kset(ctx, p, c_d[p]);
-            Launch L = kind == K_GD ? k.gd : k.cd;
-            const void *fn = kind == K_GD ? k.f_gd : k.f_cd;
+            Launch L = kind == K_GD ? k.gd : kind == K_CG ? k.cg : k.cd;
+            const void *fn = kind == K_GD ? k.f_gd : kind == K_CG ? k.f_cg : k.f_cd;
             auto fill = [&](auto &a) {
                 a.tpp = tpp_d[p];
                 a.problem = p;
@@ -1023,7 +1052,7 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
     }
     noalloc_layout(g_noalloc_ptr[ctx->device], ctx->np, n_queries, npairs, ctx->ld, es, &L);
     const int32_t *pidx = ctx->np > 1 ? problem_idx : nullptr;
-    const int kind = ctx->opts.grad == HJ_GRAD_ADJOINT ? K_GD : K_CD;
+    const int kind = desc_kind(ctx->opts.grad);
     std::vector<int> tpp_d(ctx->np), c_d(ctx->np), tpp_c(ctx->np), c_c(ctx->np);
     for (int p = 0; p < ctx->np; ++p)
         if (!choose(ctx, p, kind, &tpp_d[p], &c_d[p]) || !choose(ctx, p, K_CERT, &tpp_c[p], &c_c[p]))
@@ -1040,8 +1069,8 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
         CU(cudaMemsetAsync(L.amb_count, 0, sizeof(int32_t) * ctx->np, s));
         for (int p = 0; p < ctx->np; ++p) {
             const KSet &k = kset(ctx, p, c_d[p]);
-            Launch Lk = kind == K_GD ? k.gd : k.cd;
-            const void *fn = kind == K_GD ? k.f_gd : k.f_cd;
+            Launch Lk = kind == K_GD ? k.gd : kind == K_CG ? k.cg : k.cd;
+            const void *fn = kind == K_GD ? k.f_gd : kind == K_CG ? k.f_cg : k.f_cd;
             auto fill = [&](auto &a) {
                 a.tpp = tpp_d[p];
                 a.problem = p;

@@ -38,8 +38,11 @@ struct ProbDev {
     const T *ga;    // [DPAD] shift a of g = |x-a|^2/2
     const T *gs2;   // [DPAD] sigma^2 of g = sum x^2/(2 sigma^2)
     const T *gis2;  // [DPAD] 1/sigma^2
-    const T *A;     // [d*d] row-major (linear-quadratic family)
-    const T *B;     // [d*m] row-major
+    // linear-quadratic family, d x d each, all read as M[j*d + i] so that the
+    // lanes of a group (consecutive i) read consecutive addresses:
+    const T *At;    // At[j*d + i] = A[i][j]   (for A gamma)
+    const T *A;     // A[j*d + i]  = A[j][i]   (for A^T p)
+    const T *Cm;    // Cm[j*d + i] = (B B^T)[j][i], symmetric
 };
 
 // Solver constants on the device.
@@ -170,9 +173,15 @@ __device__ __forceinline__ T start_component(unsigned long long seed, long long 
 // Per-thread copies of the per-component parameters the field needs (the
 // initial-data parameters are read from memory at the terminal term).
 // ---------------------------------------------------------------------------
+// The linear-quadratic family also keeps its matrices' addresses and a
+// per-group shared-memory scratch of 2 C tpp values, through which a group
+// exchanges the vectors its matrix-vector products need.
 template <typename T, int C>
 struct TP {
     T w[C], e[C];
+    const T *At, *A, *Cm;
+    T *sh;
+    int d;
     __device__ void load(const ProbDev<T> &P, const Grp &g)
     {
 #pragma unroll
@@ -181,7 +190,18 @@ struct TP {
             w[k] = P.w[i];
             e[k] = P.e[i];
         }
+        At = P.At;
+        A = P.A;
+        Cm = P.Cm;
+        d = P.d;
+        sh = nullptr;
     }
+};
+
+// Shared scratch of the linear-quadratic family: 2 C values per thread.
+template <typename T, int C, int FAM>
+struct LqScratch {
+    static constexpr int N = (FAM == HJ_FAM_LINEAR_QUAD) ? 2 * C : 1;
 };
 
 // ---------------------------------------------------------------------------
@@ -384,6 +404,103 @@ struct Family<T, C, HJ_FAM_SMOOTH_NONCONVEX, PR> {
             rg[k] = dEdu * tp.w[k];
             rp[k] = fma(ce * a * er * er, er, kd * f.dphi[k]);
         }
+    }
+};
+
+// H = <A gamma, p> + p^T (B B^T) p / 2 (Cm = B B^T):
+// dZ/dtau = (-(A gamma + Cm p), A^T p), L = p^T Cm p / 2 for both principles
+// (<p, H_p> - H and H - <H_x, gamma> coincide).  The field is linear, so the
+// vector-Jacobian product needs only Cm p of the stage (for the cost row):
+// rg = -A^T ag,  rp = A ap - Cm ag + b Cm p.
+// Each product sum_j M[j][i] u_j runs over j with u staged in the group's
+// shared scratch (broadcast reads) and M read from global memory (L1
+// resident; consecutive lanes read consecutive i).
+template <typename T, int C>
+__device__ __forceinline__ void lq_stage2(const Grp &g, T *sh, const T *a, const T *b)
+{
+    const int n = C * g.tpp;
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        sh[g.lane + k * g.tpp] = a[k];
+        sh[n + g.lane + k * g.tpp] = b[k];
+    }
+    __syncwarp(g.mask);
+}
+
+template <typename T, int C, int PR>
+struct Family<T, C, HJ_FAM_LINEAR_QUAD, PR> {
+    struct FI {
+        T L;
+        T ax[C], cp[C], atp[C];
+    };
+    __device__ static __forceinline__ void prep(const Grp &g, const TP<T, C> &tp, T, const T *gam, const T *p, FI &f)
+    {
+        T *sh = tp.sh;
+        const int n = C * g.tpp, d = tp.d;
+        lq_stage2<T, C>(g, sh, gam, p);
+        bool ok[C];
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            ok[k] = g.lane + k * g.tpp < d;
+            f.ax[k] = 0;
+            f.cp[k] = 0;
+            f.atp[k] = 0;
+        }
+        for (int j = 0; j < d; ++j) {
+            const T gj = sh[j], pj = sh[n + j];
+            const T *at = tp.At + (size_t)j * d, *a = tp.A + (size_t)j * d, *cm = tp.Cm + (size_t)j * d;
+#pragma unroll
+            for (int k = 0; k < C; ++k) {
+                const int i = g.lane + k * g.tpp;
+                if (ok[k]) {
+                    f.ax[k] = fma(__ldg(at + i), gj, f.ax[k]);
+                    f.cp[k] = fma(__ldg(cm + i), pj, f.cp[k]);
+                    f.atp[k] = fma(__ldg(a + i), pj, f.atp[k]);
+                }
+            }
+        }
+        __syncwarp(g.mask);
+        T pcp = 0;
+#pragma unroll
+        for (int k = 0; k < C; ++k) pcp = fma(p[k], f.cp[k], pcp);
+        f.L = (T)0.5 * gsum(g, pcp);
+    }
+    __device__ static __forceinline__ void field_fi(const TP<T, C> &, const FI &f, T, T *dg, T *dp, T &L)
+    {
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            dg[k] = -(f.ax[k] + f.cp[k]);
+            dp[k] = f.atp[k];
+        }
+        L = f.L;
+    }
+    __device__ static __forceinline__ void vjp_fi(const Grp &g, const TP<T, C> &tp, const FI &f, T, const T *ag,
+                                                  const T *ap, T b, T *rg, T *rp)
+    {
+        T *sh = tp.sh;
+        const int n = C * g.tpp, d = tp.d;
+        lq_stage2<T, C>(g, sh, ag, ap);
+        bool ok[C];
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            ok[k] = g.lane + k * g.tpp < d;
+            rg[k] = 0;
+            rp[k] = b * f.cp[k];
+        }
+        for (int j = 0; j < d; ++j) {
+            const T agj = sh[j], apj = sh[n + j];
+            const T *at = tp.At + (size_t)j * d, *a = tp.A + (size_t)j * d, *cm = tp.Cm + (size_t)j * d;
+#pragma unroll
+            for (int k = 0; k < C; ++k) {
+                const int i = g.lane + k * g.tpp;
+                if (ok[k]) {
+                    rg[k] = fma(-__ldg(a + i), agj, rg[k]);
+                    rp[k] = fma(__ldg(at + i), apj, rp[k]);
+                    rp[k] = fma(-__ldg(cm + i), agj, rp[k]);
+                }
+            }
+        }
+        __syncwarp(g.mask);
     }
 };
 

@@ -20,10 +20,10 @@ cudaError_t launch_grad(const void *a, int grid, cudaStream_t s)
     k_grad<T, C, FAM, PR><<<grid, BLOCK, 0, s>>>(*(const RowArgs<T> *)a);
     return cudaGetLastError();
 }
-template <typename T, int C, int FAM, int PR, bool GD>
+template <typename T, int C, int FAM, int PR, int MODE>
 cudaError_t launch_desc(const void *a, int grid, cudaStream_t s)
 {
-    k_desc<T, C, FAM, PR, GD><<<grid, BLOCK, 0, s>>>(*(const DescArgs<T> *)a);
+    k_desc<T, C, FAM, PR, MODE><<<grid, BLOCK, 0, s>>>(*(const DescArgs<T> *)a);
     return cudaGetLastError();
 }
 template <typename Tv, int C, int FAM, int PR, int MODE>
@@ -44,10 +44,12 @@ void register_compute(Registry &r)
       r.k[prec_index<T>()][FAM][PR][Cs].f_eval = (const void *)&k_eval<T, Cs, FAM, PR>,
       r.k[prec_index<T>()][FAM][PR][Cs].grad = &launch_grad<T, Cs, FAM, PR>,
       r.k[prec_index<T>()][FAM][PR][Cs].f_grad = (const void *)&k_grad<T, Cs, FAM, PR>,
-      r.k[prec_index<T>()][FAM][PR][Cs].cd = &launch_desc<T, Cs, FAM, PR, false>,
-      r.k[prec_index<T>()][FAM][PR][Cs].f_cd = (const void *)&k_desc<T, Cs, FAM, PR, false>,
-      r.k[prec_index<T>()][FAM][PR][Cs].gd = &launch_desc<T, Cs, FAM, PR, true>,
-      r.k[prec_index<T>()][FAM][PR][Cs].f_gd = (const void *)&k_desc<T, Cs, FAM, PR, true>),
+      r.k[prec_index<T>()][FAM][PR][Cs].cd = &launch_desc<T, Cs, FAM, PR, DESC_CD>,
+      r.k[prec_index<T>()][FAM][PR][Cs].f_cd = (const void *)&k_desc<T, Cs, FAM, PR, DESC_CD>,
+      r.k[prec_index<T>()][FAM][PR][Cs].gd = &launch_desc<T, Cs, FAM, PR, DESC_GD>,
+      r.k[prec_index<T>()][FAM][PR][Cs].f_gd = (const void *)&k_desc<T, Cs, FAM, PR, DESC_GD>,
+      r.k[prec_index<T>()][FAM][PR][Cs].cg = &launch_desc<T, Cs, FAM, PR, DESC_CG>,
+      r.k[prec_index<T>()][FAM][PR][Cs].f_cg = (const void *)&k_desc<T, Cs, FAM, PR, DESC_CG>),
      ...);
 }
 

@@ -10,13 +10,13 @@ constexpr int MAXC = 10;  // largest components-per-thread instantiated
 using Launch = cudaError_t (*)(const void *args, int grid, cudaStream_t stream);
 
 // Launchers of one (precision, family, principle, C) combination.  eval,
-// grad, cd and gd compute in the context precision; cert_* compute in FP64
+// grad, cd, gd and cg compute in the context precision; cert_* compute in FP64
 // and read v in the context precision.
 struct KSet {
-    Launch eval = nullptr, grad = nullptr, cd = nullptr, gd = nullptr, cert_rows = nullptr, cert_pairs = nullptr,
-           cert_final = nullptr;
-    const void *f_eval = nullptr, *f_grad = nullptr, *f_cd = nullptr, *f_gd = nullptr, *f_cert_rows = nullptr,
-               *f_cert_pairs = nullptr, *f_cert_final = nullptr;
+    Launch eval = nullptr, grad = nullptr, cd = nullptr, gd = nullptr, cg = nullptr, cert_rows = nullptr,
+           cert_pairs = nullptr, cert_final = nullptr;
+    const void *f_eval = nullptr, *f_grad = nullptr, *f_cd = nullptr, *f_gd = nullptr, *f_cg = nullptr,
+               *f_cert_rows = nullptr, *f_cert_pairs = nullptr, *f_cert_final = nullptr;
 };
 
 struct Registry {

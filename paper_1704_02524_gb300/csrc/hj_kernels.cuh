@@ -112,12 +112,21 @@ __device__ __forceinline__ void store_row(const Grp &g, T *row, int d, const T *
 // ---------------------------------------------------------------------------
 // Functional values at given (x, t, v) rows.
 // ---------------------------------------------------------------------------
+// Points tp.sh at the group's slice of the block's linear-quadratic scratch.
+template <typename T, int C, int FAM>
+__device__ __forceinline__ void bind_scratch(TP<T, C> &tp, T *sh, int tpp)
+{
+    if (FAM == HJ_FAM_LINEAR_QUAD) tp.sh = sh + (threadIdx.x & ~(tpp - 1)) * 2 * C;
+}
+
 template <typename T, int C, int FAM, int PR>
 __global__ void __launch_bounds__(BLOCK) k_eval(RowArgs<T> a)
 {
     const Grp g = make_grp(a.tpp);
     TP<T, C> tp;
     tp.load(a.P, g);
+    __shared__ T lq_sh[BLOCK * LqScratch<T, C, FAM>::N];
+    bind_scratch<T, C, FAM>(tp, lq_sh, a.tpp);
     const long long groups = (long long)gridDim.x * (BLOCK / a.tpp);
     for (long long r = ((long long)blockIdx.x * BLOCK + threadIdx.x) / a.tpp; r < a.n; r += groups) {
         if (a.pidx && a.pidx[r] != a.pfilter) continue;
@@ -141,6 +150,8 @@ __global__ void __launch_bounds__(BLOCK) k_grad(RowArgs<T> a)
     const Grp g = make_grp(a.tpp);
     TP<T, C> tp;
     tp.load(a.P, g);
+    __shared__ T lq_sh[BLOCK * LqScratch<T, C, FAM>::N];
+    bind_scratch<T, C, FAM>(tp, lq_sh, a.tpp);
     T ck[MAX_CK * 2 * C];
     T seg[MAX_SEG * 2 * C];
     const long long groups = (long long)gridDim.x * (BLOCK / a.tpp);
@@ -168,6 +179,8 @@ __global__ void __launch_bounds__(BLOCK) k_cert(CertArgs<Tv> a)
     const Grp g = make_grp(a.tpp);
     TP<double, C> tp;
     tp.load(a.P, g);
+    __shared__ double lq_sh[BLOCK * LqScratch<double, C, FAM>::N];
+    bind_scratch<double, C, FAM>(tp, lq_sh, a.tpp);
     long long n, begin = 0;
     if (MODE == 1) {
         n = a.wl_count[a.problem];
@@ -225,12 +238,19 @@ __global__ void __launch_bounds__(BLOCK) k_cert(CertArgs<Tv> a)
 // group whose pair has finished takes the next pair from the problem's work
 // list between iterations, so lanes never wait for a whole warp to drain.
 // ---------------------------------------------------------------------------
-template <typename T, int C, int FAM, int PR, bool GD>
-__global__ void __launch_bounds__(BLOCK, GD ? 3 : 4) k_desc(DescArgs<T> a)
+// MODE: 0 cyclic coordinate descent with finite differences (Algorithm 1),
+// 1 gradient descent, 2 conjugate-gradient descent (both with the adjoint).
+constexpr int DESC_CD = 0, DESC_GD = 1, DESC_CG = 2;
+
+template <typename T, int C, int FAM, int PR, int MODE>
+__global__ void __launch_bounds__(BLOCK, MODE != DESC_CD ? 3 : 4) k_desc(DescArgs<T> a)
 {
+    constexpr bool GD = MODE != DESC_CD;  // adjoint gradients (checkpoint storage)
     const Grp g = make_grp(a.tpp);
     TP<T, C> tp;
     tp.load(a.P, g);
+    __shared__ T lq_sh[BLOCK * LqScratch<T, C, FAM>::N];
+    bind_scratch<T, C, FAM>(tp, lq_sh, a.tpp);
     const int d = a.P.d;
     const long long n = a.wl_count[a.problem];
     const long long begin = a.seg_begin[a.problem];
@@ -247,8 +267,15 @@ __global__ void __launch_bounds__(BLOCK, GD ? 3 : 4) k_desc(DescArgs<T> a)
     int N = 1, it = 0, count = 0, kper = 0, bad = 0;
     T t = 0;
     T x[C], v[C], alpha[C], prev[C];
+    // conjugate gradients: direction, phase (0: gradient at v, 1: probe),
+    // probe length sigma and max|dir|
+    T dir[MODE == DESC_CG ? C : 1];
+    int phase = 0;
+    T sig = 0, dn = 0;
 #pragma unroll
     for (int k = 0; k < C; ++k) { x[k] = 0; v[k] = 0; alpha[k] = 0; prev[k] = 0; }
+#pragma unroll
+    for (int k = 0; k < (MODE == DESC_CG ? C : 1); ++k) dir[k] = 0;
 
     for (;;) {
         // ---- refill: groups without a pair take the next one ----------------
@@ -273,7 +300,7 @@ __global__ void __launch_bounds__(BLOCK, GD ? 3 : 4) k_desc(DescArgs<T> a)
                     alpha[k] = (T)a.S.step;
                     prev[k] = 0;
                 }
-                it = count = kper = bad = 0;
+                it = count = kper = bad = phase = 0;
                 active = true;
             }
         }
@@ -283,7 +310,75 @@ __global__ void __launch_bounds__(BLOCK, GD ? 3 : 4) k_desc(DescArgs<T> a)
         // ---- one iteration ----------------------------------------------------
         bool stop = (it >= a.S.max_iters), conv = false;
         if (!stop) {
-            if (GD) {
+            if constexpr (MODE == DESC_CG) {
+                // one gradient per pass: at v (phase 0) or at the probe v + sig dir
+                T pt[C], gr[C];
+#pragma unroll
+                for (int k = 0; k < C; ++k) pt[k] = phase ? fma(sig, dir[k], v[k]) : v[k];
+                gradient<T, C, FAM, PR>(g, tp, a.P, a.S.quad, a.S.kahan, a.S.ck_interval, x, pt, t, N, gr, ck, seg);
+                n_g++;
+                n_rk += N;
+                n_adj += N;
+                if (phase == 0) {
+                    // new direction (Polak-Ribiere+, restart when not descending)
+                    if (it == 0) {
+#pragma unroll
+                        for (int k = 0; k < C; ++k) dir[k] = -gr[k];
+                    } else {
+                        T gg = 0, gy = 0;
+#pragma unroll
+                        for (int k = 0; k < C; ++k) {
+                            gg = fma(prev[k], prev[k], gg);
+                            gy = fma(gr[k], gr[k] - prev[k], gy);
+                        }
+                        gsum2(g, gg, gy);
+                        const T beta = (gg > (T)0) ? fmax((T)0, gy / gg) : (T)0;
+                        T gd = 0;
+#pragma unroll
+                        for (int k = 0; k < C; ++k) {
+                            dir[k] = fma(beta, dir[k], -gr[k]);
+                            gd = fma(gr[k], dir[k], gd);
+                        }
+                        if (gsum(g, gd) >= (T)0) {
+#pragma unroll
+                            for (int k = 0; k < C; ++k) dir[k] = -gr[k];
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < C; ++k) prev[k] = gr[k];
+                    T n = 0;
+#pragma unroll
+                    for (int k = 0; k < C; ++k) n = fmax(n, fabs(dir[k]));
+                    bool fin = true;
+#pragma unroll
+                    for (int k = 0; k < C; ++k) fin = fin && finite_(dir[k]);
+                    n = gmax(g, fin ? n : (T)INFINITY);
+                    if (!(n < (T)INFINITY)) { bad = 1; stop = true; }
+                    else if (n == (T)0) { conv = stop = true; }
+                    else { dn = n; sig = (T)a.S.step / n; phase = 1; }
+                } else {
+                    // secant line search along dir, then the move
+                    T s0 = 0, s1 = 0;
+#pragma unroll
+                    for (int k = 0; k < C; ++k) {
+                        s0 = fma(prev[k], dir[k], s0);
+                        s1 = fma(gr[k], dir[k], s1);
+                    }
+                    gsum2(g, s0, s1);
+                    const T curv = (s1 - s0) / sig;
+                    T al = (curv > (T)0) ? -s0 / curv : sig;
+                    const T cap = (T)a.S.step_max / dn;
+                    if (al > cap) al = cap;
+                    ++it;
+                    if (!finite_(al)) { bad = 1; stop = true; }
+                    else {
+#pragma unroll
+                        for (int k = 0; k < C; ++k) v[k] = fma(al, dir[k], v[k]);
+                        if (al * dn < eps_stop) conv = stop = true;
+                        phase = 0;
+                    }
+                }
+            } else if (GD) {
                 T gr[C];
                 gradient<T, C, FAM, PR>(g, tp, a.P, a.S.quad, a.S.kahan, a.S.ck_interval, x, v, t, N, gr, ck, seg);
                 n_g++;

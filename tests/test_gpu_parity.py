@@ -25,13 +25,18 @@ def hj():
     return H
 
 
-def _spec(family, principle, d, seed=0, n_neg=1, s_eps=1e-6, g_kind=None):
+def _spec(family, principle, d, seed=0, n_neg=1, s_eps=1e-6, g_kind=None, m=None):
     rng = np.random.default_rng(seed)
     if g_kind is None:
         g_kind = W.G_DIAG_QUAD if family == W.FAM_SMOOTH_NONCONVEX else W.G_QUAD_SHIFT
+    A = B = None
+    if family == W.FAM_LINEAR_QUAD:
+        G0 = rng.normal(size=(d, d))
+        A = W.f32(G0 / (2 * np.linalg.norm(G0, 2)))
+        B = W.f32(rng.normal(size=(d, m or max(1, d // 2))) / np.sqrt(d))
     return W.ProblemSpec(d=d, family=family, principle=principle, g_kind=g_kind,
                          w=W.f32(rng.normal(size=d) / np.sqrt(d)), a=W.f32(rng.uniform(-1, 1, d)),
-                         sigma=W.f32(rng.uniform(0.5, 2, d)), n_neg=n_neg, s_eps=s_eps, n_guesses=4)
+                         sigma=W.f32(rng.uniform(0.5, 2, d)), A=A, B=B, n_neg=n_neg, s_eps=s_eps, n_guesses=4)
 
 
 def _rows(n, d, seed, prec):
@@ -48,7 +53,8 @@ def _t(a, dtype):
 
 
 FAMS = [(W.FAM_QUAD_ISO, W.LAX), (W.FAM_QUAD_ISO, W.HOPF), (W.FAM_SPEED_QUAD, W.LAX), (W.FAM_SPEED_QUAD, W.HOPF),
-        (W.FAM_SMOOTH_NONCONVEX, W.HOPF), (W.FAM_SMOOTH_NONCONVEX, W.LAX)]
+        (W.FAM_SMOOTH_NONCONVEX, W.HOPF), (W.FAM_SMOOTH_NONCONVEX, W.LAX), (W.FAM_LINEAR_QUAD, W.LAX),
+        (W.FAM_LINEAR_QUAD, W.HOPF)]
 
 
 @pytest.mark.parametrize("family,principle", FAMS)
@@ -184,3 +190,51 @@ def test_step_counts_outside_range_give_nan_not_memory_errors(hj):
                               _t(N, torch.int32))
     assert np.all(np.isnan(E.cpu().numpy()))
     ctx.close()
+
+
+@pytest.mark.parametrize("d,m", [(64, 32), (100, 32), (128, 64), (8, 3)])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_linear_quadratic_functional_and_gradient_at_workload_sizes(hj, d, m, prec):
+    spec = _spec(W.FAM_LINEAR_QUAD, W.LAX, d, seed=d + m, m=m)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    opts = hj.opts_from_dict(W.lq_solver(), hj.HJ_PREC_FP32 if prec == "fp32" else hj.HJ_PREC_FP64, 100)
+    ctx = hj.hj_create([spec], opts, 0)
+    n = 37
+    rng = np.random.default_rng(d)
+    x = W.f32(rng.normal(size=(n, d)))
+    v = W.f32(rng.uniform(-2, 2, (n, d)))
+    t = W.f32(rng.uniform(0.1, 2.0, n))
+    N = rng.integers(1, 129, n).astype(np.int32)
+    F = hj.hj_eval_functional(ctx, _t(x, dt), _t(t, dt), _t(v, dt), _t(N, torch.int32)).cpu().numpy()
+    Fg, G = hj.hj_grad(ctx, _t(x, dt), _t(t, dt), _t(v, dt), _t(N, torch.int32))
+    Fg, G = Fg.cpu().numpy(), G.cpu().numpy()
+    P = oracle_problem(spec)
+    tolF = 2e-5 if prec == "fp32" else 1e-11
+    for i in range(n):
+        Fo, Go = O.gradient(P, x[i], t[i], int(N[i]), v[i])
+        assert rel_err(F[i], Fo) <= tolF, (i, F[i], Fo)
+        assert rel_err(Fg[i], Fo) <= tolF
+        scale = 1 + np.abs(Go).max()
+        assert np.abs(G[i] - Go).max() <= (5e-4 if prec == "fp32" else 1e-9) * scale, (i, G[i], Go)
+    ctx.close()
+
+
+def test_solve_linear_quadratic_d64_conjugate_gradients_matches_oracle(hj):
+    # conjugate directions (80 iterations) on the rank-deficient d=64 problem:
+    # phi within the accuracy target of the FP64 oracle running the same rule
+    phi, v, st, ref, info = _solve_both(hj, W.c4_linear_quad(nq=32), 32)
+    err = rel_err(phi, ref["phi"])
+    assert np.all(err <= 1e-4), err.max()
+    assert np.array_equal(st & 1, ref["status"] & 1)
+    assert info["iterations"] == 32 * 80
+
+
+def test_solve_speed_quad_d10_with_conjugate_gradients_matches_oracle(hj):
+    # smooth state-dependent functional: conjugate directions converge in
+    # ~10 iterations (20 gradients) where gradient steps take ~75
+    wl = W.c2_speed_quad(nq_x=16)
+    wl.solver.update(grad="adjoint_cg", step=0.2, step_max=2.0, max_iters=60)
+    phi, v, st, ref, info = _solve_both(hj, wl, 48)
+    err = rel_err(phi, ref["phi"])
+    assert np.all(err <= 1e-4), err.max()
+    assert np.array_equal(st & 1, ref["status"] & 1)
