@@ -266,7 +266,13 @@ hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out);
 /*
  * hj_set_tuning -- launch parameters of problem `problem` (used by the
  * autotuner and for experiments): tpp = threads per (query, start) pair of
- * the descent and gradient kernels, in {1,2,4,8,16,32} (0: automatic);
+ * the descent and gradient kernels, in {1,2,4,8,16,32} (0: automatic;
+ * for a LINEAR_QUAD problem in an fp32 context with RK4 quadrature, d <= 64
+ * and 2 d + m <= 256 after padding to multiples of 16, automatic means the
+ * tensor-core tile kernel for hj_eval_functional, hj_grad and the gradient
+ * and conjugate-gradient descents of hj_solve: 128 pairs per CTA, the stage
+ * products on the tensor cores in split-precision BF16x3 (relative error
+ * ~2^-16); any non-zero tpp selects the lane-group kernels instead);
  * ck_interval = RK4 steps between checkpoints of the adjoint, in [1, 16]
  * (0: automatic, the smallest interval whose checkpoint storage fits a
  * fixed per-thread budget).  Returns HJ_EUNSUPPORTED when no kernel is built

@@ -14,6 +14,7 @@
 #include "hj_internal.h"
 #include "hj_kernels.cuh"
 #include "hj_sched.h"
+#include "hj_tc.h"
 
 namespace hjd {
 void reg_f32_qi_lax(Registry &);
@@ -105,6 +106,10 @@ struct DevProblem {
     void *block32 = nullptr, *block64 = nullptr;
     ProbDev<float> pf{};
     ProbDev<double> pd{};
+    // linear-quadratic problems that fit the tensor-core tile kernel
+    bool tc = false;
+    LqTcGeom geom{};
+    void *wf_hi = nullptr, *wf_lo = nullptr, *wv_hi = nullptr, *wv_lo = nullptr;
 };
 
 template <typename T>
@@ -188,6 +193,10 @@ struct hj_ctx {
     void *vfin = nullptr;
     int32_t *pcount = nullptr, *seg_begin = nullptr, *wl_count = nullptr, *cursor = nullptr, *amb_count = nullptr;
     unsigned long long *stats = nullptr;
+    // tensor-core tile kernel scratch (per CTA slot) and its error word
+    float *tc_vec = nullptr, *tc_ybuf = nullptr;
+    size_t tc_vec_cap = 0, tc_ybuf_cap = 0;
+    int *tc_err = nullptr;
     // last solve
     cudaStream_t last_stream = nullptr;
     long long last_nq = 0;
@@ -351,6 +360,55 @@ int rows_grid(hj_ctx *ctx, const void *fn, long long n, int tpp)
 
 template <typename T>
 void *as_ptr(T *p) { return (void *)p; }
+
+// The tensor-core tile kernel runs problem p: fp32 context, linear-quadratic
+// problem that fits it, RK4 quadrature, no lane-group tuning override.
+bool tc_eligible(const hj_ctx *ctx, int p)
+{
+    return ctx->prec == 0 && ctx->dev[p].tc && ctx->tpp_override[p] == 0 && ctx->opts.quad == HJ_QUAD_RK4;
+}
+
+hj_status ensure_tc_scratch(hj_ctx *ctx, int p)
+{
+    const LqTcGeom &g = ctx->dev[p].geom;
+    const size_t nv = (size_t)ctx->nsm * lq_tc_vec_slot(g), ny = (size_t)ctx->nsm * lq_tc_ybuf_slot(g);
+    if (nv > ctx->tc_vec_cap) {
+        cudaFree(ctx->tc_vec);
+        ctx->tc_vec = nullptr;
+        ctx->tc_vec_cap = 0;
+        CU(cudaMalloc(&ctx->tc_vec, nv * sizeof(float)));
+        ctx->tc_vec_cap = nv;
+    }
+    if (ny > ctx->tc_ybuf_cap) {
+        cudaFree(ctx->tc_ybuf);
+        ctx->tc_ybuf = nullptr;
+        ctx->tc_ybuf_cap = 0;
+        CU(cudaMalloc(&ctx->tc_ybuf, ny * sizeof(float)));
+        ctx->tc_ybuf_cap = ny;
+    }
+    return HJ_OK;
+}
+
+LqTcArgs tc_args(const hj_ctx *ctx, int p)
+{
+    const DevProblem &D = ctx->dev[p];
+    const LqTcGeom &g = D.geom;
+    LqTcArgs a{};
+    a.d = g.d; a.dp = g.dp; a.m = g.m; a.mp = g.mp; a.ld = ctx->ld;
+    a.KF = g.KF; a.NF = g.NF; a.KV = g.KV; a.NV = g.NV; a.KZ = g.KZ;
+    a.w_bytes = g.w_bytes; a.z_bytes = g.z_bytes;
+    a.wf_hi = (const uint4 *)D.wf_hi; a.wf_lo = (const uint4 *)D.wf_lo;
+    a.wv_hi = (const uint4 *)D.wv_hi; a.wv_lo = (const uint4 *)D.wv_lo;
+    a.principle = D.pf.principle; a.g_kind = D.pf.g_kind;
+    a.ga = D.pf.ga; a.gs2 = D.pf.gs2; a.gis2 = D.pf.gis2;
+    a.n_default = ctx->opts.n_steps_default;
+    a.vec = ctx->tc_vec; a.vec_slot = lq_tc_vec_slot(g);
+    a.ybuf = ctx->tc_ybuf; a.ybuf_slot = lq_tc_ybuf_slot(g);
+    a.err = ctx->tc_err;
+    return a;
+}
+
+size_t tc_smem(const hj_ctx *ctx, int p) { return std::max(ctx->dev[p].geom.smem, LQ_TC_SMEM_MIN); }
 
 hj_status ensure_scratch(hj_ctx *ctx, long long nq, long long npairs)
 {
@@ -521,6 +579,20 @@ hj_status hj_create(const hj_problem_desc *problems, int n_problems, const hj_so
         bind_prob<float>(ctx->dev[i].block32, ctx->dev[i].pf.m, ctx->dev[i].pf);
         bind_prob<double>(ctx->dev[i].block64, ctx->dev[i].pd.m, ctx->dev[i].pd);
         ctx->dev[i].pf.n_guesses = ctx->dev[i].pd.n_guesses = D.n_guesses;
+        if (D.family == HJ_FAM_LINEAR_QUAD && ctx->prec == 0 && lq_tc_geometry(D.d, D.m, &ctx->dev[i].geom)) {
+            std::vector<uint8_t> fh, fl, vh, vl;
+            const double *pA = ctx->params[i].data(), *pB = pA + (size_t)D.d * D.d;
+            lq_tc_matrices(ctx->dev[i].geom, pA, pB, fh, fl, vh, vl);
+            CUC(cudaMalloc(&ctx->dev[i].wf_hi, fh.size()));
+            CUC(cudaMalloc(&ctx->dev[i].wf_lo, fl.size()));
+            CUC(cudaMalloc(&ctx->dev[i].wv_hi, vh.size()));
+            CUC(cudaMalloc(&ctx->dev[i].wv_lo, vl.size()));
+            CUC(cudaMemcpy(ctx->dev[i].wf_hi, fh.data(), fh.size(), cudaMemcpyHostToDevice));
+            CUC(cudaMemcpy(ctx->dev[i].wf_lo, fl.data(), fl.size(), cudaMemcpyHostToDevice));
+            CUC(cudaMemcpy(ctx->dev[i].wv_hi, vh.data(), vh.size(), cudaMemcpyHostToDevice));
+            CUC(cudaMemcpy(ctx->dev[i].wv_lo, vl.data(), vl.size(), cudaMemcpyHostToDevice));
+            ctx->dev[i].tc = true;
+        }
         pg[i] = D.n_guesses;
         pd[i] = D.d;
         pprin[i] = D.principle;
@@ -544,6 +616,8 @@ hj_status hj_create(const hj_problem_desc *problems, int n_problems, const hj_so
     CUC(cudaMalloc(&ctx->amb_count, sizeof(int32_t) * n_problems));
     CUC(cudaMalloc(&ctx->stats, sizeof(unsigned long long) * 8 * n_problems));
     CUC(cudaMemset(ctx->stats, 0, sizeof(unsigned long long) * 8 * n_problems));
+    CUC(cudaMalloc(&ctx->tc_err, sizeof(int)));
+    CUC(cudaMemset(ctx->tc_err, 0, sizeof(int)));
     CUC(cudaEventCreate(&ctx->ev_begin));
     CUC(cudaEventCreate(&ctx->ev_end));
 #undef CUC
@@ -559,7 +633,14 @@ hj_status hj_destroy(hj_ctx *ctx)
     for (auto &d : ctx->dev) {
         cudaFree(d.block32);
         cudaFree(d.block64);
+        cudaFree(d.wf_hi);
+        cudaFree(d.wf_lo);
+        cudaFree(d.wv_hi);
+        cudaFree(d.wv_lo);
     }
+    cudaFree(ctx->tc_vec);
+    cudaFree(ctx->tc_ybuf);
+    cudaFree(ctx->tc_err);
     void *ptrs[] = {ctx->d_pg, ctx->d_pd, ctx->d_pprin, ctx->starts, ctx->pair_base, ctx->block_sums, ctx->trials,
                     ctx->qflags, ctx->pair_q, ctx->pair_slot, ctx->pair_round, ctx->iters, ctx->wl, ctx->flags,
                     ctx->pP, ctx->pF, ctx->pR, ctx->vfin, ctx->pcount, ctx->seg_begin, ctx->wl_count, ctx->cursor,
@@ -602,6 +683,23 @@ static hj_status rows_launch(hj_ctx *ctx, int kind, int64_t n, const int32_t *pi
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device));
     for (int p = 0; p < ctx->np; ++p) {
+        if (tc_eligible(ctx, p)) {
+            hj_status st = ensure_tc_scratch(ctx, p);
+            if (st != HJ_OK) return st;
+            LqTcArgs a = tc_args(ctx, p);
+            a.n = n;
+            a.x = (const float *)x;
+            a.t = (const float *)t;
+            a.nsteps = ns;
+            a.v = (const float *)v;
+            a.F = (float *)F;
+            a.grad = (float *)grad;
+            a.pidx = (ctx->np > 1) ? pidx : nullptr;
+            a.pfilter = p;
+            const int grid = (int)std::min<long long>(ctx->nsm, (n + 127) / 128);
+            CU(lq_tc_launch(kind == K_EVAL ? LQ_ROWS_EVAL : LQ_ROWS_GRAD, a, std::max(grid, 1), tc_smem(ctx, p), s));
+            continue;
+        }
         int tpp, c;
         if (!choose(ctx, p, kind, &tpp, &c)) return fail(ctx, HJ_EUNSUPPORTED, "no kernel for problem %d", p);
         const KSet &k = kset(ctx, p, c);
@@ -731,6 +829,11 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
     if (st != HJ_OK) return st;
     const int32_t *pidx = ctx->np > 1 ? problem_idx : nullptr;
     const int kind = desc_kind(ctx->opts.grad);
+    for (int p = 0; p < ctx->np; ++p)
+        if (tc_eligible(ctx, p) && kind != K_CD) {
+            st = ensure_tc_scratch(ctx, p);
+            if (st != HJ_OK) return st;
+        }
     // choose kernels up front so nothing is enqueued on failure
     std::vector<int> tpp_d(ctx->np), c_d(ctx->np), tpp_c(ctx->np), c_c(ctx->np);
     for (int p = 0; p < ctx->np; ++p)
@@ -740,6 +843,10 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
     ctx->last_nq = n_queries;
     ctx->last_tpp = tpp_d[0];
     ctx->last_c = c_d[0];
+    if (tc_eligible(ctx, 0) && kind != K_CD) {
+        ctx->last_tpp = 1;  // one thread (and TMEM lane) per pair
+        ctx->last_c = ctx->dev[0].geom.dp;
+    }
     ctx->n_desc_ev = ctx->n_cert_ev = 0;
     CU(cudaEventRecord(ctx->ev_begin, s));
     CU(cudaMemsetAsync(ctx->stats, 0, sizeof(unsigned long long) * 8 * ctx->np, s));
@@ -787,6 +894,15 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                 a.P = ctx->dev[p].pd;
                 a.x = (const double *)x; a.t = (const double *)t; a.vfin = (double *)ctx->vfin;
                 CU(L(&a, persistent_grid(ctx, fn), s));
+            } else if (tc_eligible(ctx, p) && kind != K_CD) {
+                // tensor-core tile kernel: 128 pairs per CTA, one CTA per SM
+                LqTcArgs a = tc_args(ctx, p);
+                fill(a.D);
+                a.D.P = ctx->dev[p].pf;
+                a.D.x = (const float *)x; a.D.t = (const float *)t; a.D.vfin = (float *)ctx->vfin;
+                a.x = (const float *)x; a.t = (const float *)t; a.nsteps = n_steps;
+                a.mode_desc = (kind == K_CG) ? DESC_CG : DESC_GD;
+                CU(lq_tc_launch(LQ_DESC, a, ctx->nsm, tc_smem(ctx, p), s));
             } else {
                 DescArgs<float> a{};
                 fill(a);
@@ -902,6 +1018,10 @@ hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out)
     if (!ctx->last_nq) return HJ_OK;
     CU(cudaSetDevice(ctx->device));
     CU(cudaStreamSynchronize(ctx->last_stream));
+    int tc_err = 0;
+    CU(cudaMemcpy(&tc_err, ctx->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (tc_err)
+        return fail(ctx, HJ_ETIMEOUT, "tensor-core tile kernel: a bounded wait for the tensor cores ran out");
     std::vector<unsigned long long> st(8 * ctx->np);
     CU(cudaMemcpy(st.data(), ctx->stats, sizeof(unsigned long long) * st.size(), cudaMemcpyDeviceToHost));
     out->n_queries = ctx->last_nq;

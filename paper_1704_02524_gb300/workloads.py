@@ -193,12 +193,12 @@ def lq_solver(**over) -> Dict:
     """Constants of the linear-quadratic workloads.  The functional is a
     convex quadratic in v whose Hessian has eigenvalues down to ~1e-6 in the
     directions B does not reach (B has rank 32 of 64; condition ~3e6 at
-    d=64), so gradient steps stall and conjugate directions are used: 80
+    d=64), so gradient steps stall and conjugate directions are used: 100
     Polak-Ribiere+ iterations with secant line searches (probe length 1),
     one start (convex H, Sec. 5), no reseeding.  The certificate residual
     stays far above any useful tolerance there (the flat directions of F are
     not flat for p(0) - grad g(gamma(0))), on the oracle as on the GPU."""
-    c = solver_constants(grad="adjoint_cg", step=1.0, step_max=100.0, eps=0.0, max_iters=80, n_guesses=1,
+    c = solver_constants(grad="adjoint_cg", step=1.0, step_max=100.0, eps=0.0, max_iters=100, n_guesses=1,
                          max_trials=1, max_rounds=0)
     c.update(over)
     return c
