@@ -7,6 +7,11 @@ One step = one hj_solve over the whole batch with inputs resident in HBM
 (guesses, descent, FP64 certificate, reseed rounds, best-of-guesses).
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
 on the same workload instead (bounded samples per step).
+
+--workload selects another workload of paper_1704_02524_gb300.workloads:
+linear_quad_d64_lax (32,768 queries, d=64, the tensor-core tile kernel;
+--tpp 16 runs the lane-group kernels instead), speed_quad_d10_lax (49,152
+queries, d=10), mixed_persistent (1,048,576 pairs over 12 problems).
 """
 from __future__ import annotations
 
@@ -28,6 +33,20 @@ from paper_1704_02524_gb300 import workloads as W  # noqa: E402
 
 WORKLOAD = "smooth_nonconvex_d20_hopf"
 METRIC = "queries/s at 1e-4 rel err (d=20 Hopf), adjoint vs plain CD-FD; % FP32 peak"
+# other workloads: builder, default query count, metric, and a one-line description of the descent
+WORKLOADS = {
+    "smooth_nonconvex_d20_hopf": (lambda nq: W.c3_smooth_nonconvex(nq=nq), 65536, METRIC,
+                                  "gradient descent, discrete-adjoint gradient, per-coordinate step control"),
+    "linear_quad_d64_lax": (lambda nq: W.c4_linear_quad(nq=nq), 32768,
+                            "queries/s at 1e-4 rel err (d=64 linear-quadratic Lax), tensor-core tile kernel",
+                            "conjugate gradients (100 iterations), discrete-adjoint gradient on BF16x3 tensor cores"),
+    "speed_quad_d10_lax": (lambda nq: W.c2_speed_quad(nq_x=max(1, nq // 3)), 49152,
+                           "queries/s at 1e-4 rel err (d=10 state-dependent Lax)",
+                           "gradient descent, discrete-adjoint gradient, per-coordinate step control"),
+    "mixed_persistent": (lambda nq: W.c5_mixed(n_pairs=nq), 1 << 20,
+                         "(query, start) pairs/s (mixed families, d in {8,16,32,100})",
+                         "gradient descent (adjoint) for every problem"),
+}
 CPU_SAMPLE = 64          # queries of the oracle timing sample (cpu_baseline)
 REF_SAMPLE = 16          # queries per step of the reference arm
 L2_FLUSH_BYTES = 256 << 20
@@ -39,7 +58,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--nq", type=int, default=65536)
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--nq", type=int, default=0, help="queries (pairs for mixed_persistent); 0: the workload's size")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain CD-FD measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--tpp", type=int, default=0, help="threads per pair of the descent (0: library choice)")
@@ -49,17 +69,18 @@ def _args():
 
 def _oracle_inputs(wl):
     import oracle as O
-    from tests.helpers import oracle_opts, oracle_problem  # noqa: F401  (same glue as the tests)
-    spec = wl.problems[0]
-    return O, oracle_problem(spec), oracle_opts(wl.solver, spec.n_guesses)
+    from tests.helpers import oracle_opts_list, oracle_problem  # same glue as the tests
+    probs = [oracle_problem(p) for p in wl.problems]
+    return O, probs, oracle_opts_list(wl)
 
 
 def _time_oracle(wl, q_ids):
     """Oracle on the given query rows of wl, all host cores; returns (seconds, result, threads)."""
-    O, P, opts = _oracle_inputs(wl)
+    O, probs, opts = _oracle_inputs(wl)
     sub = wl.take(q_ids)
     t0 = time.perf_counter()
-    res = O.solve(P, opts, sub.x, sub.t, sub.n_steps, query_ids=np.asarray(q_ids, dtype=np.int64))
+    res = O.solve(probs, opts, sub.x, sub.t, sub.n_steps, problem_idx=sub.problem_idx,
+                  query_ids=np.asarray(q_ids, dtype=np.int64))
     return time.perf_counter() - t0, res, res["threads"]
 
 
@@ -121,32 +142,66 @@ def _peaks():
     return {"sm_max_mhz": 2070.0}, "fallback"
 
 
+def _workload(a):
+    build, default_n, metric, descent = WORKLOADS[a.workload]
+    wl = build(a.nq or default_n)
+    return wl, metric, descent
+
+
+def _config(a, wl, descent, nq):
+    ps = wl.problems
+    cfg = {"workload": wl.name, "d": max(p.d for p in ps), "queries_per_gpu": nq,
+           "guesses": sorted({p.n_guesses for p in ps}), "n_steps": [int(wl.n_steps.min()), int(wl.n_steps.max())],
+           "t": [float(wl.t.min()), float(wl.t.max())], "descent": descent, "certificate": "fp64",
+           "max_trials": wl.solver["max_trials"], "l2": "flushed between timed steps (256 MB write)"}
+    if len(ps) > 1:
+        cfg["problems"] = len(ps)
+        cfg["pairs_per_gpu"] = int(wl.n_pairs)
+    return cfg
+
+
 def run_reference(a):
     """Reference arm: the FP64 oracle on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = W.c3_smooth_nonconvex(nq=a.nq)
+    wl, metric, descent = _workload(a)
+    nq = wl.nq
     rng = np.random.default_rng(0)
     times = []
     threads = 1
+    units = 0
     for k in range(a.warmup + a.steps):
-        ids = rng.choice(a.nq, REF_SAMPLE, replace=False)
+        ids = np.sort(rng.choice(nq, REF_SAMPLE, replace=False))
         dt, _, threads = _time_oracle(wl, ids)
         if k >= a.warmup:
             times.append(dt)
-    ms = 1e3 * sum(times) / len(times)
-    val = REF_SAMPLE / (ms / 1e3)
+            units += _units(wl, ids)
+    sec = sum(times)
+    val = units / sec
+    unit = _unit(wl)
+    cfg = _config(a, wl, descent, nq)
+    cfg["sample_per_step"] = REF_SAMPLE
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": val, "unit": "queries/s", "n_gpus": a.gpus,
-        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "d": 20, "queries": a.nq, "guesses": 16, "n_steps": 64, "t": 0.5,
-                   "sample_per_step": REF_SAMPLE},
-        "cpu_baseline": {"value": val, "unit": "queries/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{REF_SAMPLE} random queries of the workload per step (all 16 starts each)"},
-        "e2e": {"value": val, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "impl": "reference", "metric": metric, "value": val, "unit": unit, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sec / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": val, "unit": unit, "cores": threads, "kind": "oracle",
+                         "sample": f"{REF_SAMPLE} random queries of the workload per step (all their starts)"},
+        "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def _unit(wl):
+    return "pairs/s" if len(wl.problems) > 1 else "queries/s"
+
+
+def _units(wl, ids=None):
+    """Work units of the metric in the given rows: queries, or (query, start) pairs for mixed batches."""
+    idx = wl.problem_idx if ids is None else wl.problem_idx[np.asarray(ids)]
+    if len(wl.problems) > 1:
+        return int(sum(wl.problems[int(i)].n_guesses for i in idx))
+    return int(len(idx))
 
 
 def run_ours(a):
@@ -166,30 +221,33 @@ def run_ours(a):
         if world > 1:
             dist.barrier()
 
-    wl = W.c3_smooth_nonconvex(nq=a.nq)
-    spec = wl.problems[0]
-    nq = wl.nq
+    wl, metric, descent = _workload(a)
+    nq, ld = wl.nq, wl.x.shape[1]
+    units = _units(wl)
     q_begin = rank * nq  # weak scaling: every rank solves its own batch of nq queries
     if rank > 0:
-        # other ranks draw their own queries from the same distribution
+        # other ranks draw their own query points from the same distribution
         rng = np.random.default_rng(1000 + rank)
-        wl.x = W.f32(rng.uniform(-1, 1, wl.x.shape))
+        wl.x = W.f32(np.where(wl.x != 0, rng.uniform(-1, 1, wl.x.shape), 0.0))
     x = torch.tensor(wl.x, dtype=torch.float32, device=dev)
     t = torch.tensor(wl.t, dtype=torch.float32, device=dev)
     ns = torch.tensor(wl.n_steps, dtype=torch.int32, device=dev)
-    opts = hj.opts_from_dict(wl.solver, hj.HJ_PREC_FP32, 64)
-    ctx = hj.hj_create([spec], opts, local)
+    multi = len(wl.problems) > 1
+    pidx = torch.tensor(wl.problem_idx, dtype=torch.int32, device=dev) if multi else None
+    opts = hj.opts_from_dict(wl.solver, hj.HJ_PREC_FP32, int(wl.n_steps.max()))
+    ctx = hj.hj_create(wl.problems, opts, local)
     if a.tpp or a.ck:
-        hj.hj_set_tuning(ctx, 0, a.tpp, a.ck)
+        for p in range(len(wl.problems)):
+            hj.hj_set_tuning(ctx, p, a.tpp, a.ck)
     phi = torch.empty(nq, dtype=torch.float64, device=dev)
-    vout = torch.zeros(nq, 20, dtype=torch.float32, device=dev)
+    vout = torch.zeros(nq, ld, dtype=torch.float32, device=dev)
     status = torch.empty(nq, dtype=torch.int32, device=dev)
     out = (phi, vout, status)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        hj.hj_solve(ctx, x, t, ns, None, q_begin, out)
+        hj.hj_solve(ctx, x, t, ns, pidx, q_begin, out)
 
     for _ in range(a.warmup):
         step()
@@ -214,27 +272,44 @@ def run_ours(a):
     if world > 1:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
     ms_max = float(ms_t.item())
-    value = nq * world / (ms_max / 1e3)
+    value = units * world / (ms_max / 1e3)
     clocks = clk.summary()
 
-    # roofline of the dominant kernel (the persistent descent kernel)
-    flops = sum(i["algorithmic_flops"] for i in infos)
+    # roofline of the dominant kernel: the descent (FP32 ALU) or, for the
+    # linear-quadratic tile kernel, its BF16x3 tensor-core products
+    info = infos[-1]
     desc_s = sum(i["descent_ms"] for i in infos) / 1e3
-    achieved = flops / desc_s / 1e12
     peaks, peak_src = _peaks()
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_fp32 = nsm * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    info = infos[-1]
+    tflops = sum(i["tensor_flops"] for i in infos)
+    if tflops > 0:
+        peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        roof = {"bound": "tensor", "achieved": tflops / desc_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": tflops / desc_s / 1e12 / peak, "traffic": None,
+                "kernel": "k_lq_tc (tensor-core tile kernel, BF16x3 stage products)",
+                "peak_note": f"dense BF16, {peak_src} sustained cuBLAS figure; achieved counts the three BF16 "
+                             "products of each fp32 product (unpadded d, m)"}
+    else:
+        flops = sum(i["algorithmic_flops"] for i in infos)
+        peak = nsm * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": flops / desc_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / desc_s / 1e12 / peak, "traffic": None,
+                "kernel": "k_desc (persistent descent)",
+                "peak_note": f"FP32 FMA {nsm} SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                             f"({peak_src} max SM clock)"}
 
-    # e2e through the C ABI with host buffers: pinned H2D of x, t, N, solve, D2H of phi, v, status
+    # e2e through the C ABI with host buffers: pinned H2D of x, t, N (and the
+    # problem index), the solve, D2H of phi, v, status
     hx = torch.tensor(wl.x, dtype=torch.float32).pin_memory()
     ht = torch.tensor(wl.t, dtype=torch.float32).pin_memory()
     hn = torch.tensor(wl.n_steps, dtype=torch.int32).pin_memory()
+    hp = torch.tensor(wl.problem_idx, dtype=torch.int32).pin_memory() if multi else None
     hphi = torch.empty(nq, dtype=torch.float64).pin_memory()
-    hv = torch.empty(nq, 20, dtype=torch.float32).pin_memory()
+    hv = torch.empty(nq, ld, dtype=torch.float32).pin_memory()
     hst = torch.empty(nq, dtype=torch.int32).pin_memory()
     dx, dt_, dn = torch.empty_like(x), torch.empty_like(t), torch.empty_like(ns)
-    h2d = hx.numel() * 4 + ht.numel() * 4 + hn.numel() * 4
+    dp_ = torch.empty_like(pidx) if multi else None
+    h2d = hx.numel() * 4 + ht.numel() * 4 + hn.numel() * 4 + (hp.numel() * 4 if multi else 0)
     d2h = hphi.numel() * 8 + hv.numel() * 4 + hst.numel() * 4
     torch.cuda.synchronize()
     barrier()
@@ -244,7 +319,9 @@ def run_ours(a):
         dx.copy_(hx, non_blocking=True)
         dt_.copy_(ht, non_blocking=True)
         dn.copy_(hn, non_blocking=True)
-        hj.hj_solve(ctx, dx, dt_, dn, None, q_begin, out)
+        if multi:
+            dp_.copy_(hp, non_blocking=True)
+        hj.hj_solve(ctx, dx, dt_, dn, dp_, q_begin, out)
         hphi.copy_(phi, non_blocking=True)
         hv.copy_(vout, non_blocking=True)
         hst.copy_(status, non_blocking=True)
@@ -254,15 +331,15 @@ def run_ours(a):
     e2e_t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
     if world > 1:
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_val = nq * world / (float(e2e_t.item()) / 1e3)
+    e2e_val = units * world / (float(e2e_t.item()) / 1e3)
     phi_np = hphi.numpy().copy()
     st_np = hst.numpy().copy()
 
     # plain path: Algorithm 1 (cyclic CD) with central differences, same workload
     plain = None
-    if not a.no_plain:
+    if not a.no_plain and a.workload == WORKLOAD:
         solver_cd = W.c3_cd_solver()
-        ctx_cd = hj.hj_create([spec], hj.opts_from_dict(solver_cd, hj.HJ_PREC_FP32, 64), local)
+        ctx_cd = hj.hj_create(wl.problems, hj.opts_from_dict(solver_cd, hj.HJ_PREC_FP32, 64), local)
         phi_cd = torch.empty_like(phi)
         out_cd = (phi_cd, torch.zeros_like(vout), torch.empty_like(status))
         hj.hj_solve(ctx_cd, x, t, ns, None, q_begin, out_cd)  # warm-up
@@ -287,13 +364,13 @@ def run_ours(a):
         cpu = None
         acc = None
         if not a.no_cpu and world == 1:
-            ids = np.arange(0, nq, nq // CPU_SAMPLE)[:CPU_SAMPLE]
+            ids = np.arange(0, nq, max(1, nq // CPU_SAMPLE))[:CPU_SAMPLE]
             sec, ref, threads = _time_oracle(wl, ids)
-            cpu = {"value": CPU_SAMPLE / sec, "unit": "queries/s", "cores": threads, "kind": "oracle",
-                   "sample": f"{CPU_SAMPLE} queries (every {nq // CPU_SAMPLE}th) of the workload, all 16 starts, "
-                             f"FP64, {sec:.1f} s wall"}
+            cpu = {"value": _units(wl, ids) / sec, "unit": _unit(wl), "cores": threads, "kind": "oracle",
+                   "sample": f"{len(ids)} queries (every {max(1, nq // CPU_SAMPLE)}th) of the workload, all their "
+                             f"starts, FP64, {sec:.1f} s wall"}
             err = np.abs(phi_np[ids] - ref["phi"]) / (1 + np.abs(ref["phi"]))
-            acc = {"sample": CPU_SAMPLE, "max_rel_err": float(err.max()),
+            acc = {"sample": len(ids), "max_rel_err": float(err.max()),
                    "frac_within_1e-4": float(np.mean(err <= 1e-4)),
                    "certified_agree": float(np.mean((st_np[ids] & 1) == (ref["status"] & 1)))}
             if plain is not None:
@@ -303,18 +380,12 @@ def run_ours(a):
         if plain is not None:
             plain.pop("phi")
         result = {
-            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": a.steps,
+            "metric": metric, "value": value, "unit": _unit(wl), "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "d": 20, "queries_per_gpu": nq, "guesses": 16, "n_steps": 64, "t": 0.5,
-                       "descent": "gradient descent, discrete-adjoint gradient, per-coordinate step control",
-                       "certificate": "fp64", "max_trials": 20, "l2": "flushed between timed steps (256 MB write)"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                         "frac": achieved / peak_fp32, "traffic": None,
-                         "kernel": "k_desc (persistent descent, adjoint)",
-                         "peak_note": f"FP32 FMA {nsm} SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
-                                      f"({peak_src} max SM clock)"},
-            "e2e": {"value": e2e_val, "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "config": _config(a, wl, descent, nq),
+            "roofline": roof,
+            "e2e": {"value": e2e_val, "unit": _unit(wl), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
             "clocks": clocks,
             "detail": {"descent_ms_per_step": desc_s * 1e3 / len(infos),
@@ -323,7 +394,8 @@ def run_ours(a):
                        "gradients_per_step": info["gradient_evals"], "pairs_per_step": info["n_pairs"],
                        "iterations_per_pair": info["iterations"] / max(1, info["n_pairs"]),
                        "threads_per_pair": info["threads_per_pair"], "comps_per_thread": info["comps_per_thread"],
-                       "algorithmic_tflop_per_step": flops / len(infos) / 1e12,
+                       "algorithmic_tflop_per_step": sum(i["algorithmic_flops"] for i in infos) / len(infos) / 1e12,
+                       "tensor_tflop_per_step": tflops / len(infos) / 1e12,
                        "certified_frac": float(np.mean(st_np & 1))},
             "plain_cd_fd": plain,
             "accuracy_vs_oracle": acc,

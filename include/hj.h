@@ -99,32 +99,6 @@ typedef enum { HJ_PREC_FP32 = 0, HJ_PREC_FP64 = 1 } hj_precision;
 #define HJ_ST_RESEEDED 8   /* at least one failed start was restarted             */
 
 /*
- * One problem: a Hamiltonian family instance and its initial data.
- * params (HOST, double, copied by hj_create) holds, in order:
- *   family block:  SPEED_QUAD, SMOOTH_NONCONVEX: w[d]
- *                  LINEAR_QUAD: A[d*d] (row-major), then B[d*m] (row-major)
- *                  QUAD_ISO: nothing
- *   g block:       HJ_G_QUAD_SHIFT: a[d];  HJ_G_DIAG_QUAD: s[d] (all > 0)
- * n_params must equal the total.  d in [1, 1024]; m in [1, 64] for
- * LINEAR_QUAD (d in [1, 128] there), else ignored.  LINEAR_QUAD computes
- * B B^T once in double precision at hj_create and integrates
- * d gamma/ds = A gamma + (B B^T) p, dp/ds = -A^T p with running cost
- * p^T (B B^T) p / 2 (the same for both principles).
- */
-typedef struct {
-    int d;
-    hj_family family;
-    hj_principle principle;
-    hj_initial g_kind;
-    int m;             /* LINEAR_QUAD: columns of B                             */
-    int n_neg;         /* SMOOTH_NONCONVEX: number of leading negative signs     */
-    double s_eps;      /* SMOOTH_NONCONVEX: smoothing of |q|, > 0                */
-    int n_guesses;     /* random starts per query for hj_solve (0: opts value)   */
-    const double *params;
-    size_t n_params;
-} hj_problem_desc;
-
-/*
  * Solver constants.  Names follow Algorithm 1: step = alpha = 1/L; every
  * `halving_period` iterations alpha is halved (0: never); the descent stops
  * when every move of a full sweep is smaller than `eps` (coordinate descent:
@@ -177,6 +151,39 @@ typedef struct {
     int kahan;
 } hj_solver_opts;
 
+/*
+ * One problem: a Hamiltonian family instance and its initial data.
+ * params (HOST, double, copied by hj_create) holds, in order:
+ *   family block:  SPEED_QUAD, SMOOTH_NONCONVEX: w[d]
+ *                  LINEAR_QUAD: A[d*d] (row-major), then B[d*m] (row-major)
+ *                  QUAD_ISO: nothing
+ *   g block:       HJ_G_QUAD_SHIFT: a[d];  HJ_G_DIAG_QUAD: s[d] (all > 0)
+ * n_params must equal the total.  d in [1, 1024]; m in [1, 64] for
+ * LINEAR_QUAD (d in [1, 128] there), else ignored.  LINEAR_QUAD computes
+ * B B^T once in double precision at hj_create and integrates
+ * d gamma/ds = A gamma + (B B^T) p, dp/ds = -A^T p with running cost
+ * p^T (B B^T) p / 2 (the same for both principles).
+ */
+typedef struct {
+    int d;
+    hj_family family;
+    hj_principle principle;
+    hj_initial g_kind;
+    int m;             /* LINEAR_QUAD: columns of B                             */
+    int n_neg;         /* SMOOTH_NONCONVEX: number of leading negative signs     */
+    double s_eps;      /* SMOOTH_NONCONVEX: smoothing of |q|, > 0                */
+    int n_guesses;     /* random starts per query for hj_solve (0: the solver value) */
+    const double *params;
+    size_t n_params;
+    /* HOST, nullable, copied by hj_create: this problem's descent constants
+     * (grad, fd_h, step, max_iters, halving_period, eps, adapt, grow, shrink,
+     * step_max, n_guesses, max_trials, cert_tol); NULL takes the context's.
+     * precision, quad, kahan, seed, guess_dist, n_steps_default and
+     * max_rounds always come from the context's options. */
+    const hj_solver_opts *solver;
+} hj_problem_desc;
+
+
 /* Counters and device timings of the last hj_solve on a context
  * (hj_last_solve_info); times come from CUDA events on the solve's stream. */
 typedef struct {
@@ -196,6 +203,9 @@ typedef struct {
     double total_ms;            /* device time of the whole hj_solve                 */
     int64_t kernel_launches;    /* kernels the library launched in the last hj_solve */
     double descent_ms_round0;   /* device time of the first round's descent launches */
+    double tensor_flops;        /* tensor-core tile kernel: BF16 flops of its stage products,
+                                   3 x 2 (3 d^2 + d m) per pair and RK4 stage (the fp32
+                                   product, unpadded, times the three BF16x3 terms)       */
 } hj_solve_info;
 
 /*
@@ -279,6 +289,22 @@ hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out);
  * for the resulting components per thread.
  */
 hj_status hj_set_tuning(hj_ctx *ctx, int problem, int tpp, int ck_interval);
+
+/*
+ * hj_autotune -- choose each problem's launch parameters by measurement (the
+ * batching scheme of the solver, not a step of the paper): for every
+ * candidate -- the automatic choice (for a linear-quadratic problem that fits
+ * it, the tensor-core tile kernel) and every threads-per-pair count with a
+ * built kernel -- run hj_solve on the given sample of queries with each
+ * problem's descent capped at `iters` iterations (coordinate descent: iters
+ * sweeps) and no reseeding, time each problem's descent launch with CUDA
+ * events, and keep the fastest (a later candidate must be 3% faster).  The
+ * choice is applied as by hj_set_tuning and, when tpp_out (HOST, int32 [n
+ * problems]) is non-NULL, returned there (0 = automatic).  Synchronous;
+ * allocates and frees temporary outputs; hj_last_solve_info is cleared.
+ */
+hj_status hj_autotune(hj_ctx *ctx, int64_t n_queries, const int32_t *problem_idx, const void *x, const void *t,
+                      const int32_t *n_steps, int iters, int32_t *tpp_out, void *stream);
 
 /*
  * hj_solve_noalloc -- hj_solve that allocates nothing.  The paper has no

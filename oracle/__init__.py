@@ -237,7 +237,8 @@ def default_threads() -> int:
     return max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1))
 
 
-def solve(problems, O: Opts, x, t, N, problem_idx=None, query_ids=None, threads: Optional[int] = None):
+def solve(problems, O: Opts, x, t, N, problem_idx=None, query_ids=None, threads: Optional[int] = None,
+          guesses=None):
     """Solve every query: guesses, descent, certificate, reseed, best-of-guesses.
 
     problems    : one Problem or a list of them
@@ -245,11 +246,24 @@ def solve(problems, O: Opts, x, t, N, problem_idx=None, query_ids=None, threads:
     t, N        : [nq] times and RK4 step counts
     problem_idx : [nq] index into problems (None: all 0)
     query_ids   : [nq] global query index used in the Philox counter (None: 0..nq-1)
-    Returns a dict of arrays: phi, v [nq, ld], status, and per-slot diagnostics.
+    guesses     : per-problem number of initial guesses (None: O.n_guesses for all)
+    O may also be a list with one Opts per problem (each with its own guesses).
+    Returns a dict of arrays: phi, v [nq, ld], status, and per-slot diagnostics
+    ([nq, G] with G the largest guess count; unused slots stay NaN / 0).
     """
     lib = _load()
     probs = problems if isinstance(problems, (list, tuple)) else [problems]
     cprobs = [p.c() for p in probs]
+    olist = list(O) if isinstance(O, (list, tuple)) else [O] * len(probs)
+    if guesses is None:
+        gper = [o.n_guesses for o in olist]
+    else:
+        gper = [int(g) for g in guesses]
+    copts = []
+    for o_, g in zip(olist, gper):
+        o = o_.c()
+        o.n_guesses = g
+        copts.append(o)
     x = _f64(x)
     nq = x.shape[0]
     ld = x.shape[1]
@@ -257,8 +271,7 @@ def solve(problems, O: Opts, x, t, N, problem_idx=None, query_ids=None, threads:
     N = np.broadcast_to(np.asarray(N, dtype=np.int64), (nq,)).copy()
     pidx = np.zeros(nq, dtype=np.int64) if problem_idx is None else np.asarray(problem_idx, dtype=np.int64)
     qids = np.arange(nq, dtype=np.int64) if query_ids is None else np.asarray(query_ids, dtype=np.int64)
-    G = O.n_guesses
-    co = O.c()
+    G = max(gper)
     phi = np.full(nq, np.nan)
     vout = np.full((nq, ld), np.nan)
     status = np.zeros(nq, dtype=np.int32)
@@ -273,20 +286,21 @@ def solve(problems, O: Opts, x, t, N, problem_idx=None, query_ids=None, threads:
     def one(q):
         P = probs[pidx[q]]
         d = P.d
+        g = gper[pidx[q]]
         xq = np.ascontiguousarray(x[q, :d])
         ph = C.c_double(0.0)
         vs = np.zeros(d)
-        f, r_ = np.zeros(G), np.zeros(G)
-        pa, it, rd = np.zeros(G, dtype=np.int32), np.zeros(G, dtype=np.int32), np.zeros(G, dtype=np.int32)
-        sv = np.zeros(G * d)
-        st = lib.orc_solve_query(C.byref(cprobs[pidx[q]]), C.byref(co), int(qids[q]), _dp(xq), float(t[q]),
-                                 int(N[q]), C.byref(ph), _dp(vs), _dp(f), _dp(r_), pa.ctypes.data_as(_IP),
-                                 it.ctypes.data_as(_IP), rd.ctypes.data_as(_IP), _dp(sv))
+        f, r_ = np.zeros(g), np.zeros(g)
+        pa, it, rd = np.zeros(g, dtype=np.int32), np.zeros(g, dtype=np.int32), np.zeros(g, dtype=np.int32)
+        sv = np.zeros(g * d)
+        st = lib.orc_solve_query(C.byref(cprobs[pidx[q]]), C.byref(copts[pidx[q]]), int(qids[q]), _dp(xq),
+                                 float(t[q]), int(N[q]), C.byref(ph), _dp(vs), _dp(f), _dp(r_),
+                                 pa.ctypes.data_as(_IP), it.ctypes.data_as(_IP), rd.ctypes.data_as(_IP), _dp(sv))
         phi[q] = ph.value
         vout[q, :d] = vs
         status[q] = st
-        sF[q], sR[q], sP[q], sI[q], sRd[q] = f, r_, pa, it, rd
-        sV[q, :, :d] = sv.reshape(G, d)
+        sF[q, :g], sR[q, :g], sP[q, :g], sI[q, :g], sRd[q, :g] = f, r_, pa, it, rd
+        sV[q, :g, :d] = sv.reshape(g, d)
 
     nthreads = threads or default_threads()
     if nthreads <= 1 or nq == 1:

@@ -178,10 +178,11 @@ struct hj_ctx {
     int device = 0, nsm = 0, np = 0, ld = 0, prec = 0, gmax = 1;
     hj_solver_opts opts{};
     std::vector<hj_problem_desc> desc;
+    std::vector<hj_solver_opts> popts;  // per-problem descent constants (context-wide fields overridden)
     std::vector<std::vector<double>> params;
     std::vector<DevProblem> dev;
     std::vector<int> tpp_override, ck_interval;
-    int32_t *d_pg = nullptr, *d_pd = nullptr, *d_pprin = nullptr;
+    int32_t *d_pg = nullptr, *d_pd = nullptr, *d_pprin = nullptr, *d_ptrials = nullptr;
     // scratch
     long long cap_q = 0, cap_p = 0;
     int32_t *starts = nullptr, *pair_base = nullptr, *block_sums = nullptr, *trials = nullptr, *qflags = nullptr,
@@ -201,8 +202,18 @@ struct hj_ctx {
     cudaStream_t last_stream = nullptr;
     long long last_nq = 0;
     int last_tpp = 0, last_c = 0;
+    std::vector<char> last_tc;  // problem ran on the tensor-core tile kernel in the last solve
     bool timing = true;
     std::vector<cudaEvent_t> ev_desc, ev_cert;
+    // concurrent per-problem descent launches (several problems): auxiliary
+    // streams forked from and joined back into the caller's stream
+    bool concurrent = true;
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> ev_join;
+    cudaEvent_t ev_fork = nullptr;
+    // per-problem descent timing of round 0 (autotuner)
+    bool pp_timing = false;
+    std::vector<cudaEvent_t> pp_ev;
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
     int n_desc_ev = 0, n_cert_ev = 0;
     long long launches = 0;
@@ -519,13 +530,24 @@ hj_status hj_create(const hj_problem_desc *problems, int n_problems, const hj_so
     if (!problems || n_problems < 1 || !opts || !out)
         return fail(nullptr, HJ_EINVAL, "hj_create: problems, opts and out must be non-NULL, n_problems >= 1");
     if (n_problems > 4096) return fail(nullptr, HJ_EINVAL, "hj_create: at most 4096 problems");
-    for (int i = 0; i < n_problems; ++i) {
-        hj_status s = validate_problem(nullptr, problems[i], i);
-        if (s != HJ_OK) return s;
-    }
     {
         hj_status s = validate_opts(nullptr, *opts);
         if (s != HJ_OK) return s;
+    }
+    for (int i = 0; i < n_problems; ++i) {
+        hj_status s = validate_problem(nullptr, problems[i], i);
+        if (s != HJ_OK) return s;
+        if (problems[i].solver) {
+            hj_solver_opts o = *problems[i].solver;
+            o.precision = opts->precision;
+            o.n_steps_default = opts->n_steps_default;
+            o.quad = opts->quad;
+            s = validate_opts(nullptr, o);
+            if (s != HJ_OK) {
+                g_create_error = "problem " + std::to_string(i) + " solver: " + g_create_error;
+                return s;
+            }
+        }
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)
@@ -539,6 +561,7 @@ hj_status hj_create(const hj_problem_desc *problems, int n_problems, const hj_so
     ctx->opts = *opts;
     ctx->prec = opts->precision == HJ_PREC_FP64 ? 1 : 0;
     ctx->desc.assign(problems, problems + n_problems);
+    ctx->popts.resize(n_problems);
     ctx->params.resize(n_problems);
     ctx->dev.resize(n_problems);
     ctx->tpp_override.assign(n_problems, 0);
@@ -546,7 +569,17 @@ hj_status hj_create(const hj_problem_desc *problems, int n_problems, const hj_so
     for (int i = 0; i < n_problems; ++i) {
         ctx->params[i].assign(problems[i].params, problems[i].params + problems[i].n_params);
         ctx->desc[i].params = ctx->params[i].data();
-        if (ctx->desc[i].n_guesses == 0) ctx->desc[i].n_guesses = opts->n_guesses;
+        hj_solver_opts &po = ctx->popts[i];
+        po = problems[i].solver ? *problems[i].solver : *opts;
+        po.precision = opts->precision;
+        po.quad = opts->quad;
+        po.kahan = opts->kahan;
+        po.seed = opts->seed;
+        po.guess_dist = opts->guess_dist;
+        po.n_steps_default = opts->n_steps_default;
+        po.max_rounds = opts->max_rounds;
+        ctx->desc[i].solver = nullptr;
+        if (ctx->desc[i].n_guesses == 0) ctx->desc[i].n_guesses = po.n_guesses;
         ctx->ld = std::max(ctx->ld, problems[i].d);
         ctx->gmax = std::max(ctx->gmax, ctx->desc[i].n_guesses);
     }
@@ -565,7 +598,7 @@ hj_status hj_create(const hj_problem_desc *problems, int n_problems, const hj_so
     } while (0)
     CUC(cudaSetDevice(cuda_device));
     CUC(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, cuda_device));
-    std::vector<int32_t> pg(n_problems), pd(n_problems), pprin(n_problems);
+    std::vector<int32_t> pg(n_problems), pd(n_problems), pprin(n_problems), ptr(n_problems);
     for (int i = 0; i < n_problems; ++i) {
         const hj_problem_desc &D = ctx->desc[i];
         std::vector<float> hf;
@@ -596,9 +629,10 @@ hj_status hj_create(const hj_problem_desc *problems, int n_problems, const hj_so
         pg[i] = D.n_guesses;
         pd[i] = D.d;
         pprin[i] = D.principle;
+        ptr[i] = ctx->popts[i].max_trials;
         int tpp, c;
         if (!choose(ctx, i, K_EVAL, &tpp, &c) || !choose(ctx, i, K_CERT, &tpp, &c) ||
-            !choose(ctx, i, desc_kind(opts->grad), &tpp, &c)) {
+            !choose(ctx, i, desc_kind(ctx->popts[i].grad), &tpp, &c)) {
             fail(ctx, HJ_EUNSUPPORTED, "problem %d: no kernel built for d=%d in this precision", i, D.d);
             return bail(HJ_EUNSUPPORTED);
         }
@@ -609,6 +643,8 @@ hj_status hj_create(const hj_problem_desc *problems, int n_problems, const hj_so
     CUC(cudaMemcpy(ctx->d_pg, pg.data(), sizeof(int32_t) * n_problems, cudaMemcpyHostToDevice));
     CUC(cudaMemcpy(ctx->d_pd, pd.data(), sizeof(int32_t) * n_problems, cudaMemcpyHostToDevice));
     CUC(cudaMemcpy(ctx->d_pprin, pprin.data(), sizeof(int32_t) * n_problems, cudaMemcpyHostToDevice));
+    CUC(cudaMalloc(&ctx->d_ptrials, sizeof(int32_t) * n_problems));
+    CUC(cudaMemcpy(ctx->d_ptrials, ptr.data(), sizeof(int32_t) * n_problems, cudaMemcpyHostToDevice));
     CUC(cudaMalloc(&ctx->pcount, sizeof(int32_t) * n_problems));
     CUC(cudaMalloc(&ctx->seg_begin, sizeof(int32_t) * (n_problems + 1)));
     CUC(cudaMalloc(&ctx->wl_count, sizeof(int32_t) * n_problems));
@@ -641,11 +677,15 @@ hj_status hj_destroy(hj_ctx *ctx)
     cudaFree(ctx->tc_vec);
     cudaFree(ctx->tc_ybuf);
     cudaFree(ctx->tc_err);
-    void *ptrs[] = {ctx->d_pg, ctx->d_pd, ctx->d_pprin, ctx->starts, ctx->pair_base, ctx->block_sums, ctx->trials,
+    void *ptrs[] = {ctx->d_pg, ctx->d_pd, ctx->d_pprin, ctx->d_ptrials, ctx->starts, ctx->pair_base, ctx->block_sums, ctx->trials,
                     ctx->qflags, ctx->pair_q, ctx->pair_slot, ctx->pair_round, ctx->iters, ctx->wl, ctx->flags,
                     ctx->pP, ctx->pF, ctx->pR, ctx->vfin, ctx->pcount, ctx->seg_begin, ctx->wl_count, ctx->cursor,
                     ctx->stats, ctx->amb_wl, ctx->amb_count, ctx->best_pid};
     for (void *p : ptrs) cudaFree(p);
+    for (auto a : ctx->aux) cudaStreamDestroy(a);
+    for (auto e : ctx->ev_join) cudaEventDestroy(e);
+    for (auto e : ctx->pp_ev) cudaEventDestroy(e);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     for (auto e : ctx->ev_desc) cudaEventDestroy(e);
     for (auto e : ctx->ev_cert) cudaEventDestroy(e);
     if (ctx->ev_begin) cudaEventDestroy(ctx->ev_begin);
@@ -667,7 +707,7 @@ hj_status hj_set_tuning(hj_ctx *ctx, int problem, int tpp, int ck_interval)
     int old = ctx->tpp_override[problem];
     ctx->tpp_override[problem] = tpp;
     int t, c;
-    const int kind = desc_kind(ctx->opts.grad);
+    const int kind = desc_kind(ctx->popts[problem].grad);
     if (!choose(ctx, problem, kind, &t, &c) || !choose(ctx, problem, K_EVAL, &t, &c) ||
         !choose(ctx, problem, K_GRAD, &t, &c)) {
         ctx->tpp_override[problem] = old;
@@ -765,7 +805,7 @@ hj_status hj_certify(hj_ctx *ctx, int64_t n, const int32_t *problem_idx, const v
             a.F = F;
             a.resid = residual_out;
             a.pass = pass_out;
-            a.tol = ctx->opts.cert_tol;
+            a.tol = ctx->popts[p].cert_tol;
             a.pidx = ctx->np > 1 ? problem_idx : nullptr;
             a.pfilter = p;
             a.quad = ctx->opts.quad;
@@ -799,6 +839,23 @@ hj_status hj_guesses(hj_ctx *ctx, int64_t n, const int64_t *query_id, const int3
     return HJ_OK;
 }
 
+// Auxiliary streams of the concurrent descent launches (created once).
+static hj_status ensure_aux(hj_ctx *ctx)
+{
+    const int want = std::min(ctx->np, 4);
+    if ((int)ctx->aux.size() >= want) return HJ_OK;
+    if (!ctx->ev_fork) CU(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    while ((int)ctx->aux.size() < want) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        ctx->aux.push_back(st);
+        ctx->ev_join.push_back(ev);
+    }
+    return HJ_OK;
+}
+
 static hj_status record(hj_ctx *ctx, std::vector<cudaEvent_t> &pool, int idx, cudaStream_t s)
 {
     while ((int)pool.size() <= idx) {
@@ -828,25 +885,28 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
     hj_status st = ensure_scratch(ctx, n_queries, npairs);
     if (st != HJ_OK) return st;
     const int32_t *pidx = ctx->np > 1 ? problem_idx : nullptr;
-    const int kind = desc_kind(ctx->opts.grad);
+    std::vector<int> kinds(ctx->np);
+    for (int p = 0; p < ctx->np; ++p) kinds[p] = desc_kind(ctx->popts[p].grad);
     for (int p = 0; p < ctx->np; ++p)
-        if (tc_eligible(ctx, p) && kind != K_CD) {
+        if (tc_eligible(ctx, p) && kinds[p] != K_CD) {
             st = ensure_tc_scratch(ctx, p);
             if (st != HJ_OK) return st;
         }
     // choose kernels up front so nothing is enqueued on failure
     std::vector<int> tpp_d(ctx->np), c_d(ctx->np), tpp_c(ctx->np), c_c(ctx->np);
     for (int p = 0; p < ctx->np; ++p)
-        if (!choose(ctx, p, kind, &tpp_d[p], &c_d[p]) || !choose(ctx, p, K_CERT, &tpp_c[p], &c_c[p]))
+        if (!choose(ctx, p, kinds[p], &tpp_d[p], &c_d[p]) || !choose(ctx, p, K_CERT, &tpp_c[p], &c_c[p]))
             return fail(ctx, HJ_EUNSUPPORTED, "no kernel for problem %d", p);
     ctx->last_stream = s;
     ctx->last_nq = n_queries;
     ctx->last_tpp = tpp_d[0];
     ctx->last_c = c_d[0];
-    if (tc_eligible(ctx, 0) && kind != K_CD) {
+    if (tc_eligible(ctx, 0) && kinds[0] != K_CD) {
         ctx->last_tpp = 1;  // one thread (and TMEM lane) per pair
         ctx->last_c = ctx->dev[0].geom.dp;
     }
+    ctx->last_tc.assign(ctx->np, 0);
+    for (int p = 0; p < ctx->np; ++p) ctx->last_tc[p] = (tc_eligible(ctx, p) && kinds[p] != K_CD) ? 1 : 0;
     ctx->n_desc_ev = ctx->n_cert_ev = 0;
     CU(cudaEventRecord(ctx->ev_begin, s));
     CU(cudaMemsetAsync(ctx->stats, 0, sizeof(unsigned long long) * 8 * ctx->np, s));
@@ -855,13 +915,40 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
     CU(launch_scan(n_queries, ctx->starts, ctx->pair_base, ctx->block_sums, s));
     CU(launch_build_pairs(n_queries, pidx, ctx->d_pg, ctx->pair_base, ctx->pair_q, ctx->pair_slot, ctx->pair_round,
                           ctx->trials, ctx->qflags, ctx->seg_begin, ctx->wl_count, ctx->wl, s));
-    const SolverDev S = solver_dev(ctx->opts);
+    // Several problems: each round's descent launches go to auxiliary streams
+    // (tensor-core problems share the first, the lane-group ones take the
+    // others in turn) so that their tails overlap and the tensor-core tile
+    // kernel runs beside the FP32 kernels; the caller's stream joins them.
+    const bool conc = ctx->concurrent && ctx->np > 1 && !ctx->pp_timing;
+    if (conc) {
+        st = ensure_aux(ctx);
+        if (st != HJ_OK) return st;
+    }
+    auto stream_of = [&](int p) -> cudaStream_t {
+        if (!conc) return s;
+        const int na = (int)ctx->aux.size();
+        if (ctx->last_tc[p] || na == 1) return ctx->aux[0];
+        return ctx->aux[1 + p % (na - 1)];
+    };
+    if (ctx->pp_timing)
+        while ((int)ctx->pp_ev.size() < 2 * ctx->np) {
+            cudaEvent_t e;
+            CU(cudaEventCreate(&e));
+            ctx->pp_ev.push_back(e);
+        }
     for (int round = 0; round <= ctx->opts.max_rounds; ++round) {
         CU(cudaMemsetAsync(ctx->cursor, 0, sizeof(int32_t) * ctx->np, s));
         CU(cudaMemsetAsync(ctx->amb_count, 0, sizeof(int32_t) * ctx->np, s));
         if (ctx->timing) { st = record(ctx, ctx->ev_desc, ctx->n_desc_ev++, s); if (st != HJ_OK) return st; }
+        if (conc) {
+            CU(cudaEventRecord(ctx->ev_fork, s));
+            for (cudaStream_t a : ctx->aux) CU(cudaStreamWaitEvent(a, ctx->ev_fork, 0));
+        }
         for (int p = 0; p < ctx->np; ++p) {
             const KSet &k = kset(ctx, p, c_d[p]);
+            const int kind = kinds[p];
+            const cudaStream_t sp = stream_of(p);
+            if (ctx->pp_timing && round == 0) CU(cudaEventRecord(ctx->pp_ev[2 * p], s));
             Launch L = kind == K_GD ? k.gd : kind == K_CG ? k.cg : k.cd;
             const void *fn = kind == K_GD ? k.f_gd : kind == K_CG ? k.f_cg : k.f_cd;
             auto fill = [&](auto &a) {
@@ -869,7 +956,7 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                 a.problem = p;
                 a.nsteps = n_steps;
                 a.q_begin = q_begin;
-                a.S = S;
+                a.S = solver_dev(ctx->popts[p]);
                 a.S.ck_interval = ctx->ck_interval[p];
                 a.wl = ctx->wl;
                 a.seg_begin = ctx->seg_begin;
@@ -886,14 +973,14 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                 a.pP = ctx->pP;
                 a.amb_wl = ctx->amb_wl;
                 a.amb_count = ctx->amb_count;
-                a.tol = ctx->opts.cert_tol;
+                a.tol = ctx->popts[p].cert_tol;
             };
             if (ctx->prec) {
                 DescArgs<double> a{};
                 fill(a);
                 a.P = ctx->dev[p].pd;
                 a.x = (const double *)x; a.t = (const double *)t; a.vfin = (double *)ctx->vfin;
-                CU(L(&a, persistent_grid(ctx, fn), s));
+                CU(L(&a, persistent_grid(ctx, fn), sp));
             } else if (tc_eligible(ctx, p) && kind != K_CD) {
                 // tensor-core tile kernel: 128 pairs per CTA, one CTA per SM
                 LqTcArgs a = tc_args(ctx, p);
@@ -902,16 +989,22 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                 a.D.x = (const float *)x; a.D.t = (const float *)t; a.D.vfin = (float *)ctx->vfin;
                 a.x = (const float *)x; a.t = (const float *)t; a.nsteps = n_steps;
                 a.mode_desc = (kind == K_CG) ? DESC_CG : DESC_GD;
-                CU(lq_tc_launch(LQ_DESC, a, ctx->nsm, tc_smem(ctx, p), s));
+                CU(lq_tc_launch(LQ_DESC, a, ctx->nsm, tc_smem(ctx, p), sp));
             } else {
                 DescArgs<float> a{};
                 fill(a);
                 a.P = ctx->dev[p].pf;
                 a.x = (const float *)x; a.t = (const float *)t; a.vfin = (float *)ctx->vfin;
-                CU(L(&a, persistent_grid(ctx, fn), s));
+                CU(L(&a, persistent_grid(ctx, fn), sp));
             }
+            if (ctx->pp_timing && round == 0) CU(cudaEventRecord(ctx->pp_ev[2 * p + 1], s));
             ctx->launches++;
         }
+        if (conc)
+            for (size_t i = 0; i < ctx->aux.size(); ++i) {
+                CU(cudaEventRecord(ctx->ev_join[i], ctx->aux[i]));
+                CU(cudaStreamWaitEvent(s, ctx->ev_join[i], 0));
+            }
         if (ctx->timing) { st = record(ctx, ctx->ev_desc, ctx->n_desc_ev++, s); if (st != HJ_OK) return st; }
         for (int p = 0; p < ctx->np; ++p) {
             const KSet &k = kset(ctx, p, c_c[p]);
@@ -923,7 +1016,7 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                 a.F = ctx->pF;
                 a.resid = ctx->pR;
                 a.pass = ctx->pP;
-                a.tol = ctx->opts.cert_tol;
+                a.tol = ctx->popts[p].cert_tol;
                 a.quad = ctx->opts.quad;
                 a.wl = ctx->amb_wl;
                 a.seg_begin = ctx->seg_begin;
@@ -967,7 +1060,7 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
         a.qflags = ctx->qflags;
         a.round = round;
         a.schedule = schedule;
-        a.max_trials = ctx->opts.max_trials;
+        a.ptrials = ctx->d_ptrials;
         a.seg_begin = ctx->seg_begin;
         a.wl_count = ctx->wl_count;
         a.wl = ctx->wl;
@@ -1036,6 +1129,10 @@ hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out)
         out->n_pairs += (int64_t)c[5];
         out->algorithmic_flops += (double)c[3] * fm.fwd_step + (double)c[4] * fm.adj_step;
         out->certify_flops += (double)c[7] * fm.fwd_step;
+        if (p < (int)ctx->last_tc.size() && ctx->last_tc[p]) {
+            const double d = D.d, m = D.m;
+            out->tensor_flops += (double)(c[3] + c[4] + c[7]) * 4.0 * 3.0 * 2.0 * (3.0 * d * d + d * m);
+        }
     }
     out->threads_per_pair = ctx->last_tpp;
     out->comps_per_thread = ctx->last_c;
@@ -1063,6 +1160,88 @@ hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out)
     out->certify_ms = cert_ms;
     out->descent_launches = ctx->n_desc_ev / 2;
     out->kernel_launches = ctx->launches;
+    return HJ_OK;
+}
+
+hj_status hj_autotune(hj_ctx *ctx, int64_t n_queries, const int32_t *problem_idx, const void *x, const void *t,
+                      const int32_t *n_steps, int iters, int32_t *tpp_out, void *stream)
+{
+    if (!ctx) return HJ_EINVAL;
+    if (n_queries < 1) return fail(ctx, HJ_EINVAL, "hj_autotune needs at least one query");
+    if (iters < 1) return fail(ctx, HJ_EINVAL, "iters must be >= 1");
+    if (!x || !t) return fail(ctx, HJ_EINVAL, "x and t must be non-NULL");
+    if (ctx->np > 1 && !problem_idx) return fail(ctx, HJ_EINVAL, "problem_idx is required with several problems");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(ctx->device));
+    // candidates: the automatic choice first, then every lane count with a kernel
+    std::vector<std::vector<int>> cand(ctx->np);
+    size_t maxc = 0;
+    const std::vector<int> saved_tpp = ctx->tpp_override;
+    for (int p = 0; p < ctx->np; ++p) {
+        const int kind = desc_kind(ctx->popts[p].grad);
+        cand[p].push_back(0);
+        for (int tp = 1; tp <= 32; tp <<= 1) {
+            ctx->tpp_override[p] = tp;
+            int a_, c_;
+            if (choose(ctx, p, kind, &a_, &c_)) cand[p].push_back(tp);
+        }
+        ctx->tpp_override[p] = saved_tpp[p];
+        maxc = std::max(maxc, cand[p].size());
+    }
+    double *phi = nullptr;
+    void *v = nullptr;
+    int32_t *status = nullptr;
+    const size_t es = ctx->prec ? sizeof(double) : sizeof(float);
+    CU(cudaMalloc(&phi, sizeof(double) * n_queries));
+    CU(cudaMalloc(&v, es * n_queries * ctx->ld));
+    CU(cudaMalloc(&status, sizeof(int32_t) * n_queries));
+    const std::vector<hj_solver_opts> saved_popts = ctx->popts;
+    const int saved_rounds = ctx->opts.max_rounds;
+    for (int p = 0; p < ctx->np; ++p)
+        ctx->popts[p].max_iters =
+            (desc_kind(ctx->popts[p].grad) == K_CD) ? iters * ctx->desc[p].d : iters;  // CD counts coordinate moves
+    ctx->opts.max_rounds = 0;
+    ctx->pp_timing = true;
+    std::vector<double> best_ms(ctx->np, 1e300);
+    std::vector<int> best(ctx->np, 0);
+    hj_status st = HJ_OK;
+    for (size_t c = 0; c <= maxc && st == HJ_OK; ++c) {
+        // pass 0 warms up (module load, attributes) with the automatic choice
+        const size_t ci = c == 0 ? 0 : c - 1;
+        for (int p = 0; p < ctx->np; ++p) ctx->tpp_override[p] = cand[p][std::min(ci, cand[p].size() - 1)];
+        st = hj_solve(ctx, 0, n_queries, problem_idx, x, t, n_steps, phi, v, status, stream);
+        if (st != HJ_OK) break;
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            st = fail(ctx, HJ_ECUDA, "hj_autotune: solve failed");
+            break;
+        }
+        if (c == 0) continue;
+        for (int p = 0; p < ctx->np; ++p) {
+            if (ci >= cand[p].size()) continue;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, ctx->pp_ev[2 * p], ctx->pp_ev[2 * p + 1]);
+            // a later candidate must beat the earlier ones by 3% (ties keep the automatic choice)
+            if (ms < best_ms[p] * 0.97) {
+                best_ms[p] = ms;
+                best[p] = cand[p][ci];
+            }
+        }
+    }
+    ctx->pp_timing = false;
+    ctx->opts.max_rounds = saved_rounds;
+    ctx->popts = saved_popts;
+    ctx->last_nq = 0;
+    cudaFree(phi);
+    cudaFree(v);
+    cudaFree(status);
+    if (st != HJ_OK) {
+        ctx->tpp_override = saved_tpp;
+        return st;
+    }
+    for (int p = 0; p < ctx->np; ++p) {
+        ctx->tpp_override[p] = best[p];
+        if (tpp_out) tpp_out[p] = best[p];
+    }
     return HJ_OK;
 }
 
@@ -1172,10 +1351,11 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
     }
     noalloc_layout(g_noalloc_ptr[ctx->device], ctx->np, n_queries, npairs, ctx->ld, es, &L);
     const int32_t *pidx = ctx->np > 1 ? problem_idx : nullptr;
-    const int kind = desc_kind(ctx->opts.grad);
+    std::vector<int> kinds(ctx->np);
+    for (int p = 0; p < ctx->np; ++p) kinds[p] = desc_kind(ctx->popts[p].grad);
     std::vector<int> tpp_d(ctx->np), c_d(ctx->np), tpp_c(ctx->np), c_c(ctx->np);
     for (int p = 0; p < ctx->np; ++p)
-        if (!choose(ctx, p, kind, &tpp_d[p], &c_d[p]) || !choose(ctx, p, K_CERT, &tpp_c[p], &c_c[p]))
+        if (!choose(ctx, p, kinds[p], &tpp_d[p], &c_d[p]) || !choose(ctx, p, K_CERT, &tpp_c[p], &c_c[p]))
             return fail(ctx, HJ_EUNSUPPORTED, "no kernel for problem %d", p);
     // Every array read below is written earlier in this call; only the
     // per-problem counters must start at zero, and they are cleared here.
@@ -1183,12 +1363,12 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
     CU(launch_scan(n_queries, L.starts, L.pair_base, L.block_sums, s));
     CU(launch_build_pairs(n_queries, pidx, ctx->d_pg, L.pair_base, L.pair_q, L.pair_slot, L.pair_round, L.trials,
                           L.qflags, L.seg_begin, L.wl_count, L.wl, s));
-    const SolverDev S = solver_dev(ctx->opts);
     for (int round = 0; round <= ctx->opts.max_rounds; ++round) {
         CU(cudaMemsetAsync(L.cursor, 0, sizeof(int32_t) * ctx->np, s));
         CU(cudaMemsetAsync(L.amb_count, 0, sizeof(int32_t) * ctx->np, s));
         for (int p = 0; p < ctx->np; ++p) {
             const KSet &k = kset(ctx, p, c_d[p]);
+            const int kind = kinds[p];
             Launch Lk = kind == K_GD ? k.gd : kind == K_CG ? k.cg : k.cd;
             const void *fn = kind == K_GD ? k.f_gd : kind == K_CG ? k.f_cg : k.f_cd;
             auto fill = [&](auto &a) {
@@ -1196,7 +1376,7 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
                 a.problem = p;
                 a.nsteps = n_steps;
                 a.q_begin = q_begin;
-                a.S = S;
+                a.S = solver_dev(ctx->popts[p]);
                 a.S.ck_interval = ctx->ck_interval[p];
                 a.wl = L.wl;
                 a.seg_begin = L.seg_begin;
@@ -1213,7 +1393,7 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
                 a.pP = L.pP;
                 a.amb_wl = L.amb_wl;
                 a.amb_count = L.amb_count;
-                a.tol = ctx->opts.cert_tol;
+                a.tol = ctx->popts[p].cert_tol;
             };
             if (ctx->prec) {
                 DescArgs<double> a{};
@@ -1239,7 +1419,7 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
                 a.F = L.pF;
                 a.resid = L.pR;
                 a.pass = L.pP;
-                a.tol = ctx->opts.cert_tol;
+                a.tol = ctx->popts[p].cert_tol;
                 a.quad = ctx->opts.quad;
                 a.wl = L.amb_wl;
                 a.seg_begin = L.seg_begin;
@@ -1279,7 +1459,7 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
         a.qflags = L.qflags;
         a.round = round;
         a.schedule = schedule;
-        a.max_trials = ctx->opts.max_trials;
+        a.ptrials = ctx->d_ptrials;
         a.seg_begin = L.seg_begin;
         a.wl_count = L.wl_count;
         a.wl = L.wl;

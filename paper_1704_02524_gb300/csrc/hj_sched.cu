@@ -95,14 +95,14 @@ __global__ void k_build_pairs(long long nq, const int32_t *pidx, const int32_t *
 }
 
 // Best of the starts of each query, then the reseed decisions for the next
-// round: failed slots, in slot order, while fewer than max_trials starts of
-// the query have run.  phi = F (Lax) or -G (Hopf) at the chosen start (the
+// round: failed slots, in slot order, while fewer than the problem's trial
+// budget (ptrials) of starts of the query have run.  phi = F (Lax) or -G (Hopf) at the chosen start (the
 // FP64 value replaces it after the last round); best_pid records the start.
 template <typename T>
 __global__ void k_select(long long nq, const int32_t *pidx, const int32_t *pg, const int32_t *pd,
                          const int32_t *pprin, int ld, const int32_t *pair_base, const double *pF,
                          const uint8_t *pP, const uint8_t *flags, const T *vfin, int32_t *pair_round,
-                         int32_t *trials, int32_t *qflags, int round, int schedule, int max_trials,
+                         int32_t *trials, int32_t *qflags, int round, int schedule, const int32_t *ptrials,
                          const int32_t *seg_begin, int32_t *wl_count, int32_t *wl, double *phi, T *v_out,
                          int32_t *status, int32_t *best_pid)
 {
@@ -138,6 +138,7 @@ __global__ void k_select(long long nq, const int32_t *pidx, const int32_t *pg, c
         }
         if (schedule) {
             int tr = trials[q];
+            const int max_trials = ptrials[p];
             for (int s = 0; s < G && tr < max_trials; ++s) {
                 const int pid = base + s;
                 if (pP[pid]) continue;
@@ -214,7 +215,7 @@ cudaError_t launch_select_t(const SelectArgs &a, cudaStream_t s)
 {
     k_select<T><<<grid_for(a.nq, 128), 128, 0, s>>>(
         a.nq, a.pidx, a.pg, a.pd, a.pprin, a.ld, a.pair_base, a.pF, a.pP, a.flags, (const T *)a.vfin, a.pair_round,
-        a.trials, a.qflags, a.round, a.schedule, a.max_trials, a.seg_begin, a.wl_count, a.wl, a.phi, (T *)a.v_out,
+        a.trials, a.qflags, a.round, a.schedule, a.ptrials, a.seg_begin, a.wl_count, a.wl, a.phi, (T *)a.v_out,
         a.status, a.best_pid);
     return cudaGetLastError();
 }

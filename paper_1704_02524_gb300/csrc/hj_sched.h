@@ -15,7 +15,8 @@ struct SelectArgs {
     const uint8_t *pP, *flags;
     const void *vfin;
     int32_t *pair_round, *trials, *qflags;
-    int round, schedule, max_trials;
+    int round, schedule;
+    const int32_t *ptrials;  // per-problem trial budget
     const int32_t *seg_begin;
     int32_t *wl_count, *wl;
     double *phi;

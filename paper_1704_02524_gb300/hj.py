@@ -32,13 +32,7 @@ HJ_PREC_FP32, HJ_PREC_FP64 = 0, 1
 HJ_ST_CERTIFIED, HJ_ST_MAX_ITERS, HJ_ST_NONFINITE, HJ_ST_RESEEDED = 1, 2, 4, 8
 
 EXPORTED = ("hj_create", "hj_destroy", "hj_eval_functional", "hj_grad", "hj_certify", "hj_solve", "hj_guesses",
-            "hj_last_solve_info", "hj_set_tuning", "hj_last_error", "hj_solve_noalloc")
-
-
-class hj_problem_desc(C.Structure):
-    _fields_ = [("d", C.c_int), ("family", C.c_int), ("principle", C.c_int), ("g_kind", C.c_int), ("m", C.c_int),
-                ("n_neg", C.c_int), ("s_eps", C.c_double), ("n_guesses", C.c_int),
-                ("params", C.POINTER(C.c_double)), ("n_params", C.c_size_t)]
+            "hj_last_solve_info", "hj_set_tuning", "hj_last_error", "hj_solve_noalloc", "hj_autotune")
 
 
 class hj_solver_opts(C.Structure):
@@ -49,13 +43,20 @@ class hj_solver_opts(C.Structure):
                 ("guess_dist", C.c_int), ("cert_tol", C.c_double), ("precision", C.c_int), ("kahan", C.c_int)]
 
 
+class hj_problem_desc(C.Structure):
+    _fields_ = [("d", C.c_int), ("family", C.c_int), ("principle", C.c_int), ("g_kind", C.c_int), ("m", C.c_int),
+                ("n_neg", C.c_int), ("s_eps", C.c_double), ("n_guesses", C.c_int),
+                ("params", C.POINTER(C.c_double)), ("n_params", C.c_size_t),
+                ("solver", C.POINTER(hj_solver_opts))]
+
+
 class hj_solve_info(C.Structure):
     _fields_ = [("n_queries", C.c_int64), ("n_pairs", C.c_int64), ("iterations", C.c_int64),
                 ("functional_evals", C.c_int64), ("gradient_evals", C.c_int64), ("rk4_steps", C.c_int64),
                 ("algorithmic_flops", C.c_double), ("certify_flops", C.c_double), ("threads_per_pair", C.c_int),
                 ("comps_per_thread", C.c_int), ("descent_launches", C.c_int), ("descent_ms", C.c_double),
                 ("certify_ms", C.c_double), ("total_ms", C.c_double), ("kernel_launches", C.c_int64),
-                ("descent_ms_round0", C.c_double)]
+                ("descent_ms_round0", C.c_double), ("tensor_flops", C.c_double)]
 
 
 _lib = None
@@ -82,6 +83,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.hj_guesses.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
     lib.hj_last_solve_info.argtypes = [vp, C.POINTER(hj_solve_info)]
     lib.hj_set_tuning.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+    lib.hj_autotune.argtypes = [vp, i64, vp, vp, vp, vp, C.c_int, i32p, vp]
     lib.hj_last_error.argtypes = [vp]
     lib.hj_last_error.restype = C.c_char_p
     for name in EXPORTED:
@@ -163,16 +165,24 @@ def opts_from_dict(solver: Dict, precision: int = HJ_PREC_FP32, n_steps_default:
 
 def hj_create(problems: Sequence, opts: hj_solver_opts, device: int = 0) -> Context:
     """problems: objects with d, family, principle, g_kind, m, n_neg, s_eps,
-    n_guesses and params() (the flat parameter vector of include/hj.h)."""
+    n_guesses and params() (the flat parameter vector of include/hj.h), and
+    optionally `solver` (a dict as for opts_from_dict: that problem's own
+    descent constants)."""
     lib = load_library()
     arr = (hj_problem_desc * len(problems))()
-    keep: List[np.ndarray] = []
+    keep: List = []
     for i, p in enumerate(problems):
         par = np.ascontiguousarray(np.asarray(p.params(), dtype=np.float64))
         keep.append(par)
+        sol = getattr(p, "solver", None)
+        sp = None
+        if sol is not None:
+            so = opts_from_dict(sol, opts.precision, opts.n_steps_default, opts.kahan)
+            keep.append(so)
+            sp = C.pointer(so)
         arr[i] = hj_problem_desc(p.d, p.family, p.principle, p.g_kind, getattr(p, "m", 0), getattr(p, "n_neg", 0),
                                  getattr(p, "s_eps", 1e-6), getattr(p, "n_guesses", 0),
-                                 par.ctypes.data_as(C.POINTER(C.c_double)), par.size)
+                                 par.ctypes.data_as(C.POINTER(C.c_double)), par.size, sp)
     h = C.c_void_p()
     st = lib.hj_create(arr, len(problems), C.byref(opts), device, C.byref(h))
     _check(None, st)
@@ -279,6 +289,19 @@ def hj_last_solve_info(ctx: Context) -> Dict:
 
 def hj_set_tuning(ctx: Context, problem: int, tpp: int = 0, ck_interval: int = 0):
     _check(ctx, load_library().hj_set_tuning(ctx.handle, problem, tpp, ck_interval))
+
+
+def hj_autotune(ctx: Context, x: torch.Tensor, t: torch.Tensor, n_steps: Optional[torch.Tensor] = None,
+                problem_idx: Optional[torch.Tensor] = None, iters: int = 4) -> List[int]:
+    """Times the launch candidates of every problem on the sample (x, t, ...)
+    and applies the fastest; returns the chosen threads per pair (0 = automatic)."""
+    n = x.shape[0]
+    _dev(ctx, x, "x", ctx.dtype, (n, ctx.ld)); _dev(ctx, t, "t", ctx.dtype, (n,))
+    _dev(ctx, n_steps, "n_steps", torch.int32, (n,)); _dev(ctx, problem_idx, "problem_idx", torch.int32, (n,))
+    out = (C.c_int32 * len(ctx.problems))()
+    _check(ctx, load_library().hj_autotune(ctx.handle, n, _ptr(problem_idx), _ptr(x), _ptr(t), _ptr(n_steps), iters,
+                                           out, _stream(x.device)))
+    return list(out)
 
 
 class Functional(torch.autograd.Function):

@@ -54,6 +54,7 @@ class ProblemSpec:
     n_neg: int = 1
     s_eps: float = 1e-6
     n_guesses: int = 1
+    solver: Optional[Dict] = None        # this problem's descent constants (None: the workload's)
 
     def params(self) -> np.ndarray:
         """Flat parameter vector in the library's documented order:
@@ -209,20 +210,25 @@ def c5_mixed(n_pairs: int = 1 << 20) -> Workload:
     the d=10-style speed-quadratic Lax family (8 guesses), the d=20-style
     non-convex Hopf family (16 guesses) and the linear-quadratic Lax family
     (1 guess).  Each query draws d from {8, 16, 32, 100}, t ~ U[0.1, 2] and
-    N = ceil(64 t).  Family parameters are drawn per (family, d)."""
+    N = ceil(64 t).  Family parameters are drawn per (family, d).  Each
+    family keeps the descent constants of its own workload: gradient descent
+    with reseeding (at most 20 trials) for the first two, conjugate
+    gradients with one start for the linear-quadratic one."""
     rng = rng_for(5)
     dims = [8, 16, 32, 100]
     probs: List[ProblemSpec] = []
     for d in dims:
         probs.append(ProblemSpec(d=d, family=FAM_SPEED_QUAD, principle=LAX, g_kind=G_QUAD_SHIFT,
-                                 w=_speed_w(rng, d), a=f32(rng.uniform(-1, 1, d)), n_guesses=8))
+                                 w=_speed_w(rng, d), a=f32(rng.uniform(-1, 1, d)), n_guesses=8,
+                                 solver=solver_constants(n_guesses=8)))
     for d in dims:
         probs.append(ProblemSpec(d=d, family=FAM_SMOOTH_NONCONVEX, principle=HOPF, g_kind=G_DIAG_QUAD,
-                                 w=_speed_w(rng, d), sigma=f32(rng.uniform(0.5, 2.0, d)), n_guesses=16))
+                                 w=_speed_w(rng, d), sigma=f32(rng.uniform(0.5, 2.0, d)), n_guesses=16,
+                                 solver=solver_constants(n_guesses=16)))
     for d in dims:
         A, B = _lq_matrices(rng, d)
         probs.append(ProblemSpec(d=d, family=FAM_LINEAR_QUAD, principle=LAX, g_kind=G_QUAD_SHIFT, A=A, B=B,
-                                 a=np.zeros(d), n_guesses=1))
+                                 a=np.zeros(d), n_guesses=1, solver=lq_solver()))
     per_fam = n_pairs // 3
     n_q = [per_fam // 8, per_fam // 16]
     n_q.append(n_pairs - 8 * n_q[0] - 16 * n_q[1])
@@ -243,7 +249,7 @@ def c5_mixed(n_pairs: int = 1 << 20) -> Workload:
     t = np.concatenate(ts)
     pidx = np.concatenate(idx).astype(np.int32)
     N = np.ceil(64.0 * t).astype(np.int32)
-    return Workload("mixed_persistent", probs, x, t, N, pidx, solver_constants(max_iters=300), "fp32")
+    return Workload("mixed_persistent", probs, x, t, N, pidx, solver_constants(), "fp32")
 
 
 WORKLOADS = {

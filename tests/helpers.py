@@ -32,3 +32,17 @@ def rel_err(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return np.abs(a - b) / (1.0 + np.abs(b))
+
+
+def oracle_opts_list(wl) -> list:
+    """One oracle Opts per problem of a workload: the problem's own descent
+    constants where it has them, the workload's otherwise; the context-wide
+    fields (quadrature, seed, start distribution, reseed rounds) are the
+    workload's, as in the library."""
+    out = []
+    for p in wl.problems:
+        s = dict(p.solver) if p.solver is not None else dict(wl.solver)
+        for k in ("quad", "seed", "guess_dist", "max_rounds"):
+            s[k] = wl.solver[k]
+        out.append(oracle_opts(s, p.n_guesses))
+    return out
