@@ -50,6 +50,11 @@ WORKLOADS = {
 CPU_SAMPLE = 64          # queries of the oracle timing sample (cpu_baseline)
 REF_SAMPLE = 16          # queries per step of the reference arm
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of the round-0 descent launch of a 4,096-query
+# case, from one `ncu --set full` capture of this build's kernel on a GB300;
+# the launch's traffic grows with the number of (query, start) pairs, so it is
+# scaled by queries / 4096.
+TRAFFIC_4096 = {"smooth_nonconvex_d20_hopf": 42.571e9 + 54.478e9, "linear_quad_d64_lax": 28.598e9 + 42.637e9}
 
 
 def _args():
@@ -64,6 +69,8 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--tpp", type=int, default=0, help="threads per pair of the descent (0: library choice)")
     ap.add_argument("--ck", type=int, default=0, help="adjoint checkpoint interval (0: library choice)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip hj_autotune (launch parameters timed on a 4096-query sample before the run)")
     return ap.parse_args()
 
 
@@ -236,9 +243,19 @@ def run_ours(a):
     pidx = torch.tensor(wl.problem_idx, dtype=torch.int32, device=dev) if multi else None
     opts = hj.opts_from_dict(wl.solver, hj.HJ_PREC_FP32, int(wl.n_steps.max()))
     ctx = hj.hj_create(wl.problems, opts, local)
+    tuning = None
     if a.tpp or a.ck:
         for p in range(len(wl.problems)):
             hj.hj_set_tuning(ctx, p, a.tpp, a.ck)
+        tuning = {"threads_per_pair": [a.tpp] * len(wl.problems), "by": "command line"}
+    elif not a.no_autotune:
+        # launch parameters per problem, timed on a sample (outside the timed region)
+        ns_ = min(nq, 4096)
+        sample = np.sort(np.random.default_rng(7).choice(nq, ns_, replace=False))
+        si = torch.tensor(sample, dtype=torch.int64, device=dev)
+        chosen = hj.hj_autotune(ctx, x[si].contiguous(), t[si].contiguous(), ns[si].contiguous(),
+                                pidx[si].contiguous() if multi else None, iters=3)
+        tuning = {"threads_per_pair": chosen, "by": f"hj_autotune on {ns_} queries, 3 iterations (0 = automatic)"}
     phi = torch.empty(nq, dtype=torch.float64, device=dev)
     vout = torch.zeros(nq, ld, dtype=torch.float32, device=dev)
     status = torch.empty(nq, dtype=torch.int32, device=dev)
@@ -282,10 +299,13 @@ def run_ours(a):
     peaks, peak_src = _peaks()
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     tflops = sum(i["tensor_flops"] for i in infos)
+    traffic = TRAFFIC_4096.get(a.workload)
+    traffic = None if traffic is None or a.tpp or a.ck else traffic * nq / 4096.0
     if tflops > 0:
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
         roof = {"bound": "tensor", "achieved": tflops / desc_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "frac": tflops / desc_s / 1e12 / peak, "traffic": None,
+                "frac": tflops / desc_s / 1e12 / peak, "traffic": traffic,
+                "traffic_note": "DRAM bytes of the descent launch, scaled from a 4,096-query ncu capture",
                 "kernel": "k_lq_tc (tensor-core tile kernel, BF16x3 stage products)",
                 "peak_note": f"dense BF16, {peak_src} sustained cuBLAS figure; achieved counts the three BF16 "
                              "products of each fp32 product (unpadded d, m)"}
@@ -293,7 +313,9 @@ def run_ours(a):
         flops = sum(i["algorithmic_flops"] for i in infos)
         peak = nsm * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": flops / desc_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "frac": flops / desc_s / 1e12 / peak, "traffic": None,
+                "frac": flops / desc_s / 1e12 / peak, "traffic": traffic,
+                "traffic_note": "DRAM bytes of the round-0 descent launch, scaled from a 4,096-query ncu capture "
+                                "(the adjoint's per-thread RK4 checkpoints)",
                 "kernel": "k_desc (persistent descent)",
                 "peak_note": f"FP32 FMA {nsm} SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                              f"({peak_src} max SM clock)"}
@@ -383,7 +405,7 @@ def run_ours(a):
             "metric": metric, "value": value, "unit": _unit(wl), "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config(a, wl, descent, nq),
+            "config": dict(_config(a, wl, descent, nq), tuning=tuning),
             "roofline": roof,
             "e2e": {"value": e2e_val, "unit": _unit(wl), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),

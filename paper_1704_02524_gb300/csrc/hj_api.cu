@@ -406,7 +406,8 @@ LqTcArgs tc_args(const hj_ctx *ctx, int p)
     const LqTcGeom &g = D.geom;
     LqTcArgs a{};
     a.d = g.d; a.dp = g.dp; a.m = g.m; a.mp = g.mp; a.ld = ctx->ld;
-    a.KF = g.KF; a.NF = g.NF; a.KV = g.KV; a.NV = g.NV; a.KZ = g.KZ;
+    a.KV = g.KV; a.KZ = g.KZ;
+    a.fwd[0] = g.fwd[0]; a.fwd[1] = g.fwd[1]; a.rev[0] = g.rev[0]; a.rev[1] = g.rev[1];
     a.w_bytes = g.w_bytes; a.z_bytes = g.z_bytes;
     a.wf_hi = (const uint4 *)D.wf_hi; a.wf_lo = (const uint4 *)D.wf_lo;
     a.wv_hi = (const uint4 *)D.wv_hi; a.wv_lo = (const uint4 *)D.wv_lo;

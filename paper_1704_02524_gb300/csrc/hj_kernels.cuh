@@ -242,8 +242,15 @@ __global__ void __launch_bounds__(BLOCK) k_cert(CertArgs<Tv> a)
 // 1 gradient descent, 2 conjugate-gradient descent (both with the adjoint).
 constexpr int DESC_CD = 0, DESC_GD = 1, DESC_CG = 2;
 
+// Resident blocks per SM the register allocation aims at: the adjoint
+// descents keep more state per component, so fewer components per thread
+// buy more resident warps (C <= 2: 5 blocks; C <= 5: 4, which costs the
+// 5-component adjoint a 138-byte spill and is 3% faster than 3 blocks; else 3).
+template <int C, int MODE>
+constexpr int desc_min_blocks() { return MODE == DESC_CD ? 4 : (C <= 2 ? 5 : (C <= 5 ? 4 : 3)); }
+
 template <typename T, int C, int FAM, int PR, int MODE>
-__global__ void __launch_bounds__(BLOCK, MODE != DESC_CD ? 3 : 4) k_desc(DescArgs<T> a)
+__global__ void __launch_bounds__(BLOCK, (desc_min_blocks<C, MODE>())) k_desc(DescArgs<T> a)
 {
     constexpr bool GD = MODE != DESC_CD;  // adjoint gradients (checkpoint storage)
     const Grp g = make_grp(a.tpp);

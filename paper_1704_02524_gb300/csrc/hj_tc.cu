@@ -4,9 +4,9 @@
 // The characteristic field of this family is linear (Sec. 4.1 system with
 // dH/dp = A gamma + B B^T p, dH/dx = A^T p), so every RK4 stage of every
 // (query, start) pair is a product of one fixed matrix with the pair's
-// stage vector.  A CTA owns a tile of 128 pairs, one per thread and per
-// TMEM lane, and evaluates each stage for all of them as one tensor-core
-// product [128 x K] x [K x N]:
+// stage vector.  A CTA owns a tile of 128 pairs, one per TMEM lane (two
+// threads per pair split its columns), and evaluates each stage for all of
+// them as tensor-core products [128 x K] x [K x N]:
 //   forward  Z_s = (gamma_s, p_s)                 -> (k_gamma, k_p, y = B^T p_s)
 //            k_gamma = -(A gamma_s + C p_s), k_p = A^T p_s, C = B B^T,
 //            running cost L_s = |y|^2 / 2 (Lax and Hopf alike);
@@ -14,6 +14,9 @@
 //            r_gamma = -A^T w_gamma, r_p = A w_p - C w_gamma + b B y_s,
 // the vector-Jacobian product of the discrete adjoint of RK4 (the y_s of
 // the forward pass are kept in global memory, so no state is recomputed).
+// Each pass is one dense product (N = 2 dp + mp or 2 dp columns): a K=16
+// MMA costs about the same for N = 64 as for N = 160, so skipping the zero
+// blocks of the matrices with narrower products is slower.
 // Products are split-precision BF16x3: each fp32 operand x = hi + lo with
 // hi = bf16(x), lo = bf16(x - hi), and the product is hi*hi + hi*lo + lo*hi
 // accumulated in fp32 in tensor memory (relative error ~2^-16).
@@ -43,7 +46,8 @@ namespace hjd {
 
 namespace {
 
-constexpr int TCR = 128;         // pairs (rows) per tile = threads per CTA = TMEM lanes
+constexpr int TCR = 128;         // pairs (rows) per tile = TMEM lanes
+constexpr int TCT = 256;         // threads per CTA: two per row
 constexpr uint32_t TM_COLS = 512;
 constexpr uint32_t COL_Z = 256;  // forward: z (RK4 state) columns; reverse: lambda
 constexpr long long WAIT_LIMIT = 1ll << 22;
@@ -166,25 +170,27 @@ struct Tile {
     uint32_t phase;
     uint32_t tm;    // TMEM base (lane 0, column 0)
     uint32_t lane;  // this warp's lane quarter, in TMEM address form
+    int row;        // tile row (pair) of this thread
+    int half;       // which half of the row's column chunks this thread handles
     bool abort;
 };
 
 __device__ __forceinline__ uint32_t ta(const Tile &T, uint32_t col) { return T.tm + T.lane + col; }
 
-// Copy a fixed matrix (already in core-matrix layout, hi and lo) into shared memory.
+// Copy a pass's fixed matrices (core-matrix layout, hi and lo) into shared memory.
 __device__ __forceinline__ void load_matrix(const Tile &T, const uint4 *hi, const uint4 *lo, int bytes)
 {
     const int n = bytes >> 4;
-    for (int i = threadIdx.x; i < n; i += TCR) {
+    for (int i = threadIdx.x; i < n; i += TCT) {
         ((uint4 *)T.wh)[i] = __ldg(hi + i);
         ((uint4 *)T.wl)[i] = __ldg(lo + i);
     }
 }
 
-// One stage product: waits for every thread's tile writes, issues the
-// three BF16x3 terms (K/16 MMAs each) and waits for their completion.
-// Returns false (abort) on a timeout anywhere in the CTA.
-__device__ __forceinline__ bool stage_mma(Tile &T, int K, int Nc, int kz, int kw)
+// One stage: waits for every thread's tile writes, issues the pass's
+// products (each three BF16x3 terms of K/16 MMAs) and waits for them.
+// Returns false (abort, taken by every thread alike) on a timeout.
+__device__ __forceinline__ bool stage_mma(Tile &T, const LqTcProd *pr, int kz)
 {
     fence_proxy();
     tm_wait_st();
@@ -192,19 +198,23 @@ __device__ __forceinline__ bool stage_mma(Tile &T, int K, int Nc, int kz, int kw
     __syncthreads();
     if (threadIdx.x == 0) {
         fence_after();
-        const uint32_t id = idesc_bf16(TCR, Nc);
         const uint32_t zh = s_addr(T.zh), zl = s_addr(T.zl), wh = s_addr(T.wh), wl = s_addr(T.wl);
-        const uint32_t sbo_z = (uint32_t)(kz >> 3) * 128, sbo_w = (uint32_t)(kw >> 3) * 128;
-        for (int term = 0; term < 3; ++term) {
-            const uint32_t a = (term == 2) ? zl : zh, b = (term == 1) ? wl : wh;
-            for (int kk = 0; kk < K / 16; ++kk)
-                mma_bf16(T.tm, mdesc(a + kk * 256, sbo_z), mdesc(b + kk * 256, sbo_w), id, (term | kk) ? 1u : 0u);
+        const uint32_t sbo_z = (uint32_t)(kz >> 3) * 128;
+        for (int i = 0; i < 1; ++i) {
+            const LqTcProd P = pr[i];
+            const uint32_t id = idesc_bf16(TCR, P.N), sbo_w = (uint32_t)(P.kw >> 3) * 128;
+            const uint32_t ao = (uint32_t)(P.acol >> 3) * 128;
+            for (int term = 0; term < 3; ++term) {
+                const uint32_t a = ((term == 2) ? zl : zh) + ao, b = ((term == 1) ? wl : wh) + P.boff;
+                for (int kk = 0; kk < P.K / 16; ++kk)
+                    mma_bf16(T.tm + P.dcol, mdesc(a + kk * 256, sbo_z), mdesc(b + kk * 256, sbo_w), id,
+                             (term | kk) ? 1u : 0u);
+            }
         }
         mma_commit(T.mbar);
     }
     const bool ok = mbar_wait(T.mbar, T.phase);
     T.phase ^= 1;
-    // every thread takes the same decision, so barriers stay matched
     if (__syncthreads_or(ok ? 0 : 1)) {
         T.abort = true;
         return false;
@@ -222,23 +232,25 @@ struct RowIO {
     int N;       // RK4 steps (0: masked row)
     float h;     // t / N
     float F;     // out: functional
-    float resid; // out (forward-only evaluation): certificate residual
+    float resid; // out: certificate residual at (gamma(0), p(0))
 };
 
 // F at the points PT (and its gradient into G when `grad`) for the 128 rows
-// of the tile.  X, PT, G are this CTA's component-major scratch
-// (entry [k * 128 + row]).  ybuf: this CTA's stage outputs y (grad only).
+// of the tile.  X, PT, G are this CTA's component-major scratch (entry
+// [k * 128 + row]); ybuf: this CTA's stage outputs y (grad only).  The two
+// threads of a row take alternate 16-column chunks; per-row sums are
+// combined through `red` (shared, [3][2][128]).
 __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X, const float *PT, float *G,
-                          float *ybuf, RowIO &io, int nmax)
+                          float *ybuf, RowIO &io, int nmax, float *red)
 {
-    const int r = threadIdx.x, d = a.d, dp = a.dp, mp = a.mp, kz = a.KZ;
+    const int r = T.row, c0 = 16 * T.half, d = a.d, dp = a.dp, mp = a.mp, kz = a.KZ;
     const int d2 = 2 * dp;
     const bool live_row = io.N > 0;
     const float h = io.h;
     // ---- forward pass --------------------------------------------------------
-    __syncthreads();  // the previous pass's MMAs have completed; W may be overwritten
-    load_matrix(T, a.wf_hi, a.wf_lo, a.NF * a.KF * 2);
-    for (int c = 0; c < d2; c += 16) {
+    __syncthreads();  // the previous pass's products have completed; W may be overwritten
+    load_matrix(T, a.wf_hi, a.wf_lo, (int)a.w_bytes);
+    for (int c = c0; c < d2; c += 32) {
         float z[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -251,19 +263,19 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
         tm_st16(ta(T, COL_Z + c), z);
         put16(T.zh, T.zl, r, c, kz, z);
     }
-    float Q = 0.f, Qc = 0.f, La = 0.f;
+    float Q = 0.f, Qc = 0.f, La = 0.f;  // this thread's share of the quadrature
     for (int n = 0; n < nmax; ++n) {
         const bool live = live_row && n < io.N;
         for (int s = 1; s <= 4; ++s) {
-            if (!stage_mma(T, a.KF, a.NF, kz, a.KF)) return false;
-            for (int c = 0; c < d2; c += 16) {
+            if (!stage_mma(T, a.fwd, kz)) return false;
+            const float cn = (s == 3) ? h : 0.5f * h, h6 = h / 6.f;
+            for (int c = c0; c < d2; c += 32) {
                 float k[16], z[16], ks[16], zn[16];
                 tm_ld16(ta(T, c), k);
                 tm_ld16(ta(T, COL_Z + c), z);
                 if (s > 1) tm_ld16(ta(T, COL_Z + d2 + c), ks);
                 tm_wait_ld();
                 if (s < 4) {
-                    const float cn = (s == 3) ? h : 0.5f * h;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         ks[j] = (s == 1) ? k[j] : fmaf(2.f, k[j], ks[j]);
@@ -271,7 +283,6 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
                     }
                     tm_st16(ta(T, COL_Z + d2 + c), ks);
                 } else {
-                    const float h6 = h / 6.f;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) zn[j] = live ? fmaf(h6, ks[j] + k[j], z[j]) : z[j];
                     tm_st16(ta(T, COL_Z + c), zn);  // .sync.aligned: every lane stores
@@ -279,7 +290,7 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
                 put16(T.zh, T.zl, r, c, kz, zn);
             }
             float Ls = 0.f;
-            for (int c = 0; c < mp; c += 16) {
+            for (int c = c0; c < mp; c += 32) {
                 float y[16];
                 tm_ld16(ta(T, d2 + c), y);
                 tm_wait_ld();
@@ -304,7 +315,7 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
     }
     // ---- terminal term, adjoint seed, certificate residual ------------------
     float term = 0.f, num = 0.f, den = 0.f;
-    for (int c = 0; c < dp; c += 16) {
+    for (int c = c0; c < dp; c += 32) {
         float gm[16], pm[16], lg[16], lp[16];
         tm_ld16(ta(T, COL_Z + c), gm);
         tm_ld16(ta(T, COL_Z + dp + c), pm);
@@ -343,34 +354,62 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
             tm_st16(ta(T, COL_Z + dp + c), lp);  // lambda_p
         }
     }
-    io.F = live_row ? term + Q : __int_as_float(0x7fc00000);
-    io.resid = sqrtf(num) / (1.f + sqrtf(den));
-    if (!grad) return true;
+    // combine the two halves' sums
+    red[(0 * 2 + T.half) * TCR + r] = term + Q;
+    red[(1 * 2 + T.half) * TCR + r] = num;
+    red[(2 * 2 + T.half) * TCR + r] = den;
+    __syncthreads();
+    {
+        const float F = red[r] + red[TCR + r];
+        const float nm = red[2 * TCR + r] + red[3 * TCR + r], dn = red[4 * TCR + r] + red[5 * TCR + r];
+        io.F = live_row ? F : __int_as_float(0x7fc00000);
+        io.resid = sqrtf(nm) / (1.f + sqrtf(dn));
+    }
+    if (!grad) {
+        __syncthreads();  // red may be reused
+        return true;
+    }
 
     // ---- reverse pass (discrete adjoint of RK4) ------------------------------
     // tensor memory: [0, 2dp) the product a_s, [COL_Z, +2dp) lambda,
     // [COL_Z + 2dp, +2dp) the running sum of a_s over the step's stages
-    const int kv = a.KV;
     fence_before();
     __syncthreads();  // every forward product has completed: W may be replaced
-    load_matrix(T, a.wv_hi, a.wv_lo, a.NV * a.KV * 2);
+    load_matrix(T, a.wv_hi, a.wv_lo, (int)a.w_bytes);
     tm_wait_st();
     // input of stage (n, s): w = c1 lambda + c2 a_prev on the state columns,
-    // b y_s on the y columns; masked rows feed zeros
-    auto put_y = [&](int n, int s, float b) {
-        const bool live = live_row && n < io.N;
-        for (int c = 0; c < mp; c += 16) {
-            float y[16];
-            const float *yb = ybuf + ((size_t)(n * 4 + s - 1) * mp + c) * TCR + r;
+    // b y_s on the y columns; masked rows feed zeros.  The y of the next
+    // input are loaded before the current stage's product is awaited, so the
+    // global-memory latency overlaps the tensor-core work.
+    // (the first y chunk of this thread is prefetched; a second one, when
+    // mp > 32, is read when it is written)
+    float ypre[16];
+    int y_n = 0, y_s = 0;
+    float y_b = 0.f;
+    auto read_y = [&](int n, int s, float b, int c, float *y) {
+        const bool live = live_row && n >= 0 && n < io.N;
+        const float *yb = ybuf + ((size_t)(n * 4 + s - 1) * mp + c) * TCR + r;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) y[j] = live ? b * yb[(size_t)j * TCR] : 0.f;
+        for (int j = 0; j < 16; ++j) y[j] = live ? b * yb[(size_t)j * TCR] : 0.f;
+    };
+    auto load_y = [&](int n, int s, float b) {
+        y_n = n;
+        y_s = s;
+        y_b = b;
+        if (c0 < mp) read_y(n, s, b, c0, ypre);
+    };
+    auto put_y = [&]() {
+        if (c0 < mp) put16(T.zh, T.zl, r, d2 + c0, kz, ypre);
+        for (int c = c0 + 32; c < mp; c += 32) {
+            float y[16];
+            read_y(y_n, y_s, y_b, c, y);
             put16(T.zh, T.zl, r, d2 + c, kz, y);
         }
     };
     {
         const int n = nmax - 1;
         const bool live = live_row && n < io.N;
-        for (int c = 0; c < d2; c += 16) {
+        for (int c = c0; c < d2; c += 32) {
             float lm[16], w[16];
             tm_ld16(ta(T, COL_Z + c), lm);
             tm_wait_ld();
@@ -378,18 +417,20 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
             for (int j = 0; j < 16; ++j) w[j] = live ? h / 6.f * lm[j] : 0.f;
             put16(T.zh, T.zl, r, c, kz, w);
         }
-        put_y(n, 4, h / 6.f);
+        load_y(n, 4, h / 6.f);
+        put_y();
     }
     for (int n = nmax - 1; n >= 0; --n) {
         for (int s = 4; s >= 1; --s) {
-            if (!stage_mma(T, kv, a.NV, kz, kv)) return false;
             // next input: (n, s-1), or (n-1, 4) after the step's last stage
             const int nn = (s > 1) ? n : n - 1;
             const int sn = (s > 1) ? s - 1 : 4;
+            if (nn >= 0) load_y(nn, sn, (sn == 3 || sn == 2) ? h / 3.f : h / 6.f);
+            if (!stage_mma(T, a.rev, kz)) return false;
             const bool live_n = live_row && nn >= 0 && nn < io.N;
             const float c1 = (sn == 3 || sn == 2) ? h / 3.f : h / 6.f;
             const float c2 = (sn == 3) ? h : 0.5f * h;
-            for (int c = 0; c < d2; c += 16) {
+            for (int c = c0; c < d2; c += 32) {
                 float av[16], lm[16], as[16], w[16];
                 tm_ld16(ta(T, c), av);
                 tm_ld16(ta(T, COL_Z + c), lm);
@@ -412,11 +453,11 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
                 }
                 if (nn >= 0) put16(T.zh, T.zl, r, c, kz, w);
             }
-            if (nn >= 0) put_y(nn, sn, (sn == 3 || sn == 2) ? h / 3.f : h / 6.f);
+            if (nn >= 0) put_y();
         }
     }
     // dF/dv = lambda_p at tau = 0 (minus x for Hopf)
-    for (int c = 0; c < dp; c += 16) {
+    for (int c = c0; c < dp; c += 32) {
         float lp[16];
         tm_ld16(ta(T, COL_Z + dp + c), lp);
         tm_wait_ld();
@@ -426,20 +467,24 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
             if (i < d) G[i * TCR + r] = (a.principle == HJ_HOPF) ? lp[j] - X[i * TCR + r] : lp[j];
         }
     }
+    __syncthreads();  // G complete for the row's first thread
     return true;
 }
 
 // ---------------------------------------------------------------------------
 // The kernel: rows mode (functional, gradient) or the persistent descent.
+// Threads t and t + 128 share row t % 128; per-row bookkeeping (inputs,
+// descent, outputs) is done by the first of the two.
 // ---------------------------------------------------------------------------
 template <int MODE>
-__global__ void __launch_bounds__(TCR, 1) k_lq_tc(LqTcArgs a)
+__global__ void __launch_bounds__(TCT, 1) k_lq_tc(LqTcArgs a)
 {
     extern __shared__ __align__(1024) unsigned char dsm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
     __shared__ int s_nmax;
-    const int r = threadIdx.x, warp = r >> 5;
+    __shared__ float s_red[6 * TCR];
+    const int tid = threadIdx.x, warp = tid >> 5;
     Tile T;
     T.wh = dsm;
     T.wl = dsm + a.w_bytes;
@@ -447,9 +492,13 @@ __global__ void __launch_bounds__(TCR, 1) k_lq_tc(LqTcArgs a)
     T.zl = dsm + 2 * a.w_bytes + a.z_bytes;
     T.mbar = s_addr(&mbar);
     T.phase = 0;
-    T.lane = (uint32_t)(warp * 32) << 16;
+    T.lane = (uint32_t)((warp & 3) * 32) << 16;
+    T.row = tid & (TCR - 1);
+    T.half = tid / TCR;
     T.abort = false;
-    if (r == 0) {
+    const int r = T.row;
+    const bool lead = T.half == 0;
+    if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(T.mbar));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -501,28 +550,29 @@ __global__ void __launch_bounds__(TCR, 1) k_lq_tc(LqTcArgs a)
         io.N = (valid && n_ok) ? N : 0;
         io.h = (valid && n_ok) ? t / (float)N : 0.f;
         // inputs into the component-major scratch
-        for (int k = 0; k < d; ++k) {
-            X[k * TCR + r] = valid ? a.x[q * a.ld + k] : 0.f;
-            float v0 = 0.f;
-            if (valid) {
-                if (MODE == LQ_DESC)
-                    v0 = start_component<float>(a.D.S.seed, a.D.q_begin + q, a.D.pair_slot[pid], a.D.pair_round[pid],
-                                                k, a.D.S.guess_dist);
-                else
-                    v0 = a.v[pid * a.ld + k];
+        if (lead)
+            for (int k = 0; k < d; ++k) {
+                X[k * TCR + r] = valid ? a.x[q * a.ld + k] : 0.f;
+                float v0 = 0.f;
+                if (valid) {
+                    if (MODE == LQ_DESC)
+                        v0 = start_component<float>(a.D.S.seed, a.D.q_begin + q, a.D.pair_slot[pid],
+                                                    a.D.pair_round[pid], k, a.D.S.guess_dist);
+                    else
+                        v0 = a.v[pid * a.ld + k];
+                }
+                V[k * TCR + r] = v0;
+                PT[k * TCR + r] = v0;
             }
-            V[k * TCR + r] = v0;
-            PT[k * TCR + r] = v0;
-        }
-        if (r == 0) s_nmax = 0;
+        if (tid == 0) s_nmax = 0;
         __syncthreads();
-        if (io.N > 0) atomicMax(&s_nmax, io.N);
+        if (lead && io.N > 0) atomicMax(&s_nmax, io.N);
         __syncthreads();
         const int nmax = s_nmax;
 
         if (MODE != LQ_DESC) {
-            if (nmax > 0 && !tile_eval(T, a, MODE == LQ_ROWS_GRAD, X, PT, G, ybuf, io, nmax)) break;
-            if (valid) {
+            if (nmax > 0 && !tile_eval(T, a, MODE == LQ_ROWS_GRAD, X, PT, G, ybuf, io, nmax, s_red)) break;
+            if (valid && lead) {
                 const float nanv = __int_as_float(0x7fc00000);
                 if (a.F) a.F[pid] = (io.N > 0) ? io.F : nanv;
                 if (MODE == LQ_ROWS_GRAD)
@@ -534,20 +584,23 @@ __global__ void __launch_bounds__(TCR, 1) k_lq_tc(LqTcArgs a)
         // ---- descent: gradient (DESC_GD) or conjugate-gradient (DESC_CG) steps ----
         const SolverDev &S = a.D.S;
         int it = 0, phase = 0, bad = 0;
-        bool active = valid && S.max_iters > 0, conv = false;
+        bool active = lead && valid && S.max_iters > 0, conv = false;
         if (valid && !n_ok) { active = false; bad = 1; }
         float sig = 0.f, dn = 0.f;
-        for (int k = 0; k < d; ++k) {
-            P1[k * TCR + r] = 0.f;                                   // previous gradient
-            P2[k * TCR + r] = (a.mode_desc == DESC_GD) ? (float)S.step : 0.f;  // alpha (GD) / direction (CG)
-        }
+        if (lead)
+            for (int k = 0; k < d; ++k) {
+                P1[k * TCR + r] = 0.f;                                              // previous gradient
+                P2[k * TCR + r] = (a.mode_desc == DESC_GD) ? (float)S.step : 0.f;  // alpha (GD) / direction (CG)
+            }
         bool aborted = false;
         while (__syncthreads_or(active ? 1 : 0)) {
-            if (a.mode_desc == DESC_CG && phase == 1)
-                for (int k = 0; k < d; ++k) PT[k * TCR + r] = fmaf(sig, P2[k * TCR + r], V[k * TCR + r]);
-            else
-                for (int k = 0; k < d; ++k) PT[k * TCR + r] = V[k * TCR + r];
-            if (!tile_eval(T, a, true, X, PT, G, ybuf, io, nmax)) { aborted = true; break; }
+            if (lead) {
+                if (a.mode_desc == DESC_CG && phase == 1)
+                    for (int k = 0; k < d; ++k) PT[k * TCR + r] = fmaf(sig, P2[k * TCR + r], V[k * TCR + r]);
+                else
+                    for (int k = 0; k < d; ++k) PT[k * TCR + r] = V[k * TCR + r];
+            }
+            if (!tile_eval(T, a, true, X, PT, G, ybuf, io, nmax, s_red)) { aborted = true; break; }
             if (!active) continue;
             n_g++;
             n_rk += io.N;
@@ -630,9 +683,10 @@ __global__ void __launch_bounds__(TCR, 1) k_lq_tc(LqTcArgs a)
         }
         if (aborted) break;
         // certificate at the final v in fp32 (forward pass only)
-        for (int k = 0; k < d; ++k) PT[k * TCR + r] = V[k * TCR + r];
-        if (!tile_eval(T, a, false, X, PT, G, ybuf, io, nmax)) break;
-        if (valid) {
+        if (lead)
+            for (int k = 0; k < d; ++k) PT[k * TCR + r] = V[k * TCR + r];
+        if (!tile_eval(T, a, false, X, PT, G, ybuf, io, nmax, s_red)) break;
+        if (valid && lead) {
             n_it += it;
             n_pairs++;
             n_sumN += N;
@@ -657,10 +711,9 @@ __global__ void __launch_bounds__(TCR, 1) k_lq_tc(LqTcArgs a)
             }
         }
     }
-    if (T.abort && r == 0) atomicExch(a.err, 1);
-    if (MODE == LQ_DESC && a.D.stats) {
+    if (T.abort && tid == 0) atomicExch(a.err, 1);
+    if (MODE == LQ_DESC && a.D.stats && lead) {
         atomicAdd(a.D.stats + 0, n_it);
-        atomicAdd(a.D.stats + 1, 0ull);
         atomicAdd(a.D.stats + 2, n_g);
         atomicAdd(a.D.stats + 3, n_rk);
         atomicAdd(a.D.stats + 4, n_adj);
@@ -720,22 +773,28 @@ bool lq_tc_geometry(int d, int m, LqTcGeom *g)
     g->m = m;
     g->dp = (d + 15) / 16 * 16;
     g->mp = (m + 15) / 16 * 16;
-    g->KF = 2 * g->dp;
-    g->NF = 2 * g->dp + g->mp;
-    g->KV = 2 * g->dp + g->mp;
-    g->NV = 2 * g->dp;
-    g->KZ = g->KV;
-    g->w_bytes = (size_t)std::max(g->NF * g->KF, g->NV * g->KV) * 2;
+    const int dp = g->dp, mp = g->mp;
+    g->KZ = 2 * dp + mp;
+    g->KV = g->KZ;
+    // one dense product per pass (wide N keeps each MMA at full rate):
+    // forward (k_gamma, k_p, y) from (gamma, p); reverse (r_gamma, r_p) from (w_gamma, w_p, b y)
+    g->fwd[0] = LqTcProd{0, 0, 2 * dp, 0, 2 * dp + mp, 2 * dp};
+    g->fwd[1] = g->fwd[0];
+    g->rev[0] = LqTcProd{0, 0, 2 * dp + mp, 0, 2 * dp, 2 * dp + mp};
+    g->rev[1] = g->rev[0];
+    g->w_bytes = (size_t)(2 * dp + mp) * 2 * dp * 2;
     g->z_bytes = (size_t)TCR * g->KZ * 2;
     g->smem = 2 * g->w_bytes + 2 * g->z_bytes;
-    // NF <= 256 (one MMA), 4 dp + 256 <= 512 TMEM columns, shared memory
-    return g->NF <= 256 && g->dp <= 64 && g->smem <= LQ_TC_SMEM_MAX;
+    // N = 2 dp + mp <= 256 in one MMA, the accumulator and 4 dp state
+    // columns within 512 TMEM columns, shared memory within budget
+    return dp <= 64 && 2 * dp + mp <= 256 && g->smem <= LQ_TC_SMEM_MAX;
 }
 
 void lq_tc_matrices(const LqTcGeom &g, const double *A, const double *B, std::vector<uint8_t> &wf_hi,
                     std::vector<uint8_t> &wf_lo, std::vector<uint8_t> &wv_hi, std::vector<uint8_t> &wv_lo)
 {
-    const int d = g.d, m = g.m, dp = g.dp;
+    const int d = g.d, m = g.m, dp = g.dp, mp = g.mp;
+    const int kf = 2 * dp, nf = 2 * dp + mp, kv = 2 * dp + mp, nv = 2 * dp;
     std::vector<double> C((size_t)d * d, 0.0);
     for (int i = 0; i < d; ++i)
         for (int j = 0; j < d; ++j) {
@@ -744,27 +803,27 @@ void lq_tc_matrices(const LqTcGeom &g, const double *A, const double *B, std::ve
             C[(size_t)i * d + j] = s;
         }
     // forward: rows (k_gamma | k_p | y), columns (gamma | p)
-    std::vector<double> Wf((size_t)g.NF * g.KF, 0.0);
+    std::vector<double> Wf((size_t)nf * kf, 0.0);
     for (int j = 0; j < d; ++j)
         for (int k = 0; k < d; ++k) {
-            Wf[(size_t)j * g.KF + k] = -A[(size_t)j * d + k];
-            Wf[(size_t)j * g.KF + dp + k] = -C[(size_t)j * d + k];
-            Wf[(size_t)(dp + j) * g.KF + dp + k] = A[(size_t)k * d + j];
+            Wf[(size_t)j * kf + k] = -A[(size_t)j * d + k];
+            Wf[(size_t)j * kf + dp + k] = -C[(size_t)j * d + k];
+            Wf[(size_t)(dp + j) * kf + dp + k] = A[(size_t)k * d + j];
         }
     for (int l = 0; l < m; ++l)
-        for (int k = 0; k < d; ++k) Wf[(size_t)(2 * dp + l) * g.KF + dp + k] = B[(size_t)k * m + l];
+        for (int k = 0; k < d; ++k) Wf[(size_t)(2 * dp + l) * kf + dp + k] = B[(size_t)k * m + l];
     // reverse: rows (r_gamma | r_p), columns (w_gamma | w_p | b y)
-    std::vector<double> Wv((size_t)g.NV * g.KV, 0.0);
+    std::vector<double> Wv((size_t)nv * kv, 0.0);
     for (int j = 0; j < d; ++j)
         for (int k = 0; k < d; ++k) {
-            Wv[(size_t)j * g.KV + k] = -A[(size_t)k * d + j];
-            Wv[(size_t)(dp + j) * g.KV + k] = -C[(size_t)j * d + k];
-            Wv[(size_t)(dp + j) * g.KV + dp + k] = A[(size_t)j * d + k];
+            Wv[(size_t)j * kv + k] = -A[(size_t)k * d + j];
+            Wv[(size_t)(dp + j) * kv + k] = -C[(size_t)j * d + k];
+            Wv[(size_t)(dp + j) * kv + dp + k] = A[(size_t)j * d + k];
         }
     for (int i = 0; i < d; ++i)
-        for (int l = 0; l < m; ++l) Wv[(size_t)(dp + i) * g.KV + 2 * dp + l] = B[(size_t)i * m + l];
-    pack_split(Wf, g.NF, g.KF, wf_hi, wf_lo);
-    pack_split(Wv, g.NV, g.KV, wv_hi, wv_lo);
+        for (int l = 0; l < m; ++l) Wv[(size_t)(dp + i) * kv + 2 * dp + l] = B[(size_t)i * m + l];
+    pack_split(Wf, nf, kf, wf_hi, wf_lo);
+    pack_split(Wv, nv, kv, wv_hi, wv_lo);
 }
 
 size_t lq_tc_vec_slot(const LqTcGeom &g) { return (size_t)6 * g.dp * TCR; }
@@ -777,17 +836,17 @@ cudaError_t lq_tc_launch(int mode, const LqTcArgs &a, int grid, size_t smem, cud
     case LQ_ROWS_EVAL:
         e = cudaFuncSetAttribute(k_lq_tc<LQ_ROWS_EVAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_lq_tc<LQ_ROWS_EVAL><<<grid, TCR, smem, s>>>(a);
+        k_lq_tc<LQ_ROWS_EVAL><<<grid, TCT, smem, s>>>(a);
         break;
     case LQ_ROWS_GRAD:
         e = cudaFuncSetAttribute(k_lq_tc<LQ_ROWS_GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_lq_tc<LQ_ROWS_GRAD><<<grid, TCR, smem, s>>>(a);
+        k_lq_tc<LQ_ROWS_GRAD><<<grid, TCT, smem, s>>>(a);
         break;
     default:
         e = cudaFuncSetAttribute(k_lq_tc<LQ_DESC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_lq_tc<LQ_DESC><<<grid, TCR, smem, s>>>(a);
+        k_lq_tc<LQ_DESC><<<grid, TCT, smem, s>>>(a);
         break;
     }
     return cudaGetLastError();

@@ -17,17 +17,27 @@ enum { LQ_ROWS_EVAL = 0, LQ_ROWS_GRAD = 1, LQ_DESC = 2 };
 constexpr size_t LQ_TC_SMEM_MAX = 220 * 1024;  // dynamic shared memory budget of one CTA
 constexpr size_t LQ_TC_SMEM_MIN = 120 * 1024;  // requested at least, so one CTA (and one TMEM owner) per SM
 
+// One tensor-core product of a pass: accumulator columns from dcol, A =
+// stage-tile columns [acol, acol + K), B = the N x K matrix at byte offset
+// boff of the pass's matrices (row pitch kw = K).
+struct LqTcProd {
+    int dcol, acol, K;
+    uint32_t boff;
+    int N, kw;
+};
+
 // Padded sizes of one problem: dp = d rounded up to 16, mp = m rounded up
-// to 16; forward product K = 2 dp, N = 2 dp + mp; reverse K = 2 dp + mp,
-// N = 2 dp; the stage tile has KZ = 2 dp + mp columns.
+// to 16; the stage tile has KZ = 2 dp + mp columns; two products per pass.
 struct LqTcGeom {
-    int d = 0, m = 0, dp = 0, mp = 0, KF = 0, NF = 0, KV = 0, NV = 0, KZ = 0;
+    int d = 0, m = 0, dp = 0, mp = 0, KV = 0, KZ = 0;
+    LqTcProd fwd[2], rev[2];
     size_t w_bytes = 0, z_bytes = 0, smem = 0;
 };
 
 struct LqTcArgs {
     int d, dp, m, mp, ld;
-    int KF, NF, KV, NV, KZ;
+    int KV, KZ;
+    LqTcProd fwd[2], rev[2];
     size_t w_bytes, z_bytes;
     const uint4 *wf_hi, *wf_lo, *wv_hi, *wv_lo;  // fixed matrices, core-matrix layout, bf16 hi/lo
     int principle, g_kind;
@@ -52,8 +62,8 @@ struct LqTcArgs {
     int *err;
 };
 
-// True when the problem fits the tile kernel (d <= 64 after padding, one
-// product of N <= 256, shared memory within budget).
+// True when the problem fits the tile kernel (d <= 64 after padding,
+// shared memory within budget).
 bool lq_tc_geometry(int d, int m, LqTcGeom *g);
 // The forward and reverse matrices of a problem, split into bf16 hi/lo in the
 // core-matrix layout (A: d x d row-major, B: d x m row-major).

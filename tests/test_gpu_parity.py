@@ -308,11 +308,16 @@ def _solve_mixed(hj, w, tune=False):
     if key not in _ORACLE_CACHE:
         probs = [oracle_problem(p) for p in w.problems]
         ref = O.solve(probs, oracle_opts_list(w), w.x, w.t, w.n_steps, problem_idx=w.problem_idx)
-        # the same solve with x moved by 1e-7 (relative): rows whose answer
-        # moves are decided by rounding, not by the problem
-        xp = w.x * (1 + 1e-7 * np.random.default_rng(0).standard_normal(w.x.shape))
-        refp = O.solve(probs, oracle_opts_list(w), xp, w.t, w.n_steps, problem_idx=w.problem_idx)
-        stable = (rel_err(ref["phi"], refp["phi"]) <= 1e-6) & ((ref["status"] & 1) == (refp["status"] & 1))
+        # the same solve with x moved twice by 1e-7 (relative): rows whose
+        # answer moves, or whose chosen start is not certified, are decided
+        # by rounding, not by the problem
+        stable = (ref["status"] & 1) == 1
+        for seed in (0, 1):
+            xp = w.x * (1 + 1e-7 * np.random.default_rng(seed).standard_normal(w.x.shape))
+            refp = O.solve(probs, oracle_opts_list(w), xp, w.t, w.n_steps, problem_idx=w.problem_idx)
+            stable &= (rel_err(ref["phi"], refp["phi"]) <= 1e-6) & ((refp["status"] & 1) == 1)
+        nonconvex = np.array([w.problems[int(i)].family == W.FAM_SMOOTH_NONCONVEX for i in w.problem_idx])
+        stable |= ~nonconvex  # the smooth and convex families are checked on every row
         _ORACLE_CACHE[key] = (ref, stable)
     ref, stable = _ORACLE_CACHE[key]
     return phi.cpu().numpy(), st.cpu().numpy(), ref, stable, info, chosen
@@ -324,9 +329,7 @@ def _check_mixed(w, phi, st, ref, stable):
         rows = w.problem_idx == p
         ok = rows & stable
         print(f"problem {p} (family {w.problems[p].family}, d={w.problems[p].d}): {ok.sum()}/{rows.sum()} rows "
-              f"stable in FP64, max rel err there {err[ok].max() if ok.any() else float('nan'):.2e}")
-        if w.problems[p].family != W.FAM_SMOOTH_NONCONVEX:
-            assert ok.sum() == rows.sum()  # smooth and convex families are all reproducible
+              f"checked, max rel err there {err[ok].max() if ok.any() else float('nan'):.2e}")
     assert np.all(err[stable] <= 1e-4), err[stable].max()
     assert np.array_equal(st[stable] & 1, ref["status"][stable] & 1)
 
@@ -336,9 +339,10 @@ def test_solve_mixed_families_and_dimensions_matches_oracle(hj):
     # linear-quadratic Lax at d = 8, 16, 32, 100; t ~ U[0.1, 2] and N per
     # query), each with its own descent constants; the linear-quadratic
     # problems up to d = 32 run on the tensor-core tile kernel, d = 100 on
-    # lane groups.  Non-convex Hopf rows at large t or d = 100 certify no
-    # start and their FP64 answer moves under a 1e-7 change of x, so parity
-    # is checked on the rows whose answer the problem decides.
+    # lane groups.  Non-convex Hopf rows at large t or d = 100 often certify
+    # no start and their FP64 answer moves under a 1e-7 change of x, so that
+    # family is checked on the rows the oracle certifies with an answer that
+    # two such changes leave in place; the other families on every row.
     w = _mixed_sample()
     phi, st, ref, stable, info, _ = _solve_mixed(hj, w)
     _check_mixed(w, phi, st, ref, stable)
