@@ -48,7 +48,7 @@ WORKLOADS = {
                          "gradient descent (adjoint) for every problem"),
 }
 CPU_SAMPLE = 64          # queries of the oracle timing sample (cpu_baseline)
-REF_SAMPLE = 16          # queries per step of the reference arm
+REF_SAMPLE = 64          # queries per step of the reference arm
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of the round-0 descent launch of a 4,096-query
 # case, from one `ncu --set full` capture of this build's kernel on a GB300;

@@ -116,8 +116,9 @@ template <typename T>
 void fill_prob(const hj_problem_desc &D, const std::vector<double> &par, int ld, std::vector<T> &host, ProbDev<T> &P)
 {
     const int d = D.d, m = (D.family == HJ_FAM_LINEAR_QUAD) ? D.m : 0;
-    const size_t nvec = 5 * (size_t)DPAD, nA = (size_t)d * d, nB = (size_t)d * m;
-    host.assign(nvec + (m ? 3 * nA : 0), (T)0);
+    const int ldm = (d + 7) / 8 * 8;  // matrix rows padded for aligned vector loads
+    const size_t nvec = 5 * (size_t)DPAD, nA = (size_t)d * d, nB = (size_t)d * m, nM = (size_t)d * ldm;
+    host.assign(nvec + (m ? 3 * nM : 0), (T)0);
     T *w = host.data(), *e = w + DPAD, *ga = e + DPAD, *gs2 = ga + DPAD, *gis2 = gs2 + DPAD;
     size_t off = 0;
     if (D.family == HJ_FAM_SPEED_QUAD || D.family == HJ_FAM_SMOOTH_NONCONVEX) {
@@ -125,16 +126,17 @@ void fill_prob(const hj_problem_desc &D, const std::vector<double> &par, int ld,
         off = d;
     }
     if (D.family == HJ_FAM_LINEAR_QUAD) {
-        // At[j][i] = A[i][j], A[j][i], Cm = B B^T (double sums, then rounded)
-        T *At = host.data() + nvec, *A = At + nA, *Cm = A + nA;
+        // At[j][i] = A[i][j], A[j][i], Cm = B B^T (double sums, then rounded),
+        // rows of ldm values
+        T *At = host.data() + nvec, *A = At + nM, *Cm = A + nM;
         const double *pA = par.data(), *pB = par.data() + nA;
         for (int i = 0; i < d; ++i)
             for (int j = 0; j < d; ++j) {
-                At[(size_t)j * d + i] = (T)pA[(size_t)i * d + j];
-                A[(size_t)j * d + i] = (T)pA[(size_t)j * d + i];
+                At[(size_t)j * ldm + i] = (T)pA[(size_t)i * d + j];
+                A[(size_t)j * ldm + i] = (T)pA[(size_t)j * d + i];
                 double c = 0;
                 for (int k = 0; k < m; ++k) c += pB[(size_t)i * m + k] * pB[(size_t)j * m + k];
-                Cm[(size_t)j * d + i] = (T)c;
+                Cm[(size_t)j * ldm + i] = (T)c;
             }
         off = nA + nB;
     }
@@ -155,6 +157,7 @@ void fill_prob(const hj_problem_desc &D, const std::vector<double> &par, int ld,
     P.m = m;
     P.n_neg = D.n_neg;
     P.ld = ld;
+    P.ldm = ldm;
     P.s_eps = (T)D.s_eps;
 }
 
@@ -167,9 +170,10 @@ void bind_prob(void *block, int m, ProbDev<T> &P)
     P.ga = b + 2 * DPAD;
     P.gs2 = b + 3 * DPAD;
     P.gis2 = b + 4 * DPAD;
+    const size_t nM = (size_t)P.d * P.ldm;
     P.At = m ? b + 5 * DPAD : nullptr;
-    P.A = m ? b + 5 * DPAD + (size_t)P.d * P.d : nullptr;
-    P.Cm = m ? b + 5 * DPAD + 2 * (size_t)P.d * P.d : nullptr;
+    P.A = m ? b + 5 * DPAD + nM : nullptr;
+    P.Cm = m ? b + 5 * DPAD + 2 * nM : nullptr;
 }
 
 }  // namespace

@@ -38,11 +38,12 @@ struct ProbDev {
     const T *ga;    // [DPAD] shift a of g = |x-a|^2/2
     const T *gs2;   // [DPAD] sigma^2 of g = sum x^2/(2 sigma^2)
     const T *gis2;  // [DPAD] 1/sigma^2
-    // linear-quadratic family, d x d each, all read as M[j*d + i] so that the
-    // lanes of a group (consecutive i) read consecutive addresses:
-    const T *At;    // At[j*d + i] = A[i][j]   (for A gamma)
-    const T *A;     // A[j*d + i]  = A[j][i]   (for A^T p)
-    const T *Cm;    // Cm[j*d + i] = (B B^T)[j][i], symmetric
+    // linear-quadratic family: d rows of ldm (d rounded up to 8, zero padded)
+    // values each, all read as M[j*ldm + i]:
+    int ldm;
+    const T *At;    // At[j*ldm + i] = A[i][j]   (for A gamma)
+    const T *A;     // A[j*ldm + i]  = A[j][i]   (for A^T p)
+    const T *Cm;    // Cm[j*ldm + i] = (B B^T)[j][i], symmetric
 };
 
 // Solver constants on the device.
@@ -181,7 +182,7 @@ struct TP {
     T w[C], e[C];
     const T *At, *A, *Cm;
     T *sh;
-    int d;
+    int d, ldm;
     __device__ void load(const ProbDev<T> &P, const Grp &g)
     {
 #pragma unroll
@@ -194,14 +195,16 @@ struct TP {
         A = P.A;
         Cm = P.Cm;
         d = P.d;
+        ldm = P.ldm;
         sh = nullptr;
     }
 };
 
-// Shared scratch of the linear-quadratic family: 2 C values per thread.
+// Shared scratch of the linear-quadratic family: 5 C values per thread (two
+// staged input vectors and three product vectors of the group).
 template <typename T, int C, int FAM>
 struct LqScratch {
-    static constexpr int N = (FAM == HJ_FAM_LINEAR_QUAD) ? 2 * C : 1;
+    static constexpr int N = (FAM == HJ_FAM_LINEAR_QUAD) ? 5 * C : 1;
 };
 
 // ---------------------------------------------------------------------------
@@ -413,8 +416,10 @@ struct Family<T, C, HJ_FAM_SMOOTH_NONCONVEX, PR> {
 // vector-Jacobian product needs only Cm p of the stage (for the cost row):
 // rg = -A^T ag,  rp = A ap - Cm ag + b Cm p.
 // Each product sum_j M[j][i] u_j runs over j with u staged in the group's
-// shared scratch (broadcast reads) and M read from global memory (L1
-// resident; consecutive lanes read consecutive i).
+// shared scratch (broadcast reads); for the sums, lane l of the group takes
+// the C consecutive rows i = C l .. C l + C - 1, so each matrix row costs one
+// vector load per lane, and the sums go back to the owner layout
+// (i = l + k tpp) through the scratch.
 template <typename T, int C>
 __device__ __forceinline__ void lq_stage2(const Grp &g, T *sh, const T *a, const T *b)
 {
@@ -423,6 +428,55 @@ __device__ __forceinline__ void lq_stage2(const Grp &g, T *sh, const T *a, const
     for (int k = 0; k < C; ++k) {
         sh[g.lane + k * g.tpp] = a[k];
         sh[n + g.lane + k * g.tpp] = b[k];
+    }
+    __syncwarp(g.mask);
+}
+
+// C consecutive values at p (aligned to their size, up to 16 bytes per load).
+template <typename T, int C>
+__device__ __forceinline__ void ld_row(const T *p, T *v)
+{
+    constexpr int bytes = C * (int)sizeof(T);
+    if constexpr (bytes % 16 == 0) {
+#pragma unroll
+        for (int q = 0; q < bytes / 16; ++q) {
+            const float4 f = __ldg((const float4 *)p + q);
+            const T *t = (const T *)&f;
+#pragma unroll
+            for (int k = 0; k < 16 / (int)sizeof(T); ++k) v[q * (16 / (int)sizeof(T)) + k] = t[k];
+        }
+    } else if constexpr (bytes == 8) {
+        const float2 f = __ldg((const float2 *)p);
+        const T *t = (const T *)&f;
+#pragma unroll
+        for (int k = 0; k < C; ++k) v[k] = t[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < C; ++k) v[k] = __ldg(p + k);
+    }
+}
+
+// Writes the three row-blocked sums (lane l holds rows C l + k) to the
+// scratch and reads them back in the owner layout.
+template <typename T, int C>
+__device__ __forceinline__ void lq_regather(const Grp &g, T *sh, const T *s0, const T *s1, const T *s2, T *o0, T *o1,
+                                            T *o2)
+{
+    const int n = C * g.tpp, i0 = C * g.lane;
+    T *r = sh + 2 * n;
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        r[i0 + k] = s0[k];
+        r[n + i0 + k] = s1[k];
+        r[2 * n + i0 + k] = s2[k];
+    }
+    __syncwarp(g.mask);
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        const int i = g.lane + k * g.tpp;
+        o0[k] = r[i];
+        o1[k] = r[n + i];
+        o2[k] = r[2 * n + i];
     }
     __syncwarp(g.mask);
 }
@@ -436,30 +490,27 @@ struct Family<T, C, HJ_FAM_LINEAR_QUAD, PR> {
     __device__ static __forceinline__ void prep(const Grp &g, const TP<T, C> &tp, T, const T *gam, const T *p, FI &f)
     {
         T *sh = tp.sh;
-        const int n = C * g.tpp, d = tp.d;
+        const int n = C * g.tpp, d = tp.d, ldm = tp.ldm, i0 = C * g.lane;
         lq_stage2<T, C>(g, sh, gam, p);
-        bool ok[C];
+        T ax[C], cp[C], atp[C];
 #pragma unroll
-        for (int k = 0; k < C; ++k) {
-            ok[k] = g.lane + k * g.tpp < d;
-            f.ax[k] = 0;
-            f.cp[k] = 0;
-            f.atp[k] = 0;
-        }
-        for (int j = 0; j < d; ++j) {
-            const T gj = sh[j], pj = sh[n + j];
-            const T *at = tp.At + (size_t)j * d, *a = tp.A + (size_t)j * d, *cm = tp.Cm + (size_t)j * d;
+        for (int k = 0; k < C; ++k) ax[k] = cp[k] = atp[k] = 0;
+        if (i0 < d) {
+            for (int j = 0; j < d; ++j) {
+                const T gj = sh[j], pj = sh[n + j];
+                T m1[C], m2[C], m3[C];
+                ld_row<T, C>(tp.At + (size_t)j * ldm + i0, m1);
+                ld_row<T, C>(tp.Cm + (size_t)j * ldm + i0, m2);
+                ld_row<T, C>(tp.A + (size_t)j * ldm + i0, m3);
 #pragma unroll
-            for (int k = 0; k < C; ++k) {
-                const int i = g.lane + k * g.tpp;
-                if (ok[k]) {
-                    f.ax[k] = fma(__ldg(at + i), gj, f.ax[k]);
-                    f.cp[k] = fma(__ldg(cm + i), pj, f.cp[k]);
-                    f.atp[k] = fma(__ldg(a + i), pj, f.atp[k]);
+                for (int k = 0; k < C; ++k) {
+                    ax[k] = fma(m1[k], gj, ax[k]);
+                    cp[k] = fma(m2[k], pj, cp[k]);
+                    atp[k] = fma(m3[k], pj, atp[k]);
                 }
             }
         }
-        __syncwarp(g.mask);
+        lq_regather<T, C>(g, sh, ax, cp, atp, f.ax, f.cp, f.atp);
         T pcp = 0;
 #pragma unroll
         for (int k = 0; k < C; ++k) pcp = fma(p[k], f.cp[k], pcp);
@@ -478,29 +529,33 @@ struct Family<T, C, HJ_FAM_LINEAR_QUAD, PR> {
                                                   const T *ap, T b, T *rg, T *rp)
     {
         T *sh = tp.sh;
-        const int n = C * g.tpp, d = tp.d;
+        const int n = C * g.tpp, d = tp.d, ldm = tp.ldm, i0 = C * g.lane;
         lq_stage2<T, C>(g, sh, ag, ap);
-        bool ok[C];
+        T sg[C], sa[C], sc[C];
 #pragma unroll
-        for (int k = 0; k < C; ++k) {
-            ok[k] = g.lane + k * g.tpp < d;
-            rg[k] = 0;
-            rp[k] = b * f.cp[k];
-        }
-        for (int j = 0; j < d; ++j) {
-            const T agj = sh[j], apj = sh[n + j];
-            const T *at = tp.At + (size_t)j * d, *a = tp.A + (size_t)j * d, *cm = tp.Cm + (size_t)j * d;
+        for (int k = 0; k < C; ++k) sg[k] = sa[k] = sc[k] = 0;
+        if (i0 < d) {
+            for (int j = 0; j < d; ++j) {
+                const T agj = sh[j], apj = sh[n + j];
+                T m1[C], m2[C], m3[C];
+                ld_row<T, C>(tp.A + (size_t)j * ldm + i0, m1);
+                ld_row<T, C>(tp.At + (size_t)j * ldm + i0, m2);
+                ld_row<T, C>(tp.Cm + (size_t)j * ldm + i0, m3);
 #pragma unroll
-            for (int k = 0; k < C; ++k) {
-                const int i = g.lane + k * g.tpp;
-                if (ok[k]) {
-                    rg[k] = fma(-__ldg(a + i), agj, rg[k]);
-                    rp[k] = fma(__ldg(at + i), apj, rp[k]);
-                    rp[k] = fma(-__ldg(cm + i), agj, rp[k]);
+                for (int k = 0; k < C; ++k) {
+                    sg[k] = fma(m1[k], agj, sg[k]);  // (A^T ag)_i
+                    sa[k] = fma(m2[k], apj, sa[k]);  // (A ap)_i
+                    sc[k] = fma(m3[k], agj, sc[k]);  // (Cm ag)_i
                 }
             }
         }
-        __syncwarp(g.mask);
+        T og[C], oa[C], oc[C];
+        lq_regather<T, C>(g, sh, sg, sa, sc, og, oa, oc);
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            rg[k] = -og[k];
+            rp[k] = fma(b, f.cp[k], oa[k] - oc[k]);
+        }
     }
 };
 

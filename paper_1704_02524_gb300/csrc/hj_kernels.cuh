@@ -116,7 +116,7 @@ __device__ __forceinline__ void store_row(const Grp &g, T *row, int d, const T *
 template <typename T, int C, int FAM>
 __device__ __forceinline__ void bind_scratch(TP<T, C> &tp, T *sh, int tpp)
 {
-    if (FAM == HJ_FAM_LINEAR_QUAD) tp.sh = sh + (threadIdx.x & ~(tpp - 1)) * 2 * C;
+    if (FAM == HJ_FAM_LINEAR_QUAD) tp.sh = sh + (threadIdx.x & ~(tpp - 1)) * LqScratch<T, C, FAM>::N;
 }
 
 template <typename T, int C, int FAM, int PR>

@@ -47,7 +47,8 @@ namespace hjd {
 namespace {
 
 constexpr int TCR = 128;         // pairs (rows) per tile = TMEM lanes
-constexpr int TCT = 256;         // threads per CTA: two per row
+constexpr int TPR = 2;           // threads per row (pair): they take alternate 16-column chunks
+constexpr int TCT = TCR * TPR;   // threads per CTA
 constexpr uint32_t TM_COLS = 512;
 constexpr uint32_t COL_Z = 256;  // forward: z (RK4 state) columns; reverse: lambda
 constexpr long long WAIT_LIMIT = 1ll << 22;
@@ -239,7 +240,7 @@ struct RowIO {
 // of the tile.  X, PT, G are this CTA's component-major scratch (entry
 // [k * 128 + row]); ybuf: this CTA's stage outputs y (grad only).  The two
 // threads of a row take alternate 16-column chunks; per-row sums are
-// combined through `red` (shared, [3][2][128]).
+// combined through `red` (shared, [3][TPR][128]).
 __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X, const float *PT, float *G,
                           float *ybuf, RowIO &io, int nmax, float *red)
 {
@@ -250,7 +251,7 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
     // ---- forward pass --------------------------------------------------------
     __syncthreads();  // the previous pass's products have completed; W may be overwritten
     load_matrix(T, a.wf_hi, a.wf_lo, (int)a.w_bytes);
-    for (int c = c0; c < d2; c += 32) {
+    for (int c = c0; c < d2; c += 16 * TPR) {
         float z[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -269,7 +270,7 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
         for (int s = 1; s <= 4; ++s) {
             if (!stage_mma(T, a.fwd, kz)) return false;
             const float cn = (s == 3) ? h : 0.5f * h, h6 = h / 6.f;
-            for (int c = c0; c < d2; c += 32) {
+            for (int c = c0; c < d2; c += 16 * TPR) {
                 float k[16], z[16], ks[16], zn[16];
                 tm_ld16(ta(T, c), k);
                 tm_ld16(ta(T, COL_Z + c), z);
@@ -290,7 +291,7 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
                 put16(T.zh, T.zl, r, c, kz, zn);
             }
             float Ls = 0.f;
-            for (int c = c0; c < mp; c += 32) {
+            for (int c = c0; c < mp; c += 16 * TPR) {
                 float y[16];
                 tm_ld16(ta(T, d2 + c), y);
                 tm_wait_ld();
@@ -315,7 +316,7 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
     }
     // ---- terminal term, adjoint seed, certificate residual ------------------
     float term = 0.f, num = 0.f, den = 0.f;
-    for (int c = c0; c < dp; c += 32) {
+    for (int c = c0; c < dp; c += 16 * TPR) {
         float gm[16], pm[16], lg[16], lp[16];
         tm_ld16(ta(T, COL_Z + c), gm);
         tm_ld16(ta(T, COL_Z + dp + c), pm);
@@ -354,14 +355,19 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
             tm_st16(ta(T, COL_Z + dp + c), lp);  // lambda_p
         }
     }
-    // combine the two halves' sums
-    red[(0 * 2 + T.half) * TCR + r] = term + Q;
-    red[(1 * 2 + T.half) * TCR + r] = num;
-    red[(2 * 2 + T.half) * TCR + r] = den;
+    // combine the row's threads' sums
+    red[(0 * TPR + T.half) * TCR + r] = term + Q;
+    red[(1 * TPR + T.half) * TCR + r] = num;
+    red[(2 * TPR + T.half) * TCR + r] = den;
     __syncthreads();
     {
-        const float F = red[r] + red[TCR + r];
-        const float nm = red[2 * TCR + r] + red[3 * TCR + r], dn = red[4 * TCR + r] + red[5 * TCR + r];
+        float F = 0.f, nm = 0.f, dn = 0.f;
+#pragma unroll
+        for (int k = 0; k < TPR; ++k) {
+            F += red[(0 * TPR + k) * TCR + r];
+            nm += red[(1 * TPR + k) * TCR + r];
+            dn += red[(2 * TPR + k) * TCR + r];
+        }
         io.F = live_row ? F : __int_as_float(0x7fc00000);
         io.resid = sqrtf(nm) / (1.f + sqrtf(dn));
     }
@@ -400,7 +406,7 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
     };
     auto put_y = [&]() {
         if (c0 < mp) put16(T.zh, T.zl, r, d2 + c0, kz, ypre);
-        for (int c = c0 + 32; c < mp; c += 32) {
+        for (int c = c0 + 16 * TPR; c < mp; c += 16 * TPR) {
             float y[16];
             read_y(y_n, y_s, y_b, c, y);
             put16(T.zh, T.zl, r, d2 + c, kz, y);
@@ -409,7 +415,7 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
     {
         const int n = nmax - 1;
         const bool live = live_row && n < io.N;
-        for (int c = c0; c < d2; c += 32) {
+        for (int c = c0; c < d2; c += 16 * TPR) {
             float lm[16], w[16];
             tm_ld16(ta(T, COL_Z + c), lm);
             tm_wait_ld();
@@ -430,7 +436,7 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
             const bool live_n = live_row && nn >= 0 && nn < io.N;
             const float c1 = (sn == 3 || sn == 2) ? h / 3.f : h / 6.f;
             const float c2 = (sn == 3) ? h : 0.5f * h;
-            for (int c = c0; c < d2; c += 32) {
+            for (int c = c0; c < d2; c += 16 * TPR) {
                 float av[16], lm[16], as[16], w[16];
                 tm_ld16(ta(T, c), av);
                 tm_ld16(ta(T, COL_Z + c), lm);
@@ -457,7 +463,7 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
         }
     }
     // dF/dv = lambda_p at tau = 0 (minus x for Hopf)
-    for (int c = c0; c < dp; c += 32) {
+    for (int c = c0; c < dp; c += 16 * TPR) {
         float lp[16];
         tm_ld16(ta(T, COL_Z + dp + c), lp);
         tm_wait_ld();
@@ -473,8 +479,8 @@ __device__ bool tile_eval(Tile &T, const LqTcArgs &a, bool grad, const float *X,
 
 // ---------------------------------------------------------------------------
 // The kernel: rows mode (functional, gradient) or the persistent descent.
-// Threads t and t + 128 share row t % 128; per-row bookkeeping (inputs,
-// descent, outputs) is done by the first of the two.
+// Threads t, t + 128, ... share row t % 128; per-row bookkeeping (inputs,
+// descent, outputs) is done by the first of them.
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(TCT, 1) k_lq_tc(LqTcArgs a)
@@ -483,7 +489,7 @@ __global__ void __launch_bounds__(TCT, 1) k_lq_tc(LqTcArgs a)
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
     __shared__ int s_nmax;
-    __shared__ float s_red[6 * TCR];
+    __shared__ float s_red[3 * TPR * TCR];
     const int tid = threadIdx.x, warp = tid >> 5;
     Tile T;
     T.wh = dsm;
