@@ -60,3 +60,51 @@ def test_create_rejects_bad_arguments_without_a_gpu(lib):
     with pytest.raises(hj.HJError) as e:
         hj.hj_create([neg], hj.opts_from_dict(wl.solver), 0)
     assert "sigma" in str(e.value)
+
+
+def test_create_rejects_a_bad_per_problem_solver_without_a_gpu(lib):
+    # a problem's own descent constants are validated on the host, and the
+    # message names the problem
+    from paper_1704_02524_gb300 import hj
+    from paper_1704_02524_gb300 import workloads as W
+    hj.load_library()
+    wl = W.c3_smooth_nonconvex(nq=2)
+    good = wl.problems[0]
+    bad = W.ProblemSpec(**{**good.__dict__, "solver": W.solver_constants(n_guesses=16, step=-1.0)})
+    with pytest.raises(hj.HJError) as e:
+        hj.hj_create([good, bad], hj.opts_from_dict(wl.solver), 0)
+    assert e.value.status == hj.HJ_EINVAL and "problem 1 solver" in str(e.value) and "step" in str(e.value)
+    cg = W.ProblemSpec(**{**good.__dict__, "solver": W.solver_constants(grad="adjoint_cg", step_max=0.0)})
+    with pytest.raises(hj.HJError) as e:
+        hj.hj_create([cg], hj.opts_from_dict(wl.solver), 0)
+    assert "step_max" in str(e.value)
+
+
+def test_linear_quadratic_limits_are_checked_without_a_gpu(lib):
+    from paper_1704_02524_gb300 import hj
+    from paper_1704_02524_gb300 import workloads as W
+    import numpy as np
+    hj.load_library()
+    d = 130
+    spec = W.ProblemSpec(d=d, family=W.FAM_LINEAR_QUAD, principle=W.LAX, g_kind=W.G_QUAD_SHIFT,
+                         A=np.zeros((d, d)), B=np.zeros((d, 4)), a=np.zeros(d))
+    with pytest.raises(hj.HJError) as e:
+        hj.hj_create([spec], hj.opts_from_dict(W.lq_solver()), 0)
+    assert e.value.status == hj.HJ_EINVAL and "d <= 128" in str(e.value)
+
+
+def test_mixed_workload_structure():
+    # twelve problems (three families x d in {8,16,32,100}) with their own
+    # descent constants, N = ceil(64 t), padded rows zero past each row's d
+    from paper_1704_02524_gb300 import workloads as W
+    import numpy as np
+    wl = W.c5_mixed(n_pairs=3000)
+    assert len(wl.problems) == 12
+    assert wl.n_pairs == 3000
+    assert np.array_equal(wl.n_steps, np.ceil(64 * wl.t).astype(np.int32))
+    for q in range(0, wl.nq, 37):
+        p = wl.problems[int(wl.problem_idx[q])]
+        assert np.all(wl.x[q, p.d:] == 0)
+        assert p.solver is not None
+    lq = [p for p in wl.problems if p.family == W.FAM_LINEAR_QUAD]
+    assert all(p.solver["grad"] == "adjoint_cg" and p.n_guesses == 1 for p in lq)
