@@ -291,6 +291,22 @@ hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out);
 hj_status hj_set_tuning(hj_ctx *ctx, int problem, int tpp, int ck_interval);
 
 /*
+ * hj_set_graph -- enable (1) or disable (0) CUDA graphs for hj_solve: with
+ * graphs on, the first hj_solve on a non-NULL stream records its whole
+ * launch sequence (kernels, memsets, events, the forks and joins of the
+ * concurrent per-problem launches) into a CUDA graph and launches it;
+ * later calls with the same q_begin, n_queries, pointers and stream replay
+ * that graph instead of enqueuing ~30-70 operations again (the buffers'
+ * contents may change between calls, their addresses not).  Calls with other
+ * arguments record a new graph; hj_set_tuning and hj_autotune discard it.
+ * The NULL (legacy default) stream cannot be captured: calls on it enqueue
+ * directly.  A graph-launched solve reports its total device time in
+ * hj_last_solve_info (descent_ms, certify_ms and descent_ms_round0 are 0:
+ * events recorded inside a graph cannot be timed).  Off by default.
+ */
+hj_status hj_set_graph(hj_ctx *ctx, int enable);
+
+/*
  * hj_autotune -- choose each problem's launch parameters by measurement (the
  * batching scheme of the solver, not a step of the paper): for every
  * candidate -- the automatic choice (for a linear-quadratic problem that fits

@@ -218,6 +218,20 @@ struct hj_ctx {
     // per-problem descent timing of round 0 (autotuner)
     bool pp_timing = false;
     std::vector<cudaEvent_t> pp_ev;
+    // CUDA graph of the last solve's launch sequence (hj_set_graph)
+    bool use_graph = false;
+    cudaGraphExec_t gexec = nullptr;
+    struct GraphKey {
+        long long q_begin = -1, nq = -1;
+        const void *pidx = nullptr, *x = nullptr, *t = nullptr, *ns = nullptr, *phi = nullptr, *v = nullptr,
+                   *st = nullptr;
+        cudaStream_t s = nullptr;
+        bool operator==(const GraphKey &o) const
+        {
+            return q_begin == o.q_begin && nq == o.nq && pidx == o.pidx && x == o.x && t == o.t && ns == o.ns &&
+                   phi == o.phi && v == o.v && st == o.st && s == o.s;
+        }
+    } gkey;
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
     int n_desc_ev = 0, n_cert_ev = 0;
     long long launches = 0;
@@ -687,6 +701,7 @@ hj_status hj_destroy(hj_ctx *ctx)
                     ctx->pP, ctx->pF, ctx->pR, ctx->vfin, ctx->pcount, ctx->seg_begin, ctx->wl_count, ctx->cursor,
                     ctx->stats, ctx->amb_wl, ctx->amb_count, ctx->best_pid};
     for (void *p : ptrs) cudaFree(p);
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     for (auto a : ctx->aux) cudaStreamDestroy(a);
     for (auto e : ctx->ev_join) cudaEventDestroy(e);
     for (auto e : ctx->pp_ev) cudaEventDestroy(e);
@@ -719,6 +734,20 @@ hj_status hj_set_tuning(hj_ctx *ctx, int problem, int tpp, int ck_interval)
         return fail(ctx, HJ_EUNSUPPORTED, "no kernel for d=%d with %d threads per pair", ctx->desc[problem].d, tpp);
     }
     ctx->ck_interval[problem] = ck_interval;
+    ctx->gkey = hj_ctx::GraphKey();  // launch parameters changed: record a new graph
+    return HJ_OK;
+}
+
+hj_status hj_set_graph(hj_ctx *ctx, int enable)
+{
+    if (!ctx) return HJ_EINVAL;
+    ctx->use_graph = enable != 0;
+    if (!ctx->use_graph && ctx->gexec) {
+        CU(cudaSetDevice(ctx->device));
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    ctx->gkey = hj_ctx::GraphKey();
     return HJ_OK;
 }
 
@@ -912,201 +941,253 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
     }
     ctx->last_tc.assign(ctx->np, 0);
     for (int p = 0; p < ctx->np; ++p) ctx->last_tc[p] = (tc_eligible(ctx, p) && kinds[p] != K_CD) ? 1 : 0;
-    ctx->n_desc_ev = ctx->n_cert_ev = 0;
-    CU(cudaEventRecord(ctx->ev_begin, s));
-    CU(cudaMemsetAsync(ctx->stats, 0, sizeof(unsigned long long) * 8 * ctx->np, s));
-    ctx->launches = 6;  // count, offsets, three scan phases, pair build
-    CU(launch_count(n_queries, pidx, ctx->d_pg, ctx->starts, ctx->pcount, ctx->np, ctx->seg_begin, ctx->wl_count, s));
-    CU(launch_scan(n_queries, ctx->starts, ctx->pair_base, ctx->block_sums, s));
-    CU(launch_build_pairs(n_queries, pidx, ctx->d_pg, ctx->pair_base, ctx->pair_q, ctx->pair_slot, ctx->pair_round,
-                          ctx->trials, ctx->qflags, ctx->seg_begin, ctx->wl_count, ctx->wl, s));
-    // Several problems: each round's descent launches go to auxiliary streams
-    // (tensor-core problems share the first, the lane-group ones take the
-    // others in turn) so that their tails overlap and the tensor-core tile
-    // kernel runs beside the FP32 kernels; the caller's stream joins them.
-    const bool conc = ctx->concurrent && ctx->np > 1 && !ctx->pp_timing;
-    if (conc) {
-        st = ensure_aux(ctx);
-        if (st != HJ_OK) return st;
-    }
-    auto stream_of = [&](int p) -> cudaStream_t {
-        if (!conc) return s;
-        const int na = (int)ctx->aux.size();
-        if (ctx->last_tc[p] || na == 1) return ctx->aux[0];
-        return ctx->aux[1 + p % (na - 1)];
-    };
-    if (ctx->pp_timing)
-        while ((int)ctx->pp_ev.size() < 2 * ctx->np) {
-            cudaEvent_t e;
-            CU(cudaEventCreate(&e));
-            ctx->pp_ev.push_back(e);
-        }
-    for (int round = 0; round <= ctx->opts.max_rounds; ++round) {
-        CU(cudaMemsetAsync(ctx->cursor, 0, sizeof(int32_t) * ctx->np, s));
-        CU(cudaMemsetAsync(ctx->amb_count, 0, sizeof(int32_t) * ctx->np, s));
-        if (ctx->timing) { st = record(ctx, ctx->ev_desc, ctx->n_desc_ev++, s); if (st != HJ_OK) return st; }
+    // everything the solve enqueues on `s` (recorded into a CUDA graph when
+    // hj_set_graph is on)
+    // (events recorded inside a graph cannot be timed: a captured solve keeps
+    // only the begin/end events, recorded around the graph launch)
+    bool capturing = false;
+    auto enqueue = [&]() -> hj_status {
+        ctx->n_desc_ev = ctx->n_cert_ev = 0;
+        const bool timing_saved = ctx->timing;
+        if (capturing) ctx->timing = false;
+        else CU(cudaEventRecord(ctx->ev_begin, s));
+        CU(cudaMemsetAsync(ctx->stats, 0, sizeof(unsigned long long) * 8 * ctx->np, s));
+        ctx->launches = 6;  // count, offsets, three scan phases, pair build
+        CU(launch_count(n_queries, pidx, ctx->d_pg, ctx->starts, ctx->pcount, ctx->np, ctx->seg_begin, ctx->wl_count, s));
+        CU(launch_scan(n_queries, ctx->starts, ctx->pair_base, ctx->block_sums, s));
+        CU(launch_build_pairs(n_queries, pidx, ctx->d_pg, ctx->pair_base, ctx->pair_q, ctx->pair_slot, ctx->pair_round,
+                              ctx->trials, ctx->qflags, ctx->seg_begin, ctx->wl_count, ctx->wl, s));
+        // Several problems: each round's descent launches go to auxiliary streams
+        // (tensor-core problems share the first, the lane-group ones take the
+        // others in turn) so that their tails overlap and the tensor-core tile
+        // kernel runs beside the FP32 kernels; the caller's stream joins them.
+        const bool conc = ctx->concurrent && ctx->np > 1 && !ctx->pp_timing;
         if (conc) {
-            CU(cudaEventRecord(ctx->ev_fork, s));
-            for (cudaStream_t a : ctx->aux) CU(cudaStreamWaitEvent(a, ctx->ev_fork, 0));
+            st = ensure_aux(ctx);
+            if (st != HJ_OK) return st;
         }
-        for (int p = 0; p < ctx->np; ++p) {
-            const KSet &k = kset(ctx, p, c_d[p]);
-            const int kind = kinds[p];
-            const cudaStream_t sp = stream_of(p);
-            if (ctx->pp_timing && round == 0) CU(cudaEventRecord(ctx->pp_ev[2 * p], s));
-            Launch L = kind == K_GD ? k.gd : kind == K_CG ? k.cg : k.cd;
-            const void *fn = kind == K_GD ? k.f_gd : kind == K_CG ? k.f_cg : k.f_cd;
-            auto fill = [&](auto &a) {
-                a.tpp = tpp_d[p];
-                a.problem = p;
-                a.nsteps = n_steps;
-                a.q_begin = q_begin;
-                a.S = solver_dev(ctx->popts[p]);
-                a.S.ck_interval = ctx->ck_interval[p];
-                a.wl = ctx->wl;
-                a.seg_begin = ctx->seg_begin;
-                a.wl_count = ctx->wl_count;
-                a.cursor = ctx->cursor;
-                a.pair_q = ctx->pair_q;
-                a.pair_slot = ctx->pair_slot;
-                a.pair_round = ctx->pair_round;
-                a.iters = ctx->iters;
-                a.flags = ctx->flags;
-                a.stats = ctx->stats + 8 * p;
-                a.pF = ctx->pF;
-                a.pR = ctx->pR;
-                a.pP = ctx->pP;
-                a.amb_wl = ctx->amb_wl;
-                a.amb_count = ctx->amb_count;
-                a.tol = ctx->popts[p].cert_tol;
-            };
-            if (ctx->prec) {
-                DescArgs<double> a{};
-                fill(a);
-                a.P = ctx->dev[p].pd;
-                a.x = (const double *)x; a.t = (const double *)t; a.vfin = (double *)ctx->vfin;
-                CU(L(&a, persistent_grid(ctx, fn), sp));
-            } else if (tc_eligible(ctx, p) && kind != K_CD) {
-                // tensor-core tile kernel: 128 pairs per CTA, one CTA per SM
-                LqTcArgs a = tc_args(ctx, p);
-                fill(a.D);
-                a.D.P = ctx->dev[p].pf;
-                a.D.x = (const float *)x; a.D.t = (const float *)t; a.D.vfin = (float *)ctx->vfin;
-                a.x = (const float *)x; a.t = (const float *)t; a.nsteps = n_steps;
-                a.mode_desc = (kind == K_CG) ? DESC_CG : DESC_GD;
-                CU(lq_tc_launch(LQ_DESC, a, ctx->nsm, tc_smem(ctx, p), sp));
-            } else {
-                DescArgs<float> a{};
-                fill(a);
-                a.P = ctx->dev[p].pf;
-                a.x = (const float *)x; a.t = (const float *)t; a.vfin = (float *)ctx->vfin;
-                CU(L(&a, persistent_grid(ctx, fn), sp));
+        auto stream_of = [&](int p) -> cudaStream_t {
+            if (!conc) return s;
+            const int na = (int)ctx->aux.size();
+            if (ctx->last_tc[p] || na == 1) return ctx->aux[0];
+            return ctx->aux[1 + p % (na - 1)];
+        };
+        if (ctx->pp_timing)
+            while ((int)ctx->pp_ev.size() < 2 * ctx->np) {
+                cudaEvent_t e;
+                CU(cudaEventCreate(&e));
+                ctx->pp_ev.push_back(e);
             }
-            if (ctx->pp_timing && round == 0) CU(cudaEventRecord(ctx->pp_ev[2 * p + 1], s));
+        for (int round = 0; round <= ctx->opts.max_rounds; ++round) {
+            CU(cudaMemsetAsync(ctx->cursor, 0, sizeof(int32_t) * ctx->np, s));
+            CU(cudaMemsetAsync(ctx->amb_count, 0, sizeof(int32_t) * ctx->np, s));
+            if (ctx->timing) { st = record(ctx, ctx->ev_desc, ctx->n_desc_ev++, s); if (st != HJ_OK) return st; }
+            if (conc) {
+                CU(cudaEventRecord(ctx->ev_fork, s));
+                for (cudaStream_t a : ctx->aux) CU(cudaStreamWaitEvent(a, ctx->ev_fork, 0));
+            }
+            for (int p = 0; p < ctx->np; ++p) {
+                const KSet &k = kset(ctx, p, c_d[p]);
+                const int kind = kinds[p];
+                const cudaStream_t sp = stream_of(p);
+                if (ctx->pp_timing && round == 0) CU(cudaEventRecord(ctx->pp_ev[2 * p], s));
+                Launch L = kind == K_GD ? k.gd : kind == K_CG ? k.cg : k.cd;
+                const void *fn = kind == K_GD ? k.f_gd : kind == K_CG ? k.f_cg : k.f_cd;
+                auto fill = [&](auto &a) {
+                    a.tpp = tpp_d[p];
+                    a.problem = p;
+                    a.nsteps = n_steps;
+                    a.q_begin = q_begin;
+                    a.S = solver_dev(ctx->popts[p]);
+                    a.S.ck_interval = ctx->ck_interval[p];
+                    a.wl = ctx->wl;
+                    a.seg_begin = ctx->seg_begin;
+                    a.wl_count = ctx->wl_count;
+                    a.cursor = ctx->cursor;
+                    a.pair_q = ctx->pair_q;
+                    a.pair_slot = ctx->pair_slot;
+                    a.pair_round = ctx->pair_round;
+                    a.iters = ctx->iters;
+                    a.flags = ctx->flags;
+                    a.stats = ctx->stats + 8 * p;
+                    a.pF = ctx->pF;
+                    a.pR = ctx->pR;
+                    a.pP = ctx->pP;
+                    a.amb_wl = ctx->amb_wl;
+                    a.amb_count = ctx->amb_count;
+                    a.tol = ctx->popts[p].cert_tol;
+                };
+                if (ctx->prec) {
+                    DescArgs<double> a{};
+                    fill(a);
+                    a.P = ctx->dev[p].pd;
+                    a.x = (const double *)x; a.t = (const double *)t; a.vfin = (double *)ctx->vfin;
+                    CU(L(&a, persistent_grid(ctx, fn), sp));
+                } else if (tc_eligible(ctx, p) && kind != K_CD) {
+                    // tensor-core tile kernel: 128 pairs per CTA, one CTA per SM
+                    LqTcArgs a = tc_args(ctx, p);
+                    fill(a.D);
+                    a.D.P = ctx->dev[p].pf;
+                    a.D.x = (const float *)x; a.D.t = (const float *)t; a.D.vfin = (float *)ctx->vfin;
+                    a.x = (const float *)x; a.t = (const float *)t; a.nsteps = n_steps;
+                    a.mode_desc = (kind == K_CG) ? DESC_CG : DESC_GD;
+                    CU(lq_tc_launch(LQ_DESC, a, ctx->nsm, tc_smem(ctx, p), sp));
+                } else {
+                    DescArgs<float> a{};
+                    fill(a);
+                    a.P = ctx->dev[p].pf;
+                    a.x = (const float *)x; a.t = (const float *)t; a.vfin = (float *)ctx->vfin;
+                    CU(L(&a, persistent_grid(ctx, fn), sp));
+                }
+                if (ctx->pp_timing && round == 0) CU(cudaEventRecord(ctx->pp_ev[2 * p + 1], s));
+                ctx->launches++;
+            }
+            if (conc)
+                for (size_t i = 0; i < ctx->aux.size(); ++i) {
+                    CU(cudaEventRecord(ctx->ev_join[i], ctx->aux[i]));
+                    CU(cudaStreamWaitEvent(s, ctx->ev_join[i], 0));
+                }
+            if (ctx->timing) { st = record(ctx, ctx->ev_desc, ctx->n_desc_ev++, s); if (st != HJ_OK) return st; }
+            for (int p = 0; p < ctx->np; ++p) {
+                const KSet &k = kset(ctx, p, c_c[p]);
+                auto fill = [&](auto &a) {
+                    a.P = ctx->dev[p].pd;
+                    a.tpp = tpp_c[p];
+                    a.nsteps = n_steps;
+                    a.n_default = ctx->opts.n_steps_default;
+                    a.F = ctx->pF;
+                    a.resid = ctx->pR;
+                    a.pass = ctx->pP;
+                    a.tol = ctx->popts[p].cert_tol;
+                    a.quad = ctx->opts.quad;
+                    a.wl = ctx->amb_wl;
+                    a.seg_begin = ctx->seg_begin;
+                    a.wl_count = ctx->amb_count;
+                    a.problem = p;
+                    a.pair_q = ctx->pair_q;
+                };
+                // FP64 certificate of the starts whose binary32 residual fell in
+                // the band around the tolerance (few): a small grid suffices
+                const long long cap = std::min<long long>((long long)n_queries * ctx->desc[p].n_guesses, 1 << 16);
+                if (ctx->prec) {
+                    CertArgs<double> a{};
+                    fill(a);
+                    a.x = (const double *)x; a.t = (const double *)t; a.v = (const double *)ctx->vfin;
+                    CU(k.cert_pairs(&a, rows_grid(ctx, k.f_cert_pairs, cap, tpp_c[p]), s));
+                } else {
+                    CertArgs<float> a{};
+                    fill(a);
+                    a.x = (const float *)x; a.t = (const float *)t; a.v = (const float *)ctx->vfin;
+                    CU(k.cert_pairs(&a, rows_grid(ctx, k.f_cert_pairs, cap, tpp_c[p]), s));
+                }
+                ctx->launches++;
+            }
+            if (ctx->timing) { st = record(ctx, ctx->ev_cert, ctx->n_cert_ev++, s); if (st != HJ_OK) return st; }
+            const int schedule = round < ctx->opts.max_rounds;
+            if (schedule) CU(cudaMemsetAsync(ctx->wl_count, 0, sizeof(int32_t) * ctx->np, s));
+            SelectArgs a{};
+            a.nq = n_queries;
+            a.pidx = pidx;
+            a.pg = ctx->d_pg;
+            a.pd = ctx->d_pd;
+            a.pprin = ctx->d_pprin;
+            a.ld = ctx->ld;
+            a.pair_base = ctx->pair_base;
+            a.pF = ctx->pF;
+            a.pP = ctx->pP;
+            a.flags = ctx->flags;
+            a.vfin = ctx->vfin;
+            a.pair_round = ctx->pair_round;
+            a.trials = ctx->trials;
+            a.qflags = ctx->qflags;
+            a.round = round;
+            a.schedule = schedule;
+            a.ptrials = ctx->d_ptrials;
+            a.seg_begin = ctx->seg_begin;
+            a.wl_count = ctx->wl_count;
+            a.wl = ctx->wl;
+            a.phi = phi_out;
+            a.v_out = v_out;
+            a.status = status_out;
+            a.best_pid = ctx->best_pid;
+            CU(launch_select(a, ctx->prec, s));
             ctx->launches++;
         }
-        if (conc)
-            for (size_t i = 0; i < ctx->aux.size(); ++i) {
-                CU(cudaEventRecord(ctx->ev_join[i], ctx->aux[i]));
-                CU(cudaStreamWaitEvent(s, ctx->ev_join[i], 0));
-            }
-        if (ctx->timing) { st = record(ctx, ctx->ev_desc, ctx->n_desc_ev++, s); if (st != HJ_OK) return st; }
+        // phi in FP64 at each query's chosen start
         for (int p = 0; p < ctx->np; ++p) {
             const KSet &k = kset(ctx, p, c_c[p]);
             auto fill = [&](auto &a) {
                 a.P = ctx->dev[p].pd;
                 a.tpp = tpp_c[p];
+                a.n = n_queries;
                 a.nsteps = n_steps;
                 a.n_default = ctx->opts.n_steps_default;
-                a.F = ctx->pF;
-                a.resid = ctx->pR;
-                a.pass = ctx->pP;
-                a.tol = ctx->popts[p].cert_tol;
                 a.quad = ctx->opts.quad;
-                a.wl = ctx->amb_wl;
-                a.seg_begin = ctx->seg_begin;
-                a.wl_count = ctx->amb_count;
-                a.problem = p;
-                a.pair_q = ctx->pair_q;
+                a.pidx = pidx;
+                a.pfilter = p;
+                a.best_pid = ctx->best_pid;
+                a.phi = phi_out;
             };
-            // FP64 certificate of the starts whose binary32 residual fell in
-            // the band around the tolerance (few): a small grid suffices
-            const long long cap = std::min<long long>((long long)n_queries * ctx->desc[p].n_guesses, 1 << 16);
             if (ctx->prec) {
                 CertArgs<double> a{};
                 fill(a);
                 a.x = (const double *)x; a.t = (const double *)t; a.v = (const double *)ctx->vfin;
-                CU(k.cert_pairs(&a, rows_grid(ctx, k.f_cert_pairs, cap, tpp_c[p]), s));
+                CU(k.cert_final(&a, rows_grid(ctx, k.f_cert_final, n_queries, tpp_c[p]), s));
             } else {
                 CertArgs<float> a{};
                 fill(a);
                 a.x = (const float *)x; a.t = (const float *)t; a.v = (const float *)ctx->vfin;
-                CU(k.cert_pairs(&a, rows_grid(ctx, k.f_cert_pairs, cap, tpp_c[p]), s));
+                CU(k.cert_final(&a, rows_grid(ctx, k.f_cert_final, n_queries, tpp_c[p]), s));
             }
             ctx->launches++;
         }
         if (ctx->timing) { st = record(ctx, ctx->ev_cert, ctx->n_cert_ev++, s); if (st != HJ_OK) return st; }
-        const int schedule = round < ctx->opts.max_rounds;
-        if (schedule) CU(cudaMemsetAsync(ctx->wl_count, 0, sizeof(int32_t) * ctx->np, s));
-        SelectArgs a{};
-        a.nq = n_queries;
-        a.pidx = pidx;
-        a.pg = ctx->d_pg;
-        a.pd = ctx->d_pd;
-        a.pprin = ctx->d_pprin;
-        a.ld = ctx->ld;
-        a.pair_base = ctx->pair_base;
-        a.pF = ctx->pF;
-        a.pP = ctx->pP;
-        a.flags = ctx->flags;
-        a.vfin = ctx->vfin;
-        a.pair_round = ctx->pair_round;
-        a.trials = ctx->trials;
-        a.qflags = ctx->qflags;
-        a.round = round;
-        a.schedule = schedule;
-        a.ptrials = ctx->d_ptrials;
-        a.seg_begin = ctx->seg_begin;
-        a.wl_count = ctx->wl_count;
-        a.wl = ctx->wl;
-        a.phi = phi_out;
-        a.v_out = v_out;
-        a.status = status_out;
-        a.best_pid = ctx->best_pid;
-        CU(launch_select(a, ctx->prec, s));
-        ctx->launches++;
-    }
-    // phi in FP64 at each query's chosen start
-    for (int p = 0; p < ctx->np; ++p) {
-        const KSet &k = kset(ctx, p, c_c[p]);
-        auto fill = [&](auto &a) {
-            a.P = ctx->dev[p].pd;
-            a.tpp = tpp_c[p];
-            a.n = n_queries;
-            a.nsteps = n_steps;
-            a.n_default = ctx->opts.n_steps_default;
-            a.quad = ctx->opts.quad;
-            a.pidx = pidx;
-            a.pfilter = p;
-            a.best_pid = ctx->best_pid;
-            a.phi = phi_out;
-        };
-        if (ctx->prec) {
-            CertArgs<double> a{};
-            fill(a);
-            a.x = (const double *)x; a.t = (const double *)t; a.v = (const double *)ctx->vfin;
-            CU(k.cert_final(&a, rows_grid(ctx, k.f_cert_final, n_queries, tpp_c[p]), s));
-        } else {
-            CertArgs<float> a{};
-            fill(a);
-            a.x = (const float *)x; a.t = (const float *)t; a.v = (const float *)ctx->vfin;
-            CU(k.cert_final(&a, rows_grid(ctx, k.f_cert_final, n_queries, tpp_c[p]), s));
+        ctx->timing = timing_saved;
+        if (!capturing) CU(cudaEventRecord(ctx->ev_end, s));
+        return HJ_OK;
+    };
+    if (ctx->use_graph && s != nullptr && !ctx->pp_timing) {
+        hj_ctx::GraphKey key;
+        key.q_begin = q_begin; key.nq = n_queries; key.pidx = pidx; key.x = x; key.t = t; key.ns = n_steps;
+        key.phi = phi_out; key.v = v_out; key.st = status_out; key.s = s;
+        if (ctx->gexec && key == ctx->gkey) {
+            CU(cudaEventRecord(ctx->ev_begin, s));
+            CU(cudaGraphLaunch(ctx->gexec, s));
+            CU(cudaEventRecord(ctx->ev_end, s));
+            return HJ_OK;
         }
-        ctx->launches++;
+        if (ctx->gexec) {
+            cudaGraphExecDestroy(ctx->gexec);
+            ctx->gexec = nullptr;
+        }
+        if (ctx->np > 1 && ctx->concurrent) {
+            st = ensure_aux(ctx);
+            if (st != HJ_OK) return st;
+        }
+        CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+        capturing = true;
+        st = enqueue();
+        capturing = false;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (st != HJ_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return fail(ctx, HJ_ECUDA, "graph capture of hj_solve: %s", cudaGetErrorString(e));
+        const cudaError_t e2 = cudaGraphInstantiate(&ctx->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e2 != cudaSuccess) {
+            ctx->gexec = nullptr;
+            return fail(ctx, HJ_ECUDA, "graph instantiation of hj_solve: %s", cudaGetErrorString(e2));
+        }
+        ctx->gkey = key;
+        CU(cudaEventRecord(ctx->ev_begin, s));
+        CU(cudaGraphLaunch(ctx->gexec, s));
+        CU(cudaEventRecord(ctx->ev_end, s));
+        return HJ_OK;
     }
-    if (ctx->timing) { st = record(ctx, ctx->ev_cert, ctx->n_cert_ev++, s); if (st != HJ_OK) return st; }
-    CU(cudaEventRecord(ctx->ev_end, s));
-    return HJ_OK;
+    return enqueue();
 }
 
 hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out)
@@ -1247,6 +1328,7 @@ hj_status hj_autotune(hj_ctx *ctx, int64_t n_queries, const int32_t *problem_idx
         ctx->tpp_override[p] = best[p];
         if (tpp_out) tpp_out[p] = best[p];
     }
+    ctx->gkey = hj_ctx::GraphKey();
     return HJ_OK;
 }
 

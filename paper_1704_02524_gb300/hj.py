@@ -32,7 +32,8 @@ HJ_PREC_FP32, HJ_PREC_FP64 = 0, 1
 HJ_ST_CERTIFIED, HJ_ST_MAX_ITERS, HJ_ST_NONFINITE, HJ_ST_RESEEDED = 1, 2, 4, 8
 
 EXPORTED = ("hj_create", "hj_destroy", "hj_eval_functional", "hj_grad", "hj_certify", "hj_solve", "hj_guesses",
-            "hj_last_solve_info", "hj_set_tuning", "hj_last_error", "hj_solve_noalloc", "hj_autotune")
+            "hj_last_solve_info", "hj_set_tuning", "hj_last_error", "hj_solve_noalloc", "hj_autotune",
+            "hj_set_graph")
 
 
 class hj_solver_opts(C.Structure):
@@ -84,6 +85,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.hj_last_solve_info.argtypes = [vp, C.POINTER(hj_solve_info)]
     lib.hj_set_tuning.argtypes = [vp, C.c_int, C.c_int, C.c_int]
     lib.hj_autotune.argtypes = [vp, i64, vp, vp, vp, vp, C.c_int, i32p, vp]
+    lib.hj_set_graph.argtypes = [vp, C.c_int]
     lib.hj_last_error.argtypes = [vp]
     lib.hj_last_error.restype = C.c_char_p
     for name in EXPORTED:
@@ -289,6 +291,10 @@ def hj_last_solve_info(ctx: Context) -> Dict:
 
 def hj_set_tuning(ctx: Context, problem: int, tpp: int = 0, ck_interval: int = 0):
     _check(ctx, load_library().hj_set_tuning(ctx.handle, problem, tpp, ck_interval))
+
+
+def hj_set_graph(ctx: Context, enable: bool = True):
+    _check(ctx, load_library().hj_set_graph(ctx.handle, 1 if enable else 0))
 
 
 def hj_autotune(ctx: Context, x: torch.Tensor, t: torch.Tensor, n_steps: Optional[torch.Tensor] = None,

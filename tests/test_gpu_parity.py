@@ -355,3 +355,33 @@ def test_autotuned_mixed_solve_still_matches_oracle(hj):
     print("autotuned threads per pair:", chosen)
     assert len(chosen) == len(w.problems) and all(c in (0, 1, 2, 4, 8, 16, 32) for c in chosen)
     _check_mixed(w, phi, st, ref, stable)
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_solve_through_a_cuda_graph_matches_direct_solves(hj, mixed):
+    # hj_set_graph: the first solve records the launch sequence (with the
+    # forked per-problem streams of a mixed batch) and launches it, the next
+    # one with the same buffers replays it; both equal direct solves bit for bit
+    w = _mixed_sample(per_problem=6) if mixed else W.c3_smooth_nonconvex(nq=200)
+    opts = hj.opts_from_dict(w.solver, hj.HJ_PREC_FP32, 64)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g_ctx, d_ctx = hj.hj_create(w.problems, opts, 0), hj.hj_create(w.problems, opts, 0)
+        hj.hj_set_graph(g_ctx, True)
+        x = _t(w.x, torch.float32)
+        t, ns = _t(w.t, torch.float32), _t(w.n_steps, torch.int32)
+        pi = _t(w.problem_idx, torch.int32) if mixed else None
+        out = (torch.empty(w.nq, dtype=torch.float64, device=DEV), torch.zeros_like(x),
+               torch.empty(w.nq, dtype=torch.int32, device=DEV))
+        rng = np.random.default_rng(1)
+        for call in range(3):
+            if call:
+                x.copy_(_t(W.f32(np.where(w.x != 0, w.x + 0.05 * rng.standard_normal(w.x.shape), 0.0)), torch.float32))
+            hj.hj_solve(g_ctx, x, t, ns, pi, 0, out)
+            ref = hj.hj_solve(d_ctx, x, t, ns, pi)
+            stream.synchronize()
+            assert torch.equal(out[0], ref[0]) and torch.equal(out[2], ref[2]) and torch.equal(out[1], ref[1])
+            info = hj.hj_last_solve_info(g_ctx)
+            assert info["n_queries"] == w.nq and info["total_ms"] > 0
+        g_ctx.close()
+        d_ctx.close()
