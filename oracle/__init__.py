@@ -74,7 +74,7 @@ class _Opts(C.Structure):
                 ("eps", C.c_double), ("adapt", C.c_int), ("grow", C.c_double), ("shrink", C.c_double),
                 ("step_max", C.c_double), ("n_guesses", C.c_int), ("max_trials", C.c_int),
                 ("max_rounds", C.c_int), ("seed", C.c_uint64), ("guess_dist", C.c_int),
-                ("cert_tol", C.c_double)]
+                ("cert_tol", C.c_double), ("coarse_div", C.c_int), ("coarse_eps", C.c_double)]
 
 
 _DP = C.POINTER(C.c_double)
@@ -163,12 +163,14 @@ class Opts:
     seed: int = 0
     guess_dist: int = 0
     cert_tol: float = 1e-3
+    coarse_div: int = 1
+    coarse_eps: float = 1e-4
 
     def c(self) -> _Opts:
         return _Opts(self.quad, self.descent, self.grad, self.fd_h, self.step, self.max_iters,
                      self.halving_period, self.eps, self.adapt, self.grow, self.shrink, self.step_max,
                      self.n_guesses, self.max_trials, self.max_rounds, self.seed & (2**64 - 1),
-                     self.guess_dist, self.cert_tol)
+                     self.guess_dist, self.cert_tol, self.coarse_div, self.coarse_eps)
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

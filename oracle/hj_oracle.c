@@ -93,6 +93,10 @@ typedef struct {
     uint64_t seed;       /* Philox key                                           */
     int guess_dist;      /* 0: U[-2,2]^d, 1: Irwin-Hall(12) approximate N(0,1)   */
     double cert_tol;     /* certificate tolerance tau                            */
+    int coarse_div;      /* > 1: descend first on the functional with N/coarse_div */
+                         /* RK4 steps until moves < coarse_eps, then on the full  */
+                         /* functional from there (gradient forms only)           */
+    double coarse_eps;
 } orc_opts;
 
 /* ------------------------------------------------------------------------ */
@@ -579,6 +583,22 @@ int orc_descend(const orc_problem *P, const orc_opts *O, const double *x, double
     int d = P->d;
     *hit_cap = 0;
     *nonfinite = 0;
+    if (O->coarse_div > 1 && O->descent != DESC_CD) {
+        /* continuation in the step size: the same descent, first on the
+         * functional discretised with N / coarse_div steps (stopping at moves
+         * < coarse_eps), then, with its step control started afresh, on the
+         * functional with N steps from the point reached */
+        orc_opts C = *O, F = *O;
+        C.coarse_div = F.coarse_div = 1;
+        C.eps = O->coarse_eps;
+        int Nc = N / O->coarse_div;
+        if (Nc < 1) Nc = 1;
+        int cap1 = 0, nf1 = 0;
+        int it1 = orc_descend(P, &C, x, t, Nc, v, &cap1, &nf1);
+        if (nf1) { *nonfinite = 1; return it1; }
+        int it2 = orc_descend(P, &F, x, t, N, v, hit_cap, nonfinite);
+        return it1 + it2;
+    }
     if (O->descent == DESC_CG) return descend_cg(P, O, x, t, N, v, hit_cap, nonfinite);
     if (O->descent == DESC_CD) {
         double alpha[ORC_DMAX], dprev[ORC_DMAX];

@@ -835,27 +835,35 @@ void lq_tc_matrices(const LqTcGeom &g, const double *A, const double *B, std::ve
 size_t lq_tc_vec_slot(const LqTcGeom &g) { return (size_t)6 * g.dp * TCR; }
 size_t lq_tc_ybuf_slot(const LqTcGeom &g) { return (size_t)MAX_N * 4 * g.mp * TCR; }
 
+// The dynamic shared-memory limit of each kernel is raised once per device
+// (raising it again while an instance runs on another stream would wait for
+// that instance).
+static size_t g_smem_set[64][3];
+
+template <int MODE>
+static cudaError_t launch_mode(const LqTcArgs &a, int grid, size_t smem, cudaStream_t s)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (smem > g_smem_set[dev][MODE]) {
+        e = cudaFuncSetAttribute(k_lq_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LQ_TC_SMEM_MAX);
+        if (e != cudaSuccess) return e;
+        g_smem_set[dev][MODE] = LQ_TC_SMEM_MAX;
+    }
+    k_lq_tc<MODE><<<grid, TCT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t lq_tc_launch(int mode, const LqTcArgs &a, int grid, size_t smem, cudaStream_t s)
 {
-    cudaError_t e;
+    if (smem > LQ_TC_SMEM_MAX) return cudaErrorInvalidValue;
     switch (mode) {
-    case LQ_ROWS_EVAL:
-        e = cudaFuncSetAttribute(k_lq_tc<LQ_ROWS_EVAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_lq_tc<LQ_ROWS_EVAL><<<grid, TCT, smem, s>>>(a);
-        break;
-    case LQ_ROWS_GRAD:
-        e = cudaFuncSetAttribute(k_lq_tc<LQ_ROWS_GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_lq_tc<LQ_ROWS_GRAD><<<grid, TCT, smem, s>>>(a);
-        break;
-    default:
-        e = cudaFuncSetAttribute(k_lq_tc<LQ_DESC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_lq_tc<LQ_DESC><<<grid, TCT, smem, s>>>(a);
-        break;
+    case LQ_ROWS_EVAL: return launch_mode<LQ_ROWS_EVAL>(a, grid, smem, s);
+    case LQ_ROWS_GRAD: return launch_mode<LQ_ROWS_GRAD>(a, grid, smem, s);
+    default: return launch_mode<LQ_DESC>(a, grid, smem, s);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace hjd

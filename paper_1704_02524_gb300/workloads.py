@@ -115,7 +115,7 @@ def solver_constants(**over) -> Dict:
     {1.2, 1.5, 2}, shrink in {0.3, 0.5}, alpha_0 in {0.05, 0.2}."""
     c = dict(grad="adjoint", quad="rk4", fd_h=2.0 ** -10, step=0.05, max_iters=200, halving_period=0,
              eps=1e-5, adapt=1, grow=1.2, shrink=0.5, step_max=1.0, n_guesses=1, max_trials=20,
-             max_rounds=4, seed=0x5EED1704, guess_dist=0, cert_tol=1e-3)
+             max_rounds=4, seed=0x5EED1704, guess_dist=0, cert_tol=1e-3, coarse_div=1, coarse_eps=1e-4)
     c.update(over)
     return c
 

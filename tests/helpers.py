@@ -25,7 +25,8 @@ def oracle_opts(solver: dict, n_guesses: int) -> O.Opts:
                   adapt=solver["adapt"], grow=solver["grow"], shrink=solver["shrink"],
                   step_max=solver["step_max"], n_guesses=n_guesses, max_trials=solver["max_trials"],
                   max_rounds=solver["max_rounds"], seed=solver["seed"], guess_dist=solver["guess_dist"],
-                  cert_tol=solver["cert_tol"])
+                  cert_tol=solver["cert_tol"], coarse_div=solver.get("coarse_div", 1),
+                  coarse_eps=solver.get("coarse_eps", 1e-4))
 
 
 def rel_err(a, b):

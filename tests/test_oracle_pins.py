@@ -294,6 +294,38 @@ def test_gradient_descent_rule_on_closed_form():
     assert np.abs(v - vr).max() < 1e-10
 
 
+def test_coarse_to_fine_descent_is_two_descents_in_sequence():
+    # continuation in the step size: the descent on the N/coarse_div-step
+    # functional (stopping at moves < coarse_eps), then the descent on the
+    # N-step functional from there, its step control started afresh.  For
+    # H = |p|^2/2 and g = |x|^2/2, F(v) = |x - t v|^2/2 + t|v|^2/2 for any N,
+    # so both stages follow the closed-form gradient
+    P = _p_quad_iso(d=2)
+    x, t = np.array([1.2, -0.7]), 0.5
+    kw = dict(descent=O.DESC_GD, grad=O.GRAD_ADJOINT, step=0.9, max_iters=60, adapt=1, grow=1.3, shrink=0.5,
+              step_max=3.0)
+    v0 = np.array([2.0, -2.0])
+    grad = lambda v: -t * (x - t * v) + t * v
+    O2 = O.Opts(eps=1e-12, coarse_div=4, coarse_eps=1e-3, **kw)
+    v, it, cap, nf = O.descend(P, O2, x, t, 12, v0)
+    v1, it1 = _gd_rule_reference(grad, v0, O.Opts(eps=1e-3, **kw))
+    v2, it2 = _gd_rule_reference(grad, v1, O.Opts(eps=1e-12, **kw))
+    assert it == it1 + it2 and not nf
+    assert np.abs(v - v2).max() < 1e-10
+    # on a state-dependent problem both descents reach the same discrete
+    # minimiser of the N-step functional (stationary: gradient ~ 0 there)
+    Pn = O.Problem(d=3, family=O.FAM_SPEED_QUAD, principle=O.LAX, g_kind=O.G_QUAD_SHIFT,
+                   w=np.array([0.4, -0.3, 0.2]), a=np.array([0.1, 0.2, -0.3]))
+    xs = np.array([0.7, -0.4, 0.3])
+    one = O.Opts(eps=1e-10, **dict(kw, step=0.1, max_iters=400))
+    two = O.Opts(eps=1e-10, coarse_div=4, coarse_eps=1e-4, **dict(kw, step=0.1, max_iters=400))
+    va, *_ = O.descend(Pn, one, xs, 0.8, 32, np.zeros(3))
+    vb, *_ = O.descend(Pn, two, xs, 0.8, 32, np.zeros(3))
+    assert np.abs(va - vb).max() < 1e-7
+    _, g = O.gradient(Pn, xs, 0.8, 32, vb)
+    assert np.abs(g).max() < 1e-7
+
+
 def _cg_rule_reference(grad, v0, step, step_max, iters):
     """Polak-Ribiere+ conjugate gradients with one secant line search per
     iteration, stepped by hand (the rule the oracle's DESC_CG states)."""
