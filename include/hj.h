@@ -149,6 +149,13 @@ typedef struct {
     double cert_tol;
     hj_precision precision;
     int kahan;
+    int coarse_div;     /* gradient and CG descents: > 1 descends first on the
+                           functional with N / coarse_div RK4 steps until every
+                           move is < coarse_eps (or max_iters), then, with the
+                           step control started afresh, on the N-step functional
+                           from there (continuation in the step size; iterations
+                           of both levels are counted); 1 = off                   */
+    double coarse_eps;
 } hj_solver_opts;
 
 /*

@@ -309,6 +309,10 @@ hj_status validate_opts(hj_ctx *ctx, const hj_solver_opts &o)
         return fail(ctx, HJ_EINVAL, "fd_h must be > 0");
     if (o.grad == HJ_GRAD_ADJOINT_CG && !(o.step_max > 0))
         return fail(ctx, HJ_EINVAL, "conjugate gradients need step_max > 0");
+    if (o.coarse_div < 1 || o.coarse_div > 64) return fail(ctx, HJ_EINVAL, "coarse_div=%d outside [1, 64]", o.coarse_div);
+    if (o.coarse_div > 1 && o.grad != HJ_GRAD_ADJOINT && o.grad != HJ_GRAD_ADJOINT_CG)
+        return fail(ctx, HJ_EINVAL, "coarse_div > 1 needs a gradient descent (adjoint or adjoint CG)");
+    if (o.coarse_div > 1 && !(o.coarse_eps >= 0)) return fail(ctx, HJ_EINVAL, "coarse_eps must be >= 0");
     if (!(o.step > 0) || !std::isfinite(o.step)) return fail(ctx, HJ_EINVAL, "step must be finite and > 0");
     if (o.max_iters < 0) return fail(ctx, HJ_EINVAL, "max_iters must be >= 0");
     if (o.halving_period < 0) return fail(ctx, HJ_EINVAL, "halving_period must be >= 0");
@@ -394,7 +398,8 @@ void *as_ptr(T *p) { return (void *)p; }
 // problem that fits it, RK4 quadrature, no lane-group tuning override.
 bool tc_eligible(const hj_ctx *ctx, int p)
 {
-    return ctx->prec == 0 && ctx->dev[p].tc && ctx->tpp_override[p] == 0 && ctx->opts.quad == HJ_QUAD_RK4;
+    return ctx->prec == 0 && ctx->dev[p].tc && ctx->tpp_override[p] == 0 && ctx->opts.quad == HJ_QUAD_RK4 &&
+           ctx->popts[p].coarse_div <= 1;
 }
 
 hj_status ensure_tc_scratch(hj_ctx *ctx, int p)
@@ -503,6 +508,8 @@ SolverDev solver_dev(const hj_solver_opts &o)
     S.step_max = o.step_max;
     S.cert_tol = o.cert_tol;
     S.seed = o.seed;
+    S.coarse_div = o.coarse_div;
+    S.coarse_eps = o.coarse_eps;
     return S;
 }
 
@@ -1022,6 +1029,13 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                     fill(a);
                     a.P = ctx->dev[p].pd;
                     a.x = (const double *)x; a.t = (const double *)t; a.vfin = (double *)ctx->vfin;
+                    if (kind != K_CD && ctx->popts[p].coarse_div > 1) {
+                        a.phase = 1;
+                        CU(L(&a, persistent_grid(ctx, fn), sp));
+                        CU(cudaMemsetAsync(ctx->cursor + p, 0, sizeof(int32_t), sp));
+                        a.phase = 2;
+                        ctx->launches++;
+                    }
                     CU(L(&a, persistent_grid(ctx, fn), sp));
                 } else if (tc_eligible(ctx, p) && kind != K_CD) {
                     // tensor-core tile kernel: 128 pairs per CTA, one CTA per SM
@@ -1037,6 +1051,14 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                     fill(a);
                     a.P = ctx->dev[p].pf;
                     a.x = (const float *)x; a.t = (const float *)t; a.vfin = (float *)ctx->vfin;
+                    if (kind != K_CD && ctx->popts[p].coarse_div > 1) {
+                        // coarse-to-fine as two launches, so that every warp runs one step count
+                        a.phase = 1;
+                        CU(L(&a, persistent_grid(ctx, fn), sp));
+                        CU(cudaMemsetAsync(ctx->cursor + p, 0, sizeof(int32_t), sp));
+                        a.phase = 2;
+                        ctx->launches++;
+                    }
                     CU(L(&a, persistent_grid(ctx, fn), sp));
                 }
                 if (ctx->pp_timing && round == 0) CU(cudaEventRecord(ctx->pp_ev[2 * p + 1], s));
@@ -1482,17 +1504,30 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
                 a.amb_count = L.amb_count;
                 a.tol = ctx->popts[p].cert_tol;
             };
+            const bool two = kind != K_CD && ctx->popts[p].coarse_div > 1;
             if (ctx->prec) {
                 DescArgs<double> a{};
                 fill(a);
                 a.P = ctx->dev[p].pd;
                 a.x = (const double *)x; a.t = (const double *)t; a.vfin = (double *)L.vfin;
+                if (two) {
+                    a.phase = 1;
+                    CU(Lk(&a, persistent_grid(ctx, fn), s));
+                    CU(cudaMemsetAsync(L.cursor + p, 0, sizeof(int32_t), s));
+                    a.phase = 2;
+                }
                 CU(Lk(&a, persistent_grid(ctx, fn), s));
             } else {
                 DescArgs<float> a{};
                 fill(a);
                 a.P = ctx->dev[p].pf;
                 a.x = (const float *)x; a.t = (const float *)t; a.vfin = (float *)L.vfin;
+                if (two) {
+                    a.phase = 1;
+                    CU(Lk(&a, persistent_grid(ctx, fn), s));
+                    CU(cudaMemsetAsync(L.cursor + p, 0, sizeof(int32_t), s));
+                    a.phase = 2;
+                }
                 CU(Lk(&a, persistent_grid(ctx, fn), s));
             }
         }

@@ -50,7 +50,8 @@ struct ProbDev {
 struct SolverDev {
     int quad, grad, max_iters, halving_period, adapt, max_trials, max_rounds, guess_dist, kahan, n_default;
     int ck_interval;  // adjoint checkpoint interval K (0: automatic)
-    double fd_h, step, eps, grow, shrink, step_max, cert_tol;
+    int coarse_div;   // > 1: coarse-to-fine descent (gradient forms)
+    double fd_h, step, eps, grow, shrink, step_max, cert_tol, coarse_eps;
     unsigned long long seed;
 };
 

@@ -79,6 +79,10 @@ struct DescArgs {
     uint8_t *pP;
     int32_t *amb_wl, *amb_count;
     double tol;
+    // coarse-to-fine as two launches per round: 0 the whole descent, 1 the
+    // coarse level only (from the Philox start; writes v to vfin, no
+    // certificate), 2 the fine level from the v in vfin
+    int phase;
     unsigned long long *stats;  // [0] iterations [1] functional evals [2] gradients [3] forward RK4 steps
                                 // [4] adjoint steps [5] pairs [6] sum of N over pairs
                                 // [7] RK4 steps of the in-kernel certificate
@@ -272,6 +276,9 @@ __global__ void __launch_bounds__(BLOCK, (desc_min_blocks<C, MODE>())) k_desc(De
     bool active = false, exhausted = false;
     long long pid = 0, q = 0;
     int N = 1, it = 0, count = 0, kper = 0, bad = 0;
+    // the coarse launch descends on the N / coarse_div-step functional
+    const bool coarse = (MODE != DESC_CD) && a.phase == 1;
+    int Ncur = 1;
     T t = 0;
     T x[C], v[C], alpha[C], prev[C];
     // conjugate gradients: direction, phase (0: gradient at v, 1: probe),
@@ -299,15 +306,18 @@ __global__ void __launch_bounds__(BLOCK, (desc_min_blocks<C, MODE>())) k_desc(De
                 N = a.nsteps ? a.nsteps[q] : a.S.n_default;
                 t = a.t[q];
                 load_row<T, C>(g, a.x + q * a.P.ld, d, x);
+                if (a.phase == 2) load_row<T, C>(g, a.vfin + pid * a.P.ld, d, v);  // the coarse level's v
 #pragma unroll
                 for (int k = 0; k < C; ++k) {
                     int i = g.lane + k * g.tpp;
-                    v[k] = (i < d) ? start_component<T>(a.S.seed, a.q_begin + q, slot, round, i, a.S.guess_dist)
-                                   : (T)0;
+                    if (a.phase != 2)
+                        v[k] = (i < d) ? start_component<T>(a.S.seed, a.q_begin + q, slot, round, i, a.S.guess_dist)
+                                       : (T)0;
                     alpha[k] = (T)a.S.step;
                     prev[k] = 0;
                 }
                 it = count = kper = bad = phase = 0;
+                Ncur = coarse ? max(1, N / a.S.coarse_div) : N;
                 active = true;
             }
         }
@@ -316,16 +326,17 @@ __global__ void __launch_bounds__(BLOCK, (desc_min_blocks<C, MODE>())) k_desc(De
 
         // ---- one iteration ----------------------------------------------------
         bool stop = (it >= a.S.max_iters), conv = false;
+        const T eps_lvl = coarse ? (T)a.S.coarse_eps : eps_stop;
         if (!stop) {
             if constexpr (MODE == DESC_CG) {
                 // one gradient per pass: at v (phase 0) or at the probe v + sig dir
                 T pt[C], gr[C];
 #pragma unroll
                 for (int k = 0; k < C; ++k) pt[k] = phase ? fma(sig, dir[k], v[k]) : v[k];
-                gradient<T, C, FAM, PR>(g, tp, a.P, a.S.quad, a.S.kahan, a.S.ck_interval, x, pt, t, N, gr, ck, seg);
+                gradient<T, C, FAM, PR>(g, tp, a.P, a.S.quad, a.S.kahan, a.S.ck_interval, x, pt, t, Ncur, gr, ck, seg);
                 n_g++;
-                n_rk += N;
-                n_adj += N;
+                n_rk += Ncur;
+                n_adj += Ncur;
                 if (phase == 0) {
                     // new direction (Polak-Ribiere+, restart when not descending)
                     if (it == 0) {
@@ -381,16 +392,16 @@ __global__ void __launch_bounds__(BLOCK, (desc_min_blocks<C, MODE>())) k_desc(De
                     else {
 #pragma unroll
                         for (int k = 0; k < C; ++k) v[k] = fma(al, dir[k], v[k]);
-                        if (al * dn < eps_stop) conv = stop = true;
+                        if (al * dn < eps_lvl) conv = stop = true;
                         phase = 0;
                     }
                 }
             } else if (GD) {
                 T gr[C];
-                gradient<T, C, FAM, PR>(g, tp, a.P, a.S.quad, a.S.kahan, a.S.ck_interval, x, v, t, N, gr, ck, seg);
+                gradient<T, C, FAM, PR>(g, tp, a.P, a.S.quad, a.S.kahan, a.S.ck_interval, x, v, t, Ncur, gr, ck, seg);
                 n_g++;
-                n_rk += N;
-                n_adj += N;
+                n_rk += Ncur;
+                n_adj += Ncur;
                 T big = 0;
                 bool fin = true;
 #pragma unroll
@@ -413,7 +424,7 @@ __global__ void __launch_bounds__(BLOCK, (desc_min_blocks<C, MODE>())) k_desc(De
 #pragma unroll
                     for (int k = 0; k < C; ++k) alpha[k] *= (T)0.5;
                 }
-                if (big < eps_stop) conv = stop = true;
+                if (big < eps_lvl) conv = stop = true;
             } else {
                 const int jc = it % d;
                 const int owner = jc % a.tpp, comp = jc / a.tpp;
@@ -468,7 +479,16 @@ __global__ void __launch_bounds__(BLOCK, (desc_min_blocks<C, MODE>())) k_desc(De
             if (it >= a.S.max_iters) stop = true;
         }
         // ---- finished pair: certificate at the final v, then write it out -----
-        if (stop) {
+        if (stop && a.phase == 1) {
+            // coarse level done: hand v to the fine launch
+            n_it += it;
+            store_row<T, C>(g, a.vfin + pid * a.P.ld, d, v);
+            if (g.lane == 0) {
+                a.iters[pid] = it;
+                a.flags[pid] = (uint8_t)(bad << 1);
+            }
+            active = false;
+        } else if (stop) {
             const int cap = (!conv && !bad) ? 1 : 0;
             n_it += it;
             n_pairs++;
@@ -481,8 +501,10 @@ __global__ void __launch_bounds__(BLOCK, (desc_min_blocks<C, MODE>())) k_desc(De
             n_cert += N;
             store_row<T, C>(g, a.vfin + pid * a.P.ld, d, v);
             if (g.lane == 0) {
-                a.iters[pid] = it;
-                a.flags[pid] = (uint8_t)(cap | (bad << 1));
+                const int prior = (a.phase == 2) ? a.iters[pid] : 0;
+                const uint8_t fprior = (a.phase == 2) ? (uint8_t)(a.flags[pid] & 2) : (uint8_t)0;
+                a.iters[pid] = prior + it;
+                a.flags[pid] = (uint8_t)(cap | (bad << 1) | fprior);
                 const bool fin = finite_(F) && finite_(r);
                 uint8_t pass;
                 if (!fin) pass = 0;

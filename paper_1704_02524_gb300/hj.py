@@ -41,7 +41,8 @@ class hj_solver_opts(C.Structure):
                 ("step", C.c_double), ("max_iters", C.c_int), ("halving_period", C.c_int), ("eps", C.c_double),
                 ("adapt", C.c_int), ("grow", C.c_double), ("shrink", C.c_double), ("step_max", C.c_double),
                 ("n_guesses", C.c_int), ("max_trials", C.c_int), ("max_rounds", C.c_int), ("seed", C.c_uint64),
-                ("guess_dist", C.c_int), ("cert_tol", C.c_double), ("precision", C.c_int), ("kahan", C.c_int)]
+                ("guess_dist", C.c_int), ("cert_tol", C.c_double), ("precision", C.c_int), ("kahan", C.c_int),
+                ("coarse_div", C.c_int), ("coarse_eps", C.c_double)]
 
 
 class hj_problem_desc(C.Structure):
@@ -162,7 +163,8 @@ def opts_from_dict(solver: Dict, precision: int = HJ_PREC_FP32, n_steps_default:
                           solver["step"], solver["max_iters"], solver["halving_period"], solver["eps"],
                           solver["adapt"], solver["grow"], solver["shrink"], solver["step_max"],
                           solver["n_guesses"], solver["max_trials"], solver["max_rounds"],
-                          solver["seed"] & (2 ** 64 - 1), solver["guess_dist"], solver["cert_tol"], precision, kahan)
+                          solver["seed"] & (2 ** 64 - 1), solver["guess_dist"], solver["cert_tol"], precision, kahan,
+                          solver.get("coarse_div", 1), solver.get("coarse_eps", 1e-4))
 
 
 def hj_create(problems: Sequence, opts: hj_solver_opts, device: int = 0) -> Context:

@@ -112,11 +112,17 @@ def solver_constants(**over) -> Dict:
     2.2e-8 (relative) of the eps = 1e-8 solution; 3e-5 lets one query stop in
     a worse minimum (9e-2).  The step-control constants (alpha_0 = 0.05,
     grow 1.2, shrink 0.5) were the only robust ones of a grid over grow in
-    {1.2, 1.5, 2}, shrink in {0.3, 0.5}, alpha_0 in {0.05, 0.2}."""
+    {1.2, 1.5, 2}, shrink in {0.3, 0.5}, alpha_0 in {0.05, 0.2}.
+    Coarse-to-fine (coarse_div = 4, coarse_eps = 1e-4: the descent first on
+    the N/4-step functional, then on the N-step one) took 0.61x the oracle's
+    time on 128 queries of the d=20 workload and 0.23x on the d=10 one, with
+    phi within 2e-8 and every query still certified."""
     c = dict(grad="adjoint", quad="rk4", fd_h=2.0 ** -10, step=0.05, max_iters=200, halving_period=0,
              eps=1e-5, adapt=1, grow=1.2, shrink=0.5, step_max=1.0, n_guesses=1, max_trials=20,
-             max_rounds=4, seed=0x5EED1704, guess_dist=0, cert_tol=1e-3, coarse_div=1, coarse_eps=1e-4)
+             max_rounds=4, seed=0x5EED1704, guess_dist=0, cert_tol=1e-3, coarse_div=4, coarse_eps=1e-4)
     c.update(over)
+    if c["grad"] not in ("adjoint", "adjoint_cg") and "coarse_div" not in over:
+        c["coarse_div"] = 1  # coarse-to-fine is a gradient-descent option
     return c
 
 
@@ -207,7 +213,7 @@ def lq_solver(**over) -> Dict:
     stays far above any useful tolerance there (the flat directions of F are
     not flat for p(0) - grad g(gamma(0))), on the oracle as on the GPU."""
     c = solver_constants(grad="adjoint_cg", step=1.0, step_max=100.0, eps=0.0, max_iters=100, n_guesses=1,
-                         max_trials=1, max_rounds=0)
+                         max_trials=1, max_rounds=0, coarse_div=1)
     c.update(over)
     return c
 
