@@ -50,11 +50,12 @@ WORKLOADS = {
 CPU_SAMPLE = 64          # queries of the oracle timing sample (cpu_baseline)
 REF_SAMPLE = 64          # queries per step of the reference arm
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) of the round-0 descent launch of a 4,096-query
-# case, from one `ncu --set full` capture of this build's kernel on a GB300;
-# the launch's traffic grows with the number of (query, start) pairs, so it is
+# DRAM bytes (read + write) of the dominant descent launch of a 4,096-query
+# case (d=20: round 0's fine-level launch; d=64: the tile kernel's launch),
+# from one `ncu --set full` capture of this build's kernels on a GB300; the
+# launch's traffic grows with the number of (query, start) pairs, so it is
 # scaled by queries / 4096.
-TRAFFIC_4096 = {"smooth_nonconvex_d20_hopf": 42.571e9 + 54.478e9, "linear_quad_d64_lax": 28.598e9 + 42.637e9}
+TRAFFIC_4096 = {"smooth_nonconvex_d20_hopf": 16.423e9 + 20.268e9, "linear_quad_d64_lax": 28.598e9 + 42.637e9}
 
 
 def _args():
@@ -314,8 +315,8 @@ def run_ours(a):
         peak = nsm * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": flops / desc_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "frac": flops / desc_s / 1e12 / peak, "traffic": traffic,
-                "traffic_note": "DRAM bytes of the round-0 descent launch, scaled from a 4,096-query ncu capture "
-                                "(the adjoint's per-thread RK4 checkpoints)",
+                "traffic_note": "DRAM bytes of round 0's fine-level descent launch, scaled from a 4,096-query "
+                                "ncu capture (the adjoint's per-thread RK4 checkpoints)",
                 "kernel": "k_desc (persistent descent)",
                 "peak_note": f"FP32 FMA {nsm} SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                              f"({peak_src} max SM clock)"}
