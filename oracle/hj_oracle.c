@@ -576,8 +576,6 @@ void orc_gradient_fd(const orc_problem *P, int quad, const double *x, double t, 
  * Returns the number of iterations; *hit_cap is set when the cap stopped it. */
 static int descend_cg(const orc_problem *P, const orc_opts *O, const double *x, double t, int N, double *v,
                       int *hit_cap, int *nonfinite);
-static int descend_gd(const orc_problem *P, const orc_opts *O, const double *x, double t, int N, double *v,
-                      double *alpha_io, int *hit_cap, int *nonfinite);
 
 int orc_descend(const orc_problem *P, const orc_opts *O, const double *x, double t, int N, double *v, int *hit_cap,
                 int *nonfinite)
@@ -588,27 +586,17 @@ int orc_descend(const orc_problem *P, const orc_opts *O, const double *x, double
     if (O->coarse_div > 1 && O->descent != DESC_CD) {
         /* continuation in the step size: the same descent, first on the
          * functional discretised with N / coarse_div steps (stopping at moves
-         * < coarse_eps), then on the functional with N steps from the point
-         * reached; the gradient form carries its per-coordinate steps over,
-         * conjugate gradients restart from the steepest direction */
+         * < coarse_eps), then, with its step control started afresh, on the
+         * functional with N steps from the point reached */
         orc_opts C = *O, F = *O;
         C.coarse_div = F.coarse_div = 1;
         C.eps = O->coarse_eps;
         int Nc = N / O->coarse_div;
         if (Nc < 1) Nc = 1;
-        int cap1 = 0, nf1 = 0, it1, it2;
-        if (O->descent == DESC_GD) {
-            double *alpha = (double *)malloc(sizeof(double) * (size_t)d);
-            for (int i = 0; i < d; ++i) alpha[i] = O->step;
-            it1 = descend_gd(P, &C, x, t, Nc, v, alpha, &cap1, &nf1);
-            if (nf1) { *nonfinite = 1; free(alpha); return it1; }
-            it2 = descend_gd(P, &F, x, t, N, v, alpha, hit_cap, nonfinite);
-            free(alpha);
-        } else {
-            it1 = orc_descend(P, &C, x, t, Nc, v, &cap1, &nf1);
-            if (nf1) { *nonfinite = 1; return it1; }
-            it2 = orc_descend(P, &F, x, t, N, v, hit_cap, nonfinite);
-        }
+        int cap1 = 0, nf1 = 0;
+        int it1 = orc_descend(P, &C, x, t, Nc, v, &cap1, &nf1);
+        if (nf1) { *nonfinite = 1; return it1; }
+        int it2 = orc_descend(P, &F, x, t, N, v, hit_cap, nonfinite);
         return it1 + it2;
     }
     if (O->descent == DESC_CG) return descend_cg(P, O, x, t, N, v, hit_cap, nonfinite);
@@ -642,20 +630,8 @@ int orc_descend(const orc_problem *P, const orc_opts *O, const double *x, double
         *hit_cap = 1;
         return it;
     } else {
-        return descend_gd(P, O, x, t, N, v, NULL, hit_cap, nonfinite);
-    }
-}
-
-/* Gradient form of the descent (see orc_descend).  alpha_io (may be NULL):
- * the per-coordinate steps to start from, and on return the steps reached;
- * NULL starts every coordinate at O->step. */
-static int descend_gd(const orc_problem *P, const orc_opts *O, const double *x, double t, int N, double *v,
-                      double *alpha_io, int *hit_cap, int *nonfinite)
-{
-    int d = P->d;
-    {
         double *g = (double *)malloc(sizeof(double) * 3 * (size_t)d), *gprev = g + d, *alpha = gprev + d;
-        for (int i = 0; i < d; ++i) { alpha[i] = alpha_io ? alpha_io[i] : O->step; gprev[i] = 0.0; }
+        for (int i = 0; i < d; ++i) { alpha[i] = O->step; gprev[i] = 0.0; }
         int it;
         for (it = 0; it < O->max_iters; ++it) {
             if (O->grad == GRAD_ADJOINT) orc_gradient(P, O->quad, x, t, N, v, g);
@@ -668,25 +644,15 @@ static int descend_gd(const orc_problem *P, const orc_opts *O, const double *x, 
                     else if (prod > 0.0) alpha[i] = fmin(alpha[i] * O->grow, O->step_max);
                 }
                 double step = alpha[i] * g[i];
-                if (!isfinite(step)) {
-                    *nonfinite = 1;
-                    if (alpha_io) memcpy(alpha_io, alpha, sizeof(double) * d);
-                    free(g);
-                    return it + 1;
-                }
+                if (!isfinite(step)) { *nonfinite = 1; free(g); return it + 1; }
                 v[i] -= step;
                 if (fabs(step) > big) big = fabs(step);
                 gprev[i] = g[i];
             }
             if (O->halving_period > 0 && (it + 1) % O->halving_period == 0)
                 for (int i = 0; i < d; ++i) alpha[i] *= 0.5;
-            if (big < O->eps) {
-                if (alpha_io) memcpy(alpha_io, alpha, sizeof(double) * d);
-                free(g);
-                return it + 1;
-            }
+            if (big < O->eps) { free(g); return it + 1; }
         }
-        if (alpha_io) memcpy(alpha_io, alpha, sizeof(double) * d);
         free(g);
         *hit_cap = 1;
         return it;

@@ -265,10 +265,10 @@ def test_cd_stops_after_d_small_steps():
     assert np.abs(v - x / 2).max() < 1e-9
 
 
-def _gd_rule_reference(grad, v0, O_, with_alpha=False, alpha0=None):
+def _gd_rule_reference(grad, v0, O_):
     """The per-coordinate sign-change step rule stepped by hand."""
     v = v0.copy()
-    alpha = np.full(v.size, O_.step) if alpha0 is None else alpha0.copy()
+    alpha = np.full(v.size, O_.step)
     gprev = np.zeros(v.size)
     for it in range(O_.max_iters):
         g = grad(v)
@@ -278,8 +278,8 @@ def _gd_rule_reference(grad, v0, O_, with_alpha=False, alpha0=None):
         v = v - step
         gprev = g
         if np.abs(step).max() <= O_.eps:
-            return (v, it + 1, alpha) if with_alpha else (v, it + 1)
-    return (v, O_.max_iters, alpha) if with_alpha else (v, O_.max_iters)
+            return v, it + 1
+    return v, O_.max_iters
 
 
 def test_gradient_descent_rule_on_closed_form():
@@ -297,7 +297,7 @@ def test_gradient_descent_rule_on_closed_form():
 def test_coarse_to_fine_descent_is_two_descents_in_sequence():
     # continuation in the step size: the descent on the N/coarse_div-step
     # functional (stopping at moves < coarse_eps), then the descent on the
-    # N-step functional from there, starting from the steps reached.  For
+    # N-step functional from there, its step control started afresh.  For
     # H = |p|^2/2 and g = |x|^2/2, F(v) = |x - t v|^2/2 + t|v|^2/2 for any N,
     # so both stages follow the closed-form gradient
     P = _p_quad_iso(d=2)
@@ -308,9 +308,8 @@ def test_coarse_to_fine_descent_is_two_descents_in_sequence():
     grad = lambda v: -t * (x - t * v) + t * v
     O2 = O.Opts(eps=1e-12, coarse_div=4, coarse_eps=1e-3, **kw)
     v, it, cap, nf = O.descend(P, O2, x, t, 12, v0)
-    # the gradient form carries its per-coordinate steps into the fine level
-    v1, it1, al = _gd_rule_reference(grad, v0, O.Opts(eps=1e-3, **kw), with_alpha=True)
-    v2, it2, _ = _gd_rule_reference(grad, v1, O.Opts(eps=1e-12, **kw), with_alpha=True, alpha0=al)
+    v1, it1 = _gd_rule_reference(grad, v0, O.Opts(eps=1e-3, **kw))
+    v2, it2 = _gd_rule_reference(grad, v1, O.Opts(eps=1e-12, **kw))
     assert it == it1 + it2 and not nf
     assert np.abs(v - v2).max() < 1e-10
     # on a state-dependent problem both descents reach the same discrete
