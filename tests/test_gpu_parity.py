@@ -385,3 +385,37 @@ def test_solve_through_a_cuda_graph_matches_direct_solves(hj, mixed):
             assert info["n_queries"] == w.nq and info["total_ms"] > 0
         g_ctx.close()
         d_ctx.close()
+
+
+@pytest.mark.parametrize("family,prec", [(W.FAM_SMOOTH_NONCONVEX, "fp32"), (W.FAM_SMOOTH_NONCONVEX, "fp64"),
+                                         (W.FAM_SPEED_QUAD, "fp64"), (W.FAM_LINEAR_QUAD, "fp32")])
+def test_autograd_functional_backward_is_the_adjoint_gradient(hj, family, prec):
+    # hj.Functional: forward hj_eval_functional, backward hj_grad; the
+    # gradient reaching v equals the upstream weight times the oracle's exact
+    # gradient of the discretised functional (the linear-quadratic fp32 case
+    # runs on the tensor-core tile kernel)
+    d = 20
+    spec = _spec(family, W.HOPF if family == W.FAM_SMOOTH_NONCONVEX else W.LAX, d, seed=4, s_eps=1e-2)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    ctx = hj.hj_create([spec], hj.opts_from_dict(W.solver_constants(), hj.HJ_PREC_FP32 if prec == "fp32" else
+                                                  hj.HJ_PREC_FP64, 32), 0)
+    n = 11
+    x, v, t, N = _rows(n, d, 7, prec)
+    xt, tt, Nt = _t(x, dt), _t(t, dt), _t(N, torch.int32)
+    vt = _t(v, dt).requires_grad_(True)
+    w = np.random.default_rng(8).uniform(-2, 2, n)
+    F = hj.Functional.apply(ctx, xt, tt, vt, Nt)
+    (F * _t(w, dt)).sum().backward()
+    G = vt.grad.cpu().numpy()
+    P = oracle_problem(spec)
+    tc = family == W.FAM_LINEAR_QUAD and prec == "fp32"
+    tol = TC_TOL_G if tc else (5e-4 if prec == "fp32" else 1e-9)
+    for i in range(n):
+        Fo, Go = O.gradient(P, x[i], t[i], int(N[i]), v[i])
+        assert np.abs(G[i] - w[i] * Go).max() <= tol * (1 + np.abs(w[i] * Go).max()), i
+    if prec == "fp64":
+        # finite differences of the forward against the backward
+        vs = _t(v[:2], dt).requires_grad_(True)
+        assert torch.autograd.gradcheck(lambda vv: hj.Functional.apply(ctx, xt[:2], tt[:2], vv, Nt[:2]), (vs,),
+                                        eps=1e-6, atol=1e-5, rtol=1e-4)
+    ctx.close()
