@@ -29,8 +29,11 @@
  *    context's problems; a row of a problem with smaller d uses its first d
  *    entries (the rest is ignored on input and left untouched on output).
  *  - problem_idx (int32 [n], nullable = all 0) selects the problem of each
- *    row; n_steps (int32 [n], nullable = opts.n_steps_default) its RK4 step
- *    count N.  t must be > 0, N in [1, 256].
+ *    row (a row whose index is outside [0, n problems) is skipped: its
+ *    outputs are left untouched, or for hj_solve phi = NaN and status
+ *    HJ_ST_NONFINITE); n_steps (int32 [n], nullable = opts.n_steps_default)
+ *    its RK4 step count N.  t must be > 0, N in [1, 256] (other step counts
+ *    give NaN results).
  *  - Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy
  *    default stream).  Argument errors are detected on the host and
  *    returned before anything is enqueued; the message is available from

@@ -875,7 +875,7 @@ hj_status hj_guesses(hj_ctx *ctx, int64_t n, const int64_t *query_id, const int3
     if (n == 0) return HJ_OK;
     if (!query_id || !slot || !round || !v_out) return fail(ctx, HJ_EINVAL, "query_id, slot, round, v_out must be non-NULL");
     CU(cudaSetDevice(ctx->device));
-    CU(launch_guess(n, (const long long *)query_id, slot, round, ctx->np > 1 ? problem_idx : nullptr, ctx->d_pd,
+    CU(launch_guess(n, (const long long *)query_id, slot, round, ctx->np > 1 ? problem_idx : nullptr, ctx->np, ctx->d_pd,
                     ctx->ld, ctx->opts.seed, ctx->opts.guess_dist, ctx->prec, v_out, (cudaStream_t)stream));
     return HJ_OK;
 }
@@ -962,7 +962,7 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
         ctx->launches = 6;  // count, offsets, three scan phases, pair build
         CU(launch_count(n_queries, pidx, ctx->d_pg, ctx->starts, ctx->pcount, ctx->np, ctx->seg_begin, ctx->wl_count, s));
         CU(launch_scan(n_queries, ctx->starts, ctx->pair_base, ctx->block_sums, s));
-        CU(launch_build_pairs(n_queries, pidx, ctx->d_pg, ctx->pair_base, ctx->pair_q, ctx->pair_slot, ctx->pair_round,
+        CU(launch_build_pairs(n_queries, pidx, ctx->np, ctx->d_pg, ctx->pair_base, ctx->pair_q, ctx->pair_slot, ctx->pair_round,
                               ctx->trials, ctx->qflags, ctx->seg_begin, ctx->wl_count, ctx->wl, s));
         // Several problems: each round's descent launches go to auxiliary streams
         // (tensor-core problems share the first, the lane-group ones take the
@@ -1110,6 +1110,7 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
             SelectArgs a{};
             a.nq = n_queries;
             a.pidx = pidx;
+            a.np = ctx->np;
             a.pg = ctx->d_pg;
             a.pd = ctx->d_pd;
             a.pprin = ctx->d_pprin;
@@ -1470,7 +1471,7 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
     // per-problem counters must start at zero, and they are cleared here.
     CU(launch_count(n_queries, pidx, ctx->d_pg, L.starts, L.pcount, ctx->np, L.seg_begin, L.wl_count, s));
     CU(launch_scan(n_queries, L.starts, L.pair_base, L.block_sums, s));
-    CU(launch_build_pairs(n_queries, pidx, ctx->d_pg, L.pair_base, L.pair_q, L.pair_slot, L.pair_round, L.trials,
+    CU(launch_build_pairs(n_queries, pidx, ctx->np, ctx->d_pg, L.pair_base, L.pair_q, L.pair_slot, L.pair_round, L.trials,
                           L.qflags, L.seg_begin, L.wl_count, L.wl, s));
     for (int round = 0; round <= ctx->opts.max_rounds; ++round) {
         CU(cudaMemsetAsync(L.cursor, 0, sizeof(int32_t) * ctx->np, s));
@@ -1567,6 +1568,7 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
         SelectArgs a{};
         a.nq = n_queries;
         a.pidx = pidx;
+        a.np = ctx->np;
         a.pg = ctx->d_pg;
         a.pd = ctx->d_pd;
         a.pprin = ctx->d_pprin;

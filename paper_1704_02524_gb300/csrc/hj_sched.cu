@@ -9,14 +9,23 @@
 
 namespace hjd {
 
+// A query's problem index, or -1 when it is outside [0, np) (such a query
+// gets no starts and the status HJ_ST_NONFINITE).
+__device__ __forceinline__ int problem_of(const int32_t *pidx, long long q, int np)
+{
+    const int p = pidx ? pidx[q] : 0;
+    return (p >= 0 && p < np) ? p : -1;
+}
+
 // Starts per query -> starts[q]; pairs per problem accumulated in pcount.
-__global__ void k_count(long long nq, const int32_t *pidx, const int32_t *pg, int32_t *starts, int32_t *pcount)
+__global__ void k_count(long long nq, const int32_t *pidx, int np, const int32_t *pg, int32_t *starts,
+                        int32_t *pcount)
 {
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (long long)gridDim.x * blockDim.x) {
-        int p = pidx ? pidx[q] : 0;
-        int G = pg[p];
+        const int p = problem_of(pidx, q, np);
+        const int G = (p >= 0) ? pg[p] : 0;
         starts[q] = G;
-        atomicAdd(pcount + p, G);
+        if (p >= 0) atomicAdd(pcount + p, G);
     }
 }
 
@@ -74,12 +83,17 @@ __global__ void k_scan_add(long long n, int32_t *out, const int32_t *block_sums)
 }
 
 // Round 0: every (query, slot) pair, appended to its problem's work list.
-__global__ void k_build_pairs(long long nq, const int32_t *pidx, const int32_t *pg, const int32_t *pair_base,
+__global__ void k_build_pairs(long long nq, const int32_t *pidx, int np, const int32_t *pg, const int32_t *pair_base,
                               int32_t *pair_q, int32_t *pair_slot, int32_t *pair_round, int32_t *trials,
                               int32_t *qflags, const int32_t *seg_begin, int32_t *wl_count, int32_t *wl)
 {
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (long long)gridDim.x * blockDim.x) {
-        int p = pidx ? pidx[q] : 0;
+        const int p = problem_of(pidx, q, np);
+        if (p < 0) {
+            trials[q] = 0;
+            qflags[q] = HJ_ST_NONFINITE;
+            continue;
+        }
         int G = pg[p];
         int base = pair_base[q];
         int pos = atomicAdd(wl_count + p, G);
@@ -99,7 +113,7 @@ __global__ void k_build_pairs(long long nq, const int32_t *pidx, const int32_t *
 // budget (ptrials) of starts of the query have run.  phi = F (Lax) or -G (Hopf) at the chosen start (the
 // FP64 value replaces it after the last round); best_pid records the start.
 template <typename T>
-__global__ void k_select(long long nq, const int32_t *pidx, const int32_t *pg, const int32_t *pd,
+__global__ void k_select(long long nq, const int32_t *pidx, int np, const int32_t *pg, const int32_t *pd,
                          const int32_t *pprin, int ld, const int32_t *pair_base, const double *pF,
                          const uint8_t *pP, const uint8_t *flags, const T *vfin, int32_t *pair_round,
                          int32_t *trials, int32_t *qflags, int round, int schedule, const int32_t *ptrials,
@@ -107,7 +121,13 @@ __global__ void k_select(long long nq, const int32_t *pidx, const int32_t *pg, c
                          int32_t *status, int32_t *best_pid)
 {
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (long long)gridDim.x * blockDim.x) {
-        const int p = pidx ? pidx[q] : 0;
+        const int p = problem_of(pidx, q, np);
+        if (p < 0) {
+            best_pid[q] = -1;
+            phi[q] = nan("");
+            status[q] = HJ_ST_NONFINITE;
+            continue;
+        }
         const int G = pg[p], d = pd[p];
         const int base = pair_base[q];
         int best = -1, best_cert = 0, qf = qflags[q];
@@ -158,13 +178,15 @@ __global__ void k_select(long long nq, const int32_t *pidx, const int32_t *pg, c
 // hj_guesses: the starts drawn by hj_solve, for testing.
 template <typename T>
 __global__ void k_guess(long long n, const long long *qid, const int32_t *slot, const int32_t *round,
-                        const int32_t *pidx, const int32_t *pd, int ld, unsigned long long seed, int dist, T *v)
+                        const int32_t *pidx, int np, const int32_t *pd, int ld, unsigned long long seed, int dist, T *v)
 {
     const long long total = n * ld;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
         const long long r = e / ld;
         const int i = (int)(e % ld);
-        const int d = pd[pidx ? pidx[r] : 0];
+        const int p = pidx ? pidx[r] : 0;
+        if (p < 0 || p >= np) continue;  // rows of an unknown problem are left untouched
+        const int d = pd[p];
         if (i < d) v[e] = start_component<T>(seed, qid[r], slot[r], round[r], i, dist);
     }
 }
@@ -185,7 +207,7 @@ cudaError_t launch_count(long long nq, const int32_t *pidx, const int32_t *pg, i
 {
     cudaError_t e = cudaMemsetAsync(pcount, 0, sizeof(int32_t) * np, s);
     if (e != cudaSuccess) return e;
-    k_count<<<grid_for(nq, 256), 256, 0, s>>>(nq, pidx, pg, starts, pcount);
+    k_count<<<grid_for(nq, 256), 256, 0, s>>>(nq, pidx, np, pg, starts, pcount);
     k_problem_offsets<<<1, 1, 0, s>>>(np, pcount, seg_begin, wl_count);
     return cudaGetLastError();
 }
@@ -200,13 +222,13 @@ cudaError_t launch_scan(long long n, const int32_t *in, int32_t *out, int32_t *b
     return cudaGetLastError();
 }
 
-cudaError_t launch_build_pairs(long long nq, const int32_t *pidx, const int32_t *pg, const int32_t *pair_base,
-                               int32_t *pair_q, int32_t *pair_slot, int32_t *pair_round, int32_t *trials,
-                               int32_t *qflags, const int32_t *seg_begin, int32_t *wl_count, int32_t *wl,
-                               cudaStream_t s)
+cudaError_t launch_build_pairs(long long nq, const int32_t *pidx, int np, const int32_t *pg,
+                               const int32_t *pair_base, int32_t *pair_q, int32_t *pair_slot, int32_t *pair_round,
+                               int32_t *trials, int32_t *qflags, const int32_t *seg_begin, int32_t *wl_count,
+                               int32_t *wl, cudaStream_t s)
 {
-    k_build_pairs<<<grid_for(nq, 256), 256, 0, s>>>(nq, pidx, pg, pair_base, pair_q, pair_slot, pair_round, trials,
-                                                    qflags, seg_begin, wl_count, wl);
+    k_build_pairs<<<grid_for(nq, 256), 256, 0, s>>>(nq, pidx, np, pg, pair_base, pair_q, pair_slot, pair_round,
+                                                    trials, qflags, seg_begin, wl_count, wl);
     return cudaGetLastError();
 }
 
@@ -214,7 +236,7 @@ template <typename T>
 cudaError_t launch_select_t(const SelectArgs &a, cudaStream_t s)
 {
     k_select<T><<<grid_for(a.nq, 128), 128, 0, s>>>(
-        a.nq, a.pidx, a.pg, a.pd, a.pprin, a.ld, a.pair_base, a.pF, a.pP, a.flags, (const T *)a.vfin, a.pair_round,
+        a.nq, a.pidx, a.np, a.pg, a.pd, a.pprin, a.ld, a.pair_base, a.pF, a.pP, a.flags, (const T *)a.vfin, a.pair_round,
         a.trials, a.qflags, a.round, a.schedule, a.ptrials, a.seg_begin, a.wl_count, a.wl, a.phi, (T *)a.v_out,
         a.status, a.best_pid);
     return cudaGetLastError();
@@ -226,12 +248,12 @@ cudaError_t launch_select(const SelectArgs &a, int prec, cudaStream_t s)
 }
 
 cudaError_t launch_guess(long long n, const long long *qid, const int32_t *slot, const int32_t *round,
-                         const int32_t *pidx, const int32_t *pd, int ld, unsigned long long seed, int dist, int prec,
-                         void *v, cudaStream_t s)
+                         const int32_t *pidx, int np, const int32_t *pd, int ld, unsigned long long seed, int dist,
+                         int prec, void *v, cudaStream_t s)
 {
     int g = grid_for(n * ld, 256);
-    if (prec) k_guess<double><<<g, 256, 0, s>>>(n, qid, slot, round, pidx, pd, ld, seed, dist, (double *)v);
-    else k_guess<float><<<g, 256, 0, s>>>(n, qid, slot, round, pidx, pd, ld, seed, dist, (float *)v);
+    if (prec) k_guess<double><<<g, 256, 0, s>>>(n, qid, slot, round, pidx, np, pd, ld, seed, dist, (double *)v);
+    else k_guess<float><<<g, 256, 0, s>>>(n, qid, slot, round, pidx, np, pd, ld, seed, dist, (float *)v);
     return cudaGetLastError();
 }
 

@@ -8,7 +8,9 @@ namespace hjd {
 
 struct SelectArgs {
     long long nq;
-    const int32_t *pidx, *pg, *pd, *pprin;
+    const int32_t *pidx;
+    int np;  // problems (a problem index outside [0, np) marks the query invalid)
+    const int32_t *pg, *pd, *pprin;
     int ld;
     const int32_t *pair_base;
     const double *pF;
@@ -28,13 +30,13 @@ struct SelectArgs {
 cudaError_t launch_count(long long nq, const int32_t *pidx, const int32_t *pg, int32_t *starts, int32_t *pcount,
                          int np, int32_t *seg_begin, int32_t *wl_count, cudaStream_t s);
 cudaError_t launch_scan(long long n, const int32_t *in, int32_t *out, int32_t *block_sums, cudaStream_t s);
-cudaError_t launch_build_pairs(long long nq, const int32_t *pidx, const int32_t *pg, const int32_t *pair_base,
+cudaError_t launch_build_pairs(long long nq, const int32_t *pidx, int np, const int32_t *pg, const int32_t *pair_base,
                                int32_t *pair_q, int32_t *pair_slot, int32_t *pair_round, int32_t *trials,
                                int32_t *qflags, const int32_t *seg_begin, int32_t *wl_count, int32_t *wl,
                                cudaStream_t s);
 cudaError_t launch_select(const SelectArgs &a, int prec, cudaStream_t s);
 cudaError_t launch_guess(long long n, const long long *qid, const int32_t *slot, const int32_t *round,
-                         const int32_t *pidx, const int32_t *pd, int ld, unsigned long long seed, int dist, int prec,
+                         const int32_t *pidx, int np, const int32_t *pd, int ld, unsigned long long seed, int dist, int prec,
                          void *v, cudaStream_t s);
 
 }  // namespace hjd

@@ -419,3 +419,27 @@ def test_autograd_functional_backward_is_the_adjoint_gradient(hj, family, prec):
         assert torch.autograd.gradcheck(lambda vv: hj.Functional.apply(ctx, xt[:2], tt[:2], vv, Nt[:2]), (vs,),
                                         eps=1e-6, atol=1e-5, rtol=1e-4)
     ctx.close()
+
+
+def test_queries_of_unknown_problems_and_empty_calls(hj):
+    # a problem index outside [0, n problems) marks the query invalid (no
+    # starts, phi NaN, status HJ_ST_NONFINITE) and leaves the other queries'
+    # answers as they are; calls with no rows do nothing
+    w = _mixed_sample(per_problem=3)
+    ctx = hj.hj_create(w.problems, hj.opts_from_dict(w.solver, hj.HJ_PREC_FP32, 64), 0)
+    x, t, ns = _t(w.x, torch.float32), _t(w.t, torch.float32), _t(w.n_steps, torch.int32)
+    good = _t(w.problem_idx, torch.int32)
+    bad = good.clone()
+    bad[3], bad[10] = 99, -1
+    phi0, _, st0 = hj.hj_solve(ctx, x, t, ns, good)
+    phi1, _, st1 = hj.hj_solve(ctx, x, t, ns, bad)
+    phi0, st0, phi1, st1 = phi0.cpu().numpy(), st0.cpu().numpy(), phi1.cpu().numpy(), st1.cpu().numpy()
+    keep = np.ones(w.nq, bool)
+    keep[[3, 10]] = False
+    assert np.isnan(phi1[3]) and np.isnan(phi1[10]) and st1[3] == hj.HJ_ST_NONFINITE and st1[10] == hj.HJ_ST_NONFINITE
+    assert np.array_equal(phi1[keep], phi0[keep]) and np.array_equal(st1[keep], st0[keep])
+    e = torch.empty(0, w.x.shape[1], dtype=torch.float32, device=DEV)
+    et = torch.empty(0, dtype=torch.float32, device=DEV)
+    assert hj.hj_eval_functional(ctx, e, et, e).numel() == 0
+    assert hj.hj_solve(ctx, e, et, None, torch.empty(0, dtype=torch.int32, device=DEV))[0].numel() == 0
+    ctx.close()
