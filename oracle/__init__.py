@@ -43,6 +43,7 @@ FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD = 0, 1, 2, 3
 LAX, HOPF = 0, 1
 G_QUAD_SHIFT, G_DIAG_QUAD = 0, 1
 QUAD_RK4, QUAD_RECT = 0, 1
+ODE_EULER = 2  # or-ed into a quad argument: forward Euler instead of RK4
 GRAD_FD_CENTRAL, GRAD_FD_FORWARD, GRAD_ADJOINT = 0, 1, 2
 DESC_CD, DESC_GD, DESC_CG = 0, 1, 2
 ST_CERTIFIED, ST_MAX_ITERS, ST_NONFINITE, ST_RESEEDED = 1, 2, 4, 8

@@ -13,16 +13,16 @@
  * What it computes, per (query x, time t, initial guess v):
  *   - the bi-characteristics (Sec. 4.1, final value problem):
  *         d gamma/ds = dH/dp,  dp/ds = -dH/dx,  gamma(t) = x,  p(t) = v,
- *     integrated backward from s = t to s = 0 with N classical RK4 steps
- *     (the paper suggests forward Euler "for illustration" and allows better
- *     solvers, Sec. 4.2);
+ *     integrated backward from s = t to s = 0 with N classical RK4 steps,
+ *     or with N forward Euler steps, the solver Sec. 4.2 uses as its
+ *     example while leaving higher-order schemes open;
  *   - the functional F^1 (Lax, eq. lax_formula / Sec. 4.1) or G (Hopf,
  *     eq. hopf_formula / Sec. 4.1) with the running-cost integral taken
  *     either by RK4 on an augmented quadrature state (default) or by the
  *     rectangular rule of eq. num_int;
  *   - derivatives by the finite differences of eq. num_diff (forward) or
  *     the central form, and the exact gradient of the discretised
- *     functional by the discrete adjoint of the RK4 map;
+ *     functional by the discrete adjoint of the RK4 (or Euler) map;
  *   - cyclic coordinate descent (Algorithm 1), gradient descent, and a
  *     conjugate-gradient (momentum) descent for ill-conditioned functionals
  *     (Sec. 5 points to momentum methods when plain descent drags);
@@ -50,6 +50,10 @@ enum { FAM_QUAD_ISO = 0, FAM_SPEED_QUAD = 1, FAM_SMOOTH_NONCONVEX = 2, FAM_LINEA
 enum { LAX = 0, HOPF = 1 };
 enum { G_QUAD_SHIFT = 0, G_DIAG_QUAD = 1 };
 enum { QUAD_RK4 = 0, QUAD_RECT = 1 };
+/* Flag or-ed into a `quad` argument: integrate with forward Euler (the
+ * solver Sec. 4.2 suggests) instead of RK4.  With QUAD_RK4 the running cost
+ * is then integrated by the same Euler steps on the augmented state. */
+enum { ODE_EULER = 2 };
 enum { GRAD_FD_CENTRAL = 0, GRAD_FD_FORWARD = 1, GRAD_ADJOINT = 2 };
 enum { DESC_CD = 0, DESC_GD = 1, DESC_CG = 2 };
 
@@ -75,7 +79,7 @@ typedef struct {
 } orc_problem;
 
 typedef struct {
-    int quad;            /* QUAD_RK4 / QUAD_RECT                                 */
+    int quad;            /* QUAD_RK4 / QUAD_RECT, optionally | ODE_EULER          */
     int descent;         /* DESC_CD / DESC_GD / DESC_CG                          */
     int grad;            /* GRAD_FD_CENTRAL / GRAD_FD_FORWARD / GRAD_ADJOINT     */
     double fd_h;         /* finite-difference step sigma of eq. num_diff         */
@@ -425,9 +429,24 @@ static double integrate(const orc_problem *P, int quad, const double *x, double 
     double h = t / N;
     double z[2 * ORC_DMAX + 1], zs[2 * ORC_DMAX + 1];
     double k1[2 * ORC_DMAX + 1], k2[2 * ORC_DMAX + 1], k3[2 * ORC_DMAX + 1], k4[2 * ORC_DMAX + 1];
+    const int euler = quad & ODE_EULER;
+    quad &= ~ODE_EULER;
     for (int i = 0; i < d; ++i) { z[i] = x[i]; z[d + i] = v[i]; }
     double Q = 0.0;
     if (traj) memcpy(traj, z, sizeof(double) * n2);
+    if (euler) {
+        /* forward Euler, z_{n+1} = z_n + h f(z_n); the Euler step of the
+         * augmented state adds h L(z_n), the rectangle rule h L(z_{n+1}) */
+        for (int n = 0; n < N; ++n) {
+            if (stages) memcpy(stages + (size_t)(4 * n) * n2, z, sizeof(double) * n2);
+            field(P, z, k1);
+            for (int i = 0; i < n2; ++i) z[i] += h * k1[i];
+            if (quad == QUAD_RK4) Q += h * k1[n2];
+            else Q += h * running_cost(P, z, z + d);
+            if (traj) memcpy(traj + (size_t)(n + 1) * n2, z, sizeof(double) * n2);
+        }
+        return Q;
+    }
     for (int n = 0; n < N; ++n) {
         if (stages) memcpy(stages + (size_t)(4 * n + 0) * n2, z, sizeof(double) * n2);
         field(P, z, k1);
@@ -496,9 +515,26 @@ double orc_gradient(const orc_problem *P, int quad, const double *x, double t, i
         F = gstar_val(P, zN + d) + Q - dot(x, v, d);
         gstar_grad(P, zN + d, lam + d);
     }
+    const int euler = quad & ODE_EULER;
+    quad &= ~ODE_EULER;
     double beta_q = (quad == QUAD_RK4) ? 1.0 : 0.0; /* dF/dQ flows through the stages only for RK4 quadrature */
     for (int n = N - 1; n >= 0; --n) {
         const double *Z1 = stages + (size_t)(4 * n + 0) * n2, *Z2 = Z1 + n2, *Z3 = Z2 + n2, *Z4 = Z3 + n2;
+        if (euler) {
+            /* z_{n+1} = z_n + h f(z_n) (and Q += h L(z_n)); reverse:
+             * lam_n = lam_{n+1} + h J(z_n)^T lam_{n+1} + h beta dL/dz(z_n),
+             * after the rectangle node at z_{n+1} when that rule is used */
+            if (quad == QUAD_RECT) {
+                double gl[2 * ORC_DMAX], zero[2 * ORC_DMAX];
+                for (int i = 0; i < n2; ++i) zero[i] = 0.0;
+                field_vjp(P, traj + (size_t)(n + 1) * n2, zero, 1.0, gl);
+                for (int i = 0; i < n2; ++i) lam[i] += h * gl[i];
+            }
+            for (int i = 0; i < n2; ++i) w[i] = h * lam[i];
+            field_vjp(P, Z1, w, beta_q * h, a1);
+            for (int i = 0; i < n2; ++i) lam[i] += a1[i];
+            continue;
+        }
         if (quad == QUAD_RECT) {
             /* rectangle node at the state after step n, weight h: add h grad L */
             double gl[2 * ORC_DMAX], zero[2 * ORC_DMAX];

@@ -195,6 +195,70 @@ def test_rect_rule_first_order_convergence():
 
 
 # --------------------------------------------------------------------------
+# Forward Euler (the example solver of Sec. 4.2)
+# --------------------------------------------------------------------------
+
+EULER = O.QUAD_RK4 | O.ODE_EULER
+EULER_RECT = O.QUAD_RECT | O.ODE_EULER
+
+
+@pytest.mark.parametrize("quad", [EULER, EULER_RECT])
+def test_euler_exact_when_momentum_is_constant(quad):
+    # H = |p|^2/2: the field is constant along the path, so one Euler step is
+    # as exact as RK4 and both quadratures see the constant integrand
+    rng = np.random.default_rng(30)
+    P = _p_quad_iso()
+    for N in (1, 7):
+        x, v, t = rng.normal(size=2), rng.normal(size=2), rng.uniform(0.1, 2)
+        F = O.functional(P, x, t, N, v, quad=quad)
+        assert abs(F - (0.5 * np.sum((x - t * v) ** 2) + 0.5 * t * np.sum(v ** 2))) < 1e-13
+
+
+@pytest.mark.parametrize("quad", [EULER, EULER_RECT])
+def test_euler_linear_quadratic_matches_matrix_recursion(quad):
+    # Linear-quadratic Lax problem: in reversed time the characteristic
+    # system is the linear ODE z' = M z, M = [[-A, -BB^T], [0, A^T]], so N
+    # Euler steps are z_n = (I + hM)^n z_0; the running cost |B^T p|^2/2 is
+    # summed at z_0..z_{N-1} (Euler on the augmented state) or at z_1..z_N
+    # (rectangle rule), and g(gamma_N) = |gamma_N - a|^2/2 is added.
+    rng = np.random.default_rng(31)
+    d, m, t, N = 5, 3, 0.7, 9
+    A = rng.normal(size=(d, d)) * 0.4
+    B = rng.normal(size=(d, m)) / math.sqrt(d)
+    a = rng.uniform(-1, 1, d)
+    P = O.Problem(d=d, family=O.FAM_LINEAR_QUAD, principle=O.LAX, g_kind=O.G_QUAD_SHIFT, A=A, B=B, a=a)
+    Cm = B @ B.T
+    M = np.block([[-A, -Cm], [np.zeros((d, d)), A.T]])
+    h = t / N
+    step = np.eye(2 * d) + h * M
+    for _ in range(3):
+        x, v = rng.uniform(-1, 1, d), rng.uniform(-1, 1, d)
+        zs = [np.concatenate([x, v])]
+        for _n in range(N):
+            zs.append(step @ zs[-1])
+        nodes = zs[:-1] if quad == EULER else zs[1:]
+        Q = sum(h * 0.5 * z[d:] @ Cm @ z[d:] for z in nodes)
+        expect = 0.5 * np.sum((zs[-1][:d] - a) ** 2) + Q
+        assert abs(O.functional(P, x, t, N, v, quad=quad) - expect) < 1e-13 * (1 + abs(expect))
+
+
+def test_euler_first_order_convergence_state_dependent():
+    # |F_N - F_2N| halves per halving of h, and the limit is the RK4 value
+    rng = np.random.default_rng(32)
+    d = 10
+    P = O.Problem(d=d, family=O.FAM_SPEED_QUAD, principle=O.LAX, g_kind=O.G_QUAD_SHIFT,
+                  w=rng.normal(size=d) / math.sqrt(d), a=rng.uniform(-1, 1, d))
+    x, v = rng.uniform(-2, 2, d), rng.uniform(-1, 1, d)
+    Fs = [O.functional(P, x, 1.0, N, v, quad=EULER) for N in (64, 128, 256, 512)]
+    diffs = np.abs(np.diff(Fs))
+    ratios = diffs[:-1] / diffs[1:]
+    assert np.all(ratios > 1.8) and np.all(ratios < 2.2)
+    ref = O.functional(P, x, 1.0, 256, v)
+    # Richardson extrapolation of the first-order sequence lands on the limit
+    assert abs(2 * Fs[3] - Fs[2] - ref) < 0.05 * abs(Fs[3] - ref)
+
+
+# --------------------------------------------------------------------------
 # Gradients: the adjoint against the plain derivative
 # --------------------------------------------------------------------------
 
@@ -209,7 +273,7 @@ def test_adjoint_gradient_closed_form_quad_iso():
     (O.FAM_SPEED_QUAD, O.LAX, O.G_QUAD_SHIFT), (O.FAM_SPEED_QUAD, O.HOPF, O.G_QUAD_SHIFT),
     (O.FAM_SMOOTH_NONCONVEX, O.HOPF, O.G_DIAG_QUAD), (O.FAM_SMOOTH_NONCONVEX, O.LAX, O.G_DIAG_QUAD),
     (O.FAM_LINEAR_QUAD, O.LAX, O.G_QUAD_SHIFT), (O.FAM_LINEAR_QUAD, O.HOPF, O.G_QUAD_SHIFT)])
-@pytest.mark.parametrize("quad", [O.QUAD_RK4, O.QUAD_RECT])
+@pytest.mark.parametrize("quad", [O.QUAD_RK4, O.QUAD_RECT, EULER, EULER_RECT])
 def test_adjoint_gradient_matches_central_differences(family, principle, g_kind, quad):
     rng = np.random.default_rng(7 + family + 3 * principle)
     d = 6
