@@ -88,9 +88,17 @@ typedef enum {
                                along flat trenches; see hj_solver_opts)                     */
 } hj_grad_mode;
 
+/* Integrator and quadrature of the characteristic system (Sec. 4.2).  The
+ * characteristics are integrated by N classical RK4 steps, or by N forward
+ * Euler steps (Sec. 4.2's example solver) when HJ_ODE_EULER is or-ed into
+ * the value (HJ_QUAD_RK4 | HJ_ODE_EULER: Euler on the augmented state, which
+ * sums h L(z_n) at the left nodes; HJ_QUAD_RECT | HJ_ODE_EULER: Euler with
+ * the rectangle rule).  The discrete adjoint follows the chosen integrator,
+ * so gradients stay exact for the discretised functional. */
 typedef enum {
-    HJ_QUAD_RK4 = 0,  /* running cost integrated by RK4 on an augmented state          */
-    HJ_QUAD_RECT = 1  /* rectangle rule on the solver mesh, nodes s_i = i t/N, i<N     */
+    HJ_QUAD_RK4 = 0,  /* running cost integrated by the integrator on an augmented state */
+    HJ_QUAD_RECT = 1, /* rectangle rule on the solver mesh, nodes s_i = i t/N, i<N       */
+    HJ_ODE_EULER = 2  /* flag: forward Euler instead of RK4                              */
 } hj_quad_mode;
 
 typedef enum { HJ_PREC_FP32 = 0, HJ_PREC_FP64 = 1 } hj_precision;

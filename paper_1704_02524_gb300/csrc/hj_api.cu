@@ -71,17 +71,17 @@ enum Kind { K_EVAL = 0, K_GRAD = 1, K_CD = 2, K_GD = 3, K_CERT = 4, K_CG = 5 };
 // Descent kernel kind of a gradient mode.
 int desc_kind(int grad) { return grad == HJ_GRAD_ADJOINT ? K_GD : grad == HJ_GRAD_ADJOINT_CG ? K_CG : K_CD; }
 
-// Arithmetic per RK4 step of one pair (FMA = 2, add/mul = 1, sin/cos and
-// rsqrt not counted), from the operations written in hj_device.cuh.  The
+// Arithmetic per integrator step of one pair (FMA = 2, add/mul = 1, sin/cos
+// and rsqrt not counted), from the operations written in hj_device.cuh.  The
 // reverse step counts only the vector-Jacobian products (the stage
 // intermediates they reuse and the recomputation of stage inputs from
 // checkpoints are not counted).
 struct FlopModel {
-    double fwd_step;  // one forward step: 4 field evaluations + stage combinations
-    double adj_step;  // one reverse step: 4 vector-Jacobian products + combinations
+    double fwd_step;  // one forward step: 4 field evaluations + stage combinations (Euler: 1 + update)
+    double adj_step;  // one reverse step: 4 vector-Jacobian products + combinations (Euler: 1 + update)
 };
 
-FlopModel flop_model(int fam, int pr, int d)
+FlopModel flop_model(int fam, int pr, int d, int quad)
 {
     double fld = 0, vjp = 0;
     switch (fam) {
@@ -99,6 +99,7 @@ FlopModel flop_model(int fam, int pr, int d)
         break;
     default: break;
     }
+    if (quad & HJ_ODE_EULER) return FlopModel{fld + 4.0 * d + 2, vjp + 4.0 * d + 1};
     return FlopModel{4 * fld + 26.0 * d + 12, 4 * vjp + 28.0 * d + 6};
 }
 
@@ -302,7 +303,8 @@ hj_status validate_opts(hj_ctx *ctx, const hj_solver_opts &o)
 {
     if (o.n_steps_default < 1 || o.n_steps_default > MAX_N)
         return fail(ctx, HJ_EINVAL, "n_steps_default=%d outside [1, %d]", o.n_steps_default, MAX_N);
-    if (o.quad != HJ_QUAD_RK4 && o.quad != HJ_QUAD_RECT) return fail(ctx, HJ_EINVAL, "unknown quad %d", (int)o.quad);
+    if ((int)o.quad < 0 || (int)o.quad > (HJ_QUAD_RECT | HJ_ODE_EULER))
+        return fail(ctx, HJ_EINVAL, "unknown quad %d", (int)o.quad);
     if (o.grad < HJ_GRAD_FD_CENTRAL || o.grad > HJ_GRAD_ADJOINT_CG)
         return fail(ctx, HJ_EINVAL, "unknown grad mode %d", (int)o.grad);
     if ((o.grad == HJ_GRAD_FD_CENTRAL || o.grad == HJ_GRAD_FD_FORWARD) && !(o.fd_h > 0))
@@ -1230,7 +1232,7 @@ hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out)
     for (int p = 0; p < ctx->np; ++p) {
         const unsigned long long *c = st.data() + 8 * p;
         const hj_problem_desc &D = ctx->desc[p];
-        FlopModel fm = flop_model(D.family, D.principle, D.d);
+        FlopModel fm = flop_model(D.family, D.principle, D.d, (int)ctx->opts.quad);
         out->iterations += (int64_t)c[0];
         out->functional_evals += (int64_t)c[1];
         out->gradient_evals += (int64_t)c[2];

@@ -639,10 +639,25 @@ __device__ __forceinline__ T cert_residual(const Grp &g, const ProbDev<T> &P, co
 }
 
 // ---------------------------------------------------------------------------
-// Forward integration.  One classical RK4 step of the augmented system;
-// Q accumulates the running cost (RK4 weights, or the rectangle node at the
-// new state), with optional Kahan compensation.
+// Forward integration.  One step of the augmented system: classical RK4, or
+// forward Euler when quad carries HJ_ODE_EULER (Sec. 4.2's example solver).
+// Q accumulates the running cost (the integrator's own weights on the
+// augmented state, or the rectangle node at the new state), with optional
+// Kahan compensation.  quad is uniform across a launch, so the branch is too.
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void add_q(int kahan, T dQ, T &Q, T &Qc)
+{
+    if (kahan) {
+        T y = dQ - Qc;
+        T s = Q + y;
+        Qc = (s - Q) - y;
+        Q = s;
+    } else {
+        Q += dQ;
+    }
+}
+
 template <typename T, int C, int FAM, int PR>
 __device__ __forceinline__ void rk4_step(const Grp &g, const TP<T, C> &tp, T eps, T h, int quad, int kahan, T *gam,
                                          T *p, T &Q, T &Qc)
@@ -650,6 +665,22 @@ __device__ __forceinline__ void rk4_step(const Grp &g, const TP<T, C> &tp, T eps
     T ag[C], ap[C], zg[C], zp[C], kg[C], kp[C], L, aL;
     const T h2 = (T)0.5 * h;
     field<T, C, FAM, PR>(g, tp, eps, gam, p, kg, kp, L);
+    if (quad & HJ_ODE_EULER) {
+        // z_{n+1} = z_n + h f(z_n); the augmented state gains h L(z_n)
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            gam[k] = fma(h, kg[k], gam[k]);
+            p[k] = fma(h, kp[k], p[k]);
+        }
+        T dQ = h * L;
+        if (quad & HJ_QUAD_RECT) {
+            T dg_[C], dp_[C];
+            field<T, C, FAM, PR>(g, tp, eps, gam, p, dg_, dp_, L);
+            dQ = h * L;
+        }
+        add_q(kahan, dQ, Q, Qc);
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < C; ++k) {
         ag[k] = kg[k];
@@ -685,21 +716,14 @@ __device__ __forceinline__ void rk4_step(const Grp &g, const TP<T, C> &tp, T eps
     }
     aL += L;
     T dQ;
-    if (quad == HJ_QUAD_RK4) {
+    if (!(quad & HJ_QUAD_RECT)) {
         dQ = h6 * aL;
     } else {
         T Ln, dg_[C], dp_[C];
         field<T, C, FAM, PR>(g, tp, eps, gam, p, dg_, dp_, Ln);
         dQ = h * Ln;
     }
-    if (kahan) {
-        T y = dQ - Qc;
-        T s = Q + y;
-        Qc = (s - Q) - y;
-        Q = s;
-    } else {
-        Q += dQ;
-    }
+    add_q(kahan, dQ, Q, Qc);
 }
 
 // Functional value F (Lax) or G (Hopf); gam/p hold (x, v) on entry and
@@ -728,8 +752,11 @@ __device__ __forceinline__ T functional(const Grp &g, const TP<T, C> &tp, const 
 //   a1 = J(Z1)^T(h/6 lam + h/2 a2, h/6 b)
 //   lam += a1 + a2 + a3 + a4
 // with b = 1 for the RK4 quadrature (0 for the rectangle rule, whose nodes
-// add h grad L(z_{n+1}) to lam directly).  The seed lam(tau=t) comes from
-// the terminal term; dF/dv = lam_p(tau=0) (minus x for Hopf).
+// add h grad L(z_{n+1}) to lam directly).  The forward Euler map
+// z_{n+1} = z_n + h f(z_n) has the one-stage adjoint
+//   lam += J(z_n)^T(h lam, h b).
+// The seed lam(tau=t) comes from the terminal term; dF/dv = lam_p(tau=0)
+// (minus x for Hopf).
 // Per-thread scratch (local memory): ck >= ceil(N/K)*2C, seg >= K*2C values,
 // both sized for N <= MAX_N.
 // ---------------------------------------------------------------------------
@@ -834,7 +861,8 @@ __device__ __forceinline__ T gradient(const Grp &g, const TP<T, C> &tp, const Pr
     // gam, p hold z_N
     T lg[C], lp[C];
     T F = terminal<T, C, PR>(g, P, x, v, gam, p, lg, lp) + Q;
-    const T b = (quad == HJ_QUAD_RK4) ? (T)1 : (T)0;
+    const T b = (quad & HJ_QUAD_RECT) ? (T)0 : (T)1;
+    const int ode = quad & HJ_ODE_EULER;
     const int nseg = (N + K - 1) / K;
     for (int s = nseg - 1; s >= 0; --s) {
         const int n0 = s * K, n1 = min(N, n0 + K);
@@ -849,7 +877,7 @@ __device__ __forceinline__ T gradient(const Grp &g, const TP<T, C> &tp, const Pr
             for (int k = 0; k < C; ++k) { st[k] = zg[k]; st[C + k] = zp[k]; }
             if (n + 1 < n1) {
                 T Qd = 0, Qcd = 0;
-                rk4_step<T, C, FAM, PR>(g, tp, eps, h, HJ_QUAD_RK4, 0, zg, zp, Qd, Qcd);
+                rk4_step<T, C, FAM, PR>(g, tp, eps, h, ode, 0, zg, zp, Qd, Qcd);
             }
         }
         for (int n = n1 - 1; n >= n0; --n) {
@@ -857,7 +885,7 @@ __device__ __forceinline__ T gradient(const Grp &g, const TP<T, C> &tp, const Pr
             T ug[C], up[C];
 #pragma unroll
             for (int k = 0; k < C; ++k) { ug[k] = st[k]; up[k] = st[C + k]; }
-            if (quad == HJ_QUAD_RECT) {
+            if (quad & HJ_QUAD_RECT) {
                 // rectangle node at z_{n+1}: lam += h grad L(z_{n+1}); z_{n+1} is the
                 // next stored state, the next checkpoint, or z_N
                 T zeros[C], rg[C], rp[C], ng[C], np[C];
@@ -872,7 +900,16 @@ __device__ __forceinline__ T gradient(const Grp &g, const TP<T, C> &tp, const Pr
 #pragma unroll
                 for (int k = 0; k < C; ++k) { lg[k] = fma(h, rg[k], lg[k]); lp[k] = fma(h, rp[k], lp[k]); }
             }
-            adjoint_step<T, C, FAM, PR>(g, tp, eps, h, b, ug, up, lg, lp);
+            if (ode) {
+                T wg[C], wp[C], rg[C], rp[C];
+#pragma unroll
+                for (int k = 0; k < C; ++k) { wg[k] = h * lg[k]; wp[k] = h * lp[k]; }
+                vjp<T, C, FAM, PR>(g, tp, eps, ug, up, wg, wp, h * b, rg, rp);
+#pragma unroll
+                for (int k = 0; k < C; ++k) { lg[k] += rg[k]; lp[k] += rp[k]; }
+            } else {
+                adjoint_step<T, C, FAM, PR>(g, tp, eps, h, b, ug, up, lg, lp);
+            }
         }
     }
 #pragma unroll

@@ -27,7 +27,7 @@ HJ_FAM_QUAD_ISO, HJ_FAM_SPEED_QUAD, HJ_FAM_SMOOTH_NONCONVEX, HJ_FAM_LINEAR_QUAD 
 HJ_LAX, HJ_HOPF = 0, 1
 HJ_G_QUAD_SHIFT, HJ_G_DIAG_QUAD = 0, 1
 HJ_GRAD_FD_CENTRAL, HJ_GRAD_FD_FORWARD, HJ_GRAD_ADJOINT, HJ_GRAD_ADJOINT_CG = 0, 1, 2, 3
-HJ_QUAD_RK4, HJ_QUAD_RECT = 0, 1
+HJ_QUAD_RK4, HJ_QUAD_RECT, HJ_ODE_EULER = 0, 1, 2
 HJ_PREC_FP32, HJ_PREC_FP64 = 0, 1
 HJ_ST_CERTIFIED, HJ_ST_MAX_ITERS, HJ_ST_NONFINITE, HJ_ST_RESEEDED = 1, 2, 4, 8
 
@@ -158,7 +158,8 @@ def opts_from_dict(solver: Dict, precision: int = HJ_PREC_FP32, n_steps_default:
                    kahan: int = 1) -> hj_solver_opts:
     grad = {"fd_central": HJ_GRAD_FD_CENTRAL, "fd_forward": HJ_GRAD_FD_FORWARD, "adjoint": HJ_GRAD_ADJOINT,
             "adjoint_cg": HJ_GRAD_ADJOINT_CG}
-    quad = {"rk4": HJ_QUAD_RK4, "rect": HJ_QUAD_RECT}
+    quad = {"rk4": HJ_QUAD_RK4, "rect": HJ_QUAD_RECT, "euler": HJ_QUAD_RK4 | HJ_ODE_EULER,
+            "euler_rect": HJ_QUAD_RECT | HJ_ODE_EULER}
     return hj_solver_opts(n_steps_default, quad[solver["quad"]], grad[solver["grad"]], solver["fd_h"],
                           solver["step"], solver["max_iters"], solver["halving_period"], solver["eps"],
                           solver["adapt"], solver["grow"], solver["shrink"], solver["step_max"],

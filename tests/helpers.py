@@ -9,7 +9,8 @@ from paper_1704_02524_gb300 import workloads as W
 GRAD_CODES = {"fd_central": O.GRAD_FD_CENTRAL, "fd_forward": O.GRAD_FD_FORWARD, "adjoint": O.GRAD_ADJOINT,
               "adjoint_cg": O.GRAD_ADJOINT}
 DESCENT_CODES = {"fd_central": O.DESC_CD, "fd_forward": O.DESC_CD, "adjoint": O.DESC_GD, "adjoint_cg": O.DESC_CG}
-QUAD_CODES = {"rk4": O.QUAD_RK4, "rect": O.QUAD_RECT}
+QUAD_CODES = {"rk4": O.QUAD_RK4, "rect": O.QUAD_RECT, "euler": O.QUAD_RK4 | O.ODE_EULER,
+              "euler_rect": O.QUAD_RECT | O.ODE_EULER}
 
 
 def oracle_problem(spec: W.ProblemSpec) -> O.Problem:

@@ -56,6 +56,11 @@ def test_create_rejects_bad_arguments_without_a_gpu(lib):
     with pytest.raises(hj.HJError) as e:
         hj.hj_create([spec], o, 0)
     assert e.value.status == hj.HJ_EINVAL
+    o = hj.opts_from_dict(wl.solver)
+    o.quad = 4  # neither RK4/rectangle nor the Euler flag
+    with pytest.raises(hj.HJError) as e:
+        hj.hj_create([spec], o, 0)
+    assert e.value.status == hj.HJ_EINVAL and "quad" in str(e.value)
     neg = W.ProblemSpec(**{**spec.__dict__, "sigma": -np.ones(20)})
     with pytest.raises(hj.HJError) as e:
         hj.hj_create([neg], hj.opts_from_dict(wl.solver), 0)

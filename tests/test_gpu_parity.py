@@ -11,7 +11,7 @@ import torch
 
 import oracle as O
 from paper_1704_02524_gb300 import workloads as W
-from tests.helpers import oracle_opts, oracle_problem, rel_err
+from tests.helpers import QUAD_CODES, oracle_opts, oracle_problem, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -79,6 +79,47 @@ def test_functional_and_gradient_match_oracle(hj, family, principle, d, prec):
         scale = 1 + np.abs(Go).max()
         assert np.abs(G[i] - Go).max() <= (5e-4 if prec == "fp32" else 1e-9) * scale, (i, G[i], Go)
     ctx.close()
+
+
+@pytest.mark.parametrize("family,principle", FAMS)
+@pytest.mark.parametrize("quad", ["euler", "euler_rect"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_forward_euler_functional_gradient_and_certificate_match_oracle(hj, family, principle, quad, prec):
+    # forward Euler (Sec. 4.2's example solver) on every family: values,
+    # discrete-adjoint gradients and the FP64 certificate against the oracle
+    d = 13
+    spec = _spec(family, principle, d, seed=40 + d, s_eps=1e-2)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    solver = W.solver_constants(quad=quad, cert_tol=0.3)
+    ctx = hj.hj_create([spec], hj.opts_from_dict(solver, hj.HJ_PREC_FP32 if prec == "fp32" else hj.HJ_PREC_FP64, 32),
+                       0)
+    n = 67
+    x, v, t, N = _rows(n, d, 200 + family, prec)
+    args = (_t(x, dt), _t(t, dt), _t(v, dt), _t(N, torch.int32))
+    F = hj.hj_eval_functional(ctx, *args).cpu().numpy()
+    Fg, G = (a.cpu().numpy() for a in hj.hj_grad(ctx, *args))
+    Fc, R, Pa = (a.cpu().numpy() for a in hj.hj_certify(ctx, *args))
+    P = oracle_problem(spec)
+    q = QUAD_CODES[quad]
+    tolF = 2e-5 if prec == "fp32" else 1e-11
+    for i in range(n):
+        Fo, Go = O.gradient(P, x[i], t[i], int(N[i]), v[i], quad=q)
+        assert rel_err(F[i], Fo) <= tolF and rel_err(Fg[i], Fo) <= tolF, (i, F[i], Fo)
+        assert np.abs(G[i] - Go).max() <= (5e-4 if prec == "fp32" else 1e-9) * (1 + np.abs(Go).max()), i
+        Fco, Ro, ok = O.certify(P, x[i], t[i], int(N[i]), v[i], 0.3, quad=q)
+        assert rel_err(Fc[i], Fco) < 1e-11 and abs(R[i] - Ro) < 1e-11 and bool(Pa[i]) == ok, i
+    ctx.close()
+
+
+def test_solve_speed_quad_d10_with_forward_euler_matches_oracle(hj):
+    # the whole solve (descent on the Euler-discretised functional, reseeds,
+    # certificate) against the oracle run with the same integrator
+    wl = W.c2_speed_quad(nq_x=16)
+    wl.solver = dict(wl.solver, quad="euler")
+    phi, v, st, ref, info = _solve_both(hj, wl, 48)
+    assert np.all(rel_err(phi, ref["phi"]) <= 1e-4), rel_err(phi, ref["phi"]).max()
+    assert np.array_equal(st & 1, ref["status"] & 1)
+    assert info["rk4_steps"] > 0
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
@@ -164,10 +205,11 @@ def test_solve_smooth_nonconvex_d20_matches_oracle(hj):
 
 
 @pytest.mark.parametrize("ck", [1, 2, 3, 8, 16])
-@pytest.mark.parametrize("quad", ["rk4", "rect"])
+@pytest.mark.parametrize("quad", ["rk4", "rect", "euler", "euler_rect"])
 def test_gradient_checkpoint_intervals_and_quadrature(hj, ck, quad):
-    # every checkpoint interval (including ones that do not divide N) and
-    # both quadratures give the oracle's exact gradient of the discretised functional
+    # every checkpoint interval (including ones that do not divide N), both
+    # quadratures and both integrators give the oracle's exact gradient of
+    # the discretised functional
     spec = _spec(W.FAM_SMOOTH_NONCONVEX, W.HOPF, 20, seed=11, s_eps=1e-2)
     solver = W.solver_constants(quad=quad)
     ctx = hj.hj_create([spec], hj.opts_from_dict(solver, hj.HJ_PREC_FP32, 64), 0)
@@ -178,7 +220,7 @@ def test_gradient_checkpoint_intervals_and_quadrature(hj, ck, quad):
     F, G = hj.hj_grad(ctx, _t(x, torch.float32), _t(t, torch.float32), _t(v, torch.float32), _t(N, torch.int32))
     F, G = F.cpu().numpy(), G.cpu().numpy()
     P = oracle_problem(spec)
-    q = O.QUAD_RK4 if quad == "rk4" else O.QUAD_RECT
+    q = QUAD_CODES[quad]
     for i in range(n):
         Fo, Go = O.gradient(P, x[i], t[i], int(N[i]), v[i], quad=q)
         assert rel_err(F[i], Fo) <= 2e-5
