@@ -46,6 +46,10 @@ WORKLOADS = {
     "mixed_persistent": (lambda nq: W.c5_mixed(n_pairs=nq), 1 << 20,
                          "(query, start) pairs/s (mixed families, d in {8,16,32,100})",
                          "gradient descent (adjoint) for every problem"),
+    "bump_norm_d2_plus_lax_paper": (lambda nq: W.bump_ex3(n_side=max(1, int(round(nq ** 0.5)))), 16384,
+                                    "points/s (H = c(x)|p|, d=2 cross-section grid, the paper's numerics)",
+                                    "Algorithm 1 (cyclic coordinate descent, alpha halving), forward "
+                                    "differences, forward Euler with the rectangle rule"),
 }
 CPU_SAMPLE = 64          # queries of the oracle timing sample (cpu_baseline)
 REF_SAMPLE = 64          # queries per step of the reference arm

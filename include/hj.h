@@ -68,7 +68,9 @@ typedef enum {
     HJ_FAM_SPEED_QUAD = 1,       /* H = c(x)^2 |p|^2/2,  c = 1 + sin(<w,x>)/2                 */
     HJ_FAM_SMOOTH_NONCONVEX = 2, /* H = c(x) sum_i e_i s(p_i), s(q) = sqrt(q^2 + s_eps),
                                     e_i = -1 for i < n_neg, +1 otherwise                       */
-    HJ_FAM_LINEAR_QUAD = 3       /* H = <A x, p> + |B^T p|^2/2                               */
+    HJ_FAM_LINEAR_QUAD = 3,      /* H = <A x, p> + |B^T p|^2/2                               */
+    HJ_FAM_BUMP_NORM = 4         /* H = sign c(x) |p|_eps,  c = 1 + kappa exp(-mu |x - xc|^2),
+                                    |p|_eps = sqrt(|p|^2 + s_eps) (Sec. 6, Example 3)        */
 } hj_family;
 
 typedef enum { HJ_LAX = 0, HJ_HOPF = 1 } hj_principle;
@@ -76,7 +78,10 @@ typedef enum { HJ_LAX = 0, HJ_HOPF = 1 } hj_principle;
 /* Initial data g. */
 typedef enum {
     HJ_G_QUAD_SHIFT = 0,  /* g = |x - a|^2/2,          g* = |p|^2/2 + <a,p>       */
-    HJ_G_DIAG_QUAD = 1    /* g = sum x_i^2/(2 s_i^2),  g* = sum s_i^2 p_i^2/2     */
+    HJ_G_DIAG_QUAD = 1,   /* g = sum x_i^2/(2 s_i^2),  g* = sum s_i^2 p_i^2/2     */
+    HJ_G_ELLIPSE = 2      /* g = (sum x_i^2/s_i^2 - 1)/2, g* = (sum s_i^2 p_i^2 + 1)/2:
+                             zero level set the ellipse <x, Ax> = 1 with
+                             A = diag(1/s_i^2) (the initial data of Sec. 6)  */
 } hj_initial;
 
 typedef enum {
@@ -174,8 +179,9 @@ typedef struct {
  * params (HOST, double, copied by hj_create) holds, in order:
  *   family block:  SPEED_QUAD, SMOOTH_NONCONVEX: w[d]
  *                  LINEAR_QUAD: A[d*d] (row-major), then B[d*m] (row-major)
+ *                  BUMP_NORM: xc[d], then kappa, mu (>= 0), sign (+1 or -1)
  *                  QUAD_ISO: nothing
- *   g block:       HJ_G_QUAD_SHIFT: a[d];  HJ_G_DIAG_QUAD: s[d] (all > 0)
+ *   g block:       HJ_G_QUAD_SHIFT: a[d];  HJ_G_DIAG_QUAD, HJ_G_ELLIPSE: s[d] (all > 0)
  * n_params must equal the total.  d in [1, 1024]; m in [1, 64] for
  * LINEAR_QUAD (d in [1, 128] there), else ignored.  LINEAR_QUAD computes
  * B B^T once in double precision at hj_create and integrates
@@ -189,7 +195,8 @@ typedef struct {
     hj_initial g_kind;
     int m;             /* LINEAR_QUAD: columns of B                             */
     int n_neg;         /* SMOOTH_NONCONVEX: number of leading negative signs     */
-    double s_eps;      /* SMOOTH_NONCONVEX: smoothing of |q|, > 0                */
+    double s_eps;      /* SMOOTH_NONCONVEX: smoothing of |q|, > 0;
+                          BUMP_NORM: smoothing of |p|, >= 0 (0: the plain norm)  */
     int n_guesses;     /* random starts per query for hj_solve (0: the solver value) */
     const double *params;
     size_t n_params;

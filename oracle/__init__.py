@@ -39,9 +39,9 @@ _LIB_PATH = os.path.join(_HERE, "libhj_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD = 0, 1, 2, 3
+FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD, FAM_BUMP_NORM = 0, 1, 2, 3, 4
 LAX, HOPF = 0, 1
-G_QUAD_SHIFT, G_DIAG_QUAD = 0, 1
+G_QUAD_SHIFT, G_DIAG_QUAD, G_ELLIPSE = 0, 1, 2
 QUAD_RK4, QUAD_RECT = 0, 1
 ODE_EULER = 2  # or-ed into a quad argument: forward Euler instead of RK4
 GRAD_FD_CENTRAL, GRAD_FD_FORWARD, GRAD_ADJOINT = 0, 1, 2
@@ -66,7 +66,8 @@ class _Problem(C.Structure):
     _fields_ = [("d", C.c_int), ("family", C.c_int), ("principle", C.c_int), ("g_kind", C.c_int),
                 ("m", C.c_int), ("n_neg", C.c_int), ("s_eps", C.c_double),
                 ("w", C.POINTER(C.c_double)), ("A", C.POINTER(C.c_double)), ("B", C.POINTER(C.c_double)),
-                ("ga", C.POINTER(C.c_double)), ("gs", C.POINTER(C.c_double))]
+                ("ga", C.POINTER(C.c_double)), ("gs", C.POINTER(C.c_double)),
+                ("xc", C.POINTER(C.c_double)), ("kappa", C.c_double), ("mu", C.c_double), ("hsign", C.c_double)]
 
 
 class _Opts(C.Structure):
@@ -129,17 +130,22 @@ class Problem:
     sigma: Optional[np.ndarray] = None
     n_neg: int = 1
     s_eps: float = 1e-6
+    xc: Optional[np.ndarray] = None  # bump-norm family: centre of c(x)
+    kappa: float = 0.0               # bump-norm family: c(x) = 1 + kappa exp(-mu |x - xc|^2)
+    mu: float = 0.0
+    hsign: float = 1.0               # bump-norm family: H = hsign c(x) |p|
     _c: Optional[_Problem] = field(default=None, repr=False)
 
     def c(self) -> _Problem:
         if self._c is None:
-            for name in ("w", "A", "B", "a", "sigma"):
+            for name in ("w", "A", "B", "a", "sigma", "xc"):
                 v = getattr(self, name)
                 if v is not None:
                     setattr(self, name, _f64(v))
             m = 0 if self.B is None else int(self.B.shape[1])
             self._c = _Problem(self.d, self.family, self.principle, self.g_kind, m, self.n_neg, self.s_eps,
-                               _dp(self.w), _dp(self.A), _dp(self.B), _dp(self.a), _dp(self.sigma))
+                               _dp(self.w), _dp(self.A), _dp(self.B), _dp(self.a), _dp(self.sigma),
+                               _dp(self.xc), float(self.kappa), float(self.mu), float(self.hsign))
         return self._c
 
 

@@ -10,6 +10,13 @@
  * straight loops over coordinates, full storage of every RK4 stage for the
  * adjoint, one pair at a time.  Each function names the passage it follows.
  *
+ * Families: H = |p|^2/2; H = c(x)^2|p|^2/2 with c = 1 + sin<w,x>/2; the
+ * smooth non-convex H = c(x) sum_i e_i sqrt(p_i^2 + eps); the linear-
+ * quadratic H = <Ax,p> + |B^T p|^2/2; and H = +-c(x)|p| with the Gaussian
+ * bump speed c = 1 + kappa exp(-mu|x - xc|^2) of Sec. 6, Example 3.
+ * Initial data: |x - a|^2/2, sum x_i^2/(2 s_i^2), and the ellipse data
+ * (<x, Ax> - 1)/2, A diagonal, of Sec. 6.
+ *
  * What it computes, per (query x, time t, initial guess v):
  *   - the bi-characteristics (Sec. 4.1, final value problem):
  *         d gamma/ds = dH/dp,  dp/ds = -dH/dx,  gamma(t) = x,  p(t) = v,
@@ -46,9 +53,9 @@
 /* Problem description                                                       */
 /* ------------------------------------------------------------------------ */
 
-enum { FAM_QUAD_ISO = 0, FAM_SPEED_QUAD = 1, FAM_SMOOTH_NONCONVEX = 2, FAM_LINEAR_QUAD = 3 };
+enum { FAM_QUAD_ISO = 0, FAM_SPEED_QUAD = 1, FAM_SMOOTH_NONCONVEX = 2, FAM_LINEAR_QUAD = 3, FAM_BUMP_NORM = 4 };
 enum { LAX = 0, HOPF = 1 };
-enum { G_QUAD_SHIFT = 0, G_DIAG_QUAD = 1 };
+enum { G_QUAD_SHIFT = 0, G_DIAG_QUAD = 1, G_ELLIPSE = 2 };
 enum { QUAD_RK4 = 0, QUAD_RECT = 1 };
 /* Flag or-ed into a `quad` argument: integrate with forward Euler (the
  * solver Sec. 4.2 suggests) instead of RK4.  With QUAD_RK4 the running cost
@@ -75,7 +82,12 @@ typedef struct {
     const double *A;  /* [d*d] row-major drift matrix                           */
     const double *B;  /* [d*m] row-major control matrix                         */
     const double *ga; /* [d]   shift a of g = |x-a|^2/2                         */
-    const double *gs; /* [d]   sigma of g = sum x_i^2/(2 sigma_i^2)             */
+    const double *gs; /* [d]   sigma of g = sum x_i^2/(2 sigma_i^2) (- 1/2 for  */
+                      /*       the ellipse data of Sec. 6)                      */
+    /* bump-norm family (Sec. 6, Example 3): H = sign c(x) |p|_eps with
+     * c(x) = 1 + kappa exp(-mu |x - xc|^2), |p|_eps = sqrt(|p|^2 + s_eps) */
+    const double *xc; /* [d] */
+    double kappa, mu, hsign;
 } orc_problem;
 
 typedef struct {
@@ -183,6 +195,20 @@ static void speed(const orc_problem *P, const double *gam, double *u, double *c,
     *c2 = -0.5 * sin(*u);
 }
 
+/* Bump speed c(x) = 1 + kappa exp(-mu |x - xc|^2) with grad c = k (x - xc),
+ * k = -2 mu kappa exp(-mu |x - xc|^2); y receives x - xc. */
+static void bump(const orc_problem *P, const double *gam, double *y, double *c, double *k)
+{
+    double rr = 0.0;
+    for (int i = 0; i < P->d; ++i) {
+        y[i] = gam[i] - P->xc[i];
+        rr += y[i] * y[i];
+    }
+    double e = exp(-P->mu * rr);
+    *c = 1.0 + P->kappa * e;
+    *k = -2.0 * P->mu * P->kappa * e;
+}
+
 /* Hamiltonian value H(gamma, p). */
 static double ham(const orc_problem *P, const double *gam, const double *p)
 {
@@ -213,6 +239,11 @@ static double ham(const orc_problem *P, const double *gam, const double *p)
             h += 0.5 * btp * btp;
         }
         return h;
+    }
+    case FAM_BUMP_NORM: {
+        double y[ORC_DMAX], c, k;
+        bump(P, gam, y, &c, &k);
+        return P->hsign * c * sqrt(dot(p, p, d) + P->s_eps);
     }
     }
     return NAN;
@@ -262,6 +293,17 @@ static void ham_grads(const orc_problem *P, const double *gam, const double *p, 
             for (int k = 0; k < P->m; ++k) bbtp += P->B[i * P->m + k] * btp[k];
             Hp[i] = ax + bbtp;
             Hx[i] = atp;
+        }
+        return;
+    }
+    case FAM_BUMP_NORM: {
+        /* H_p = sign c p / |p|_eps,  H_x = sign |p|_eps grad c */
+        double y[ORC_DMAX], c, k;
+        bump(P, gam, y, &c, &k);
+        double n = sqrt(dot(p, p, d) + P->s_eps);
+        for (int i = 0; i < d; ++i) {
+            Hp[i] = P->hsign * c * p[i] / n;
+            Hx[i] = P->hsign * n * k * y[i];
         }
         return;
     }
@@ -376,13 +418,41 @@ static void field_vjp(const orc_problem *P, const double *z, const double *a, do
         }
         return;
     }
+    case FAM_BUMP_NORM: {
+        /* field_gamma = -S c p/n, field_p = S n k y with y = gamma - xc,
+         * n = |p|_eps, grad c = k y, grad k = -2 mu k y;
+         * Lax L = S c (|p|^2/n - n) = -S c eps/n;
+         * Hopf L = H - <H_x, gamma> = S n (c - k <y, gamma>) */
+        double y[ORC_DMAX], c, k;
+        bump(P, gam, y, &c, &k);
+        const double S = P->hsign, eps = P->s_eps, mu = P->mu;
+        double n = sqrt(dot(p, p, d) + eps);
+        double Agp = dot(ag, p, d), Apy = dot(ap, y, d), yg = dot(y, gam, d);
+        for (int i = 0; i < d; ++i) {
+            /* d/dgamma of <ag, field_gamma> and <ap, field_p> */
+            double g_i = -S * (Agp / n) * k * y[i] + S * n * (-2.0 * mu * k * Apy * y[i] + k * ap[i]);
+            /* d/dp of the same */
+            double p_i = -S * c * (ag[i] / n - Agp * p[i] / (n * n * n)) + S * k * Apy * p[i] / n;
+            if (P->principle == LAX) {
+                g_i += b * (-S * eps / n) * k * y[i];
+                p_i += b * S * c * eps * p[i] / (n * n * n);
+            } else {
+                /* d<y,gamma>/dgamma = y + gamma */
+                g_i += b * S * n * (k * y[i] + 2.0 * mu * k * yg * y[i] - k * (y[i] + gam[i]));
+                p_i += b * S * (c - k * yg) * p[i] / n;
+            }
+            rg[i] = g_i;
+            rp[i] = p_i;
+        }
+        return;
+    }
     }
 }
 
 /* Initial data g, its gradient, its Legendre transform g* and grad g*. */
 static double g_val(const orc_problem *P, const double *x)
 {
-    double s = 0.0;
+    double s = (P->g_kind == G_ELLIPSE) ? -0.5 : 0.0;
     for (int i = 0; i < P->d; ++i) {
         if (P->g_kind == G_QUAD_SHIFT) {
             double a = P->ga ? P->ga[i] : 0.0;
@@ -400,7 +470,8 @@ static void g_grad(const orc_problem *P, const double *x, double *out)
 }
 static double gstar_val(const orc_problem *P, const double *p)
 {
-    double s = 0.0;
+    /* the ellipse data's constant -1/2 becomes +1/2 in the transform */
+    double s = (P->g_kind == G_ELLIPSE) ? 0.5 : 0.0;
     for (int i = 0; i < P->d; ++i) {
         if (P->g_kind == G_QUAD_SHIFT) s += 0.5 * p[i] * p[i] + (P->ga ? P->ga[i] : 0.0) * p[i];
         else s += 0.5 * P->gs[i] * P->gs[i] * p[i] * p[i];

@@ -33,6 +33,10 @@ void reg_f32_lq_lax(Registry &);
 void reg_f32_lq_hopf(Registry &);
 void reg_f64_lq_lax(Registry &);
 void reg_f64_lq_hopf(Registry &);
+void reg_f32_bn_lax(Registry &);
+void reg_f32_bn_hopf(Registry &);
+void reg_f64_bn_lax(Registry &);
+void reg_f64_bn_hopf(Registry &);
 
 Registry &registry()
 {
@@ -54,6 +58,10 @@ Registry &registry()
         reg_f32_lq_hopf(*x);
         reg_f64_lq_lax(*x);
         reg_f64_lq_hopf(*x);
+        reg_f32_bn_lax(*x);
+        reg_f32_bn_hopf(*x);
+        reg_f64_bn_lax(*x);
+        reg_f64_bn_hopf(*x);
         return x;
     }();
     return *r;
@@ -97,6 +105,10 @@ FlopModel flop_model(int fam, int pr, int d, int quad)
         fld = 6.0 * d * d + 3.0 * d + 1;
         vjp = 6.0 * d * d + 2.0 * d;
         break;
+    case HJ_FAM_BUMP_NORM:
+        fld = (pr == HJ_HOPF ? 9.0 : 7.0) * d + 14;
+        vjp = (pr == HJ_HOPF ? 10.0 : 8.0) * d + 24;
+        break;
     default: break;
     }
     if (quad & HJ_ODE_EULER) return FlopModel{fld + 4.0 * d + 2, vjp + 4.0 * d + 1};
@@ -125,6 +137,16 @@ void fill_prob(const hj_problem_desc &D, const std::vector<double> &par, int ld,
     if (D.family == HJ_FAM_SPEED_QUAD || D.family == HJ_FAM_SMOOTH_NONCONVEX) {
         for (int i = 0; i < d; ++i) w[i] = (T)par[i];
         off = d;
+    }
+    P.kappa = P.mu = (T)0;
+    P.hsign = (T)1;
+    if (D.family == HJ_FAM_BUMP_NORM) {
+        // the centre xc takes the w slot; kappa, mu and the sign are scalars
+        for (int i = 0; i < d; ++i) w[i] = (T)par[i];
+        P.kappa = (T)par[d];
+        P.mu = (T)par[d + 1];
+        P.hsign = (T)par[d + 2];
+        off = d + 3;
     }
     if (D.family == HJ_FAM_LINEAR_QUAD) {
         // At[j][i] = A[i][j], A[j][i], Cm = B B^T (double sums, then rounded),
@@ -266,6 +288,7 @@ size_t expected_params(const hj_problem_desc &D)
     size_t n = 0;
     if (D.family == HJ_FAM_SPEED_QUAD || D.family == HJ_FAM_SMOOTH_NONCONVEX) n += D.d;
     if (D.family == HJ_FAM_LINEAR_QUAD) n += (size_t)D.d * D.d + (size_t)D.d * D.m;
+    if (D.family == HJ_FAM_BUMP_NORM) n += D.d + 3;
     n += D.d;
     return n;
 }
@@ -273,11 +296,11 @@ size_t expected_params(const hj_problem_desc &D)
 hj_status validate_problem(hj_ctx *ctx, const hj_problem_desc &D, int idx)
 {
     if (D.d < 1 || D.d > DPAD) return fail(ctx, HJ_EINVAL, "problem %d: d=%d outside [1, %d]", idx, D.d, DPAD);
-    if (D.family < HJ_FAM_QUAD_ISO || D.family > HJ_FAM_LINEAR_QUAD)
+    if (D.family < HJ_FAM_QUAD_ISO || D.family > HJ_FAM_BUMP_NORM)
         return fail(ctx, HJ_EINVAL, "problem %d: unknown family %d", idx, (int)D.family);
     if (D.principle != HJ_LAX && D.principle != HJ_HOPF)
         return fail(ctx, HJ_EINVAL, "problem %d: unknown principle %d", idx, (int)D.principle);
-    if (D.g_kind != HJ_G_QUAD_SHIFT && D.g_kind != HJ_G_DIAG_QUAD)
+    if (D.g_kind != HJ_G_QUAD_SHIFT && D.g_kind != HJ_G_DIAG_QUAD && D.g_kind != HJ_G_ELLIPSE)
         return fail(ctx, HJ_EINVAL, "problem %d: unknown initial data %d", idx, (int)D.g_kind);
     if (D.family == HJ_FAM_LINEAR_QUAD) {
         if (D.m < 1 || D.m > 64 || D.d > 128)
@@ -293,7 +316,14 @@ hj_status validate_problem(hj_ctx *ctx, const hj_problem_desc &D, int idx)
     size_t off = expected_params(D) - D.d;
     for (size_t i = 0; i < D.n_params; ++i)
         if (!std::isfinite(D.params[i])) return fail(ctx, HJ_EINVAL, "problem %d: params[%zu] not finite", idx, i);
-    if (D.g_kind == HJ_G_DIAG_QUAD)
+    if (D.family == HJ_FAM_BUMP_NORM) {
+        if (!(D.s_eps >= 0) || !std::isfinite(D.s_eps))
+            return fail(ctx, HJ_EINVAL, "problem %d: s_eps must be >= 0", idx);
+        const double *sc = D.params + D.d;
+        if (!(sc[1] >= 0)) return fail(ctx, HJ_EINVAL, "problem %d: bump mu must be >= 0", idx);
+        if (sc[2] != 1.0 && sc[2] != -1.0) return fail(ctx, HJ_EINVAL, "problem %d: bump sign must be +1 or -1", idx);
+    }
+    if (D.g_kind == HJ_G_DIAG_QUAD || D.g_kind == HJ_G_ELLIPSE)
         for (int i = 0; i < D.d; ++i)
             if (!(D.params[off + i] > 0)) return fail(ctx, HJ_EINVAL, "problem %d: sigma[%d] must be > 0", idx, i);
     return HJ_OK;
@@ -401,6 +431,7 @@ void *as_ptr(T *p) { return (void *)p; }
 bool tc_eligible(const hj_ctx *ctx, int p)
 {
     return ctx->prec == 0 && ctx->dev[p].tc && ctx->tpp_override[p] == 0 && ctx->opts.quad == HJ_QUAD_RK4 &&
+           ctx->desc[p].g_kind != HJ_G_ELLIPSE &&
            ctx->popts[p].coarse_div <= 1;
 }
 

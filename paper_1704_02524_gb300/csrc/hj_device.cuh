@@ -33,7 +33,8 @@ template <typename T>
 struct ProbDev {
     int d, family, principle, g_kind, m, n_neg, n_guesses, ld;
     T s_eps;
-    const T *w;     // [DPAD] speed direction
+    T kappa, mu, hsign;  // bump-norm family: c = 1 + kappa exp(-mu |x - xc|^2), H = hsign c |p|
+    const T *w;     // [DPAD] speed direction (bump-norm family: the centre xc)
     const T *e;     // [DPAD] signs of the smooth non-convex family (0 past d)
     const T *ga;    // [DPAD] shift a of g = |x-a|^2/2
     const T *gs2;   // [DPAD] sigma^2 of g = sum x^2/(2 sigma^2)
@@ -114,13 +115,15 @@ __device__ __forceinline__ T gmax(const Grp &g, T x)
 
 // ---------------------------------------------------------------------------
 // Precision-dispatched math.  fp32 uses the hardware reciprocal square root
-// and the fast sine/cosine (|<w,gamma>| stays O(1) in these problems); fp64
-// uses the correctly rounded library routines.
+// and the fast sine/cosine/exponential (|<w,gamma>| stays O(1) in these
+// problems, and the bump's exponent is <= 0); fp64 uses the library routines.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float rsq(float q) { return rsqrtf(q); }
 __device__ __forceinline__ double rsq(double q) { return rsqrt(q); }
 __device__ __forceinline__ void sin_cos(float u, float *s, float *c) { __sincosf(u, s, c); }
 __device__ __forceinline__ void sin_cos(double u, double *s, double *c) { sincos(u, s, c); }
+__device__ __forceinline__ float exp_(float x) { return __expf(x); }
+__device__ __forceinline__ double exp_(double x) { return exp(x); }
 __device__ __forceinline__ bool finite_(float x) { return isfinite(x); }
 __device__ __forceinline__ bool finite_(double x) { return isfinite(x); }
 
@@ -181,11 +184,15 @@ __device__ __forceinline__ T start_component(unsigned long long seed, long long 
 template <typename T, int C>
 struct TP {
     T w[C], e[C];
+    T kap, mu, sg;
     const T *At, *A, *Cm;
     T *sh;
     int d, ldm;
     __device__ void load(const ProbDev<T> &P, const Grp &g)
     {
+        kap = P.kappa;
+        mu = P.mu;
+        sg = P.hsign;
 #pragma unroll
         for (int k = 0; k < C; ++k) {
             int i = g.lane + k * g.tpp;
@@ -324,6 +331,91 @@ struct Family<T, C, HJ_FAM_SPEED_QUAD, PR> {
         for (int k = 0; k < C; ++k) {
             rg[k] = dEdu * tp.w[k];
             rp[k] = fma(mc2, ag[k], kp * f.p[k]);
+        }
+    }
+};
+
+// H = S c(gamma) |p|_n with c = 1 + kappa exp(-mu |y|^2), y = gamma - xc
+// (xc held in w), grad c = k y with k = -2 mu kappa exp(-mu |y|^2),
+// n = |p|_eps = sqrt(|p|^2 + eps):
+// dZ/dtau = (-S c p / n, S n k y),
+// L_Lax = S c (|p|^2/n - n) = -S c eps / n,  L_Hopf = S n (c - k <y, gamma>).
+// With grad k = -2 mu k y and dn/dp = p/n the vector-Jacobian product is
+//   rg = (-S k <ag,p>/n - 2 mu S n k <ap,y>) y + S n k ap
+//        + b (Lax: -S eps k / n y;  Hopf: S n k (2 mu <y,gamma> y - gamma)),
+//   rp = -S c / n ag + (S c <ag,p>/n^3 + S k <ap,y>/n) p
+//        + b (Lax: S c eps / n^3;  Hopf: S (c - k <y,gamma>) / n) p.
+template <typename T, int C, int PR>
+struct Family<T, C, HJ_FAM_BUMP_NORM, PR> {
+    struct FI {
+        T c, k, n, ninv, yg;
+        T y[C], p[C];
+    };
+    __device__ static __forceinline__ void prep(const Grp &g, const TP<T, C> &tp, T eps, const T *gam, const T *p,
+                                                FI &f)
+    {
+        T rr = 0, pp = 0, yg = 0;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            const T y = gam[k] - tp.w[k];
+            f.y[k] = y;
+            f.p[k] = p[k];
+            rr = fma(y, y, rr);
+            pp = fma(p[k], p[k], pp);
+            if (PR == HJ_HOPF) yg = fma(y, gam[k], yg);
+        }
+        if (PR == HJ_HOPF) gsum3(g, rr, pp, yg);
+        else gsum2(g, rr, pp);
+        const T e = exp_(-tp.mu * rr);
+        f.c = fma(tp.kap, e, (T)1);
+        f.k = (T)-2 * tp.mu * tp.kap * e;
+        const T q = pp + eps;
+        f.ninv = rsq(q);
+        f.n = q * f.ninv;
+        f.yg = yg;
+    }
+    __device__ static __forceinline__ void field_fi(const TP<T, C> &tp, const FI &f, T eps, T *dg, T *dp, T &L)
+    {
+        const T a = -tp.sg * f.c * f.ninv, b = tp.sg * f.n * f.k;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            dg[k] = a * f.p[k];
+            dp[k] = b * f.y[k];
+        }
+        if (PR == HJ_LAX) L = -tp.sg * f.c * eps * f.ninv;
+        else L = tp.sg * f.n * (f.c - f.k * f.yg);
+    }
+    __device__ static __forceinline__ void vjp_fi(const Grp &g, const TP<T, C> &tp, const FI &f, T eps, const T *ag,
+                                                  const T *ap, T b, T *rg, T *rp)
+    {
+        T A = 0, By = 0;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            A = fma(ag[k], f.p[k], A);
+            By = fma(ap[k], f.y[k], By);
+        }
+        gsum2(g, A, By);
+        const T S = tp.sg, n = f.n, ni = f.ninv, c = f.c, kk = f.k, mu = tp.mu;
+        const T ni3 = ni * ni * ni;
+        const T snk = S * n * kk;
+        T cy = -S * kk * A * ni - (T)2 * mu * snk * By;
+        T cgam = 0;
+        T cp = S * c * A * ni3 + S * kk * By * ni;
+        if (PR == HJ_LAX) {
+            cy -= b * S * eps * kk * ni;
+            cp += b * S * c * eps * ni3;
+        } else {
+            cy += b * (T)2 * mu * snk * f.yg;
+            cgam = -b * snk;
+            cp += b * S * (c - kk * f.yg) * ni;
+        }
+        const T cag = -S * c * ni;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            T r = fma(cy, f.y[k], snk * ap[k]);
+            if (PR == HJ_HOPF) r = fma(cgam, f.y[k] + tp.w[k], r);
+            rg[k] = r;
+            rp[k] = fma(cag, ag[k], cp * f.p[k]);
         }
     }
 };
@@ -610,7 +702,10 @@ __device__ __forceinline__ T terminal(const Grp &g, const ProbDev<T> &P, const T
             if (sg) { sg[k] = 0; sp[k] = gr; }
         }
     }
-    return gsum(g, acc);
+    acc = gsum(g, acc);
+    // the ellipse data's constant: g - 1/2 (Lax), g* + 1/2 (Hopf)
+    if (P.g_kind == HJ_G_ELLIPSE) acc += (PR == HJ_LAX) ? (T)-0.5 : (T)0.5;
+    return acc;
 }
 
 // Relative certificate residual (Sec. 4.3) from (gamma(0), p(0)).

@@ -1,0 +1,10 @@
+// hj_inst_f32_bn_lax.cu -- float kernels of the bump-norm family, Lax principle.
+#include "hj_inst.cuh"
+
+namespace hjd {
+void reg_f32_bn_lax(Registry &r)
+{
+    register_compute<float, HJ_FAM_BUMP_NORM, HJ_LAX, 1, 2, 4, 8>(r);
+    register_cert<float, HJ_FAM_BUMP_NORM, HJ_LAX, 1, 2, 4>(r);
+}
+}  // namespace hjd

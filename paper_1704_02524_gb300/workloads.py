@@ -23,9 +23,9 @@ from typing import Dict, List, Optional
 
 import numpy as np
 
-FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD = 0, 1, 2, 3
+FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD, FAM_BUMP_NORM = 0, 1, 2, 3, 4
 LAX, HOPF = 0, 1
-G_QUAD_SHIFT, G_DIAG_QUAD = 0, 1
+G_QUAD_SHIFT, G_DIAG_QUAD, G_ELLIPSE = 0, 1, 2
 
 HARNESS_SEED = 0x170402524
 
@@ -50,20 +50,27 @@ class ProblemSpec:
     A: Optional[np.ndarray] = None       # [d,d] drift
     B: Optional[np.ndarray] = None       # [d,m] control
     a: Optional[np.ndarray] = None       # [d]   g = |x-a|^2/2
-    sigma: Optional[np.ndarray] = None   # [d]   g = sum x_i^2/(2 sigma_i^2)
+    sigma: Optional[np.ndarray] = None   # [d]   g = sum x_i^2/(2 sigma_i^2) (ellipse data: minus 1/2)
     n_neg: int = 1
     s_eps: float = 1e-6
     n_guesses: int = 1
     solver: Optional[Dict] = None        # this problem's descent constants (None: the workload's)
+    xc: Optional[np.ndarray] = None      # [d]   bump-norm family: H = hsign c(x)|p|,
+    kappa: float = 0.0                   #       c = 1 + kappa exp(-mu |x - xc|^2)
+    mu: float = 0.0
+    hsign: float = 1.0
 
     def params(self) -> np.ndarray:
         """Flat parameter vector in the library's documented order:
-        family block (w | A row-major then B row-major), then g block (a | sigma)."""
+        family block (w | A row-major then B row-major | xc, kappa, mu, sign),
+        then g block (a | sigma)."""
         parts: List[np.ndarray] = []
         if self.family in (FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX):
             parts.append(self.w)
         if self.family == FAM_LINEAR_QUAD:
             parts += [self.A.reshape(-1), self.B.reshape(-1)]
+        if self.family == FAM_BUMP_NORM:
+            parts += [self.xc, np.array([self.kappa, self.mu, self.hsign])]
         parts.append(self.a if self.g_kind == G_QUAD_SHIFT else self.sigma)
         return np.concatenate([np.asarray(p, dtype=np.float64).reshape(-1) for p in parts])
 
@@ -265,12 +272,62 @@ def c5_mixed(n_pairs: int = 1 << 20) -> Workload:
     return Workload("mixed_persistent", probs, x, t, N, pidx, solver_constants(), "fp32")
 
 
+def paper_solver(**over) -> Dict:
+    """The paper's own numerics (Sec. 5, Sec. 6): forward Euler with the
+    rectangle rule, forward differences (eq. num_diff), and Algorithm 1 with
+    alpha = 1/L, halving every M = 500 iterations and eps = 0.5e-7; random
+    starts uniform in [-2,2]^d and no reseeding (Sec. 6 makes one start per
+    convex problem and up to 20 independent ones otherwise).  The paper sets
+    no iteration cap; 20000 coordinate moves is twice what the d=2 runs
+    below need after the halvings have shrunk alpha."""
+    c = solver_constants(quad="euler_rect", grad="fd_forward", fd_h=1e-3, step=1.0 / 0.02, max_iters=20000,
+                         halving_period=500, eps=0.5e-7, adapt=0, n_guesses=5, max_trials=5, max_rounds=0,
+                         coarse_div=1)
+    c.update(over)
+    return c
+
+
+def ellipse_sigma(d: int) -> np.ndarray:
+    """sigma of the ellipse data of Sec. 6: A^-1 = diag(1, 25/4, 1/4, ...)."""
+    s = np.full(d, 0.5)
+    s[0] = 1.0
+    if d > 1:
+        s[1] = 2.5
+    return s
+
+
+def bump_ex3(n_side: int = 128, d: int = 2, sign: float = 1.0, t: float = 0.3, ds: float = 0.02,
+             fd_h: float = 1e-3, n_guesses: int = 5, precision: str = "fp32") -> Workload:
+    """Sec. 6 Example 3 in the paper's numerics: H = sign c(x)|p| with
+    c = 1 + 3 exp(-4 |x - (1,1,0,...)|^2), the ellipse data g, the Lax
+    functional, on the n_side x n_side grid over the cross-section
+    [-3,3]^2 x {0}^(d-2) at time t (0.3 for H+, as in the paper's d=2 run),
+    forward Euler with step ds (N = t/ds), forward differences with step
+    fd_h and L = 0.02, five starts per point (the paper's time format
+    counts five).  Nothing is random but the starts."""
+    g = np.linspace(-3.0, 3.0, n_side)
+    X = np.zeros((n_side * n_side, d))
+    X[:, 0] = np.repeat(g, n_side)
+    X[:, 1] = np.tile(g, n_side)
+    X = f32(X)
+    xc = np.zeros(d)
+    xc[:2] = 1.0
+    P = ProblemSpec(d=d, family=FAM_BUMP_NORM, principle=LAX, g_kind=G_ELLIPSE, sigma=ellipse_sigma(d), xc=xc,
+                    kappa=3.0, mu=4.0, hsign=sign, s_eps=0.0, n_guesses=n_guesses)
+    nq = X.shape[0]
+    N = int(round(t / ds))
+    name = f"bump_norm_d{d}_{'plus' if sign > 0 else 'minus'}_lax_paper"
+    return Workload(name, [P], X, np.full(nq, t), np.full(nq, N, np.int32), np.zeros(nq, np.int32),
+                    paper_solver(fd_h=fd_h, n_guesses=n_guesses, max_trials=n_guesses), precision)
+
+
 WORKLOADS = {
     "quad_iso_d2_lax": c1_quad_iso,
     "speed_quad_d10_lax": c2_speed_quad,
     "smooth_nonconvex_d20_hopf": c3_smooth_nonconvex,
     "linear_quad_d64_lax": c4_linear_quad,
     "mixed_persistent": c5_mixed,
+    "bump_norm_d2_plus_lax_paper": bump_ex3,
 }
 
 

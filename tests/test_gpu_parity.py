@@ -28,7 +28,7 @@ def hj():
 def _spec(family, principle, d, seed=0, n_neg=1, s_eps=1e-6, g_kind=None, m=None):
     rng = np.random.default_rng(seed)
     if g_kind is None:
-        g_kind = W.G_DIAG_QUAD if family == W.FAM_SMOOTH_NONCONVEX else W.G_QUAD_SHIFT
+        g_kind = {W.FAM_SMOOTH_NONCONVEX: W.G_DIAG_QUAD, W.FAM_BUMP_NORM: W.G_ELLIPSE}.get(family, W.G_QUAD_SHIFT)
     A = B = None
     if family == W.FAM_LINEAR_QUAD:
         G0 = rng.normal(size=(d, d))
@@ -36,7 +36,9 @@ def _spec(family, principle, d, seed=0, n_neg=1, s_eps=1e-6, g_kind=None, m=None
         B = W.f32(rng.normal(size=(d, m or max(1, d // 2))) / np.sqrt(d))
     return W.ProblemSpec(d=d, family=family, principle=principle, g_kind=g_kind,
                          w=W.f32(rng.normal(size=d) / np.sqrt(d)), a=W.f32(rng.uniform(-1, 1, d)),
-                         sigma=W.f32(rng.uniform(0.5, 2, d)), A=A, B=B, n_neg=n_neg, s_eps=s_eps, n_guesses=4)
+                         sigma=W.f32(rng.uniform(0.5, 2, d)), A=A, B=B, n_neg=n_neg, s_eps=s_eps, n_guesses=4,
+                         xc=W.f32(rng.uniform(-0.5, 0.5, d)), kappa=3.0, mu=1.5,
+                         hsign=1.0 if principle == W.LAX else -1.0)
 
 
 def _rows(n, d, seed, prec):
@@ -54,7 +56,7 @@ def _t(a, dtype):
 
 FAMS = [(W.FAM_QUAD_ISO, W.LAX), (W.FAM_QUAD_ISO, W.HOPF), (W.FAM_SPEED_QUAD, W.LAX), (W.FAM_SPEED_QUAD, W.HOPF),
         (W.FAM_SMOOTH_NONCONVEX, W.HOPF), (W.FAM_SMOOTH_NONCONVEX, W.LAX), (W.FAM_LINEAR_QUAD, W.LAX),
-        (W.FAM_LINEAR_QUAD, W.HOPF)]
+        (W.FAM_LINEAR_QUAD, W.HOPF), (W.FAM_BUMP_NORM, W.LAX), (W.FAM_BUMP_NORM, W.HOPF)]
 
 
 @pytest.mark.parametrize("family,principle", FAMS)
@@ -120,6 +122,21 @@ def test_solve_speed_quad_d10_with_forward_euler_matches_oracle(hj):
     assert np.all(rel_err(phi, ref["phi"]) <= 1e-4), rel_err(phi, ref["phi"]).max()
     assert np.array_equal(st & 1, ref["status"] & 1)
     assert info["rk4_steps"] > 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_paper_mode_example3_solve_matches_oracle(hj, prec):
+    # Sec. 6 Example 3 (H+ = c(x)|p|, ellipse data, t = 0.3) in the paper's
+    # numerics -- forward Euler, rectangle rule, forward differences,
+    # Algorithm 1 with halving, five starts -- on 96 points spread over the
+    # [-3,3]^2 grid, against the oracle run with the same constants
+    wl = W.bump_ex3(n_side=128, precision=prec)
+    w = wl.take(np.arange(0, wl.nq, wl.nq // 96)[:96])
+    phi, v, st, ref, info = _solve_both(hj, w, w.nq)
+    err = rel_err(phi, ref["phi"])
+    assert np.all(err <= 1e-4), (err.max(), int(np.argmax(err)))
+    assert np.array_equal(st & 1, ref["status"] & 1)
+    assert info["iterations"] > 0
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])

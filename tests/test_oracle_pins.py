@@ -11,6 +11,7 @@ import os
 import numpy as np
 import pytest
 import scipy.integrate
+import scipy.optimize
 
 import oracle as O
 from paper_1704_02524_gb300 import workloads as W
@@ -259,6 +260,138 @@ def test_euler_first_order_convergence_state_dependent():
 
 
 # --------------------------------------------------------------------------
+# H = +-c(x)|p| with the ellipse data (Sec. 6, Example 3)
+# --------------------------------------------------------------------------
+
+ELL_SIG = np.array([1.0, 2.5])  # A^-1 = diag(1, 25/4)
+
+
+def _g_ellipse(y, sig=ELL_SIG):
+    return 0.5 * (np.sum(y ** 2 / sig ** 2, axis=-1) - 1.0)
+
+
+def _p_bump(principle=O.LAX, kappa=3.0, hsign=1.0, s_eps=0.0, d=2, sig=ELL_SIG):
+    xc = np.zeros(d)
+    xc[:2] = 1.0
+    return O.Problem(d=d, family=O.FAM_BUMP_NORM, principle=principle, g_kind=O.G_ELLIPSE, sigma=sig, xc=xc,
+                     kappa=kappa, mu=4.0, hsign=hsign, s_eps=s_eps)
+
+
+@pytest.mark.parametrize("quad", [O.QUAD_RK4, O.QUAD_RECT, EULER, EULER_RECT])
+@pytest.mark.parametrize("hsign", [1.0, -1.0])
+def test_bump_norm_with_flat_speed_closed_form(quad, hsign):
+    # kappa = 0: H = S|p| is state independent, p stays v and gamma moves on
+    # the straight line x - S t v/|v| (exact for every integrator); the Lax
+    # running cost <p,H_p> - H vanishes, the Hopf one is S|v|, so
+    #   F = g(x - S t v/|v|),  G = g*(v) + S t |v| - <x, v>,
+    # with g = (<x,Ax> - 1)/2 and g* = (<p,A^-1 p> + 1)/2.
+    rng = np.random.default_rng(33)
+    for principle in (O.LAX, O.HOPF):
+        P = _p_bump(principle, kappa=0.0, hsign=hsign)
+        for _ in range(4):
+            x, v, t = rng.uniform(-2, 2, 2), rng.uniform(-2, 2, 2), rng.uniform(0.1, 1)
+            F = O.functional(P, x, t, 11, v, quad=quad)
+            if principle == O.LAX:
+                expect = _g_ellipse(x - hsign * t * v / np.linalg.norm(v))
+            else:
+                expect = 0.5 * (np.sum(ELL_SIG ** 2 * v ** 2) + 1) + hsign * t * np.linalg.norm(v) - x @ v
+            assert abs(F - expect) < 1e-13, (principle, F, expect)
+
+
+def _circle_min(x, t):
+    # exact Hopf-Lax value for H = |p| where the disc |y - x| <= t misses the
+    # minimiser of g: the minimum of g over the circle |y - x| = t
+    th = np.linspace(0, 2 * np.pi, 400001)
+    y = x[None, :] - t * np.stack([np.cos(th), np.sin(th)], 1)
+    k = int(np.argmin(_g_ellipse(y)))
+    f = lambda a: _g_ellipse(x - t * np.array([np.cos(a), np.sin(a)]))
+    r = scipy.optimize.minimize_scalar(f, bracket=(th[k] - 1e-4, th[k], th[k] + 1e-4), tol=1e-14)
+    return r.fun
+
+
+def _paper_opts(fd_h=1e-3, guesses=5):
+    return O.Opts(quad=EULER_RECT, descent=O.DESC_CD, grad=O.GRAD_FD_FORWARD, fd_h=fd_h, step=1 / 0.02,
+                  max_iters=20000, halving_period=500, eps=0.5e-7, n_guesses=guesses, max_trials=guesses,
+                  max_rounds=0, seed=7, cert_tol=1e-3)
+
+
+def test_paper_mode_eikonal_matches_minimum_over_circle():
+    # kappa = 0 (c = 1): the paper's numerics (Euler, rectangle rule, forward
+    # differences, Algorithm 1 with halving) on the Lax functional reach the
+    # exact Hopf-Lax value to the O(sigma^2) bias of the forward differences
+    P = _p_bump(kappa=0.0)
+    t = 0.3
+    xq = np.array([[-0.93, -0.35], [1.2, -0.5], [-1.5, 0.8], [0.4, 1.9], [2.2, 1.0], [-0.2, -2.4]])
+    phi = O.solve(P, _paper_opts(), xq, t, 15)["phi"]
+    for q in range(len(xq)):
+        assert abs(phi[q] - _circle_min(xq[q], t)) < 2e-6, q
+
+
+def test_bump_norm_lax_matches_lax_friedrichs():
+    # Example 3's H+ at t = 0.3 (the bump makes the characteristics bend)
+    # against the paper's d=2 comparison scheme: first-order convergence of
+    # Lax-Friedrichs to the oracle's RK4 value, and Richardson extrapolation
+    # landing on it, at points whose reachable set misses the minimiser of g
+    P = _p_bump()
+    t = 0.3
+    opts = O.Opts(descent=O.DESC_GD, grad=O.GRAD_ADJOINT, step=0.05, max_iters=3000, eps=1e-12, adapt=1,
+                  grow=1.2, shrink=0.5, step_max=1.0, n_guesses=8, max_trials=8, max_rounds=0, seed=3,
+                  cert_tol=1e-3)
+    xq = np.array([[-0.93, -0.35], [1.2, -0.5], [-1.5, 0.8], [0.8, 1.6], [-0.5, 1.8], [1.6, 1.2], [0.3, -1.0]])
+    phi = O.solve(P, opts, xq, t, 60)["phi"]
+
+    def H(X, Pg):
+        c = 1 + 3 * np.exp(-4 * ((X[0] - 1) ** 2 + (X[1] - 1) ** 2))
+        return c * np.sqrt(Pg[0] ** 2 + Pg[1] ** 2)
+
+    g = lambda X: 0.5 * (X[0] ** 2 / ELL_SIG[0] ** 2 + X[1] ** 2 / ELL_SIG[1] ** 2 - 1)
+    from scipy.interpolate import RegularGridInterpolator
+    lf = {}
+    for dx in (0.04, 0.02):
+        xs, sol = pins.lax_friedrichs(H, 4.0, g, -3.0, 3.0, dx, t, 2)
+        lf[dx] = RegularGridInterpolator((xs, xs), sol)(xq)
+    e = {dx: np.abs(lf[dx] - phi) for dx in lf}
+    assert np.all(e[0.04] / e[0.02] > 1.6) and np.all(e[0.04] / e[0.02] < 2.4)
+    assert np.all(np.abs(2 * lf[0.02] - lf[0.04] - phi) < 0.25 * e[0.02])
+
+
+def _golden_tables():
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "ex3_convergence_tables.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                tab, ds, sg, err = line.split()
+                rows.append((int(tab), float(ds), float(sg), float(err)))
+    return rows
+
+
+def test_example3_convergence_study_within_printed_errors():
+    # Sec. 6, Tables 1-2: errors at x = (-0.93, -0.35), t = 0.3 against the
+    # finest run (ds = 0.005, sigma = 0.01), in the paper's numerics.  There
+    # c = 1 + 7e-10 (the bump sits 2.4 away), so the characteristics are
+    # straight lines that Euler follows exactly: the ds error is at rounding
+    # level and the sigma error is the O(sigma^2) bias of forward
+    # differences at the optimum.  Both stay below every printed error, and
+    # the finest run equals the exact circle minimum to within the smallest.
+    P = _p_bump()
+    x, t = np.array([[-0.93, -0.35]]), 0.3
+    run = lambda ds, sg: O.solve(P, _paper_opts(fd_h=sg), x, t, int(round(t / ds)))["phi"][0]
+    ref = run(0.005, 0.01)
+    assert abs(ref - _circle_min(x[0], t)) < 1.818e-4
+    errs_sigma = []
+    for tab, ds, sg, printed in _golden_tables():
+        err = abs(run(ds, sg) - ref)
+        assert err < printed, (tab, ds, sg, err, printed)
+        if tab == 1:
+            errs_sigma.append((sg, err))
+        else:
+            assert err < 1e-8  # exact integrator along straight characteristics
+    # the sigma error grows like sigma^2 - 0.01^2
+    for sg, err in errs_sigma:
+        assert 0.2 < err / (sg ** 2 - 0.01 ** 2) / 3.9e-4 < 5, (sg, err)
+
+
+# --------------------------------------------------------------------------
 # Gradients: the adjoint against the plain derivative
 # --------------------------------------------------------------------------
 
@@ -272,14 +405,16 @@ def test_adjoint_gradient_closed_form_quad_iso():
 @pytest.mark.parametrize("family,principle,g_kind", [
     (O.FAM_SPEED_QUAD, O.LAX, O.G_QUAD_SHIFT), (O.FAM_SPEED_QUAD, O.HOPF, O.G_QUAD_SHIFT),
     (O.FAM_SMOOTH_NONCONVEX, O.HOPF, O.G_DIAG_QUAD), (O.FAM_SMOOTH_NONCONVEX, O.LAX, O.G_DIAG_QUAD),
-    (O.FAM_LINEAR_QUAD, O.LAX, O.G_QUAD_SHIFT), (O.FAM_LINEAR_QUAD, O.HOPF, O.G_QUAD_SHIFT)])
+    (O.FAM_LINEAR_QUAD, O.LAX, O.G_QUAD_SHIFT), (O.FAM_LINEAR_QUAD, O.HOPF, O.G_QUAD_SHIFT),
+    (O.FAM_BUMP_NORM, O.LAX, O.G_ELLIPSE), (O.FAM_BUMP_NORM, O.HOPF, O.G_ELLIPSE)])
 @pytest.mark.parametrize("quad", [O.QUAD_RK4, O.QUAD_RECT, EULER, EULER_RECT])
 def test_adjoint_gradient_matches_central_differences(family, principle, g_kind, quad):
     rng = np.random.default_rng(7 + family + 3 * principle)
     d = 6
     P = O.Problem(d=d, family=family, principle=principle, g_kind=g_kind, w=rng.normal(size=d) / math.sqrt(d),
                   a=rng.uniform(-1, 1, d), sigma=rng.uniform(0.5, 2, d), A=rng.normal(size=(d, d)) * 0.2,
-                  B=rng.normal(size=(d, 4)) / math.sqrt(d), n_neg=2, s_eps=1e-2)
+                  B=rng.normal(size=(d, 4)) / math.sqrt(d), n_neg=2, s_eps=1e-2,
+                  xc=rng.uniform(-0.5, 0.5, d), kappa=3.0, mu=1.5, hsign=1.0 if principle == O.LAX else -1.0)
     for _ in range(3):
         x, v = rng.uniform(-1, 1, d), rng.uniform(-1, 1, d)
         F, g = O.gradient(P, x, 0.5, 16, v, quad=quad)
