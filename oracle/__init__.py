@@ -40,7 +40,7 @@ _lock = threading.Lock()
 _lib = None
 
 FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD, FAM_BUMP_NORM = 0, 1, 2, 3, 4
-LAX, HOPF = 0, 1
+LAX, HOPF, HUYGENS = 0, 1, 2  # HUYGENS: the Lax principle through F^2 (eq. num_min)
 G_QUAD_SHIFT, G_DIAG_QUAD, G_ELLIPSE = 0, 1, 2
 QUAD_RK4, QUAD_RECT = 0, 1
 ODE_EULER = 2  # or-ed into a quad argument: forward Euler instead of RK4

@@ -54,7 +54,10 @@
 /* ------------------------------------------------------------------------ */
 
 enum { FAM_QUAD_ISO = 0, FAM_SPEED_QUAD = 1, FAM_SMOOTH_NONCONVEX = 2, FAM_LINEAR_QUAD = 3, FAM_BUMP_NORM = 4 };
-enum { LAX = 0, HOPF = 1 };
+/* HUYGENS: the Lax principle through F^2 (Sec. 4.1), the smallest g over the
+ * endpoints gamma(x, v, r, 0), 0 <= r <= t, taken on the solver grid r = n dt
+ * (eq. num_min) -- for Hamiltonians of degree one in p, with no running cost. */
+enum { LAX = 0, HOPF = 1, HUYGENS = 2 };
 enum { G_QUAD_SHIFT = 0, G_DIAG_QUAD = 1, G_ELLIPSE = 2 };
 enum { QUAD_RK4 = 0, QUAD_RECT = 1 };
 /* Flag or-ed into a `quad` argument: integrate with forward Euler (the
@@ -73,7 +76,7 @@ enum { DESC_CD = 0, DESC_GD = 1, DESC_CG = 2 };
 typedef struct {
     int d;            /* dimension of x, p, v                                   */
     int family;       /* FAM_*                                                  */
-    int principle;    /* LAX or HOPF                                            */
+    int principle;    /* LAX, HOPF or HUYGENS                                   */
     int g_kind;       /* G_*                                                    */
     int m;            /* columns of B (linear-quadratic family)                 */
     int n_neg;        /* smooth non-convex family: first n_neg signs negative   */
@@ -548,6 +551,18 @@ static double integrate(const orc_problem *P, int quad, const double *x, double 
 /* F^1 (Lax) = g(gamma(0)) + int_0^t (<p, H_p> - H) ds;
  * G (Hopf)  = g*(p(0)) + int_0^t (H - <H_x, gamma>) ds - <x, v>.
  * gamma0, p0 may be NULL. */
+/* Node of the smallest g(gamma_n), n = 0..N (first one on ties). */
+static int huygens_node(const orc_problem *P, const double *traj, int N)
+{
+    int best = 0;
+    double gb = g_val(P, traj);
+    for (int n = 1; n <= N; ++n) {
+        double gn = g_val(P, traj + (size_t)n * 2 * P->d);
+        if (gn < gb) { gb = gn; best = n; }
+    }
+    return best;
+}
+
 double orc_functional(const orc_problem *P, int quad, const double *x, double t, int N, const double *v,
                       double *gamma0, double *p0)
 {
@@ -555,7 +570,17 @@ double orc_functional(const orc_problem *P, int quad, const double *x, double t,
     double *traj = (double *)malloc(sizeof(double) * (size_t)(N + 1) * n2);
     double Q = integrate(P, quad, x, t, N, v, traj, NULL);
     const double *zN = traj + (size_t)N * n2; /* (gamma(0), p(0)) */
-    double F = (P->principle == LAX) ? g_val(P, zN) + Q : gstar_val(P, zN + d) + Q - dot(x, v, d);
+    double F;
+    if (P->principle == HUYGENS) {
+        /* eq. num_min: the grid node n = r/dt after n steps holds
+         * (gamma(x,v,r,0), p(x,v,r,0)); the first smallest g wins, and its
+         * node is the one reported (and certified) */
+        int ns = huygens_node(P, traj, N);
+        zN = traj + (size_t)ns * n2;
+        F = g_val(P, zN);
+    } else {
+        F = (P->principle == LAX) ? g_val(P, zN) + Q : gstar_val(P, zN + d) + Q - dot(x, v, d);
+    }
     if (gamma0) memcpy(gamma0, zN, sizeof(double) * d);
     if (p0) memcpy(p0, zN + d, sizeof(double) * d);
     free(traj);
@@ -577,9 +602,14 @@ double orc_gradient(const orc_problem *P, int quad, const double *x, double t, i
     double Q = integrate(P, quad, x, t, N, v, traj, stages);
     const double *zN = traj + (size_t)N * n2;
     double F;
-    /* adjoint of the terminal term */
+    /* adjoint of the terminal term; for F^2 the seed grad g enters at the
+     * minimising node ns instead (no running cost) */
+    int ns = N;
     for (int i = 0; i < n2; ++i) lam[i] = 0.0;
-    if (P->principle == LAX) {
+    if (P->principle == HUYGENS) {
+        ns = huygens_node(P, traj, N);
+        F = g_val(P, traj + (size_t)ns * n2);
+    } else if (P->principle == LAX) {
         F = g_val(P, zN) + Q;
         g_grad(P, zN, lam);
     } else {
@@ -589,8 +619,17 @@ double orc_gradient(const orc_problem *P, int quad, const double *x, double t, i
     const int euler = quad & ODE_EULER;
     quad &= ~ODE_EULER;
     double beta_q = (quad == QUAD_RK4) ? 1.0 : 0.0; /* dF/dQ flows through the stages only for RK4 quadrature */
+    if (P->principle == HUYGENS) {
+        beta_q = 0.0;
+        quad = QUAD_RK4; /* no rectangle nodes either */
+    }
     for (int n = N - 1; n >= 0; --n) {
         const double *Z1 = stages + (size_t)(4 * n + 0) * n2, *Z2 = Z1 + n2, *Z3 = Z2 + n2, *Z4 = Z3 + n2;
+        if (P->principle == HUYGENS && n + 1 == ns) {
+            double gs[2 * ORC_DMAX];
+            g_grad(P, traj + (size_t)ns * n2, gs);
+            for (int i = 0; i < d; ++i) lam[i] += gs[i];
+        }
         if (euler) {
             /* z_{n+1} = z_n + h f(z_n) (and Q += h L(z_n)); reverse:
              * lam_n = lam_{n+1} + h J(z_n)^T lam_{n+1} + h beta dL/dz(z_n),
@@ -835,7 +874,7 @@ double orc_certify(const orc_problem *P, int quad, const double *x, double t, in
     double *g0 = (double *)malloc(sizeof(double) * 3 * (size_t)d), *p0 = g0 + d, *gr = p0 + d;
     double F = orc_functional(P, quad, x, t, N, v, g0, p0);
     double num = 0.0, den = 0.0;
-    if (P->principle == LAX) {
+    if (P->principle != HOPF) { /* F^2: the Lax test at the minimising node */
         g_grad(P, g0, gr);
         for (int i = 0; i < d; ++i) { num += (p0[i] - gr[i]) * (p0[i] - gr[i]); den += p0[i] * p0[i]; }
     } else {
@@ -910,7 +949,7 @@ int orc_solve_query(const orc_problem *P, const orc_opts *O, int64_t q, const do
     }
     int status = 0;
     if (best >= 0) {
-        *phi = (P->principle == LAX) ? F[best] : -F[best];
+        *phi = (P->principle == HOPF) ? -F[best] : F[best];
         memcpy(vstar, V + (size_t)best * d, sizeof(double) * d);
         if (best_cert) status |= ST_CERTIFIED;
         if (cap[best]) status |= ST_MAX_ITERS;

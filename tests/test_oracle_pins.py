@@ -355,6 +355,38 @@ def test_bump_norm_lax_matches_lax_friedrichs():
     assert np.all(np.abs(2 * lf[0.02] - lf[0.04] - phi) < 0.25 * e[0.02])
 
 
+def test_huygens_functional_closed_form_on_straight_characteristics():
+    # kappa = 0, H = |p|: the node n of the solver grid sits at
+    # gamma = x - n dt v/|v| for RK4 and Euler alike, so F^2 of eq. num_min
+    # is the smallest ellipse value over those N + 1 points
+    rng = np.random.default_rng(34)
+    P = _p_bump(O.HUYGENS, kappa=0.0)
+    for quad in (O.QUAD_RK4, EULER_RECT):
+        for _ in range(6):
+            x, v, t, N = rng.uniform(-1, 1, 2), rng.uniform(-2, 2, 2), rng.uniform(0.2, 1.5), int(rng.integers(3, 40))
+            r = np.arange(N + 1) * (t / N)
+            nodes = x[None, :] - r[:, None] * (v / np.linalg.norm(v))[None, :]
+            assert abs(O.functional(P, x, t, N, v, quad=quad) - _g_ellipse(nodes).min()) < 1e-13
+
+
+def test_huygens_solve_is_the_minimum_over_the_reachable_disc():
+    # kappa = 0: phi(x,t) = min of g over |y - x| <= t (Hopf-Lax for H = |p|).
+    # Inside the disc of the ellipse's centre that is min g = -1/2, which the
+    # Lax functional F^1 (the circle |y - x| = t only) misses; outside, both
+    # agree with the circle minimum.  Grid error: g varies by <= (dt/2)^2/2
+    # between nodes around the minimum.
+    t, N = 0.3, 60
+    xin = np.array([[0.1, 0.0], [-0.15, 0.05], [0.05, -0.02]])
+    xout = np.array([[-0.93, -0.35], [1.2, -0.5], [0.4, 1.9]])
+    opts = _paper_opts()
+    ph = O.solve(_p_bump(O.HUYGENS, kappa=0.0), opts, np.vstack([xin, xout]), t, N)["phi"]
+    f1 = O.solve(_p_bump(O.LAX, kappa=0.0), opts, xin, t, N)["phi"]
+    assert np.all(np.abs(ph[:3] + 0.5) < 1e-5), ph[:3]
+    assert np.all(f1 > -0.5 + 2e-3), f1
+    for q in range(3):
+        assert abs(ph[3 + q] - _circle_min(xout[q], t)) < 1e-5
+
+
 def _golden_tables():
     rows = []
     with open(os.path.join(os.path.dirname(__file__), "golden", "ex3_convergence_tables.txt")) as f:
@@ -406,7 +438,8 @@ def test_adjoint_gradient_closed_form_quad_iso():
     (O.FAM_SPEED_QUAD, O.LAX, O.G_QUAD_SHIFT), (O.FAM_SPEED_QUAD, O.HOPF, O.G_QUAD_SHIFT),
     (O.FAM_SMOOTH_NONCONVEX, O.HOPF, O.G_DIAG_QUAD), (O.FAM_SMOOTH_NONCONVEX, O.LAX, O.G_DIAG_QUAD),
     (O.FAM_LINEAR_QUAD, O.LAX, O.G_QUAD_SHIFT), (O.FAM_LINEAR_QUAD, O.HOPF, O.G_QUAD_SHIFT),
-    (O.FAM_BUMP_NORM, O.LAX, O.G_ELLIPSE), (O.FAM_BUMP_NORM, O.HOPF, O.G_ELLIPSE)])
+    (O.FAM_BUMP_NORM, O.LAX, O.G_ELLIPSE), (O.FAM_BUMP_NORM, O.HOPF, O.G_ELLIPSE),
+    (O.FAM_BUMP_NORM, O.HUYGENS, O.G_ELLIPSE)])
 @pytest.mark.parametrize("quad", [O.QUAD_RK4, O.QUAD_RECT, EULER, EULER_RECT])
 def test_adjoint_gradient_matches_central_differences(family, principle, g_kind, quad):
     rng = np.random.default_rng(7 + family + 3 * principle)
