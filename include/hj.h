@@ -73,7 +73,16 @@ typedef enum {
                                     |p|_eps = sqrt(|p|^2 + s_eps) (Sec. 6, Example 3)        */
 } hj_family;
 
-typedef enum { HJ_LAX = 0, HJ_HOPF = 1 } hj_principle;
+/* Which functional is minimised over v (Sec. 4.1):
+ *   HJ_LAX      F^1 = g(gamma(0)) + int_0^t (<p, H_p> - H) ds,  phi = min F^1;
+ *   HJ_HOPF     G = g*(p(0)) + int_0^t (H - <H_x, gamma>) ds - <x, v>,  phi = -min G;
+ *   HJ_HUYGENS  F^2 = min over 0 <= r <= t of g(gamma(x, v, r, 0)), taken on the
+ *               solver grid r = n t/N, n = 0..N (eq. num_min; the first smallest
+ *               node on ties), phi = min F^2 -- for Hamiltonians of degree one
+ *               in p (the BUMP_NORM family, the only one accepted with it);
+ *               no running cost, the certificate is the Lax test at the
+ *               minimising node, and the gradient is the adjoint seeded there. */
+typedef enum { HJ_LAX = 0, HJ_HOPF = 1, HJ_HUYGENS = 2 } hj_principle;
 
 /* Initial data g. */
 typedef enum {

@@ -176,6 +176,7 @@ void fill_prob(const hj_problem_desc &D, const std::vector<double> &par, int ld,
     P.d = d;
     P.family = D.family;
     P.principle = D.principle;
+    P.huygens = D.principle == HJ_HUYGENS;
     P.g_kind = D.g_kind;
     P.m = m;
     P.n_neg = D.n_neg;
@@ -298,8 +299,10 @@ hj_status validate_problem(hj_ctx *ctx, const hj_problem_desc &D, int idx)
     if (D.d < 1 || D.d > DPAD) return fail(ctx, HJ_EINVAL, "problem %d: d=%d outside [1, %d]", idx, D.d, DPAD);
     if (D.family < HJ_FAM_QUAD_ISO || D.family > HJ_FAM_BUMP_NORM)
         return fail(ctx, HJ_EINVAL, "problem %d: unknown family %d", idx, (int)D.family);
-    if (D.principle != HJ_LAX && D.principle != HJ_HOPF)
+    if (D.principle != HJ_LAX && D.principle != HJ_HOPF && D.principle != HJ_HUYGENS)
         return fail(ctx, HJ_EINVAL, "problem %d: unknown principle %d", idx, (int)D.principle);
+    if (D.principle == HJ_HUYGENS && D.family != HJ_FAM_BUMP_NORM)
+        return fail(ctx, HJ_EINVAL, "problem %d: the Huygens functional needs a degree-one H (BUMP_NORM)", idx);
     if (D.g_kind != HJ_G_QUAD_SHIFT && D.g_kind != HJ_G_DIAG_QUAD && D.g_kind != HJ_G_ELLIPSE)
         return fail(ctx, HJ_EINVAL, "problem %d: unknown initial data %d", idx, (int)D.g_kind);
     if (D.family == HJ_FAM_LINEAR_QUAD) {
@@ -361,6 +364,10 @@ hj_status validate_opts(hj_ctx *ctx, const hj_solver_opts &o)
     return HJ_OK;
 }
 
+// Kernel set of a principle: F^2 runs in the Lax kernels (a runtime switch
+// on the problem).
+int kprin(int principle) { return principle == HJ_HOPF ? HJ_HOPF : HJ_LAX; }
+
 // Smallest instantiated C >= need for this (precision, family, principle, kind).
 int pick_c(int prec, int fam, int pr, int kind, int need)
 {
@@ -392,7 +399,7 @@ bool choose(const hj_ctx *ctx, int p, int kind, int *tpp_out, int *c_out)
         if (ov && kind != K_CERT && tpp != ov) continue;
         const int need = (D.d + tpp - 1) / tpp;
         if (!ov && need > pref && tpp < 32) continue;
-        const int c = pick_c(prec, D.family, D.principle, kind, need);
+        const int c = pick_c(prec, D.family, kprin(D.principle), kind, need);
         if (c > 0) {
             *tpp_out = tpp;
             *c_out = c;
@@ -405,7 +412,7 @@ bool choose(const hj_ctx *ctx, int p, int kind, int *tpp_out, int *c_out)
 const KSet &kset(const hj_ctx *ctx, int p, int c)
 {
     const hj_problem_desc &D = ctx->desc[p];
-    return registry().k[ctx->prec][D.family][D.principle][c];
+    return registry().k[ctx->prec][D.family][kprin(D.principle)][c];
 }
 
 int persistent_grid(hj_ctx *ctx, const void *fn)
@@ -431,7 +438,7 @@ void *as_ptr(T *p) { return (void *)p; }
 bool tc_eligible(const hj_ctx *ctx, int p)
 {
     return ctx->prec == 0 && ctx->dev[p].tc && ctx->tpp_override[p] == 0 && ctx->opts.quad == HJ_QUAD_RK4 &&
-           ctx->desc[p].g_kind != HJ_G_ELLIPSE &&
+           ctx->desc[p].g_kind != HJ_G_ELLIPSE && ctx->desc[p].principle != HJ_HUYGENS &&
            ctx->popts[p].coarse_div <= 1;
 }
 

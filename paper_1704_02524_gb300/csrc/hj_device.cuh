@@ -32,6 +32,7 @@ constexpr int CK_BUDGET = 3072;  // bytes of checkpoint + segment storage per th
 template <typename T>
 struct ProbDev {
     int d, family, principle, g_kind, m, n_neg, n_guesses, ld;
+    int huygens;  // Lax kernels of the bump-norm family: minimise F^2 (smallest g over the grid nodes)
     T s_eps;
     T kappa, mu, hsign;  // bump-norm family: c = 1 + kappa exp(-mu |x - xc|^2), H = hsign c |p|
     const T *w;     // [DPAD] speed direction (bump-norm family: the centre xc)
@@ -830,6 +831,26 @@ __device__ __forceinline__ T functional(const Grp &g, const TP<T, C> &tp, const 
     if (N < 1 || N > MAX_N) return (T)NAN;  // step counts outside [1, MAX_N] are rejected
     const T h = t / (T)N;
     T Q = 0, Qc = 0;
+    if (PR == HJ_LAX && FAM == HJ_FAM_BUMP_NORM && P.huygens) {
+        // F^2: the smallest g over the nodes z_0 .. z_N (first one on ties;
+        // group sums are identical on every lane, so the choice is uniform);
+        // gam, p return the minimising node for the certificate
+        T gb = terminal<T, C, HJ_LAX>(g, P, x, v, gam, p, (T *)nullptr, (T *)nullptr), bg[C], bp[C];
+#pragma unroll
+        for (int k = 0; k < C; ++k) { bg[k] = gam[k]; bp[k] = p[k]; }
+        for (int n = 0; n < N; ++n) {
+            rk4_step<T, C, FAM, PR>(g, tp, P.s_eps, h, quad, 0, gam, p, Q, Qc);
+            const T gn = terminal<T, C, HJ_LAX>(g, P, x, v, gam, p, (T *)nullptr, (T *)nullptr);
+            if (gn < gb) {
+                gb = gn;
+#pragma unroll
+                for (int k = 0; k < C; ++k) { bg[k] = gam[k]; bp[k] = p[k]; }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < C; ++k) { gam[k] = bg[k]; p[k] = bp[k]; }
+        return gb;
+    }
     for (int n = 0; n < N; ++n) rk4_step<T, C, FAM, PR>(g, tp, P.s_eps, h, quad, kahan, gam, p, Q, Qc);
     return terminal<T, C, PR>(g, P, x, v, gam, p, (T *)nullptr, (T *)nullptr) + Q;
 }
@@ -940,10 +961,14 @@ __device__ __forceinline__ T gradient(const Grp &g, const TP<T, C> &tp, const Pr
     }
     const T h = t / (T)N;
     const T eps = P.s_eps;
+    const bool huy = PR == HJ_LAX && FAM == HJ_FAM_BUMP_NORM && P.huygens;
     T gam[C], p[C], Q = 0, Qc = 0;
 #pragma unroll
     for (int k = 0; k < C; ++k) { gam[k] = x[k]; p[k] = v[k]; }
     T *c = ck;
+    // F^2: smallest g over the nodes and its node nstar (first on ties)
+    T gb = huy ? terminal<T, C, HJ_LAX>(g, P, x, v, gam, p, (T *)nullptr, (T *)nullptr) : (T)0;
+    int nstar = 0;
     for (int n = 0, kk = 0; n < N; ++n) {
         if (kk == 0) {
 #pragma unroll
@@ -952,11 +977,25 @@ __device__ __forceinline__ T gradient(const Grp &g, const TP<T, C> &tp, const Pr
         }
         if (++kk == K) kk = 0;
         rk4_step<T, C, FAM, PR>(g, tp, eps, h, quad, kahan, gam, p, Q, Qc);
+        if (huy) {
+            const T gn = terminal<T, C, HJ_LAX>(g, P, x, v, gam, p, (T *)nullptr, (T *)nullptr);
+            if (gn < gb) { gb = gn; nstar = n + 1; }
+        }
     }
     // gam, p hold z_N
     T lg[C], lp[C];
-    T F = terminal<T, C, PR>(g, P, x, v, gam, p, lg, lp) + Q;
-    const T b = (quad & HJ_QUAD_RECT) ? (T)0 : (T)1;
+    T F;
+    if (huy) {
+        // the seed grad g enters at node nstar during the reverse sweep
+        F = gb;
+#pragma unroll
+        for (int k = 0; k < C; ++k) { lg[k] = 0; lp[k] = 0; }
+    } else {
+        F = terminal<T, C, PR>(g, P, x, v, gam, p, lg, lp) + Q;
+    }
+    // F^2 has no running cost: no quadrature weight, no rectangle nodes
+    const T b = ((quad & HJ_QUAD_RECT) || huy) ? (T)0 : (T)1;
+    const bool rect = (quad & HJ_QUAD_RECT) && !huy;
     const int ode = quad & HJ_ODE_EULER;
     const int nseg = (N + K - 1) / K;
     for (int s = nseg - 1; s >= 0; --s) {
@@ -980,9 +1019,8 @@ __device__ __forceinline__ T gradient(const Grp &g, const TP<T, C> &tp, const Pr
             T ug[C], up[C];
 #pragma unroll
             for (int k = 0; k < C; ++k) { ug[k] = st[k]; up[k] = st[C + k]; }
-            if (quad & HJ_QUAD_RECT) {
-                // rectangle node at z_{n+1}: lam += h grad L(z_{n+1}); z_{n+1} is the
-                // next stored state, the next checkpoint, or z_N
+            if (rect || (huy && n + 1 == nstar)) {
+                // z_{n+1} is the next stored state, the next checkpoint, or z_N
                 T zeros[C], rg[C], rp[C], ng[C], np[C];
                 const T *sn = (n + 1 < n1) ? seg + (n + 1 - n0) * 2 * C : (s + 1 < nseg ? ck + (s + 1) * 2 * C : nullptr);
 #pragma unroll
@@ -991,9 +1029,17 @@ __device__ __forceinline__ T gradient(const Grp &g, const TP<T, C> &tp, const Pr
                     ng[k] = sn ? sn[k] : gam[k];
                     np[k] = sn ? sn[C + k] : p[k];
                 }
-                vjp<T, C, FAM, PR>(g, tp, eps, ng, np, zeros, zeros, (T)1, rg, rp);
+                if (huy) {
+                    // F^2 seed at its node: lam_gamma += grad g(gamma_{n+1})
+                    terminal<T, C, HJ_LAX>(g, P, x, v, ng, np, rg, rp);
 #pragma unroll
-                for (int k = 0; k < C; ++k) { lg[k] = fma(h, rg[k], lg[k]); lp[k] = fma(h, rp[k], lp[k]); }
+                    for (int k = 0; k < C; ++k) lg[k] += rg[k];
+                } else {
+                    // rectangle node at z_{n+1}: lam += h grad L(z_{n+1})
+                    vjp<T, C, FAM, PR>(g, tp, eps, ng, np, zeros, zeros, (T)1, rg, rp);
+#pragma unroll
+                    for (int k = 0; k < C; ++k) { lg[k] = fma(h, rg[k], lg[k]); lp[k] = fma(h, rp[k], lp[k]); }
+                }
             }
             if (ode) {
                 T wg[C], wp[C], rg[C], rp[C];

@@ -145,7 +145,7 @@ __global__ void k_select(long long nq, const int32_t *pidx, int np, const int32_
         if (best >= 0) {
             const int pid = base + best;
             const double F = pF[pid];
-            phi[q] = (pprin[p] == HJ_LAX) ? F : -F;
+            phi[q] = (pprin[p] == HJ_HOPF) ? -F : F;
             for (int i = 0; i < d; ++i) v_out[q * ld + i] = vfin[(long long)pid * ld + i];
             if (best_cert) st |= HJ_ST_CERTIFIED;
             if (flags[pid] & 1) st |= HJ_ST_MAX_ITERS;

@@ -24,7 +24,7 @@ from typing import Dict, List, Optional
 import numpy as np
 
 FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD, FAM_BUMP_NORM = 0, 1, 2, 3, 4
-LAX, HOPF = 0, 1
+LAX, HOPF, HUYGENS = 0, 1, 2
 G_QUAD_SHIFT, G_DIAG_QUAD, G_ELLIPSE = 0, 1, 2
 
 HARNESS_SEED = 0x170402524
@@ -297,14 +297,15 @@ def ellipse_sigma(d: int) -> np.ndarray:
 
 
 def bump_ex3(n_side: int = 128, d: int = 2, sign: float = 1.0, t: float = 0.3, ds: float = 0.02,
-             fd_h: float = 1e-3, n_guesses: int = 5, precision: str = "fp32") -> Workload:
+             fd_h: float = 1e-3, n_guesses: int = 5, precision: str = "fp32", principle: int = LAX) -> Workload:
     """Sec. 6 Example 3 in the paper's numerics: H = sign c(x)|p| with
     c = 1 + 3 exp(-4 |x - (1,1,0,...)|^2), the ellipse data g, the Lax
     functional, on the n_side x n_side grid over the cross-section
     [-3,3]^2 x {0}^(d-2) at time t (0.3 for H+, as in the paper's d=2 run),
     forward Euler with step ds (N = t/ds), forward differences with step
     fd_h and L = 0.02, five starts per point (the paper's time format
-    counts five).  Nothing is random but the starts."""
+    counts five).  principle = HUYGENS minimises F^2 (eq. num_min) instead
+    of F^1.  Nothing is random but the starts."""
     g = np.linspace(-3.0, 3.0, n_side)
     X = np.zeros((n_side * n_side, d))
     X[:, 0] = np.repeat(g, n_side)
@@ -312,11 +313,12 @@ def bump_ex3(n_side: int = 128, d: int = 2, sign: float = 1.0, t: float = 0.3, d
     X = f32(X)
     xc = np.zeros(d)
     xc[:2] = 1.0
-    P = ProblemSpec(d=d, family=FAM_BUMP_NORM, principle=LAX, g_kind=G_ELLIPSE, sigma=ellipse_sigma(d), xc=xc,
-                    kappa=3.0, mu=4.0, hsign=sign, s_eps=0.0, n_guesses=n_guesses)
+    P = ProblemSpec(d=d, family=FAM_BUMP_NORM, principle=principle, g_kind=G_ELLIPSE, sigma=ellipse_sigma(d),
+                    xc=xc, kappa=3.0, mu=4.0, hsign=sign, s_eps=0.0, n_guesses=n_guesses)
     nq = X.shape[0]
     N = int(round(t / ds))
-    name = f"bump_norm_d{d}_{'plus' if sign > 0 else 'minus'}_lax_paper"
+    pname = {LAX: "lax", HUYGENS: "huygens", HOPF: "hopf"}[principle]
+    name = f"bump_norm_d{d}_{'plus' if sign > 0 else 'minus'}_{pname}_paper"
     return Workload(name, [P], X, np.full(nq, t), np.full(nq, N, np.int32), np.zeros(nq, np.int32),
                     paper_solver(fd_h=fd_h, n_guesses=n_guesses, max_trials=n_guesses), precision)
 

@@ -62,6 +62,9 @@ def test_create_rejects_bad_arguments_without_a_gpu(lib):
         hj.hj_create([spec], o, 0)
     assert e.value.status == hj.HJ_EINVAL and "quad" in str(e.value)
     bump = W.bump_ex3(n_side=2).problems[0]
+    with pytest.raises(hj.HJError) as e:
+        hj.hj_create([W.ProblemSpec(**{**spec.__dict__, "principle": W.HUYGENS})], hj.opts_from_dict(wl.solver), 0)
+    assert e.value.status == hj.HJ_EINVAL and "Huygens" in str(e.value)
     for field, val, msg in (("hsign", 0.5, "sign"), ("mu", -1.0, "mu"), ("s_eps", -1e-3, "s_eps")):
         with pytest.raises(hj.HJError) as e:
             hj.hj_create([W.ProblemSpec(**{**bump.__dict__, field: val})], hj.opts_from_dict(wl.solver), 0)

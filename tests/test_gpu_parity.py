@@ -38,7 +38,7 @@ def _spec(family, principle, d, seed=0, n_neg=1, s_eps=1e-6, g_kind=None, m=None
                          w=W.f32(rng.normal(size=d) / np.sqrt(d)), a=W.f32(rng.uniform(-1, 1, d)),
                          sigma=W.f32(rng.uniform(0.5, 2, d)), A=A, B=B, n_neg=n_neg, s_eps=s_eps, n_guesses=4,
                          xc=W.f32(rng.uniform(-0.5, 0.5, d)), kappa=3.0, mu=1.5,
-                         hsign=1.0 if principle == W.LAX else -1.0)
+                         hsign=-1.0 if principle == W.HOPF else 1.0)
 
 
 def _rows(n, d, seed, prec):
@@ -122,6 +122,70 @@ def test_solve_speed_quad_d10_with_forward_euler_matches_oracle(hj):
     assert np.all(rel_err(phi, ref["phi"]) <= 1e-4), rel_err(phi, ref["phi"]).max()
     assert np.array_equal(st & 1, ref["status"] & 1)
     assert info["rk4_steps"] > 0
+
+
+def _huygens_node_gaps(spec, x, v, t, N):
+    # gap between the two smallest g over the grid nodes of each row (the
+    # Lax functional of the same path with s_eps = 0 has no running cost,
+    # so its value after n steps of length t/N is g at node n)
+    lax = oracle_problem(W.ProblemSpec(**{**spec.__dict__, "principle": W.LAX}))
+    gaps = []
+    for i in range(len(x)):
+        h = t[i] / N[i]
+        g = np.sort([O.functional(lax, x[i], n * h, n, v[i]) if n else 0.5 * (np.sum(x[i][:spec.d] ** 2 /
+                     spec.sigma ** 2) - 1) for n in range(int(N[i]) + 1)])
+        gaps.append((g[1] - g[0]) / (1 + abs(g[0])))
+    return np.array(gaps)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("quad", ["rk4", "euler"])
+@pytest.mark.parametrize("d", [2, 13])
+def test_huygens_functional_gradient_and_certificate_match_oracle(hj, prec, quad, d):
+    # F^2 (eq. num_min) on H = c(x)|p| with the ellipse data: values, the
+    # adjoint seeded at the minimising node, and the Lax certificate there.
+    # The gradient is compared on rows whose two smallest node values differ
+    # by more than the functional's rounding (else either node may win).
+    spec = _spec(W.FAM_BUMP_NORM, W.HUYGENS, d, seed=50 + d, s_eps=0.0)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    solver = W.solver_constants(quad=quad, cert_tol=0.3)
+    ctx = hj.hj_create([spec], hj.opts_from_dict(solver, hj.HJ_PREC_FP32 if prec == "fp32" else hj.HJ_PREC_FP64, 32),
+                       0)
+    n = 67
+    x, v, t, N = _rows(n, d, 300 + d, prec)
+    args = (_t(x, dt), _t(t, dt), _t(v, dt), _t(N, torch.int32))
+    F = hj.hj_eval_functional(ctx, *args).cpu().numpy()
+    Fg, G = (a.cpu().numpy() for a in hj.hj_grad(ctx, *args))
+    Fc, R, Pa = (a.cpu().numpy() for a in hj.hj_certify(ctx, *args))
+    P = oracle_problem(spec)
+    q = QUAD_CODES[quad]
+    gaps = _huygens_node_gaps(spec, x, v, t, N)
+    tie = 3e-5 if prec == "fp32" else 1e-10
+    assert np.mean(gaps > tie) > 0.8
+    tolF = 2e-5 if prec == "fp32" else 1e-11
+    for i in range(n):
+        Fo, Go = O.gradient(P, x[i], t[i], int(N[i]), v[i], quad=q)
+        assert rel_err(F[i], Fo) <= tolF and rel_err(Fg[i], Fo) <= tolF, (i, F[i], Fo)
+        if gaps[i] > tie:
+            assert np.abs(G[i] - Go).max() <= (5e-4 if prec == "fp32" else 1e-9) * (1 + np.abs(Go).max()), i
+            Fco, Ro, ok = O.certify(P, x[i], t[i], int(N[i]), v[i], 0.3, quad=q)
+            assert rel_err(Fc[i], Fco) < 1e-11 and abs(R[i] - Ro) < 1e-11 and bool(Pa[i]) == ok, i
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_paper_mode_example3_huygens_solve_matches_oracle(hj, prec):
+    # F^2 in the paper's numerics on the Example 3 grid: the whole solve
+    # against the oracle, and min g = -1/2 wherever the reachable set holds
+    # the ellipse's centre (|x| < t suffices, since c >= 1)
+    wl = W.bump_ex3(n_side=128, precision=prec, principle=W.HUYGENS, ds=0.005)
+    near = np.flatnonzero(np.hypot(wl.x[:, 0], wl.x[:, 1]) < 0.25)
+    w = wl.take(np.concatenate([np.arange(0, wl.nq, wl.nq // 64)[:64], near]))
+    phi, v, st, ref, info = _solve_both(hj, w, w.nq)
+    err = rel_err(phi, ref["phi"])
+    assert np.all(err <= 1e-4), (err.max(), int(np.argmax(err)))
+    assert np.array_equal(st & 1, ref["status"] & 1)
+    assert len(near) > 0 and np.all(np.abs(phi[64:] + 0.5) < 1e-4)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
