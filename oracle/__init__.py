@@ -39,7 +39,7 @@ _LIB_PATH = os.path.join(_HERE, "libhj_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD, FAM_BUMP_NORM = 0, 1, 2, 3, 4
+FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD, FAM_BUMP_NORM, FAM_SPLIT_NORM = range(6)
 LAX, HOPF, HUYGENS = 0, 1, 2  # HUYGENS: the Lax principle through F^2 (eq. num_min)
 G_QUAD_SHIFT, G_DIAG_QUAD, G_ELLIPSE = 0, 1, 2
 QUAD_RK4, QUAD_RECT = 0, 1
@@ -67,7 +67,9 @@ class _Problem(C.Structure):
                 ("m", C.c_int), ("n_neg", C.c_int), ("s_eps", C.c_double),
                 ("w", C.POINTER(C.c_double)), ("A", C.POINTER(C.c_double)), ("B", C.POINTER(C.c_double)),
                 ("ga", C.POINTER(C.c_double)), ("gs", C.POINTER(C.c_double)),
-                ("xc", C.POINTER(C.c_double)), ("kappa", C.c_double), ("mu", C.c_double), ("hsign", C.c_double)]
+                ("xc", C.POINTER(C.c_double)), ("kappa", C.c_double), ("mu", C.c_double), ("hsign", C.c_double),
+                ("xcb", C.POINTER(C.c_double)), ("ksplit", C.c_int), ("alpha_a", C.c_double),
+                ("alpha_b", C.c_double)]
 
 
 class _Opts(C.Structure):
@@ -134,18 +136,23 @@ class Problem:
     kappa: float = 0.0               # bump-norm family: c(x) = 1 + kappa exp(-mu |x - xc|^2)
     mu: float = 0.0
     hsign: float = 1.0               # bump-norm family: H = hsign c(x) |p|
+    xcb: Optional[np.ndarray] = None  # split-norm family: H = c_A|p_A| + c_B|p_B| over blocks [0,k), [k,d),
+    ksplit: int = 0                   #   c_A = alpha_a (1 + kappa exp(-mu|x - xc|^2)),
+    alpha_a: float = 0.0              #   c_B = alpha_b (1 + kappa exp(-mu|x - xcb|^2))
+    alpha_b: float = 0.0
     _c: Optional[_Problem] = field(default=None, repr=False)
 
     def c(self) -> _Problem:
         if self._c is None:
-            for name in ("w", "A", "B", "a", "sigma", "xc"):
+            for name in ("w", "A", "B", "a", "sigma", "xc", "xcb"):
                 v = getattr(self, name)
                 if v is not None:
                     setattr(self, name, _f64(v))
             m = 0 if self.B is None else int(self.B.shape[1])
             self._c = _Problem(self.d, self.family, self.principle, self.g_kind, m, self.n_neg, self.s_eps,
                                _dp(self.w), _dp(self.A), _dp(self.B), _dp(self.a), _dp(self.sigma),
-                               _dp(self.xc), float(self.kappa), float(self.mu), float(self.hsign))
+                               _dp(self.xc), float(self.kappa), float(self.mu), float(self.hsign),
+                               _dp(self.xcb), int(self.ksplit), float(self.alpha_a), float(self.alpha_b))
         return self._c
 
 

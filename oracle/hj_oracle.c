@@ -13,7 +13,9 @@
  * Families: H = |p|^2/2; H = c(x)^2|p|^2/2 with c = 1 + sin<w,x>/2; the
  * smooth non-convex H = c(x) sum_i e_i sqrt(p_i^2 + eps); the linear-
  * quadratic H = <Ax,p> + |B^T p|^2/2; and H = +-c(x)|p| with the Gaussian
- * bump speed c = 1 + kappa exp(-mu|x - xc|^2) of Sec. 6, Example 3.
+ * bump speed c = 1 + kappa exp(-mu|x - xc|^2) of Sec. 6, Example 3; and the
+ * split norm H = c_A(x)|p_A| + c_B(x)|p_B| over two coordinate blocks, each
+ * speed a signed multiple of such a bump (Sec. 6, Example 5).
  * Initial data: |x - a|^2/2, sum x_i^2/(2 s_i^2), and the ellipse data
  * (<x, Ax> - 1)/2, A diagonal, of Sec. 6.
  *
@@ -53,7 +55,8 @@
 /* Problem description                                                       */
 /* ------------------------------------------------------------------------ */
 
-enum { FAM_QUAD_ISO = 0, FAM_SPEED_QUAD = 1, FAM_SMOOTH_NONCONVEX = 2, FAM_LINEAR_QUAD = 3, FAM_BUMP_NORM = 4 };
+enum { FAM_QUAD_ISO = 0, FAM_SPEED_QUAD = 1, FAM_SMOOTH_NONCONVEX = 2, FAM_LINEAR_QUAD = 3, FAM_BUMP_NORM = 4,
+       FAM_SPLIT_NORM = 5 };
 /* HUYGENS: the Lax principle through F^2 (Sec. 4.1), the smallest g over the
  * endpoints gamma(x, v, r, 0), 0 <= r <= t, taken on the solver grid r = n dt
  * (eq. num_min) -- for Hamiltonians of degree one in p, with no running cost. */
@@ -91,6 +94,13 @@ typedef struct {
      * c(x) = 1 + kappa exp(-mu |x - xc|^2), |p|_eps = sqrt(|p|^2 + s_eps) */
     const double *xc; /* [d] */
     double kappa, mu, hsign;
+    /* split-norm family (Sec. 6, Example 5): H = c_A(x)|p_A|_eps + c_B(x)|p_B|_eps
+     * over the blocks A = coordinates 0..k-1 and B = k..d-1, with
+     * c_A = alpha_a (1 + kappa exp(-mu |x - xc|^2)),
+     * c_B = alpha_b (1 + kappa exp(-mu |x - xcb|^2)); signs in the alphas */
+    const double *xcb; /* [d] */
+    int ksplit;
+    double alpha_a, alpha_b;
 } orc_problem;
 
 typedef struct {
@@ -212,6 +222,35 @@ static void bump(const orc_problem *P, const double *gam, double *y, double *c, 
     *k = -2.0 * P->mu * P->kappa * e;
 }
 
+/* Split-norm family: per block b in {A, B}, the speed c_b, its gradient
+ * factor k_b (grad c_b = k_b (x - xc_b)), y_b = x - xc_b, and the block norm
+ * n_b = sqrt(|p_b|^2 + s_eps) (0 for an empty block). */
+typedef struct {
+    double c[2], k[2], n[2];
+    double y[2][ORC_DMAX];
+} split_t;
+static int block_of(const orc_problem *P, int i) { return i < P->ksplit ? 0 : 1; }
+static void split_eval(const orc_problem *P, const double *gam, const double *p, split_t *S)
+{
+    const double *ctr[2] = { P->xc, P->xcb };
+    const double alpha[2] = { P->alpha_a, P->alpha_b };
+    for (int b = 0; b < 2; ++b) {
+        double rr = 0.0;
+        for (int i = 0; i < P->d; ++i) {
+            S->y[b][i] = gam[i] - ctr[b][i];
+            rr += S->y[b][i] * S->y[b][i];
+        }
+        double e = exp(-P->mu * rr);
+        S->c[b] = alpha[b] * (1.0 + P->kappa * e);
+        S->k[b] = -2.0 * P->mu * alpha[b] * P->kappa * e;
+        double pp = 0.0;
+        int cnt = 0;
+        for (int i = 0; i < P->d; ++i)
+            if (block_of(P, i) == b) { pp += p[i] * p[i]; ++cnt; }
+        S->n[b] = cnt ? sqrt(pp + P->s_eps) : 0.0;
+    }
+}
+
 /* Hamiltonian value H(gamma, p). */
 static double ham(const orc_problem *P, const double *gam, const double *p)
 {
@@ -247,6 +286,11 @@ static double ham(const orc_problem *P, const double *gam, const double *p)
         double y[ORC_DMAX], c, k;
         bump(P, gam, y, &c, &k);
         return P->hsign * c * sqrt(dot(p, p, d) + P->s_eps);
+    }
+    case FAM_SPLIT_NORM: {
+        split_t S;
+        split_eval(P, gam, p, &S);
+        return S.c[0] * S.n[0] + S.c[1] * S.n[1];
     }
     }
     return NAN;
@@ -307,6 +351,17 @@ static void ham_grads(const orc_problem *P, const double *gam, const double *p, 
         for (int i = 0; i < d; ++i) {
             Hp[i] = P->hsign * c * p[i] / n;
             Hx[i] = P->hsign * n * k * y[i];
+        }
+        return;
+    }
+    case FAM_SPLIT_NORM: {
+        /* H_p on block b = c_b p_b / n_b;  H_x = sum_b n_b k_b y_b */
+        split_t S;
+        split_eval(P, gam, p, &S);
+        for (int i = 0; i < d; ++i) {
+            int b = block_of(P, i);
+            Hp[i] = S.c[b] * p[i] / S.n[b];
+            Hx[i] = S.n[0] * S.k[0] * S.y[0][i] + S.n[1] * S.k[1] * S.y[1][i];
         }
         return;
     }
@@ -444,6 +499,38 @@ static void field_vjp(const orc_problem *P, const double *z, const double *a, do
                 g_i += b * S * n * (k * y[i] + 2.0 * mu * k * yg * y[i] - k * (y[i] + gam[i]));
                 p_i += b * S * (c - k * yg) * p[i] / n;
             }
+            rg[i] = g_i;
+            rp[i] = p_i;
+        }
+        return;
+    }
+    case FAM_SPLIT_NORM: {
+        /* each block contributes the bump-norm terms with S c -> c_blk:
+         * field_gamma on the block = -c_blk p_blk/n_blk, field_p = sum_blk n_blk k_blk y_blk,
+         * Lax L = -eps sum_blk c_blk/n_blk, Hopf L = sum_blk n_blk (c_blk - k_blk <y_blk, gamma>) */
+        split_t S;
+        split_eval(P, gam, p, &S);
+        const double eps = P->s_eps, mu = P->mu;
+        double Agp[2] = { 0.0, 0.0 }, Apy[2], yg[2];
+        for (int i = 0; i < d; ++i) Agp[block_of(P, i)] += ag[i] * p[i];
+        for (int bl = 0; bl < 2; ++bl) {
+            Apy[bl] = dot(ap, S.y[bl], d);
+            yg[bl] = dot(S.y[bl], gam, d);
+        }
+        for (int i = 0; i < d; ++i) {
+            double g_i = 0.0;
+            for (int bl = 0; bl < 2; ++bl) {
+                if (S.n[bl] == 0.0) continue; /* empty block */
+                const double n = S.n[bl], k = S.k[bl], y = S.y[bl][i];
+                g_i += -(Agp[bl] / n) * k * y + n * (-2.0 * mu * k * Apy[bl] * y + k * ap[i]);
+                if (P->principle == LAX) g_i += b * (-eps / n) * k * y;
+                else g_i += b * n * (2.0 * mu * k * yg[bl] * y - k * gam[i]);
+            }
+            const int bi = block_of(P, i);
+            const double n = S.n[bi], c = S.c[bi], k = S.k[bi];
+            double p_i = -c * (ag[i] / n - Agp[bi] * p[i] / (n * n * n)) + k * Apy[bi] * p[i] / n;
+            if (P->principle == LAX) p_i += b * c * eps * p[i] / (n * n * n);
+            else p_i += b * (c - k * yg[bi]) * p[i] / n;
             rg[i] = g_i;
             rp[i] = p_i;
         }
