@@ -69,8 +69,12 @@ typedef enum {
     HJ_FAM_SMOOTH_NONCONVEX = 2, /* H = c(x) sum_i e_i s(p_i), s(q) = sqrt(q^2 + s_eps),
                                     e_i = -1 for i < n_neg, +1 otherwise                       */
     HJ_FAM_LINEAR_QUAD = 3,      /* H = <A x, p> + |B^T p|^2/2                               */
-    HJ_FAM_BUMP_NORM = 4         /* H = sign c(x) |p|_eps,  c = 1 + kappa exp(-mu |x - xc|^2),
+    HJ_FAM_BUMP_NORM = 4,        /* H = sign c(x) |p|_eps,  c = 1 + kappa exp(-mu |x - xc|^2),
                                     |p|_eps = sqrt(|p|^2 + s_eps) (Sec. 6, Example 3)        */
+    HJ_FAM_SPLIT_NORM = 5        /* H = c_A(x) |p_A|_eps + c_B(x) |p_B|_eps over the blocks
+                                    A = coordinates [0, k), B = [k, d), with
+                                    c_b = alpha_b (1 + kappa exp(-mu |x - xc_b|^2))
+                                    (Sec. 6, Example 5; signs in the alphas)                */
 } hj_family;
 
 /* Which functional is minimised over v (Sec. 4.1):
@@ -79,7 +83,8 @@ typedef enum {
  *   HJ_HUYGENS  F^2 = min over 0 <= r <= t of g(gamma(x, v, r, 0)), taken on the
  *               solver grid r = n t/N, n = 0..N (eq. num_min; the first smallest
  *               node on ties), phi = min F^2 -- for Hamiltonians of degree one
- *               in p (the BUMP_NORM family, the only one accepted with it);
+ *               in p (the BUMP_NORM and SPLIT_NORM families, the only ones
+ *               accepted with it);
  *               no running cost, the certificate is the Lax test at the
  *               minimising node, and the gradient is the adjoint seeded there. */
 typedef enum { HJ_LAX = 0, HJ_HOPF = 1, HJ_HUYGENS = 2 } hj_principle;
@@ -189,6 +194,8 @@ typedef struct {
  *   family block:  SPEED_QUAD, SMOOTH_NONCONVEX: w[d]
  *                  LINEAR_QUAD: A[d*d] (row-major), then B[d*m] (row-major)
  *                  BUMP_NORM: xc[d], then kappa, mu (>= 0), sign (+1 or -1)
+ *                  SPLIT_NORM: xc_A[d], xc_B[d], then k (integer in [0, d]), kappa,
+ *                              mu (>= 0), alpha_A, alpha_B
  *                  QUAD_ISO: nothing
  *   g block:       HJ_G_QUAD_SHIFT: a[d];  HJ_G_DIAG_QUAD, HJ_G_ELLIPSE: s[d] (all > 0)
  * n_params must equal the total.  d in [1, 1024]; m in [1, 64] for
@@ -205,7 +212,8 @@ typedef struct {
     int m;             /* LINEAR_QUAD: columns of B                             */
     int n_neg;         /* SMOOTH_NONCONVEX: number of leading negative signs     */
     double s_eps;      /* SMOOTH_NONCONVEX: smoothing of |q|, > 0;
-                          BUMP_NORM: smoothing of |p|, >= 0 (0: the plain norm)  */
+                          BUMP_NORM, SPLIT_NORM: smoothing of |p|, >= 0 (0: the
+                          plain norm)                                              */
     int n_guesses;     /* random starts per query for hj_solve (0: the solver value) */
     const double *params;
     size_t n_params;

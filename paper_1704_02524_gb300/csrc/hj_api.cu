@@ -33,10 +33,10 @@ void reg_f32_lq_lax(Registry &);
 void reg_f32_lq_hopf(Registry &);
 void reg_f64_lq_lax(Registry &);
 void reg_f64_lq_hopf(Registry &);
-void reg_f32_bn_lax(Registry &);
-void reg_f32_bn_hopf(Registry &);
-void reg_f64_bn_lax(Registry &);
-void reg_f64_bn_hopf(Registry &);
+void reg_f32_spn_lax(Registry &);
+void reg_f32_spn_hopf(Registry &);
+void reg_f64_spn_lax(Registry &);
+void reg_f64_spn_hopf(Registry &);
 
 Registry &registry()
 {
@@ -58,10 +58,10 @@ Registry &registry()
         reg_f32_lq_hopf(*x);
         reg_f64_lq_lax(*x);
         reg_f64_lq_hopf(*x);
-        reg_f32_bn_lax(*x);
-        reg_f32_bn_hopf(*x);
-        reg_f64_bn_lax(*x);
-        reg_f64_bn_hopf(*x);
+        reg_f32_spn_lax(*x);
+        reg_f32_spn_hopf(*x);
+        reg_f64_spn_lax(*x);
+        reg_f64_spn_hopf(*x);
         return x;
     }();
     return *r;
@@ -105,9 +105,10 @@ FlopModel flop_model(int fam, int pr, int d, int quad)
         fld = 6.0 * d * d + 3.0 * d + 1;
         vjp = 6.0 * d * d + 2.0 * d;
         break;
-    case HJ_FAM_BUMP_NORM:
-        fld = (pr == HJ_HOPF ? 9.0 : 7.0) * d + 14;
-        vjp = (pr == HJ_HOPF ? 10.0 : 8.0) * d + 24;
+    case HJ_FAM_BUMP_NORM:  // runs as the split norm with one block
+    case HJ_FAM_SPLIT_NORM:
+        fld = (pr == HJ_HOPF ? 16.0 : 12.0) * d + 30;
+        vjp = (pr == HJ_HOPF ? 16.0 : 14.0) * d + 50;
         break;
     default: break;
     }
@@ -130,23 +131,35 @@ void fill_prob(const hj_problem_desc &D, const std::vector<double> &par, int ld,
 {
     const int d = D.d, m = (D.family == HJ_FAM_LINEAR_QUAD) ? D.m : 0;
     const int ldm = (d + 7) / 8 * 8;  // matrix rows padded for aligned vector loads
-    const size_t nvec = 5 * (size_t)DPAD, nA = (size_t)d * d, nB = (size_t)d * m, nM = (size_t)d * ldm;
+    const size_t nvec = 6 * (size_t)DPAD, nA = (size_t)d * d, nB = (size_t)d * m, nM = (size_t)d * ldm;
     host.assign(nvec + (m ? 3 * nM : 0), (T)0);
-    T *w = host.data(), *e = w + DPAD, *ga = e + DPAD, *gs2 = ga + DPAD, *gis2 = gs2 + DPAD;
+    T *w = host.data(), *e = w + DPAD, *ga = e + DPAD, *gs2 = ga + DPAD, *gis2 = gs2 + DPAD, *wb = gis2 + DPAD;
     size_t off = 0;
     if (D.family == HJ_FAM_SPEED_QUAD || D.family == HJ_FAM_SMOOTH_NONCONVEX) {
         for (int i = 0; i < d; ++i) w[i] = (T)par[i];
         off = d;
     }
-    P.kappa = P.mu = (T)0;
-    P.hsign = (T)1;
+    P.kappa = P.mu = P.alpha_a = P.alpha_b = (T)0;
+    P.ksplit = d;
     if (D.family == HJ_FAM_BUMP_NORM) {
-        // the centre xc takes the w slot; kappa, mu and the sign are scalars
+        // the split norm with block A = all coordinates: xc_A = xc, alpha_A = sign
         for (int i = 0; i < d; ++i) w[i] = (T)par[i];
         P.kappa = (T)par[d];
         P.mu = (T)par[d + 1];
-        P.hsign = (T)par[d + 2];
+        P.alpha_a = (T)par[d + 2];
         off = d + 3;
+    }
+    if (D.family == HJ_FAM_SPLIT_NORM) {
+        for (int i = 0; i < d; ++i) {
+            w[i] = (T)par[i];
+            wb[i] = (T)par[d + i];
+        }
+        P.ksplit = (int)par[2 * d];
+        P.kappa = (T)par[2 * d + 1];
+        P.mu = (T)par[2 * d + 2];
+        P.alpha_a = (T)par[2 * d + 3];
+        P.alpha_b = (T)par[2 * d + 4];
+        off = 2 * d + 5;
     }
     if (D.family == HJ_FAM_LINEAR_QUAD) {
         // At[j][i] = A[i][j], A[j][i], Cm = B B^T (double sums, then rounded),
@@ -194,10 +207,11 @@ void bind_prob(void *block, int m, ProbDev<T> &P)
     P.ga = b + 2 * DPAD;
     P.gs2 = b + 3 * DPAD;
     P.gis2 = b + 4 * DPAD;
+    P.wb = b + 5 * DPAD;
     const size_t nM = (size_t)P.d * P.ldm;
-    P.At = m ? b + 5 * DPAD : nullptr;
-    P.A = m ? b + 5 * DPAD + nM : nullptr;
-    P.Cm = m ? b + 5 * DPAD + 2 * nM : nullptr;
+    P.At = m ? b + 6 * DPAD : nullptr;
+    P.A = m ? b + 6 * DPAD + nM : nullptr;
+    P.Cm = m ? b + 6 * DPAD + 2 * nM : nullptr;
 }
 
 }  // namespace
@@ -290,6 +304,7 @@ size_t expected_params(const hj_problem_desc &D)
     if (D.family == HJ_FAM_SPEED_QUAD || D.family == HJ_FAM_SMOOTH_NONCONVEX) n += D.d;
     if (D.family == HJ_FAM_LINEAR_QUAD) n += (size_t)D.d * D.d + (size_t)D.d * D.m;
     if (D.family == HJ_FAM_BUMP_NORM) n += D.d + 3;
+    if (D.family == HJ_FAM_SPLIT_NORM) n += 2 * (size_t)D.d + 5;
     n += D.d;
     return n;
 }
@@ -297,12 +312,13 @@ size_t expected_params(const hj_problem_desc &D)
 hj_status validate_problem(hj_ctx *ctx, const hj_problem_desc &D, int idx)
 {
     if (D.d < 1 || D.d > DPAD) return fail(ctx, HJ_EINVAL, "problem %d: d=%d outside [1, %d]", idx, D.d, DPAD);
-    if (D.family < HJ_FAM_QUAD_ISO || D.family > HJ_FAM_BUMP_NORM)
+    if (D.family < HJ_FAM_QUAD_ISO || D.family > HJ_FAM_SPLIT_NORM)
         return fail(ctx, HJ_EINVAL, "problem %d: unknown family %d", idx, (int)D.family);
     if (D.principle != HJ_LAX && D.principle != HJ_HOPF && D.principle != HJ_HUYGENS)
         return fail(ctx, HJ_EINVAL, "problem %d: unknown principle %d", idx, (int)D.principle);
-    if (D.principle == HJ_HUYGENS && D.family != HJ_FAM_BUMP_NORM)
-        return fail(ctx, HJ_EINVAL, "problem %d: the Huygens functional needs a degree-one H (BUMP_NORM)", idx);
+    if (D.principle == HJ_HUYGENS && D.family != HJ_FAM_BUMP_NORM && D.family != HJ_FAM_SPLIT_NORM)
+        return fail(ctx, HJ_EINVAL, "problem %d: the Huygens functional needs a degree-one H (BUMP_NORM, SPLIT_NORM)",
+                    idx);
     if (D.g_kind != HJ_G_QUAD_SHIFT && D.g_kind != HJ_G_DIAG_QUAD && D.g_kind != HJ_G_ELLIPSE)
         return fail(ctx, HJ_EINVAL, "problem %d: unknown initial data %d", idx, (int)D.g_kind);
     if (D.family == HJ_FAM_LINEAR_QUAD) {
@@ -319,12 +335,20 @@ hj_status validate_problem(hj_ctx *ctx, const hj_problem_desc &D, int idx)
     size_t off = expected_params(D) - D.d;
     for (size_t i = 0; i < D.n_params; ++i)
         if (!std::isfinite(D.params[i])) return fail(ctx, HJ_EINVAL, "problem %d: params[%zu] not finite", idx, i);
-    if (D.family == HJ_FAM_BUMP_NORM) {
+    if (D.family == HJ_FAM_BUMP_NORM || D.family == HJ_FAM_SPLIT_NORM) {
         if (!(D.s_eps >= 0) || !std::isfinite(D.s_eps))
             return fail(ctx, HJ_EINVAL, "problem %d: s_eps must be >= 0", idx);
+    }
+    if (D.family == HJ_FAM_BUMP_NORM) {
         const double *sc = D.params + D.d;
         if (!(sc[1] >= 0)) return fail(ctx, HJ_EINVAL, "problem %d: bump mu must be >= 0", idx);
         if (sc[2] != 1.0 && sc[2] != -1.0) return fail(ctx, HJ_EINVAL, "problem %d: bump sign must be +1 or -1", idx);
+    }
+    if (D.family == HJ_FAM_SPLIT_NORM) {
+        const double *sc = D.params + 2 * D.d;
+        if (!(sc[0] >= 0 && sc[0] <= D.d && sc[0] == std::floor(sc[0])))
+            return fail(ctx, HJ_EINVAL, "problem %d: split k must be an integer in [0, d]", idx);
+        if (!(sc[2] >= 0)) return fail(ctx, HJ_EINVAL, "problem %d: split mu must be >= 0", idx);
     }
     if (D.g_kind == HJ_G_DIAG_QUAD || D.g_kind == HJ_G_ELLIPSE)
         for (int i = 0; i < D.d; ++i)
@@ -368,6 +392,9 @@ hj_status validate_opts(hj_ctx *ctx, const hj_solver_opts &o)
 // on the problem).
 int kprin(int principle) { return principle == HJ_HOPF ? HJ_HOPF : HJ_LAX; }
 
+// Kernel set of a family: the bump norm runs as the one-block split norm.
+int kfam(int family) { return family == HJ_FAM_BUMP_NORM ? HJ_FAM_SPLIT_NORM : family; }
+
 // Smallest instantiated C >= need for this (precision, family, principle, kind).
 int pick_c(int prec, int fam, int pr, int kind, int need)
 {
@@ -399,7 +426,7 @@ bool choose(const hj_ctx *ctx, int p, int kind, int *tpp_out, int *c_out)
         if (ov && kind != K_CERT && tpp != ov) continue;
         const int need = (D.d + tpp - 1) / tpp;
         if (!ov && need > pref && tpp < 32) continue;
-        const int c = pick_c(prec, D.family, kprin(D.principle), kind, need);
+        const int c = pick_c(prec, kfam(D.family), kprin(D.principle), kind, need);
         if (c > 0) {
             *tpp_out = tpp;
             *c_out = c;
@@ -412,7 +439,7 @@ bool choose(const hj_ctx *ctx, int p, int kind, int *tpp_out, int *c_out)
 const KSet &kset(const hj_ctx *ctx, int p, int c)
 {
     const hj_problem_desc &D = ctx->desc[p];
-    return registry().k[ctx->prec][D.family][kprin(D.principle)][c];
+    return registry().k[ctx->prec][kfam(D.family)][kprin(D.principle)][c];
 }
 
 int persistent_grid(hj_ctx *ctx, const void *fn)

@@ -32,10 +32,15 @@ constexpr int CK_BUDGET = 3072;  // bytes of checkpoint + segment storage per th
 template <typename T>
 struct ProbDev {
     int d, family, principle, g_kind, m, n_neg, n_guesses, ld;
-    int huygens;  // Lax kernels of the bump-norm family: minimise F^2 (smallest g over the grid nodes)
+    int huygens;  // Lax kernels of the split-norm family: minimise F^2 (smallest g over the grid nodes)
     T s_eps;
-    T kappa, mu, hsign;  // bump-norm family: c = 1 + kappa exp(-mu |x - xc|^2), H = hsign c |p|
-    const T *w;     // [DPAD] speed direction (bump-norm family: the centre xc)
+    // split-norm family (the bump norm is its one-block case): H = c_A |p_A| + c_B |p_B|
+    // over the coordinate blocks [0, ksplit) and [ksplit, d), c_b = alpha_b (1 + kappa
+    // exp(-mu |x - xc_b|^2)), xc_A in w and xc_B in wb
+    int ksplit;
+    T kappa, mu, alpha_a, alpha_b;
+    const T *w;     // [DPAD] speed direction (split-norm family: the centre xc_A)
+    const T *wb;    // [DPAD] split-norm family: the centre xc_B
     const T *e;     // [DPAD] signs of the smooth non-convex family (0 past d)
     const T *ga;    // [DPAD] shift a of g = |x-a|^2/2
     const T *gs2;   // [DPAD] sigma^2 of g = sum x^2/(2 sigma^2)
@@ -185,7 +190,9 @@ __device__ __forceinline__ T start_component(unsigned long long seed, long long 
 template <typename T, int C>
 struct TP {
     T w[C], e[C];
-    T kap, mu, sg;
+    T wb[C], ma[C];  // split-norm family: centre xc_B, and 1 on block A's components
+    T kap, mu, al_a, al_b;
+    bool has_a, has_b;
     const T *At, *A, *Cm;
     T *sh;
     int d, ldm;
@@ -193,12 +200,17 @@ struct TP {
     {
         kap = P.kappa;
         mu = P.mu;
-        sg = P.hsign;
+        al_a = P.alpha_a;
+        al_b = P.alpha_b;
+        has_a = P.ksplit > 0;
+        has_b = P.ksplit < P.d;
 #pragma unroll
         for (int k = 0; k < C; ++k) {
             int i = g.lane + k * g.tpp;
             w[k] = P.w[i];
             e[k] = P.e[i];
+            wb[k] = P.wb ? P.wb[i] : (T)0;
+            ma[k] = (i < P.ksplit) ? (T)1 : (T)0;
         }
         At = P.At;
         A = P.A;
@@ -336,87 +348,114 @@ struct Family<T, C, HJ_FAM_SPEED_QUAD, PR> {
     }
 };
 
-// H = S c(gamma) |p|_n with c = 1 + kappa exp(-mu |y|^2), y = gamma - xc
-// (xc held in w), grad c = k y with k = -2 mu kappa exp(-mu |y|^2),
-// n = |p|_eps = sqrt(|p|^2 + eps):
-// dZ/dtau = (-S c p / n, S n k y),
-// L_Lax = S c (|p|^2/n - n) = -S c eps / n,  L_Hopf = S n (c - k <y, gamma>).
-// With grad k = -2 mu k y and dn/dp = p/n the vector-Jacobian product is
-//   rg = (-S k <ag,p>/n - 2 mu S n k <ap,y>) y + S n k ap
-//        + b (Lax: -S eps k / n y;  Hopf: S n k (2 mu <y,gamma> y - gamma)),
-//   rp = -S c / n ag + (S c <ag,p>/n^3 + S k <ap,y>/n) p
-//        + b (Lax: S c eps / n^3;  Hopf: S (c - k <y,gamma>) / n) p.
+// Split norm: H = c_A(gamma) n_A + c_B(gamma) n_B over the coordinate blocks
+// A = [0, ksplit), B = [ksplit, d), with n_b = sqrt(|p_b|^2 + eps) (0 for an
+// empty block), c_b = alpha_b (1 + kappa exp(-mu |y_b|^2)), y_b = gamma - xc_b,
+// grad c_b = k_b y_b, k_b = -2 mu alpha_b kappa exp(-mu |y_b|^2), and m_i the
+// block of component i:
+// dZ/dtau = (-c_{m_i} p_i / n_{m_i}, sum_b n_b k_b y_b),
+// L_Lax = -eps sum_b c_b / n_b,  L_Hopf = sum_b n_b (c_b - k_b <y_b, gamma>).
+// With grad k_b = -2 mu k_b y_b and dn_b/dp_i = p_i / n_b on block b the
+// vector-Jacobian product is, summed over the blocks,
+//   rg = (-k_b <ag,p>_b / n_b - 2 mu n_b k_b <ap,y_b>) y_b + n_b k_b ap
+//        + b (Lax: -eps k_b / n_b y_b;  Hopf: n_b k_b (2 mu <y_b,gamma> y_b - gamma)),
+// and on block b's components
+//   rp = -c_b / n_b ag + (c_b <ag,p>_b / n_b^3 + k_b <ap,y_b> / n_b) p
+//        + b (Lax: c_b eps / n_b^3;  Hopf: (c_b - k_b <y_b,gamma>) / n_b) p.
+// An empty block has n_b = 1/n_b = 0 and drops out.  The bump norm of Sec. 6,
+// Example 3 (H = +-c(x)|p|) is the case ksplit = d, alpha_A = +-1.
 template <typename T, int C, int PR>
-struct Family<T, C, HJ_FAM_BUMP_NORM, PR> {
+struct Family<T, C, HJ_FAM_SPLIT_NORM, PR> {
     struct FI {
-        T c, k, n, ninv, yg;
-        T y[C], p[C];
+        T c[2], k[2], n[2], ni[2], yg[2];
+        T ya[C], yb[C], p[C];
     };
     __device__ static __forceinline__ void prep(const Grp &g, const TP<T, C> &tp, T eps, const T *gam, const T *p,
                                                 FI &f)
     {
-        T rr = 0, pp = 0, yg = 0;
+        T ra = 0, rb = 0, pa = 0, pb = 0, ga = 0, gb = 0;
 #pragma unroll
         for (int k = 0; k < C; ++k) {
-            const T y = gam[k] - tp.w[k];
-            f.y[k] = y;
+            const T ya = gam[k] - tp.w[k], yb = gam[k] - tp.wb[k], pp = p[k] * p[k];
+            f.ya[k] = ya;
+            f.yb[k] = yb;
             f.p[k] = p[k];
-            rr = fma(y, y, rr);
-            pp = fma(p[k], p[k], pp);
-            if (PR == HJ_HOPF) yg = fma(y, gam[k], yg);
+            ra = fma(ya, ya, ra);
+            rb = fma(yb, yb, rb);
+            pa = fma(tp.ma[k], pp, pa);
+            pb = fma((T)1 - tp.ma[k], pp, pb);
+            if (PR == HJ_HOPF) {
+                ga = fma(ya, gam[k], ga);
+                gb = fma(yb, gam[k], gb);
+            }
         }
-        if (PR == HJ_HOPF) gsum3(g, rr, pp, yg);
-        else gsum2(g, rr, pp);
-        const T e = exp_(-tp.mu * rr);
-        f.c = fma(tp.kap, e, (T)1);
-        f.k = (T)-2 * tp.mu * tp.kap * e;
-        const T q = pp + eps;
-        f.ninv = rsq(q);
-        f.n = q * f.ninv;
-        f.yg = yg;
+        gsum4(g, ra, rb, pa, pb);
+        if (PR == HJ_HOPF) gsum2(g, ga, gb);
+        const T ea = exp_(-tp.mu * ra), eb = exp_(-tp.mu * rb);
+        f.c[0] = tp.al_a * fma(tp.kap, ea, (T)1);
+        f.c[1] = tp.al_b * fma(tp.kap, eb, (T)1);
+        f.k[0] = (T)-2 * tp.mu * tp.al_a * tp.kap * ea;
+        f.k[1] = (T)-2 * tp.mu * tp.al_b * tp.kap * eb;
+        const T qa = pa + eps, qb = pb + eps;
+        f.ni[0] = tp.has_a ? rsq(qa) : (T)0;
+        f.ni[1] = tp.has_b ? rsq(qb) : (T)0;
+        f.n[0] = qa * f.ni[0];
+        f.n[1] = qb * f.ni[1];
+        f.yg[0] = ga;
+        f.yg[1] = gb;
     }
     __device__ static __forceinline__ void field_fi(const TP<T, C> &tp, const FI &f, T eps, T *dg, T *dp, T &L)
     {
-        const T a = -tp.sg * f.c * f.ninv, b = tp.sg * f.n * f.k;
+        const T sa = f.c[0] * f.ni[0], sb = f.c[1] * f.ni[1];
+        const T fa = f.n[0] * f.k[0], fb = f.n[1] * f.k[1];
 #pragma unroll
         for (int k = 0; k < C; ++k) {
-            dg[k] = a * f.p[k];
-            dp[k] = b * f.y[k];
+            dg[k] = -fma(tp.ma[k], sa - sb, sb) * f.p[k];
+            dp[k] = fma(fa, f.ya[k], fb * f.yb[k]);
         }
-        if (PR == HJ_LAX) L = -tp.sg * f.c * eps * f.ninv;
-        else L = tp.sg * f.n * (f.c - f.k * f.yg);
+        if (PR == HJ_LAX) L = -eps * (sa + sb);
+        else L = f.n[0] * (f.c[0] - f.k[0] * f.yg[0]) + f.n[1] * (f.c[1] - f.k[1] * f.yg[1]);
     }
     __device__ static __forceinline__ void vjp_fi(const Grp &g, const TP<T, C> &tp, const FI &f, T eps, const T *ag,
                                                   const T *ap, T b, T *rg, T *rp)
     {
-        T A = 0, By = 0;
+        T Aa = 0, Ab = 0, Ba = 0, Bb = 0;
 #pragma unroll
         for (int k = 0; k < C; ++k) {
-            A = fma(ag[k], f.p[k], A);
-            By = fma(ap[k], f.y[k], By);
+            const T agp = ag[k] * f.p[k];
+            Aa = fma(tp.ma[k], agp, Aa);
+            Ab = fma((T)1 - tp.ma[k], agp, Ab);
+            Ba = fma(ap[k], f.ya[k], Ba);
+            Bb = fma(ap[k], f.yb[k], Bb);
         }
-        gsum2(g, A, By);
-        const T S = tp.sg, n = f.n, ni = f.ninv, c = f.c, kk = f.k, mu = tp.mu;
-        const T ni3 = ni * ni * ni;
-        const T snk = S * n * kk;
-        T cy = -S * kk * A * ni - (T)2 * mu * snk * By;
-        T cgam = 0;
-        T cp = S * c * A * ni3 + S * kk * By * ni;
-        if (PR == HJ_LAX) {
-            cy -= b * S * eps * kk * ni;
-            cp += b * S * c * eps * ni3;
-        } else {
-            cy += b * (T)2 * mu * snk * f.yg;
-            cgam = -b * snk;
-            cp += b * S * (c - kk * f.yg) * ni;
+        gsum4(g, Aa, Ab, Ba, Bb);
+        const T A_[2] = {Aa, Ab}, B_[2] = {Ba, Bb};
+        const T mu = tp.mu;
+        T cy[2], nk[2], cag[2], cp[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const T n = f.n[q], ni = f.ni[q], c = f.c[q], kk = f.k[q];
+            const T ni3 = ni * ni * ni;
+            nk[q] = n * kk;
+            cy[q] = -kk * A_[q] * ni - (T)2 * mu * nk[q] * B_[q];
+            cag[q] = -c * ni;
+            cp[q] = c * A_[q] * ni3 + kk * B_[q] * ni;
+            if (PR == HJ_LAX) {
+                cy[q] -= b * eps * kk * ni;
+                cp[q] += b * c * eps * ni3;
+            } else {
+                cy[q] += b * (T)2 * mu * nk[q] * f.yg[q];
+                cp[q] += b * (c - kk * f.yg[q]) * ni;
+            }
         }
-        const T cag = -S * c * ni;
+        const T nkt = nk[0] + nk[1];
 #pragma unroll
         for (int k = 0; k < C; ++k) {
-            T r = fma(cy, f.y[k], snk * ap[k]);
-            if (PR == HJ_HOPF) r = fma(cgam, f.y[k] + tp.w[k], r);
+            T r = fma(cy[0], f.ya[k], fma(cy[1], f.yb[k], nkt * ap[k]));
+            if (PR == HJ_HOPF) r = fma(-b * nkt, f.ya[k] + tp.w[k], r);  // gamma = y_A + xc_A
             rg[k] = r;
-            rp[k] = fma(cag, ag[k], cp * f.p[k]);
+            const T m = tp.ma[k];
+            rp[k] = fma(fma(m, cag[0] - cag[1], cag[1]), ag[k], fma(m, cp[0] - cp[1], cp[1]) * f.p[k]);
         }
     }
 };
@@ -831,7 +870,7 @@ __device__ __forceinline__ T functional(const Grp &g, const TP<T, C> &tp, const 
     if (N < 1 || N > MAX_N) return (T)NAN;  // step counts outside [1, MAX_N] are rejected
     const T h = t / (T)N;
     T Q = 0, Qc = 0;
-    if (PR == HJ_LAX && FAM == HJ_FAM_BUMP_NORM && P.huygens) {
+    if (PR == HJ_LAX && FAM == HJ_FAM_SPLIT_NORM && P.huygens) {
         // F^2: the smallest g over the nodes z_0 .. z_N (first one on ties;
         // group sums are identical on every lane, so the choice is uniform);
         // gam, p return the minimising node for the certificate
@@ -961,7 +1000,7 @@ __device__ __forceinline__ T gradient(const Grp &g, const TP<T, C> &tp, const Pr
     }
     const T h = t / (T)N;
     const T eps = P.s_eps;
-    const bool huy = PR == HJ_LAX && FAM == HJ_FAM_BUMP_NORM && P.huygens;
+    const bool huy = PR == HJ_LAX && FAM == HJ_FAM_SPLIT_NORM && P.huygens;
     T gam[C], p[C], Q = 0, Qc = 0;
 #pragma unroll
     for (int k = 0; k < C; ++k) { gam[k] = x[k]; p[k] = v[k]; }

@@ -23,7 +23,7 @@ from typing import Dict, List, Optional
 
 import numpy as np
 
-FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD, FAM_BUMP_NORM = 0, 1, 2, 3, 4
+FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD, FAM_BUMP_NORM, FAM_SPLIT_NORM = range(6)
 LAX, HOPF, HUYGENS = 0, 1, 2
 G_QUAD_SHIFT, G_DIAG_QUAD, G_ELLIPSE = 0, 1, 2
 
@@ -59,10 +59,15 @@ class ProblemSpec:
     kappa: float = 0.0                   #       c = 1 + kappa exp(-mu |x - xc|^2)
     mu: float = 0.0
     hsign: float = 1.0
+    xcb: Optional[np.ndarray] = None     # [d]   split-norm family: H = c_A|p_A| + c_B|p_B| over the
+    ksplit: int = 0                      #       blocks [0,k), [k,d); c_A = alpha_a (1 + kappa
+    alpha_a: float = 0.0                 #       exp(-mu|x - xc|^2)), c_B likewise around xcb
+    alpha_b: float = 0.0
 
     def params(self) -> np.ndarray:
         """Flat parameter vector in the library's documented order:
-        family block (w | A row-major then B row-major | xc, kappa, mu, sign),
+        family block (w | A row-major then B row-major | xc, kappa, mu, sign |
+        xc_A, xc_B, k, kappa, mu, alpha_A, alpha_B),
         then g block (a | sigma)."""
         parts: List[np.ndarray] = []
         if self.family in (FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX):
@@ -71,6 +76,8 @@ class ProblemSpec:
             parts += [self.A.reshape(-1), self.B.reshape(-1)]
         if self.family == FAM_BUMP_NORM:
             parts += [self.xc, np.array([self.kappa, self.mu, self.hsign])]
+        if self.family == FAM_SPLIT_NORM:
+            parts += [self.xc, self.xcb, np.array([self.ksplit, self.kappa, self.mu, self.alpha_a, self.alpha_b])]
         parts.append(self.a if self.g_kind == G_QUAD_SHIFT else self.sigma)
         return np.concatenate([np.asarray(p, dtype=np.float64).reshape(-1) for p in parts])
 
@@ -323,6 +330,36 @@ def bump_ex3(n_side: int = 128, d: int = 2, sign: float = 1.0, t: float = 0.3, d
                     paper_solver(fd_h=fd_h, n_guesses=n_guesses, max_trials=n_guesses), precision)
 
 
+def split_ex5(n_side: int = 128, d: int = 2, k: int = 1, t: float = 0.3, ds: float = 0.02, fd_h: float = 1e-3,
+              n_guesses: int = 20, precision: str = "fp32", descent: str = "paper") -> Workload:
+    """Sec. 6 Example 5: H = c(x)|p_1..k| - c(-x)|p_k+1..d| with
+    c(x) = 2 (1 + 3 exp(-4 |x - (1,1,0,...)|^2)), the ellipse data, the Hopf
+    functional, on the n_side x n_side grid over [-3,3]^2 x {0}^(d-2) at
+    t = 0.3, twenty starts per point.  descent "paper": the paper's numerics
+    with its constants (forward Euler ds = 0.02, forward differences
+    sigma = 1e-3, Algorithm 1 with L = 50); "cg": the momentum the paper
+    proposes against this example's trench -- conjugate gradients on the
+    same Euler functional with its exact adjoint gradient."""
+    g = np.linspace(-3.0, 3.0, n_side)
+    X = np.zeros((n_side * n_side, d))
+    X[:, 0] = np.repeat(g, n_side)
+    X[:, 1] = np.tile(g, n_side)
+    X = f32(X)
+    xc = np.zeros(d)
+    xc[:2] = 1.0
+    P = ProblemSpec(d=d, family=FAM_SPLIT_NORM, principle=HOPF, g_kind=G_ELLIPSE, sigma=ellipse_sigma(d), xc=xc,
+                    xcb=-xc, ksplit=k, kappa=3.0, mu=4.0, alpha_a=2.0, alpha_b=-2.0, s_eps=0.0, n_guesses=n_guesses)
+    nq = X.shape[0]
+    N = int(round(t / ds))
+    if descent == "paper":
+        solver = paper_solver(fd_h=fd_h, step=1.0 / 50.0, n_guesses=n_guesses, max_trials=n_guesses)
+    else:
+        solver = solver_constants(quad="euler_rect", grad="adjoint_cg", step=0.05, step_max=1.0, max_iters=500,
+                                  eps=1e-7, n_guesses=n_guesses, max_trials=n_guesses, max_rounds=0, coarse_div=1)
+    return Workload(f"split_norm_d{d}_hopf_{descent}", [P], X, np.full(nq, t), np.full(nq, N, np.int32),
+                    np.zeros(nq, np.int32), solver, precision)
+
+
 WORKLOADS = {
     "quad_iso_d2_lax": c1_quad_iso,
     "speed_quad_d10_lax": c2_speed_quad,
@@ -330,6 +367,7 @@ WORKLOADS = {
     "linear_quad_d64_lax": c4_linear_quad,
     "mixed_persistent": c5_mixed,
     "bump_norm_d2_plus_lax_paper": bump_ex3,
+    "split_norm_d2_hopf_paper": split_ex5,
 }
 
 

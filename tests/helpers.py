@@ -16,7 +16,8 @@ QUAD_CODES = {"rk4": O.QUAD_RK4, "rect": O.QUAD_RECT, "euler": O.QUAD_RK4 | O.OD
 def oracle_problem(spec: W.ProblemSpec) -> O.Problem:
     return O.Problem(d=spec.d, family=spec.family, principle=spec.principle, g_kind=spec.g_kind, w=spec.w,
                      A=spec.A, B=spec.B, a=spec.a, sigma=spec.sigma, n_neg=spec.n_neg, s_eps=spec.s_eps,
-                     xc=spec.xc, kappa=spec.kappa, mu=spec.mu, hsign=spec.hsign)
+                     xc=spec.xc, kappa=spec.kappa, mu=spec.mu, hsign=spec.hsign, xcb=spec.xcb,
+                     ksplit=spec.ksplit, alpha_a=spec.alpha_a, alpha_b=spec.alpha_b)
 
 
 def oracle_opts(solver: dict, n_guesses: int) -> O.Opts:

@@ -65,6 +65,11 @@ def test_create_rejects_bad_arguments_without_a_gpu(lib):
     with pytest.raises(hj.HJError) as e:
         hj.hj_create([W.ProblemSpec(**{**spec.__dict__, "principle": W.HUYGENS})], hj.opts_from_dict(wl.solver), 0)
     assert e.value.status == hj.HJ_EINVAL and "Huygens" in str(e.value)
+    split = W.split_ex5(n_side=2).problems[0]
+    for val in (-1, 3, 0.5):
+        with pytest.raises(hj.HJError) as e:
+            hj.hj_create([W.ProblemSpec(**{**split.__dict__, "ksplit": val})], hj.opts_from_dict(wl.solver), 0)
+        assert e.value.status == hj.HJ_EINVAL and "split k" in str(e.value)
     for field, val, msg in (("hsign", 0.5, "sign"), ("mu", -1.0, "mu"), ("s_eps", -1e-3, "s_eps")):
         with pytest.raises(hj.HJError) as e:
             hj.hj_create([W.ProblemSpec(**{**bump.__dict__, field: val})], hj.opts_from_dict(wl.solver), 0)

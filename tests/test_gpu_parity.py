@@ -28,7 +28,8 @@ def hj():
 def _spec(family, principle, d, seed=0, n_neg=1, s_eps=1e-6, g_kind=None, m=None):
     rng = np.random.default_rng(seed)
     if g_kind is None:
-        g_kind = {W.FAM_SMOOTH_NONCONVEX: W.G_DIAG_QUAD, W.FAM_BUMP_NORM: W.G_ELLIPSE}.get(family, W.G_QUAD_SHIFT)
+        g_kind = {W.FAM_SMOOTH_NONCONVEX: W.G_DIAG_QUAD, W.FAM_BUMP_NORM: W.G_ELLIPSE,
+                  W.FAM_SPLIT_NORM: W.G_ELLIPSE}.get(family, W.G_QUAD_SHIFT)
     A = B = None
     if family == W.FAM_LINEAR_QUAD:
         G0 = rng.normal(size=(d, d))
@@ -38,7 +39,8 @@ def _spec(family, principle, d, seed=0, n_neg=1, s_eps=1e-6, g_kind=None, m=None
                          w=W.f32(rng.normal(size=d) / np.sqrt(d)), a=W.f32(rng.uniform(-1, 1, d)),
                          sigma=W.f32(rng.uniform(0.5, 2, d)), A=A, B=B, n_neg=n_neg, s_eps=s_eps, n_guesses=4,
                          xc=W.f32(rng.uniform(-0.5, 0.5, d)), kappa=3.0, mu=1.5,
-                         hsign=-1.0 if principle == W.HOPF else 1.0)
+                         hsign=-1.0 if principle == W.HOPF else 1.0, xcb=W.f32(rng.uniform(-0.5, 0.5, d)),
+                         ksplit=d // 2, alpha_a=1.5, alpha_b=-1.25)
 
 
 def _rows(n, d, seed, prec):
@@ -56,7 +58,8 @@ def _t(a, dtype):
 
 FAMS = [(W.FAM_QUAD_ISO, W.LAX), (W.FAM_QUAD_ISO, W.HOPF), (W.FAM_SPEED_QUAD, W.LAX), (W.FAM_SPEED_QUAD, W.HOPF),
         (W.FAM_SMOOTH_NONCONVEX, W.HOPF), (W.FAM_SMOOTH_NONCONVEX, W.LAX), (W.FAM_LINEAR_QUAD, W.LAX),
-        (W.FAM_LINEAR_QUAD, W.HOPF), (W.FAM_BUMP_NORM, W.LAX), (W.FAM_BUMP_NORM, W.HOPF)]
+        (W.FAM_LINEAR_QUAD, W.HOPF), (W.FAM_BUMP_NORM, W.LAX), (W.FAM_BUMP_NORM, W.HOPF),
+        (W.FAM_SPLIT_NORM, W.LAX), (W.FAM_SPLIT_NORM, W.HOPF)]
 
 
 @pytest.mark.parametrize("family,principle", FAMS)
@@ -204,6 +207,32 @@ def test_paper_mode_example3_huygens_solve_matches_oracle(hj, prec):
     # short of the ray through the centre stays above it, on both sides)
     assert len(near) > 0 and np.all(phi[64:] >= -0.5 - 1e-5)
     assert np.mean(np.abs(phi[64:] + 0.5) < 1e-4) >= 0.9
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("descent", ["paper", "cg"])
+def test_example5_split_norm_hopf_solve_matches_oracle(hj, prec, descent):
+    # Sec. 6 Example 5 (H = c(x)|p_1| - c(-x)|p_2|, Hopf, twenty starts) on 64
+    # points spread over the [-3,3]^2 grid, in the paper's numerics and with
+    # the conjugate-gradient momentum on the same Euler functional.  FP64
+    # matches the oracle on every row.  The functional is non-convex and,
+    # where a block's momentum passes through zero, not smooth; in binary32
+    # starts near a basin boundary may end in the other basin, so fp32 is
+    # compared on rows where two of the twenty oracle starts reach the
+    # oracle's phi, 90% of them within 1e-4.
+    wl = W.split_ex5(n_side=128, precision=prec, descent=descent)
+    w = wl.take(np.arange(0, wl.nq, wl.nq // 64)[:64])
+    phi, v, st, ref, info = _solve_both(hj, w, w.nq)
+    rphi = ref["phi"]
+    if prec == "fp64":
+        err = rel_err(phi, rphi)
+        assert np.all(err <= 1e-4), (err.max(), int(np.argmax(err)))
+        assert np.array_equal(st & 1, ref["status"] & 1)
+    else:
+        keep = np.sum(np.abs(ref["slot_F"] - (-rphi[:, None])) <= 1e-6 * (1 + np.abs(rphi[:, None])), 1) >= 2
+        assert keep.mean() > 0.75
+        err = rel_err(phi, rphi)[keep]
+        assert np.mean(err <= 1e-4) >= 0.9, (np.mean(err <= 1e-4), err.max())
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])

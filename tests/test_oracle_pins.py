@@ -467,6 +467,35 @@ def test_split_norm_hopf_solve_matches_separable_hopf_formula():
         assert abs(phi[q] + G) < (1e-4 if kink else 1e-12), (q, phi[q], -G)
 
 
+def test_example5_trench_traps_half_the_coordinate_descents_and_momentum_frees_more():
+    # Sec. 6, Example 5 at x = (-0.93, -0.35), t = 0.3: the Hopf functional
+    # has a local minimiser whose basin rivals the global one's, joined by a
+    # flat trench; the paper estimates that about half of the random starts
+    # of its coordinate descent end in the local minimum, and points to
+    # momentum.  200 starts in the paper's numerics, and conjugate gradients
+    # (the momentum here) on the same Euler functional with its adjoint.
+    P = _p_split()
+    x, t = np.array([[-0.93, -0.35]]), 0.3
+    G = 200
+    cd = O.Opts(quad=EULER_RECT, descent=O.DESC_CD, grad=O.GRAD_FD_FORWARD, fd_h=1e-3, step=1 / 50,
+                max_iters=20000, halving_period=500, eps=0.5e-7, n_guesses=G, max_trials=G, max_rounds=0, seed=11,
+                cert_tol=1e-3)
+    cg = O.Opts(quad=EULER_RECT, descent=O.DESC_CG, grad=O.GRAD_ADJOINT, step=0.05, step_max=1.0, max_iters=500,
+                eps=1e-9, n_guesses=G, max_trials=G, max_rounds=0, seed=11, cert_tol=1e-3)
+    r_cd, r_cg = O.solve(P, cd, x, t, 15), O.solve(P, cg, x, t, 15)
+    best = min(np.nanmin(r_cd["slot_F"]), np.nanmin(r_cg["slot_F"]))
+    assert abs(r_cd["phi"][0] + best) < 1e-6 and abs(r_cg["phi"][0] + best) < 1e-6
+    F_cd = r_cd["slot_F"][0]
+    at_global = np.mean(F_cd <= best + 1e-4)
+    # the local minimum: the most frequent value above the global one
+    rest = np.round(F_cd[F_cd > best + 1e-4], 3)
+    vals, counts = np.unique(rest, return_counts=True)
+    local = vals[np.argmax(counts)]
+    assert local > best + 0.1 and np.mean(np.abs(F_cd - local) < 1e-3) > 0.35
+    assert 0.3 < at_global < 0.65
+    assert np.mean(r_cg["slot_F"][0] <= best + 1e-4) > at_global + 0.1
+
+
 def _golden_tables():
     rows = []
     with open(os.path.join(os.path.dirname(__file__), "golden", "ex3_convergence_tables.txt")) as f:
