@@ -39,7 +39,8 @@ _LIB_PATH = os.path.join(_HERE, "libhj_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD, FAM_BUMP_NORM, FAM_SPLIT_NORM = range(6)
+(FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD, FAM_BUMP_NORM, FAM_SPLIT_NORM, FAM_HARMONIC,
+ FAM_EVANS) = range(8)
 LAX, HOPF, HUYGENS = 0, 1, 2  # HUYGENS: the Lax principle through F^2 (eq. num_min)
 G_QUAD_SHIFT, G_DIAG_QUAD, G_ELLIPSE = 0, 1, 2
 QUAD_RK4, QUAD_RECT = 0, 1
@@ -69,7 +70,7 @@ class _Problem(C.Structure):
                 ("ga", C.POINTER(C.c_double)), ("gs", C.POINTER(C.c_double)),
                 ("xc", C.POINTER(C.c_double)), ("kappa", C.c_double), ("mu", C.c_double), ("hsign", C.c_double),
                 ("xcb", C.POINTER(C.c_double)), ("ksplit", C.c_int), ("alpha_a", C.c_double),
-                ("alpha_b", C.c_double)]
+                ("alpha_b", C.c_double), ("beta", C.c_double), ("gamma0", C.c_double)]
 
 
 class _Opts(C.Structure):
@@ -140,6 +141,8 @@ class Problem:
     ksplit: int = 0                   #   c_A = alpha_a (1 + kappa exp(-mu|x - xc|^2)),
     alpha_a: float = 0.0              #   c_B = alpha_b (1 + kappa exp(-mu|x - xcb|^2))
     alpha_b: float = 0.0
+    beta: float = 0.0                 # Evans-type family: H = -c(x) p_1 + beta|p_2| - |p| - gamma0,
+    gamma0: float = 0.0               #   c = alpha_a (1 + kappa exp(-mu|x - xc|^2)); harmonic: H = hsign(|p|^2+|x|^2)/2
     _c: Optional[_Problem] = field(default=None, repr=False)
 
     def c(self) -> _Problem:
@@ -152,7 +155,8 @@ class Problem:
             self._c = _Problem(self.d, self.family, self.principle, self.g_kind, m, self.n_neg, self.s_eps,
                                _dp(self.w), _dp(self.A), _dp(self.B), _dp(self.a), _dp(self.sigma),
                                _dp(self.xc), float(self.kappa), float(self.mu), float(self.hsign),
-                               _dp(self.xcb), int(self.ksplit), float(self.alpha_a), float(self.alpha_b))
+                               _dp(self.xcb), int(self.ksplit), float(self.alpha_a), float(self.alpha_b),
+                               float(self.beta), float(self.gamma0))
         return self._c
 
 

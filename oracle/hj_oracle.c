@@ -15,7 +15,9 @@
  * quadratic H = <Ax,p> + |B^T p|^2/2; and H = +-c(x)|p| with the Gaussian
  * bump speed c = 1 + kappa exp(-mu|x - xc|^2) of Sec. 6, Example 3; and the
  * split norm H = c_A(x)|p_A| + c_B(x)|p_B| over two coordinate blocks, each
- * speed a signed multiple of such a bump (Sec. 6, Example 5).
+ * speed a signed multiple of such a bump (Sec. 6, Example 5); the harmonic
+ * oscillator H = +-(|p|^2 + |x|^2)/2 (Sec. 6, Example 2); and the non-convex
+ * H = -c(x) p_1 + beta|p_2| - |p| - gamma0 with c a bump (Sec. 6, Example 4).
  * Initial data: |x - a|^2/2, sum x_i^2/(2 s_i^2), and the ellipse data
  * (<x, Ax> - 1)/2, A diagonal, of Sec. 6.
  *
@@ -56,7 +58,7 @@
 /* ------------------------------------------------------------------------ */
 
 enum { FAM_QUAD_ISO = 0, FAM_SPEED_QUAD = 1, FAM_SMOOTH_NONCONVEX = 2, FAM_LINEAR_QUAD = 3, FAM_BUMP_NORM = 4,
-       FAM_SPLIT_NORM = 5 };
+       FAM_SPLIT_NORM = 5, FAM_HARMONIC = 6, FAM_EVANS = 7 };
 /* HUYGENS: the Lax principle through F^2 (Sec. 4.1), the smallest g over the
  * endpoints gamma(x, v, r, 0), 0 <= r <= t, taken on the solver grid r = n dt
  * (eq. num_min) -- for Hamiltonians of degree one in p, with no running cost. */
@@ -101,6 +103,10 @@ typedef struct {
     const double *xcb; /* [d] */
     int ksplit;
     double alpha_a, alpha_b;
+    /* harmonic family (Example 2): H = hsign (|p|^2 + |x|^2)/2.
+     * Evans-type family (Example 4): H = -c(x) p_1 + beta |p_2|_eps - |p|_eps - gamma0
+     * with c = alpha_a (1 + kappa exp(-mu |x - xc|^2)) and |q|_eps = sqrt(q^2 + s_eps) */
+    double beta, gamma0;
 } orc_problem;
 
 typedef struct {
@@ -292,6 +298,14 @@ static double ham(const orc_problem *P, const double *gam, const double *p)
         split_eval(P, gam, p, &S);
         return S.c[0] * S.n[0] + S.c[1] * S.n[1];
     }
+    case FAM_HARMONIC:
+        return P->hsign * 0.5 * (dot(p, p, d) + dot(gam, gam, d));
+    case FAM_EVANS: {
+        double y[ORC_DMAX], c, k;
+        bump(P, gam, y, &c, &k);
+        c *= P->alpha_a;
+        return -c * p[0] + P->beta * sqrt(p[1] * p[1] + P->s_eps) - sqrt(dot(p, p, d) + P->s_eps) - P->gamma0;
+    }
     }
     return NAN;
 }
@@ -352,6 +366,27 @@ static void ham_grads(const orc_problem *P, const double *gam, const double *p, 
             Hp[i] = P->hsign * c * p[i] / n;
             Hx[i] = P->hsign * n * k * y[i];
         }
+        return;
+    }
+    case FAM_HARMONIC:
+        for (int i = 0; i < d; ++i) {
+            Hp[i] = P->hsign * p[i];
+            Hx[i] = P->hsign * gam[i];
+        }
+        return;
+    case FAM_EVANS: {
+        /* H_p = -c e_1 + beta p_2/s_2 e_2 - p/n,  H_x = -p_1 grad c = -p_1 alpha k y */
+        double y[ORC_DMAX], c, k;
+        bump(P, gam, y, &c, &k);
+        c *= P->alpha_a;
+        k *= P->alpha_a;
+        double n = sqrt(dot(p, p, d) + P->s_eps), s2 = sqrt(p[1] * p[1] + P->s_eps);
+        for (int i = 0; i < d; ++i) {
+            Hp[i] = -p[i] / n;
+            Hx[i] = -p[0] * k * y[i];
+        }
+        Hp[0] -= c;
+        Hp[1] += P->beta * p[1] / s2;
         return;
     }
     case FAM_SPLIT_NORM: {
@@ -501,6 +536,51 @@ static void field_vjp(const orc_problem *P, const double *z, const double *a, do
             }
             rg[i] = g_i;
             rp[i] = p_i;
+        }
+        return;
+    }
+    case FAM_HARMONIC: {
+        /* field = (-S p, S gamma), Lax and Hopf L = S (|p|^2 - |gamma|^2)/2 */
+        const double S = P->hsign;
+        for (int i = 0; i < d; ++i) {
+            rg[i] = S * ap[i] - b * S * gam[i];
+            rp[i] = -S * ag[i] + b * S * p[i];
+        }
+        return;
+    }
+    case FAM_EVANS: {
+        /* field_gamma = c e_1 - beta p_2/s_2 e_2 + p/n, field_p = -p_1 k y
+         * (c, k including alpha); grad c = k y, grad k = -2 mu k y;
+         * Lax L = <p,H_p> - H = gamma0 - beta eps/s_2 + eps/n;
+         * Hopf L = H - <H_x, gamma> = H + p_1 k <y, gamma> */
+        double y[ORC_DMAX], c, k;
+        bump(P, gam, y, &c, &k);
+        c *= P->alpha_a;
+        k *= P->alpha_a;
+        const double eps = P->s_eps, mu = P->mu, beta = P->beta;
+        const double n = sqrt(dot(p, p, d) + eps), s2 = sqrt(p[1] * p[1] + eps);
+        const double Agp = dot(ag, p, d), Apy = dot(ap, y, d), yg = dot(y, gam, d);
+        for (int i = 0; i < d; ++i) {
+            /* d/dgamma: ag_1 grad c, and -p_1 (grad k <ap,y> + k ap) */
+            double g_i = ag[0] * k * y[i] + 2.0 * mu * p[0] * k * Apy * y[i] - p[0] * k * ap[i];
+            /* d/dp: ag/n - <ag,p> p/n^3 (- beta eps/s_2^3 ag_2 on p_2), -k <ap,y> on p_1 */
+            double p_i = ag[i] / n - Agp * p[i] / (n * n * n);
+            if (P->principle == LAX) {
+                p_i += b * (-eps * p[i] / (n * n * n));
+            } else {
+                g_i += b * p[0] * k * (gam[i] - 2.0 * mu * yg * y[i]);
+                p_i += b * (-p[i] / n);
+            }
+            rg[i] = g_i;
+            rp[i] = p_i;
+        }
+        rp[0] += -k * Apy;
+        rp[1] += -beta * eps / (s2 * s2 * s2) * ag[1];
+        if (P->principle == LAX) {
+            rp[1] += b * beta * eps * p[1] / (s2 * s2 * s2);
+        } else {
+            rp[0] += b * (-c + k * yg);
+            rp[1] += b * beta * p[1] / s2;
         }
         return;
     }

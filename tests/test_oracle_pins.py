@@ -496,6 +496,81 @@ def test_example5_trench_traps_half_the_coordinate_descents_and_momentum_frees_m
     assert np.mean(r_cg["slot_F"][0] <= best + 1e-4) > at_global + 0.1
 
 
+def _p_harmonic(principle, hsign, d=2, sig=ELL_SIG):
+    return O.Problem(d=d, family=O.FAM_HARMONIC, principle=principle, g_kind=O.G_ELLIPSE, sigma=sig, hsign=hsign)
+
+
+@pytest.mark.parametrize("hsign", [1.0, -1.0])
+def test_harmonic_functional_matches_exact_rotation(hsign):
+    # H = S(|p|^2 + |x|^2)/2 (Example 2) turns (gamma, p) rigidly:
+    # gamma(tau) = x cos tau - S v sin tau, p(tau) = v cos tau + S x sin tau,
+    # and the running cost S(|p|^2 - |gamma|^2)/2 (both principles)
+    # integrates to S/2 [(|v|^2 - |x|^2) sin(2t)/2 + S <x,v> (1 - cos 2t)]
+    rng = np.random.default_rng(37)
+    for principle in (O.LAX, O.HOPF):
+        P = _p_harmonic(principle, hsign, d=3, sig=np.array([1.0, 2.5, 0.5]))
+        for _ in range(4):
+            x, v, t = rng.uniform(-2, 2, 3), rng.uniform(-2, 2, 3), rng.uniform(0.1, 1)
+            gam = x * np.cos(t) - hsign * v * np.sin(t)
+            pt = v * np.cos(t) + hsign * x * np.sin(t)
+            Q = 0.5 * hsign * ((v @ v - x @ x) * np.sin(2 * t) / 2 + hsign * (x @ v) * (1 - np.cos(2 * t)))
+            sig2 = np.array([1.0, 6.25, 0.25])
+            if principle == O.LAX:
+                expect = 0.5 * (np.sum(gam ** 2 / sig2) - 1) + Q
+            else:
+                expect = 0.5 * (np.sum(sig2 * pt ** 2) + 1) + Q - x @ v
+            assert abs(O.functional(P, x, t, 200, v) - expect) < 1e-9
+
+
+@pytest.mark.parametrize("hsign,principle,t", [(1.0, O.LAX, 0.5), (1.0, O.HOPF, 0.5), (-1.0, O.HOPF, 0.5),
+                                                (-1.0, O.HOPF, 0.2)])
+def test_harmonic_solve_matches_riccati(hsign, principle, t):
+    # phi = sum_i P_i(t) x_i^2/2 - 1/2 with P_i' = -S (1 + P_i^2), P_i(0) = 1/s_i^2,
+    # i.e. P_i = tan(arctan(1/s_i^2) - S t): the smooth solution while no
+    # characteristics cross (Example 2, d = 2, ellipse data)
+    P = _p_harmonic(principle, hsign)
+    xq = np.array([[-0.93, -0.35], [1.2, -0.5], [-1.5, 0.8], [0.4, 1.9], [0.1, 0.0]])
+    opts = O.Opts(descent=O.DESC_GD, grad=O.GRAD_ADJOINT, step=0.05, max_iters=3000, eps=1e-12, adapt=1,
+                  grow=1.2, shrink=0.5, step_max=1.0, n_guesses=4, max_trials=4, max_rounds=0, seed=3, cert_tol=1e-3)
+    phi = O.solve(P, opts, xq, t, 100)["phi"]
+    Pt = np.tan(np.arctan(1.0 / ELL_SIG ** 2) - hsign * t)
+    expect = 0.5 * (xq ** 2) @ Pt - 0.5
+    assert np.abs(phi - expect).max() < 1e-8, (phi, expect)
+
+
+def _p_evans(principle, kappa=3.0, d=2, s_eps=0.0):
+    xc = np.zeros(d)
+    xc[:2] = 1.0
+    return O.Problem(d=d, family=O.FAM_EVANS, principle=principle, g_kind=O.G_ELLIPSE, sigma=ELL_SIG, xc=xc,
+                     kappa=kappa, mu=4.0, alpha_a=2.0, beta=2.0, gamma0=1.0, s_eps=s_eps)
+
+
+def test_evans_state_independent_hopf_solve_matches_brute_force():
+    # kappa = 0: H(p) = -2 p_1 + 2|p_2| - |p| - 1 (Example 4 with a flat
+    # speed) is state independent and non-convex, g convex: phi is
+    # -min_v [g*(v) + t H(v) - <x,v>] (classical Hopf formula), found here by
+    # a dense grid search refined by Nelder-Mead from the best grid points
+    P = _p_evans(O.HOPF, kappa=0.0)
+    t = 0.1
+    s2 = ELL_SIG ** 2
+    H = lambda v: -2 * v[..., 0] + 2 * np.abs(v[..., 1]) - np.hypot(v[..., 0], v[..., 1]) - 1
+    xq = np.array([[-0.93, -0.35], [1.2, -0.5], [-1.5, 0.8], [0.4, 1.9]])
+    opts = O.Opts(descent=O.DESC_CD, grad=O.GRAD_FD_CENTRAL, fd_h=1e-6, step=0.25, max_iters=8000,
+                  halving_period=500, eps=1e-12, n_guesses=20, max_trials=20, max_rounds=0, seed=4, cert_tol=1e-3)
+    phi = O.solve(P, opts, xq, t, 20)["phi"]
+    g1 = np.linspace(-4, 4, 801)
+    V = np.stack(np.meshgrid(g1, g1, indexing="ij"), -1)
+    for q, x in enumerate(xq):
+        Gf = lambda v: 0.5 * (np.sum(s2 * v ** 2, -1) + 1) + t * H(v) - v @ x
+        vals = Gf(V)
+        best = np.inf
+        for k in np.argsort(vals.ravel())[:5]:
+            r = scipy.optimize.minimize(Gf, V.reshape(-1, 2)[k], method="Nelder-Mead",
+                                        options=dict(xatol=1e-10, fatol=1e-13, maxiter=4000))
+            best = min(best, r.fun)
+        assert abs(phi[q] + best) < 1e-4, (q, phi[q], -best)
+
+
 def _golden_tables():
     rows = []
     with open(os.path.join(os.path.dirname(__file__), "golden", "ex3_convergence_tables.txt")) as f:
@@ -549,7 +624,8 @@ def test_adjoint_gradient_closed_form_quad_iso():
     (O.FAM_LINEAR_QUAD, O.LAX, O.G_QUAD_SHIFT), (O.FAM_LINEAR_QUAD, O.HOPF, O.G_QUAD_SHIFT),
     (O.FAM_BUMP_NORM, O.LAX, O.G_ELLIPSE), (O.FAM_BUMP_NORM, O.HOPF, O.G_ELLIPSE),
     (O.FAM_BUMP_NORM, O.HUYGENS, O.G_ELLIPSE), (O.FAM_SPLIT_NORM, O.LAX, O.G_ELLIPSE),
-    (O.FAM_SPLIT_NORM, O.HOPF, O.G_ELLIPSE)])
+    (O.FAM_SPLIT_NORM, O.HOPF, O.G_ELLIPSE), (O.FAM_HARMONIC, O.LAX, O.G_ELLIPSE),
+    (O.FAM_HARMONIC, O.HOPF, O.G_ELLIPSE), (O.FAM_EVANS, O.LAX, O.G_ELLIPSE), (O.FAM_EVANS, O.HOPF, O.G_ELLIPSE)])
 @pytest.mark.parametrize("quad", [O.QUAD_RK4, O.QUAD_RECT, EULER, EULER_RECT])
 def test_adjoint_gradient_matches_central_differences(family, principle, g_kind, quad):
     rng = np.random.default_rng(7 + family + 3 * principle)
@@ -558,7 +634,7 @@ def test_adjoint_gradient_matches_central_differences(family, principle, g_kind,
                   a=rng.uniform(-1, 1, d), sigma=rng.uniform(0.5, 2, d), A=rng.normal(size=(d, d)) * 0.2,
                   B=rng.normal(size=(d, 4)) / math.sqrt(d), n_neg=2, s_eps=1e-2,
                   xc=rng.uniform(-0.5, 0.5, d), kappa=3.0, mu=1.5, hsign=1.0 if principle == O.LAX else -1.0,
-                  xcb=rng.uniform(-0.5, 0.5, d), ksplit=2, alpha_a=1.5, alpha_b=-1.2)
+                  xcb=rng.uniform(-0.5, 0.5, d), ksplit=2, alpha_a=1.5, alpha_b=-1.2, beta=2.0, gamma0=1.0)
     for _ in range(3):
         x, v = rng.uniform(-1, 1, d), rng.uniform(-1, 1, d)
         F, g = O.gradient(P, x, 0.5, 16, v, quad=quad)
