@@ -50,6 +50,18 @@ WORKLOADS = {
                                     "points/s (H = c(x)|p|, d=2 cross-section grid, the paper's numerics)",
                                     "Algorithm 1 (cyclic coordinate descent, alpha halving), forward "
                                     "differences, forward Euler with the rectangle rule"),
+    "split_norm_d2_hopf_paper": (lambda nq: W.split_ex5(n_side=max(1, int(round(nq ** 0.5)))), 16384,
+                                 "points/s (Example 5 H = c(x)|p_1| - c(-x)|p_2|, d=2 grid, the paper's numerics)",
+                                 "Algorithm 1, forward differences, forward Euler with the rectangle rule; 20 starts"),
+    "split_norm_d2_hopf_cg": (lambda nq: W.split_ex5(n_side=max(1, int(round(nq ** 0.5))), descent="cg"), 16384,
+                              "points/s (Example 5, d=2 grid, conjugate-gradient momentum on the Euler functional)",
+                              "conjugate gradients with the discrete adjoint of forward Euler; 20 starts"),
+    "harmonic_d2_minus_hopf_paper": (lambda nq: W.harmonic_ex2(n_side=max(1, int(round(nq ** 0.5)))), 16384,
+                                     "points/s (Example 2 H = -(|p|^2+|x|^2)/2, d=2 grid, the paper's numerics)",
+                                     "Algorithm 1, forward differences, forward Euler with the rectangle rule"),
+    "evans_d2_hopf_paper": (lambda nq: W.evans_ex4(n_side=max(1, int(round(nq ** 0.5)))), 16384,
+                            "points/s (Example 4 Evans-type H, d=2 grid, the paper's numerics)",
+                            "Algorithm 1, forward differences, forward Euler with the rectangle rule"),
 }
 CPU_SAMPLE = 64          # queries of the oracle timing sample (cpu_baseline)
 REF_SAMPLE = 64          # queries per step of the reference arm

@@ -71,10 +71,14 @@ typedef enum {
     HJ_FAM_LINEAR_QUAD = 3,      /* H = <A x, p> + |B^T p|^2/2                               */
     HJ_FAM_BUMP_NORM = 4,        /* H = sign c(x) |p|_eps,  c = 1 + kappa exp(-mu |x - xc|^2),
                                     |p|_eps = sqrt(|p|^2 + s_eps) (Sec. 6, Example 3)        */
-    HJ_FAM_SPLIT_NORM = 5        /* H = c_A(x) |p_A|_eps + c_B(x) |p_B|_eps over the blocks
+    HJ_FAM_SPLIT_NORM = 5,       /* H = c_A(x) |p_A|_eps + c_B(x) |p_B|_eps over the blocks
                                     A = coordinates [0, k), B = [k, d), with
                                     c_b = alpha_b (1 + kappa exp(-mu |x - xc_b|^2))
                                     (Sec. 6, Example 5; signs in the alphas)                */
+    HJ_FAM_HARMONIC = 6,         /* H = sign (|p|^2 + |x|^2)/2 (Sec. 6, Example 2)          */
+    HJ_FAM_EVANS = 7             /* H = -c(x) p_1 + beta |p_2|_eps - |p|_eps - gamma0, d >= 2,
+                                    c = alpha (1 + kappa exp(-mu |x - xc|^2))
+                                    (Sec. 6, Example 4)                                      */
 } hj_family;
 
 /* Which functional is minimised over v (Sec. 4.1):
@@ -196,6 +200,8 @@ typedef struct {
  *                  BUMP_NORM: xc[d], then kappa, mu (>= 0), sign (+1 or -1)
  *                  SPLIT_NORM: xc_A[d], xc_B[d], then k (integer in [0, d]), kappa,
  *                              mu (>= 0), alpha_A, alpha_B
+ *                  HARMONIC: sign (+1 or -1)
+ *                  EVANS: xc[d], then kappa, mu (>= 0), alpha, beta, gamma0
  *                  QUAD_ISO: nothing
  *   g block:       HJ_G_QUAD_SHIFT: a[d];  HJ_G_DIAG_QUAD, HJ_G_ELLIPSE: s[d] (all > 0)
  * n_params must equal the total.  d in [1, 1024]; m in [1, 64] for
@@ -212,8 +218,8 @@ typedef struct {
     int m;             /* LINEAR_QUAD: columns of B                             */
     int n_neg;         /* SMOOTH_NONCONVEX: number of leading negative signs     */
     double s_eps;      /* SMOOTH_NONCONVEX: smoothing of |q|, > 0;
-                          BUMP_NORM, SPLIT_NORM: smoothing of |p|, >= 0 (0: the
-                          plain norm)                                              */
+                          BUMP_NORM, SPLIT_NORM, EVANS: smoothing of the norms,
+                          >= 0 (0: the plain norms)                                */
     int n_guesses;     /* random starts per query for hj_solve (0: the solver value) */
     const double *params;
     size_t n_params;

@@ -33,6 +33,14 @@ void reg_f32_lq_lax(Registry &);
 void reg_f32_lq_hopf(Registry &);
 void reg_f64_lq_lax(Registry &);
 void reg_f64_lq_hopf(Registry &);
+void reg_f32_ho_lax(Registry &);
+void reg_f32_ho_hopf(Registry &);
+void reg_f64_ho_lax(Registry &);
+void reg_f64_ho_hopf(Registry &);
+void reg_f32_ev_lax(Registry &);
+void reg_f32_ev_hopf(Registry &);
+void reg_f64_ev_lax(Registry &);
+void reg_f64_ev_hopf(Registry &);
 void reg_f32_spn_lax(Registry &);
 void reg_f32_spn_hopf(Registry &);
 void reg_f64_spn_lax(Registry &);
@@ -58,6 +66,14 @@ Registry &registry()
         reg_f32_lq_hopf(*x);
         reg_f64_lq_lax(*x);
         reg_f64_lq_hopf(*x);
+        reg_f32_ho_lax(*x);
+        reg_f32_ho_hopf(*x);
+        reg_f64_ho_lax(*x);
+        reg_f64_ho_hopf(*x);
+        reg_f32_ev_lax(*x);
+        reg_f32_ev_hopf(*x);
+        reg_f64_ev_lax(*x);
+        reg_f64_ev_hopf(*x);
         reg_f32_spn_lax(*x);
         reg_f32_spn_hopf(*x);
         reg_f64_spn_lax(*x);
@@ -110,6 +126,11 @@ FlopModel flop_model(int fam, int pr, int d, int quad)
         fld = (pr == HJ_HOPF ? 16.0 : 12.0) * d + 30;
         vjp = (pr == HJ_HOPF ? 16.0 : 14.0) * d + 50;
         break;
+    case HJ_FAM_HARMONIC: fld = 6.0 * d + 3; vjp = 4.0 * d + 2; break;
+    case HJ_FAM_EVANS:
+        fld = (pr == HJ_HOPF ? 16.0 : 14.0) * d + 30;
+        vjp = (pr == HJ_HOPF ? 18.0 : 16.0) * d + 30;
+        break;
     default: break;
     }
     if (quad & HJ_ODE_EULER) return FlopModel{fld + 4.0 * d + 2, vjp + 4.0 * d + 1};
@@ -139,8 +160,21 @@ void fill_prob(const hj_problem_desc &D, const std::vector<double> &par, int ld,
         for (int i = 0; i < d; ++i) w[i] = (T)par[i];
         off = d;
     }
-    P.kappa = P.mu = P.alpha_a = P.alpha_b = (T)0;
+    P.kappa = P.mu = P.alpha_a = P.alpha_b = P.beta = P.gamma0 = (T)0;
     P.ksplit = d;
+    if (D.family == HJ_FAM_HARMONIC) {
+        P.alpha_a = (T)par[0];  // the sign
+        off = 1;
+    }
+    if (D.family == HJ_FAM_EVANS) {
+        for (int i = 0; i < d; ++i) w[i] = (T)par[i];
+        P.kappa = (T)par[d];
+        P.mu = (T)par[d + 1];
+        P.alpha_a = (T)par[d + 2];
+        P.beta = (T)par[d + 3];
+        P.gamma0 = (T)par[d + 4];
+        off = d + 5;
+    }
     if (D.family == HJ_FAM_BUMP_NORM) {
         // the split norm with block A = all coordinates: xc_A = xc, alpha_A = sign
         for (int i = 0; i < d; ++i) w[i] = (T)par[i];
@@ -305,6 +339,8 @@ size_t expected_params(const hj_problem_desc &D)
     if (D.family == HJ_FAM_LINEAR_QUAD) n += (size_t)D.d * D.d + (size_t)D.d * D.m;
     if (D.family == HJ_FAM_BUMP_NORM) n += D.d + 3;
     if (D.family == HJ_FAM_SPLIT_NORM) n += 2 * (size_t)D.d + 5;
+    if (D.family == HJ_FAM_HARMONIC) n += 1;
+    if (D.family == HJ_FAM_EVANS) n += D.d + 5;
     n += D.d;
     return n;
 }
@@ -312,7 +348,7 @@ size_t expected_params(const hj_problem_desc &D)
 hj_status validate_problem(hj_ctx *ctx, const hj_problem_desc &D, int idx)
 {
     if (D.d < 1 || D.d > DPAD) return fail(ctx, HJ_EINVAL, "problem %d: d=%d outside [1, %d]", idx, D.d, DPAD);
-    if (D.family < HJ_FAM_QUAD_ISO || D.family > HJ_FAM_SPLIT_NORM)
+    if (D.family < HJ_FAM_QUAD_ISO || D.family > HJ_FAM_EVANS)
         return fail(ctx, HJ_EINVAL, "problem %d: unknown family %d", idx, (int)D.family);
     if (D.principle != HJ_LAX && D.principle != HJ_HOPF && D.principle != HJ_HUYGENS)
         return fail(ctx, HJ_EINVAL, "problem %d: unknown principle %d", idx, (int)D.principle);
@@ -335,7 +371,13 @@ hj_status validate_problem(hj_ctx *ctx, const hj_problem_desc &D, int idx)
     size_t off = expected_params(D) - D.d;
     for (size_t i = 0; i < D.n_params; ++i)
         if (!std::isfinite(D.params[i])) return fail(ctx, HJ_EINVAL, "problem %d: params[%zu] not finite", idx, i);
-    if (D.family == HJ_FAM_BUMP_NORM || D.family == HJ_FAM_SPLIT_NORM) {
+    if (D.family == HJ_FAM_HARMONIC && D.params[0] != 1.0 && D.params[0] != -1.0)
+        return fail(ctx, HJ_EINVAL, "problem %d: harmonic sign must be +1 or -1", idx);
+    if (D.family == HJ_FAM_EVANS) {
+        if (D.d < 2) return fail(ctx, HJ_EINVAL, "problem %d: the Evans-type family needs d >= 2", idx);
+        if (!(D.params[D.d + 1] >= 0)) return fail(ctx, HJ_EINVAL, "problem %d: Evans mu must be >= 0", idx);
+    }
+    if (D.family == HJ_FAM_BUMP_NORM || D.family == HJ_FAM_SPLIT_NORM || D.family == HJ_FAM_EVANS) {
         if (!(D.s_eps >= 0) || !std::isfinite(D.s_eps))
             return fail(ctx, HJ_EINVAL, "problem %d: s_eps must be >= 0", idx);
     }

@@ -39,6 +39,9 @@ struct ProbDev {
     // exp(-mu |x - xc_b|^2)), xc_A in w and xc_B in wb
     int ksplit;
     T kappa, mu, alpha_a, alpha_b;
+    // Evans-type family: H = -c(x) p_1 + beta |p_2| - |p| - gamma0, c = alpha_a (1 + kappa
+    // exp(-mu |x - xc|^2)), xc in w; harmonic family: H = alpha_a (|p|^2 + |x|^2)/2
+    T beta, gamma0;
     const T *w;     // [DPAD] speed direction (split-norm family: the centre xc_A)
     const T *wb;    // [DPAD] split-norm family: the centre xc_B
     const T *e;     // [DPAD] signs of the smooth non-convex family (0 past d)
@@ -191,7 +194,8 @@ template <typename T, int C>
 struct TP {
     T w[C], e[C];
     T wb[C], ma[C];  // split-norm family: centre xc_B, and 1 on block A's components
-    T kap, mu, al_a, al_b;
+    T m1[C], m2[C];  // 1 on the first / second coordinate (Evans-type family)
+    T kap, mu, al_a, al_b, beta, gamma0;
     bool has_a, has_b;
     const T *At, *A, *Cm;
     T *sh;
@@ -202,6 +206,8 @@ struct TP {
         mu = P.mu;
         al_a = P.alpha_a;
         al_b = P.alpha_b;
+        beta = P.beta;
+        gamma0 = P.gamma0;
         has_a = P.ksplit > 0;
         has_b = P.ksplit < P.d;
 #pragma unroll
@@ -211,6 +217,8 @@ struct TP {
             e[k] = P.e[i];
             wb[k] = P.wb ? P.wb[i] : (T)0;
             ma[k] = (i < P.ksplit) ? (T)1 : (T)0;
+            m1[k] = (i == 0) ? (T)1 : (T)0;
+            m2[k] = (i == 1) ? (T)1 : (T)0;
         }
         At = P.At;
         A = P.A;
@@ -456,6 +464,152 @@ struct Family<T, C, HJ_FAM_SPLIT_NORM, PR> {
             rg[k] = r;
             const T m = tp.ma[k];
             rp[k] = fma(fma(m, cag[0] - cag[1], cag[1]), ag[k], fma(m, cp[0] - cp[1], cp[1]) * f.p[k]);
+        }
+    }
+};
+
+// Harmonic oscillator H = S (|p|^2 + |gamma|^2)/2, S = alpha_a (Sec. 6,
+// Example 2): dZ/dtau = (-S p, S gamma), L = S (|p|^2 - |gamma|^2)/2 for both
+// principles; rg = S ap - b S gamma, rp = -S ag + b S p.
+template <typename T, int C, int PR>
+struct Family<T, C, HJ_FAM_HARMONIC, PR> {
+    struct FI {
+        T pp, gg;
+        T g[C], p[C];
+    };
+    __device__ static __forceinline__ void prep(const Grp &g, const TP<T, C> &, T, const T *gam, const T *p, FI &f)
+    {
+        T pp = 0, gg = 0;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            f.g[k] = gam[k];
+            f.p[k] = p[k];
+            pp = fma(p[k], p[k], pp);
+            gg = fma(gam[k], gam[k], gg);
+        }
+        gsum2(g, pp, gg);
+        f.pp = pp;
+        f.gg = gg;
+    }
+    __device__ static __forceinline__ void field_fi(const TP<T, C> &tp, const FI &f, T, T *dg, T *dp, T &L)
+    {
+        const T S = tp.al_a;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            dg[k] = -S * f.p[k];
+            dp[k] = S * f.g[k];
+        }
+        L = (T)0.5 * S * (f.pp - f.gg);
+    }
+    __device__ static __forceinline__ void vjp_fi(const Grp &, const TP<T, C> &tp, const FI &f, T, const T *ag,
+                                                  const T *ap, T b, T *rg, T *rp)
+    {
+        const T S = tp.al_a, bS = b * tp.al_a;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            rg[k] = fma(S, ap[k], -bS * f.g[k]);
+            rp[k] = fma(-S, ag[k], bS * f.p[k]);
+        }
+    }
+};
+
+// Evans-type non-convex H = -c(gamma) p_1 + beta s_2 - n - gamma0 (Sec. 6,
+// Example 4) with s_2 = sqrt(p_2^2 + eps), n = sqrt(|p|^2 + eps),
+// c = alpha (1 + kappa exp(-mu |y|^2)), y = gamma - xc, grad c = k y,
+// k = -2 mu alpha kappa exp(-mu |y|^2), grad k = -2 mu k y, e_1, e_2 the
+// first two coordinates:
+// dZ/dtau = (c e_1 - beta p_2/s_2 e_2 + p/n, -p_1 k y),
+// L_Lax = gamma0 - beta eps/s_2 + eps/n,  L_Hopf = H + p_1 k <y, gamma>;
+//   rg = (<ag,e_1> k + 2 mu p_1 k <ap,y>) y - p_1 k ap
+//        + b (Hopf: p_1 k (gamma - 2 mu <y,gamma> y)),
+//   rp = ag/n - <ag,p> p/n^3 - k <ap,y> e_1 - beta eps/s_2^3 <ag,e_2> e_2
+//        + b (Lax: -eps p/n^3 + beta eps p_2/s_2^3 e_2;
+//             Hopf: -p/n + (-c + k <y,gamma>) e_1 + beta p_2/s_2 e_2).
+template <typename T, int C, int PR>
+struct Family<T, C, HJ_FAM_EVANS, PR> {
+    struct FI {
+        T c, k, n, ni, s2, s2i, p1, p2, yg;
+        T y[C], p[C];
+    };
+    __device__ static __forceinline__ void prep(const Grp &g, const TP<T, C> &tp, T eps, const T *gam, const T *p,
+                                                FI &f)
+    {
+        T rr = 0, pp = 0, p1 = 0, p2 = 0, yg = 0;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            const T y = gam[k] - tp.w[k];
+            f.y[k] = y;
+            f.p[k] = p[k];
+            rr = fma(y, y, rr);
+            pp = fma(p[k], p[k], pp);
+            p1 = fma(tp.m1[k], p[k], p1);
+            p2 = fma(tp.m2[k], p[k], p2);
+            if (PR == HJ_HOPF) yg = fma(y, gam[k], yg);
+        }
+        gsum4(g, rr, pp, p1, p2);
+        if (PR == HJ_HOPF) yg = gsum(g, yg);
+        const T e = exp_(-tp.mu * rr);
+        f.c = tp.al_a * fma(tp.kap, e, (T)1);
+        f.k = (T)-2 * tp.mu * tp.al_a * tp.kap * e;
+        const T q = pp + eps, q2 = fma(p2, p2, eps);
+        f.ni = rsq(q);
+        f.n = q * f.ni;
+        f.s2i = rsq(q2);
+        f.s2 = q2 * f.s2i;
+        f.p1 = p1;
+        f.p2 = p2;
+        f.yg = yg;
+    }
+    __device__ static __forceinline__ void field_fi(const TP<T, C> &tp, const FI &f, T eps, T *dg, T *dp, T &L)
+    {
+        const T a2 = -tp.beta * f.p2 * f.s2i, fp = -f.p1 * f.k;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            dg[k] = fma(tp.m1[k], f.c, fma(tp.m2[k], a2, f.p[k] * f.ni));
+            dp[k] = fp * f.y[k];
+        }
+        if (PR == HJ_LAX) {
+            L = tp.gamma0 - tp.beta * eps * f.s2i + eps * f.ni;
+        } else {
+            const T H = -f.c * f.p1 + tp.beta * f.s2 - f.n - tp.gamma0;
+            L = fma(f.p1 * f.k, f.yg, H);
+        }
+    }
+    __device__ static __forceinline__ void vjp_fi(const Grp &g, const TP<T, C> &tp, const FI &f, T eps, const T *ag,
+                                                  const T *ap, T b, T *rg, T *rp)
+    {
+        T A = 0, By = 0, ag1 = 0, ag2 = 0;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            A = fma(ag[k], f.p[k], A);
+            By = fma(ap[k], f.y[k], By);
+            ag1 = fma(tp.m1[k], ag[k], ag1);
+            ag2 = fma(tp.m2[k], ag[k], ag2);
+        }
+        gsum4(g, A, By, ag1, ag2);
+        const T kk = f.k, mu = tp.mu, ni = f.ni, ni3 = ni * ni * ni, s2i3 = f.s2i * f.s2i * f.s2i;
+        const T p1k = f.p1 * kk;
+        T cy = fma(ag1, kk, (T)2 * mu * p1k * By);
+        T cgam = 0;
+        T cp = -A * ni3;                              // on p
+        T c1 = -kk * By;                              // on e_1
+        T c2 = -tp.beta * eps * s2i3 * ag2;           // on e_2
+        if (PR == HJ_LAX) {
+            cp -= b * eps * ni3;
+            c2 += b * tp.beta * eps * f.p2 * s2i3;
+        } else {
+            cy -= b * (T)2 * mu * p1k * f.yg;
+            cgam = b * p1k;
+            cp -= b * ni;
+            c1 += b * (-f.c + kk * f.yg);
+            c2 += b * tp.beta * f.p2 * f.s2i;
+        }
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            T r = fma(cy, f.y[k], -p1k * ap[k]);
+            if (PR == HJ_HOPF) r = fma(cgam, f.y[k] + tp.w[k], r);  // gamma = y + xc
+            rg[k] = r;
+            rp[k] = fma(ag[k], ni, fma(cp, f.p[k], fma(tp.m1[k], c1, tp.m2[k] * c2)));
         }
     }
 };

@@ -1,0 +1,10 @@
+// hj_inst_f32_ho_lax.cu -- float kernels of the harmonic-oscillator family, Lax principle.
+#include "hj_inst.cuh"
+
+namespace hjd {
+void reg_f32_ho_lax(Registry &r)
+{
+    register_compute<float, HJ_FAM_HARMONIC, HJ_LAX, 1, 2, 4, 8>(r);
+    register_cert<float, HJ_FAM_HARMONIC, HJ_LAX, 1, 2, 4>(r);
+}
+}  // namespace hjd

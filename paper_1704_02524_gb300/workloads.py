@@ -23,7 +23,8 @@ from typing import Dict, List, Optional
 
 import numpy as np
 
-FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD, FAM_BUMP_NORM, FAM_SPLIT_NORM = range(6)
+(FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD, FAM_BUMP_NORM, FAM_SPLIT_NORM, FAM_HARMONIC,
+ FAM_EVANS) = range(8)
 LAX, HOPF, HUYGENS = 0, 1, 2
 G_QUAD_SHIFT, G_DIAG_QUAD, G_ELLIPSE = 0, 1, 2
 
@@ -63,11 +64,15 @@ class ProblemSpec:
     ksplit: int = 0                      #       blocks [0,k), [k,d); c_A = alpha_a (1 + kappa
     alpha_a: float = 0.0                 #       exp(-mu|x - xc|^2)), c_B likewise around xcb
     alpha_b: float = 0.0
+    beta: float = 0.0                    # Evans-type family: H = -c(x) p_1 + beta|p_2| - |p| - gamma0,
+    gamma0: float = 0.0                  #       c = alpha_a (1 + kappa exp(-mu|x - xc|^2))
+                                         # harmonic family: H = hsign (|p|^2 + |x|^2)/2
 
     def params(self) -> np.ndarray:
         """Flat parameter vector in the library's documented order:
         family block (w | A row-major then B row-major | xc, kappa, mu, sign |
-        xc_A, xc_B, k, kappa, mu, alpha_A, alpha_B),
+        xc_A, xc_B, k, kappa, mu, alpha_A, alpha_B | sign | xc, kappa, mu, alpha,
+        beta, gamma0),
         then g block (a | sigma)."""
         parts: List[np.ndarray] = []
         if self.family in (FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX):
@@ -78,6 +83,10 @@ class ProblemSpec:
             parts += [self.xc, np.array([self.kappa, self.mu, self.hsign])]
         if self.family == FAM_SPLIT_NORM:
             parts += [self.xc, self.xcb, np.array([self.ksplit, self.kappa, self.mu, self.alpha_a, self.alpha_b])]
+        if self.family == FAM_HARMONIC:
+            parts.append(np.array([self.hsign]))
+        if self.family == FAM_EVANS:
+            parts += [self.xc, np.array([self.kappa, self.mu, self.alpha_a, self.beta, self.gamma0])]
         parts.append(self.a if self.g_kind == G_QUAD_SHIFT else self.sigma)
         return np.concatenate([np.asarray(p, dtype=np.float64).reshape(-1) for p in parts])
 
@@ -360,6 +369,46 @@ def split_ex5(n_side: int = 128, d: int = 2, k: int = 1, t: float = 0.3, ds: flo
                     np.zeros(nq, np.int32), solver, precision)
 
 
+def _grid(n_side: int, d: int) -> np.ndarray:
+    g = np.linspace(-3.0, 3.0, n_side)
+    X = np.zeros((n_side * n_side, d))
+    X[:, 0] = np.repeat(g, n_side)
+    X[:, 1] = np.tile(g, n_side)
+    return f32(X)
+
+
+def harmonic_ex2(n_side: int = 128, d: int = 2, sign: float = -1.0, t: float = 0.5, ds: float = 0.02,
+                 n_guesses: int = 5, precision: str = "fp32") -> Workload:
+    """Sec. 6 Example 2: H = sign (|p|^2 + |x|^2)/2 with the ellipse data, the
+    Hopf functional for both signs, on the n_side x n_side grid over
+    [-3,3]^2 x {0}^(d-2) (t = 0.5 at d = 2; the paper's d = 7 run uses
+    t = 0.2), in the paper's numerics with ds = 0.02, sigma = 1e-3, L = 3."""
+    X = _grid(n_side, d)
+    P = ProblemSpec(d=d, family=FAM_HARMONIC, principle=HOPF, g_kind=G_ELLIPSE, sigma=ellipse_sigma(d), hsign=sign,
+                    n_guesses=n_guesses)
+    nq = X.shape[0]
+    N = int(round(t / ds))
+    return Workload(f"harmonic_d{d}_{'plus' if sign > 0 else 'minus'}_hopf_paper", [P], X, np.full(nq, t),
+                    np.full(nq, N, np.int32), np.zeros(nq, np.int32),
+                    paper_solver(step=1.0 / 3.0, n_guesses=n_guesses, max_trials=n_guesses), precision)
+
+
+def evans_ex4(n_side: int = 128, t: float = 0.1, ds: float = 0.005, n_guesses: int = 5,
+              precision: str = "fp32") -> Workload:
+    """Sec. 6 Example 4: H = -c(x) p_1 + 2|p_2| - |p| - 1 with
+    c = 2 (1 + 3 exp(-4 |x - (1,1)|^2)), d = 2, the ellipse data, the Hopf
+    functional, on the n_side x n_side grid over [-3,3]^2 at t = 0.1, in the
+    paper's numerics with ds = 0.005, sigma = 1e-3, L = 4."""
+    X = _grid(n_side, 2)
+    P = ProblemSpec(d=2, family=FAM_EVANS, principle=HOPF, g_kind=G_ELLIPSE, sigma=ellipse_sigma(2),
+                    xc=np.array([1.0, 1.0]), kappa=3.0, mu=4.0, alpha_a=2.0, beta=2.0, gamma0=1.0, s_eps=0.0,
+                    n_guesses=n_guesses)
+    nq = X.shape[0]
+    N = int(round(t / ds))
+    return Workload("evans_d2_hopf_paper", [P], X, np.full(nq, t), np.full(nq, N, np.int32), np.zeros(nq, np.int32),
+                    paper_solver(step=1.0 / 4.0, n_guesses=n_guesses, max_trials=n_guesses), precision)
+
+
 WORKLOADS = {
     "quad_iso_d2_lax": c1_quad_iso,
     "speed_quad_d10_lax": c2_speed_quad,
@@ -368,6 +417,8 @@ WORKLOADS = {
     "mixed_persistent": c5_mixed,
     "bump_norm_d2_plus_lax_paper": bump_ex3,
     "split_norm_d2_hopf_paper": split_ex5,
+    "harmonic_d2_minus_hopf_paper": harmonic_ex2,
+    "evans_d2_hopf_paper": evans_ex4,
 }
 
 

@@ -17,7 +17,8 @@ def oracle_problem(spec: W.ProblemSpec) -> O.Problem:
     return O.Problem(d=spec.d, family=spec.family, principle=spec.principle, g_kind=spec.g_kind, w=spec.w,
                      A=spec.A, B=spec.B, a=spec.a, sigma=spec.sigma, n_neg=spec.n_neg, s_eps=spec.s_eps,
                      xc=spec.xc, kappa=spec.kappa, mu=spec.mu, hsign=spec.hsign, xcb=spec.xcb,
-                     ksplit=spec.ksplit, alpha_a=spec.alpha_a, alpha_b=spec.alpha_b)
+                     ksplit=spec.ksplit, alpha_a=spec.alpha_a, alpha_b=spec.alpha_b, beta=spec.beta,
+                     gamma0=spec.gamma0)
 
 
 def oracle_opts(solver: dict, n_guesses: int) -> O.Opts:
