@@ -97,9 +97,12 @@ typedef enum { HJ_LAX = 0, HJ_HOPF = 1, HJ_HUYGENS = 2 } hj_principle;
 typedef enum {
     HJ_G_QUAD_SHIFT = 0,  /* g = |x - a|^2/2,          g* = |p|^2/2 + <a,p>       */
     HJ_G_DIAG_QUAD = 1,   /* g = sum x_i^2/(2 s_i^2),  g* = sum s_i^2 p_i^2/2     */
-    HJ_G_ELLIPSE = 2      /* g = (sum x_i^2/s_i^2 - 1)/2, g* = (sum s_i^2 p_i^2 + 1)/2:
+    HJ_G_ELLIPSE = 2,     /* g = (sum x_i^2/s_i^2 - 1)/2, g* = (sum s_i^2 p_i^2 + 1)/2:
                              zero level set the ellipse <x, Ax> = 1 with
                              A = diag(1/s_i^2) (the initial data of Sec. 6)  */
+    HJ_G_ROSENBROCK = 3   /* d = 2: g = 4e-4 (-100 + (1 - x_1)^2 + 100 (1 + x_2 - x_1^2)^2)
+                             (Sec. 6, Example 2); not convex, so Lax and Huygens
+                             only                                             */
 } hj_initial;
 
 typedef enum {
@@ -203,7 +206,8 @@ typedef struct {
  *                  HARMONIC: sign (+1 or -1)
  *                  EVANS: xc[d], then kappa, mu (>= 0), alpha, beta, gamma0
  *                  QUAD_ISO: nothing
- *   g block:       HJ_G_QUAD_SHIFT: a[d];  HJ_G_DIAG_QUAD, HJ_G_ELLIPSE: s[d] (all > 0)
+ *   g block:       HJ_G_QUAD_SHIFT: a[d];  HJ_G_DIAG_QUAD, HJ_G_ELLIPSE: s[d] (all > 0);
+ *                  HJ_G_ROSENBROCK: nothing
  * n_params must equal the total.  d in [1, 1024]; m in [1, 64] for
  * LINEAR_QUAD (d in [1, 128] there), else ignored.  LINEAR_QUAD computes
  * B B^T once in double precision at hj_create and integrates

@@ -42,7 +42,7 @@ _lib = None
 (FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD, FAM_BUMP_NORM, FAM_SPLIT_NORM, FAM_HARMONIC,
  FAM_EVANS) = range(8)
 LAX, HOPF, HUYGENS = 0, 1, 2  # HUYGENS: the Lax principle through F^2 (eq. num_min)
-G_QUAD_SHIFT, G_DIAG_QUAD, G_ELLIPSE = 0, 1, 2
+G_QUAD_SHIFT, G_DIAG_QUAD, G_ELLIPSE, G_ROSENBROCK = 0, 1, 2, 3
 QUAD_RK4, QUAD_RECT = 0, 1
 ODE_EULER = 2  # or-ed into a quad argument: forward Euler instead of RK4
 GRAD_FD_CENTRAL, GRAD_FD_FORWARD, GRAD_ADJOINT = 0, 1, 2

@@ -63,7 +63,9 @@ enum { FAM_QUAD_ISO = 0, FAM_SPEED_QUAD = 1, FAM_SMOOTH_NONCONVEX = 2, FAM_LINEA
  * endpoints gamma(x, v, r, 0), 0 <= r <= t, taken on the solver grid r = n dt
  * (eq. num_min) -- for Hamiltonians of degree one in p, with no running cost. */
 enum { LAX = 0, HOPF = 1, HUYGENS = 2 };
-enum { G_QUAD_SHIFT = 0, G_DIAG_QUAD = 1, G_ELLIPSE = 2 };
+/* G_ROSENBROCK (Sec. 6, Example 2, d = 2): g = 4e-4 (-100 + (1 - x_1)^2 + 100 (1 + x_2 - x_1^2)^2),
+ * non-convex, so it has no Legendre transform here: Lax and Huygens only. */
+enum { G_QUAD_SHIFT = 0, G_DIAG_QUAD = 1, G_ELLIPSE = 2, G_ROSENBROCK = 3 };
 enum { QUAD_RK4 = 0, QUAD_RECT = 1 };
 /* Flag or-ed into a `quad` argument: integrate with forward Euler (the
  * solver Sec. 4.2 suggests) instead of RK4.  With QUAD_RK4 the running cost
@@ -622,6 +624,10 @@ static void field_vjp(const orc_problem *P, const double *z, const double *a, do
 /* Initial data g, its gradient, its Legendre transform g* and grad g*. */
 static double g_val(const orc_problem *P, const double *x)
 {
+    if (P->g_kind == G_ROSENBROCK) {
+        double a = 1.0 - x[0], b = 1.0 + x[1] - x[0] * x[0];
+        return 4e-4 * (-100.0 + a * a + 100.0 * b * b);
+    }
     double s = (P->g_kind == G_ELLIPSE) ? -0.5 : 0.0;
     for (int i = 0; i < P->d; ++i) {
         if (P->g_kind == G_QUAD_SHIFT) {
@@ -635,11 +641,18 @@ static double g_val(const orc_problem *P, const double *x)
 }
 static void g_grad(const orc_problem *P, const double *x, double *out)
 {
+    if (P->g_kind == G_ROSENBROCK) {
+        double a = 1.0 - x[0], b = 1.0 + x[1] - x[0] * x[0];
+        out[0] = 4e-4 * (-2.0 * a - 400.0 * b * x[0]);
+        out[1] = 4e-4 * 200.0 * b;
+        return;
+    }
     for (int i = 0; i < P->d; ++i)
         out[i] = (P->g_kind == G_QUAD_SHIFT) ? x[i] - (P->ga ? P->ga[i] : 0.0) : x[i] / (P->gs[i] * P->gs[i]);
 }
 static double gstar_val(const orc_problem *P, const double *p)
 {
+    if (P->g_kind == G_ROSENBROCK) return NAN; /* not convex: no transform */
     /* the ellipse data's constant -1/2 becomes +1/2 in the transform */
     double s = (P->g_kind == G_ELLIPSE) ? 0.5 : 0.0;
     for (int i = 0; i < P->d; ++i) {

@@ -212,6 +212,7 @@ void fill_prob(const hj_problem_desc &D, const std::vector<double> &par, int ld,
     }
     for (int i = 0; i < d; ++i) {
         e[i] = (T)((i < D.n_neg) ? -1 : 1);
+        if (D.g_kind == HJ_G_ROSENBROCK) continue;  // no g parameters
         if (D.g_kind == HJ_G_QUAD_SHIFT) {
             ga[i] = (T)par[off + i];
         } else {
@@ -341,7 +342,7 @@ size_t expected_params(const hj_problem_desc &D)
     if (D.family == HJ_FAM_SPLIT_NORM) n += 2 * (size_t)D.d + 5;
     if (D.family == HJ_FAM_HARMONIC) n += 1;
     if (D.family == HJ_FAM_EVANS) n += D.d + 5;
-    n += D.d;
+    if (D.g_kind != HJ_G_ROSENBROCK) n += D.d;
     return n;
 }
 
@@ -352,10 +353,12 @@ hj_status validate_problem(hj_ctx *ctx, const hj_problem_desc &D, int idx)
         return fail(ctx, HJ_EINVAL, "problem %d: unknown family %d", idx, (int)D.family);
     if (D.principle != HJ_LAX && D.principle != HJ_HOPF && D.principle != HJ_HUYGENS)
         return fail(ctx, HJ_EINVAL, "problem %d: unknown principle %d", idx, (int)D.principle);
+    if (D.g_kind == HJ_G_ROSENBROCK && (D.d != 2 || D.principle == HJ_HOPF))
+        return fail(ctx, HJ_EINVAL, "problem %d: the Rosenbrock data needs d = 2 and no Hopf principle", idx);
     if (D.principle == HJ_HUYGENS && D.family != HJ_FAM_BUMP_NORM && D.family != HJ_FAM_SPLIT_NORM)
         return fail(ctx, HJ_EINVAL, "problem %d: the Huygens functional needs a degree-one H (BUMP_NORM, SPLIT_NORM)",
                     idx);
-    if (D.g_kind != HJ_G_QUAD_SHIFT && D.g_kind != HJ_G_DIAG_QUAD && D.g_kind != HJ_G_ELLIPSE)
+    if (D.g_kind < HJ_G_QUAD_SHIFT || D.g_kind > HJ_G_ROSENBROCK)
         return fail(ctx, HJ_EINVAL, "problem %d: unknown initial data %d", idx, (int)D.g_kind);
     if (D.family == HJ_FAM_LINEAR_QUAD) {
         if (D.m < 1 || D.m > 64 || D.d > 128)
@@ -368,7 +371,7 @@ hj_status validate_problem(hj_ctx *ctx, const hj_problem_desc &D, int idx)
     if (!D.params && expected_params(D) > 0) return fail(ctx, HJ_EINVAL, "problem %d: params is NULL", idx);
     if (D.n_params != expected_params(D))
         return fail(ctx, HJ_EINVAL, "problem %d: n_params=%zu, expected %zu", idx, D.n_params, expected_params(D));
-    size_t off = expected_params(D) - D.d;
+    size_t off = expected_params(D) - (D.g_kind == HJ_G_ROSENBROCK ? 0 : D.d);
     for (size_t i = 0; i < D.n_params; ++i)
         if (!std::isfinite(D.params[i])) return fail(ctx, HJ_EINVAL, "problem %d: params[%zu] not finite", idx, i);
     if (D.family == HJ_FAM_HARMONIC && D.params[0] != 1.0 && D.params[0] != -1.0)
@@ -507,7 +510,8 @@ void *as_ptr(T *p) { return (void *)p; }
 bool tc_eligible(const hj_ctx *ctx, int p)
 {
     return ctx->prec == 0 && ctx->dev[p].tc && ctx->tpp_override[p] == 0 && ctx->opts.quad == HJ_QUAD_RK4 &&
-           ctx->desc[p].g_kind != HJ_G_ELLIPSE && ctx->desc[p].principle != HJ_HUYGENS &&
+           (ctx->desc[p].g_kind == HJ_G_QUAD_SHIFT || ctx->desc[p].g_kind == HJ_G_DIAG_QUAD) &&
+           ctx->desc[p].principle != HJ_HUYGENS &&
            ctx->popts[p].coarse_div <= 1;
 }
 

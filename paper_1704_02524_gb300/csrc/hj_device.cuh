@@ -870,10 +870,43 @@ __device__ __forceinline__ void vjp(const Grp &g, const TP<T, C> &tp, T eps, con
 //   Lax  term g(gamma0), seed (grad g(gamma0), 0)
 //   Hopf term g*(p0) - <x, v>, seed (0, grad g*(p0))
 // ---------------------------------------------------------------------------
+// Rosenbrock data (Sec. 6, Example 2; d = 2, Lax only):
+// g = 4e-4 (-100 + (1 - x_1)^2 + 100 (1 + x_2 - x_1^2)^2).  Returns g; gr gets
+// grad g on each lane's components (0 past the first two).
+template <typename T, int C>
+__device__ __forceinline__ T rosenbrock(const Grp &g, const T *gam, T *gr)
+{
+    T x1 = 0, x2 = 0;
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        const int i = g.lane + k * g.tpp;
+        if (i == 0) x1 = gam[k];
+        if (i == 1) x2 = gam[k];
+    }
+    gsum2(g, x1, x2);
+    const T a = (T)1 - x1, b = (T)1 + x2 - x1 * x1, s = (T)4e-4;
+    const T d1 = s * ((T)-2 * a - (T)400 * b * x1), d2 = s * (T)200 * b;
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        const int i = g.lane + k * g.tpp;
+        gr[k] = (i == 0) ? d1 : (i == 1) ? d2 : (T)0;
+    }
+    return s * ((T)-100 + a * a + (T)100 * b * b);
+}
+
 template <typename T, int C, int PR>
 __device__ __forceinline__ T terminal(const Grp &g, const ProbDev<T> &P, const T *x, const T *v, const T *gam,
                                       const T *p, T *sg, T *sp)
 {
+    if (PR == HJ_LAX && P.g_kind == HJ_G_ROSENBROCK) {
+        T gr[C];
+        const T val = rosenbrock<T, C>(g, gam, gr);
+        if (sg) {
+#pragma unroll
+            for (int k = 0; k < C; ++k) { sg[k] = gr[k]; sp[k] = 0; }
+        }
+        return val;
+    }
     T acc = 0;
 #pragma unroll
     for (int k = 0; k < C; ++k) {
@@ -907,12 +940,15 @@ template <typename T, int C, int PR>
 __device__ __forceinline__ T cert_residual(const Grp &g, const ProbDev<T> &P, const T *gam, const T *p)
 {
     T num = 0, den = 0;
+    T rg[C];
+    if (PR == HJ_LAX && P.g_kind == HJ_G_ROSENBROCK) rosenbrock<T, C>(g, gam, rg);
 #pragma unroll
     for (int k = 0; k < C; ++k) {
         const int i = g.lane + k * g.tpp;
         T diff, base;
         if (PR == HJ_LAX) {
             T gr = (P.g_kind == HJ_G_QUAD_SHIFT) ? gam[k] - __ldg(P.ga + i) : gam[k] * __ldg(P.gis2 + i);
+            if (P.g_kind == HJ_G_ROSENBROCK) gr = rg[k];
             diff = p[k] - gr;
             base = p[k];
         } else {

@@ -26,7 +26,7 @@ import numpy as np
 (FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD, FAM_BUMP_NORM, FAM_SPLIT_NORM, FAM_HARMONIC,
  FAM_EVANS) = range(8)
 LAX, HOPF, HUYGENS = 0, 1, 2
-G_QUAD_SHIFT, G_DIAG_QUAD, G_ELLIPSE = 0, 1, 2
+G_QUAD_SHIFT, G_DIAG_QUAD, G_ELLIPSE, G_ROSENBROCK = 0, 1, 2, 3
 
 HARNESS_SEED = 0x170402524
 
@@ -87,7 +87,8 @@ class ProblemSpec:
             parts.append(np.array([self.hsign]))
         if self.family == FAM_EVANS:
             parts += [self.xc, np.array([self.kappa, self.mu, self.alpha_a, self.beta, self.gamma0])]
-        parts.append(self.a if self.g_kind == G_QUAD_SHIFT else self.sigma)
+        if self.g_kind != G_ROSENBROCK:  # the Rosenbrock data has no parameters
+            parts.append(self.a if self.g_kind == G_QUAD_SHIFT else self.sigma)
         return np.concatenate([np.asarray(p, dtype=np.float64).reshape(-1) for p in parts])
 
     @property
@@ -378,17 +379,25 @@ def _grid(n_side: int, d: int) -> np.ndarray:
 
 
 def harmonic_ex2(n_side: int = 128, d: int = 2, sign: float = -1.0, t: float = 0.5, ds: float = 0.02,
-                 n_guesses: int = 5, precision: str = "fp32") -> Workload:
+                 n_guesses: int = 5, precision: str = "fp32", rosenbrock: bool = False) -> Workload:
     """Sec. 6 Example 2: H = sign (|p|^2 + |x|^2)/2 with the ellipse data, the
     Hopf functional for both signs, on the n_side x n_side grid over
     [-3,3]^2 x {0}^(d-2) (t = 0.5 at d = 2; the paper's d = 7 run uses
-    t = 0.2), in the paper's numerics with ds = 0.02, sigma = 1e-3, L = 3."""
+    t = 0.2), in the paper's numerics with ds = 0.02, sigma = 1e-3, L = 3.
+    rosenbrock: the non-convex Rosenbrock data instead, with H+ and the Lax
+    functional (d = 2), as in the paper's last run of this example."""
     X = _grid(n_side, d)
-    P = ProblemSpec(d=d, family=FAM_HARMONIC, principle=HOPF, g_kind=G_ELLIPSE, sigma=ellipse_sigma(d), hsign=sign,
-                    n_guesses=n_guesses)
+    if rosenbrock:
+        P = ProblemSpec(d=2, family=FAM_HARMONIC, principle=LAX, g_kind=G_ROSENBROCK, hsign=1.0,
+                        n_guesses=n_guesses)
+        sign = 1.0
+    else:
+        P = ProblemSpec(d=d, family=FAM_HARMONIC, principle=HOPF, g_kind=G_ELLIPSE, sigma=ellipse_sigma(d),
+                        hsign=sign, n_guesses=n_guesses)
     nq = X.shape[0]
     N = int(round(t / ds))
-    return Workload(f"harmonic_d{d}_{'plus' if sign > 0 else 'minus'}_hopf_paper", [P], X, np.full(nq, t),
+    pname = "lax_rosenbrock" if rosenbrock else "hopf"
+    return Workload(f"harmonic_d{d}_{'plus' if sign > 0 else 'minus'}_{pname}_paper", [P], X, np.full(nq, t),
                     np.full(nq, N, np.int32), np.zeros(nq, np.int32),
                     paper_solver(step=1.0 / 3.0, n_guesses=n_guesses, max_trials=n_guesses), precision)
 

@@ -65,6 +65,10 @@ def test_create_rejects_bad_arguments_without_a_gpu(lib):
     with pytest.raises(hj.HJError) as e:
         hj.hj_create([W.ProblemSpec(**{**spec.__dict__, "principle": W.HUYGENS})], hj.opts_from_dict(wl.solver), 0)
     assert e.value.status == hj.HJ_EINVAL and "Huygens" in str(e.value)
+    ros = W.harmonic_ex2(n_side=2, rosenbrock=True).problems[0]
+    with pytest.raises(hj.HJError) as e:
+        hj.hj_create([W.ProblemSpec(**{**ros.__dict__, "principle": W.HOPF})], hj.opts_from_dict(wl.solver), 0)
+    assert e.value.status == hj.HJ_EINVAL and "Rosenbrock" in str(e.value)
     split = W.split_ex5(n_side=2).problems[0]
     for val in (-1, 3, 0.5):
         with pytest.raises(hj.HJError) as e:

@@ -239,7 +239,7 @@ def test_example5_split_norm_hopf_solve_matches_oracle(hj, prec, descent):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-@pytest.mark.parametrize("example", ["ex2_minus", "ex2_plus", "ex4"])
+@pytest.mark.parametrize("example", ["ex2_minus", "ex2_plus", "ex2_rosenbrock", "ex4"])
 def test_examples_2_and_4_solve_matches_oracle(hj, prec, example):
     # Sec. 6 Examples 2 (harmonic oscillator, both signs, Hopf) and 4
     # (Evans-type non-convex, Hopf) in the paper's numerics on 64 points
@@ -247,6 +247,8 @@ def test_examples_2_and_4_solve_matches_oracle(hj, prec, example):
     # two of the five oracle starts reach the oracle's phi, 90% within 1e-4
     if example == "ex4":
         wl = W.evans_ex4(n_side=128, precision=prec)
+    elif example == "ex2_rosenbrock":
+        wl = W.harmonic_ex2(n_side=128, precision=prec, rosenbrock=True)
     else:
         wl = W.harmonic_ex2(n_side=128, precision=prec, sign=-1.0 if example == "ex2_minus" else 1.0)
     w = wl.take(np.arange(0, wl.nq, wl.nq // 64)[:64])
@@ -257,10 +259,34 @@ def test_examples_2_and_4_solve_matches_oracle(hj, prec, example):
         assert np.all(err <= 1e-4), (err.max(), int(np.argmax(err)))
         assert np.array_equal(st & 1, ref["status"] & 1)
     else:
-        keep = np.sum(np.abs(ref["slot_F"] - (-rphi[:, None])) <= 1e-6 * (1 + np.abs(rphi[:, None])), 1) >= 2
+        sgn = -1.0 if w.problems[0].principle == W.HOPF else 1.0  # slot values are G (Hopf) or F
+        keep = np.sum(np.abs(ref["slot_F"] - sgn * rphi[:, None]) <= 1e-6 * (1 + np.abs(rphi[:, None])), 1) >= 2
         assert keep.mean() > 0.75
         err = rel_err(phi, rphi)[keep]
         assert np.mean(err <= 1e-4) >= 0.9, (np.mean(err <= 1e-4), err.max())
+
+
+def test_rosenbrock_data_rows_match_oracle(hj):
+    # the non-convex data's value, gradient and certificate through the
+    # harmonic family's Lax kernels (fp32 and fp64 rows)
+    spec = W.harmonic_ex2(n_side=2, rosenbrock=True).problems[0]
+    P = oracle_problem(spec)
+    for prec, dt, tolF, tolG in (("fp32", torch.float32, 2e-5, 5e-4), ("fp64", torch.float64, 1e-11, 1e-9)):
+        solver = W.solver_constants(quad="euler_rect", cert_tol=0.3)
+        ctx = hj.hj_create([spec], hj.opts_from_dict(solver, hj.HJ_PREC_FP32 if prec == "fp32" else hj.HJ_PREC_FP64,
+                                                     25), 0)
+        x, v, t, N = _rows(67, 2, 400, prec)
+        args = (_t(x, dt), _t(t, dt), _t(v, dt), _t(N, torch.int32))
+        F = hj.hj_eval_functional(ctx, *args).cpu().numpy()
+        Fg, G = (a.cpu().numpy() for a in hj.hj_grad(ctx, *args))
+        Fc, R, Pa = (a.cpu().numpy() for a in hj.hj_certify(ctx, *args))
+        for i in range(67):
+            Fo, Go = O.gradient(P, x[i], t[i], int(N[i]), v[i], quad=QUAD_CODES["euler_rect"])
+            assert rel_err(F[i], Fo) <= tolF and rel_err(Fg[i], Fo) <= tolF, (prec, i)
+            assert np.abs(G[i] - Go).max() <= tolG * (1 + np.abs(Go).max()), (prec, i)
+            Fco, Ro, ok = O.certify(P, x[i], t[i], int(N[i]), v[i], 0.3, quad=QUAD_CODES["euler_rect"])
+            assert abs(R[i] - Ro) < 1e-11 and bool(Pa[i]) == ok, (prec, i)
+        ctx.close()
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])

@@ -538,6 +538,47 @@ def test_harmonic_solve_matches_riccati(hsign, principle, t):
     assert np.abs(phi - expect).max() < 1e-8, (phi, expect)
 
 
+def _rosenbrock(y):
+    return 4e-4 * (-100 + (1 - y[..., 0]) ** 2 + 100 * (1 + y[..., 1] - y[..., 0] ** 2) ** 2)
+
+
+def test_harmonic_with_rosenbrock_data_matches_exact_rotation_and_differences():
+    # Example 2's non-convex initial data under H+ (Lax): F = g(gamma(t)) + Q
+    # on the exact rotation, and the adjoint against central differences
+    rng = np.random.default_rng(38)
+    P = O.Problem(d=2, family=O.FAM_HARMONIC, principle=O.LAX, g_kind=O.G_ROSENBROCK, hsign=1.0)
+    for _ in range(4):
+        x, v, t = rng.uniform(-2, 2, 2), rng.uniform(-2, 2, 2), rng.uniform(0.1, 1)
+        gam = x * np.cos(t) - v * np.sin(t)
+        Q = 0.5 * ((v @ v - x @ x) * np.sin(2 * t) / 2 + (x @ v) * (1 - np.cos(2 * t)))
+        assert abs(O.functional(P, x, t, 200, v) - (_rosenbrock(gam) + Q)) < 1e-9
+        F, g = O.gradient(P, x, t, 25, v)
+        gfd = O.gradient_fd(P, x, t, 25, v, h=1e-5)
+        assert np.abs(g - gfd).max() <= 1e-7 * (1 + np.abs(gfd).max())
+
+
+def test_harmonic_rosenbrock_lax_matches_lax_friedrichs():
+    # convex H+ = (|p|^2 + |x|^2)/2 with the non-convex Rosenbrock data
+    # (Example 2, t = 0.5, d = 2) against the paper's comparison scheme
+    P = O.Problem(d=2, family=O.FAM_HARMONIC, principle=O.LAX, g_kind=O.G_ROSENBROCK, hsign=1.0)
+    t = 0.5
+    opts = O.Opts(descent=O.DESC_GD, grad=O.GRAD_ADJOINT, step=0.05, max_iters=3000, eps=1e-12, adapt=1,
+                  grow=1.2, shrink=0.5, step_max=1.0, n_guesses=8, max_trials=8, max_rounds=0, seed=3,
+                  cert_tol=1e-3)
+    xq = np.array([[-0.93, -0.35], [1.2, -0.5], [-1.5, 0.8], [0.4, 1.2], [0.1, 0.0], [1.0, 0.5]])
+    phi = O.solve(P, opts, xq, t, 100)["phi"]
+    H = lambda X, Pg: 0.5 * (Pg[0] ** 2 + Pg[1] ** 2 + X[0] ** 2 + X[1] ** 2)
+    from scipy.interpolate import RegularGridInterpolator
+    lf = {}
+    for dx in (0.04, 0.02):
+        # |dH/dp| = |p| stays below ~3 for this data on [-3,3]^2 over t = 0.5
+        xs, sol = pins.lax_friedrichs(H, 3.0, lambda X: _rosenbrock(np.stack(X, -1)), -3.0, 3.0, dx, t, 2)
+        lf[dx] = RegularGridInterpolator((xs, xs), sol)(xq)
+    e = {dx: np.abs(lf[dx] - phi) for dx in lf}
+    assert np.all(e[0.04] / e[0.02] > 1.5) and np.all(e[0.04] / e[0.02] < 2.5), e
+    assert np.all(np.abs(2 * lf[0.02] - lf[0.04] - phi) < 0.25 * e[0.02])
+
+
 def _p_evans(principle, kappa=3.0, d=2, s_eps=0.0):
     xc = np.zeros(d)
     xc[:2] = 1.0
