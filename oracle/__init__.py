@@ -40,7 +40,7 @@ _lock = threading.Lock()
 _lib = None
 
 (FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD, FAM_BUMP_NORM, FAM_SPLIT_NORM, FAM_HARMONIC,
- FAM_EVANS) = range(8)
+ FAM_EVANS, FAM_LINEAR_GAME) = range(9)
 LAX, HOPF, HUYGENS = 0, 1, 2  # HUYGENS: the Lax principle through F^2 (eq. num_min)
 G_QUAD_SHIFT, G_DIAG_QUAD, G_ELLIPSE, G_ROSENBROCK = 0, 1, 2, 3
 QUAD_RK4, QUAD_RECT = 0, 1
@@ -70,7 +70,8 @@ class _Problem(C.Structure):
                 ("ga", C.POINTER(C.c_double)), ("gs", C.POINTER(C.c_double)),
                 ("xc", C.POINTER(C.c_double)), ("kappa", C.c_double), ("mu", C.c_double), ("hsign", C.c_double),
                 ("xcb", C.POINTER(C.c_double)), ("ksplit", C.c_int), ("alpha_a", C.c_double),
-                ("alpha_b", C.c_double), ("beta", C.c_double), ("gamma0", C.c_double)]
+                ("alpha_b", C.c_double), ("beta", C.c_double), ("gamma0", C.c_double),
+                ("r_c", C.c_double), ("r_d", C.c_double), ("omega", C.c_double)]
 
 
 class _Opts(C.Structure):
@@ -143,6 +144,9 @@ class Problem:
     alpha_b: float = 0.0
     beta: float = 0.0                 # Evans-type family: H = -c(x) p_1 + beta|p_2| - |p| - gamma0,
     gamma0: float = 0.0               #   c = alpha_a (1 + kappa exp(-mu|x - xc|^2)); harmonic: H = hsign(|p|^2+|x|^2)/2
+    r_c: float = 0.0                  # linear game: H(x,p,s) = -<diag(w) x, p> + a(s)|p|,
+    r_d: float = 0.0                  #   a(s) = r_c - r_d (1 + beta sin(omega s))
+    omega: float = 0.0
     _c: Optional[_Problem] = field(default=None, repr=False)
 
     def c(self) -> _Problem:
@@ -156,7 +160,8 @@ class Problem:
                                _dp(self.w), _dp(self.A), _dp(self.B), _dp(self.a), _dp(self.sigma),
                                _dp(self.xc), float(self.kappa), float(self.mu), float(self.hsign),
                                _dp(self.xcb), int(self.ksplit), float(self.alpha_a), float(self.alpha_b),
-                               float(self.beta), float(self.gamma0))
+                               float(self.beta), float(self.gamma0), float(self.r_c), float(self.r_d),
+                               float(self.omega))
         return self._c
 
 

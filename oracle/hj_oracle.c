@@ -17,7 +17,10 @@
  * split norm H = c_A(x)|p_A| + c_B(x)|p_B| over two coordinate blocks, each
  * speed a signed multiple of such a bump (Sec. 6, Example 5); the harmonic
  * oscillator H = +-(|p|^2 + |x|^2)/2 (Sec. 6, Example 2); and the non-convex
- * H = -c(x) p_1 + beta|p_2| - |p| - gamma0 with c a bump (Sec. 6, Example 4).
+ * H = -c(x) p_1 + beta|p_2| - |p| - gamma0 with c a bump (Sec. 6, Example 4);
+ * and the time-dependent linear differential game of Sec. 3.4, Example 3,
+ * H(x,p,s) = -<Mx,p> + a(s)|p| with M diagonal and the support functions of
+ * balls, a(s) = r_C - r_D (1 + beta sin(omega s)).
  * Initial data: |x - a|^2/2, sum x_i^2/(2 s_i^2), and the ellipse data
  * (<x, Ax> - 1)/2, A diagonal, of Sec. 6.
  *
@@ -58,7 +61,7 @@
 /* ------------------------------------------------------------------------ */
 
 enum { FAM_QUAD_ISO = 0, FAM_SPEED_QUAD = 1, FAM_SMOOTH_NONCONVEX = 2, FAM_LINEAR_QUAD = 3, FAM_BUMP_NORM = 4,
-       FAM_SPLIT_NORM = 5, FAM_HARMONIC = 6, FAM_EVANS = 7 };
+       FAM_SPLIT_NORM = 5, FAM_HARMONIC = 6, FAM_EVANS = 7, FAM_LINEAR_GAME = 8 };
 /* HUYGENS: the Lax principle through F^2 (Sec. 4.1), the smallest g over the
  * endpoints gamma(x, v, r, 0), 0 <= r <= t, taken on the solver grid r = n dt
  * (eq. num_min) -- for Hamiltonians of degree one in p, with no running cost. */
@@ -109,6 +112,9 @@ typedef struct {
      * Evans-type family (Example 4): H = -c(x) p_1 + beta |p_2|_eps - |p|_eps - gamma0
      * with c = alpha_a (1 + kappa exp(-mu |x - xc|^2)) and |q|_eps = sqrt(q^2 + s_eps) */
     double beta, gamma0;
+    /* linear game (Sec. 3.4, Example 3): H(x,p,s) = -<Mx,p> + a(s)|p|_eps with
+     * M = diag(m), a(s) = r_C - r_D (1 + beta sin(omega s)); m in w */
+    double r_c, r_d, omega;
 } orc_problem;
 
 typedef struct {
@@ -259,8 +265,14 @@ static void split_eval(const orc_problem *P, const double *gam, const double *p,
     }
 }
 
-/* Hamiltonian value H(gamma, p). */
-static double ham(const orc_problem *P, const double *gam, const double *p)
+/* Speed of the linear game at PDE time s. */
+static double game_speed(const orc_problem *P, double s)
+{
+    return P->r_c - P->r_d * (1.0 + P->beta * sin(P->omega * s));
+}
+
+/* Hamiltonian value H(gamma, p) at PDE time s (only the linear game uses s). */
+static double ham(const orc_problem *P, const double *gam, const double *p, double s)
 {
     int d = P->d;
     double u, c, c1, c2;
@@ -302,6 +314,11 @@ static double ham(const orc_problem *P, const double *gam, const double *p)
     }
     case FAM_HARMONIC:
         return P->hsign * 0.5 * (dot(p, p, d) + dot(gam, gam, d));
+    case FAM_LINEAR_GAME: {
+        double mxp = 0.0;
+        for (int i = 0; i < d; ++i) mxp += P->w[i] * gam[i] * p[i];
+        return -mxp + game_speed(P, s) * sqrt(dot(p, p, d) + P->s_eps);
+    }
     case FAM_EVANS: {
         double y[ORC_DMAX], c, k;
         bump(P, gam, y, &c, &k);
@@ -313,7 +330,7 @@ static double ham(const orc_problem *P, const double *gam, const double *p)
 }
 
 /* dH/dp and dH/dx at (gamma, p). */
-static void ham_grads(const orc_problem *P, const double *gam, const double *p, double *Hp, double *Hx)
+static void ham_grads(const orc_problem *P, const double *gam, const double *p, double s, double *Hp, double *Hx)
 {
     int d = P->d;
     double u, c, c1, c2;
@@ -376,6 +393,15 @@ static void ham_grads(const orc_problem *P, const double *gam, const double *p, 
             Hx[i] = P->hsign * gam[i];
         }
         return;
+    case FAM_LINEAR_GAME: {
+        /* H_p = -M gamma + a(s) p/n,  H_x = -M p */
+        double a = game_speed(P, s), n = sqrt(dot(p, p, d) + P->s_eps);
+        for (int i = 0; i < d; ++i) {
+            Hp[i] = -P->w[i] * gam[i] + a * p[i] / n;
+            Hx[i] = -P->w[i] * p[i];
+        }
+        return;
+    }
     case FAM_EVANS: {
         /* H_p = -c e_1 + beta p_2/s_2 e_2 - p/n,  H_x = -p_1 grad c = -p_1 alpha k y */
         double y[ORC_DMAX], c, k;
@@ -407,36 +433,36 @@ static void ham_grads(const orc_problem *P, const double *gam, const double *p, 
 
 /* Running cost inside the integral: Lax <p, dH/dp> - H (eq. lax_formula),
  * Hopf H - <dH/dx, gamma> (eq. hopf_formula). */
-static double running_cost(const orc_problem *P, const double *gam, const double *p)
+static double running_cost(const orc_problem *P, const double *gam, const double *p, double s)
 {
     int d = P->d;
     double Hp[ORC_DMAX], Hx[ORC_DMAX];
-    ham_grads(P, gam, p, Hp, Hx);
-    double H = ham(P, gam, p);
+    ham_grads(P, gam, p, s, Hp, Hx);
+    double H = ham(P, gam, p, s);
     return (P->principle == LAX) ? dot(p, Hp, d) - H : H - dot(Hx, gam, d);
 }
 
 /* Right-hand side in reversed time tau = t - s: the state z = (gamma, p)
  * moves by dz/dtau = (-dH/dp, +dH/dx) and the quadrature state by the
  * running cost.  out has 2d + 1 entries. */
-static void field(const orc_problem *P, const double *z, double *out)
+static void field(const orc_problem *P, const double *z, double s, double *out)
 {
     int d = P->d;
     const double *gam = z, *p = z + d;
     double Hp[ORC_DMAX], Hx[ORC_DMAX];
-    ham_grads(P, gam, p, Hp, Hx);
+    ham_grads(P, gam, p, s, Hp, Hx);
     for (int i = 0; i < d; ++i) {
         out[i] = -Hp[i];
         out[d + i] = Hx[i];
     }
-    out[2 * d] = running_cost(P, gam, p);
+    out[2 * d] = running_cost(P, gam, p, s);
 }
 
 /* Vector-Jacobian product of `field`: given weights a (2d entries, on the
  * state rows) and b (on the quadrature row), return
  *     r = a^T d(field_z)/dz + b d(field_Q)/dz     (2d entries).
  * The Jacobians are written out per family from the formulas above. */
-static void field_vjp(const orc_problem *P, const double *z, const double *a, double b, double *r)
+static void field_vjp(const orc_problem *P, const double *z, double s, const double *a, double b, double *r)
 {
     int d = P->d;
     const double *gam = z, *p = z + d;
@@ -538,6 +564,19 @@ static void field_vjp(const orc_problem *P, const double *z, const double *a, do
             }
             rg[i] = g_i;
             rp[i] = p_i;
+        }
+        return;
+    }
+    case FAM_LINEAR_GAME: {
+        /* field = (M gamma - a p/n, -M p); Lax L = a (|p|^2/n - n) = -a eps/n,
+         * Hopf L = H - <H_x, gamma> = a n (M diagonal) */
+        const double a_s = game_speed(P, s), eps = P->s_eps;
+        const double n = sqrt(dot(p, p, d) + eps), Agp = dot(ag, p, d);
+        for (int i = 0; i < d; ++i) {
+            rg[i] = ag[i] * P->w[i];
+            rp[i] = -a_s * (ag[i] / n - Agp * p[i] / (n * n * n)) - ap[i] * P->w[i];
+            if (P->principle == LAX) rp[i] += b * a_s * eps * p[i] / (n * n * n);
+            else rp[i] += b * a_s * p[i] / n;
         }
         return;
     }
@@ -693,26 +732,28 @@ static double integrate(const orc_problem *P, int quad, const double *x, double 
          * augmented state adds h L(z_n), the rectangle rule h L(z_{n+1}) */
         for (int n = 0; n < N; ++n) {
             if (stages) memcpy(stages + (size_t)(4 * n) * n2, z, sizeof(double) * n2);
-            field(P, z, k1);
+            field(P, z, t - n * h, k1);
             for (int i = 0; i < n2; ++i) z[i] += h * k1[i];
             if (quad == QUAD_RK4) Q += h * k1[n2];
-            else Q += h * running_cost(P, z, z + d);
+            else Q += h * running_cost(P, z, z + d, t - (n + 1) * h);
             if (traj) memcpy(traj + (size_t)(n + 1) * n2, z, sizeof(double) * n2);
         }
         return Q;
     }
     for (int n = 0; n < N; ++n) {
         if (stages) memcpy(stages + (size_t)(4 * n + 0) * n2, z, sizeof(double) * n2);
-        field(P, z, k1);
+        /* stage times in the PDE's own time s = t - tau */
+        const double s0 = t - n * h, sm = t - (n + 0.5) * h, s1 = t - (n + 1) * h;
+        field(P, z, s0, k1);
         for (int i = 0; i < n2; ++i) zs[i] = z[i] + 0.5 * h * k1[i];
         if (stages) memcpy(stages + (size_t)(4 * n + 1) * n2, zs, sizeof(double) * n2);
-        field(P, zs, k2);
+        field(P, zs, sm, k2);
         for (int i = 0; i < n2; ++i) zs[i] = z[i] + 0.5 * h * k2[i];
         if (stages) memcpy(stages + (size_t)(4 * n + 2) * n2, zs, sizeof(double) * n2);
-        field(P, zs, k3);
+        field(P, zs, sm, k3);
         for (int i = 0; i < n2; ++i) zs[i] = z[i] + h * k3[i];
         if (stages) memcpy(stages + (size_t)(4 * n + 3) * n2, zs, sizeof(double) * n2);
-        field(P, zs, k4);
+        field(P, zs, s1, k4);
         for (int i = 0; i < n2; ++i) z[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
         if (quad == QUAD_RK4) {
             /* RK4 on the augmented quadrature state */
@@ -721,7 +762,7 @@ static double integrate(const orc_problem *P, int quad, const double *x, double 
             /* eq. num_int: rectangle rule on the solver's mesh.  The node
              * s_i = i ds (i = 0..N-1) is the state after N - i steps of
              * reversed time, i.e. the states z_1..z_N reached here. */
-            Q += h * running_cost(P, z, z + d);
+            Q += h * running_cost(P, z, z + d, s1);
         }
         if (traj) memcpy(traj + (size_t)(n + 1) * n2, z, sizeof(double) * n2);
     }
@@ -817,11 +858,11 @@ double orc_gradient(const orc_problem *P, int quad, const double *x, double t, i
             if (quad == QUAD_RECT) {
                 double gl[2 * ORC_DMAX], zero[2 * ORC_DMAX];
                 for (int i = 0; i < n2; ++i) zero[i] = 0.0;
-                field_vjp(P, traj + (size_t)(n + 1) * n2, zero, 1.0, gl);
+                field_vjp(P, traj + (size_t)(n + 1) * n2, t - (n + 1) * h, zero, 1.0, gl);
                 for (int i = 0; i < n2; ++i) lam[i] += h * gl[i];
             }
             for (int i = 0; i < n2; ++i) w[i] = h * lam[i];
-            field_vjp(P, Z1, w, beta_q * h, a1);
+            field_vjp(P, Z1, t - n * h, w, beta_q * h, a1);
             for (int i = 0; i < n2; ++i) lam[i] += a1[i];
             continue;
         }
@@ -829,18 +870,20 @@ double orc_gradient(const orc_problem *P, int quad, const double *x, double t, i
             /* rectangle node at the state after step n, weight h: add h grad L */
             double gl[2 * ORC_DMAX], zero[2 * ORC_DMAX];
             for (int i = 0; i < n2; ++i) zero[i] = 0.0;
-            field_vjp(P, traj + (size_t)(n + 1) * n2, zero, 1.0, gl);
+            field_vjp(P, traj + (size_t)(n + 1) * n2, t - (n + 1) * h, zero, 1.0, gl);
             for (int i = 0; i < n2; ++i) lam[i] += h * gl[i];
         }
-        /* z_{n+1} = z_n + h/6 (k1 + 2k2 + 2k3 + k4), Q likewise; reverse: */
+        /* z_{n+1} = z_n + h/6 (k1 + 2k2 + 2k3 + k4), Q likewise; reverse
+         * (each stage at its own time, as in the forward step): */
+        const double s0 = t - n * h, sm = t - (n + 0.5) * h, s1 = t - (n + 1) * h;
         for (int i = 0; i < n2; ++i) w[i] = h / 6.0 * lam[i];
-        field_vjp(P, Z4, w, beta_q * h / 6.0, a4);
+        field_vjp(P, Z4, s1, w, beta_q * h / 6.0, a4);
         for (int i = 0; i < n2; ++i) w[i] = h / 3.0 * lam[i] + h * a4[i];
-        field_vjp(P, Z3, w, beta_q * h / 3.0, a3);
+        field_vjp(P, Z3, sm, w, beta_q * h / 3.0, a3);
         for (int i = 0; i < n2; ++i) w[i] = h / 3.0 * lam[i] + 0.5 * h * a3[i];
-        field_vjp(P, Z2, w, beta_q * h / 3.0, a2);
+        field_vjp(P, Z2, sm, w, beta_q * h / 3.0, a2);
         for (int i = 0; i < n2; ++i) w[i] = h / 6.0 * lam[i] + 0.5 * h * a2[i];
-        field_vjp(P, Z1, w, beta_q * h / 6.0, a1);
+        field_vjp(P, Z1, s0, w, beta_q * h / 6.0, a1);
         for (int i = 0; i < n2; ++i) lam[i] += a1[i] + a2[i] + a3[i] + a4[i];
     }
     for (int i = 0; i < d; ++i) grad[i] = lam[d + i] - (P->principle == HOPF ? x[i] : 0.0);

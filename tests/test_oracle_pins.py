@@ -612,6 +612,62 @@ def test_evans_state_independent_hopf_solve_matches_brute_force():
         assert abs(phi[q] + best) < 1e-4, (q, phi[q], -best)
 
 
+def _p_game(principle, m, r_c=1.0, r_d=0.4, beta=0.5, omega=3.0, sig=ELL_SIG):
+    return O.Problem(d=len(m), family=O.FAM_LINEAR_GAME, principle=principle, g_kind=O.G_ELLIPSE, sigma=sig,
+                     w=np.asarray(m, float), r_c=r_c, r_d=r_d, beta=beta, omega=omega, s_eps=0.0)
+
+
+def _game_speed(s, r_c=1.0, r_d=0.4, beta=0.5, omega=3.0):
+    return r_c - r_d * (1 + beta * np.sin(omega * s))
+
+
+def test_linear_game_functionals_match_quadrature_of_the_exact_flow():
+    # H(x,p,s) = -<Mx,p> + a(s)|p| (Sec. 3.4, Example 3 with balls, M
+    # diagonal): in tau = t - s, p_i = v_i exp(-m_i tau) and
+    # gamma(tau) = e^{M tau} (x - int_0^tau e^{-M r} a(t - r) p(r)/|p(r)| dr);
+    # F^1 = g(gamma(t)) (the Lax cost of a degree-one H vanishes) and
+    # G = g*(p(t)) + int_0^t a(t - r)|p(r)| dr - <x, v>.  The speed is read at
+    # the PDE time t - tau: a(tau) instead would move G by 1.4e-3 to 5.9e-3 here.
+    m = np.array([0.7, -0.4])
+    t = 0.8
+    rng = np.random.default_rng(39)
+    Pl, Ph = _p_game(O.LAX, m), _p_game(O.HOPF, m)
+    for _ in range(3):
+        x, v = rng.uniform(-2, 2, 2), rng.uniform(-2, 2, 2)
+        p_of = lambda r: v * np.exp(-m * r)
+        dirn = lambda r: p_of(r) / np.linalg.norm(p_of(r))
+        drift = [scipy.integrate.quad(lambda r, i=i: np.exp(-m[i] * r) * _game_speed(t - r) * dirn(r)[i], 0, t,
+                                      epsabs=1e-14, epsrel=1e-14)[0] for i in range(2)]
+        gam = np.exp(m * t) * (x - np.array(drift))
+        assert abs(O.functional(Pl, x, t, 200, v) - _g_ellipse(gam)) < 1e-9
+        cost = scipy.integrate.quad(lambda r: _game_speed(t - r) * np.linalg.norm(p_of(r)), 0, t,
+                                    epsabs=1e-14, epsrel=1e-14)[0]
+        G = 0.5 * (np.sum(ELL_SIG ** 2 * p_of(t) ** 2) + 1) + cost - x @ v
+        assert abs(O.functional(Ph, x, t, 200, v) - G) < 1e-9
+
+
+def test_linear_game_hopf_solve_matches_generalized_hopf_formula():
+    # with a(s) > 0 the Hopf functional above is convex in v; its minimum,
+    # found by scipy on the quadrature form, is -phi (Sec. 3.4, Example 3)
+    m = np.array([0.7, -0.4])
+    t = 0.8
+    P = _p_game(O.HOPF, m)
+    xq = np.array([[-0.93, -0.35], [1.2, -0.5], [-1.5, 0.8], [0.4, 1.9]])
+    opts = O.Opts(descent=O.DESC_GD, grad=O.GRAD_ADJOINT, step=0.05, max_iters=4000, eps=1e-12, adapt=1,
+                  grow=1.2, shrink=0.5, step_max=1.0, n_guesses=2, max_trials=2, max_rounds=0, seed=3, cert_tol=1e-3)
+    phi = O.solve(P, opts, xq, t, 100)["phi"]
+    r_nodes, r_w = np.polynomial.legendre.leggauss(60)
+    r_nodes, r_w = 0.5 * t * (r_nodes + 1), 0.5 * t * r_w
+    def G(v, x):
+        pr = v[None, :] * np.exp(-np.outer(r_nodes, m))
+        return (0.5 * (np.sum(ELL_SIG ** 2 * (v * np.exp(-m * t)) ** 2) + 1)
+                + np.sum(r_w * _game_speed(t - r_nodes) * np.linalg.norm(pr, axis=1)) - x @ v)
+    for q, x in enumerate(xq):
+        r = scipy.optimize.minimize(G, np.ones(2), args=(x,), method="Nelder-Mead",
+                                    options=dict(xatol=1e-11, fatol=1e-14, maxiter=20000))
+        assert abs(phi[q] + r.fun) < 1e-7, (q, phi[q], -r.fun)
+
+
 def _golden_tables():
     rows = []
     with open(os.path.join(os.path.dirname(__file__), "golden", "ex3_convergence_tables.txt")) as f:
@@ -666,7 +722,8 @@ def test_adjoint_gradient_closed_form_quad_iso():
     (O.FAM_BUMP_NORM, O.LAX, O.G_ELLIPSE), (O.FAM_BUMP_NORM, O.HOPF, O.G_ELLIPSE),
     (O.FAM_BUMP_NORM, O.HUYGENS, O.G_ELLIPSE), (O.FAM_SPLIT_NORM, O.LAX, O.G_ELLIPSE),
     (O.FAM_SPLIT_NORM, O.HOPF, O.G_ELLIPSE), (O.FAM_HARMONIC, O.LAX, O.G_ELLIPSE),
-    (O.FAM_HARMONIC, O.HOPF, O.G_ELLIPSE), (O.FAM_EVANS, O.LAX, O.G_ELLIPSE), (O.FAM_EVANS, O.HOPF, O.G_ELLIPSE)])
+    (O.FAM_HARMONIC, O.HOPF, O.G_ELLIPSE), (O.FAM_EVANS, O.LAX, O.G_ELLIPSE), (O.FAM_EVANS, O.HOPF, O.G_ELLIPSE),
+    (O.FAM_LINEAR_GAME, O.LAX, O.G_ELLIPSE), (O.FAM_LINEAR_GAME, O.HOPF, O.G_ELLIPSE)])
 @pytest.mark.parametrize("quad", [O.QUAD_RK4, O.QUAD_RECT, EULER, EULER_RECT])
 def test_adjoint_gradient_matches_central_differences(family, principle, g_kind, quad):
     rng = np.random.default_rng(7 + family + 3 * principle)
@@ -675,7 +732,8 @@ def test_adjoint_gradient_matches_central_differences(family, principle, g_kind,
                   a=rng.uniform(-1, 1, d), sigma=rng.uniform(0.5, 2, d), A=rng.normal(size=(d, d)) * 0.2,
                   B=rng.normal(size=(d, 4)) / math.sqrt(d), n_neg=2, s_eps=1e-2,
                   xc=rng.uniform(-0.5, 0.5, d), kappa=3.0, mu=1.5, hsign=1.0 if principle == O.LAX else -1.0,
-                  xcb=rng.uniform(-0.5, 0.5, d), ksplit=2, alpha_a=1.5, alpha_b=-1.2, beta=2.0, gamma0=1.0)
+                  xcb=rng.uniform(-0.5, 0.5, d), ksplit=2, alpha_a=1.5, alpha_b=-1.2, beta=2.0, gamma0=1.0,
+                  r_c=1.0, r_d=0.6, omega=3.0)
     for _ in range(3):
         x, v = rng.uniform(-1, 1, d), rng.uniform(-1, 1, d)
         F, g = O.gradient(P, x, 0.5, 16, v, quad=quad)
