@@ -59,6 +59,9 @@ WORKLOADS = {
     "harmonic_d2_minus_hopf_paper": (lambda nq: W.harmonic_ex2(n_side=max(1, int(round(nq ** 0.5)))), 16384,
                                      "points/s (Example 2 H = -(|p|^2+|x|^2)/2, d=2 grid, the paper's numerics)",
                                      "Algorithm 1, forward differences, forward Euler with the rectangle rule"),
+    "linear_game_d16_hopf": (lambda nq: W.linear_game(nq=nq), 65536,
+                             "queries/s (time-dependent linear game, d=16 Hopf, Sec. 3.4 Example 3)",
+                             "gradient descent, discrete-adjoint gradient with stage times, coarse-to-fine"),
     "evans_d2_hopf_paper": (lambda nq: W.evans_ex4(n_side=max(1, int(round(nq ** 0.5)))), 16384,
                             "points/s (Example 4 Evans-type H, d=2 grid, the paper's numerics)",
                             "Algorithm 1, forward differences, forward Euler with the rectangle rule"),

@@ -76,9 +76,13 @@ typedef enum {
                                     c_b = alpha_b (1 + kappa exp(-mu |x - xc_b|^2))
                                     (Sec. 6, Example 5; signs in the alphas)                */
     HJ_FAM_HARMONIC = 6,         /* H = sign (|p|^2 + |x|^2)/2 (Sec. 6, Example 2)          */
-    HJ_FAM_EVANS = 7             /* H = -c(x) p_1 + beta |p_2|_eps - |p|_eps - gamma0, d >= 2,
+    HJ_FAM_EVANS = 7,            /* H = -c(x) p_1 + beta |p_2|_eps - |p|_eps - gamma0, d >= 2,
                                     c = alpha (1 + kappa exp(-mu |x - xc|^2))
                                     (Sec. 6, Example 4)                                      */
+    HJ_FAM_LINEAR_GAME = 8       /* time dependent: H(x, p, s) = -<diag(m) x, p> + a(s) |p|_eps,
+                                    a(s) = r_C - r_D (1 + beta sin(omega s)), s the PDE time
+                                    (the linear differential game of Sec. 3.4, Example 3,
+                                    with ball-shaped control sets)                           */
 } hj_family;
 
 /* Which functional is minimised over v (Sec. 4.1):
@@ -205,6 +209,7 @@ typedef struct {
  *                              mu (>= 0), alpha_A, alpha_B
  *                  HARMONIC: sign (+1 or -1)
  *                  EVANS: xc[d], then kappa, mu (>= 0), alpha, beta, gamma0
+ *                  LINEAR_GAME: m[d] (the diagonal drift), then r_C, r_D, beta, omega
  *                  QUAD_ISO: nothing
  *   g block:       HJ_G_QUAD_SHIFT: a[d];  HJ_G_DIAG_QUAD, HJ_G_ELLIPSE: s[d] (all > 0);
  *                  HJ_G_ROSENBROCK: nothing
@@ -222,7 +227,7 @@ typedef struct {
     int m;             /* LINEAR_QUAD: columns of B                             */
     int n_neg;         /* SMOOTH_NONCONVEX: number of leading negative signs     */
     double s_eps;      /* SMOOTH_NONCONVEX: smoothing of |q|, > 0;
-                          BUMP_NORM, SPLIT_NORM, EVANS: smoothing of the norms,
+                          BUMP_NORM, SPLIT_NORM, EVANS, LINEAR_GAME: smoothing of the norms,
                           >= 0 (0: the plain norms)                                */
     int n_guesses;     /* random starts per query for hj_solve (0: the solver value) */
     const double *params;

@@ -33,6 +33,10 @@ void reg_f32_lq_lax(Registry &);
 void reg_f32_lq_hopf(Registry &);
 void reg_f64_lq_lax(Registry &);
 void reg_f64_lq_hopf(Registry &);
+void reg_f32_lg_lax(Registry &);
+void reg_f32_lg_hopf(Registry &);
+void reg_f64_lg_lax(Registry &);
+void reg_f64_lg_hopf(Registry &);
 void reg_f32_ho_lax(Registry &);
 void reg_f32_ho_hopf(Registry &);
 void reg_f64_ho_lax(Registry &);
@@ -66,6 +70,10 @@ Registry &registry()
         reg_f32_lq_hopf(*x);
         reg_f64_lq_lax(*x);
         reg_f64_lq_hopf(*x);
+        reg_f32_lg_lax(*x);
+        reg_f32_lg_hopf(*x);
+        reg_f64_lg_lax(*x);
+        reg_f64_lg_hopf(*x);
         reg_f32_ho_lax(*x);
         reg_f32_ho_hopf(*x);
         reg_f64_ho_lax(*x);
@@ -127,6 +135,7 @@ FlopModel flop_model(int fam, int pr, int d, int quad)
         vjp = (pr == HJ_HOPF ? 16.0 : 14.0) * d + 50;
         break;
     case HJ_FAM_HARMONIC: fld = 6.0 * d + 3; vjp = 4.0 * d + 2; break;
+    case HJ_FAM_LINEAR_GAME: fld = 7.0 * d + 12; vjp = 9.0 * d + 10; break;
     case HJ_FAM_EVANS:
         fld = (pr == HJ_HOPF ? 16.0 : 14.0) * d + 30;
         vjp = (pr == HJ_HOPF ? 18.0 : 16.0) * d + 30;
@@ -160,7 +169,15 @@ void fill_prob(const hj_problem_desc &D, const std::vector<double> &par, int ld,
         for (int i = 0; i < d; ++i) w[i] = (T)par[i];
         off = d;
     }
-    P.kappa = P.mu = P.alpha_a = P.alpha_b = P.beta = P.gamma0 = (T)0;
+    P.kappa = P.mu = P.alpha_a = P.alpha_b = P.beta = P.gamma0 = P.r_c = P.r_d = P.omega = (T)0;
+    if (D.family == HJ_FAM_LINEAR_GAME) {
+        for (int i = 0; i < d; ++i) w[i] = (T)par[i];  // the diagonal drift m
+        P.r_c = (T)par[d];
+        P.r_d = (T)par[d + 1];
+        P.beta = (T)par[d + 2];
+        P.omega = (T)par[d + 3];
+        off = d + 4;
+    }
     P.ksplit = d;
     if (D.family == HJ_FAM_HARMONIC) {
         P.alpha_a = (T)par[0];  // the sign
@@ -342,6 +359,7 @@ size_t expected_params(const hj_problem_desc &D)
     if (D.family == HJ_FAM_SPLIT_NORM) n += 2 * (size_t)D.d + 5;
     if (D.family == HJ_FAM_HARMONIC) n += 1;
     if (D.family == HJ_FAM_EVANS) n += D.d + 5;
+    if (D.family == HJ_FAM_LINEAR_GAME) n += D.d + 4;
     if (D.g_kind != HJ_G_ROSENBROCK) n += D.d;
     return n;
 }
@@ -349,7 +367,7 @@ size_t expected_params(const hj_problem_desc &D)
 hj_status validate_problem(hj_ctx *ctx, const hj_problem_desc &D, int idx)
 {
     if (D.d < 1 || D.d > DPAD) return fail(ctx, HJ_EINVAL, "problem %d: d=%d outside [1, %d]", idx, D.d, DPAD);
-    if (D.family < HJ_FAM_QUAD_ISO || D.family > HJ_FAM_EVANS)
+    if (D.family < HJ_FAM_QUAD_ISO || D.family > HJ_FAM_LINEAR_GAME)
         return fail(ctx, HJ_EINVAL, "problem %d: unknown family %d", idx, (int)D.family);
     if (D.principle != HJ_LAX && D.principle != HJ_HOPF && D.principle != HJ_HUYGENS)
         return fail(ctx, HJ_EINVAL, "problem %d: unknown principle %d", idx, (int)D.principle);
@@ -380,7 +398,8 @@ hj_status validate_problem(hj_ctx *ctx, const hj_problem_desc &D, int idx)
         if (D.d < 2) return fail(ctx, HJ_EINVAL, "problem %d: the Evans-type family needs d >= 2", idx);
         if (!(D.params[D.d + 1] >= 0)) return fail(ctx, HJ_EINVAL, "problem %d: Evans mu must be >= 0", idx);
     }
-    if (D.family == HJ_FAM_BUMP_NORM || D.family == HJ_FAM_SPLIT_NORM || D.family == HJ_FAM_EVANS) {
+    if (D.family == HJ_FAM_BUMP_NORM || D.family == HJ_FAM_SPLIT_NORM || D.family == HJ_FAM_EVANS ||
+        D.family == HJ_FAM_LINEAR_GAME) {
         if (!(D.s_eps >= 0) || !std::isfinite(D.s_eps))
             return fail(ctx, HJ_EINVAL, "problem %d: s_eps must be >= 0", idx);
     }

@@ -42,6 +42,8 @@ struct ProbDev {
     // Evans-type family: H = -c(x) p_1 + beta |p_2| - |p| - gamma0, c = alpha_a (1 + kappa
     // exp(-mu |x - xc|^2)), xc in w; harmonic family: H = alpha_a (|p|^2 + |x|^2)/2
     T beta, gamma0;
+    // linear game: H(x,p,s) = -<diag(w) x, p> + a(s) |p|, a(s) = r_c - r_d (1 + beta sin(omega s))
+    T r_c, r_d, omega;
     const T *w;     // [DPAD] speed direction (split-norm family: the centre xc_A)
     const T *wb;    // [DPAD] split-norm family: the centre xc_B
     const T *e;     // [DPAD] signs of the smooth non-convex family (0 past d)
@@ -196,6 +198,8 @@ struct TP {
     T wb[C], ma[C];  // split-norm family: centre xc_B, and 1 on block A's components
     T m1[C], m2[C];  // 1 on the first / second coordinate (Evans-type family)
     T kap, mu, al_a, al_b, beta, gamma0;
+    T r_c, r_d, omega;  // linear game: a(s) = r_c - r_d (1 + beta sin(omega s))
+    mutable T st;       // PDE time s = t - tau of the stage being evaluated (set by the integrator)
     bool has_a, has_b;
     const T *At, *A, *Cm;
     T *sh;
@@ -208,6 +212,10 @@ struct TP {
         al_b = P.alpha_b;
         beta = P.beta;
         gamma0 = P.gamma0;
+        r_c = P.r_c;
+        r_d = P.r_d;
+        omega = P.omega;
+        st = 0;
         has_a = P.ksplit > 0;
         has_b = P.ksplit < P.d;
 #pragma unroll
@@ -614,6 +622,64 @@ struct Family<T, C, HJ_FAM_EVANS, PR> {
     }
 };
 
+// Linear differential game (Sec. 3.4, Example 3) with a diagonal drift
+// M = diag(m) (m in w) and ball-shaped control sets:
+// H(gamma, p, s) = -<M gamma, p> + a(s) n, a(s) = r_c - r_d (1 + beta sin(omega s)),
+// n = sqrt(|p|^2 + eps), s the PDE time of the stage (tp.st):
+// dZ/dtau = (M gamma - a p/n, -M p), L_Lax = -a eps/n, L_Hopf = a n;
+//   rg = m ag,  rp = -a (ag/n - <ag,p> p/n^3) - m ap + b (Lax: a eps p/n^3; Hopf: a p/n).
+template <typename T, int C, int PR>
+struct Family<T, C, HJ_FAM_LINEAR_GAME, PR> {
+    struct FI {
+        T a, n, ni;
+        T g[C], p[C];
+    };
+    __device__ static __forceinline__ void prep(const Grp &g, const TP<T, C> &tp, T eps, const T *gam, const T *p,
+                                                FI &f)
+    {
+        T pp = 0;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            f.g[k] = gam[k];
+            f.p[k] = p[k];
+            pp = fma(p[k], p[k], pp);
+        }
+        pp = gsum(g, pp);
+        T sn, cs;
+        sin_cos(tp.omega * tp.st, &sn, &cs);
+        f.a = tp.r_c - tp.r_d * fma(tp.beta, sn, (T)1);
+        const T q = pp + eps;
+        f.ni = rsq(q);
+        f.n = q * f.ni;
+    }
+    __device__ static __forceinline__ void field_fi(const TP<T, C> &tp, const FI &f, T eps, T *dg, T *dp, T &L)
+    {
+        const T an = f.a * f.ni;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            dg[k] = fma(tp.w[k], f.g[k], -an * f.p[k]);
+            dp[k] = -tp.w[k] * f.p[k];
+        }
+        L = (PR == HJ_LAX) ? -eps * an : f.a * f.n;
+    }
+    __device__ static __forceinline__ void vjp_fi(const Grp &g, const TP<T, C> &tp, const FI &f, T eps, const T *ag,
+                                                  const T *ap, T b, T *rg, T *rp)
+    {
+        T A = 0;
+#pragma unroll
+        for (int k = 0; k < C; ++k) A = fma(ag[k], f.p[k], A);
+        A = gsum(g, A);
+        const T ni = f.ni, ni3 = ni * ni * ni;
+        T cp = f.a * A * ni3 + ((PR == HJ_LAX) ? b * f.a * eps * ni3 : b * f.a * ni);
+        const T cag = -f.a * ni;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            rg[k] = tp.w[k] * ag[k];
+            rp[k] = fma(cag, ag[k], fma(cp, f.p[k], -tp.w[k] * ap[k]));
+        }
+    }
+};
+
 // H = c Phi(p), Phi = sum_i e_i s(p_i), s = sqrt(p^2 + eps):
 // dZ/dtau = (-c Phi', Phi c' w), Phi'_i = e_i p_i / s_i, Phi''_i = e_i eps / s_i^3,
 // L_Lax = c (<p, Phi'> - Phi) = -c eps sum_i e_i / s_i, L_Hopf = Phi (c - c' u).
@@ -983,12 +1049,15 @@ __device__ __forceinline__ void add_q(int kahan, T dQ, T &Q, T &Qc)
     }
 }
 
+// s0 is the PDE time s = t - tau at the start of the step; each stage sets
+// tp.st to its own time (only a time-dependent H reads it).
 template <typename T, int C, int FAM, int PR>
-__device__ __forceinline__ void rk4_step(const Grp &g, const TP<T, C> &tp, T eps, T h, int quad, int kahan, T *gam,
-                                         T *p, T &Q, T &Qc)
+__device__ __forceinline__ void rk4_step(const Grp &g, const TP<T, C> &tp, T eps, T h, T s0, int quad, int kahan,
+                                         T *gam, T *p, T &Q, T &Qc)
 {
     T ag[C], ap[C], zg[C], zp[C], kg[C], kp[C], L, aL;
     const T h2 = (T)0.5 * h;
+    tp.st = s0;
     field<T, C, FAM, PR>(g, tp, eps, gam, p, kg, kp, L);
     if (quad & HJ_ODE_EULER) {
         // z_{n+1} = z_n + h f(z_n); the augmented state gains h L(z_n)
@@ -1000,6 +1069,7 @@ __device__ __forceinline__ void rk4_step(const Grp &g, const TP<T, C> &tp, T eps
         T dQ = h * L;
         if (quad & HJ_QUAD_RECT) {
             T dg_[C], dp_[C];
+            tp.st = s0 - h;
             field<T, C, FAM, PR>(g, tp, eps, gam, p, dg_, dp_, L);
             dQ = h * L;
         }
@@ -1014,6 +1084,7 @@ __device__ __forceinline__ void rk4_step(const Grp &g, const TP<T, C> &tp, T eps
         zp[k] = fma(h2, kp[k], p[k]);
     }
     aL = L;
+    tp.st = s0 - h2;
     field<T, C, FAM, PR>(g, tp, eps, zg, zp, kg, kp, L);
 #pragma unroll
     for (int k = 0; k < C; ++k) {
@@ -1032,6 +1103,7 @@ __device__ __forceinline__ void rk4_step(const Grp &g, const TP<T, C> &tp, T eps
         zp[k] = fma(h, kp[k], p[k]);
     }
     aL = fma((T)2, L, aL);
+    tp.st = s0 - h;
     field<T, C, FAM, PR>(g, tp, eps, zg, zp, kg, kp, L);
     const T h6 = h / (T)6;
 #pragma unroll
@@ -1045,6 +1117,7 @@ __device__ __forceinline__ void rk4_step(const Grp &g, const TP<T, C> &tp, T eps
         dQ = h6 * aL;
     } else {
         T Ln, dg_[C], dp_[C];
+        tp.st = s0 - h;
         field<T, C, FAM, PR>(g, tp, eps, gam, p, dg_, dp_, Ln);
         dQ = h * Ln;
     }
@@ -1068,7 +1141,7 @@ __device__ __forceinline__ T functional(const Grp &g, const TP<T, C> &tp, const 
 #pragma unroll
         for (int k = 0; k < C; ++k) { bg[k] = gam[k]; bp[k] = p[k]; }
         for (int n = 0; n < N; ++n) {
-            rk4_step<T, C, FAM, PR>(g, tp, P.s_eps, h, quad, 0, gam, p, Q, Qc);
+            rk4_step<T, C, FAM, PR>(g, tp, P.s_eps, h, t - (T)n * h, quad, 0, gam, p, Q, Qc);
             const T gn = terminal<T, C, HJ_LAX>(g, P, x, v, gam, p, (T *)nullptr, (T *)nullptr);
             if (gn < gb) {
                 gb = gn;
@@ -1080,7 +1153,7 @@ __device__ __forceinline__ T functional(const Grp &g, const TP<T, C> &tp, const 
         for (int k = 0; k < C; ++k) { gam[k] = bg[k]; p[k] = bp[k]; }
         return gb;
     }
-    for (int n = 0; n < N; ++n) rk4_step<T, C, FAM, PR>(g, tp, P.s_eps, h, quad, kahan, gam, p, Q, Qc);
+    for (int n = 0; n < N; ++n) rk4_step<T, C, FAM, PR>(g, tp, P.s_eps, h, t - (T)n * h, quad, kahan, gam, p, Q, Qc);
     return terminal<T, C, PR>(g, P, x, v, gam, p, (T *)nullptr, (T *)nullptr) + Q;
 }
 
@@ -1106,7 +1179,7 @@ __device__ __forceinline__ T functional(const Grp &g, const TP<T, C> &tp, const 
 // both sized for N <= MAX_N.
 // ---------------------------------------------------------------------------
 template <typename T, int C, int FAM, int PR>
-__device__ __forceinline__ void adjoint_step(const Grp &g, const TP<T, C> &tp, T eps, T h, T b, const T *zg,
+__device__ __forceinline__ void adjoint_step(const Grp &g, const TP<T, C> &tp, T eps, T h, T s0, T b, const T *zg,
                                              const T *zp, T *lg, T *lp)
 {
     using Fam = Family<T, C, FAM, PR>;
@@ -1114,10 +1187,13 @@ __device__ __forceinline__ void adjoint_step(const Grp &g, const TP<T, C> &tp, T
     T kg[C], kp[C], sg[C], sp[C], L;
     const T h6 = h / (T)6, h3 = h / (T)3, h2 = (T)0.5 * h;
     // rebuild the stage inputs of the step from z_n, keeping each stage's FI
+    // (each prepared at its stage's PDE time, s0, s0 - h/2, s0 - h/2, s0 - h)
+    tp.st = s0;
     Fam::prep(g, tp, eps, zg, zp, f1);
     Fam::field_fi(tp, f1, eps, kg, kp, L);
 #pragma unroll
     for (int k = 0; k < C; ++k) { sg[k] = fma(h2, kg[k], zg[k]); sp[k] = fma(h2, kp[k], zp[k]); }
+    tp.st = s0 - h2;
     Fam::prep(g, tp, eps, sg, sp, f2);
     Fam::field_fi(tp, f2, eps, kg, kp, L);
 #pragma unroll
@@ -1126,6 +1202,7 @@ __device__ __forceinline__ void adjoint_step(const Grp &g, const TP<T, C> &tp, T
     Fam::field_fi(tp, f3, eps, kg, kp, L);
 #pragma unroll
     for (int k = 0; k < C; ++k) { sg[k] = fma(h, kg[k], zg[k]); sp[k] = fma(h, kp[k], zp[k]); }
+    tp.st = s0 - h;
     Fam::prep(g, tp, eps, sg, sp, f4);
 
     T wg[C], wp[C], rg[C], rp[C], sumg[C], sump[C];
@@ -1205,7 +1282,7 @@ __device__ __forceinline__ T gradient(const Grp &g, const TP<T, C> &tp, const Pr
             c += 2 * C;
         }
         if (++kk == K) kk = 0;
-        rk4_step<T, C, FAM, PR>(g, tp, eps, h, quad, kahan, gam, p, Q, Qc);
+        rk4_step<T, C, FAM, PR>(g, tp, eps, h, t - (T)n * h, quad, kahan, gam, p, Q, Qc);
         if (huy) {
             const T gn = terminal<T, C, HJ_LAX>(g, P, x, v, gam, p, (T *)nullptr, (T *)nullptr);
             if (gn < gb) { gb = gn; nstar = n + 1; }
@@ -1240,7 +1317,7 @@ __device__ __forceinline__ T gradient(const Grp &g, const TP<T, C> &tp, const Pr
             for (int k = 0; k < C; ++k) { st[k] = zg[k]; st[C + k] = zp[k]; }
             if (n + 1 < n1) {
                 T Qd = 0, Qcd = 0;
-                rk4_step<T, C, FAM, PR>(g, tp, eps, h, ode, 0, zg, zp, Qd, Qcd);
+                rk4_step<T, C, FAM, PR>(g, tp, eps, h, t - (T)n * h, ode, 0, zg, zp, Qd, Qcd);
             }
         }
         for (int n = n1 - 1; n >= n0; --n) {
@@ -1265,6 +1342,7 @@ __device__ __forceinline__ T gradient(const Grp &g, const TP<T, C> &tp, const Pr
                     for (int k = 0; k < C; ++k) lg[k] += rg[k];
                 } else {
                     // rectangle node at z_{n+1}: lam += h grad L(z_{n+1})
+                    tp.st = t - (T)(n + 1) * h;
                     vjp<T, C, FAM, PR>(g, tp, eps, ng, np, zeros, zeros, (T)1, rg, rp);
 #pragma unroll
                     for (int k = 0; k < C; ++k) { lg[k] = fma(h, rg[k], lg[k]); lp[k] = fma(h, rp[k], lp[k]); }
@@ -1274,11 +1352,12 @@ __device__ __forceinline__ T gradient(const Grp &g, const TP<T, C> &tp, const Pr
                 T wg[C], wp[C], rg[C], rp[C];
 #pragma unroll
                 for (int k = 0; k < C; ++k) { wg[k] = h * lg[k]; wp[k] = h * lp[k]; }
+                tp.st = t - (T)n * h;
                 vjp<T, C, FAM, PR>(g, tp, eps, ug, up, wg, wp, h * b, rg, rp);
 #pragma unroll
                 for (int k = 0; k < C; ++k) { lg[k] += rg[k]; lp[k] += rp[k]; }
             } else {
-                adjoint_step<T, C, FAM, PR>(g, tp, eps, h, b, ug, up, lg, lp);
+                adjoint_step<T, C, FAM, PR>(g, tp, eps, h, t - (T)n * h, b, ug, up, lg, lp);
             }
         }
     }

@@ -20,7 +20,7 @@ struct KSet {
 };
 
 struct Registry {
-    KSet k[2][8][2][MAXC + 1];  // [precision][family][principle][C]
+    KSet k[2][9][2][MAXC + 1];  // [precision][family][principle][C]
 };
 
 Registry &registry();

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libhj.so")
 
 HJ_OK, HJ_EINVAL, HJ_ENOMEM, HJ_ECUDA, HJ_ETIMEOUT, HJ_EUNSUPPORTED = range(6)
 (HJ_FAM_QUAD_ISO, HJ_FAM_SPEED_QUAD, HJ_FAM_SMOOTH_NONCONVEX, HJ_FAM_LINEAR_QUAD, HJ_FAM_BUMP_NORM,
- HJ_FAM_SPLIT_NORM, HJ_FAM_HARMONIC, HJ_FAM_EVANS) = range(8)
+ HJ_FAM_SPLIT_NORM, HJ_FAM_HARMONIC, HJ_FAM_EVANS, HJ_FAM_LINEAR_GAME) = range(9)
 HJ_LAX, HJ_HOPF, HJ_HUYGENS = 0, 1, 2
 HJ_G_QUAD_SHIFT, HJ_G_DIAG_QUAD, HJ_G_ELLIPSE = 0, 1, 2
 HJ_GRAD_FD_CENTRAL, HJ_GRAD_FD_FORWARD, HJ_GRAD_ADJOINT, HJ_GRAD_ADJOINT_CG = 0, 1, 2, 3

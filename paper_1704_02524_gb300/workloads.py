@@ -24,7 +24,7 @@ from typing import Dict, List, Optional
 import numpy as np
 
 (FAM_QUAD_ISO, FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX, FAM_LINEAR_QUAD, FAM_BUMP_NORM, FAM_SPLIT_NORM, FAM_HARMONIC,
- FAM_EVANS) = range(8)
+ FAM_EVANS, FAM_LINEAR_GAME) = range(9)
 LAX, HOPF, HUYGENS = 0, 1, 2
 G_QUAD_SHIFT, G_DIAG_QUAD, G_ELLIPSE, G_ROSENBROCK = 0, 1, 2, 3
 
@@ -67,12 +67,15 @@ class ProblemSpec:
     beta: float = 0.0                    # Evans-type family: H = -c(x) p_1 + beta|p_2| - |p| - gamma0,
     gamma0: float = 0.0                  #       c = alpha_a (1 + kappa exp(-mu|x - xc|^2))
                                          # harmonic family: H = hsign (|p|^2 + |x|^2)/2
+    r_c: float = 0.0                     # linear game: H(x,p,s) = -<diag(w) x, p> + a(s)|p|,
+    r_d: float = 0.0                     #       a(s) = r_c - r_d (1 + beta sin(omega s))
+    omega: float = 0.0
 
     def params(self) -> np.ndarray:
         """Flat parameter vector in the library's documented order:
         family block (w | A row-major then B row-major | xc, kappa, mu, sign |
         xc_A, xc_B, k, kappa, mu, alpha_A, alpha_B | sign | xc, kappa, mu, alpha,
-        beta, gamma0),
+        beta, gamma0 | m, r_C, r_D, beta, omega),
         then g block (a | sigma)."""
         parts: List[np.ndarray] = []
         if self.family in (FAM_SPEED_QUAD, FAM_SMOOTH_NONCONVEX):
@@ -87,6 +90,8 @@ class ProblemSpec:
             parts.append(np.array([self.hsign]))
         if self.family == FAM_EVANS:
             parts += [self.xc, np.array([self.kappa, self.mu, self.alpha_a, self.beta, self.gamma0])]
+        if self.family == FAM_LINEAR_GAME:
+            parts += [self.w, np.array([self.r_c, self.r_d, self.beta, self.omega])]
         if self.g_kind != G_ROSENBROCK:  # the Rosenbrock data has no parameters
             parts.append(self.a if self.g_kind == G_QUAD_SHIFT else self.sigma)
         return np.concatenate([np.asarray(p, dtype=np.float64).reshape(-1) for p in parts])
@@ -418,6 +423,26 @@ def evans_ex4(n_side: int = 128, t: float = 0.1, ds: float = 0.005, n_guesses: i
                     paper_solver(step=1.0 / 4.0, n_guesses=n_guesses, max_trials=n_guesses), precision)
 
 
+def linear_game(nq: int = 65536, d: int = 16, t: float = 0.8, n_steps: int = 64, r_d: float = 0.4,
+                n_guesses: int = 2) -> Workload:
+    """The time-dependent linear differential game of Sec. 3.4, Example 3:
+    dynamics dx/ds = M x + a + b with controls a, b in balls of radii r_C = 1
+    and r_D (1 + beta sin(omega s)), beta = 0.5, omega = 3, M = diag(m) with
+    m ~ U[-0.5, 0.5]^d, giving H(x,p,s) = -<Mx,p> + (r_C - r_D (1 + beta
+    sin(omega s)))|p|; the ellipse data, the Hopf functional (the formula
+    that section derives), x ~ U[-2,2]^d, t = 0.8, RK4 with 64 steps, the
+    default gradient descent with two starts.  With r_d = 0.4 the speed
+    stays positive and the functional convex in v; r_d > 1/1.5 lets it
+    change sign (a non-convex game)."""
+    rng = rng_for(6)
+    m = f32(rng.uniform(-0.5, 0.5, d))
+    X = f32(rng.uniform(-2, 2, (nq, d)))
+    P = ProblemSpec(d=d, family=FAM_LINEAR_GAME, principle=HOPF, g_kind=G_ELLIPSE, sigma=ellipse_sigma(d), w=m,
+                    r_c=1.0, r_d=r_d, beta=0.5, omega=3.0, s_eps=0.0, n_guesses=n_guesses)
+    return Workload(f"linear_game_d{d}_hopf", [P], X, np.full(nq, t), np.full(nq, n_steps, np.int32),
+                    np.zeros(nq, np.int32), solver_constants(n_guesses=n_guesses), "fp32")
+
+
 WORKLOADS = {
     "quad_iso_d2_lax": c1_quad_iso,
     "speed_quad_d10_lax": c2_speed_quad,
@@ -428,6 +453,7 @@ WORKLOADS = {
     "split_norm_d2_hopf_paper": split_ex5,
     "harmonic_d2_minus_hopf_paper": harmonic_ex2,
     "evans_d2_hopf_paper": evans_ex4,
+    "linear_game_d16_hopf": linear_game,
 }
 
 

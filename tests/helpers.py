@@ -18,7 +18,7 @@ def oracle_problem(spec: W.ProblemSpec) -> O.Problem:
                      A=spec.A, B=spec.B, a=spec.a, sigma=spec.sigma, n_neg=spec.n_neg, s_eps=spec.s_eps,
                      xc=spec.xc, kappa=spec.kappa, mu=spec.mu, hsign=spec.hsign, xcb=spec.xcb,
                      ksplit=spec.ksplit, alpha_a=spec.alpha_a, alpha_b=spec.alpha_b, beta=spec.beta,
-                     gamma0=spec.gamma0)
+                     gamma0=spec.gamma0, r_c=spec.r_c, r_d=spec.r_d, omega=spec.omega)
 
 
 def oracle_opts(solver: dict, n_guesses: int) -> O.Opts:

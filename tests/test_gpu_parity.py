@@ -29,7 +29,8 @@ def _spec(family, principle, d, seed=0, n_neg=1, s_eps=1e-6, g_kind=None, m=None
     rng = np.random.default_rng(seed)
     if g_kind is None:
         g_kind = {W.FAM_SMOOTH_NONCONVEX: W.G_DIAG_QUAD, W.FAM_BUMP_NORM: W.G_ELLIPSE, W.FAM_SPLIT_NORM: W.G_ELLIPSE,
-                  W.FAM_HARMONIC: W.G_ELLIPSE, W.FAM_EVANS: W.G_ELLIPSE}.get(family, W.G_QUAD_SHIFT)
+                  W.FAM_HARMONIC: W.G_ELLIPSE, W.FAM_EVANS: W.G_ELLIPSE,
+                  W.FAM_LINEAR_GAME: W.G_ELLIPSE}.get(family, W.G_QUAD_SHIFT)
     A = B = None
     if family == W.FAM_LINEAR_QUAD:
         G0 = rng.normal(size=(d, d))
@@ -40,7 +41,8 @@ def _spec(family, principle, d, seed=0, n_neg=1, s_eps=1e-6, g_kind=None, m=None
                          sigma=W.f32(rng.uniform(0.5, 2, d)), A=A, B=B, n_neg=n_neg, s_eps=s_eps, n_guesses=4,
                          xc=W.f32(rng.uniform(-0.5, 0.5, d)), kappa=3.0, mu=1.5,
                          hsign=-1.0 if principle == W.HOPF else 1.0, xcb=W.f32(rng.uniform(-0.5, 0.5, d)),
-                         ksplit=d // 2, alpha_a=1.5, alpha_b=-1.25, beta=2.0, gamma0=1.0)
+                         ksplit=d // 2, alpha_a=1.5, alpha_b=-1.25, beta=2.0, gamma0=1.0, r_c=1.0, r_d=0.6,
+                         omega=3.0)
 
 
 def _rows(n, d, seed, prec):
@@ -60,7 +62,7 @@ FAMS = [(W.FAM_QUAD_ISO, W.LAX), (W.FAM_QUAD_ISO, W.HOPF), (W.FAM_SPEED_QUAD, W.
         (W.FAM_SMOOTH_NONCONVEX, W.HOPF), (W.FAM_SMOOTH_NONCONVEX, W.LAX), (W.FAM_LINEAR_QUAD, W.LAX),
         (W.FAM_LINEAR_QUAD, W.HOPF), (W.FAM_BUMP_NORM, W.LAX), (W.FAM_BUMP_NORM, W.HOPF),
         (W.FAM_SPLIT_NORM, W.LAX), (W.FAM_SPLIT_NORM, W.HOPF), (W.FAM_HARMONIC, W.LAX), (W.FAM_HARMONIC, W.HOPF),
-        (W.FAM_EVANS, W.LAX), (W.FAM_EVANS, W.HOPF)]
+        (W.FAM_EVANS, W.LAX), (W.FAM_EVANS, W.HOPF), (W.FAM_LINEAR_GAME, W.LAX), (W.FAM_LINEAR_GAME, W.HOPF)]
 
 
 @pytest.mark.parametrize("family,principle", FAMS)
@@ -264,6 +266,19 @@ def test_examples_2_and_4_solve_matches_oracle(hj, prec, example):
         assert keep.mean() > 0.75
         err = rel_err(phi, rphi)[keep]
         assert np.mean(err <= 1e-4) >= 0.9, (np.mean(err <= 1e-4), err.max())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("r_d", [0.4, 1.0])
+def test_linear_game_solve_matches_oracle(hj, prec, r_d):
+    # the time-dependent game (Sec. 3.4, Example 3) at d = 16: convex
+    # (r_d = 0.4, speed > 0) and sign-changing speed (r_d = 1.0), Hopf
+    wl = W.linear_game(nq=96, r_d=r_d)
+    prec_code = hj.HJ_PREC_FP32 if prec == "fp32" else hj.HJ_PREC_FP64
+    phi, v, st, ref, info = _solve_both(hj, wl, 96, prec_code=prec_code)
+    err = rel_err(phi, ref["phi"])
+    assert np.all(err <= 1e-4), (err.max(), int(np.argmax(err)))
+    assert np.array_equal(st & 1, ref["status"] & 1)
 
 
 def test_rosenbrock_data_rows_match_oracle(hj):
