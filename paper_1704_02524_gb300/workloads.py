@@ -439,7 +439,8 @@ def linear_game(nq: int = 65536, d: int = 16, t: float = 0.8, n_steps: int = 64,
     X = f32(rng.uniform(-2, 2, (nq, d)))
     P = ProblemSpec(d=d, family=FAM_LINEAR_GAME, principle=HOPF, g_kind=G_ELLIPSE, sigma=ellipse_sigma(d), w=m,
                     r_c=1.0, r_d=r_d, beta=0.5, omega=3.0, s_eps=0.0, n_guesses=n_guesses)
-    return Workload(f"linear_game_d{d}_hopf", [P], X, np.full(nq, t), np.full(nq, n_steps, np.int32),
+    name = f"linear_game_d{d}_hopf" if r_d == 0.4 else f"linear_game_d{d}_rd{r_d:g}_hopf"
+    return Workload(name, [P], X, np.full(nq, t), np.full(nq, n_steps, np.int32),
                     np.zeros(nq, np.int32), solver_constants(n_guesses=n_guesses), "fp32")
 
 

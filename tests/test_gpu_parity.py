@@ -369,7 +369,8 @@ def _solve_both(hj, wl, nq, prec_code=None, tpp=0):
     phi, v, st = hj.hj_solve(ctx, _t(w.x, dt), _t(w.t, dt), _t(w.n_steps, torch.int32))
     info = hj.hj_last_solve_info(ctx)
     ctx.close()
-    key = (w.name, nq, repr(sorted(w.solver.items())))
+    key = (w.name, nq, repr(sorted(w.solver.items())), repr([p.params().tolist() for p in w.problems]),
+           hash(w.x.tobytes()), hash(w.t.tobytes()), hash(w.n_steps.tobytes()))
     if key not in _ORACLE_CACHE:
         _ORACLE_CACHE[key] = O.solve(oracle_problem(spec), oracle_opts(w.solver, spec.n_guesses), w.x, w.t, w.n_steps)
     return phi.cpu().numpy(), v.cpu().numpy(), st.cpu().numpy(), _ORACLE_CACHE[key], info
