@@ -90,7 +90,7 @@ def _args():
     ap.add_argument("--tpp", type=int, default=0, help="threads per pair of the descent (0: library choice)")
     ap.add_argument("--ck", type=int, default=0, help="adjoint checkpoint interval (0: library choice)")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="skip hj_autotune (launch parameters timed on a 4096-query sample before the run)")
+                    help="skip hj_autotune (launch parameters timed on up to 65,536 queries before the run)")
     return ap.parse_args()
 
 
@@ -269,8 +269,13 @@ def run_ours(a):
             hj.hj_set_tuning(ctx, p, a.tpp, a.ck)
         tuning = {"threads_per_pair": [a.tpp] * len(wl.problems), "by": "command line"}
     elif not a.no_autotune:
-        # launch parameters per problem, timed on a sample (outside the timed region)
-        ns_ = min(nq, 4096)
+        # launch parameters per problem, timed on a sample (outside the timed region).
+        # The sample must fill the GPU as the run does: on a batch that fits in
+        # one wave the candidates' single-pair latencies decide (more lanes per
+        # pair look faster), while the full run is throughput bound (measured on
+        # the d=2 paper workloads: one lane per pair runs 2.6-3.6x faster there
+        # than the lane count a 4,096-query sample picked).
+        ns_ = min(nq, 65536)
         sample = np.sort(np.random.default_rng(7).choice(nq, ns_, replace=False))
         si = torch.tensor(sample, dtype=torch.int64, device=dev)
         chosen = hj.hj_autotune(ctx, x[si].contiguous(), t[si].contiguous(), ns[si].contiguous(),
