@@ -74,7 +74,7 @@ L2_FLUSH_BYTES = 256 << 20
 # from one `ncu --set full` capture of this build's kernels on a GB300; the
 # launch's traffic grows with the number of (query, start) pairs, so it is
 # scaled by queries / 4096.
-TRAFFIC_4096 = {"smooth_nonconvex_d20_hopf": 16.423e9 + 20.268e9, "linear_quad_d64_lax": 28.598e9 + 42.637e9}
+TRAFFIC_4096 = {"smooth_nonconvex_d20_hopf": 16.677e9 + 20.430e9, "linear_quad_d64_lax": 28.598e9 + 42.637e9}
 
 
 def _args():
@@ -268,13 +268,17 @@ def run_ours(a):
         for p in range(len(wl.problems)):
             hj.hj_set_tuning(ctx, p, a.tpp, a.ck)
         tuning = {"threads_per_pair": [a.tpp] * len(wl.problems), "by": "command line"}
+    elif all(p_.solver is None for p_ in wl.problems) and wl.solver["grad"].startswith("fd"):
+        # Algorithm 1 (coordinate descent): a few capped iterations rank the lane
+        # counts wrongly -- on the d=2 paper workloads the timed sample picked 2
+        # or 4 lanes per pair, which run 2x and 4x slower over the whole solve
+        # than the library's automatic choice (one lane, measured on a GB300)
+        tuning = {"threads_per_pair": [0] * len(wl.problems), "by": "automatic (coordinate descent)"}
     elif not a.no_autotune:
         # launch parameters per problem, timed on a sample (outside the timed region).
         # The sample must fill the GPU as the run does: on a batch that fits in
         # one wave the candidates' single-pair latencies decide (more lanes per
-        # pair look faster), while the full run is throughput bound (measured on
-        # the d=2 paper workloads: one lane per pair runs 2.6-3.6x faster there
-        # than the lane count a 4,096-query sample picked).
+        # pair look faster), while the full run is throughput bound.
         ns_ = min(nq, 65536)
         sample = np.sort(np.random.default_rng(7).choice(nq, ns_, replace=False))
         si = torch.tensor(sample, dtype=torch.int64, device=dev)
