@@ -3,22 +3,26 @@
  * Hamilton-Jacobi equations by the generalized Lax minimisation and Hopf
  * maximisation principles of Chow, Darbon, Osher and Yin (arXiv 1704.02524).
  *
- * The equation is phi_t + H(x, grad phi) = 0, phi(x, 0) = g(x) (Sec. 2.1).
+ * The equation is phi_t + H(x, grad phi, t) = 0, phi(x, 0) = g(x) (Sec. 2.1).
  * For a query (x, t) and a vector v the library integrates the
  * bi-characteristics (Sec. 4.1)
- *      d gamma/ds = dH/dp(gamma, p),  dp/ds = -dH/dx(gamma, p),
+ *      d gamma/ds = dH/dp(gamma, p, s),  dp/ds = -dH/dx(gamma, p, s),
  *      gamma(t) = x,  p(t) = v,
- * backward from s = t to s = 0 with N classical RK4 steps, and evaluates
+ * backward from s = t to s = 0 with N classical RK4 steps (or N forward
+ * Euler steps, HJ_ODE_EULER), and evaluates
  *   Lax  (convex H, eq. lax_formula):
  *      F(v) = g(gamma(0)) + int_0^t ( <p, dH/dp> - H ) ds,       phi = min_v F
  *   Hopf (g convex, eq. hopf_formula):
  *      G(v) = g*(p(0)) + int_0^t ( H - <dH/dx, gamma> ) ds - <x, v>,
  *                                                                phi = -min_v G
+ *   Huygens (H of degree one in p, eq. num_min): the smallest g(gamma) over
+ *      the solver's grid nodes, phi = min_v of it (see hj_principle).
  * It minimises over v by the paper's cyclic coordinate descent with
- * finite differences (Algorithm 1, eq. num_diff) or by gradient descent with
+ * finite differences (Algorithm 1, eq. num_diff), by gradient descent with
  * the exact gradient of the discretised functional (discrete adjoint of
- * RK4), checks the certificate p(0) in dg(gamma(0)) (Sec. 4.3), reseeds
- * failed starts and keeps the best of several random guesses (Sec. 5).
+ * the integrator), or by conjugate gradients with that gradient, checks the
+ * certificate p(0) in dg(gamma(0)) (Sec. 4.3), reseeds failed starts and
+ * keeps the best of several random guesses (Sec. 5).
  *
  * Conventions for every entry point below
  *  - Array arguments are DEVICE pointers owned by the caller, contiguous,
