@@ -71,9 +71,9 @@ REF_SAMPLE = 64          # queries per step of the reference arm
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of the dominant descent launch of a 4,096-query
 # case (d=20: round 0's fine-level launch; d=64: the tile kernel's launch),
-# from one `ncu --set full` capture of this build's kernels on a GB300; the
-# launch's traffic grows with the number of (query, start) pairs, so it is
-# scaled by queries / 4096.
+# from ncu captures of the current kernels on a GB300 (dram__bytes_read.sum +
+# dram__bytes_write.sum); the launch's traffic grows with the number of
+# (query, start) pairs, so it is scaled by queries / 4096.
 TRAFFIC_4096 = {"smooth_nonconvex_d20_hopf": 16.677e9 + 20.430e9, "linear_quad_d64_lax": 28.598e9 + 42.637e9}
 
 
