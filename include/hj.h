@@ -36,7 +36,7 @@
  *    row (a row whose index is outside [0, n problems) is skipped: its
  *    outputs are left untouched, or for hj_solve phi = NaN and status
  *    HJ_ST_NONFINITE); n_steps (int32 [n], nullable = opts.n_steps_default)
- *    its RK4 step count N.  t must be > 0, N in [1, 256] (other step counts
+ *    its integrator step count N.  t must be > 0, N in [1, 256] (other step counts
  *    give NaN results).
  *  - Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy
  *    default stream).  Argument errors are detected on the host and
@@ -195,7 +195,7 @@ typedef struct {
     hj_precision precision;
     int kahan;
     int coarse_div;     /* gradient and CG descents: > 1 descends first on the
-                           functional with N / coarse_div RK4 steps until every
+                           functional with N / coarse_div steps until every
                            move is < coarse_eps (or max_iters), then, with the
                            step control started afresh, on the N-step functional
                            from there (continuation in the step size; iterations
@@ -253,7 +253,8 @@ typedef struct {
     int64_t iterations;         /* descent iterations summed over pairs             */
     int64_t functional_evals;   /* forward functional evaluations                   */
     int64_t gradient_evals;     /* adjoint gradients                                */
-    int64_t rk4_steps;          /* RK4 steps of all evaluations (forward sweeps)    */
+    int64_t rk4_steps;          /* integrator (RK4 or Euler) steps of all evaluations
+                                   (forward sweeps)                                 */
     double algorithmic_flops;   /* fp32/fp64 arithmetic of the descent, FMA = 2     */
     double certify_flops;       /* arithmetic of the in-kernel certificate passes   */
     int threads_per_pair;       /* of the first problem's descent launch            */
@@ -290,7 +291,7 @@ hj_status hj_eval_functional(hj_ctx *ctx, int64_t n, const int32_t *problem_idx,
 
 /*
  * hj_grad -- F and its exact gradient dF/dv of the discretised functional
- * (discrete adjoint of the RK4 map with sqrt(N)-step checkpointing):
+ * (discrete adjoint of the RK4 or Euler map with sqrt(N)-step checkpointing):
  * F_out [n] (nullable), grad_out [n, ld].
  */
 hj_status hj_grad(hj_ctx *ctx, int64_t n, const int32_t *problem_idx, const void *x, const void *t,
@@ -338,13 +339,15 @@ hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out);
  * hj_set_tuning -- launch parameters of problem `problem` (used by the
  * autotuner and for experiments): tpp = threads per (query, start) pair of
  * the descent and gradient kernels, in {1,2,4,8,16,32} (0: automatic;
- * for a LINEAR_QUAD problem in an fp32 context with RK4 quadrature, d <= 64
- * and 2 d + m <= 256 after padding to multiples of 16, automatic means the
+ * for a LINEAR_QUAD problem with quadratic data (HJ_G_QUAD_SHIFT or
+ * HJ_G_DIAG_QUAD) in an fp32 context with RK4 and its quadrature, no
+ * coarse-to-fine descent, d <= 64 and 2 d + m <= 256 after padding to
+ * multiples of 16, automatic means the
  * tensor-core tile kernel for hj_eval_functional, hj_grad and the gradient
  * and conjugate-gradient descents of hj_solve: 128 pairs per CTA, the stage
  * products on the tensor cores in split-precision BF16x3 (relative error
  * ~2^-16); any non-zero tpp selects the lane-group kernels instead);
- * ck_interval = RK4 steps between checkpoints of the adjoint, in [1, 16]
+ * ck_interval = integrator steps between checkpoints of the adjoint, in [1, 16]
  * (0: automatic, the smallest interval whose checkpoint storage fits a
  * fixed per-thread budget).  Returns HJ_EUNSUPPORTED when no kernel is built
  * for the resulting components per thread.
