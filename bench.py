@@ -348,6 +348,9 @@ def run_ours(a):
                 "kernel": "k_desc (persistent descent)",
                 "peak_note": f"FP32 FMA {nsm} SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                              f"({peak_src} max SM clock)"}
+        # cross-check of that peak: the project's FMA-chain microbenchmark
+        # (outside the timed region)
+        roof["peak_check_tflops"] = hj.hj_fp32_fma_rate(local)
 
     # e2e through the C ABI with host buffers: pinned H2D of x, t, N (and the
     # problem index), the solve, D2H of phi, v, status

@@ -416,6 +416,17 @@ hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, cons
 /* Message of the last error on ctx (or of the last failed hj_create when ctx is NULL). */
 const char *hj_last_error(const hj_ctx *ctx);
 
+/*
+ * hj_fp32_fma_rate -- measured FP32 FMA rate of CUDA device `device` in
+ * TFLOP/s (FMA = 2 flops), written to *tflops (HOST): every thread of
+ * 8 x 256-thread blocks per SM runs 8 independent chains of 65,536 FMAs;
+ * the best of five timed launches (after one warm-up) is reported.  It is the
+ * measured counterpart of the ALU roofline peak (SMs x 128 lanes x 2 x
+ * clock), with no context needed.  Allocates and frees its own 2048 floats
+ * per SM.  HJ_EINVAL for a NULL tflops, HJ_ECUDA / HJ_ENOMEM on CUDA errors.
+ */
+hj_status hj_fp32_fma_rate(int device, double *tflops);
+
 #ifdef __cplusplus
 }
 #endif

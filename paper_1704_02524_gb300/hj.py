@@ -34,7 +34,7 @@ HJ_ST_CERTIFIED, HJ_ST_MAX_ITERS, HJ_ST_NONFINITE, HJ_ST_RESEEDED = 1, 2, 4, 8
 
 EXPORTED = ("hj_create", "hj_destroy", "hj_eval_functional", "hj_grad", "hj_certify", "hj_solve", "hj_guesses",
             "hj_last_solve_info", "hj_set_tuning", "hj_last_error", "hj_solve_noalloc", "hj_autotune",
-            "hj_set_graph")
+            "hj_set_graph", "hj_fp32_fma_rate")
 
 
 class hj_solver_opts(C.Structure):
@@ -88,6 +88,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.hj_set_tuning.argtypes = [vp, C.c_int, C.c_int, C.c_int]
     lib.hj_autotune.argtypes = [vp, i64, vp, vp, vp, vp, C.c_int, i32p, vp]
     lib.hj_set_graph.argtypes = [vp, C.c_int]
+    lib.hj_fp32_fma_rate.argtypes = [C.c_int, C.POINTER(C.c_double)]
     lib.hj_last_error.argtypes = [vp]
     lib.hj_last_error.restype = C.c_char_p
     for name in EXPORTED:
@@ -295,6 +296,15 @@ def hj_last_solve_info(ctx: Context) -> Dict:
 
 def hj_set_tuning(ctx: Context, problem: int, tpp: int = 0, ck_interval: int = 0):
     _check(ctx, load_library().hj_set_tuning(ctx.handle, problem, tpp, ck_interval))
+
+
+def hj_fp32_fma_rate(device: int = 0) -> float:
+    """Measured FP32 FMA rate of the device in TFLOP/s (FMA-chain microbenchmark)."""
+    out = C.c_double(0.0)
+    st = load_library().hj_fp32_fma_rate(int(device), C.byref(out))
+    if st != HJ_OK:
+        raise HJError(st, f"hj_fp32_fma_rate failed with status {st}")
+    return out.value
 
 
 def hj_set_graph(ctx: Context, enable: bool = True):

@@ -281,6 +281,16 @@ def test_linear_game_solve_matches_oracle(hj, prec, r_d):
     assert np.array_equal(st & 1, ref["status"] & 1)
 
 
+def test_fp32_fma_rate_microbenchmark_is_below_the_formula_peak(hj):
+    # the measured FMA rate cannot exceed SMs x 128 lanes x 2 flop x the
+    # highest clock this part runs (2.07 GHz; 2.2 as a margin) and, with 16
+    # chains' worth of independent FMAs per scheduler slot, reaches most of it
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    rate = hj.hj_fp32_fma_rate(0)
+    bound = nsm * 128 * 2 * 2.2e9 / 1e12
+    assert 0.5 * bound < rate < bound, (rate, bound)
+
+
 def test_rosenbrock_data_rows_match_oracle(hj):
     # the non-convex data's value, gradient and certificate through the
     # harmonic family's Lax kernels (fp32 and fp64 rows)
