@@ -281,6 +281,30 @@ def test_linear_game_solve_matches_oracle(hj, prec, r_d):
     assert np.array_equal(st & 1, ref["status"] & 1)
 
 
+@pytest.mark.parametrize("name,sample", [("smooth_nonconvex_d20_hopf", 64), ("speed_quad_d10_lax", 64),
+                                         ("linear_quad_d64_lax", 16)])
+def test_full_size_workloads_match_oracle_on_sampled_queries(hj, name, sample):
+    # the benchmark's full batches (65,536 d=20 Hopf queries x 16 starts;
+    # 49,152 d=10 Lax queries x 8; 32,768 d=64 linear-quadratic queries on the
+    # tensor-core tile kernel) in one solve each, with the library's automatic
+    # launch choice; sampled queries against the oracle run one by one with the
+    # same query ids (the Philox counters)
+    builders = {"smooth_nonconvex_d20_hopf": W.c3_smooth_nonconvex, "speed_quad_d10_lax": W.c2_speed_quad,
+                "linear_quad_d64_lax": W.c4_linear_quad}
+    wl = builders[name]()
+    spec = wl.problems[0]
+    ctx = hj.hj_create(wl.problems, hj.opts_from_dict(wl.solver, hj.HJ_PREC_FP32, int(wl.n_steps[0])), 0)
+    phi, v, st = hj.hj_solve(ctx, _t(wl.x, torch.float32), _t(wl.t, torch.float32), _t(wl.n_steps, torch.int32))
+    phi, st = phi.cpu().numpy(), st.cpu().numpy()
+    ctx.close()
+    ids = np.sort(np.random.default_rng(11).choice(wl.nq, sample, replace=False))
+    ref = O.solve(oracle_problem(spec), oracle_opts(wl.solver, spec.n_guesses), wl.x[ids], wl.t[ids],
+                  wl.n_steps[ids], query_ids=ids)
+    err = rel_err(phi[ids], ref["phi"])
+    assert np.all(err <= 1e-4), (err.max(), int(ids[np.argmax(err)]))
+    assert np.array_equal(st[ids] & 1, ref["status"] & 1)
+
+
 def test_fp32_fma_rate_microbenchmark_is_below_the_formula_peak(hj):
     # the measured FMA rate cannot exceed SMs x 128 lanes x 2 flop x the
     # highest clock this part runs (2.07 GHz; 2.2 as a margin) and, with 16
