@@ -395,7 +395,13 @@ hj_status hj_autotune(hj_ctx *ctx, int64_t n_queries, const int32_t *problem_idx
  * context once beforehand (hj_create allocates); this call then makes no
  * cudaMalloc/cudaFree and uses no allocating library routine.
  *
- * Arguments, results and status codes are those of hj_solve.  All of the
+ * Arguments, results and status codes are those of hj_solve, and so are the
+ * kernels, with one exception: a linear-quadratic problem that hj_solve
+ * would run on the tensor-core tile kernel (see hj_solve) runs here on the
+ * lane-group kernels, whose results agree with it within the tile kernel's
+ * BF16x3 rounding but not bit for bit; every other problem gets hj_solve's
+ * results bit for bit.  A batch of more than 2^31 - 1 (query, start) pairs
+ * returns HJ_EINVAL before any size arithmetic.  All of the
  * call's scratch lives in one static device array of
  * HJ_SOLVE_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps
  * for the life of the process; a call that needs more (about

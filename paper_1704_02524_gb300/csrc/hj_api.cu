@@ -1051,8 +1051,8 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
     if (!x || !t || !phi_out || !v_out || !status_out)
         return fail(ctx, HJ_EINVAL, "x, t, phi_out, v_out and status_out must be non-NULL");
     if (ctx->np > 1 && !problem_idx) return fail(ctx, HJ_EINVAL, "problem_idx is required with several problems");
+    if (n_queries > (((long long)1 << 31) - 1) / ctx->gmax) return fail(ctx, HJ_EINVAL, "too many (query, start) pairs");
     const long long npairs = (long long)n_queries * ctx->gmax;
-    if (npairs > ((long long)1 << 31) - 1) return fail(ctx, HJ_EINVAL, "too many (query, start) pairs");
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device));
     hj_status st = ensure_scratch(ctx, n_queries, npairs);
@@ -1574,6 +1574,9 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
     if (ctx->np > 1 && !problem_idx) return fail(ctx, HJ_EINVAL, "problem_idx is required with several problems");
     if (ctx->device < 0 || ctx->device >= NOALLOC_MAX_DEVICES)
         return fail(ctx, HJ_EUNSUPPORTED, "hj_solve_noalloc supports devices 0..%d", NOALLOC_MAX_DEVICES - 1);
+    // bound the batch before any size arithmetic: (query, start) pairs are
+    // indexed in int32, and n_queries * starts must not wrap
+    if (n_queries > (((long long)1 << 31) - 1) / ctx->gmax) return fail(ctx, HJ_EINVAL, "too many (query, start) pairs");
     const long long npairs = (long long)n_queries * ctx->gmax;
     const size_t es = ctx->prec ? sizeof(double) : sizeof(float);
     NoallocLayout L{};

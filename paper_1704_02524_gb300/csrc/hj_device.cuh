@@ -1159,7 +1159,13 @@ __device__ __forceinline__ T functional(const Grp &g, const TP<T, C> &tp, const 
 
 // ---------------------------------------------------------------------------
 // Discrete adjoint of the RK4 map (exact gradient of the discretised
-// functional).  Forward: checkpoints of z every K = ceil(sqrt(N)) steps.
+// functional).  Forward: checkpoints of z every K steps, K from
+// ck_interval: the caller's fixed interval, or else the smallest K whose
+// ceil(N/K) checkpoints plus a K-state segment fit CK_BUDGET bytes per thread
+// (K = 1, every state stored, at d = 20 and N = 64; K = ceil(sqrt(N)) is the
+// choice that minimises that storage, at the price of one extra forward
+// pass).  Every K gives the same gradient: the recomputed states repeat the
+// forward pass's arithmetic.
 // Reverse, segment by segment: recompute the segment's states z_n from its
 // checkpoint (stored, 2C values per step), then for each step backward
 // rebuild its stage inputs Z1 = z_n, Z2 = z_n + h/2 k1, Z3 = z_n + h/2 k2,

@@ -156,6 +156,21 @@ def _dev(ctx: Context, t: Optional[torch.Tensor], name: str, dtype=None, shape=N
     return t
 
 
+def _solve_out(ctx: Context, out, n: int):
+    """Caller-supplied (phi, v, status) of a solve: checked for device, dtype,
+    shape and contiguity, since the kernels write every row of each."""
+    if len(out) != 3:
+        raise ValueError("out must be (phi, v, status)")
+    phi, v, status = out
+    _dev(ctx, phi, "phi", torch.float64, (n,))
+    _dev(ctx, v, "v", ctx.dtype, (n, ctx.ld))
+    _dev(ctx, status, "status", torch.int32, (n,))
+    for name, o in (("phi", phi), ("v", v), ("status", status)):
+        if o is None:
+            raise ValueError(f"out {name} must be a tensor")
+    return phi, v, status
+
+
 def opts_from_dict(solver: Dict, precision: int = HJ_PREC_FP32, n_steps_default: int = 64,
                    kahan: int = 1) -> hj_solver_opts:
     grad = {"fd_central": HJ_GRAD_FD_CENTRAL, "fd_forward": HJ_GRAD_FD_FORWARD, "adjoint": HJ_GRAD_ADJOINT,
@@ -251,7 +266,7 @@ def hj_solve(ctx: Context, x: torch.Tensor, t: torch.Tensor, n_steps: Optional[t
         v = torch.zeros(n, ctx.ld, dtype=ctx.dtype, device=x.device)
         status = torch.empty(n, dtype=torch.int32, device=x.device)
     else:
-        phi, v, status = out
+        phi, v, status = _solve_out(ctx, out, n)
     _check(ctx, load_library().hj_solve(ctx.handle, q_begin, n, _ptr(problem_idx), _ptr(x), _ptr(t), _ptr(n_steps),
                                         _ptr(phi), _ptr(v), _ptr(status), _stream(x.device)))
     return phi, v, status
@@ -271,7 +286,7 @@ def hj_solve_noalloc(ctx: Context, x: torch.Tensor, t: torch.Tensor, n_steps: Op
         v = torch.zeros(n, ctx.ld, dtype=ctx.dtype, device=x.device)
         status = torch.empty(n, dtype=torch.int32, device=x.device)
     else:
-        phi, v, status = out
+        phi, v, status = _solve_out(ctx, out, n)
     _check(ctx, load_library().hj_solve_noalloc(ctx.handle, q_begin, n, _ptr(problem_idx), _ptr(x), _ptr(t),
                                                 _ptr(n_steps), _ptr(phi), _ptr(v), _ptr(status), _stream(x.device)))
     return phi, v, status

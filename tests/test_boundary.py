@@ -130,3 +130,16 @@ def test_mixed_workload_structure():
         assert p.solver is not None
     lq = [p for p in wl.problems if p.family == W.FAM_LINEAR_QUAD]
     assert all(p.solver["grad"] == "adjoint_cg" and p.n_guesses == 1 for p in lq)
+
+
+def test_caller_supplied_solve_outputs_are_checked_before_the_call():
+    # the solve writes every row of phi, v and status: tensors on the wrong
+    # device (or missing) are refused on the host, before the C call
+    import torch
+    from paper_1704_02524_gb300 import hj
+    ctx = hj.Context(None, [type("P", (), {"d": 3})()], hj.hj_solver_opts(precision=hj.HJ_PREC_FP32), 0)
+    good_cpu = (torch.zeros(4, dtype=torch.float64), torch.zeros(4, 3), torch.zeros(4, dtype=torch.int32))
+    with pytest.raises(ValueError, match="phi must be on cuda"):
+        hj._solve_out(ctx, good_cpu, 4)
+    with pytest.raises(ValueError, match="out must be"):
+        hj._solve_out(ctx, good_cpu[:2], 4)

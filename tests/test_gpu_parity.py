@@ -717,3 +717,24 @@ def test_queries_of_unknown_problems_and_empty_calls(hj):
     assert hj.hj_eval_functional(ctx, e, et, e).numel() == 0
     assert hj.hj_solve(ctx, e, et, None, torch.empty(0, dtype=torch.int32, device=DEV))[0].numel() == 0
     ctx.close()
+
+
+def test_caller_supplied_solve_outputs_of_the_wrong_shape_or_type_are_refused(hj):
+    wl = W.c3_smooth_nonconvex(nq=8)
+    ctx = hj.hj_create(wl.problems, hj.opts_from_dict(wl.solver, hj.HJ_PREC_FP32, 64), 0)
+    x, t = _t(wl.x, torch.float32), _t(wl.t, torch.float32)
+    good = (torch.zeros(8, dtype=torch.float64, device=DEV), torch.zeros(8, 20, device=DEV),
+            torch.zeros(8, dtype=torch.int32, device=DEV))
+    bad = [(torch.zeros(7, dtype=torch.float64, device=DEV),) + good[1:],
+           (good[0], torch.zeros(8, 19, device=DEV), good[2]),
+           (good[0], torch.zeros(8, 20, dtype=torch.float64, device=DEV), good[2]),
+           good[:2] + (torch.zeros(8, dtype=torch.int64, device=DEV),),
+           (good[0], torch.zeros(20, 8, device=DEV).t(), good[2])]
+    for fn in (hj.hj_solve, hj.hj_solve_noalloc):
+        for out in bad:
+            with pytest.raises(ValueError):
+                fn(ctx, x, t, out=out)
+        phi, v, st = fn(ctx, x, t, out=good)
+        torch.cuda.synchronize()
+        assert np.all(np.isfinite(phi.cpu().numpy()))
+    ctx.close()
