@@ -268,6 +268,16 @@ typedef struct {
     double tensor_flops;        /* tensor-core tile kernel: BF16 flops of its stage products,
                                    3 x 2 (3 d^2 + d m) per pair and RK4 stage (the fp32
                                    product, unpadded, times the three BF16x3 terms)       */
+    int64_t adjoint_steps;      /* reverse integrator steps of all adjoint gradients       */
+    double nominal_flops;       /* the descent launches' work at fixed per-evaluation counts
+                                   of the general RK4 form: per forward step and pair 36d
+                                   (H = |p|^2/2), 52d (c^2|p|^2/2), 64d (c Phi(p)),
+                                   4(4d^2 + 4md) + 28d (linear-quadratic), the lane-group
+                                   operation count for the other families; an adjoint
+                                   gradient counts as four functional evaluations and the
+                                   in-kernel certificate as one.  Independent of how the
+                                   kernels arrange the arithmetic (the one-thread-per-pair
+                                   kernels execute fewer operations than these counts)   */
 } hj_solve_info;
 
 /*

@@ -49,6 +49,11 @@ void reg_f32_spn_lax(Registry &);
 void reg_f32_spn_hopf(Registry &);
 void reg_f64_spn_lax(Registry &);
 void reg_f64_spn_hopf(Registry &);
+void reg_f32_r1_c04(Registry &);
+void reg_f32_r1_c08(Registry &);
+void reg_f32_r1_c16(Registry &);
+void reg_f32_r1_c20(Registry &);
+void reg_f32_r1_c32(Registry &);
 
 Registry &registry()
 {
@@ -86,6 +91,11 @@ Registry &registry()
         reg_f32_spn_hopf(*x);
         reg_f64_spn_lax(*x);
         reg_f64_spn_hopf(*x);
+        reg_f32_r1_c04(*x);
+        reg_f32_r1_c08(*x);
+        reg_f32_r1_c16(*x);
+        reg_f32_r1_c20(*x);
+        reg_f32_r1_c32(*x);
         return x;
     }();
     return *r;
@@ -144,6 +154,26 @@ FlopModel flop_model(int fam, int pr, int d, int quad)
     }
     if (quad & HJ_ODE_EULER) return FlopModel{fld + 4.0 * d + 2, vjp + 4.0 * d + 1};
     return FlopModel{4 * fld + 26.0 * d + 12, 4 * vjp + 28.0 * d + 6};
+}
+
+// Nominal arithmetic of one forward step of one pair in the general RK4
+// form (FMA = 2): about 28d for the stage combinations plus four field
+// evaluations, the field of H = |p|^2/2 ~2d, c(x)^2|p|^2/2 ~6d,
+// c(x) Phi(p) ~9d, <Ax,p> + |B^T p|^2/2 4d^2 + 4md -- 36d, 52d, 64d and
+// 4(4d^2 + 4md) + 28d per step.  An adjoint gradient counts as four
+// evaluations (one forward, a reverse of about three), the in-kernel
+// certificate as one.  These are fixed per-evaluation counts, independent of
+// how a kernel arranges the arithmetic; families without one use the
+// operation count of the lane-group kernels (flop_model).
+double nominal_fwd_step(int fam, int pr, int d, int m, int quad)
+{
+    switch (fam) {
+    case HJ_FAM_QUAD_ISO: return 36.0 * d;
+    case HJ_FAM_SPEED_QUAD: return 52.0 * d;
+    case HJ_FAM_SMOOTH_NONCONVEX: return 64.0 * d;
+    case HJ_FAM_LINEAR_QUAD: return 4.0 * (4.0 * d * d + 4.0 * m * d) + 28.0 * d;
+    default: return flop_model(fam, pr, d, quad).fwd_step;
+    }
 }
 
 struct DevProblem {
@@ -237,6 +267,24 @@ void fill_prob(const hj_problem_desc &D, const std::vector<double> &par, int ld,
             gs2[i] = s * s;
             gis2[i] = (T)1 / (s * s);
         }
+    }
+    for (int i = 0; i < R1_MAXD; ++i) P.rw[i] = P.re[i] = P.rew[i] = P.rg2[i] = P.rga[i] = 0.f;
+    P.rcst = 0.f;
+    if (D.family == HJ_FAM_SMOOTH_NONCONVEX && d <= R1_MAXD) {
+        for (int i = 0; i < d; ++i) {
+            const float wi = (float)par[i], ei = (i < D.n_neg) ? -1.f : 1.f;
+            P.rw[i] = wi;
+            P.re[i] = ei;
+            P.rew[i] = wi * ei;
+            if (D.g_kind == HJ_G_QUAD_SHIFT) {
+                P.rg2[i] = 1.f;
+                P.rga[i] = (float)par[off + i];
+            } else {
+                const float s = (float)par[off + i];
+                P.rg2[i] = s * s;
+            }
+        }
+        if (D.g_kind == HJ_G_ELLIPSE) P.rcst = 0.5f;
     }
     P.d = d;
     P.family = D.family;
@@ -473,12 +521,37 @@ int pick_c(int prec, int fam, int pr, int kind, int need)
     return -1;
 }
 
-// Threads per pair and components per thread for one launch.  Preference:
-// at most `pref` components per thread (fewer registers for the adjoint and
-// for FP64), then the fewest lanes.
+// Padded dimension of the one-thread-per-pair kernel for problem p and
+// kernel kind, or 0 when those kernels do not apply: fp32 context, smooth
+// non-convex family, Hopf principle, d <= R1_MAXD, RK4 with its own
+// quadrature, no lane-count override, and a functional, gradient, coordinate
+// or gradient descent kernel (conjugate gradients and the FP64 certificate
+// use the lane groups).
+int r1_c(const hj_ctx *ctx, int p, int kind)
+{
+    const hj_problem_desc &D = ctx->desc[p];
+    if (ctx->prec != 0 || D.family != HJ_FAM_SMOOTH_NONCONVEX || D.principle != HJ_HOPF || D.d > R1_MAXD) return 0;
+    if (ctx->tpp_override[p] != 0 || ctx->opts.quad != HJ_QUAD_RK4) return 0;
+    if (kind != K_EVAL && kind != K_GRAD && kind != K_CD && kind != K_GD) return 0;
+    const Registry &R = registry();
+    for (int c = D.d; c <= R1_MAXD; ++c)
+        if (R.r1[c].eval) return c;
+    return 0;
+}
+
+// Threads per pair and components per thread for one launch.  The
+// one-thread-per-pair kernels where they apply (reported as tpp 1 and a
+// negative C, the padded dimension); otherwise lane groups with at most
+// `pref` components per thread (fewer registers for the adjoint and for
+// FP64), then the fewest lanes.
 bool choose(const hj_ctx *ctx, int p, int kind, int *tpp_out, int *c_out)
 {
     const hj_problem_desc &D = ctx->desc[p];
+    if (const int c1 = r1_c(ctx, p, kind)) {
+        *tpp_out = 1;
+        *c_out = -c1;
+        return true;
+    }
     const int prec = (kind == K_CERT) ? ctx->prec : ctx->prec;
     int pref;
     if (kind == K_CERT) pref = 2;
@@ -503,6 +576,7 @@ bool choose(const hj_ctx *ctx, int p, int kind, int *tpp_out, int *c_out)
 const KSet &kset(const hj_ctx *ctx, int p, int c)
 {
     const hj_problem_desc &D = ctx->desc[p];
+    if (c < 0) return registry().r1[-c];
     return registry().k[ctx->prec][kfam(D.family)][kprin(D.principle)][c];
 }
 
@@ -1073,7 +1147,7 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
     ctx->last_stream = s;
     ctx->last_nq = n_queries;
     ctx->last_tpp = tpp_d[0];
-    ctx->last_c = c_d[0];
+    ctx->last_c = std::abs(c_d[0]);
     if (tc_eligible(ctx, 0) && kinds[0] != K_CD) {
         ctx->last_tpp = 1;  // one thread (and TMEM lane) per pair
         ctx->last_c = ctx->dev[0].geom.dp;
@@ -1369,6 +1443,9 @@ hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out)
         out->rk4_steps += (int64_t)c[3];
         out->n_pairs += (int64_t)c[5];
         out->algorithmic_flops += (double)c[3] * fm.fwd_step + (double)c[4] * fm.adj_step;
+        const double nf = nominal_fwd_step(D.family, D.principle, D.d, D.m, (int)ctx->opts.quad);
+        out->adjoint_steps += (int64_t)c[4];
+        out->nominal_flops += nf * (double)(c[3] + c[7]) + 3.0 * nf * (double)c[4];
         out->certify_flops += (double)c[7] * fm.fwd_step;
         if (p < (int)ctx->last_tc.size() && ctx->last_tc[p]) {
             const double d = D.d, m = D.m;

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include "hj.h"
+#include "hj_internal.h"
 
 namespace hjd {
 
@@ -56,6 +57,11 @@ struct ProbDev {
     const T *At;    // At[j*ldm + i] = A[i][j]   (for A gamma)
     const T *A;     // A[j*ldm + i]  = A[j][i]   (for A^T p)
     const T *Cm;    // Cm[j*ldm + i] = (B B^T)[j][i], symmetric
+    // The one-thread-per-pair kernels of the smooth non-convex family
+    // (hj_r1.cuh) read the per-component vectors as values carried in the
+    // kernel's parameters: w, the signs e, w e, and the Hopf data's
+    // g*(p) = sum_i p_i (g2_i p_i / 2 + ga_i) + rcst; all zero past d.
+    float rw[R1_MAXD], re[R1_MAXD], rew[R1_MAXD], rg2[R1_MAXD], rga[R1_MAXD], rcst;
 };
 
 // Solver constants on the device.

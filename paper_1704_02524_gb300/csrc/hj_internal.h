@@ -6,6 +6,7 @@
 namespace hjd {
 
 constexpr int MAXC = 10;  // largest components-per-thread instantiated
+constexpr int R1_MAXD = 32;  // largest d of the one-thread-per-pair kernels (hj_r1.cuh)
 
 using Launch = cudaError_t (*)(const void *args, int grid, cudaStream_t stream);
 
@@ -21,6 +22,9 @@ struct KSet {
 
 struct Registry {
     KSet k[2][9][2][MAXC + 1];  // [precision][family][principle][C]
+    // one-thread-per-pair kernels of the smooth non-convex family, fp32,
+    // Hopf principle, by padded dimension C (eval, grad, cd and gd only)
+    KSet r1[R1_MAXD + 1];
 };
 
 Registry &registry();

@@ -1,0 +1,644 @@
+// hj_r1.cuh -- one thread per (query, start) pair for the smooth non-convex
+// family H = c(x) Phi(p), c = 1 + sin(<w,x>)/2, Phi = sum_i e_i s(p_i),
+// s(q) = sqrt(q^2 + eps), under the Hopf principle, d <= 32.
+//
+// Structure of the characteristic field used here (Sec. 4.1's system with
+// this H): dp/dtau = Phi(p) c'(u) w is always parallel to w, and gamma enters
+// the field only through u = <w, gamma> (c and its derivatives are functions
+// of u).  Every RK4 stage adds a multiple of w to p and every stage field is
+// a function of (u, p), so the iterates of the discretised system are exactly
+//   p_n = v + B_n w,   u_n = <w, gamma_n>,
+// with the scalars (u_n, B_n) advanced by the RK4 combination of the stage
+// values
+//   du/dtau = <w, -c Phi'(p)> = -c D,  D = sum_i w_i e_i p_i / s_i,
+//   dB/dtau = Phi c',
+// and the Hopf running cost L = Phi (c - c' u) (Sec. 4.1) of the same stages.
+// The terminal term g*(p_N) - <x, v> needs p_N = v + B_N w only.  The result
+// is the RK4 functional of the general lane-group kernels (hj_device.cuh) up
+// to rounding: the same stages, the same weights, the same terminal term; the
+// 2d-dimensional state is carried as two scalars.
+//
+// The discrete adjoint (exact gradient of this functional) follows the
+// general adjoint_step stage by stage: with lam = (lam_gamma, lam_p), every
+// vector-Jacobian product of this family has its gamma-part along w
+// (rg = dE/du w), and the Hopf seed is (0, grad g*(p_N)), so
+// lam_gamma = alpha w stays a scalar multiple of w; the weights each stage
+// product needs reduce to the scalars a (lam_gamma's coefficient), Bw =
+// <weight_p, w> and the quadrature weight, and the p-part of each product is
+//   rp_i = e_i r_i (kd p_i - c eps a w_i r_i^2),  r_i = 1/s_i,
+// summed into lam_p.  The state checkpoints are the pairs (u_n, B_n): 8 bytes
+// per step, every step kept by default.
+//
+// Per pair the thread holds v and lam_p in registers (2d values); the
+// per-problem vectors (w, e, w e, the initial data's coefficients) are kernel
+// parameters, read as constant operands.  One thread per pair means no
+// shuffles: every dot product is a register sum.  The four RK4 stages and the
+// four stage products of the adjoint run as loops, not unrolled, so that the
+// d-wide stage body exists once per use in the code: with every stage inlined
+// the kernel's instruction stream outgrew the instruction cache (the
+// dominant stall, measured).  The stage scalars the products need are kept
+// per thread in shared memory.
+#pragma once
+
+#include "hj_kernels.cuh"
+
+namespace hjd {
+namespace r1 {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int REC = 8;  // floats per stage record in shared memory
+
+// Resident blocks of BLOCK threads per SM the register allocation aims at.
+// A problem with d <= R1_MAXD runs with C = the smallest instantiated size
+// >= d; padded components carry w = e = g2 = ga = 0 and drop out of every sum.
+template <int C>
+constexpr int min_blocks() { return C <= 16 ? 4 : (C <= 20 ? 3 : 2); }
+
+// Scalars of one RK4 stage.
+struct St {
+    float u, B;       // stage input: u = <w, gamma>, p = v + B w
+    float c, c1, c2;  // c(u), c'(u), c''(u)
+    float phi, D;     // Phi(p), sum_i w_i e_i p_i / s_i
+};
+
+// Per-thread stage records: rec points at the thread's column of a
+// [4 * REC][BLOCK] shared array.
+__device__ __forceinline__ void put(float *rec, int st, const St &s)
+{
+    float *r = rec + st * REC * BLOCK;
+    r[0] = s.u; r[BLOCK] = s.B; r[2 * BLOCK] = s.c; r[3 * BLOCK] = s.c1;
+    r[4 * BLOCK] = s.c2; r[5 * BLOCK] = s.phi; r[6 * BLOCK] = s.D;
+}
+__device__ __forceinline__ St get(const float *rec, int st)
+{
+    const float *r = rec + st * REC * BLOCK;
+    return St{r[0], r[BLOCK], r[2 * BLOCK], r[3 * BLOCK], r[4 * BLOCK], r[5 * BLOCK], r[6 * BLOCK]};
+}
+
+// The sums of a stage at input (u, B): Phi and D, with the reciprocals r_i
+// kept when KEEP.  Two partial sums each shorten the dependency chains.
+template <int C, bool KEEP>
+__device__ __forceinline__ void stage(const ProbDev<float> &P, const float *v, float eps, float u, float B, St &s,
+                                      float *r)
+{
+    float ph0 = 0.f, ph1 = 0.f, d0 = 0.f, d1 = 0.f;
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        const float p = fmaf(B, P.rw[i], v[i]);
+        const float q = fmaf(p, p, eps);
+        const float ri = rsqrtf(q);
+        if constexpr (KEEP) r[i] = ri;
+        if (i & 1) {
+            ph1 = fmaf(P.re[i], q * ri, ph1);
+            d1 = fmaf(P.rew[i], ri * p, d1);
+        } else {
+            ph0 = fmaf(P.re[i], q * ri, ph0);
+            d0 = fmaf(P.rew[i], ri * p, d0);
+        }
+    }
+    s.u = u;
+    s.B = B;
+    s.phi = ph0 + ph1;
+    s.D = d0 + d1;
+    float su, cu;
+    __sincosf(u, &su, &cu);
+    s.c = fmaf(0.5f, su, 1.f);
+    s.c1 = 0.5f * cu;
+    s.c2 = -0.5f * su;
+}
+
+// Stage rates: du/dtau, dB/dtau and the Hopf running cost.
+__device__ __forceinline__ float rate_u(const St &s) { return -s.c * s.D; }
+__device__ __forceinline__ float rate_B(const St &s) { return s.phi * s.c1; }
+__device__ __forceinline__ float cost(const St &s) { return s.phi * (s.c - s.c1 * s.u); }
+
+// RK4 bookkeeping of stage st (0..3) with rates k: the weighted sums a (k1 +
+// 2 k2 + 2 k3 + k4) and the next stage's input z + h2 k or z + h k.
+__device__ __forceinline__ void rk4_acc(int st, float k, float &a)
+{
+    if (st == 0) a = k;
+    else if (st < 3) a = fmaf(2.f, k, a);
+    else a += k;
+}
+
+// One classical RK4 step of (u, B) and the running cost; the four stage
+// records go to rec when it is non-null.
+template <int C>
+__device__ __forceinline__ void step(const ProbDev<float> &P, const float *v, float eps, float h, float &u, float &B,
+                                     float &dQ, float *rec)
+{
+    const float h2 = 0.5f * h, h6 = h / 6.f;
+    float su = u, sB = B, au = 0.f, aB = 0.f, aL = 0.f;
+#pragma unroll 1
+    for (int st = 0; st < 4; ++st) {
+        St s;
+        stage<C, false>(P, v, eps, su, sB, s, nullptr);
+        if (rec) put(rec, st, s);
+        const float ku = rate_u(s), kB = rate_B(s);
+        rk4_acc(st, ku, au);
+        rk4_acc(st, kB, aB);
+        rk4_acc(st, cost(s), aL);
+        const float hs = (st == 2) ? h : h2;
+        su = fmaf(hs, ku, u);
+        sB = fmaf(hs, kB, B);
+    }
+    u = fmaf(h6, au, u);
+    B = fmaf(h6, aB, B);
+    dQ = h6 * aL;
+}
+
+// <w, x> and <a, b>.
+template <int C>
+__device__ __forceinline__ float dot_w(const ProbDev<float> &P, const float *x)
+{
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        if (i & 1) a1 = fmaf(P.rw[i], x[i], a1);
+        else a0 = fmaf(P.rw[i], x[i], a0);
+    }
+    return a0 + a1;
+}
+template <int C>
+__device__ __forceinline__ float dot(const float *a, const float *b)
+{
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        if (i & 1) a1 = fmaf(a[i], b[i], a1);
+        else a0 = fmaf(a[i], b[i], a0);
+    }
+    return a0 + a1;
+}
+
+// Hopf terminal term g*(p_N) - <x, v> (+ the ellipse data's constant), with
+// g*(p) = sum_i p_i (g2_i p_i / 2 + ga_i) and xv = <x, v>; the seed grad g*
+// goes to lp when it is non-null.
+template <int C>
+__device__ __forceinline__ float terminal(const ProbDev<float> &P, float xv, const float *v, float B, float *lp)
+{
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        const float p = fmaf(B, P.rw[i], v[i]);
+        const float val = p * fmaf(0.5f * P.rg2[i], p, P.rga[i]);
+        if (i & 1) a1 += val;
+        else a0 += val;
+        if (lp) lp[i] = fmaf(P.rg2[i], p, P.rga[i]);
+    }
+    return (a0 + a1 - xv) + P.rcst;
+}
+
+// Functional G(v) (Hopf) from u0 = <w, x> and xv = <x, v>.  With ck != null
+// the step inputs (u_n, B_n) of every K-th step are stored there (the
+// adjoint's checkpoints).  B_N is returned in Bn.
+template <int C>
+__device__ __forceinline__ float functional(const ProbDev<float> &P, int kahan, float u0, float xv, const float *v,
+                                            float t, int N, float2 *ck, int K, float &Bn)
+{
+    if (N < 1 || N > MAX_N) {
+        Bn = NAN;
+        return NAN;
+    }
+    const float eps = P.s_eps, h = t / (float)N;
+    float u = u0, B = 0.f, Q = 0.f, Qc = 0.f;
+    for (int n = 0, kk = 0; n < N; ++n) {
+        if (ck) {
+            if (kk == 0) ck[n / K] = make_float2(u, B);
+            if (++kk == K) kk = 0;
+        }
+        float dQ;
+        step<C>(P, v, eps, h, u, B, dQ, nullptr);
+        add_q(kahan, dQ, Q, Qc);
+    }
+    Bn = B;
+    return terminal<C>(P, xv, v, B, nullptr) + Q;
+}
+
+// The functional with gamma carried along as a vector, for the certificate
+// (Sec. 4.3): gamma advances by the RK4 combination of the stage rates
+// -c Phi'(p); (u, B, Q) advance exactly as in functional().  Returns G; gam
+// holds x on entry and gamma(0) on exit, Bn gets B_N.
+template <int C>
+__device__ __forceinline__ float functional_gamma(const ProbDev<float> &P, int kahan, float u0, float xv,
+                                                  const float *v, float t, int N, float *gam, float &Bn)
+{
+    if (N < 1 || N > MAX_N) {
+        Bn = NAN;
+        return NAN;
+    }
+    const float eps = P.s_eps, h = t / (float)N, h2 = 0.5f * h, h6 = h / 6.f;
+    float u = u0, B = 0.f, Q = 0.f, Qc = 0.f;
+    for (int n = 0; n < N; ++n) {
+        float ag[C];
+        float su = u, sB = B, au = 0.f, aB = 0.f, aL = 0.f;
+#pragma unroll 1
+        for (int st = 0; st < 4; ++st) {
+            float r[C];
+            St s;
+            stage<C, true>(P, v, eps, su, sB, s, r);
+#pragma unroll
+            for (int i = 0; i < C; ++i) {
+                const float p = fmaf(sB, P.rw[i], v[i]);
+                const float kg = -s.c * ((P.re[i] * r[i]) * p);
+                if (st == 0) ag[i] = kg;
+                else if (st < 3) ag[i] = fmaf(2.f, kg, ag[i]);
+                else gam[i] = fmaf(h6, ag[i] + kg, gam[i]);
+            }
+            const float ku = rate_u(s), kB = rate_B(s);
+            rk4_acc(st, ku, au);
+            rk4_acc(st, kB, aB);
+            rk4_acc(st, cost(s), aL);
+            const float hs = (st == 2) ? h : h2;
+            su = fmaf(hs, ku, u);
+            sB = fmaf(hs, kB, B);
+        }
+        u = fmaf(h6, au, u);
+        B = fmaf(h6, aB, B);
+        add_q(kahan, h6 * aL, Q, Qc);
+    }
+    Bn = B;
+    return terminal<C>(P, xv, v, B, nullptr) + Q;
+}
+
+// Vector-Jacobian product of one stage with scalar weights: gamma weight
+// a w, p weight with <weight_p, w> = Bw, quadrature weight bb.  Adds the
+// p-part to lp; returns the gamma-part's coefficient (dE/du) in R and
+// <w, p-part> in Wr.  The stage's p and reciprocals are recomputed; the stage
+// input is made to depend on `after` (the previous product's result, finite
+// in any finite solve) so that this happens in order instead of being
+// hoisted and kept live across the step.
+template <int C>
+__device__ __forceinline__ void vjp(const ProbDev<float> &P, const float *v, float eps, const St &s, float a,
+                                    float Bw, float bb, float after, float *lp, float &R, float &Wr)
+{
+    const float A = a * s.D;
+    float dEdu = fmaf(-s.c1, A, s.phi * s.c2 * Bw);
+    dEdu -= bb * s.phi * s.c2 * s.u;
+    const float kd = fmaf(s.c1, Bw, bb * (s.c - s.c1 * s.u));
+    const float cea = s.c * eps * a;
+    const float Bs = fmaf(0.f, after, s.B);
+    float w0 = 0.f, w1 = 0.f;
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        const float p = fmaf(Bs, P.rw[i], v[i]);
+        const float ri = rsqrtf(fmaf(p, p, eps));
+        const float tt = fmaf(-cea * P.rw[i], ri * ri, kd * p);
+        const float rp = (P.re[i] * ri) * tt;
+        lp[i] += rp;
+        if (i & 1) w1 = fmaf(P.rw[i], rp, w1);
+        else w0 = fmaf(P.rw[i], rp, w0);
+    }
+    R = dEdu;
+    Wr = w0 + w1;
+}
+
+// Adjoint of one RK4 step at input (u, B): lam = (alpha w, lp) -> lam_n.
+// The rebuild (the forward step from (u, B)) leaves the four stage records
+// in rec; the products run from stage 4 down to stage 1 with the weights of
+// the RK4 adjoint: (h/6, h/3, h/3, h/6) on lam and the quadrature, and
+// (h, h/2, h/2) on the previous stage's product.
+template <int C>
+__device__ __forceinline__ void adjoint_step(const ProbDev<float> &P, const float *v, float eps, float h, float u,
+                                             float B, float &alpha, float *lp, float *rec)
+{
+    const float h2 = 0.5f * h, h3 = h / 3.f, h6 = h / 6.f;
+    float un = u, Bn = B, dQ;
+    step<C>(P, v, eps, h, un, Bn, dQ, rec);
+    const float Lw = dot_w<C>(P, lp);
+    float R = 0.f, W = 0.f, sumR = 0.f;
+#pragma unroll 1
+    for (int j = 3; j >= 0; --j) {
+        const St s = get(rec, j);
+        const float wl = (j == 0 || j == 3) ? h6 : h3;
+        const float wp = (j == 2) ? h : h2;
+        vjp<C>(P, v, eps, s, fmaf(wl, alpha, wp * R), fmaf(wl, Lw, wp * W), wl, W, lp, R, W);
+        sumR += R;
+    }
+    alpha += sumR;
+}
+
+// Gradient of G with respect to v, less the -x of the Hopf terminal term:
+// gr gets lam_p(0) (the caller subtracts x).  Returns G.  ck holds
+// ceil(N/K) checkpoints, seg K states (thread-private).
+template <int C>
+__device__ __forceinline__ float gradient(const ProbDev<float> &P, int kahan, int K, float u0, float xv, const float *v,
+                                          float t, int N, float *gr, float2 *ck, float2 *seg, float *rec)
+{
+    if (N < 1 || N > MAX_N) {
+#pragma unroll
+        for (int i = 0; i < C; ++i) gr[i] = NAN;
+        return NAN;
+    }
+    const float eps = P.s_eps, h = t / (float)N;
+    float Bn;
+    const float F = functional<C>(P, kahan, u0, xv, v, t, N, ck, K, Bn);
+    terminal<C>(P, xv, v, Bn, gr);  // seed lam_p = grad g*(p_N), kept in gr
+    float alpha = 0.f;
+    if (K == 1) {
+        float2 cur = ck[N - 1];
+        for (int n = N - 1; n >= 0; --n) {
+            const float2 nxt = ck[n > 0 ? n - 1 : 0];
+            adjoint_step<C>(P, v, eps, h, cur.x, cur.y, alpha, gr, rec);
+            cur = nxt;
+        }
+    } else {
+        const int nseg = (N + K - 1) / K;
+        for (int sg = nseg - 1; sg >= 0; --sg) {
+            const int n0 = sg * K, n1 = min(N, n0 + K);
+            float u = ck[sg].x, B = ck[sg].y;
+            for (int n = n0; n < n1; ++n) {
+                seg[n - n0] = make_float2(u, B);
+                if (n + 1 < n1) {
+                    float dQ;
+                    step<C>(P, v, eps, h, u, B, dQ, nullptr);
+                }
+            }
+            for (int n = n1 - 1; n >= n0; --n)
+                adjoint_step<C>(P, v, eps, h, seg[n - n0].x, seg[n - n0].y, alpha, gr, rec);
+        }
+    }
+    return F;
+}
+
+// Checkpoint interval: the caller's, else 1 (a checkpoint is 8 bytes).
+__device__ __forceinline__ int ck_interval(int N, int fixed)
+{
+    int K = fixed > 0 ? fixed : 1;
+    K = max(K, (N + MAX_N - 1) / MAX_N);
+    return min(K, MAX_SEG);
+}
+
+template <int C>
+__device__ __forceinline__ void load_vec(const float *row, int d, float *out)
+{
+#pragma unroll
+    for (int i = 0; i < C; ++i) out[i] = (i < d) ? __ldg(row + i) : 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// Rows: functional values and gradients (one thread per row).
+// ---------------------------------------------------------------------------
+template <int C>
+__global__ void __launch_bounds__(BLOCK, min_blocks<C>()) k_eval(RowArgs<float> a)
+{
+    const long long stride = (long long)gridDim.x * BLOCK;
+    for (long long r = (long long)blockIdx.x * BLOCK + threadIdx.x; r < a.n; r += stride) {
+        if (a.pidx && a.pidx[r] != a.pfilter) continue;
+        const int N = a.nsteps ? a.nsteps[r] : a.n_default;
+        float x[C], v[C], Bn;
+        load_vec<C>(a.x + r * a.P.ld, a.P.d, x);
+        load_vec<C>(a.v + r * a.P.ld, a.P.d, v);
+        a.F[r] = functional<C>(a.P, a.kahan, dot_w<C>(a.P, x), dot<C>(x, v), v, a.t[r], N, nullptr, 1, Bn);
+    }
+}
+
+template <int C>
+__global__ void __launch_bounds__(BLOCK, min_blocks<C>()) k_grad(RowArgs<float> a)
+{
+    __shared__ float s_rec[4 * REC][BLOCK];
+    float2 ck[MAX_N], seg[MAX_SEG];
+    float *rec = &s_rec[0][threadIdx.x];
+    const long long stride = (long long)gridDim.x * BLOCK;
+    for (long long r = (long long)blockIdx.x * BLOCK + threadIdx.x; r < a.n; r += stride) {
+        if (a.pidx && a.pidx[r] != a.pfilter) continue;
+        const int N = a.nsteps ? a.nsteps[r] : a.n_default;
+        float x[C], v[C], gr[C];
+        load_vec<C>(a.x + r * a.P.ld, a.P.d, x);
+        load_vec<C>(a.v + r * a.P.ld, a.P.d, v);
+        const int K = ck_interval(N, a.ck_interval);
+        const float F = gradient<C>(a.P, a.kahan, K, dot_w<C>(a.P, x), dot<C>(x, v), v, a.t[r], N, gr, ck, seg, rec);
+        float *g = a.grad + r * a.P.ld;
+#pragma unroll
+        for (int i = 0; i < C; ++i)
+            if (i < a.P.d) g[i] = gr[i] - x[i];
+        if (a.F) a.F[r] = F;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent descent, one thread per pair: Algorithm 1 (MODE DESC_CD, cyclic
+// coordinate descent with finite differences) or gradient descent with the
+// adjoint (DESC_GD), the same iteration rules, stop tests, coarse-to-fine
+// phases, certificate and outputs as k_desc.  Threads without a pair take
+// the next one from the problem's work list (one atomic per warp) between
+// iterations.  v lives in registers; the per-coordinate steps and the
+// previous derivatives in shared memory ([component][thread],
+// conflict-free); x is read from global memory (cached) once per iteration.
+// ---------------------------------------------------------------------------
+template <int C, int MODE>
+__global__ void __launch_bounds__(BLOCK, min_blocks<C>()) k_desc(DescArgs<float> a)
+{
+    __shared__ float s_al[C][BLOCK], s_pr[C][BLOCK];
+    __shared__ float s_rec[MODE == DESC_GD ? 4 * REC : 1][BLOCK];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int d = a.P.d;
+    const long long n = a.wl_count[a.problem];
+    const long long begin = a.seg_begin[a.problem];
+    const float eps_stop = (float)a.S.eps;
+    const float fd_h = (float)a.S.fd_h;
+    const bool central = (a.S.grad != HJ_GRAD_FD_FORWARD);
+    const bool coarse = (MODE != DESC_CD) && a.phase == 1;
+    float2 ck[MODE == DESC_GD ? MAX_N : 1], seg[MODE == DESC_GD ? MAX_SEG : 1];
+    float *rec = &s_rec[0][tid];
+    unsigned long long n_it = 0, n_f = 0, n_g = 0, n_rk = 0, n_adj = 0, n_pairs = 0, n_sumN = 0, n_cert = 0;
+
+    bool active = false, exhausted = false;
+    long long pid = 0, q = 0;
+    int N = 1, Ncur = 1, it = 0, count = 0, kper = 0, bad = 0;
+    float t = 0.f, v[C];
+#pragma unroll
+    for (int i = 0; i < C; ++i) v[i] = 0.f;
+
+    for (;;) {
+        // ---- refill: one atomic per warp for all lanes that need a pair ------
+        const bool need = !active && !exhausted;
+        const unsigned nm = __ballot_sync(FULL, need);
+        if (nm) {
+            const int leader = __ffs(nm) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(a.cursor + a.problem, __popc(nm));
+            base = __shfl_sync(FULL, base, leader);
+            if (need) {
+                const long long j = (long long)base + __popc(nm & ((1u << lane) - 1u));
+                if (j >= n) {
+                    exhausted = true;
+                } else {
+                    pid = a.wl[begin + j];
+                    q = a.pair_q[pid];
+                    const int slot = a.pair_slot[pid], round = a.pair_round[pid];
+                    N = a.nsteps ? a.nsteps[q] : a.S.n_default;
+                    t = a.t[q];
+#pragma unroll
+                    for (int i = 0; i < C; ++i) {
+                        s_al[i][tid] = (float)a.S.step;
+                        s_pr[i][tid] = 0.f;
+                    }
+                    if (a.phase == 2) {
+                        load_vec<C>(a.vfin + pid * a.P.ld, d, v);  // the coarse level's v
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < C; ++i)
+                            v[i] = (i < d) ? start_component<float>(a.S.seed, a.q_begin + q, slot, round, i,
+                                                                    a.S.guess_dist)
+                                           : 0.f;
+                    }
+                    it = count = kper = bad = 0;
+                    Ncur = coarse ? max(1, N / a.S.coarse_div) : N;
+                    active = true;
+                }
+            }
+        }
+        if (!__any_sync(FULL, active)) break;
+        if (!active) continue;
+
+        const float *xr = a.x + q * a.P.ld;
+        float u0, xv;  // <w, x>, <x, v>
+        {
+            float x[C];
+            load_vec<C>(xr, d, x);
+            u0 = dot_w<C>(a.P, x);
+            xv = dot<C>(x, v);
+        }
+        // ---- one iteration -----------------------------------------------------
+        bool stop = (it >= a.S.max_iters), conv = false;
+        const float eps_lvl = coarse ? (float)a.S.coarse_eps : eps_stop;
+        if (!stop) {
+            if constexpr (MODE == DESC_GD) {
+                float gr[C];
+                const int K = ck_interval(Ncur, a.S.ck_interval);
+                gradient<C>(a.P, a.S.kahan, K, u0, xv, v, t, Ncur, gr, ck, seg, rec);
+                n_g++;
+                n_rk += Ncur;
+                n_adj += Ncur;
+                float big = 0.f;
+                bool fin = true;
+#pragma unroll
+                for (int i = 0; i < C; ++i) {
+                    const float g = gr[i] - ((i < d) ? __ldg(xr + i) : 0.f);
+                    float al = s_al[i][tid];
+                    if (a.S.adapt) {
+                        const float prod = g * s_pr[i][tid];
+                        if (prod < 0.f) al *= (float)a.S.shrink;
+                        else if (prod > 0.f) al = fminf(al * (float)a.S.grow, (float)a.S.step_max);
+                    }
+                    const float st = al * g;
+                    fin = fin && isfinite(st);
+                    v[i] -= st;
+                    big = fmaxf(big, fabsf(st));
+                    s_pr[i][tid] = g;
+                    s_al[i][tid] = al;
+                }
+                if (!fin) big = INFINITY;
+                ++it;
+                if (!(big < INFINITY)) { bad = 1; stop = true; }
+                if (a.S.halving_period > 0 && it % a.S.halving_period == 0) {
+#pragma unroll
+                    for (int i = 0; i < C; ++i) s_al[i][tid] *= 0.5f;
+                }
+                if (big < eps_lvl) conv = stop = true;
+            } else {
+                const int jc = it % d;
+                const float xj = __ldg(xr + jc);
+                float vp[C], Bn;
+#pragma unroll
+                for (int i = 0; i < C; ++i) vp[i] = v[i] + ((i == jc) ? fd_h : 0.f);
+                const float Fp = functional<C>(a.P, a.S.kahan, u0, fmaf(xj, fd_h, xv), vp, t, N, nullptr, 1, Bn);
+#pragma unroll
+                for (int i = 0; i < C; ++i) vp[i] = v[i] - ((central && i == jc) ? fd_h : 0.f);
+                const float Fm = functional<C>(a.P, a.S.kahan, u0, central ? fmaf(-xj, fd_h, xv) : xv, vp, t, N,
+                                               nullptr, 1, Bn);
+                n_f += 2;
+                n_rk += 2 * N;
+                const float dj = central ? (Fp - Fm) / (2.f * fd_h) : (Fp - Fm) / fd_h;
+                float al = s_al[jc][tid];
+                if (a.S.adapt) {
+                    const float prod = dj * s_pr[jc][tid];
+                    if (prod < 0.f) al *= (float)a.S.shrink;
+                    else if (prod > 0.f) al = fminf(al * (float)a.S.grow, (float)a.S.step_max);
+                    s_pr[jc][tid] = dj;
+                }
+                const float st = al * dj;
+#pragma unroll
+                for (int i = 0; i < C; ++i)
+                    if (i == jc) v[i] -= st;
+                ++it;
+                if (!isfinite(st)) { bad = 1; stop = true; }
+                // steps 3-4 of Algorithm 1: reset on a move > eps, count a move < eps
+                if (fabsf(st) > eps_stop) count = 0;
+                else if (fabsf(st) < eps_stop) ++count;
+                s_al[jc][tid] = al;
+                if (a.S.halving_period > 0 && ++kper == a.S.halving_period) {
+                    kper = 0;
+#pragma unroll
+                    for (int i = 0; i < C; ++i) s_al[i][tid] *= 0.5f;
+                }
+                if (count >= d) conv = stop = true;
+            }
+            if (it >= a.S.max_iters) stop = true;
+        }
+        // ---- finished pair: certificate at the final v, then write it out -----
+        if (stop && a.phase == 1) {
+            n_it += it;
+            float *vr = a.vfin + pid * a.P.ld;
+#pragma unroll
+            for (int i = 0; i < C; ++i)
+                if (i < d) vr[i] = v[i];
+            a.iters[pid] = it;
+            a.flags[pid] = (uint8_t)(bad << 1);
+            active = false;
+        } else if (stop) {
+            const int cap = (!conv && !bad) ? 1 : 0;
+            n_it += it;
+            n_pairs++;
+            n_sumN += N;
+            float gam[C], Bn;
+            load_vec<C>(xr, d, gam);
+            const float F = functional_gamma<C>(a.P, a.S.kahan, u0, dot<C>(gam, v), v, t, N, gam, Bn);
+            // Hopf residual |gamma(0) - grad g*(p(0))| / (1 + |gamma(0)|)
+            float num = 0.f, den = 0.f;
+#pragma unroll
+            for (int i = 0; i < C; ++i) {
+                const float p = fmaf(Bn, a.P.rw[i], v[i]);
+                const float diff = gam[i] - fmaf(a.P.rg2[i], p, a.P.rga[i]);
+                num = fmaf(diff, diff, num);
+                den = fmaf(gam[i], gam[i], den);
+            }
+            const float r = sqrtf(num) / (1.f + sqrtf(den));
+            n_cert += N;
+            float *vr = a.vfin + pid * a.P.ld;
+#pragma unroll
+            for (int i = 0; i < C; ++i)
+                if (i < d) vr[i] = v[i];
+            const int prior = (a.phase == 2) ? a.iters[pid] : 0;
+            const uint8_t fprior = (a.phase == 2) ? (uint8_t)(a.flags[pid] & 2) : (uint8_t)0;
+            a.iters[pid] = prior + it;
+            a.flags[pid] = (uint8_t)(cap | (bad << 1) | fprior);
+            const bool fin = isfinite(F) && isfinite(r);
+            uint8_t pass;
+            if (!fin) pass = 0;
+            else if ((double)r < CERT_BAND_LO * a.tol) pass = 1;
+            else if ((double)r > CERT_BAND_HI * a.tol) pass = 0;
+            else pass = 2;
+            a.pF[pid] = (double)F;
+            a.pR[pid] = (double)r;
+            a.pP[pid] = pass;
+            if (pass == 2) {
+                const int pos = atomicAdd(a.amb_count + a.problem, 1);
+                a.amb_wl[begin + pos] = (int32_t)pid;
+            }
+            active = false;
+        }
+    }
+    if (a.stats) {
+        unsigned long long c[8] = {n_it, n_f, n_g, n_rk, n_adj, n_pairs, n_sumN, n_cert};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_xor_sync(FULL, c[k], o);
+            if (lane == 0 && c[k]) atomicAdd(a.stats + k, c[k]);
+        }
+    }
+}
+
+}  // namespace r1
+}  // namespace hjd

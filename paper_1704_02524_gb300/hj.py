@@ -59,7 +59,8 @@ class hj_solve_info(C.Structure):
                 ("algorithmic_flops", C.c_double), ("certify_flops", C.c_double), ("threads_per_pair", C.c_int),
                 ("comps_per_thread", C.c_int), ("descent_launches", C.c_int), ("descent_ms", C.c_double),
                 ("certify_ms", C.c_double), ("total_ms", C.c_double), ("kernel_launches", C.c_int64),
-                ("descent_ms_round0", C.c_double), ("tensor_flops", C.c_double)]
+                ("descent_ms_round0", C.c_double), ("tensor_flops", C.c_double), ("adjoint_steps", C.c_int64),
+                ("nominal_flops", C.c_double)]
 
 
 _lib = None

@@ -738,3 +738,84 @@ def test_caller_supplied_solve_outputs_of_the_wrong_shape_or_type_are_refused(hj
         torch.cuda.synchronize()
         assert np.all(np.isfinite(phi.cpu().numpy()))
     ctx.close()
+
+
+@pytest.mark.parametrize("d", [2, 5, 8, 13, 16, 20, 27, 32])
+def test_one_thread_per_pair_kernels_match_oracle_and_lane_groups(hj, d):
+    # the smooth non-convex Hopf family at d <= 32 runs one thread per pair
+    # with (u, B) as its state; every instantiated size, exact and padded,
+    # against the oracle's functional and adjoint gradient, and against the
+    # lane-group kernels forced by a lane-count override
+    spec = _spec(W.FAM_SMOOTH_NONCONVEX, W.HOPF, d, seed=d, s_eps=1e-3, n_neg=min(2, d))
+    ctx = hj.hj_create([spec], hj.opts_from_dict(W.solver_constants(), hj.HJ_PREC_FP32, 64), 0)
+    n = 150  # more than one block, ragged
+    x, v, t, N = _rows(n, d, 100 + d, "fp32")
+    args = (_t(x, torch.float32), _t(t, torch.float32), _t(v, torch.float32), _t(N, torch.int32))
+    E = hj.hj_eval_functional(ctx, *args).cpu().numpy()
+    F, G = (a.cpu().numpy() for a in hj.hj_grad(ctx, *args))
+    hj.hj_set_tuning(ctx, 0, 4 if d > 4 else 2, 0)
+    F4, G4 = (a.cpu().numpy() for a in hj.hj_grad(ctx, *args))
+    ctx.close()
+    P = oracle_problem(spec)
+    for i in range(n):
+        Fo, Go = O.gradient(P, x[i], t[i], int(N[i]), v[i])
+        assert rel_err(E[i], Fo) <= 2e-5 and rel_err(F[i], Fo) <= 2e-5, (i, E[i], F[i], Fo)
+        scale = 1 + np.abs(Go).max()
+        assert np.abs(G[i] - Go).max() <= 5e-4 * scale, (i, N[i])
+        assert np.abs(G[i] - G4[i]).max() <= 1e-3 * scale
+    assert np.all(rel_err(F, F4) <= 4e-5)
+
+
+def test_one_thread_per_pair_gradient_is_the_same_for_every_checkpoint_interval(hj):
+    # the (u, B) checkpoints every K steps with the segment recomputed: the
+    # recomputed states repeat the forward arithmetic, so every K (dividing N
+    # or not) gives the K = 1 gradient bit for bit, for N across [1, 256]
+    spec = _spec(W.FAM_SMOOTH_NONCONVEX, W.HOPF, 20, seed=11, s_eps=1e-2)
+    ctx = hj.hj_create([spec], hj.opts_from_dict(W.solver_constants(), hj.HJ_PREC_FP32, 64), 0)
+    n = 40
+    x, v, t, _ = _rows(n, 20, 21, "fp32")
+    N = np.array([1, 2, 5, 17, 64, 100, 255, 256] * 5)[:n].astype(np.int32)
+    args = (_t(x, torch.float32), _t(t, torch.float32), _t(v, torch.float32), _t(N, torch.int32))
+    F1, G1 = (a.cpu().numpy() for a in hj.hj_grad(ctx, *args))
+    for ck in (2, 3, 8, 16):
+        hj.hj_set_tuning(ctx, 0, 0, ck)
+        F, G = (a.cpu().numpy() for a in hj.hj_grad(ctx, *args))
+        assert np.array_equal(F, F1) and np.array_equal(G, G1), ck
+    ctx.close()
+    P = oracle_problem(spec)
+    for i in range(n):
+        Fo, Go = O.gradient(P, x[i], t[i], int(N[i]), v[i])
+        assert rel_err(F1[i], Fo) <= 2e-5
+        assert np.abs(G1[i] - Go).max() <= 5e-4 * (1 + np.abs(Go).max()), (i, N[i])
+
+
+def test_d20_hopf_solve_runs_one_thread_per_pair(hj):
+    wl = W.c3_smooth_nonconvex(nq=64)
+    ctx = hj.hj_create(wl.problems, hj.opts_from_dict(wl.solver, hj.HJ_PREC_FP32, 64), 0)
+    hj.hj_solve(ctx, _t(wl.x, torch.float32), _t(wl.t, torch.float32))
+    info = hj.hj_last_solve_info(ctx)
+    ctx.close()
+    assert info["threads_per_pair"] == 1 and info["comps_per_thread"] == 20
+    # nominal work: 64 d per forward step, an adjoint step counted as three more
+    assert info["nominal_flops"] == pytest.approx(64 * 20 * (info["rk4_steps"] + 3 * info["adjoint_steps"]),
+                                                  rel=0.05)
+
+
+@pytest.mark.parametrize("split", [[0, 100, 200], [0, 1, 77, 200]])
+def test_solve_split_into_query_ranges_equals_the_unsplit_solve(hj, split):
+    # the multi-GPU partition on the product path: consecutive query ranges
+    # solved by separate hj_solve calls with q_begin = the range's first
+    # global query index draw the same Philox starts as one unsplit solve, so
+    # phi, v and status agree bit for bit (one GPU here; one range per rank
+    # under torchrun)
+    wl = W.c3_smooth_nonconvex(nq=200)
+    ctx = hj.hj_create(wl.problems, hj.opts_from_dict(wl.solver, hj.HJ_PREC_FP32, 64), 0)
+    x, t = _t(wl.x, torch.float32), _t(wl.t, torch.float32)
+    phi, v, st = (a.cpu().numpy() for a in hj.hj_solve(ctx, x, t))
+    parts = []
+    for a, b in zip(split[:-1], split[1:]):
+        parts.append([o.cpu().numpy() for o in hj.hj_solve(ctx, x[a:b].contiguous(), t[a:b].contiguous(), q_begin=a)])
+    ctx.close()
+    assert np.array_equal(np.concatenate([p[0] for p in parts]), phi)
+    assert np.array_equal(np.concatenate([p[1] for p in parts]), v)
+    assert np.array_equal(np.concatenate([p[2] for p in parts]), st)
