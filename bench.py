@@ -65,16 +65,22 @@ WORKLOADS = {
     "evans_d2_hopf_paper": (lambda nq: W.evans_ex4(n_side=max(1, int(round(nq ** 0.5)))), 16384,
                             "points/s (Example 4 Evans-type H, d=2 grid, the paper's numerics)",
                             "Algorithm 1, forward differences, forward Euler with the rectangle rule"),
+    "quad_iso_d2_lax": (lambda nq: W.c1_quad_iso(nq=min(nq, 64)), 64,
+                        "queries/s (d=2 Lax, H = |p|^2/2, FP64, the 8x8 grid)",
+                        "Algorithm 1 with central differences, exactly 200 sweeps, 4 starts"),
 }
-CPU_SAMPLE = 64          # queries of the oracle timing sample (cpu_baseline)
+CPU_SAMPLE = 64          # queries of the oracle timing sample (cpu_baseline, all host cores)
+CPU_SAMPLE_1 = 8         # queries of the one-core oracle timing sample
 REF_SAMPLE = 64          # queries per step of the reference arm
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) of the dominant descent launch of a 4,096-query
-# case (d=20: round 0's fine-level launch; d=64: the tile kernel's launch),
-# from ncu captures of the current kernels on a GB300 (dram__bytes_read.sum +
-# dram__bytes_write.sum); the launch's traffic grows with the number of
-# (query, start) pairs, so it is scaled by queries / 4096.
-TRAFFIC_4096 = {"smooth_nonconvex_d20_hopf": 16.677e9 + 20.430e9, "linear_quad_d64_lax": 28.598e9 + 42.637e9}
+# DRAM bytes (read + write) of the dominant descent launch of a smaller case
+# (d=20: round 0's fine-level launch; d=64: the tile kernel's launch), from
+# ncu captures of the current kernels on a GB300 (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by workload: (queries captured, bytes).  The
+# launch's traffic grows with the number of (query, start) pairs, so it is
+# scaled by queries / queries captured.  None: not captured for the current
+# kernel.
+TRAFFIC = {"smooth_nonconvex_d20_hopf": None, "linear_quad_d64_lax": (4096, 28.598e9 + 42.637e9)}
 
 
 def _args():
@@ -87,7 +93,13 @@ def _args():
     ap.add_argument("--nq", type=int, default=0, help="queries (pairs for mixed_persistent); 0: the workload's size")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain CD-FD measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
-    ap.add_argument("--tpp", type=int, default=0, help="threads per pair of the descent (0: library choice)")
+    ap.add_argument("--tpp", type=int, default=0,
+                    help="threads per pair of the descent (0: library choice; -1 / -2: one / two lanes per pair "
+                         "of the one-pair-per-thread kernels in every round)")
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "fp64"],
+                    help="arithmetic of the solve (auto: the workload's own)")
+    ap.add_argument("--cd-h", type=float, default=0.0, help="plain CD-FD path: difference step (0: the workload's)")
+    ap.add_argument("--cd-sweeps", type=int, default=0, help="plain CD-FD path: sweep cap (0: the workload's)")
     ap.add_argument("--ck", type=int, default=0, help="adjoint checkpoint interval (0: library choice)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip hj_autotune (launch parameters timed on up to 65,536 queries before the run)")
@@ -101,13 +113,14 @@ def _oracle_inputs(wl):
     return O, probs, oracle_opts_list(wl)
 
 
-def _time_oracle(wl, q_ids):
-    """Oracle on the given query rows of wl, all host cores; returns (seconds, result, threads)."""
+def _time_oracle(wl, q_ids, threads=None):
+    """Oracle on the given query rows of wl (all host cores unless threads is
+    given); returns (seconds, result, threads)."""
     O, probs, opts = _oracle_inputs(wl)
     sub = wl.take(q_ids)
     t0 = time.perf_counter()
     res = O.solve(probs, opts, sub.x, sub.t, sub.n_steps, problem_idx=sub.problem_idx,
-                  query_ids=np.asarray(q_ids, dtype=np.int64))
+                  query_ids=np.asarray(q_ids, dtype=np.int64), threads=threads)
     return time.perf_counter() - t0, res, res["threads"]
 
 
@@ -172,6 +185,8 @@ def _peaks():
 def _workload(a):
     build, default_n, metric, descent = WORKLOADS[a.workload]
     wl = build(a.nq or default_n)
+    if a.precision != "auto":
+        wl.precision = a.precision
     return wl, metric, descent
 
 
@@ -256,12 +271,14 @@ def run_ours(a):
         # other ranks draw their own query points from the same distribution
         rng = np.random.default_rng(1000 + rank)
         wl.x = W.f32(np.where(wl.x != 0, rng.uniform(-1, 1, wl.x.shape), 0.0))
-    x = torch.tensor(wl.x, dtype=torch.float32, device=dev)
-    t = torch.tensor(wl.t, dtype=torch.float32, device=dev)
+    fp64 = wl.precision == "fp64"
+    tdt, esz = (torch.float64, 8) if fp64 else (torch.float32, 4)
+    x = torch.tensor(wl.x, dtype=tdt, device=dev)
+    t = torch.tensor(wl.t, dtype=tdt, device=dev)
     ns = torch.tensor(wl.n_steps, dtype=torch.int32, device=dev)
     multi = len(wl.problems) > 1
     pidx = torch.tensor(wl.problem_idx, dtype=torch.int32, device=dev) if multi else None
-    opts = hj.opts_from_dict(wl.solver, hj.HJ_PREC_FP32, int(wl.n_steps.max()))
+    opts = hj.opts_from_dict(wl.solver, hj.HJ_PREC_FP64 if fp64 else hj.HJ_PREC_FP32, int(wl.n_steps.max()))
     ctx = hj.hj_create(wl.problems, opts, local)
     tuning = None
     if a.tpp or a.ck:
@@ -286,7 +303,7 @@ def run_ours(a):
                                 pidx[si].contiguous() if multi else None, iters=3)
         tuning = {"threads_per_pair": chosen, "by": f"hj_autotune on {ns_} queries, 3 iterations (0 = automatic)"}
     phi = torch.empty(nq, dtype=torch.float64, device=dev)
-    vout = torch.zeros(nq, ld, dtype=torch.float32, device=dev)
+    vout = torch.zeros(nq, ld, dtype=tdt, device=dev)
     status = torch.empty(nq, dtype=torch.int32, device=dev)
     out = (phi, vout, status)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -328,8 +345,8 @@ def run_ours(a):
     peaks, peak_src = _peaks()
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     tflops = sum(i["tensor_flops"] for i in infos)
-    traffic = TRAFFIC_4096.get(a.workload)
-    traffic = None if traffic is None or a.tpp or a.ck else traffic * nq / 4096.0
+    traffic = TRAFFIC.get(a.workload)
+    traffic = None if traffic is None or a.tpp or a.ck else traffic[1] * nq / traffic[0]
     if tflops > 0:
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
         roof = {"bound": "tensor", "achieved": tflops / desc_s / 1e12, "peak": peak, "unit": "TFLOP/s",
@@ -339,32 +356,45 @@ def run_ours(a):
                 "peak_note": f"dense BF16, {peak_src} sustained cuBLAS figure; achieved counts the three BF16 "
                              "products of each fp32 product (unpadded d, m)"}
     else:
-        flops = sum(i["algorithmic_flops"] for i in infos)
+        # achieved: the descent's work at the fixed per-evaluation counts of
+        # the general RK4 form (64 d N flops per functional evaluation of the
+        # d=20 family, an adjoint gradient counted as four evaluations, the
+        # in-kernel certificate as one) over the descent launches' device time
+        flops = sum(i["nominal_flops"] for i in infos)
+        flops_lg = sum(i["algorithmic_flops"] for i in infos)
         peak = nsm * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        if fp64:
+            peak /= 64.0
         roof = {"bound": "alu", "achieved": flops / desc_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "frac": flops / desc_s / 1e12 / peak, "traffic": traffic,
-                "traffic_note": "DRAM bytes of round 0's fine-level descent launch, scaled from a 4,096-query "
-                                "ncu capture (the adjoint's per-thread RK4 checkpoints)",
+                "traffic_note": "DRAM bytes of round 0's fine-level descent launch, scaled by queries from a "
+                                "smaller ncu capture of the same kernel",
                 "kernel": "k_desc (persistent descent)",
+                "flops_note": "nominal per-evaluation counts of the general RK4 form (64 d N per functional "
+                              "evaluation at d=20, an adjoint gradient as four evaluations, the in-kernel "
+                              "certificate as one); the one-pair-per-thread kernel carries the iterate as two "
+                              "scalars and executes fewer operations than these counts",
+                "achieved_lane_group_model": flops_lg / desc_s / 1e12,
+                "frac_lane_group_model": flops_lg / desc_s / 1e12 / peak,
                 "peak_note": f"FP32 FMA {nsm} SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz "
-                             f"({peak_src} max SM clock)"}
+                             f"({peak_src} max SM clock)" + ("; FP64 at 1/64 of that" if fp64 else "")}
         # cross-check of that peak: the project's FMA-chain microbenchmark
         # (outside the timed region)
         roof["peak_check_tflops"] = hj.hj_fp32_fma_rate(local)
 
     # e2e through the C ABI with host buffers: pinned H2D of x, t, N (and the
     # problem index), the solve, D2H of phi, v, status
-    hx = torch.tensor(wl.x, dtype=torch.float32).pin_memory()
-    ht = torch.tensor(wl.t, dtype=torch.float32).pin_memory()
+    hx = torch.tensor(wl.x, dtype=tdt).pin_memory()
+    ht = torch.tensor(wl.t, dtype=tdt).pin_memory()
     hn = torch.tensor(wl.n_steps, dtype=torch.int32).pin_memory()
     hp = torch.tensor(wl.problem_idx, dtype=torch.int32).pin_memory() if multi else None
     hphi = torch.empty(nq, dtype=torch.float64).pin_memory()
-    hv = torch.empty(nq, ld, dtype=torch.float32).pin_memory()
+    hv = torch.empty(nq, ld, dtype=tdt).pin_memory()
     hst = torch.empty(nq, dtype=torch.int32).pin_memory()
     dx, dt_, dn = torch.empty_like(x), torch.empty_like(t), torch.empty_like(ns)
     dp_ = torch.empty_like(pidx) if multi else None
-    h2d = hx.numel() * 4 + ht.numel() * 4 + hn.numel() * 4 + (hp.numel() * 4 if multi else 0)
-    d2h = hphi.numel() * 8 + hv.numel() * 4 + hst.numel() * 4
+    h2d = hx.numel() * esz + ht.numel() * esz + hn.numel() * 4 + (hp.numel() * 4 if multi else 0)
+    d2h = hphi.numel() * 8 + hv.numel() * esz + hst.numel() * 4
     torch.cuda.synchronize()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -389,13 +419,20 @@ def run_ours(a):
     phi_np = hphi.numpy().copy()
     st_np = hst.numpy().copy()
 
-    # plain path: Algorithm 1 (cyclic CD) with central differences, same workload
+    # plain path: Algorithm 1 (cyclic CD) with central differences, same
+    # workload, same kernels' forward functional
     plain = None
-    if not a.no_plain and a.workload == WORKLOAD:
-        solver_cd = W.c3_cd_solver()
-        ctx_cd = hj.hj_create(wl.problems, hj.opts_from_dict(solver_cd, hj.HJ_PREC_FP32, 64), local)
+    if not a.no_plain and a.workload in (WORKLOAD, "speed_quad_d10_lax"):
+        solver_cd = W.plain_cd_solver(wl.solver, max(p_.d for p_ in wl.problems))
+        if a.cd_h:
+            solver_cd["fd_h"] = a.cd_h
+        if a.cd_sweeps:
+            solver_cd["max_iters"] = a.cd_sweeps * max(p_.d for p_ in wl.problems)
+        ctx_cd = hj.hj_create(wl.problems, hj.opts_from_dict(solver_cd, hj.HJ_PREC_FP32, int(wl.n_steps.max())),
+                              local)
         phi_cd = torch.empty_like(phi)
-        out_cd = (phi_cd, torch.zeros_like(vout), torch.empty_like(status))
+        st_cd = torch.empty_like(status)
+        out_cd = (phi_cd, torch.zeros_like(vout), st_cd)
         hj.hj_solve(ctx_cd, x, t, ns, None, q_begin, out_cd)  # warm-up
         torch.cuda.synchronize()
         flush.fill_(1.0)
@@ -406,11 +443,39 @@ def run_ours(a):
         torch.cuda.synchronize()
         cd_ms = c0.elapsed_time(c1)
         icd = hj.hj_last_solve_info(ctx_cd)
+        sweeps = solver_cd["max_iters"] // max(p_.d for p_ in wl.problems)
         plain = {"value": nq / (cd_ms / 1e3), "unit": "queries/s", "ms_per_step": cd_ms,
-                 "descent": "cyclic coordinate descent, central differences h=2^-10",
+                 "descent": f"cyclic coordinate descent (Algorithm 1), central differences "
+                            f"h={solver_cd['fd_h']:.6g}, at most {sweeps} sweeps",
                  "functional_evals": icd["functional_evals"],
-                 "achieved_tflops": icd["algorithmic_flops"] / (icd["descent_ms"] / 1e3) / 1e12,
-                 "phi": phi_cd.cpu().numpy()}
+                 "functional_evals_per_s": icd["functional_evals"] / (cd_ms / 1e3),
+                 "achieved_tflops": icd["nominal_flops"] / (icd["descent_ms"] / 1e3) / 1e12,
+                 "certified_frac": float(np.mean(st_cd.cpu().numpy() & 1)),
+                 "phi": phi_cd.cpu().numpy(), "st": st_cd.cpu().numpy()}
+        # several times t in one batch: each t's queries solved on their own,
+        # the adjoint path and the plain path side by side (speed; the
+        # accuracy per t comes from the full runs' sampled rows below)
+        tvals = np.unique(wl.t)
+        if world == 1 and len(tvals) > 1:
+            plain["per_t"] = []
+            for tv in tvals:
+                rows = torch.tensor(np.flatnonzero(wl.t == tv), dtype=torch.int64, device=dev)
+                m = int(rows.numel())
+                xs, ts, nss = x[rows].contiguous(), t[rows].contiguous(), ns[rows].contiguous()
+                o = (torch.empty(m, dtype=torch.float64, device=dev), torch.zeros(m, ld, dtype=tdt, device=dev),
+                     torch.empty(m, dtype=torch.int32, device=dev))
+                row = {"t": float(tv), "queries": m}
+                for key, c_ in (("adjoint", ctx), ("plain_cd_fd", ctx_cd)):
+                    hj.hj_solve(c_, xs, ts, nss, None, 0, o)
+                    torch.cuda.synchronize()
+                    flush.fill_(2.0)
+                    e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0_.record(stream)
+                    hj.hj_solve(c_, xs, ts, nss, None, 0, o)
+                    e1_.record(stream)
+                    torch.cuda.synchronize()
+                    row[key + "_queries_per_s"] = m / (e0_.elapsed_time(e1_) / 1e3)
+                plain["per_t"].append(row)
         ctx_cd.close()
 
     result = None
@@ -423,26 +488,47 @@ def run_ours(a):
             cpu = {"value": _units(wl, ids) / sec, "unit": _unit(wl), "cores": threads, "kind": "oracle",
                    "sample": f"{len(ids)} queries (every {max(1, nq // CPU_SAMPLE)}th) of the workload, all their "
                              f"starts, FP64, {sec:.1f} s wall"}
+            ids1 = ids[:CPU_SAMPLE_1]
+            sec1, _, _ = _time_oracle(wl, ids1, threads=1)
+            cpu["one_core"] = {"value": _units(wl, ids1) / sec1, "cores": 1,
+                               "sample": f"the first {len(ids1)} of those queries, {sec1:.1f} s wall"}
             err = np.abs(phi_np[ids] - ref["phi"]) / (1 + np.abs(ref["phi"]))
             acc = {"sample": len(ids), "max_rel_err": float(err.max()),
                    "frac_within_1e-4": float(np.mean(err <= 1e-4)),
                    "certified_agree": float(np.mean((st_np[ids] & 1) == (ref["status"] & 1)))}
             if plain is not None:
+                # against the oracle's answer (its gradient descent with the
+                # adjoint: the discrete optimum)
                 errp = np.abs(plain["phi"][ids] - ref["phi"]) / (1 + np.abs(ref["phi"]))
                 plain["max_rel_err_vs_oracle"] = float(errp.max())
                 plain["frac_within_1e-4"] = float(np.mean(errp <= 1e-4))
+                plain["certified_agree_with_oracle"] = float(np.mean((plain["st"][ids] & 1) == (ref["status"] & 1)))
+                err_ad = np.abs(phi_np[ids] - ref["phi"]) / (1 + np.abs(ref["phi"]))
+                for row in plain.get("per_t", []):
+                    sel = wl.t[ids] == row["t"]
+                    row["sample"] = int(sel.sum())
+                    row["adjoint_max_rel_err"] = float(err_ad[sel].max()) if sel.any() else None
+                    row["plain_cd_fd_max_rel_err"] = float(errp[sel].max()) if sel.any() else None
+                    row["plain_cd_fd_frac_within_1e-4"] = float(np.mean(errp[sel] <= 1e-4)) if sel.any() else None
         if plain is not None:
             plain.pop("phi")
+            plain.pop("st")
         result = {
             "metric": metric, "value": value, "unit": _unit(wl), "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
             "config": dict(_config(a, wl, descent, nq), tuning=tuning),
             "roofline": roof,
             "e2e": {"value": e2e_val, "unit": _unit(wl), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
             "clocks": clocks,
-            "detail": {"descent_ms_per_step": desc_s * 1e3 / len(infos),
+            "detail": {"functional_evals_per_s": sum(i["functional_evals"] + i["n_pairs"] for i in infos)
+                       / (sum(ms_steps) / 1e3),
+                       "gradients_per_s": sum(i["gradient_evals"] for i in infos) / (sum(ms_steps) / 1e3),
+                       "rk4_steps_per_s": sum(i["rk4_steps"] + i["adjoint_steps"] for i in infos)
+                       / (sum(ms_steps) / 1e3),
+                       "nominal_tflop_per_step": sum(i["nominal_flops"] for i in infos) / len(infos) / 1e12,
+                       "descent_ms_per_step": desc_s * 1e3 / len(infos),
                        "descent_round0_ms_per_step": sum(i["descent_ms_round0"] for i in infos) / len(infos),
                        "certify_ms_per_step": sum(i["certify_ms"] for i in infos) / len(infos),
                        "gradients_per_step": info["gradient_evals"], "pairs_per_step": info["n_pairs"],

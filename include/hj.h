@@ -356,11 +356,19 @@ hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out);
  * tensor-core tile kernel for hj_eval_functional, hj_grad and the gradient
  * and conjugate-gradient descents of hj_solve: 128 pairs per CTA, the stage
  * products on the tensor cores in split-precision BF16x3 (relative error
- * ~2^-16); any non-zero tpp selects the lane-group kernels instead);
- * ck_interval = integrator steps between checkpoints of the adjoint, in [1, 16]
- * (0: automatic, the smallest interval whose checkpoint storage fits a
- * fixed per-thread budget).  Returns HJ_EUNSUPPORTED when no kernel is built
- * for the resulting components per thread.
+ * ~2^-16); any non-zero tpp selects the lane-group kernels instead;
+ * for a SMOOTH_NONCONVEX problem under the Hopf principle in an fp32 context
+ * with RK4 and its quadrature and d <= 32, automatic means the
+ * one-pair-per-thread kernels, which carry the RK4 iterate as the two scalars
+ * (u, B) with p = v + B w: one lane per pair in rounds of at least twice the
+ * GPU's resident threads of pairs, two lanes per pair in smaller rounds,
+ * with bit-identical results; tpp = -1 / -2 pins one / two lanes per pair in
+ * every round for such a problem with gradient descent, HJ_EUNSUPPORTED for
+ * any other); ck_interval = integrator steps between checkpoints of the
+ * adjoint, in [1, 16] (0: automatic, the smallest interval whose checkpoint
+ * storage fits a fixed per-thread budget; 1 for the one-pair-per-thread
+ * kernels, whose checkpoints are 8 bytes).  Returns HJ_EUNSUPPORTED when no
+ * kernel is built for the resulting components per thread.
  */
 hj_status hj_set_tuning(hj_ctx *ctx, int problem, int tpp, int ck_interval);
 

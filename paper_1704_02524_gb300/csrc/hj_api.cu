@@ -1,6 +1,7 @@
 // hj_api.cu -- the C ABI of include/hj.h: context, validation, parameter
 // upload, kernel choice and the hj_solve pipeline.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -531,7 +532,7 @@ int r1_c(const hj_ctx *ctx, int p, int kind)
 {
     const hj_problem_desc &D = ctx->desc[p];
     if (ctx->prec != 0 || D.family != HJ_FAM_SMOOTH_NONCONVEX || D.principle != HJ_HOPF || D.d > R1_MAXD) return 0;
-    if (ctx->tpp_override[p] != 0 || ctx->opts.quad != HJ_QUAD_RK4) return 0;
+    if (ctx->tpp_override[p] > 0 || ctx->opts.quad != HJ_QUAD_RK4) return 0;
     if (kind != K_EVAL && kind != K_GRAD && kind != K_CD && kind != K_GD) return 0;
     const Registry &R = registry();
     for (int c = D.d; c <= R1_MAXD; ++c)
@@ -558,7 +559,8 @@ bool choose(const hj_ctx *ctx, int p, int kind, int *tpp_out, int *c_out)
     else if (ctx->prec == 1) pref = 4;
     else if (kind == K_GRAD || kind == K_GD || kind == K_CG) pref = 5;
     else pref = 10;
-    const int ov = ctx->tpp_override[p];
+    // the -1 / -2 pins concern the one-pair-per-thread kernels only
+    const int ov = std::max(0, ctx->tpp_override[p]);
     for (int tpp = 1; tpp <= 32; tpp <<= 1) {
         if (ov && kind != K_CERT && tpp != ov) continue;
         const int need = (D.d + tpp - 1) / tpp;
@@ -585,6 +587,42 @@ int persistent_grid(hj_ctx *ctx, const void *fn)
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, BLOCK, 0) != cudaSuccess || nb < 1) nb = 1;
     return nb * ctx->nsm;
+}
+
+// Descent launches of one fp32 problem and round: the coarse level first
+// when coarse-to-fine is on (phase 1, then the cursor reset, then phase 2).
+// One-thread-per-pair sets enqueue both their variants with complementary
+// ranges of the round's pair count (read on the device): one lane per pair
+// from twice the launch's resident threads up, two lanes per pair below,
+// where a round is too small to fill the GPU and a pair's latency sets its
+// time.  *launched gets the number of kernels launched.
+cudaError_t launch_desc_f32(hj_ctx *ctx, const KSet &k, int kind, bool r1, bool two, DescArgs<float> &a,
+                            int32_t *cursor, cudaStream_t sp, int *launched)
+{
+    const Launch L = kind == K_GD ? k.gd : kind == K_CG ? k.cg : k.cd;
+    const void *fn = kind == K_GD ? k.f_gd : kind == K_CG ? k.f_cg : k.f_cd;
+    const bool dual = r1 && kind == K_GD && k.gd_lat;
+    const long long big = persistent_grid(ctx, fn);
+    // a lane-count override of -1 / -2 pins one / two lanes per pair for every round
+    const int ov = ctx->tpp_override[a.problem];
+    const long long split = !dual ? 0 : ov == -1 ? 0 : ov == -2 ? LLONG_MAX : 2 * big * BLOCK;
+    *launched = 0;
+    for (int ph = two ? 1 : 0; ph <= (two ? 2 : 0); ++ph) {
+        a.phase = ph;
+        cudaError_t e;
+        if (ph == 2 && (e = cudaMemsetAsync(cursor, 0, sizeof(int32_t), sp)) != cudaSuccess) return e;
+        a.run_lo = split;
+        a.run_hi = LLONG_MAX;
+        if ((e = L(&a, (int)big, sp)) != cudaSuccess) return e;
+        ++*launched;
+        if (dual) {
+            a.run_lo = 0;
+            a.run_hi = split;
+            if ((e = k.gd_lat(&a, persistent_grid(ctx, k.f_gd_lat), sp)) != cudaSuccess) return e;
+            ++*launched;
+        }
+    }
+    return cudaSuccess;
 }
 
 int rows_grid(hj_ctx *ctx, const void *fn, long long n, int tpp)
@@ -933,12 +971,18 @@ hj_status hj_set_tuning(hj_ctx *ctx, int problem, int tpp, int ck_interval)
 {
     if (!ctx) return HJ_EINVAL;
     if (problem < 0 || problem >= ctx->np) return fail(ctx, HJ_EINVAL, "problem %d outside [0, %d)", problem, ctx->np);
-    if (tpp != 0 && tpp != 1 && tpp != 2 && tpp != 4 && tpp != 8 && tpp != 16 && tpp != 32)
-        return fail(ctx, HJ_EINVAL, "tpp must be 0 or a power of two <= 32");
+    if (tpp != 0 && tpp != -1 && tpp != -2 && tpp != 1 && tpp != 2 && tpp != 4 && tpp != 8 && tpp != 16 && tpp != 32)
+        return fail(ctx, HJ_EINVAL, "tpp must be 0, -1, -2 or a power of two <= 32");
+
     if (ck_interval < 0 || ck_interval > MAX_SEG)
         return fail(ctx, HJ_EINVAL, "ck_interval must be in [0, %d]", MAX_SEG);
     int old = ctx->tpp_override[problem];
     ctx->tpp_override[problem] = tpp;
+    if (tpp < 0 && (desc_kind(ctx->popts[problem].grad) != K_GD || !r1_c(ctx, problem, K_GD))) {
+        ctx->tpp_override[problem] = old;
+        return fail(ctx, HJ_EUNSUPPORTED, "tpp %d needs a problem that runs one pair per thread (the fp32 smooth "
+                    "non-convex Hopf family, d <= %d, RK4, adjoint gradient descent)", tpp, R1_MAXD);
+    }
     int t, c;
     const int kind = desc_kind(ctx->popts[problem].grad);
     if (!choose(ctx, problem, kind, &t, &c) || !choose(ctx, problem, K_EVAL, &t, &c) ||
@@ -1257,15 +1301,11 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                     fill(a);
                     a.P = ctx->dev[p].pf;
                     a.x = (const float *)x; a.t = (const float *)t; a.vfin = (float *)ctx->vfin;
-                    if (kind != K_CD && ctx->popts[p].coarse_div > 1) {
-                        // coarse-to-fine as two launches, so that every warp runs one step count
-                        a.phase = 1;
-                        CU(L(&a, persistent_grid(ctx, fn), sp));
-                        CU(cudaMemsetAsync(ctx->cursor + p, 0, sizeof(int32_t), sp));
-                        a.phase = 2;
-                        ctx->launches++;
-                    }
-                    CU(L(&a, persistent_grid(ctx, fn), sp));
+                    // coarse-to-fine as two launches, so that every warp runs one step count
+                    int nl = 0;
+                    CU(launch_desc_f32(ctx, k, kind, c_d[p] < 0, kind != K_CD && ctx->popts[p].coarse_div > 1, a,
+                                       ctx->cursor + p, sp, &nl));
+                    ctx->launches += nl - 1;
                 }
                 if (ctx->pp_timing && round == 0) CU(cudaEventRecord(ctx->pp_ev[2 * p + 1], s));
                 ctx->launches++;
@@ -1735,13 +1775,8 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
                 fill(a);
                 a.P = ctx->dev[p].pf;
                 a.x = (const float *)x; a.t = (const float *)t; a.vfin = (float *)L.vfin;
-                if (two) {
-                    a.phase = 1;
-                    CU(Lk(&a, persistent_grid(ctx, fn), s));
-                    CU(cudaMemsetAsync(L.cursor + p, 0, sizeof(int32_t), s));
-                    a.phase = 2;
-                }
-                CU(Lk(&a, persistent_grid(ctx, fn), s));
+                int nl = 0;
+                CU(launch_desc_f32(ctx, k, kind, c_d[p] < 0, two, a, L.cursor + p, s, &nl));
             }
         }
         for (int p = 0; p < ctx->np; ++p) {

@@ -18,6 +18,11 @@ struct KSet {
            cert_pairs = nullptr, cert_final = nullptr;
     const void *f_eval = nullptr, *f_grad = nullptr, *f_cd = nullptr, *f_gd = nullptr, *f_cg = nullptr,
                *f_cert_rows = nullptr, *f_cert_pairs = nullptr, *f_cert_final = nullptr;
+    // one-thread-per-pair sets only: the gradient descent with two lanes per
+    // pair, for rounds too small to fill the GPU (lower latency per pair;
+    // bit-identical results)
+    Launch gd_lat = nullptr;
+    const void *f_gd_lat = nullptr;
 };
 
 struct Registry {

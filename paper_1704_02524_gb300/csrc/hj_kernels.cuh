@@ -86,6 +86,11 @@ struct DescArgs {
     unsigned long long *stats;  // [0] iterations [1] functional evals [2] gradients [3] forward RK4 steps
                                 // [4] adjoint steps [5] pairs [6] sum of N over pairs
                                 // [7] RK4 steps of the in-kernel certificate
+    // one-thread-per-pair kernels: run only when the problem's work list
+    // holds a number of pairs in [run_lo, run_hi) (read on the device), so
+    // that a throughput and a latency variant can both be enqueued and the
+    // one that fits the round's size does the work
+    long long run_lo, run_hi;
 };
 
 constexpr int BLOCK = 128;

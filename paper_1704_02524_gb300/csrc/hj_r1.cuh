@@ -32,7 +32,14 @@
 // Per pair the thread holds v and lam_p in registers (2d values); the
 // per-problem vectors (w, e, w e, the initial data's coefficients) are kernel
 // parameters, read as constant operands.  One thread per pair means no
-// shuffles: every dot product is a register sum.  The four RK4 stages and the
+// shuffles: every dot product is a register sum (two partial sums, over the
+// even and the odd components).  A second form runs each pair on two lanes
+// (TPP = 2), lane l holding the components i = 2k + l with its own copy of
+// their parameters: each lane's sum is then exactly one of the two partial
+// sums, and the group sum adds the other lane's, so both forms give the same
+// results bit for bit while the two-lane form halves the serial work of a
+// pair (for rounds with too few pairs to fill the GPU, where a pair's latency
+// sets the time).  The four RK4 stages and the
 // four stage products of the adjoint run as loops, not unrolled, so that the
 // d-wide stage body exists once per use in the code: with every stage inlined
 // the kernel's instruction stream outgrew the instruction cache (the
@@ -51,8 +58,77 @@ constexpr int REC = 8;  // floats per stage record in shared memory
 // Resident blocks of BLOCK threads per SM the register allocation aims at.
 // A problem with d <= R1_MAXD runs with C = the smallest instantiated size
 // >= d; padded components carry w = e = g2 = ga = 0 and drop out of every sum.
+template <int C, int TPP>
+constexpr int min_blocks()
+{
+    return TPP == 1 ? (C <= 16 ? 4 : (C <= 20 ? 3 : 2)) : (C <= 20 ? 4 : 3);
+}
+
+// The lane's view of the per-component parameters.  One lane per pair: the
+// parameter block's values, read as constants (component k is i = k).  Two
+// lanes per pair: lane l of the group holds i = 2k + l, with w, e and w e of
+// those components copied to registers.
+template <int C, int TPP>
+struct Lane;
 template <int C>
-constexpr int min_blocks() { return C <= 16 ? 4 : (C <= 20 ? 3 : 2); }
+struct Lane<C, 1> {
+    static constexpr int CL = C;
+    unsigned gm;  // lanes of the group
+    int gl;       // lane inside the group
+    __device__ void load(const ProbDev<float> &, int lane) { gm = 1u << lane; gl = 0; }
+    __device__ __forceinline__ int comp(int k) const { return k; }
+    __device__ __forceinline__ float w(const ProbDev<float> &P, int k) const { return P.rw[k]; }
+    __device__ __forceinline__ float e(const ProbDev<float> &P, int k) const { return P.re[k]; }
+    __device__ __forceinline__ float we(const ProbDev<float> &P, int k) const { return P.rew[k]; }
+    __device__ __forceinline__ float g2(const ProbDev<float> &P, int k) const { return P.rg2[k]; }
+    __device__ __forceinline__ float ga(const ProbDev<float> &P, int k) const { return P.rga[k]; }
+    // the group total of partial sums over even (a0) and odd (a1) components
+    __device__ __forceinline__ float total(float a0, float a1) const { return a0 + a1; }
+    __device__ __forceinline__ float gmaxf(float a) const { return a; }
+};
+template <int C>
+struct Lane<C, 2> {
+    static constexpr int CL = C / 2;
+    float w_[CL], e_[CL], we_[CL];
+    unsigned gm;
+    int gl;
+    __device__ void load(const ProbDev<float> &P, int lane)
+    {
+        gl = lane & 1;
+        gm = 3u << (lane & ~1);
+#pragma unroll
+        for (int k = 0; k < CL; ++k) {
+            w_[k] = P.rw[2 * k + gl];
+            e_[k] = P.re[2 * k + gl];
+            we_[k] = P.rew[2 * k + gl];
+        }
+    }
+    __device__ __forceinline__ int comp(int k) const { return 2 * k + gl; }
+    __device__ __forceinline__ float w(const ProbDev<float> &, int k) const { return w_[k]; }
+    __device__ __forceinline__ float e(const ProbDev<float> &, int k) const { return e_[k]; }
+    __device__ __forceinline__ float we(const ProbDev<float> &, int k) const { return we_[k]; }
+    __device__ __forceinline__ float g2(const ProbDev<float> &P, int k) const { return P.rg2[2 * k + gl]; }
+    __device__ __forceinline__ float ga(const ProbDev<float> &P, int k) const { return P.rga[2 * k + gl]; }
+    // this lane's sum is one parity's partial sum (in a0); the other lane has
+    // the other parity's: their sum, the same on both lanes
+    __device__ __forceinline__ float total(float a0, float) const { return a0 + __shfl_xor_sync(gm, a0, 1); }
+    __device__ __forceinline__ float gmaxf(float a) const { return fmaxf(a, __shfl_xor_sync(gm, a, 1)); }
+};
+
+// Partial sums over the lane's components: two (even and odd components)
+// with one lane per pair, one (the lane's parity) with two.  Every product
+// that feeds a sum in this file is an explicit fmaf or an explicitly rounded
+// multiply (__fmul_rn), so the compiler cannot contract the two forms'
+// arithmetic differently.
+template <int TPP>
+struct Acc {
+    float a0 = 0.f, a1 = 0.f;
+    __device__ __forceinline__ void fma_(int k, float m, float x)
+    {
+        if (TPP == 2 || !(k & 1)) a0 = fmaf(m, x, a0);
+        else a1 = fmaf(m, x, a1);
+    }
+};
 
 // Scalars of one RK4 stage.
 struct St {
@@ -75,31 +151,26 @@ __device__ __forceinline__ St get(const float *rec, int st)
     return St{r[0], r[BLOCK], r[2 * BLOCK], r[3 * BLOCK], r[4 * BLOCK], r[5 * BLOCK], r[6 * BLOCK]};
 }
 
-// The sums of a stage at input (u, B): Phi and D, with the reciprocals r_i
-// kept when KEEP.  Two partial sums each shorten the dependency chains.
-template <int C, bool KEEP>
-__device__ __forceinline__ void stage(const ProbDev<float> &P, const float *v, float eps, float u, float B, St &s,
-                                      float *r)
+// The sums of a stage at input (u, B): Phi and D, with the reciprocals r
+// kept when KEEP.
+template <int C, int TPP, bool KEEP>
+__device__ __forceinline__ void stage(const ProbDev<float> &P, const Lane<C, TPP> &L, const float *v, float eps,
+                                      float u, float B, St &s, float *r)
 {
-    float ph0 = 0.f, ph1 = 0.f, d0 = 0.f, d1 = 0.f;
+    Acc<TPP> ph, dd;
 #pragma unroll
-    for (int i = 0; i < C; ++i) {
-        const float p = fmaf(B, P.rw[i], v[i]);
+    for (int k = 0; k < Lane<C, TPP>::CL; ++k) {
+        const float p = fmaf(B, L.w(P, k), v[k]);
         const float q = fmaf(p, p, eps);
         const float ri = rsqrtf(q);
-        if constexpr (KEEP) r[i] = ri;
-        if (i & 1) {
-            ph1 = fmaf(P.re[i], q * ri, ph1);
-            d1 = fmaf(P.rew[i], ri * p, d1);
-        } else {
-            ph0 = fmaf(P.re[i], q * ri, ph0);
-            d0 = fmaf(P.rew[i], ri * p, d0);
-        }
+        if constexpr (KEEP) r[k] = ri;
+        ph.fma_(k, L.e(P, k), q * ri);
+        dd.fma_(k, L.we(P, k), ri * p);
     }
     s.u = u;
     s.B = B;
-    s.phi = ph0 + ph1;
-    s.D = d0 + d1;
+    s.phi = L.total(ph.a0, ph.a1);
+    s.D = L.total(dd.a0, dd.a1);
     float su, cu;
     __sincosf(u, &su, &cu);
     s.c = fmaf(0.5f, su, 1.f);
@@ -108,31 +179,31 @@ __device__ __forceinline__ void stage(const ProbDev<float> &P, const float *v, f
 }
 
 // Stage rates: du/dtau, dB/dtau and the Hopf running cost.
-__device__ __forceinline__ float rate_u(const St &s) { return -s.c * s.D; }
-__device__ __forceinline__ float rate_B(const St &s) { return s.phi * s.c1; }
-__device__ __forceinline__ float cost(const St &s) { return s.phi * (s.c - s.c1 * s.u); }
+__device__ __forceinline__ float rate_u(const St &s) { return __fmul_rn(-s.c, s.D); }
+__device__ __forceinline__ float rate_B(const St &s) { return __fmul_rn(s.phi, s.c1); }
+__device__ __forceinline__ float cost(const St &s) { return __fmul_rn(s.phi, fmaf(-s.c1, s.u, s.c)); }
 
-// RK4 bookkeeping of stage st (0..3) with rates k: the weighted sums a (k1 +
-// 2 k2 + 2 k3 + k4) and the next stage's input z + h2 k or z + h k.
+// RK4 bookkeeping of stage st (0..3) with rate k: the weighted sum
+// a = k1 + 2 k2 + 2 k3 + k4.
 __device__ __forceinline__ void rk4_acc(int st, float k, float &a)
 {
     if (st == 0) a = k;
     else if (st < 3) a = fmaf(2.f, k, a);
-    else a += k;
+    else a = __fadd_rn(a, k);
 }
 
 // One classical RK4 step of (u, B) and the running cost; the four stage
 // records go to rec when it is non-null.
-template <int C>
-__device__ __forceinline__ void step(const ProbDev<float> &P, const float *v, float eps, float h, float &u, float &B,
-                                     float &dQ, float *rec)
+template <int C, int TPP>
+__device__ __forceinline__ void step(const ProbDev<float> &P, const Lane<C, TPP> &L, const float *v, float eps,
+                                     float h, float &u, float &B, float &dQ, float *rec)
 {
     const float h2 = 0.5f * h, h6 = h / 6.f;
     float su = u, sB = B, au = 0.f, aB = 0.f, aL = 0.f;
 #pragma unroll 1
     for (int st = 0; st < 4; ++st) {
         St s;
-        stage<C, false>(P, v, eps, su, sB, s, nullptr);
+        stage<C, TPP, false>(P, L, v, eps, su, sB, s, nullptr);
         if (rec) put(rec, st, s);
         const float ku = rate_u(s), kB = rate_B(s);
         rk4_acc(st, ku, au);
@@ -144,57 +215,51 @@ __device__ __forceinline__ void step(const ProbDev<float> &P, const float *v, fl
     }
     u = fmaf(h6, au, u);
     B = fmaf(h6, aB, B);
-    dQ = h6 * aL;
+    dQ = __fmul_rn(h6, aL);
 }
 
-// <w, x> and <a, b>.
-template <int C>
-__device__ __forceinline__ float dot_w(const ProbDev<float> &P, const float *x)
+// <w, x> and <a, b> over the group's components.
+template <int C, int TPP>
+__device__ __forceinline__ float dot_w(const ProbDev<float> &P, const Lane<C, TPP> &L, const float *x)
 {
-    float a0 = 0.f, a1 = 0.f;
+    Acc<TPP> a;
 #pragma unroll
-    for (int i = 0; i < C; ++i) {
-        if (i & 1) a1 = fmaf(P.rw[i], x[i], a1);
-        else a0 = fmaf(P.rw[i], x[i], a0);
-    }
-    return a0 + a1;
+    for (int k = 0; k < Lane<C, TPP>::CL; ++k) a.fma_(k, L.w(P, k), x[k]);
+    return L.total(a.a0, a.a1);
 }
-template <int C>
-__device__ __forceinline__ float dot(const float *a, const float *b)
+template <int C, int TPP>
+__device__ __forceinline__ float dot(const Lane<C, TPP> &L, const float *x, const float *y)
 {
-    float a0 = 0.f, a1 = 0.f;
+    Acc<TPP> a;
 #pragma unroll
-    for (int i = 0; i < C; ++i) {
-        if (i & 1) a1 = fmaf(a[i], b[i], a1);
-        else a0 = fmaf(a[i], b[i], a0);
-    }
-    return a0 + a1;
+    for (int k = 0; k < Lane<C, TPP>::CL; ++k) a.fma_(k, x[k], y[k]);
+    return L.total(a.a0, a.a1);
 }
 
 // Hopf terminal term g*(p_N) - <x, v> (+ the ellipse data's constant), with
 // g*(p) = sum_i p_i (g2_i p_i / 2 + ga_i) and xv = <x, v>; the seed grad g*
 // goes to lp when it is non-null.
-template <int C>
-__device__ __forceinline__ float terminal(const ProbDev<float> &P, float xv, const float *v, float B, float *lp)
+template <int C, int TPP>
+__device__ __forceinline__ float terminal(const ProbDev<float> &P, const Lane<C, TPP> &L, float xv, const float *v,
+                                          float B, float *lp)
 {
-    float a0 = 0.f, a1 = 0.f;
+    Acc<TPP> a;
 #pragma unroll
-    for (int i = 0; i < C; ++i) {
-        const float p = fmaf(B, P.rw[i], v[i]);
-        const float val = p * fmaf(0.5f * P.rg2[i], p, P.rga[i]);
-        if (i & 1) a1 += val;
-        else a0 += val;
-        if (lp) lp[i] = fmaf(P.rg2[i], p, P.rga[i]);
+    for (int k = 0; k < Lane<C, TPP>::CL; ++k) {
+        const float p = fmaf(B, L.w(P, k), v[k]);
+        const float g2 = L.g2(P, k), ga = L.ga(P, k);
+        a.fma_(k, p, fmaf(0.5f * g2, p, ga));
+        if (lp) lp[k] = fmaf(g2, p, ga);
     }
-    return (a0 + a1 - xv) + P.rcst;
+    return (L.total(a.a0, a.a1) - xv) + P.rcst;
 }
 
 // Functional G(v) (Hopf) from u0 = <w, x> and xv = <x, v>.  With ck != null
 // the step inputs (u_n, B_n) of every K-th step are stored there (the
 // adjoint's checkpoints).  B_N is returned in Bn.
-template <int C>
-__device__ __forceinline__ float functional(const ProbDev<float> &P, int kahan, float u0, float xv, const float *v,
-                                            float t, int N, float2 *ck, int K, float &Bn)
+template <int C, int TPP>
+__device__ __forceinline__ float functional(const ProbDev<float> &P, const Lane<C, TPP> &L, int kahan, float u0,
+                                            float xv, const float *v, float t, int N, float2 *ck, int K, float &Bn)
 {
     if (N < 1 || N > MAX_N) {
         Bn = NAN;
@@ -208,42 +273,43 @@ __device__ __forceinline__ float functional(const ProbDev<float> &P, int kahan, 
             if (++kk == K) kk = 0;
         }
         float dQ;
-        step<C>(P, v, eps, h, u, B, dQ, nullptr);
+        step<C, TPP>(P, L, v, eps, h, u, B, dQ, nullptr);
         add_q(kahan, dQ, Q, Qc);
     }
     Bn = B;
-    return terminal<C>(P, xv, v, B, nullptr) + Q;
+    return terminal<C, TPP>(P, L, xv, v, B, nullptr) + Q;
 }
 
 // The functional with gamma carried along as a vector, for the certificate
 // (Sec. 4.3): gamma advances by the RK4 combination of the stage rates
 // -c Phi'(p); (u, B, Q) advance exactly as in functional().  Returns G; gam
-// holds x on entry and gamma(0) on exit, Bn gets B_N.
-template <int C>
-__device__ __forceinline__ float functional_gamma(const ProbDev<float> &P, int kahan, float u0, float xv,
-                                                  const float *v, float t, int N, float *gam, float &Bn)
+// holds x on entry and gamma(0) on exit (the lane's components), Bn gets B_N.
+template <int C, int TPP>
+__device__ __forceinline__ float functional_gamma(const ProbDev<float> &P, const Lane<C, TPP> &L, int kahan, float u0,
+                                                  float xv, const float *v, float t, int N, float *gam, float &Bn)
 {
     if (N < 1 || N > MAX_N) {
         Bn = NAN;
         return NAN;
     }
+    constexpr int CL = Lane<C, TPP>::CL;
     const float eps = P.s_eps, h = t / (float)N, h2 = 0.5f * h, h6 = h / 6.f;
     float u = u0, B = 0.f, Q = 0.f, Qc = 0.f;
     for (int n = 0; n < N; ++n) {
-        float ag[C];
+        float ag[CL];
         float su = u, sB = B, au = 0.f, aB = 0.f, aL = 0.f;
 #pragma unroll 1
         for (int st = 0; st < 4; ++st) {
-            float r[C];
+            float r[CL];
             St s;
-            stage<C, true>(P, v, eps, su, sB, s, r);
+            stage<C, TPP, true>(P, L, v, eps, su, sB, s, r);
 #pragma unroll
-            for (int i = 0; i < C; ++i) {
-                const float p = fmaf(sB, P.rw[i], v[i]);
-                const float kg = -s.c * ((P.re[i] * r[i]) * p);
-                if (st == 0) ag[i] = kg;
-                else if (st < 3) ag[i] = fmaf(2.f, kg, ag[i]);
-                else gam[i] = fmaf(h6, ag[i] + kg, gam[i]);
+            for (int k = 0; k < CL; ++k) {
+                const float p = fmaf(sB, L.w(P, k), v[k]);
+                const float kg = __fmul_rn(-s.c, __fmul_rn(__fmul_rn(L.e(P, k), r[k]), p));
+                if (st == 0) ag[k] = kg;
+                else if (st < 3) ag[k] = fmaf(2.f, kg, ag[k]);
+                else gam[k] = fmaf(h6, __fadd_rn(ag[k], kg), gam[k]);
             }
             const float ku = rate_u(s), kB = rate_B(s);
             rk4_acc(st, ku, au);
@@ -255,10 +321,10 @@ __device__ __forceinline__ float functional_gamma(const ProbDev<float> &P, int k
         }
         u = fmaf(h6, au, u);
         B = fmaf(h6, aB, B);
-        add_q(kahan, h6 * aL, Q, Qc);
+        add_q(kahan, __fmul_rn(h6, aL), Q, Qc);
     }
     Bn = B;
-    return terminal<C>(P, xv, v, B, nullptr) + Q;
+    return terminal<C, TPP>(P, L, xv, v, B, nullptr) + Q;
 }
 
 // Vector-Jacobian product of one stage with scalar weights: gamma weight
@@ -268,29 +334,30 @@ __device__ __forceinline__ float functional_gamma(const ProbDev<float> &P, int k
 // input is made to depend on `after` (the previous product's result, finite
 // in any finite solve) so that this happens in order instead of being
 // hoisted and kept live across the step.
-template <int C>
-__device__ __forceinline__ void vjp(const ProbDev<float> &P, const float *v, float eps, const St &s, float a,
-                                    float Bw, float bb, float after, float *lp, float &R, float &Wr)
+template <int C, int TPP>
+__device__ __forceinline__ void vjp(const ProbDev<float> &P, const Lane<C, TPP> &L, const float *v, float eps,
+                                    const St &s, float a, float Bw, float bb, float after, float *lp, float &R,
+                                    float &Wr)
 {
-    const float A = a * s.D;
-    float dEdu = fmaf(-s.c1, A, s.phi * s.c2 * Bw);
-    dEdu -= bb * s.phi * s.c2 * s.u;
-    const float kd = fmaf(s.c1, Bw, bb * (s.c - s.c1 * s.u));
-    const float cea = s.c * eps * a;
+    const float A = __fmul_rn(a, s.D);
+    float dEdu = fmaf(-s.c1, A, __fmul_rn(__fmul_rn(s.phi, s.c2), Bw));
+    dEdu = fmaf(-__fmul_rn(__fmul_rn(bb, s.phi), s.c2), s.u, dEdu);
+    const float kd = fmaf(s.c1, Bw, __fmul_rn(bb, fmaf(-s.c1, s.u, s.c)));
+    const float cea = __fmul_rn(__fmul_rn(s.c, eps), a);
     const float Bs = fmaf(0.f, after, s.B);
-    float w0 = 0.f, w1 = 0.f;
+    Acc<TPP> w;
 #pragma unroll
-    for (int i = 0; i < C; ++i) {
-        const float p = fmaf(Bs, P.rw[i], v[i]);
+    for (int k = 0; k < Lane<C, TPP>::CL; ++k) {
+        const float wk = L.w(P, k);
+        const float p = fmaf(Bs, wk, v[k]);
         const float ri = rsqrtf(fmaf(p, p, eps));
-        const float tt = fmaf(-cea * P.rw[i], ri * ri, kd * p);
-        const float rp = (P.re[i] * ri) * tt;
-        lp[i] += rp;
-        if (i & 1) w1 = fmaf(P.rw[i], rp, w1);
-        else w0 = fmaf(P.rw[i], rp, w0);
+        const float tt = fmaf(-cea * wk, ri * ri, __fmul_rn(kd, p));
+        const float rp = __fmul_rn(__fmul_rn(L.e(P, k), ri), tt);
+        lp[k] = __fadd_rn(lp[k], rp);
+        w.fma_(k, wk, rp);
     }
     R = dEdu;
-    Wr = w0 + w1;
+    Wr = L.total(w.a0, w.a1);
 }
 
 // Adjoint of one RK4 step at input (u, B): lam = (alpha w, lp) -> lam_n.
@@ -298,48 +365,50 @@ __device__ __forceinline__ void vjp(const ProbDev<float> &P, const float *v, flo
 // in rec; the products run from stage 4 down to stage 1 with the weights of
 // the RK4 adjoint: (h/6, h/3, h/3, h/6) on lam and the quadrature, and
 // (h, h/2, h/2) on the previous stage's product.
-template <int C>
-__device__ __forceinline__ void adjoint_step(const ProbDev<float> &P, const float *v, float eps, float h, float u,
-                                             float B, float &alpha, float *lp, float *rec)
+template <int C, int TPP>
+__device__ __forceinline__ void adjoint_step(const ProbDev<float> &P, const Lane<C, TPP> &L, const float *v, float eps,
+                                             float h, float u, float B, float &alpha, float *lp, float *rec)
 {
     const float h2 = 0.5f * h, h3 = h / 3.f, h6 = h / 6.f;
     float un = u, Bn = B, dQ;
-    step<C>(P, v, eps, h, un, Bn, dQ, rec);
-    const float Lw = dot_w<C>(P, lp);
+    step<C, TPP>(P, L, v, eps, h, un, Bn, dQ, rec);
+    const float Lw = dot_w<C, TPP>(P, L, lp);
     float R = 0.f, W = 0.f, sumR = 0.f;
 #pragma unroll 1
     for (int j = 3; j >= 0; --j) {
         const St s = get(rec, j);
         const float wl = (j == 0 || j == 3) ? h6 : h3;
         const float wp = (j == 2) ? h : h2;
-        vjp<C>(P, v, eps, s, fmaf(wl, alpha, wp * R), fmaf(wl, Lw, wp * W), wl, W, lp, R, W);
-        sumR += R;
+        vjp<C, TPP>(P, L, v, eps, s, fmaf(wl, alpha, __fmul_rn(wp, R)), fmaf(wl, Lw, __fmul_rn(wp, W)), wl, W, lp, R,
+                    W);
+        sumR = __fadd_rn(sumR, R);
     }
-    alpha += sumR;
+    alpha = __fadd_rn(alpha, sumR);
 }
 
 // Gradient of G with respect to v, less the -x of the Hopf terminal term:
 // gr gets lam_p(0) (the caller subtracts x).  Returns G.  ck holds
 // ceil(N/K) checkpoints, seg K states (thread-private).
-template <int C>
-__device__ __forceinline__ float gradient(const ProbDev<float> &P, int kahan, int K, float u0, float xv, const float *v,
-                                          float t, int N, float *gr, float2 *ck, float2 *seg, float *rec)
+template <int C, int TPP>
+__device__ __forceinline__ float gradient(const ProbDev<float> &P, const Lane<C, TPP> &L, int kahan, int K, float u0,
+                                          float xv, const float *v, float t, int N, float *gr, float2 *ck,
+                                          float2 *seg, float *rec)
 {
     if (N < 1 || N > MAX_N) {
 #pragma unroll
-        for (int i = 0; i < C; ++i) gr[i] = NAN;
+        for (int k = 0; k < Lane<C, TPP>::CL; ++k) gr[k] = NAN;
         return NAN;
     }
     const float eps = P.s_eps, h = t / (float)N;
     float Bn;
-    const float F = functional<C>(P, kahan, u0, xv, v, t, N, ck, K, Bn);
-    terminal<C>(P, xv, v, Bn, gr);  // seed lam_p = grad g*(p_N), kept in gr
+    const float F = functional<C, TPP>(P, L, kahan, u0, xv, v, t, N, ck, K, Bn);
+    terminal<C, TPP>(P, L, xv, v, Bn, gr);  // seed lam_p = grad g*(p_N), kept in gr
     float alpha = 0.f;
     if (K == 1) {
         float2 cur = ck[N - 1];
         for (int n = N - 1; n >= 0; --n) {
             const float2 nxt = ck[n > 0 ? n - 1 : 0];
-            adjoint_step<C>(P, v, eps, h, cur.x, cur.y, alpha, gr, rec);
+            adjoint_step<C, TPP>(P, L, v, eps, h, cur.x, cur.y, alpha, gr, rec);
             cur = nxt;
         }
     } else {
@@ -351,11 +420,11 @@ __device__ __forceinline__ float gradient(const ProbDev<float> &P, int kahan, in
                 seg[n - n0] = make_float2(u, B);
                 if (n + 1 < n1) {
                     float dQ;
-                    step<C>(P, v, eps, h, u, B, dQ, nullptr);
+                    step<C, TPP>(P, L, v, eps, h, u, B, dQ, nullptr);
                 }
             }
             for (int n = n1 - 1; n >= n0; --n)
-                adjoint_step<C>(P, v, eps, h, seg[n - n0].x, seg[n - n0].y, alpha, gr, rec);
+                adjoint_step<C, TPP>(P, L, v, eps, h, seg[n - n0].x, seg[n - n0].y, alpha, gr, rec);
         }
     }
     return F;
@@ -369,71 +438,98 @@ __device__ __forceinline__ int ck_interval(int N, int fixed)
     return min(K, MAX_SEG);
 }
 
-template <int C>
-__device__ __forceinline__ void load_vec(const float *row, int d, float *out)
+// The lane's components of a row of d values.
+template <int C, int TPP>
+__device__ __forceinline__ void load_vec(const Lane<C, TPP> &L, const float *row, int d, float *out)
 {
 #pragma unroll
-    for (int i = 0; i < C; ++i) out[i] = (i < d) ? __ldg(row + i) : 0.f;
+    for (int k = 0; k < Lane<C, TPP>::CL; ++k) {
+        const int i = L.comp(k);
+        out[k] = (i < d) ? __ldg(row + i) : 0.f;
+    }
+}
+template <int C, int TPP>
+__device__ __forceinline__ void store_vec(const Lane<C, TPP> &L, float *row, int d, const float *val)
+{
+#pragma unroll
+    for (int k = 0; k < Lane<C, TPP>::CL; ++k) {
+        const int i = L.comp(k);
+        if (i < d) row[i] = val[k];
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Rows: functional values and gradients (one thread per row).
 // ---------------------------------------------------------------------------
 template <int C>
-__global__ void __launch_bounds__(BLOCK, min_blocks<C>()) k_eval(RowArgs<float> a)
+__global__ void __launch_bounds__(BLOCK, (min_blocks<C, 1>())) k_eval(RowArgs<float> a)
 {
+    Lane<C, 1> L;
+    L.load(a.P, threadIdx.x & 31);
     const long long stride = (long long)gridDim.x * BLOCK;
     for (long long r = (long long)blockIdx.x * BLOCK + threadIdx.x; r < a.n; r += stride) {
         if (a.pidx && a.pidx[r] != a.pfilter) continue;
         const int N = a.nsteps ? a.nsteps[r] : a.n_default;
         float x[C], v[C], Bn;
-        load_vec<C>(a.x + r * a.P.ld, a.P.d, x);
-        load_vec<C>(a.v + r * a.P.ld, a.P.d, v);
-        a.F[r] = functional<C>(a.P, a.kahan, dot_w<C>(a.P, x), dot<C>(x, v), v, a.t[r], N, nullptr, 1, Bn);
+        load_vec<C, 1>(L, a.x + r * a.P.ld, a.P.d, x);
+        load_vec<C, 1>(L, a.v + r * a.P.ld, a.P.d, v);
+        a.F[r] = functional<C, 1>(a.P, L, a.kahan, dot_w<C, 1>(a.P, L, x), dot<C, 1>(L, x, v), v, a.t[r], N,
+                                  nullptr, 1, Bn);
     }
 }
 
 template <int C>
-__global__ void __launch_bounds__(BLOCK, min_blocks<C>()) k_grad(RowArgs<float> a)
+__global__ void __launch_bounds__(BLOCK, (min_blocks<C, 1>())) k_grad(RowArgs<float> a)
 {
     __shared__ float s_rec[4 * REC][BLOCK];
     float2 ck[MAX_N], seg[MAX_SEG];
     float *rec = &s_rec[0][threadIdx.x];
+    Lane<C, 1> L;
+    L.load(a.P, threadIdx.x & 31);
     const long long stride = (long long)gridDim.x * BLOCK;
     for (long long r = (long long)blockIdx.x * BLOCK + threadIdx.x; r < a.n; r += stride) {
         if (a.pidx && a.pidx[r] != a.pfilter) continue;
         const int N = a.nsteps ? a.nsteps[r] : a.n_default;
         float x[C], v[C], gr[C];
-        load_vec<C>(a.x + r * a.P.ld, a.P.d, x);
-        load_vec<C>(a.v + r * a.P.ld, a.P.d, v);
+        load_vec<C, 1>(L, a.x + r * a.P.ld, a.P.d, x);
+        load_vec<C, 1>(L, a.v + r * a.P.ld, a.P.d, v);
         const int K = ck_interval(N, a.ck_interval);
-        const float F = gradient<C>(a.P, a.kahan, K, dot_w<C>(a.P, x), dot<C>(x, v), v, a.t[r], N, gr, ck, seg, rec);
-        float *g = a.grad + r * a.P.ld;
+        const float F = gradient<C, 1>(a.P, L, a.kahan, K, dot_w<C, 1>(a.P, L, x), dot<C, 1>(L, x, v), v, a.t[r], N,
+                                       gr, ck, seg, rec);
 #pragma unroll
-        for (int i = 0; i < C; ++i)
-            if (i < a.P.d) g[i] = gr[i] - x[i];
+        for (int k = 0; k < C; ++k) gr[k] -= x[k];
+        store_vec<C, 1>(L, a.grad + r * a.P.ld, a.P.d, gr);
         if (a.F) a.F[r] = F;
     }
 }
 
 // ---------------------------------------------------------------------------
-// Persistent descent, one thread per pair: Algorithm 1 (MODE DESC_CD, cyclic
-// coordinate descent with finite differences) or gradient descent with the
-// adjoint (DESC_GD), the same iteration rules, stop tests, coarse-to-fine
-// phases, certificate and outputs as k_desc.  Threads without a pair take
-// the next one from the problem's work list (one atomic per warp) between
-// iterations.  v lives in registers; the per-coordinate steps and the
-// previous derivatives in shared memory ([component][thread],
-// conflict-free); x is read from global memory (cached) once per iteration.
+// Persistent descent, one pair per group of TPP lanes: Algorithm 1 (MODE
+// DESC_CD, cyclic coordinate descent with finite differences; one lane per
+// pair) or gradient descent with the adjoint (DESC_GD), the same iteration
+// rules, stop tests, coarse-to-fine phases, certificate and outputs as
+// k_desc.  Groups without a pair take the next one from the problem's work
+// list (one atomic per warp) between iterations.  The launch does nothing
+// unless the work list's length lies in [run_lo, run_hi).  v lives in
+// registers; the per-coordinate steps and the previous derivatives in shared
+// memory ([component][thread], conflict-free); x is read from global memory
+// (cached) once per iteration.
 // ---------------------------------------------------------------------------
-template <int C, int MODE>
-__global__ void __launch_bounds__(BLOCK, min_blocks<C>()) k_desc(DescArgs<float> a)
+template <int C, int MODE, int TPP>
+__global__ void __launch_bounds__(BLOCK, (min_blocks<C, TPP>())) k_desc(DescArgs<float> a)
 {
-    __shared__ float s_al[C][BLOCK], s_pr[C][BLOCK];
+    static_assert(MODE == DESC_GD || TPP == 1, "coordinate descent runs one lane per pair");
+    constexpr int CL = C / TPP;
+    constexpr unsigned LEAD = TPP == 1 ? FULL : 0x55555555u;  // the first lane of every group
+    const long long n = a.wl_count[a.problem];
+    if (n < a.run_lo || n >= a.run_hi) return;
+    __shared__ float s_al[CL][BLOCK], s_pr[CL][BLOCK];
     __shared__ float s_rec[MODE == DESC_GD ? 4 * REC : 1][BLOCK];
     const int tid = threadIdx.x, lane = tid & 31;
+    Lane<C, TPP> L;
+    L.load(a.P, lane);
+    const int lead = lane - L.gl;
     const int d = a.P.d;
-    const long long n = a.wl_count[a.problem];
     const long long begin = a.seg_begin[a.problem];
     const float eps_stop = (float)a.S.eps;
     const float fd_h = (float)a.S.fd_h;
@@ -446,21 +542,21 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<C>()) k_desc(DescArgs<float>
     bool active = false, exhausted = false;
     long long pid = 0, q = 0;
     int N = 1, Ncur = 1, it = 0, count = 0, kper = 0, bad = 0;
-    float t = 0.f, v[C];
+    float t = 0.f, v[CL];
 #pragma unroll
-    for (int i = 0; i < C; ++i) v[i] = 0.f;
+    for (int k = 0; k < CL; ++k) v[k] = 0.f;
 
     for (;;) {
-        // ---- refill: one atomic per warp for all lanes that need a pair ------
+        // ---- refill: one atomic per warp for all groups that need a pair -----
         const bool need = !active && !exhausted;
-        const unsigned nm = __ballot_sync(FULL, need);
+        const unsigned nm = __ballot_sync(FULL, need) & LEAD;
         if (nm) {
             const int leader = __ffs(nm) - 1;
             int base = 0;
             if (lane == leader) base = atomicAdd(a.cursor + a.problem, __popc(nm));
             base = __shfl_sync(FULL, base, leader);
             if (need) {
-                const long long j = (long long)base + __popc(nm & ((1u << lane) - 1u));
+                const long long j = (long long)base + __popc(nm & ((1u << lead) - 1u));
                 if (j >= n) {
                     exhausted = true;
                 } else {
@@ -470,18 +566,20 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<C>()) k_desc(DescArgs<float>
                     N = a.nsteps ? a.nsteps[q] : a.S.n_default;
                     t = a.t[q];
 #pragma unroll
-                    for (int i = 0; i < C; ++i) {
-                        s_al[i][tid] = (float)a.S.step;
-                        s_pr[i][tid] = 0.f;
+                    for (int k = 0; k < CL; ++k) {
+                        s_al[k][tid] = (float)a.S.step;
+                        s_pr[k][tid] = 0.f;
                     }
                     if (a.phase == 2) {
-                        load_vec<C>(a.vfin + pid * a.P.ld, d, v);  // the coarse level's v
+                        load_vec<C, TPP>(L, a.vfin + pid * a.P.ld, d, v);  // the coarse level's v
                     } else {
 #pragma unroll
-                        for (int i = 0; i < C; ++i)
-                            v[i] = (i < d) ? start_component<float>(a.S.seed, a.q_begin + q, slot, round, i,
+                        for (int k = 0; k < CL; ++k) {
+                            const int i = L.comp(k);
+                            v[k] = (i < d) ? start_component<float>(a.S.seed, a.q_begin + q, slot, round, i,
                                                                     a.S.guess_dist)
                                            : 0.f;
+                        }
                     }
                     it = count = kper = bad = 0;
                     Ncur = coarse ? max(1, N / a.S.coarse_div) : N;
@@ -495,46 +593,49 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<C>()) k_desc(DescArgs<float>
         const float *xr = a.x + q * a.P.ld;
         float u0, xv;  // <w, x>, <x, v>
         {
-            float x[C];
-            load_vec<C>(xr, d, x);
-            u0 = dot_w<C>(a.P, x);
-            xv = dot<C>(x, v);
+            float x[CL];
+            load_vec<C, TPP>(L, xr, d, x);
+            u0 = dot_w<C, TPP>(a.P, L, x);
+            xv = dot<C, TPP>(L, x, v);
         }
         // ---- one iteration -----------------------------------------------------
         bool stop = (it >= a.S.max_iters), conv = false;
         const float eps_lvl = coarse ? (float)a.S.coarse_eps : eps_stop;
         if (!stop) {
             if constexpr (MODE == DESC_GD) {
-                float gr[C];
+                float gr[CL];
                 const int K = ck_interval(Ncur, a.S.ck_interval);
-                gradient<C>(a.P, a.S.kahan, K, u0, xv, v, t, Ncur, gr, ck, seg, rec);
-                n_g++;
-                n_rk += Ncur;
-                n_adj += Ncur;
+                gradient<C, TPP>(a.P, L, a.S.kahan, K, u0, xv, v, t, Ncur, gr, ck, seg, rec);
+                if (L.gl == 0) {  // counted once per pair
+                    n_g++;
+                    n_rk += Ncur;
+                    n_adj += Ncur;
+                }
                 float big = 0.f;
                 bool fin = true;
 #pragma unroll
-                for (int i = 0; i < C; ++i) {
-                    const float g = gr[i] - ((i < d) ? __ldg(xr + i) : 0.f);
-                    float al = s_al[i][tid];
+                for (int k = 0; k < CL; ++k) {
+                    const int i = L.comp(k);
+                    const float g = gr[k] - ((i < d) ? __ldg(xr + i) : 0.f);
+                    float al = s_al[k][tid];
                     if (a.S.adapt) {
-                        const float prod = g * s_pr[i][tid];
+                        const float prod = g * s_pr[k][tid];
                         if (prod < 0.f) al *= (float)a.S.shrink;
                         else if (prod > 0.f) al = fminf(al * (float)a.S.grow, (float)a.S.step_max);
                     }
-                    const float st = al * g;
+                    const float st = __fmul_rn(al, g);
                     fin = fin && isfinite(st);
-                    v[i] -= st;
+                    v[k] = __fsub_rn(v[k], st);
                     big = fmaxf(big, fabsf(st));
-                    s_pr[i][tid] = g;
-                    s_al[i][tid] = al;
+                    s_pr[k][tid] = g;
+                    s_al[k][tid] = al;
                 }
-                if (!fin) big = INFINITY;
+                big = L.gmaxf(fin ? big : INFINITY);
                 ++it;
                 if (!(big < INFINITY)) { bad = 1; stop = true; }
                 if (a.S.halving_period > 0 && it % a.S.halving_period == 0) {
 #pragma unroll
-                    for (int i = 0; i < C; ++i) s_al[i][tid] *= 0.5f;
+                    for (int k = 0; k < CL; ++k) s_al[k][tid] *= 0.5f;
                 }
                 if (big < eps_lvl) conv = stop = true;
             } else {
@@ -542,12 +643,12 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<C>()) k_desc(DescArgs<float>
                 const float xj = __ldg(xr + jc);
                 float vp[C], Bn;
 #pragma unroll
-                for (int i = 0; i < C; ++i) vp[i] = v[i] + ((i == jc) ? fd_h : 0.f);
-                const float Fp = functional<C>(a.P, a.S.kahan, u0, fmaf(xj, fd_h, xv), vp, t, N, nullptr, 1, Bn);
+                for (int k = 0; k < C; ++k) vp[k] = v[k] + ((k == jc) ? fd_h : 0.f);
+                const float Fp = functional<C, 1>(a.P, L, a.S.kahan, u0, fmaf(xj, fd_h, xv), vp, t, N, nullptr, 1, Bn);
 #pragma unroll
-                for (int i = 0; i < C; ++i) vp[i] = v[i] - ((central && i == jc) ? fd_h : 0.f);
-                const float Fm = functional<C>(a.P, a.S.kahan, u0, central ? fmaf(-xj, fd_h, xv) : xv, vp, t, N,
-                                               nullptr, 1, Bn);
+                for (int k = 0; k < C; ++k) vp[k] = v[k] - ((central && k == jc) ? fd_h : 0.f);
+                const float Fm = functional<C, 1>(a.P, L, a.S.kahan, u0, central ? fmaf(-xj, fd_h, xv) : xv, vp, t, N,
+                                                  nullptr, 1, Bn);
                 n_f += 2;
                 n_rk += 2 * N;
                 const float dj = central ? (Fp - Fm) / (2.f * fd_h) : (Fp - Fm) / fd_h;
@@ -558,10 +659,10 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<C>()) k_desc(DescArgs<float>
                     else if (prod > 0.f) al = fminf(al * (float)a.S.grow, (float)a.S.step_max);
                     s_pr[jc][tid] = dj;
                 }
-                const float st = al * dj;
+                const float st = __fmul_rn(al, dj);
 #pragma unroll
-                for (int i = 0; i < C; ++i)
-                    if (i == jc) v[i] -= st;
+                for (int k = 0; k < C; ++k)
+                    if (k == jc) v[k] = __fsub_rn(v[k], st);
                 ++it;
                 if (!isfinite(st)) { bad = 1; stop = true; }
                 // steps 3-4 of Algorithm 1: reset on a move > eps, count a move < eps
@@ -571,61 +672,62 @@ __global__ void __launch_bounds__(BLOCK, min_blocks<C>()) k_desc(DescArgs<float>
                 if (a.S.halving_period > 0 && ++kper == a.S.halving_period) {
                     kper = 0;
 #pragma unroll
-                    for (int i = 0; i < C; ++i) s_al[i][tid] *= 0.5f;
+                    for (int k = 0; k < C; ++k) s_al[k][tid] *= 0.5f;
                 }
                 if (count >= d) conv = stop = true;
             }
             if (it >= a.S.max_iters) stop = true;
         }
         // ---- finished pair: certificate at the final v, then write it out -----
+        const bool first = L.gl == 0;  // one writer per pair
         if (stop && a.phase == 1) {
-            n_it += it;
-            float *vr = a.vfin + pid * a.P.ld;
-#pragma unroll
-            for (int i = 0; i < C; ++i)
-                if (i < d) vr[i] = v[i];
-            a.iters[pid] = it;
-            a.flags[pid] = (uint8_t)(bad << 1);
+            if (first) n_it += it;
+            store_vec<C, TPP>(L, a.vfin + pid * a.P.ld, d, v);
+            if (first) {
+                a.iters[pid] = it;
+                a.flags[pid] = (uint8_t)(bad << 1);
+            }
             active = false;
         } else if (stop) {
             const int cap = (!conv && !bad) ? 1 : 0;
-            n_it += it;
-            n_pairs++;
-            n_sumN += N;
-            float gam[C], Bn;
-            load_vec<C>(xr, d, gam);
-            const float F = functional_gamma<C>(a.P, a.S.kahan, u0, dot<C>(gam, v), v, t, N, gam, Bn);
-            // Hopf residual |gamma(0) - grad g*(p(0))| / (1 + |gamma(0)|)
-            float num = 0.f, den = 0.f;
-#pragma unroll
-            for (int i = 0; i < C; ++i) {
-                const float p = fmaf(Bn, a.P.rw[i], v[i]);
-                const float diff = gam[i] - fmaf(a.P.rg2[i], p, a.P.rga[i]);
-                num = fmaf(diff, diff, num);
-                den = fmaf(gam[i], gam[i], den);
+            if (first) {
+                n_it += it;
+                n_pairs++;
+                n_sumN += N;
+                n_cert += N;
             }
-            const float r = sqrtf(num) / (1.f + sqrtf(den));
-            n_cert += N;
-            float *vr = a.vfin + pid * a.P.ld;
+            float gam[CL], Bn;
+            load_vec<C, TPP>(L, xr, d, gam);
+            const float F = functional_gamma<C, TPP>(a.P, L, a.S.kahan, u0, dot<C, TPP>(L, gam, v), v, t, N, gam, Bn);
+            // Hopf residual |gamma(0) - grad g*(p(0))| / (1 + |gamma(0)|)
+            Acc<TPP> num, den;
 #pragma unroll
-            for (int i = 0; i < C; ++i)
-                if (i < d) vr[i] = v[i];
-            const int prior = (a.phase == 2) ? a.iters[pid] : 0;
-            const uint8_t fprior = (a.phase == 2) ? (uint8_t)(a.flags[pid] & 2) : (uint8_t)0;
-            a.iters[pid] = prior + it;
-            a.flags[pid] = (uint8_t)(cap | (bad << 1) | fprior);
-            const bool fin = isfinite(F) && isfinite(r);
-            uint8_t pass;
-            if (!fin) pass = 0;
-            else if ((double)r < CERT_BAND_LO * a.tol) pass = 1;
-            else if ((double)r > CERT_BAND_HI * a.tol) pass = 0;
-            else pass = 2;
-            a.pF[pid] = (double)F;
-            a.pR[pid] = (double)r;
-            a.pP[pid] = pass;
-            if (pass == 2) {
-                const int pos = atomicAdd(a.amb_count + a.problem, 1);
-                a.amb_wl[begin + pos] = (int32_t)pid;
+            for (int k = 0; k < CL; ++k) {
+                const float p = fmaf(Bn, L.w(a.P, k), v[k]);
+                const float diff = gam[k] - fmaf(L.g2(a.P, k), p, L.ga(a.P, k));
+                num.fma_(k, diff, diff);
+                den.fma_(k, gam[k], gam[k]);
+            }
+            const float r = sqrtf(L.total(num.a0, num.a1)) / (1.f + sqrtf(L.total(den.a0, den.a1)));
+            store_vec<C, TPP>(L, a.vfin + pid * a.P.ld, d, v);
+            if (first) {
+                const int prior = (a.phase == 2) ? a.iters[pid] : 0;
+                const uint8_t fprior = (a.phase == 2) ? (uint8_t)(a.flags[pid] & 2) : (uint8_t)0;
+                a.iters[pid] = prior + it;
+                a.flags[pid] = (uint8_t)(cap | (bad << 1) | fprior);
+                const bool fin = isfinite(F) && isfinite(r);
+                uint8_t pass;
+                if (!fin) pass = 0;
+                else if ((double)r < CERT_BAND_LO * a.tol) pass = 1;
+                else if ((double)r > CERT_BAND_HI * a.tol) pass = 0;
+                else pass = 2;
+                a.pF[pid] = (double)F;
+                a.pR[pid] = (double)r;
+                a.pP[pid] = pass;
+                if (pass == 2) {
+                    const int pos = atomicAdd(a.amb_count + a.problem, 1);
+                    a.amb_wl[begin + pos] = (int32_t)pid;
+                }
             }
             active = false;
         }

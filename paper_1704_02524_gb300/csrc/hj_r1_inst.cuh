@@ -19,10 +19,10 @@ cudaError_t launch_r1_grad(const void *a, int grid, cudaStream_t s)
     r1::k_grad<C><<<grid, BLOCK, 0, s>>>(*(const RowArgs<float> *)a);
     return cudaGetLastError();
 }
-template <int C, int MODE>
+template <int C, int MODE, int TPP>
 cudaError_t launch_r1_desc(const void *a, int grid, cudaStream_t s)
 {
-    r1::k_desc<C, MODE><<<grid, BLOCK, 0, s>>>(*(const DescArgs<float> *)a);
+    r1::k_desc<C, MODE, TPP><<<grid, BLOCK, 0, s>>>(*(const DescArgs<float> *)a);
     return cudaGetLastError();
 }
 
@@ -34,10 +34,12 @@ void register_r1(Registry &r)
     k.f_eval = (const void *)&r1::k_eval<C>;
     k.grad = &launch_r1_grad<C>;
     k.f_grad = (const void *)&r1::k_grad<C>;
-    k.cd = &launch_r1_desc<C, DESC_CD>;
-    k.f_cd = (const void *)&r1::k_desc<C, DESC_CD>;
-    k.gd = &launch_r1_desc<C, DESC_GD>;
-    k.f_gd = (const void *)&r1::k_desc<C, DESC_GD>;
+    k.cd = &launch_r1_desc<C, DESC_CD, 1>;
+    k.f_cd = (const void *)&r1::k_desc<C, DESC_CD, 1>;
+    k.gd = &launch_r1_desc<C, DESC_GD, 1>;
+    k.f_gd = (const void *)&r1::k_desc<C, DESC_GD, 1>;
+    k.gd_lat = &launch_r1_desc<C, DESC_GD, 2>;
+    k.f_gd_lat = (const void *)&r1::k_desc<C, DESC_GD, 2>;
 }
 
 }  // namespace hjd

@@ -318,8 +318,22 @@ def ellipse_sigma(d: int) -> np.ndarray:
     return s
 
 
+def _paper_precision(precision: Optional[str], fp32_every_row: bool) -> str:
+    """Default precision of a paper-numerics workload: binary32 where its
+    solve meets the 1e-4 gate against the FP64 oracle on every row, else
+    FP64 (the paper's own precision).  The paper's forward differences with
+    sigma = 1e-3 carry ~eps |F| / sigma ~ 1e-4 of binary32 rounding in every
+    derivative; on the flat or kinked functionals of Sec. 6's Examples 2, 4
+    and 5 and of the Huygens form that noise moves where Algorithm 1 stops
+    (or which basin a start ends in) by more than the gate."""
+    if precision is not None:
+        return precision
+    return "fp32" if fp32_every_row else "fp64"
+
+
 def bump_ex3(n_side: int = 128, d: int = 2, sign: float = 1.0, t: float = 0.3, ds: float = 0.02,
-             fd_h: float = 1e-3, n_guesses: int = 5, precision: str = "fp32", principle: int = LAX) -> Workload:
+             fd_h: float = 1e-3, n_guesses: int = 5, precision: Optional[str] = None,
+             principle: int = LAX) -> Workload:
     """Sec. 6 Example 3 in the paper's numerics: H = sign c(x)|p| with
     c = 1 + 3 exp(-4 |x - (1,1,0,...)|^2), the ellipse data g, the Lax
     functional, on the n_side x n_side grid over the cross-section
@@ -342,11 +356,12 @@ def bump_ex3(n_side: int = 128, d: int = 2, sign: float = 1.0, t: float = 0.3, d
     pname = {LAX: "lax", HUYGENS: "huygens", HOPF: "hopf"}[principle]
     name = f"bump_norm_d{d}_{'plus' if sign > 0 else 'minus'}_{pname}_paper"
     return Workload(name, [P], X, np.full(nq, t), np.full(nq, N, np.int32), np.zeros(nq, np.int32),
-                    paper_solver(fd_h=fd_h, n_guesses=n_guesses, max_trials=n_guesses), precision)
+                    paper_solver(fd_h=fd_h, n_guesses=n_guesses, max_trials=n_guesses),
+                    _paper_precision(precision, principle != HUYGENS))
 
 
 def split_ex5(n_side: int = 128, d: int = 2, k: int = 1, t: float = 0.3, ds: float = 0.02, fd_h: float = 1e-3,
-              n_guesses: int = 20, precision: str = "fp32", descent: str = "paper") -> Workload:
+              n_guesses: int = 20, precision: Optional[str] = None, descent: str = "paper") -> Workload:
     """Sec. 6 Example 5: H = c(x)|p_1..k| - c(-x)|p_k+1..d| with
     c(x) = 2 (1 + 3 exp(-4 |x - (1,1,0,...)|^2)), the ellipse data, the Hopf
     functional, on the n_side x n_side grid over [-3,3]^2 x {0}^(d-2) at
@@ -372,7 +387,7 @@ def split_ex5(n_side: int = 128, d: int = 2, k: int = 1, t: float = 0.3, ds: flo
         solver = solver_constants(quad="euler_rect", grad="adjoint_cg", step=0.05, step_max=1.0, max_iters=500,
                                   eps=1e-7, n_guesses=n_guesses, max_trials=n_guesses, max_rounds=0, coarse_div=1)
     return Workload(f"split_norm_d{d}_hopf_{descent}", [P], X, np.full(nq, t), np.full(nq, N, np.int32),
-                    np.zeros(nq, np.int32), solver, precision)
+                    np.zeros(nq, np.int32), solver, _paper_precision(precision, False))
 
 
 def _grid(n_side: int, d: int) -> np.ndarray:
@@ -384,7 +399,7 @@ def _grid(n_side: int, d: int) -> np.ndarray:
 
 
 def harmonic_ex2(n_side: int = 128, d: int = 2, sign: float = -1.0, t: float = 0.5, ds: float = 0.02,
-                 n_guesses: int = 5, precision: str = "fp32", rosenbrock: bool = False) -> Workload:
+                 n_guesses: int = 5, precision: Optional[str] = None, rosenbrock: bool = False) -> Workload:
     """Sec. 6 Example 2: H = sign (|p|^2 + |x|^2)/2 with the ellipse data, the
     Hopf functional for both signs, on the n_side x n_side grid over
     [-3,3]^2 x {0}^(d-2) (t = 0.5 at d = 2; the paper's d = 7 run uses
@@ -404,11 +419,12 @@ def harmonic_ex2(n_side: int = 128, d: int = 2, sign: float = -1.0, t: float = 0
     pname = "lax_rosenbrock" if rosenbrock else "hopf"
     return Workload(f"harmonic_d{d}_{'plus' if sign > 0 else 'minus'}_{pname}_paper", [P], X, np.full(nq, t),
                     np.full(nq, N, np.int32), np.zeros(nq, np.int32),
-                    paper_solver(step=1.0 / 3.0, n_guesses=n_guesses, max_trials=n_guesses), precision)
+                    paper_solver(step=1.0 / 3.0, n_guesses=n_guesses, max_trials=n_guesses),
+                    _paper_precision(precision, False))
 
 
 def evans_ex4(n_side: int = 128, t: float = 0.1, ds: float = 0.005, n_guesses: int = 5,
-              precision: str = "fp32") -> Workload:
+              precision: Optional[str] = None) -> Workload:
     """Sec. 6 Example 4: H = -c(x) p_1 + 2|p_2| - |p| - 1 with
     c = 2 (1 + 3 exp(-4 |x - (1,1)|^2)), d = 2, the ellipse data, the Hopf
     functional, on the n_side x n_side grid over [-3,3]^2 at t = 0.1, in the
@@ -420,7 +436,8 @@ def evans_ex4(n_side: int = 128, t: float = 0.1, ds: float = 0.005, n_guesses: i
     nq = X.shape[0]
     N = int(round(t / ds))
     return Workload("evans_d2_hopf_paper", [P], X, np.full(nq, t), np.full(nq, N, np.int32), np.zeros(nq, np.int32),
-                    paper_solver(step=1.0 / 4.0, n_guesses=n_guesses, max_trials=n_guesses), precision)
+                    paper_solver(step=1.0 / 4.0, n_guesses=n_guesses, max_trials=n_guesses),
+                    _paper_precision(precision, False))
 
 
 def linear_game(nq: int = 65536, d: int = 16, t: float = 0.8, n_steps: int = 64, r_d: float = 0.4,
@@ -458,9 +475,17 @@ WORKLOADS = {
 }
 
 
+def plain_cd_solver(solver: Dict, d: int, sweeps: int = 100) -> Dict:
+    """Constants of the plain path for a workload whose own descent is the
+    adjoint gradient descent: Algorithm 1 (cyclic coordinate descent) with
+    central differences, h = 2^-10 (the binary32 functional carries ~1e-6
+    absolute rounding, so smaller steps drown the difference in noise), at
+    most `sweeps` sweeps, the same per-coordinate step control, starts,
+    reseeding and certificate."""
+    c = dict(solver, grad="fd_central", fd_h=2.0 ** -10, max_iters=sweeps * d, coarse_div=1)
+    return c
+
+
 def c3_cd_solver() -> Dict:
-    """Constants of the plain path on the d=20 Hopf workload: Algorithm 1
-    (cyclic coordinate descent) with central differences, h = 2^-10 (the
-    binary32 functional carries ~1e-6 absolute rounding, so smaller steps
-    drown the difference in noise), at most 100 sweeps."""
-    return solver_constants(grad="fd_central", fd_h=2.0 ** -10, max_iters=100 * 20, n_guesses=16)
+    """The plain path's constants on the d=20 Hopf workload (plain_cd_solver)."""
+    return plain_cd_solver(solver_constants(n_guesses=16), 20)
