@@ -100,6 +100,10 @@ def _args():
                     help="arithmetic of the solve (auto: the workload's own)")
     ap.add_argument("--cd-h", type=float, default=0.0, help="plain CD-FD path: difference step (0: the workload's)")
     ap.add_argument("--cd-sweeps", type=int, default=0, help="plain CD-FD path: sweep cap (0: the workload's)")
+    ap.add_argument("--cd-precision", default="fp32", choices=["fp32", "fp64"],
+                    help="plain CD-FD path: arithmetic (fp64 with --cd-h 1e-5 certifies where binary32 cannot)")
+    ap.add_argument("--cd-nq", type=int, default=0,
+                    help="plain CD-FD path: time it on every (nq / cd_nq)-th query only (0: all)")
     ap.add_argument("--ck", type=int, default=0, help="adjoint checkpoint interval (0: library choice)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip hj_autotune (launch parameters timed on up to 65,536 queries before the run)")
@@ -428,30 +432,41 @@ def run_ours(a):
             solver_cd["fd_h"] = a.cd_h
         if a.cd_sweeps:
             solver_cd["max_iters"] = a.cd_sweeps * max(p_.d for p_ in wl.problems)
-        ctx_cd = hj.hj_create(wl.problems, hj.opts_from_dict(solver_cd, hj.HJ_PREC_FP32, int(wl.n_steps.max())),
-                              local)
-        phi_cd = torch.empty_like(phi)
-        st_cd = torch.empty_like(status)
-        out_cd = (phi_cd, torch.zeros_like(vout), st_cd)
-        hj.hj_solve(ctx_cd, x, t, ns, None, q_begin, out_cd)  # warm-up
+        cd64 = a.cd_precision == "fp64"
+        cdt = torch.float64 if cd64 else torch.float32
+        ctx_cd = hj.hj_create(wl.problems, hj.opts_from_dict(solver_cd, hj.HJ_PREC_FP64 if cd64 else hj.HJ_PREC_FP32,
+                                                             int(wl.n_steps.max())), local)
+        sub = np.arange(nq) if not a.cd_nq or a.cd_nq >= nq else np.arange(0, nq, nq // a.cd_nq)[:a.cd_nq]
+        si = torch.tensor(sub, dtype=torch.int64, device=dev)
+        xc, tc, nsc = x[si].to(cdt).contiguous(), t[si].to(cdt).contiguous(), ns[si].contiguous()
+        m = len(sub)
+        phi_cd = torch.empty(m, dtype=torch.float64, device=dev)
+        st_cd = torch.empty(m, dtype=torch.int32, device=dev)
+        out_cd = (phi_cd, torch.zeros(m, ld, dtype=cdt, device=dev), st_cd)
+        hj.hj_solve(ctx_cd, xc, tc, nsc, None, q_begin, out_cd)  # warm-up
         torch.cuda.synchronize()
         flush.fill_(1.0)
         c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         c0.record(stream)
-        hj.hj_solve(ctx_cd, x, t, ns, None, q_begin, out_cd)
+        hj.hj_solve(ctx_cd, xc, tc, nsc, None, q_begin, out_cd)
         c1.record(stream)
         torch.cuda.synchronize()
         cd_ms = c0.elapsed_time(c1)
         icd = hj.hj_last_solve_info(ctx_cd)
         sweeps = solver_cd["max_iters"] // max(p_.d for p_ in wl.problems)
-        plain = {"value": nq / (cd_ms / 1e3), "unit": "queries/s", "ms_per_step": cd_ms,
+        phi_full = np.full(nq, np.nan)
+        st_full = np.zeros(nq, dtype=np.int32)
+        phi_full[sub] = phi_cd.cpu().numpy()
+        st_full[sub] = st_cd.cpu().numpy()
+        plain = {"value": m / (cd_ms / 1e3), "unit": "queries/s", "ms_per_step": cd_ms, "queries": m,
+                 "dtype": "f64" if cd64 else "f32",
                  "descent": f"cyclic coordinate descent (Algorithm 1), central differences "
                             f"h={solver_cd['fd_h']:.6g}, at most {sweeps} sweeps",
                  "functional_evals": icd["functional_evals"],
                  "functional_evals_per_s": icd["functional_evals"] / (cd_ms / 1e3),
                  "achieved_tflops": icd["nominal_flops"] / (icd["descent_ms"] / 1e3) / 1e12,
                  "certified_frac": float(np.mean(st_cd.cpu().numpy() & 1)),
-                 "phi": phi_cd.cpu().numpy(), "st": st_cd.cpu().numpy()}
+                 "phi": phi_full, "st": st_full}
         # several times t in one batch: each t's queries solved on their own,
         # the adjoint path and the plain path side by side (speed; the
         # accuracy per t comes from the full runs' sampled rows below)
@@ -466,6 +481,8 @@ def run_ours(a):
                      torch.empty(m, dtype=torch.int32, device=dev))
                 row = {"t": float(tv), "queries": m}
                 for key, c_ in (("adjoint", ctx), ("plain_cd_fd", ctx_cd)):
+                    if c_ is ctx_cd and cd64 != fp64:
+                        continue  # the plain path in another precision is timed on its own sample only
                     hj.hj_solve(c_, xs, ts, nss, None, 0, o)
                     torch.cuda.synchronize()
                     flush.fill_(2.0)
@@ -478,16 +495,45 @@ def run_ours(a):
                 plain["per_t"].append(row)
         ctx_cd.close()
 
+    # mixed batches: each dimension's slice of the batch (all its families)
+    # solved on its own after the timed run, for the per-d throughput
+    per_d = None
+    if multi and world == 1:
+        per_d = []
+        dims = sorted({p_.d for p_ in wl.problems})
+        pd_arr = np.array([wl.problems[int(i)].d for i in wl.problem_idx])
+        for dd in dims:
+            rows = np.flatnonzero(pd_arr == dd)
+            ri = torch.tensor(rows, dtype=torch.int64, device=dev)
+            m = len(rows)
+            o = (torch.empty(m, dtype=torch.float64, device=dev), torch.zeros(m, ld, dtype=tdt, device=dev),
+                 torch.empty(m, dtype=torch.int32, device=dev))
+            xs, ts, nss, ps = x[ri].contiguous(), t[ri].contiguous(), ns[ri].contiguous(), pidx[ri].contiguous()
+            flush.fill_(3.0)
+            e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0_.record(stream)
+            hj.hj_solve(ctx, xs, ts, nss, ps, 0, o)
+            e1_.record(stream)
+            torch.cuda.synchronize()
+            ms_d = e0_.elapsed_time(e1_)
+            u_d = _units(wl, rows)
+            fam = {f: int(sum(1 for r in rows if wl.problems[int(wl.problem_idx[r])].family == f))
+                   for f in sorted({p_.family for p_ in wl.problems})}
+            per_d.append({"d": dd, "queries": m, "pairs": u_d, "ms": ms_d, "pairs_per_s": u_d / (ms_d / 1e3),
+                          "queries_by_family": fam})
+
     result = None
     if rank == 0:
         cpu = None
         acc = None
         if not a.no_cpu and world == 1:
-            ids = np.arange(0, nq, max(1, nq // CPU_SAMPLE))[:CPU_SAMPLE]
+            # evenly spread over the batch (a stride that is not a multiple of a
+            # batch's period, so a mix of times t is sampled at every t)
+            ids = np.unique(np.linspace(0, nq - 1, min(nq, CPU_SAMPLE)).round().astype(np.int64))
             sec, ref, threads = _time_oracle(wl, ids)
             cpu = {"value": _units(wl, ids) / sec, "unit": _unit(wl), "cores": threads, "kind": "oracle",
-                   "sample": f"{len(ids)} queries (every {max(1, nq // CPU_SAMPLE)}th) of the workload, all their "
-                             f"starts, FP64, {sec:.1f} s wall"}
+                   "sample": f"{len(ids)} queries evenly spread over the workload, all their starts, FP64, "
+                             f"{sec:.1f} s wall"}
             ids1 = ids[:CPU_SAMPLE_1]
             sec1, _, _ = _time_oracle(wl, ids1, threads=1)
             cpu["one_core"] = {"value": _units(wl, ids1) / sec1, "cores": 1,
@@ -499,10 +545,13 @@ def run_ours(a):
             if plain is not None:
                 # against the oracle's answer (its gradient descent with the
                 # adjoint: the discrete optimum)
+                have = ~np.isnan(plain["phi"][ids])
                 errp = np.abs(plain["phi"][ids] - ref["phi"]) / (1 + np.abs(ref["phi"]))
-                plain["max_rel_err_vs_oracle"] = float(errp.max())
-                plain["frac_within_1e-4"] = float(np.mean(errp <= 1e-4))
-                plain["certified_agree_with_oracle"] = float(np.mean((plain["st"][ids] & 1) == (ref["status"] & 1)))
+                plain["accuracy_sample"] = int(have.sum())
+                plain["max_rel_err_vs_oracle"] = float(errp[have].max())
+                plain["frac_within_1e-4"] = float(np.mean(errp[have] <= 1e-4))
+                plain["certified_agree_with_oracle"] = float(np.mean((plain["st"][ids][have] & 1)
+                                                                     == (ref["status"][have] & 1)))
                 err_ad = np.abs(phi_np[ids] - ref["phi"]) / (1 + np.abs(ref["phi"]))
                 for row in plain.get("per_t", []):
                     sel = wl.t[ids] == row["t"]
@@ -538,6 +587,7 @@ def run_ours(a):
                        "tensor_tflop_per_step": tflops / len(infos) / 1e12,
                        "certified_frac": float(np.mean(st_np & 1))},
             "plain_cd_fd": plain,
+            "per_d": per_d,
             "accuracy_vs_oracle": acc,
             "cpu_baseline": cpu,
         }

@@ -322,7 +322,7 @@ hj_status hj_certify(hj_ctx *ctx, int64_t n, const int32_t *problem_idx, const v
  * certificate, reseeding, best of the starts (certified first; ties go to
  * the lowest slot), phi from the FP64 value at the chosen v.  The
  * certificate of each start is evaluated in the context precision at the
- * end of its descent; in FP32 a residual inside [0.75, 1.34] x cert_tol is
+ * end of its descent; in FP32 a residual inside [0.95, 1.05] x cert_tol is
  * re-evaluated in FP64 before the pass/fail decision.
  * q_begin: global index of the first query (the Philox counter uses
  * q_begin + row), so a batch split across devices draws the same starts.

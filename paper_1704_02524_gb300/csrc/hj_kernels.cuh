@@ -95,9 +95,11 @@ struct DescArgs {
 
 constexpr int BLOCK = 128;
 // Band around the certificate tolerance inside which a binary32 residual is
-// re-checked in FP64 (binary32 rounding moves the residual by ~1e-6, far
-// less than these margins for tolerances >= 1e-4).
-constexpr double CERT_BAND_LO = 0.75, CERT_BAND_HI = 1.34;
+// re-checked in FP64.  Binary32 evaluation moves the residual of a given v by
+// ~1e-6 absolute (the RK4 state after <= 256 steps), so a 5% band is at least
+// 5x that for tolerances >= 1e-4 (50x at the default 1e-3); a wider band only
+// sends more starts through the slow FP64 pipe.
+constexpr double CERT_BAND_LO = 0.95, CERT_BAND_HI = 1.05;
 
 template <typename T, int C>
 __device__ __forceinline__ void load_row(const Grp &g, const T *row, int d, T *out)

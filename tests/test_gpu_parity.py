@@ -832,8 +832,12 @@ def test_plain_cd_fd_d20_solve_matches_oracle_with_the_same_constants(hj):
     # the plain path of the headline comparison: Algorithm 1 (cyclic
     # coordinate descent) with central differences h = 2^-10, per-coordinate
     # step control, at most 100 sweeps, on the d=20 Hopf workload, against the
-    # FP64 oracle running the same constants; and its answer against the
-    # adjoint descent's (the discrete optimum)
+    # FP64 oracle running the same constants: every row, same certificates.
+    # (Against the adjoint descent's answer, the discrete optimum, this plain
+    # method misses query 30 here, identically in FP64: h = 2^-10 spans the
+    # 1e-3-wide smoothing of |p_i|, the difference quotients' bias leaves the
+    # better optimum's starts with residual 1.1e-3 > 1e-3, and the
+    # certified-first rule returns the other basin.)
     wl = W.c3_smooth_nonconvex(nq=32)
     wl.solver = W.c3_cd_solver()
     phi, v, st, ref, info = _solve_both(hj, wl, wl.nq)
@@ -841,9 +845,6 @@ def test_plain_cd_fd_d20_solve_matches_oracle_with_the_same_constants(hj):
     assert info["functional_evals"] > 0 and info["gradient_evals"] == 0
     assert np.all(err <= 1e-4), (err.max(), int(np.argmax(err)))
     assert np.array_equal(st & 1, ref["status"] & 1)
-    gd = W.c3_smooth_nonconvex(nq=32)
-    ref_gd = O.solve(oracle_problem(gd.problems[0]), oracle_opts(gd.solver, 16), gd.x, gd.t, gd.n_steps)
-    assert np.all(rel_err(phi, ref_gd["phi"]) <= 1e-4)
 
 
 def test_solve_counters_do_not_depend_on_the_lanes_per_pair(hj):
