@@ -50,6 +50,12 @@ WORKLOADS = {
                                     "points/s (H = c(x)|p|, d=2 cross-section grid, the paper's numerics)",
                                     "Algorithm 1 (cyclic coordinate descent, alpha halving), forward "
                                     "differences, forward Euler with the rectangle rule"),
+    "bump_norm_d2_plus_huygens_paper": (lambda nq: W.bump_ex3(n_side=max(1, int(round(nq ** 0.5))),
+                                                               principle=W.HUYGENS, ds=0.005), 16384,
+                                        "points/s (Example 3 with the Huygens form F^2, d=2 grid, the paper's "
+                                        "numerics)",
+                                        "Algorithm 1 (alpha halving), forward differences, forward Euler; F^2 = the "
+                                        "smallest g over the solver grid"),
     "split_norm_d2_hopf_paper": (lambda nq: W.split_ex5(n_side=max(1, int(round(nq ** 0.5)))), 16384,
                                  "points/s (Example 5 H = c(x)|p_1| - c(-x)|p_2|, d=2 grid, the paper's numerics)",
                                  "Algorithm 1, forward differences, forward Euler with the rectangle rule; 20 starts"),
@@ -80,7 +86,8 @@ L2_FLUSH_BYTES = 256 << 20
 # launch's traffic grows with the number of (query, start) pairs, so it is
 # scaled by queries / queries captured.  None: not captured for the current
 # kernel.
-TRAFFIC = {"smooth_nonconvex_d20_hopf": None, "linear_quad_d64_lax": (4096, 28.598e9 + 42.637e9)}
+TRAFFIC = {"smooth_nonconvex_d20_hopf": (16384, 26.739e6 + 157.018e6),
+           "linear_quad_d64_lax": (4096, 28.598e9 + 42.637e9)}
 
 
 def _args():
