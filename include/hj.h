@@ -164,9 +164,15 @@ typedef enum { HJ_PREC_FP32 = 0, HJ_PREC_FP64 = 1 } hj_precision;
  * descent direction.  Exact line searches on quadratic functionals (the
  * linear-quadratic family), whose conditioning defeats plain gradient steps.
  * Round 0 of hj_solve runs n_guesses starts per query (Philox4x32-10 draws
- * keyed by `seed`, counter (component/4, slot | round<<16, query id));
- * then up to `max_rounds` rounds restart failed starts, in slot order,
- * while fewer than `max_trials` starts of that query have run.
+ * keyed by `seed`, counter (component/4, slot | round<<16, query id)).
+ * Reseeding (Sec. 4.3, Sec. 5: at most max_trials independent trials per
+ * query): with max_rounds >= 1, a query some of whose starts failed the
+ * certificate runs the rest of its budget, max_trials - n_guesses trials,
+ * in one more round; restart j uses the draw (slot S[j mod |S|], round
+ * 1 + j / |S|), S the failed slots in slot order.  max_rounds = 0 turns
+ * reseeding off (values above 1 act as 1).  The answer is the best trial:
+ * certified first, then the smallest functional, ties to the lowest trial
+ * (starts in slot order, then restarts in order).
  * guess_dist: 0 = uniform on [-2,2]^d (Sec. 5), 1 = Irwin-Hall(12) N(0,1)
  * approximation.  cert_tol: certificate tolerance on the relative residual
  *   Lax  |p(0) - grad g(gamma(0))| / (1 + |p(0)|),
@@ -249,7 +255,7 @@ typedef struct {
  * (hj_last_solve_info); times come from CUDA events on the solve's stream. */
 typedef struct {
     int64_t n_queries;
-    int64_t n_pairs;            /* (query, start) pairs run, reseeds included      */
+    int64_t n_pairs;            /* (query, trial) pairs run, restarts included     */
     int64_t iterations;         /* descent iterations summed over pairs             */
     int64_t functional_evals;   /* forward functional evaluations                   */
     int64_t gradient_evals;     /* adjoint gradients                                */
@@ -259,7 +265,8 @@ typedef struct {
     double certify_flops;       /* arithmetic of the in-kernel certificate passes   */
     int threads_per_pair;       /* of the first problem's descent launch            */
     int comps_per_thread;
-    int descent_launches;       /* rounds run (each: one descent launch per problem) */
+    int descent_launches;       /* rounds run (round 0 and, with reseeding, one
+                                   reseed round; each one descent launch per problem) */
     double descent_ms;          /* device time of the descent launches (CUDA events) */
     double certify_ms;          /* device time of the certificate launches           */
     double total_ms;            /* device time of the whole hj_solve                 */

@@ -105,8 +105,10 @@ def _load():
     lib.orc_certify.restype = C.c_double
     _IP = C.POINTER(C.c_int)
     lib.orc_solve_query.argtypes = [C.POINTER(_Problem), C.POINTER(_Opts), C.c_int64, _DP, C.c_double, C.c_int,
-                                    _DP, _DP, _DP, _DP, _IP, _IP, _IP, _DP]
+                                    _DP, _DP, _DP, _DP, _IP, _IP, _IP, _DP, _IP]
     lib.orc_solve_query.restype = C.c_int
+    lib.orc_trials.argtypes = [C.POINTER(_Opts)]
+    lib.orc_trials.restype = C.c_int
     _lib = lib
     return lib
 
@@ -273,8 +275,11 @@ def solve(problems, O: Opts, x, t, N, problem_idx=None, query_ids=None, threads:
     query_ids   : [nq] global query index used in the Philox counter (None: 0..nq-1)
     guesses     : per-problem number of initial guesses (None: O.n_guesses for all)
     O may also be a list with one Opts per problem (each with its own guesses).
-    Returns a dict of arrays: phi, v [nq, ld], status, and per-slot diagnostics
-    ([nq, G] with G the largest guess count; unused slots stay NaN / 0).
+    Returns a dict of arrays: phi, v [nq, ld], status, and per-trial
+    diagnostics ([nq, T] with T the largest trial count, guesses plus the
+    reseed budget; trials that did not run stay NaN / -1): slot_F, slot_res,
+    slot_pass, slot_iters, slot_round, slot_slot (the slot of the draw),
+    slot_v [nq, T, ld].  Trial g < guesses is slot g.
     """
     lib = _load()
     probs = problems if isinstance(problems, (list, tuple)) else [problems]
@@ -296,35 +301,39 @@ def solve(problems, O: Opts, x, t, N, problem_idx=None, query_ids=None, threads:
     N = np.broadcast_to(np.asarray(N, dtype=np.int64), (nq,)).copy()
     pidx = np.zeros(nq, dtype=np.int64) if problem_idx is None else np.asarray(problem_idx, dtype=np.int64)
     qids = np.arange(nq, dtype=np.int64) if query_ids is None else np.asarray(query_ids, dtype=np.int64)
-    G = max(gper)
+    tper = [lib.orc_trials(C.byref(o)) for o in copts]
+    T = max(tper)
     phi = np.full(nq, np.nan)
     vout = np.full((nq, ld), np.nan)
     status = np.zeros(nq, dtype=np.int32)
-    sF = np.full((nq, G), np.nan)
-    sR = np.full((nq, G), np.nan)
-    sP = np.zeros((nq, G), dtype=np.int32)
-    sI = np.zeros((nq, G), dtype=np.int32)
-    sRd = np.zeros((nq, G), dtype=np.int32)
-    sV = np.full((nq, G, ld), np.nan)
+    sF = np.full((nq, T), np.nan)
+    sR = np.full((nq, T), np.nan)
+    sP = np.zeros((nq, T), dtype=np.int32)
+    sI = np.zeros((nq, T), dtype=np.int32)
+    sRd = np.full((nq, T), -1, dtype=np.int32)
+    sS = np.full((nq, T), -1, dtype=np.int32)
+    sV = np.full((nq, T, ld), np.nan)
     _IP = C.POINTER(C.c_int)
 
     def one(q):
         P = probs[pidx[q]]
         d = P.d
-        g = gper[pidx[q]]
+        g = tper[pidx[q]]
         xq = np.ascontiguousarray(x[q, :d])
         ph = C.c_double(0.0)
         vs = np.zeros(d)
-        f, r_ = np.zeros(g), np.zeros(g)
-        pa, it, rd = np.zeros(g, dtype=np.int32), np.zeros(g, dtype=np.int32), np.zeros(g, dtype=np.int32)
-        sv = np.zeros(g * d)
+        f, r_ = np.full(g, np.nan), np.full(g, np.nan)
+        pa, it = np.zeros(g, dtype=np.int32), np.zeros(g, dtype=np.int32)
+        rd, sl = np.full(g, -1, dtype=np.int32), np.full(g, -1, dtype=np.int32)
+        sv = np.full(g * d, np.nan)
         st = lib.orc_solve_query(C.byref(cprobs[pidx[q]]), C.byref(copts[pidx[q]]), int(qids[q]), _dp(xq),
                                  float(t[q]), int(N[q]), C.byref(ph), _dp(vs), _dp(f), _dp(r_),
-                                 pa.ctypes.data_as(_IP), it.ctypes.data_as(_IP), rd.ctypes.data_as(_IP), _dp(sv))
+                                 pa.ctypes.data_as(_IP), it.ctypes.data_as(_IP), rd.ctypes.data_as(_IP), _dp(sv),
+                                 sl.ctypes.data_as(_IP))
         phi[q] = ph.value
         vout[q, :d] = vs
         status[q] = st
-        sF[q, :g], sR[q, :g], sP[q, :g], sI[q, :g], sRd[q, :g] = f, r_, pa, it, rd
+        sF[q, :g], sR[q, :g], sP[q, :g], sI[q, :g], sRd[q, :g], sS[q, :g] = f, r_, pa, it, rd, sl
         sV[q, :g, :d] = sv.reshape(g, d)
 
     nthreads = threads or default_threads()
@@ -335,4 +344,4 @@ def solve(problems, O: Opts, x, t, N, problem_idx=None, query_ids=None, threads:
         with ThreadPoolExecutor(max_workers=nthreads) as ex:
             list(ex.map(one, range(nq)))
     return dict(phi=phi, v=vout, status=status, slot_F=sF, slot_res=sR, slot_pass=sP, slot_iters=sI,
-                slot_round=sRd, slot_v=sV, threads=nthreads)
+                slot_round=sRd, slot_slot=sS, slot_v=sV, threads=nthreads)

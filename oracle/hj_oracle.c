@@ -132,7 +132,7 @@ typedef struct {
     double step_max;     /* GD adapt: upper bound on a coordinate's step         */
     int n_guesses;       /* initial guesses per query                            */
     int max_trials;      /* total trials per query (guesses + reseeds)           */
-    int max_rounds;      /* reseed rounds after round 0                          */
+    int max_rounds;      /* >= 1: one reseed round spends the trial budget       */
     uint64_t seed;       /* Philox key                                           */
     int guess_dist;      /* 0: U[-2,2]^d, 1: Irwin-Hall(12) approximate N(0,1)   */
     double cert_tol;     /* certificate tolerance tau                            */
@@ -1113,58 +1113,61 @@ double orc_certify(const orc_problem *P, int quad, const double *x, double t, in
 /* One query: guesses, descent, certificate, reseeding of failed starts and  */
 /* best-of-guesses (Sec. 4.3 and Sec. 5).                                    */
 /*                                                                          */
-/* Round 0 runs n_guesses slots from Philox draws (q, g, 0).  In round r >= 1 */
-/* every slot whose certificate failed is restarted from draw (q, g, r), in  */
-/* slot order, while the query's trial budget max_trials lasts.  The answer  */
-/* is the certified slot with the smallest FP64 functional value (ties: the  */
-/* lowest slot); with no certified slot, the smallest over all slots.  Lax:  */
+/* Trial g < n_guesses is slot g from Philox draw (q, g, 0).  When           */
+/* max_rounds >= 1 and some of them fail the certificate, the rest of the    */
+/* query's budget of max_trials independent trials (Sec. 5) is spent at      */
+/* once: restart j in [0, max_trials - n_guesses) draws (q, S[j mod |S|],    */
+/* 1 + j / |S|), S the failed slots in slot order.  The answer is the        */
+/* certified trial with the smallest FP64 functional value (ties: the lowest */
+/* trial), with no certified trial the smallest over all trials.  Lax:       */
 /* phi = F^1; Hopf: phi = -G.                                                */
 /*                                                                          */
-/* Per-slot diagnostics (may be NULL), each [n_guesses]: final functional,   */
-/* residual, pass flag, iterations of the last attempt, round of the last    */
-/* attempt, and the final v of every slot ([n_guesses * d]).                 */
+/* Per-trial diagnostics (may be NULL), each [orc_trials(O)] (trials that   */
+/* did not run are left untouched): functional, residual, pass flag,         */
+/* iterations, round and slot of the draw, and the final v ([trials * d]).   */
 /* ------------------------------------------------------------------------ */
+int orc_trials(const orc_opts *O)
+{
+    const int G = O->n_guesses;
+    return G + ((O->max_rounds >= 1 && O->max_trials > G) ? O->max_trials - G : 0);
+}
+
 int orc_solve_query(const orc_problem *P, const orc_opts *O, int64_t q, const double *x, double t, int N,
                     double *phi, double *vstar, double *slot_F, double *slot_res, int *slot_pass, int *slot_iters,
-                    int *slot_round, double *slot_v)
+                    int *slot_round, double *slot_v, int *slot_slot)
 {
-    int d = P->d, G = O->n_guesses;
-    double *V = (double *)malloc(sizeof(double) * (size_t)G * d);
-    double *F = (double *)malloc(sizeof(double) * (size_t)G * 2), *R = F + G;
-    int *pass = (int *)malloc(sizeof(int) * (size_t)G * 4), *iters = pass + G, *round = iters + G, *cap = round + G;
-    int any_nonfinite = 0, reseeded = 0;
-    int trials = 0;
-    for (int g = 0; g < G; ++g) {
-        double *v = V + (size_t)g * d;
-        orc_guess(O->seed, q, g, 0, d, O->guess_dist, v);
-        int nf;
-        iters[g] = orc_descend(P, O, x, t, N, v, &cap[g], &nf);
-        any_nonfinite |= nf;
-        F[g] = orc_certify(P, O->quad, x, t, N, v, &R[g]);
-        pass[g] = (R[g] <= O->cert_tol) && isfinite(F[g]);
-        round[g] = 0;
-        trials++;
-    }
-    for (int r = 1; r <= O->max_rounds; ++r) {
-        int launched = 0;
-        for (int g = 0; g < G && trials < O->max_trials; ++g) {
-            if (pass[g]) continue;
-            double *v = V + (size_t)g * d;
-            orc_guess(O->seed, q, g, r, d, O->guess_dist, v);
-            int nf;
-            iters[g] = orc_descend(P, O, x, t, N, v, &cap[g], &nf);
-            any_nonfinite |= nf;
-            F[g] = orc_certify(P, O->quad, x, t, N, v, &R[g]);
-            pass[g] = (R[g] <= O->cert_tol) && isfinite(F[g]);
-            round[g] = r;
-            trials++;
-            launched++;
+    const int d = P->d, G = O->n_guesses, T = orc_trials(O);
+    double *V = (double *)malloc(sizeof(double) * (size_t)T * d);
+    double *F = (double *)malloc(sizeof(double) * (size_t)T * 2), *R = F + T;
+    int *pass = (int *)malloc(sizeof(int) * (size_t)T * 6), *iters = pass + T, *round = iters + T, *cap = round + T,
+        *slot = cap + T, *failed = slot + T;
+    int any_nonfinite = 0, reseeded = 0, nt = 0;
+    /* trial nt: slot s, round r */
+#define RUN_TRIAL(s, r)                                                                \
+    do {                                                                               \
+        double *v_ = V + (size_t)nt * d;                                               \
+        int nf_;                                                                       \
+        orc_guess(O->seed, q, (s), (r), d, O->guess_dist, v_);                        \
+        iters[nt] = orc_descend(P, O, x, t, N, v_, &cap[nt], &nf_);                   \
+        any_nonfinite |= nf_;                                                          \
+        F[nt] = orc_certify(P, O->quad, x, t, N, v_, &R[nt]);                         \
+        pass[nt] = (R[nt] <= O->cert_tol) && isfinite(F[nt]);                         \
+        round[nt] = (r);                                                               \
+        slot[nt] = (s);                                                                \
+        ++nt;                                                                          \
+    } while (0)
+    for (int g = 0; g < G; ++g) RUN_TRIAL(g, 0);
+    int nfail = 0;
+    for (int g = 0; g < G; ++g)
+        if (!pass[g]) failed[nfail++] = g;
+    if (nfail > 0)
+        for (int j = 0; G + j < T; ++j) {
+            RUN_TRIAL(failed[j % nfail], 1 + j / nfail);
             reseeded = 1;
         }
-        if (!launched) break;
-    }
+#undef RUN_TRIAL
     int best = -1, best_cert = 0;
-    for (int g = 0; g < G; ++g) {
+    for (int g = 0; g < nt; ++g) {
         if (!isfinite(F[g])) continue;
         if (pass[g] && !best_cert) { best = g; best_cert = 1; continue; }
         if (pass[g] != best_cert) continue;
@@ -1183,12 +1186,13 @@ int orc_solve_query(const orc_problem *P, const orc_opts *O, int64_t q, const do
     }
     if (any_nonfinite) status |= ST_NONFINITE;
     if (reseeded) status |= ST_RESEEDED;
-    for (int g = 0; g < G; ++g) {
+    for (int g = 0; g < nt; ++g) {
         if (slot_F) slot_F[g] = F[g];
         if (slot_res) slot_res[g] = R[g];
         if (slot_pass) slot_pass[g] = pass[g];
         if (slot_iters) slot_iters[g] = iters[g];
         if (slot_round) slot_round[g] = round[g];
+        if (slot_slot) slot_slot[g] = slot[g];
         if (slot_v) memcpy(slot_v + (size_t)g * d, V + (size_t)g * d, sizeof(double) * d);
     }
     free(V);

@@ -318,14 +318,14 @@ void bind_prob(void *block, int m, ProbDev<T> &P)
 }  // namespace
 
 struct hj_ctx {
-    int device = 0, nsm = 0, np = 0, ld = 0, prec = 0, gmax = 1;
+    int device = 0, nsm = 0, np = 0, ld = 0, prec = 0, gmax = 1, tmax = 1;  // most starts, most trials of a problem
     hj_solver_opts opts{};
     std::vector<hj_problem_desc> desc;
     std::vector<hj_solver_opts> popts;  // per-problem descent constants (context-wide fields overridden)
     std::vector<std::vector<double>> params;
     std::vector<DevProblem> dev;
     std::vector<int> tpp_override, ck_interval;
-    int32_t *d_pg = nullptr, *d_pd = nullptr, *d_pprin = nullptr, *d_ptrials = nullptr;
+    int32_t *d_pg = nullptr, *d_pd = nullptr, *d_pprin = nullptr, *d_pt = nullptr;
     // scratch
     long long cap_q = 0, cap_p = 0;
     int32_t *starts = nullptr, *pair_base = nullptr, *block_sums = nullptr, *trials = nullptr, *qflags = nullptr,
@@ -899,7 +899,11 @@ hj_status hj_create(const hj_problem_desc *problems, int n_problems, const hj_so
         pg[i] = D.n_guesses;
         pd[i] = D.d;
         pprin[i] = D.principle;
-        ptr[i] = ctx->popts[i].max_trials;
+        // pair entries of a query: its starts, then (when reseeding is on)
+        // the rest of its trial budget, run together in one reseed round
+        const int budget = ctx->popts[i].max_trials;
+        ptr[i] = D.n_guesses + ((opts->max_rounds >= 1 && budget > D.n_guesses) ? budget - D.n_guesses : 0);
+        ctx->tmax = std::max(ctx->tmax, ptr[i]);
         int tpp, c;
         if (!choose(ctx, i, K_EVAL, &tpp, &c) || !choose(ctx, i, K_CERT, &tpp, &c) ||
             !choose(ctx, i, desc_kind(ctx->popts[i].grad), &tpp, &c)) {
@@ -913,8 +917,8 @@ hj_status hj_create(const hj_problem_desc *problems, int n_problems, const hj_so
     CUC(cudaMemcpy(ctx->d_pg, pg.data(), sizeof(int32_t) * n_problems, cudaMemcpyHostToDevice));
     CUC(cudaMemcpy(ctx->d_pd, pd.data(), sizeof(int32_t) * n_problems, cudaMemcpyHostToDevice));
     CUC(cudaMemcpy(ctx->d_pprin, pprin.data(), sizeof(int32_t) * n_problems, cudaMemcpyHostToDevice));
-    CUC(cudaMalloc(&ctx->d_ptrials, sizeof(int32_t) * n_problems));
-    CUC(cudaMemcpy(ctx->d_ptrials, ptr.data(), sizeof(int32_t) * n_problems, cudaMemcpyHostToDevice));
+    CUC(cudaMalloc(&ctx->d_pt, sizeof(int32_t) * n_problems));
+    CUC(cudaMemcpy(ctx->d_pt, ptr.data(), sizeof(int32_t) * n_problems, cudaMemcpyHostToDevice));
     CUC(cudaMalloc(&ctx->pcount, sizeof(int32_t) * n_problems));
     CUC(cudaMalloc(&ctx->seg_begin, sizeof(int32_t) * (n_problems + 1)));
     CUC(cudaMalloc(&ctx->wl_count, sizeof(int32_t) * n_problems));
@@ -947,7 +951,7 @@ hj_status hj_destroy(hj_ctx *ctx)
     cudaFree(ctx->tc_vec);
     cudaFree(ctx->tc_ybuf);
     cudaFree(ctx->tc_err);
-    void *ptrs[] = {ctx->d_pg, ctx->d_pd, ctx->d_pprin, ctx->d_ptrials, ctx->starts, ctx->pair_base, ctx->block_sums, ctx->trials,
+    void *ptrs[] = {ctx->d_pg, ctx->d_pd, ctx->d_pprin, ctx->d_pt, ctx->starts, ctx->pair_base, ctx->block_sums, ctx->trials,
                     ctx->qflags, ctx->pair_q, ctx->pair_slot, ctx->pair_round, ctx->iters, ctx->wl, ctx->flags,
                     ctx->pP, ctx->pF, ctx->pR, ctx->vfin, ctx->pcount, ctx->seg_begin, ctx->wl_count, ctx->cursor,
                     ctx->stats, ctx->amb_wl, ctx->amb_count, ctx->best_pid};
@@ -1169,8 +1173,8 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
     if (!x || !t || !phi_out || !v_out || !status_out)
         return fail(ctx, HJ_EINVAL, "x, t, phi_out, v_out and status_out must be non-NULL");
     if (ctx->np > 1 && !problem_idx) return fail(ctx, HJ_EINVAL, "problem_idx is required with several problems");
-    if (n_queries > (((long long)1 << 31) - 1) / ctx->gmax) return fail(ctx, HJ_EINVAL, "too many (query, start) pairs");
-    const long long npairs = (long long)n_queries * ctx->gmax;
+    if (n_queries > (((long long)1 << 31) - 1) / ctx->tmax) return fail(ctx, HJ_EINVAL, "too many (query, trial) pairs");
+    const long long npairs = (long long)n_queries * ctx->tmax;
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device));
     hj_status st = ensure_scratch(ctx, n_queries, npairs);
@@ -1210,10 +1214,11 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
         else CU(cudaEventRecord(ctx->ev_begin, s));
         CU(cudaMemsetAsync(ctx->stats, 0, sizeof(unsigned long long) * 8 * ctx->np, s));
         ctx->launches = 6;  // count, offsets, three scan phases, pair build
-        CU(launch_count(n_queries, pidx, ctx->d_pg, ctx->starts, ctx->pcount, ctx->np, ctx->seg_begin, ctx->wl_count, s));
+        CU(launch_count(n_queries, pidx, ctx->d_pt, ctx->starts, ctx->pcount, ctx->np, ctx->seg_begin, ctx->wl_count, s));
         CU(launch_scan(n_queries, ctx->starts, ctx->pair_base, ctx->block_sums, s));
-        CU(launch_build_pairs(n_queries, pidx, ctx->np, ctx->d_pg, ctx->pair_base, ctx->pair_q, ctx->pair_slot, ctx->pair_round,
-                              ctx->trials, ctx->qflags, ctx->seg_begin, ctx->wl_count, ctx->wl, s));
+        CU(launch_build_pairs(n_queries, pidx, ctx->np, ctx->d_pg, ctx->d_pt, ctx->pair_base, ctx->pair_q, ctx->pair_slot,
+                              ctx->pair_round, ctx->trials, ctx->qflags, ctx->seg_begin, ctx->wl_count, ctx->wl,
+                              ctx->pF, ctx->pP, ctx->flags, s));
         // Several problems: each round's descent launches go to auxiliary streams
         // (tensor-core problems share the first, the lane-group ones take the
         // others in turn) so that their tails overlap and the tensor-core tile
@@ -1235,7 +1240,8 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                 CU(cudaEventCreate(&e));
                 ctx->pp_ev.push_back(e);
             }
-        for (int round = 0; round <= ctx->opts.max_rounds; ++round) {
+        const int nrounds = std::min(ctx->opts.max_rounds, 1);  // round 0, then one reseed round
+        for (int round = 0; round <= nrounds; ++round) {
             CU(cudaMemsetAsync(ctx->cursor, 0, sizeof(int32_t) * ctx->np, s));
             CU(cudaMemsetAsync(ctx->amb_count, 0, sizeof(int32_t) * ctx->np, s));
             if (ctx->timing) { st = record(ctx, ctx->ev_desc, ctx->n_desc_ev++, s); if (st != HJ_OK) return st; }
@@ -1336,7 +1342,7 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                 };
                 // FP64 certificate of the starts whose binary32 residual fell in
                 // the band around the tolerance (few): a small grid suffices
-                const long long cap = std::min<long long>((long long)n_queries * ctx->desc[p].n_guesses, 1 << 16);
+                const long long cap = std::min<long long>(npairs, 1 << 16);
                 if (ctx->prec) {
                     CertArgs<double> a{};
                     fill(a);
@@ -1351,13 +1357,14 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                 ctx->launches++;
             }
             if (ctx->timing) { st = record(ctx, ctx->ev_cert, ctx->n_cert_ev++, s); if (st != HJ_OK) return st; }
-            const int schedule = round < ctx->opts.max_rounds;
+            const int schedule = round < nrounds;
             if (schedule) CU(cudaMemsetAsync(ctx->wl_count, 0, sizeof(int32_t) * ctx->np, s));
             SelectArgs a{};
             a.nq = n_queries;
             a.pidx = pidx;
             a.np = ctx->np;
             a.pg = ctx->d_pg;
+            a.pt = ctx->d_pt;
             a.pd = ctx->d_pd;
             a.pprin = ctx->d_pprin;
             a.ld = ctx->ld;
@@ -1366,12 +1373,12 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
             a.pP = ctx->pP;
             a.flags = ctx->flags;
             a.vfin = ctx->vfin;
+            a.pair_slot = ctx->pair_slot;
             a.pair_round = ctx->pair_round;
             a.trials = ctx->trials;
             a.qflags = ctx->qflags;
             a.round = round;
             a.schedule = schedule;
-            a.ptrials = ctx->d_ptrials;
             a.seg_begin = ctx->seg_begin;
             a.wl_count = ctx->wl_count;
             a.wl = ctx->wl;
@@ -1693,16 +1700,16 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
         return fail(ctx, HJ_EUNSUPPORTED, "hj_solve_noalloc supports devices 0..%d", NOALLOC_MAX_DEVICES - 1);
     // bound the batch before any size arithmetic: (query, start) pairs are
     // indexed in int32, and n_queries * starts must not wrap
-    if (n_queries > (((long long)1 << 31) - 1) / ctx->gmax) return fail(ctx, HJ_EINVAL, "too many (query, start) pairs");
-    const long long npairs = (long long)n_queries * ctx->gmax;
+    if (n_queries > (((long long)1 << 31) - 1) / ctx->tmax) return fail(ctx, HJ_EINVAL, "too many (query, trial) pairs");
+    const long long npairs = (long long)n_queries * ctx->tmax;
     const size_t es = ctx->prec ? sizeof(double) : sizeof(float);
     NoallocLayout L{};
     const size_t need = noalloc_layout(nullptr, ctx->np, n_queries, npairs, ctx->ld, es, &L);
     if (need > (size_t)HJ_SOLVE_NOALLOC_SCRATCH_BYTES)
         return fail(ctx, HJ_EINVAL,
-                    "hj_solve_noalloc: %lld queries x %d starts need %zu bytes of scratch, the static array holds %zu "
+                    "hj_solve_noalloc: %lld queries x %d trials need %zu bytes of scratch, the static array holds %zu "
                     "(split the batch or use hj_solve)",
-                    (long long)n_queries, ctx->gmax, need, (size_t)HJ_SOLVE_NOALLOC_SCRATCH_BYTES);
+                    (long long)n_queries, ctx->tmax, need, (size_t)HJ_SOLVE_NOALLOC_SCRATCH_BYTES);
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device));
     if (!g_noalloc_ptr[ctx->device]) {
@@ -1721,11 +1728,12 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
             return fail(ctx, HJ_EUNSUPPORTED, "no kernel for problem %d", p);
     // Every array read below is written earlier in this call; only the
     // per-problem counters must start at zero, and they are cleared here.
-    CU(launch_count(n_queries, pidx, ctx->d_pg, L.starts, L.pcount, ctx->np, L.seg_begin, L.wl_count, s));
+    CU(launch_count(n_queries, pidx, ctx->d_pt, L.starts, L.pcount, ctx->np, L.seg_begin, L.wl_count, s));
     CU(launch_scan(n_queries, L.starts, L.pair_base, L.block_sums, s));
-    CU(launch_build_pairs(n_queries, pidx, ctx->np, ctx->d_pg, L.pair_base, L.pair_q, L.pair_slot, L.pair_round, L.trials,
-                          L.qflags, L.seg_begin, L.wl_count, L.wl, s));
-    for (int round = 0; round <= ctx->opts.max_rounds; ++round) {
+    CU(launch_build_pairs(n_queries, pidx, ctx->np, ctx->d_pg, ctx->d_pt, L.pair_base, L.pair_q, L.pair_slot,
+                          L.pair_round, L.trials, L.qflags, L.seg_begin, L.wl_count, L.wl, L.pF, L.pP, L.flags, s));
+    const int nrounds = std::min(ctx->opts.max_rounds, 1);  // round 0, then one reseed round
+    for (int round = 0; round <= nrounds; ++round) {
         CU(cudaMemsetAsync(L.cursor, 0, sizeof(int32_t) * ctx->np, s));
         CU(cudaMemsetAsync(L.amb_count, 0, sizeof(int32_t) * ctx->np, s));
         for (int p = 0; p < ctx->np; ++p) {
@@ -1797,7 +1805,7 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
                 a.problem = p;
                 a.pair_q = L.pair_q;
             };
-            const long long cap = std::min<long long>((long long)n_queries * ctx->desc[p].n_guesses, 1 << 16);
+            const long long cap = std::min<long long>(npairs, 1 << 16);
             if (ctx->prec) {
                 CertArgs<double> a{};
                 fill(a);
@@ -1810,13 +1818,14 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
                 CU(k.cert_pairs(&a, rows_grid(ctx, k.f_cert_pairs, cap, tpp_c[p]), s));
             }
         }
-        const int schedule = round < ctx->opts.max_rounds;
+        const int schedule = round < nrounds;
         if (schedule) CU(cudaMemsetAsync(L.wl_count, 0, sizeof(int32_t) * ctx->np, s));
         SelectArgs a{};
         a.nq = n_queries;
         a.pidx = pidx;
         a.np = ctx->np;
         a.pg = ctx->d_pg;
+        a.pt = ctx->d_pt;
         a.pd = ctx->d_pd;
         a.pprin = ctx->d_pprin;
         a.ld = ctx->ld;
@@ -1825,12 +1834,12 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
         a.pP = L.pP;
         a.flags = L.flags;
         a.vfin = L.vfin;
+        a.pair_slot = L.pair_slot;
         a.pair_round = L.pair_round;
         a.trials = L.trials;
         a.qflags = L.qflags;
         a.round = round;
         a.schedule = schedule;
-        a.ptrials = ctx->d_ptrials;
         a.seg_begin = L.seg_begin;
         a.wl_count = L.wl_count;
         a.wl = L.wl;

@@ -17,13 +17,14 @@ __device__ __forceinline__ int problem_of(const int32_t *pidx, long long q, int 
     return (p >= 0 && p < np) ? p : -1;
 }
 
-// Starts per query -> starts[q]; pairs per problem accumulated in pcount.
-__global__ void k_count(long long nq, const int32_t *pidx, int np, const int32_t *pg, int32_t *starts,
+// Pair entries per query (its trials: starts plus reseed budget) ->
+// starts[q]; entries per problem accumulated in pcount.
+__global__ void k_count(long long nq, const int32_t *pidx, int np, const int32_t *pt, int32_t *starts,
                         int32_t *pcount)
 {
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (long long)gridDim.x * blockDim.x) {
         const int p = problem_of(pidx, q, np);
-        const int G = (p >= 0) ? pg[p] : 0;
+        const int G = (p >= 0) ? pt[p] : 0;
         starts[q] = G;
         if (p >= 0) atomicAdd(pcount + p, G);
     }
@@ -82,10 +83,13 @@ __global__ void k_scan_add(long long n, int32_t *out, const int32_t *block_sums)
     if (i < n) out[i] += block_sums[blockIdx.x];
 }
 
-// Round 0: every (query, slot) pair, appended to its problem's work list.
-__global__ void k_build_pairs(long long nq, const int32_t *pidx, int np, const int32_t *pg, const int32_t *pair_base,
-                              int32_t *pair_q, int32_t *pair_slot, int32_t *pair_round, int32_t *trials,
-                              int32_t *qflags, const int32_t *seg_begin, int32_t *wl_count, int32_t *wl)
+// Pair entries of every query: its pt[p] trials, of which the first pg[p]
+// (slot s, round 0) go to its problem's work list for round 0; the rest are
+// the reseed budget, assigned by k_select (their value NaN until they run).
+__global__ void k_build_pairs(long long nq, const int32_t *pidx, int np, const int32_t *pg, const int32_t *pt,
+                              const int32_t *pair_base, int32_t *pair_q, int32_t *pair_slot, int32_t *pair_round,
+                              int32_t *trials, int32_t *qflags, const int32_t *seg_begin, int32_t *wl_count,
+                              int32_t *wl, double *pF, uint8_t *pP, uint8_t *flags)
 {
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (long long)gridDim.x * blockDim.x) {
         const int p = problem_of(pidx, q, np);
@@ -94,29 +98,42 @@ __global__ void k_build_pairs(long long nq, const int32_t *pidx, int np, const i
             qflags[q] = HJ_ST_NONFINITE;
             continue;
         }
-        int G = pg[p];
-        int base = pair_base[q];
-        int pos = atomicAdd(wl_count + p, G);
-        for (int s = 0; s < G; ++s) {
-            pair_q[base + s] = (int32_t)q;
-            pair_slot[base + s] = s;
-            pair_round[base + s] = 0;
-            wl[seg_begin[p] + pos + s] = base + s;
+        const int G = pg[p], T = pt[p];
+        const int base = pair_base[q];
+        const int pos = atomicAdd(wl_count + p, G);
+        for (int s = 0; s < T; ++s) {
+            const int pid = base + s;
+            pair_q[pid] = (int32_t)q;
+            if (s < G) {
+                pair_slot[pid] = s;
+                pair_round[pid] = 0;
+                wl[seg_begin[p] + pos + s] = pid;
+            } else {
+                pair_slot[pid] = -1;
+                pair_round[pid] = -1;
+                pF[pid] = nan("");
+                pP[pid] = 0;
+                flags[pid] = 0;
+            }
         }
         trials[q] = G;
         qflags[q] = 0;
     }
 }
 
-// Best of the starts of each query, then the reseed decisions for the next
-// round: failed slots, in slot order, while fewer than the problem's trial
-// budget (ptrials) of starts of the query have run.  phi = F (Lax) or -G (Hopf) at the chosen start (the
-// FP64 value replaces it after the last round); best_pid records the start.
+// Best of the trials run so far of each query, and after round 0 the
+// reseed schedule (Sec. 4.3, Sec. 5): when some of the pg[p] starts failed
+// the certificate, the query's whole remaining budget (pt[p] - pg[p]
+// trials) runs in the next round, restart j drawing (q, S[j mod |S|],
+// 1 + j / |S|) with S the failed slots in slot order.  Best: certified
+// first, then the smallest value, ties to the lowest trial.  phi = F (Lax)
+// or -G (Hopf) at the chosen trial (the FP64 value replaces it after the
+// last round); best_pid records the trial.
 template <typename T>
-__global__ void k_select(long long nq, const int32_t *pidx, int np, const int32_t *pg, const int32_t *pd,
-                         const int32_t *pprin, int ld, const int32_t *pair_base, const double *pF,
-                         const uint8_t *pP, const uint8_t *flags, const T *vfin, int32_t *pair_round,
-                         int32_t *trials, int32_t *qflags, int round, int schedule, const int32_t *ptrials,
+__global__ void k_select(long long nq, const int32_t *pidx, int np, const int32_t *pg, const int32_t *pt,
+                         const int32_t *pd, const int32_t *pprin, int ld, const int32_t *pair_base, const double *pF,
+                         const uint8_t *pP, const uint8_t *flags, const T *vfin, int32_t *pair_slot,
+                         int32_t *pair_round, int32_t *trials, int32_t *qflags, int round, int schedule,
                          const int32_t *seg_begin, int32_t *wl_count, int32_t *wl, double *phi, T *v_out,
                          int32_t *status, int32_t *best_pid)
 {
@@ -128,10 +145,10 @@ __global__ void k_select(long long nq, const int32_t *pidx, int np, const int32_
             status[q] = HJ_ST_NONFINITE;
             continue;
         }
-        const int G = pg[p], d = pd[p];
+        const int G = pg[p], nt = pt[p], d = pd[p];
         const int base = pair_base[q];
         int best = -1, best_cert = 0, qf = qflags[q];
-        for (int s = 0; s < G; ++s) {
+        for (int s = 0; s < nt; ++s) {
             const int pid = base + s;
             if (flags[pid] & 2) qf |= HJ_ST_NONFINITE;
             const double F = pF[pid];
@@ -157,18 +174,25 @@ __global__ void k_select(long long nq, const int32_t *pidx, int np, const int32_
             st |= HJ_ST_NONFINITE;
         }
         if (schedule) {
-            int tr = trials[q];
-            const int max_trials = ptrials[p];
-            for (int s = 0; s < G && tr < max_trials; ++s) {
-                const int pid = base + s;
-                if (pP[pid]) continue;
-                pair_round[pid] = round + 1;
-                int pos = atomicAdd(wl_count + p, 1);
-                wl[seg_begin[p] + pos] = pid;
-                ++tr;
+            int nfail = 0;
+            for (int s = 0; s < G; ++s) nfail += pP[base + s] ? 0 : 1;
+            if (nfail > 0 && nt > G) {
+                for (int j = 0; G + j < nt; ++j) {
+                    int k = j % nfail, slot = 0;
+                    for (int s = 0; s < G; ++s)
+                        if (!pP[base + s] && k-- == 0) {
+                            slot = s;
+                            break;
+                        }
+                    const int pid = base + G + j;
+                    pair_slot[pid] = slot;
+                    pair_round[pid] = round + 1 + j / nfail;
+                    const int pos = atomicAdd(wl_count + p, 1);
+                    wl[seg_begin[p] + pos] = pid;
+                }
+                trials[q] = nt;
                 qf |= HJ_ST_RESEEDED;
             }
-            trials[q] = tr;
         }
         qflags[q] = qf;
         status[q] = st | qf;
@@ -202,12 +226,12 @@ static int grid_for(long long n, int block)
     return (int)g;
 }
 
-cudaError_t launch_count(long long nq, const int32_t *pidx, const int32_t *pg, int32_t *starts, int32_t *pcount,
+cudaError_t launch_count(long long nq, const int32_t *pidx, const int32_t *pt, int32_t *starts, int32_t *pcount,
                          int np, int32_t *seg_begin, int32_t *wl_count, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(pcount, 0, sizeof(int32_t) * np, s);
     if (e != cudaSuccess) return e;
-    k_count<<<grid_for(nq, 256), 256, 0, s>>>(nq, pidx, np, pg, starts, pcount);
+    k_count<<<grid_for(nq, 256), 256, 0, s>>>(nq, pidx, np, pt, starts, pcount);
     k_problem_offsets<<<1, 1, 0, s>>>(np, pcount, seg_begin, wl_count);
     return cudaGetLastError();
 }
@@ -222,13 +246,13 @@ cudaError_t launch_scan(long long n, const int32_t *in, int32_t *out, int32_t *b
     return cudaGetLastError();
 }
 
-cudaError_t launch_build_pairs(long long nq, const int32_t *pidx, int np, const int32_t *pg,
+cudaError_t launch_build_pairs(long long nq, const int32_t *pidx, int np, const int32_t *pg, const int32_t *pt,
                                const int32_t *pair_base, int32_t *pair_q, int32_t *pair_slot, int32_t *pair_round,
                                int32_t *trials, int32_t *qflags, const int32_t *seg_begin, int32_t *wl_count,
-                               int32_t *wl, cudaStream_t s)
+                               int32_t *wl, double *pF, uint8_t *pP, uint8_t *flags, cudaStream_t s)
 {
-    k_build_pairs<<<grid_for(nq, 256), 256, 0, s>>>(nq, pidx, np, pg, pair_base, pair_q, pair_slot, pair_round,
-                                                    trials, qflags, seg_begin, wl_count, wl);
+    k_build_pairs<<<grid_for(nq, 256), 256, 0, s>>>(nq, pidx, np, pg, pt, pair_base, pair_q, pair_slot, pair_round,
+                                                    trials, qflags, seg_begin, wl_count, wl, pF, pP, flags);
     return cudaGetLastError();
 }
 
@@ -236,9 +260,9 @@ template <typename T>
 cudaError_t launch_select_t(const SelectArgs &a, cudaStream_t s)
 {
     k_select<T><<<grid_for(a.nq, 128), 128, 0, s>>>(
-        a.nq, a.pidx, a.np, a.pg, a.pd, a.pprin, a.ld, a.pair_base, a.pF, a.pP, a.flags, (const T *)a.vfin, a.pair_round,
-        a.trials, a.qflags, a.round, a.schedule, a.ptrials, a.seg_begin, a.wl_count, a.wl, a.phi, (T *)a.v_out,
-        a.status, a.best_pid);
+        a.nq, a.pidx, a.np, a.pg, a.pt, a.pd, a.pprin, a.ld, a.pair_base, a.pF, a.pP, a.flags, (const T *)a.vfin,
+        a.pair_slot, a.pair_round, a.trials, a.qflags, a.round, a.schedule, a.seg_begin, a.wl_count, a.wl, a.phi,
+        (T *)a.v_out, a.status, a.best_pid);
     return cudaGetLastError();
 }
 

@@ -10,15 +10,14 @@ struct SelectArgs {
     long long nq;
     const int32_t *pidx;
     int np;  // problems (a problem index outside [0, np) marks the query invalid)
-    const int32_t *pg, *pd, *pprin;
+    const int32_t *pg, *pt, *pd, *pprin;  // per problem: starts, trials (starts + reseed budget), d, principle
     int ld;
     const int32_t *pair_base;
     const double *pF;
     const uint8_t *pP, *flags;
     const void *vfin;
-    int32_t *pair_round, *trials, *qflags;
+    int32_t *pair_slot, *pair_round, *trials, *qflags;
     int round, schedule;
-    const int32_t *ptrials;  // per-problem trial budget
     const int32_t *seg_begin;
     int32_t *wl_count, *wl;
     double *phi;
@@ -27,13 +26,13 @@ struct SelectArgs {
     int32_t *best_pid;
 };
 
-cudaError_t launch_count(long long nq, const int32_t *pidx, const int32_t *pg, int32_t *starts, int32_t *pcount,
+cudaError_t launch_count(long long nq, const int32_t *pidx, const int32_t *pt, int32_t *starts, int32_t *pcount,
                          int np, int32_t *seg_begin, int32_t *wl_count, cudaStream_t s);
 cudaError_t launch_scan(long long n, const int32_t *in, int32_t *out, int32_t *block_sums, cudaStream_t s);
-cudaError_t launch_build_pairs(long long nq, const int32_t *pidx, int np, const int32_t *pg, const int32_t *pair_base,
-                               int32_t *pair_q, int32_t *pair_slot, int32_t *pair_round, int32_t *trials,
-                               int32_t *qflags, const int32_t *seg_begin, int32_t *wl_count, int32_t *wl,
-                               cudaStream_t s);
+cudaError_t launch_build_pairs(long long nq, const int32_t *pidx, int np, const int32_t *pg, const int32_t *pt,
+                               const int32_t *pair_base, int32_t *pair_q, int32_t *pair_slot, int32_t *pair_round,
+                               int32_t *trials, int32_t *qflags, const int32_t *seg_begin, int32_t *wl_count,
+                               int32_t *wl, double *pF, uint8_t *pP, uint8_t *flags, cudaStream_t s);
 cudaError_t launch_select(const SelectArgs &a, int prec, cudaStream_t s);
 cudaError_t launch_guess(long long n, const long long *qid, const int32_t *slot, const int32_t *round,
                          const int32_t *pidx, int np, const int32_t *pd, int ld, unsigned long long seed, int dist, int prec,

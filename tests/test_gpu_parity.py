@@ -409,6 +409,28 @@ def test_solve_smooth_nonconvex_d20_matches_oracle(hj):
     assert np.array_equal(st & 1, ref["status"] & 1)
 
 
+@pytest.mark.parametrize("max_trials", [20, 40])
+def test_reseed_budget_runs_in_one_round_from_the_failed_slots(hj, max_trials):
+    # cert_tol = 0 fails every start, so every query spends its whole budget:
+    # 8 starts, then max_trials - 8 restarts drawn (slot j mod 8, round
+    # 1 + j / 8) in one more round (draw rounds 1-2 for 20 trials, 1-4 for
+    # 40).  Five descent iterations leave each trial near its start, so the
+    # best of the trials, and with it phi, depends on every restart's draw
+    # (phi changes on 16 and 20 of the 24 queries against no reseeding).
+    # The smooth convex d=10 family keeps these unconverged trajectories
+    # well conditioned (the oracle's phi moves by 2e-7 under a 1e-7 change
+    # of x; the non-convex family's smoothed |p_i| moves it by 5e-3).
+    wl = W.c2_speed_quad(nq_x=16)
+    wl.solver.update(cert_tol=0.0, max_iters=5, max_trials=max_trials, max_rounds=3)
+    phi, v, st, ref, info = _solve_both(hj, wl, 24)
+    err = rel_err(phi, ref["phi"])
+    assert np.all(err <= 1e-4), err.max()
+    assert np.all(st == hj.HJ_ST_RESEEDED | hj.HJ_ST_MAX_ITERS)
+    assert np.array_equal(st, ref["status"])
+    assert info["n_pairs"] == 24 * max_trials
+    assert info["descent_launches"] == 2
+
+
 @pytest.mark.parametrize("ck", [1, 2, 3, 8, 16])
 @pytest.mark.parametrize("quad", ["rk4", "rect", "euler", "euler_rect"])
 def test_gradient_checkpoint_intervals_and_quadrature(hj, ck, quad):

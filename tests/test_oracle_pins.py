@@ -1023,14 +1023,48 @@ def test_failed_certificates_spend_exactly_the_trial_budget():
     P = oracle_problem(wl.problems[0])
     opts = oracle_opts(dict(wl.solver, cert_tol=0.0, max_iters=5, max_trials=20, max_rounds=3), 16)
     res = O.solve(P, opts, wl.x, wl.t, wl.n_steps)
-    # 16 slots in round 0, then slots 0..3 reseeded once in round 1; none passes
+    # the 16 slots (round 0) all fail; the remaining budget of 4 trials runs
+    # at once, restarting the failed slots 0..3 from round-1 draws
     for q in range(2):
-        assert list(res["slot_round"][q]) == [1] * 4 + [0] * 12
+        assert list(res["slot_round"][q]) == [0] * 16 + [1] * 4
+        assert list(res["slot_slot"][q]) == list(range(16)) + [0, 1, 2, 3]
         assert not np.any(res["slot_pass"][q])
         assert res["status"][q] & O.ST_RESEEDED and not res["status"][q] & O.ST_CERTIFIED
+    # a budget beyond one restart per failed slot cycles through them again
+    # with the next round's draws: 24 restarts = slots 0..15 (round 1), 0..7 (round 2)
     opts2 = oracle_opts(dict(wl.solver, cert_tol=0.0, max_iters=5, max_trials=40, max_rounds=3), 16)
     res2 = O.solve(P, opts2, wl.x, wl.t, wl.n_steps)
-    assert list(res2["slot_round"][0]) == [2] * 8 + [1] * 8
+    assert list(res2["slot_round"][0]) == [0] * 16 + [1] * 16 + [2] * 8
+    assert list(res2["slot_slot"][0]) == list(range(16)) * 2 + list(range(8))
+    # no reseeding without a reseed round, or with every start certified
+    res3 = O.solve(P, oracle_opts(dict(wl.solver, cert_tol=0.0, max_iters=5, max_rounds=0), 16), wl.x, wl.t,
+                   wl.n_steps)
+    assert res3["slot_F"].shape[1] == 16 and not res3["status"][0] & O.ST_RESEEDED
+    res4 = O.solve(P, oracle_opts(dict(wl.solver, cert_tol=1e9, max_iters=5), 16), wl.x, wl.t, wl.n_steps)
+    assert np.all(res4["slot_round"][:, 16:] == -1) and not np.any(res4["status"] & O.ST_RESEEDED)
+
+
+def test_restarts_follow_the_failed_slots_and_draw_fresh_starts():
+    # only the failed slots restart, in slot order, each restart from the
+    # Philox draw (query, slot, round) of its round
+    wl = W.c3_smooth_nonconvex(nq=24)
+    P = oracle_problem(wl.problems[0])
+    res = O.solve(P, oracle_opts(wl.solver, 16), wl.x, wl.t, wl.n_steps)
+    seen = 0
+    for q in range(wl.nq):
+        failed = [g for g in range(16) if not res["slot_pass"][q, g]]
+        ran = res["slot_round"][q] >= 0
+        if not failed:
+            assert ran.sum() == 16
+            continue
+        seen += 1
+        assert ran.sum() == 20
+        assert list(res["slot_slot"][q, 16:]) == [failed[j % len(failed)] for j in range(4)]
+        assert list(res["slot_round"][q, 16:]) == [1 + j // len(failed) for j in range(4)]
+        best = np.nanargmin(np.where(res["slot_pass"][q] == 1, res["slot_F"][q], np.inf)) \
+            if np.any(res["slot_pass"][q]) else np.nanargmin(res["slot_F"][q])
+        assert res["phi"][q] == -res["slot_F"][q, best]
+    assert seen > 0
 
 
 def test_best_of_guesses_picks_global_minimum_of_double_well():
