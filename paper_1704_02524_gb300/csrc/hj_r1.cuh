@@ -130,6 +130,13 @@ struct Acc {
     }
 };
 
+// One lane per pair: components 2j and 2j + 1 side by side, so that the
+// even and the odd partial sums advance together in packed FP32x2
+// operations (each component rounded exactly as the scalar fmaf, __fmul_rn
+// and __fadd_rn it replaces).
+__device__ __forceinline__ float2 pair2(const float *a, int j) { return make_float2(a[2 * j], a[2 * j + 1]); }
+__device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
+
 // Scalars of one RK4 stage.
 struct St {
     float u, B;       // stage input: u = <w, gamma>, p = v + B w
@@ -157,20 +164,39 @@ template <int C, int TPP, bool KEEP>
 __device__ __forceinline__ void stage(const ProbDev<float> &P, const Lane<C, TPP> &L, const float *v, float eps,
                                       float u, float B, St &s, float *r)
 {
-    Acc<TPP> ph, dd;
+    if constexpr (TPP == 1) {
+        float2 ph = splat2(0.f), dd = ph;
+        const float2 B2 = splat2(B), eps2 = splat2(eps);
 #pragma unroll
-    for (int k = 0; k < Lane<C, TPP>::CL; ++k) {
-        const float p = fmaf(B, L.w(P, k), v[k]);
-        const float q = fmaf(p, p, eps);
-        const float ri = rsqrtf(q);
-        if constexpr (KEEP) r[k] = ri;
-        ph.fma_(k, L.e(P, k), q * ri);
-        dd.fma_(k, L.we(P, k), ri * p);
+        for (int j = 0; j < C / 2; ++j) {
+            const float2 p = __ffma2_rn(B2, pair2(P.rw, j), pair2(v, j));
+            const float2 q = __ffma2_rn(p, p, eps2);
+            const float2 ri = make_float2(rsqrtf(q.x), rsqrtf(q.y));
+            if constexpr (KEEP) {
+                r[2 * j] = ri.x;
+                r[2 * j + 1] = ri.y;
+            }
+            ph = __ffma2_rn(pair2(P.re, j), __fmul2_rn(q, ri), ph);
+            dd = __ffma2_rn(pair2(P.rew, j), __fmul2_rn(ri, p), dd);
+        }
+        s.phi = L.total(ph.x, ph.y);
+        s.D = L.total(dd.x, dd.y);
+    } else {
+        Acc<TPP> ph, dd;
+#pragma unroll
+        for (int k = 0; k < Lane<C, TPP>::CL; ++k) {
+            const float p = fmaf(B, L.w(P, k), v[k]);
+            const float q = fmaf(p, p, eps);
+            const float ri = rsqrtf(q);
+            if constexpr (KEEP) r[k] = ri;
+            ph.fma_(k, L.e(P, k), __fmul_rn(q, ri));
+            dd.fma_(k, L.we(P, k), __fmul_rn(ri, p));
+        }
+        s.phi = L.total(ph.a0, ph.a1);
+        s.D = L.total(dd.a0, dd.a1);
     }
     s.u = u;
     s.B = B;
-    s.phi = L.total(ph.a0, ph.a1);
-    s.D = L.total(dd.a0, dd.a1);
     float su, cu;
     __sincosf(u, &su, &cu);
     s.c = fmaf(0.5f, su, 1.f);
@@ -222,10 +248,17 @@ __device__ __forceinline__ void step(const ProbDev<float> &P, const Lane<C, TPP>
 template <int C, int TPP>
 __device__ __forceinline__ float dot_w(const ProbDev<float> &P, const Lane<C, TPP> &L, const float *x)
 {
-    Acc<TPP> a;
+    if constexpr (TPP == 1) {
+        float2 a = splat2(0.f);
 #pragma unroll
-    for (int k = 0; k < Lane<C, TPP>::CL; ++k) a.fma_(k, L.w(P, k), x[k]);
-    return L.total(a.a0, a.a1);
+        for (int j = 0; j < C / 2; ++j) a = __ffma2_rn(pair2(P.rw, j), pair2(x, j), a);
+        return L.total(a.x, a.y);
+    } else {
+        Acc<TPP> a;
+#pragma unroll
+        for (int k = 0; k < Lane<C, TPP>::CL; ++k) a.fma_(k, L.w(P, k), x[k]);
+        return L.total(a.a0, a.a1);
+    }
 }
 template <int C, int TPP>
 __device__ __forceinline__ float dot(const Lane<C, TPP> &L, const float *x, const float *y)
@@ -345,19 +378,38 @@ __device__ __forceinline__ void vjp(const ProbDev<float> &P, const Lane<C, TPP> 
     const float kd = fmaf(s.c1, Bw, __fmul_rn(bb, fmaf(-s.c1, s.u, s.c)));
     const float cea = __fmul_rn(__fmul_rn(s.c, eps), a);
     const float Bs = fmaf(0.f, after, s.B);
-    Acc<TPP> w;
-#pragma unroll
-    for (int k = 0; k < Lane<C, TPP>::CL; ++k) {
-        const float wk = L.w(P, k);
-        const float p = fmaf(Bs, wk, v[k]);
-        const float ri = rsqrtf(fmaf(p, p, eps));
-        const float tt = fmaf(-cea * wk, ri * ri, __fmul_rn(kd, p));
-        const float rp = __fmul_rn(__fmul_rn(L.e(P, k), ri), tt);
-        lp[k] = __fadd_rn(lp[k], rp);
-        w.fma_(k, wk, rp);
-    }
     R = dEdu;
-    Wr = L.total(w.a0, w.a1);
+    if constexpr (TPP == 1) {
+        float2 w = splat2(0.f);
+        const float2 Bs2 = splat2(Bs), eps2 = splat2(eps), kd2 = splat2(kd), mcea2 = splat2(-cea);
+#pragma unroll
+        for (int j = 0; j < C / 2; ++j) {
+            const float2 wk = pair2(P.rw, j);
+            const float2 p = __ffma2_rn(Bs2, wk, pair2(v, j));
+            const float2 q = __ffma2_rn(p, p, eps2);
+            const float2 ri = make_float2(rsqrtf(q.x), rsqrtf(q.y));
+            const float2 tt = __ffma2_rn(__fmul2_rn(mcea2, wk), __fmul2_rn(ri, ri), __fmul2_rn(kd2, p));
+            const float2 rp = __fmul2_rn(__fmul2_rn(pair2(P.re, j), ri), tt);
+            const float2 l = __fadd2_rn(pair2(lp, j), rp);
+            lp[2 * j] = l.x;
+            lp[2 * j + 1] = l.y;
+            w = __ffma2_rn(wk, rp, w);
+        }
+        Wr = L.total(w.x, w.y);
+    } else {
+        Acc<TPP> w;
+#pragma unroll
+        for (int k = 0; k < Lane<C, TPP>::CL; ++k) {
+            const float wk = L.w(P, k);
+            const float p = fmaf(Bs, wk, v[k]);
+            const float ri = rsqrtf(fmaf(p, p, eps));
+            const float tt = fmaf(__fmul_rn(-cea, wk), __fmul_rn(ri, ri), __fmul_rn(kd, p));
+            const float rp = __fmul_rn(__fmul_rn(L.e(P, k), ri), tt);
+            lp[k] = __fadd_rn(lp[k], rp);
+            w.fma_(k, wk, rp);
+        }
+        Wr = L.total(w.a0, w.a1);
+    }
 }
 
 // Adjoint of one RK4 step at input (u, B): lam = (alpha w, lp) -> lam_n.
