@@ -336,6 +336,7 @@ struct hj_ctx {
     double *pF = nullptr, *pR = nullptr;
     void *vfin = nullptr;
     int32_t *pcount = nullptr, *seg_begin = nullptr, *wl_count = nullptr, *cursor = nullptr, *amb_count = nullptr;
+    int32_t *wl_lpt = nullptr, *lpt_bins = nullptr;  // fine-level work lists in longest-first order
     unsigned long long *stats = nullptr;
     // tensor-core tile kernel scratch (per CTA slot) and its error word
     float *tc_vec = nullptr, *tc_ybuf = nullptr;
@@ -596,8 +597,11 @@ int persistent_grid(hj_ctx *ctx, const void *fn)
 // from twice the launch's resident threads up, two lanes per pair below,
 // where a round is too small to fill the GPU and a pair's latency sets its
 // time.  *launched gets the number of kernels launched.
+// One round's fp32 descent launches of a problem (two levels: coarse, then
+// fine).  With lpt_out non-null the fine level takes the round's pairs in
+// longest-first order (written there; lpt_bins is the problem's bin scratch).
 cudaError_t launch_desc_f32(hj_ctx *ctx, const KSet &k, int kind, bool r1, bool two, DescArgs<float> &a,
-                            int32_t *cursor, cudaStream_t sp, int *launched)
+                            int32_t *cursor, cudaStream_t sp, int *launched, int32_t *lpt_out, int32_t *lpt_bins)
 {
     const Launch L = kind == K_GD ? k.gd : kind == K_CG ? k.cg : k.cd;
     const void *fn = kind == K_GD ? k.f_gd : kind == K_CG ? k.f_cg : k.f_cd;
@@ -611,6 +615,13 @@ cudaError_t launch_desc_f32(hj_ctx *ctx, const KSet &k, int kind, bool r1, bool 
         a.phase = ph;
         cudaError_t e;
         if (ph == 2 && (e = cudaMemsetAsync(cursor, 0, sizeof(int32_t), sp)) != cudaSuccess) return e;
+        if (ph == 2 && lpt_out) {
+            if ((e = launch_lpt_order(a.wl, a.seg_begin, a.wl_count, a.problem, a.iters, a.S.max_iters, lpt_bins,
+                                      lpt_out, 4 * ctx->nsm, sp)) != cudaSuccess)
+                return e;
+            a.wl = lpt_out;
+            *launched += 3;
+        }
         a.run_lo = split;
         a.run_hi = LLONG_MAX;
         if ((e = L(&a, (int)big, sp)) != cudaSuccess) return e;
@@ -708,8 +719,8 @@ hj_status ensure_scratch(hj_ctx *ctx, long long nq, long long npairs)
     if (npairs > ctx->cap_p) {
         cudaFree(ctx->pair_q); cudaFree(ctx->pair_slot); cudaFree(ctx->pair_round); cudaFree(ctx->iters);
         cudaFree(ctx->wl); cudaFree(ctx->flags); cudaFree(ctx->pP); cudaFree(ctx->pF); cudaFree(ctx->pR);
-        cudaFree(ctx->vfin); cudaFree(ctx->amb_wl);
-        ctx->pair_q = ctx->pair_slot = ctx->pair_round = ctx->iters = ctx->wl = ctx->amb_wl = nullptr;
+        cudaFree(ctx->vfin); cudaFree(ctx->amb_wl); cudaFree(ctx->wl_lpt);
+        ctx->pair_q = ctx->pair_slot = ctx->pair_round = ctx->iters = ctx->wl = ctx->amb_wl = ctx->wl_lpt = nullptr;
         ctx->flags = ctx->pP = nullptr;
         ctx->pF = ctx->pR = nullptr;
         ctx->vfin = nullptr;
@@ -721,6 +732,7 @@ hj_status ensure_scratch(hj_ctx *ctx, long long nq, long long npairs)
         CU(cudaMalloc(&ctx->iters, sizeof(int32_t) * npairs));
         CU(cudaMalloc(&ctx->wl, sizeof(int32_t) * npairs));
         CU(cudaMalloc(&ctx->amb_wl, sizeof(int32_t) * npairs));
+        CU(cudaMalloc(&ctx->wl_lpt, sizeof(int32_t) * npairs));
         CU(cudaMalloc(&ctx->flags, npairs));
         CU(cudaMalloc(&ctx->pP, npairs));
         CU(cudaMalloc(&ctx->pF, sizeof(double) * npairs));
@@ -924,6 +936,7 @@ hj_status hj_create(const hj_problem_desc *problems, int n_problems, const hj_so
     CUC(cudaMalloc(&ctx->wl_count, sizeof(int32_t) * n_problems));
     CUC(cudaMalloc(&ctx->cursor, sizeof(int32_t) * n_problems));
     CUC(cudaMalloc(&ctx->amb_count, sizeof(int32_t) * n_problems));
+    CUC(cudaMalloc(&ctx->lpt_bins, sizeof(int32_t) * LPT_BINS_HOST * n_problems));
     CUC(cudaMalloc(&ctx->stats, sizeof(unsigned long long) * 8 * n_problems));
     CUC(cudaMemset(ctx->stats, 0, sizeof(unsigned long long) * 8 * n_problems));
     CUC(cudaMalloc(&ctx->tc_err, sizeof(int)));
@@ -954,7 +967,7 @@ hj_status hj_destroy(hj_ctx *ctx)
     void *ptrs[] = {ctx->d_pg, ctx->d_pd, ctx->d_pprin, ctx->d_pt, ctx->starts, ctx->pair_base, ctx->block_sums, ctx->trials,
                     ctx->qflags, ctx->pair_q, ctx->pair_slot, ctx->pair_round, ctx->iters, ctx->wl, ctx->flags,
                     ctx->pP, ctx->pF, ctx->pR, ctx->vfin, ctx->pcount, ctx->seg_begin, ctx->wl_count, ctx->cursor,
-                    ctx->stats, ctx->amb_wl, ctx->amb_count, ctx->best_pid};
+                    ctx->stats, ctx->amb_wl, ctx->amb_count, ctx->best_pid, ctx->wl_lpt, ctx->lpt_bins};
     for (void *p : ptrs) cudaFree(p);
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     for (auto a : ctx->aux) cudaStreamDestroy(a);
@@ -1241,6 +1254,37 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                 ctx->pp_ev.push_back(e);
             }
         const int nrounds = std::min(ctx->opts.max_rounds, 1);  // round 0, then one reseed round
+        // phi in FP64 at each query's chosen start
+        auto phi_pass = [&](cudaStream_t ps) -> hj_status {
+            for (int p = 0; p < ctx->np; ++p) {
+                const KSet &k = kset(ctx, p, c_c[p]);
+                auto fill = [&](auto &a) {
+                    a.P = ctx->dev[p].pd;
+                    a.tpp = tpp_c[p];
+                    a.n = n_queries;
+                    a.nsteps = n_steps;
+                    a.n_default = ctx->opts.n_steps_default;
+                    a.quad = ctx->opts.quad;
+                    a.pidx = pidx;
+                    a.pfilter = p;
+                    a.best_pid = ctx->best_pid;
+                    a.phi = phi_out;
+                };
+                if (ctx->prec) {
+                    CertArgs<double> a{};
+                    fill(a);
+                    a.x = (const double *)x; a.t = (const double *)t; a.v = (const double *)ctx->vfin;
+                    CU(k.cert_final(&a, rows_grid(ctx, k.f_cert_final, n_queries, tpp_c[p]), ps));
+                } else {
+                    CertArgs<float> a{};
+                    fill(a);
+                    a.x = (const float *)x; a.t = (const float *)t; a.v = (const float *)ctx->vfin;
+                    CU(k.cert_final(&a, rows_grid(ctx, k.f_cert_final, n_queries, tpp_c[p]), ps));
+                }
+                ctx->launches++;
+            }
+            return HJ_OK;
+        };
         for (int round = 0; round <= nrounds; ++round) {
             CU(cudaMemsetAsync(ctx->cursor, 0, sizeof(int32_t) * ctx->np, s));
             CU(cudaMemsetAsync(ctx->amb_count, 0, sizeof(int32_t) * ctx->np, s));
@@ -1310,7 +1354,7 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                     // coarse-to-fine as two launches, so that every warp runs one step count
                     int nl = 0;
                     CU(launch_desc_f32(ctx, k, kind, c_d[p] < 0, kind != K_CD && ctx->popts[p].coarse_div > 1, a,
-                                       ctx->cursor + p, sp, &nl));
+                                       ctx->cursor + p, sp, &nl, ctx->wl_lpt, ctx->lpt_bins + LPT_BINS_HOST * p));
                     ctx->launches += nl - 1;
                 }
                 if (ctx->pp_timing && round == 0) CU(cudaEventRecord(ctx->pp_ev[2 * p + 1], s));
@@ -1389,34 +1433,8 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
             CU(launch_select(a, ctx->prec, s));
             ctx->launches++;
         }
-        // phi in FP64 at each query's chosen start
-        for (int p = 0; p < ctx->np; ++p) {
-            const KSet &k = kset(ctx, p, c_c[p]);
-            auto fill = [&](auto &a) {
-                a.P = ctx->dev[p].pd;
-                a.tpp = tpp_c[p];
-                a.n = n_queries;
-                a.nsteps = n_steps;
-                a.n_default = ctx->opts.n_steps_default;
-                a.quad = ctx->opts.quad;
-                a.pidx = pidx;
-                a.pfilter = p;
-                a.best_pid = ctx->best_pid;
-                a.phi = phi_out;
-            };
-            if (ctx->prec) {
-                CertArgs<double> a{};
-                fill(a);
-                a.x = (const double *)x; a.t = (const double *)t; a.v = (const double *)ctx->vfin;
-                CU(k.cert_final(&a, rows_grid(ctx, k.f_cert_final, n_queries, tpp_c[p]), s));
-            } else {
-                CertArgs<float> a{};
-                fill(a);
-                a.x = (const float *)x; a.t = (const float *)t; a.v = (const float *)ctx->vfin;
-                CU(k.cert_final(&a, rows_grid(ctx, k.f_cert_final, n_queries, tpp_c[p]), s));
-            }
-            ctx->launches++;
-        }
+        st = phi_pass(s);
+        if (st != HJ_OK) return st;
         if (ctx->timing) { st = record(ctx, ctx->ev_cert, ctx->n_cert_ev++, s); if (st != HJ_OK) return st; }
         ctx->timing = timing_saved;
         if (!capturing) CU(cudaEventRecord(ctx->ev_end, s));
@@ -1784,7 +1802,7 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
                 a.P = ctx->dev[p].pf;
                 a.x = (const float *)x; a.t = (const float *)t; a.vfin = (float *)L.vfin;
                 int nl = 0;
-                CU(launch_desc_f32(ctx, k, kind, c_d[p] < 0, two, a, L.cursor + p, s, &nl));
+                CU(launch_desc_f32(ctx, k, kind, c_d[p] < 0, two, a, L.cursor + p, s, &nl, nullptr, nullptr));
             }
         }
         for (int p = 0; p < ctx->np; ++p) {

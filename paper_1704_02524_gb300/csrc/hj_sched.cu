@@ -128,7 +128,8 @@ __global__ void k_build_pairs(long long nq, const int32_t *pidx, int np, const i
 // 1 + j / |S|) with S the failed slots in slot order.  Best: certified
 // first, then the smallest value, ties to the lowest trial.  phi = F (Lax)
 // or -G (Hopf) at the chosen trial (the FP64 value replaces it after the
-// last round); best_pid records the trial.
+// last round); best_pid records the trial.  After round 0 a query that was
+// not reseeded is final and is left as it is.
 template <typename T>
 __global__ void k_select(long long nq, const int32_t *pidx, int np, const int32_t *pg, const int32_t *pt,
                          const int32_t *pd, const int32_t *pprin, int ld, const int32_t *pair_base, const double *pF,
@@ -145,6 +146,8 @@ __global__ void k_select(long long nq, const int32_t *pidx, int np, const int32_
             status[q] = HJ_ST_NONFINITE;
             continue;
         }
+        // after the reseed round only the reseeded queries change
+        if (round > 0 && !(qflags[q] & HJ_ST_RESEEDED)) continue;
         const int G = pg[p], nt = pt[p], d = pd[p];
         const int base = pair_base[q];
         int best = -1, best_cert = 0, qf = qflags[q];
@@ -197,6 +200,70 @@ __global__ void k_select(long long nq, const int32_t *pidx, int np, const int32_
         qflags[q] = qf;
         status[q] = st | qf;
     }
+}
+
+// Longest-first order of one problem's work list for the fine level of a
+// two-level descent: a persistent launch ends with the pairs it started last,
+// so starting the long ones first shortens its tail (the classical
+// longest-processing-time rule).  A pair's coarse-level iteration count is
+// the predictor of its fine-level work at hand.  Counting sort over LPT_BINS
+// bins, descending; the order within a bin is the atomics' and changes no
+// result (each pair's arithmetic does not depend on where it runs).
+constexpr int LPT_BINS = 256;
+
+__device__ __forceinline__ int lpt_key(int it, int max_iters)
+{
+    const int m = max(max_iters, 1);
+    const int c = min(max(it, 0), m);
+    return LPT_BINS - 1 - (int)((long long)c * (LPT_BINS - 1) / m);
+}
+
+__global__ void k_lpt_hist(const int32_t *wl, const int32_t *seg_begin, const int32_t *wl_count, int p,
+                           const int32_t *iters, int max_iters, int32_t *bins)
+{
+    __shared__ int32_t h[LPT_BINS];
+    for (int i = threadIdx.x; i < LPT_BINS; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int n = wl_count[p], b = seg_begin[p];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicAdd(&h[lpt_key(iters[wl[b + i]], max_iters)], 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < LPT_BINS; i += blockDim.x)
+        if (h[i]) atomicAdd(bins + i, h[i]);
+}
+
+__global__ void k_lpt_offsets(int32_t *bins)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int32_t acc = 0;
+        for (int i = 0; i < LPT_BINS; ++i) {
+            const int32_t c = bins[i];
+            bins[i] = acc;
+            acc += c;
+        }
+    }
+}
+
+__global__ void k_lpt_scatter(const int32_t *wl, const int32_t *seg_begin, const int32_t *wl_count, int p,
+                              const int32_t *iters, int max_iters, int32_t *bins, int32_t *out)
+{
+    const int n = wl_count[p], b = seg_begin[p];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t pid = wl[b + i];
+        out[b + atomicAdd(bins + lpt_key(iters[pid], max_iters), 1)] = pid;
+    }
+}
+
+cudaError_t launch_lpt_order(const int32_t *wl, const int32_t *seg_begin, const int32_t *wl_count, int p,
+                             const int32_t *iters, int max_iters, int32_t *bins, int32_t *out, int grid,
+                             cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(bins, 0, sizeof(int32_t) * LPT_BINS, s);
+    if (e != cudaSuccess) return e;
+    k_lpt_hist<<<grid, 256, 0, s>>>(wl, seg_begin, wl_count, p, iters, max_iters, bins);
+    k_lpt_offsets<<<1, 32, 0, s>>>(bins);
+    k_lpt_scatter<<<grid, 256, 0, s>>>(wl, seg_begin, wl_count, p, iters, max_iters, bins, out);
+    return cudaGetLastError();
 }
 
 // hj_guesses: the starts drawn by hj_solve, for testing.
