@@ -1275,6 +1275,14 @@ hj_status hj_solve(hj_ctx *ctx, int64_t q_begin, int64_t n_queries, const int32_
                     fill(a);
                     a.x = (const double *)x; a.t = (const double *)t; a.v = (const double *)ctx->vfin;
                     CU(k.cert_final(&a, rows_grid(ctx, k.f_cert_final, n_queries, tpp_c[p]), ps));
+                } else if (c_d[p] < 0) {
+                    // one-thread-per-pair family: FP64 phi in its reduced state
+                    const KSet &kr = kset(ctx, p, c_d[p]);
+                    CertArgs<float> a{};
+                    fill(a);
+                    a.tpp = 1;
+                    a.x = (const float *)x; a.t = (const float *)t; a.v = (const float *)ctx->vfin;
+                    CU(kr.cert_final(&a, rows_grid(ctx, kr.f_cert_final, n_queries, 1), ps));
                 } else {
                     CertArgs<float> a{};
                     fill(a);
@@ -1886,6 +1894,13 @@ extern "C" hj_status hj_solve_noalloc(hj_ctx *ctx, int64_t q_begin, int64_t n_qu
             fill(a);
             a.x = (const double *)x; a.t = (const double *)t; a.v = (const double *)L.vfin;
             CU(k.cert_final(&a, rows_grid(ctx, k.f_cert_final, n_queries, tpp_c[p]), s));
+        } else if (c_d[p] < 0) {
+            const KSet &kr = kset(ctx, p, c_d[p]);
+            CertArgs<float> a{};
+            fill(a);
+            a.tpp = 1;
+            a.x = (const float *)x; a.t = (const float *)t; a.v = (const float *)L.vfin;
+            CU(kr.cert_final(&a, rows_grid(ctx, kr.f_cert_final, n_queries, 1), s));
         } else {
             CertArgs<float> a{};
             fill(a);

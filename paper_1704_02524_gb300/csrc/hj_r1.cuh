@@ -219,10 +219,11 @@ __device__ __forceinline__ void rk4_acc(int st, float k, float &a)
 }
 
 // One classical RK4 step of (u, B) and the running cost; the four stage
-// records go to rec when it is non-null.
+// records go to rec (shared memory) when it is non-null, the four stages'
+// (u, B, Phi, D) to srec (the thread's local memory) when that is non-null.
 template <int C, int TPP>
 __device__ __forceinline__ void step(const ProbDev<float> &P, const Lane<C, TPP> &L, const float *v, float eps,
-                                     float h, float &u, float &B, float &dQ, float *rec)
+                                     float h, float &u, float &B, float &dQ, float *rec, float4 *srec = nullptr)
 {
     const float h2 = 0.5f * h, h6 = h / 6.f;
     float su = u, sB = B, au = 0.f, aB = 0.f, aL = 0.f;
@@ -231,6 +232,7 @@ __device__ __forceinline__ void step(const ProbDev<float> &P, const Lane<C, TPP>
         St s;
         stage<C, TPP, false>(P, L, v, eps, su, sB, s, nullptr);
         if (rec) put(rec, st, s);
+        if (srec) srec[st] = make_float4(s.u, s.B, s.phi, s.D);
         const float ku = rate_u(s), kB = rate_B(s);
         rk4_acc(st, ku, au);
         rk4_acc(st, kB, aB);
@@ -289,10 +291,12 @@ __device__ __forceinline__ float terminal(const ProbDev<float> &P, const Lane<C,
 
 // Functional G(v) (Hopf) from u0 = <w, x> and xv = <x, v>.  With ck != null
 // the step inputs (u_n, B_n) of every K-th step are stored there (the
-// adjoint's checkpoints).  B_N is returned in Bn.
+// adjoint's checkpoints); with sr != null the four stage records of every
+// step (sr[4 n + stage]).  B_N is returned in Bn.
 template <int C, int TPP>
 __device__ __forceinline__ float functional(const ProbDev<float> &P, const Lane<C, TPP> &L, int kahan, float u0,
-                                            float xv, const float *v, float t, int N, float2 *ck, int K, float &Bn)
+                                            float xv, const float *v, float t, int N, float2 *ck, int K, float &Bn,
+                                            float4 *sr = nullptr)
 {
     if (N < 1 || N > MAX_N) {
         Bn = NAN;
@@ -306,7 +310,7 @@ __device__ __forceinline__ float functional(const ProbDev<float> &P, const Lane<
             if (++kk == K) kk = 0;
         }
         float dQ;
-        step<C, TPP>(P, L, v, eps, h, u, B, dQ, nullptr);
+        step<C, TPP>(P, L, v, eps, h, u, B, dQ, nullptr, sr ? sr + 4 * n : nullptr);
         add_q(kahan, dQ, Q, Qc);
     }
     Bn = B;
@@ -438,12 +442,48 @@ __device__ __forceinline__ void adjoint_step(const ProbDev<float> &P, const Lane
     alpha = __fadd_rn(alpha, sumR);
 }
 
+// The stage scalars from a stored record (u, B, Phi, D): c and its
+// derivatives recomputed from u exactly as stage() computes them.
+__device__ __forceinline__ St from_rec(float4 r)
+{
+    float su, cu;
+    __sincosf(r.x, &su, &cu);
+    return St{r.x, r.y, fmaf(0.5f, su, 1.f), 0.5f * cu, -0.5f * su, r.z, r.w};
+}
+
+// adjoint_step with the step's four stage records taken from the forward
+// pass (sr[0..3]) instead of rebuilt: the same products in the same order on
+// the same stage values, so the same result bit for bit, without the
+// rebuild's four d-wide stage sums.
+template <int C, int TPP>
+__device__ __forceinline__ void adjoint_step_rec(const ProbDev<float> &P, const Lane<C, TPP> &L, const float *v,
+                                                 float eps, float h, const float4 *sr, float &alpha, float *lp)
+{
+    const float h2 = 0.5f * h, h3 = h / 3.f, h6 = h / 6.f;
+    const float4 r0 = sr[0], r1 = sr[1], r2 = sr[2], r3 = sr[3];
+    const float Lw = dot_w<C, TPP>(P, L, lp);
+    float R = 0.f, W = 0.f, sumR = 0.f;
+#pragma unroll 1
+    for (int j = 3; j >= 0; --j) {
+        const St s = from_rec(j == 3 ? r3 : j == 2 ? r2 : j == 1 ? r1 : r0);
+        const float wl = (j == 0 || j == 3) ? h6 : h3;
+        const float wp = (j == 2) ? h : h2;
+        vjp<C, TPP>(P, L, v, eps, s, fmaf(wl, alpha, __fmul_rn(wp, R)), fmaf(wl, Lw, __fmul_rn(wp, W)), wl, W, lp, R,
+                    W);
+        sumR = __fadd_rn(sumR, R);
+    }
+    alpha = __fadd_rn(alpha, sumR);
+}
+
 // Gradient of G with respect to v, less the -x of the Hopf terminal term:
-// gr gets lam_p(0) (the caller subtracts x).  Returns G.  ck holds
-// ceil(N/K) checkpoints, seg K states (thread-private).
+// gr gets lam_p(0) (the caller subtracts x).  Returns G.  K = 1: the forward
+// pass keeps every stage record in sr (4 N float4) and the reverse pass reads
+// them; K > 1: sr holds ceil(N/K) checkpoints (u_n, B_n) and each segment's
+// states are recomputed into seg (K states), each step's stages rebuilt.
+// Both give the same gradient bit for bit (thread-private scratch).
 template <int C, int TPP>
 __device__ __forceinline__ float gradient(const ProbDev<float> &P, const Lane<C, TPP> &L, int kahan, int K, float u0,
-                                          float xv, const float *v, float t, int N, float *gr, float2 *ck,
+                                          float xv, const float *v, float t, int N, float *gr, float4 *sr,
                                           float2 *seg, float *rec)
 {
     if (N < 1 || N > MAX_N) {
@@ -453,16 +493,13 @@ __device__ __forceinline__ float gradient(const ProbDev<float> &P, const Lane<C,
     }
     const float eps = P.s_eps, h = t / (float)N;
     float Bn;
-    const float F = functional<C, TPP>(P, L, kahan, u0, xv, v, t, N, ck, K, Bn);
+    float2 *ck = (float2 *)sr;
+    const float F = functional<C, TPP>(P, L, kahan, u0, xv, v, t, N, K == 1 ? nullptr : ck, K, Bn,
+                                       K == 1 ? sr : nullptr);
     terminal<C, TPP>(P, L, xv, v, Bn, gr);  // seed lam_p = grad g*(p_N), kept in gr
     float alpha = 0.f;
     if (K == 1) {
-        float2 cur = ck[N - 1];
-        for (int n = N - 1; n >= 0; --n) {
-            const float2 nxt = ck[n > 0 ? n - 1 : 0];
-            adjoint_step<C, TPP>(P, L, v, eps, h, cur.x, cur.y, alpha, gr, rec);
-            cur = nxt;
-        }
+        for (int n = N - 1; n >= 0; --n) adjoint_step_rec<C, TPP>(P, L, v, eps, h, sr + 4 * n, alpha, gr);
     } else {
         const int nseg = (N + K - 1) / K;
         for (int sg = nseg - 1; sg >= 0; --sg) {
@@ -534,7 +571,8 @@ template <int C>
 __global__ void __launch_bounds__(BLOCK, (min_blocks<C, 1>())) k_grad(RowArgs<float> a)
 {
     __shared__ float s_rec[4 * REC][BLOCK];
-    float2 ck[MAX_N], seg[MAX_SEG];
+    float4 sr[4 * MAX_N];
+    float2 seg[MAX_SEG];
     float *rec = &s_rec[0][threadIdx.x];
     Lane<C, 1> L;
     L.load(a.P, threadIdx.x & 31);
@@ -547,11 +585,88 @@ __global__ void __launch_bounds__(BLOCK, (min_blocks<C, 1>())) k_grad(RowArgs<fl
         load_vec<C, 1>(L, a.v + r * a.P.ld, a.P.d, v);
         const int K = ck_interval(N, a.ck_interval);
         const float F = gradient<C, 1>(a.P, L, a.kahan, K, dot_w<C, 1>(a.P, L, x), dot<C, 1>(L, x, v), v, a.t[r], N,
-                                       gr, ck, seg, rec);
+                                       gr, sr, seg, rec);
 #pragma unroll
         for (int k = 0; k < C; ++k) gr[k] -= x[k];
         store_vec<C, 1>(L, a.grad + r * a.P.ld, a.P.d, gr);
         if (a.F) a.F[r] = F;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 value of the functional at each query's chosen start (the solve's
+// final phi, Sec. 4.3: phi = -G at the returned optimum), one thread per
+// query, in the reduced state: the RK4 iterates are p_n = v + B_n w and
+// u_n = <w, gamma_n> exactly as in binary32 above, here with every stage sum
+// in double and the problem's parameters read from its FP64 block.  The same
+// stages, weights, quadrature (plain sum) and terminal term as the lane-group
+// FP64 functional, up to rounding; step counts outside [1, MAX_N] give NaN.
+// ---------------------------------------------------------------------------
+template <int C>
+__global__ void __launch_bounds__(BLOCK) k_phi64(CertArgs<float> a)
+{
+    const ProbDev<double> &P = a.P;
+    const int d = P.d;
+    const long long stride = (long long)gridDim.x * BLOCK;
+    for (long long q = (long long)blockIdx.x * BLOCK + threadIdx.x; q < a.n; q += stride) {
+        if (a.pidx && a.pidx[q] != a.pfilter) continue;
+        const long long pid = a.best_pid[q];
+        if (pid < 0) continue;
+        const int N = a.nsteps ? a.nsteps[q] : a.n_default;
+        if (N < 1 || N > MAX_N) {
+            a.phi[q] = NAN;
+            continue;
+        }
+        double v[C], u = 0.0, xv = 0.0;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            const double xk = (k < d) ? (double)__ldg(a.x + q * P.ld + k) : 0.0;
+            v[k] = (k < d) ? (double)__ldg(a.v + pid * P.ld + k) : 0.0;
+            u = fma(__ldg(P.w + k), xk, u);
+            xv = fma(xk, v[k], xv);
+        }
+        const double eps = P.s_eps, h = (double)a.t[q] / (double)N, h2 = 0.5 * h, h6 = h / 6.0;
+        double B = 0.0, Q = 0.0;
+        for (int n = 0; n < N; ++n) {
+            double su = u, sB = B, au = 0.0, aB = 0.0, aL = 0.0;
+#pragma unroll 1
+            for (int st = 0; st < 4; ++st) {
+                double phi = 0.0, D = 0.0;
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    const double wk = __ldg(P.w + k), ek = __ldg(P.e + k);
+                    const double p = fma(sB, wk, v[k]);
+                    const double qq = fma(p, p, eps);
+                    const double r = rsqrt(qq);
+                    phi = fma(ek, qq * r, phi);
+                    D = fma(wk * ek, r * p, D);
+                }
+                double sn, cs;
+                sincos(su, &sn, &cs);
+                const double c = fma(0.5, sn, 1.0), c1 = 0.5 * cs;
+                const double ku = -c * D, kB = phi * c1, kL = phi * fma(-c1, su, c);
+                const double wgt = (st == 0 || st == 3) ? 1.0 : 2.0;
+                au = fma(wgt, ku, au);
+                aB = fma(wgt, kB, aB);
+                aL = fma(wgt, kL, aL);
+                const double hs = (st == 2) ? h : h2;
+                su = fma(hs, ku, u);
+                sB = fma(hs, kB, B);
+            }
+            u = fma(h6, au, u);
+            B = fma(h6, aB, B);
+            Q += h6 * aL;
+        }
+        // Hopf terminal term g*(p_N) - <x, v>
+        double G = 0.0;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            const double p = fma(B, __ldg(P.w + k), v[k]);
+            if (P.g_kind == HJ_G_QUAD_SHIFT) G += p * fma(0.5, p, __ldg(P.ga + k));
+            else G += 0.5 * __ldg(P.gs2 + k) * p * p;
+        }
+        if (P.g_kind == HJ_G_ELLIPSE) G += 0.5;
+        a.phi[q] = -((G - xv) + Q);
     }
 }
 
@@ -587,7 +702,8 @@ __global__ void __launch_bounds__(BLOCK, (min_blocks<C, TPP>())) k_desc(DescArgs
     const float fd_h = (float)a.S.fd_h;
     const bool central = (a.S.grad != HJ_GRAD_FD_FORWARD);
     const bool coarse = (MODE != DESC_CD) && a.phase == 1;
-    float2 ck[MODE == DESC_GD ? MAX_N : 1], seg[MODE == DESC_GD ? MAX_SEG : 1];
+    float4 sr[MODE == DESC_GD ? 4 * MAX_N : 1];
+    float2 seg[MODE == DESC_GD ? MAX_SEG : 1];
     float *rec = &s_rec[0][tid];
     unsigned long long n_it = 0, n_f = 0, n_g = 0, n_rk = 0, n_adj = 0, n_pairs = 0, n_sumN = 0, n_cert = 0;
 
@@ -657,7 +773,7 @@ __global__ void __launch_bounds__(BLOCK, (min_blocks<C, TPP>())) k_desc(DescArgs
             if constexpr (MODE == DESC_GD) {
                 float gr[CL];
                 const int K = ck_interval(Ncur, a.S.ck_interval);
-                gradient<C, TPP>(a.P, L, a.S.kahan, K, u0, xv, v, t, Ncur, gr, ck, seg, rec);
+                gradient<C, TPP>(a.P, L, a.S.kahan, K, u0, xv, v, t, Ncur, gr, sr, seg, rec);
                 if (L.gl == 0) {  // counted once per pair
                     n_g++;
                     n_rk += Ncur;

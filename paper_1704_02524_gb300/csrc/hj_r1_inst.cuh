@@ -19,6 +19,12 @@ cudaError_t launch_r1_grad(const void *a, int grid, cudaStream_t s)
     r1::k_grad<C><<<grid, BLOCK, 0, s>>>(*(const RowArgs<float> *)a);
     return cudaGetLastError();
 }
+template <int C>
+cudaError_t launch_r1_phi64(const void *a, int grid, cudaStream_t s)
+{
+    r1::k_phi64<C><<<grid, BLOCK, 0, s>>>(*(const CertArgs<float> *)a);
+    return cudaGetLastError();
+}
 template <int C, int MODE, int TPP>
 cudaError_t launch_r1_desc(const void *a, int grid, cudaStream_t s)
 {
@@ -39,6 +45,8 @@ void register_r1(Registry &r)
     k.gd = &launch_r1_desc<C, DESC_GD, 1>;
     k.f_gd = (const void *)&r1::k_desc<C, DESC_GD, 1>;
     k.gd_lat = &launch_r1_desc<C, DESC_GD, 2>;
+    k.cert_final = &launch_r1_phi64<C>;
+    k.f_cert_final = (const void *)&r1::k_phi64<C>;
     k.f_gd_lat = (const void *)&r1::k_desc<C, DESC_GD, 2>;
 }
 

@@ -409,6 +409,25 @@ def test_solve_smooth_nonconvex_d20_matches_oracle(hj):
     assert np.array_equal(st & 1, ref["status"] & 1)
 
 
+@pytest.mark.parametrize("nq,split", [(40, False), (300, True)])
+def test_solve_phi_is_the_fp64_functional_at_the_returned_start(hj, nq, split):
+    # phi comes from an FP64 evaluation at each query's returned v (for this
+    # family the one-thread-per-query reduced-state kernel): the oracle's FP64
+    # functional at the same v agrees to rounding, in hj_solve and in the
+    # no-alloc entry point
+    wl = W.c3_smooth_nonconvex(nq=nq).head(nq)
+    ctx = hj.hj_create(wl.problems, hj.opts_from_dict(wl.solver, hj.HJ_PREC_FP32, int(wl.n_steps[0])), 0)
+    args = (_t(wl.x, torch.float32), _t(wl.t, torch.float32), _t(wl.n_steps, torch.int32))
+    phi, v, st = (hj.hj_solve_noalloc if split else hj.hj_solve)(ctx, *args)
+    torch.cuda.synchronize()
+    ctx.close()
+    phi, v = phi.cpu().numpy(), v.cpu().numpy().astype(np.float64)
+    P = oracle_problem(wl.problems[0])
+    for i in range(0, nq, 7 if split else 1):
+        G = O.functional(P, wl.x[i], float(wl.t[i]), int(wl.n_steps[i]), v[i])
+        assert abs(phi[i] + G) <= 1e-12 * (1 + abs(G)), (i, phi[i], -G)
+
+
 @pytest.mark.parametrize("max_trials", [20, 40])
 def test_reseed_budget_runs_in_one_round_from_the_failed_slots(hj, max_trials):
     # cert_tol = 0 fails every start, so every query spends its whole budget:
