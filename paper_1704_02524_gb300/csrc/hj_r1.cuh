@@ -219,11 +219,13 @@ __device__ __forceinline__ void rk4_acc(int st, float k, float &a)
 }
 
 // One classical RK4 step of (u, B) and the running cost; the four stage
-// records go to rec (shared memory) when it is non-null, the four stages'
-// (u, B, Phi, D) to srec (the thread's local memory) when that is non-null.
+// records go to rec (shared memory) when it is non-null.  With srec
+// non-null the step's record for the adjoint goes to the thread's local
+// memory: srec[0] = (u_n, B_n), srec[1 + s] = (Phi, D) of stage s (the
+// stage inputs follow from these by the step's own arithmetic).
 template <int C, int TPP>
 __device__ __forceinline__ void step(const ProbDev<float> &P, const Lane<C, TPP> &L, const float *v, float eps,
-                                     float h, float &u, float &B, float &dQ, float *rec, float4 *srec = nullptr)
+                                     float h, float &u, float &B, float &dQ, float *rec, float2 *srec = nullptr)
 {
     const float h2 = 0.5f * h, h6 = h / 6.f;
     float su = u, sB = B, au = 0.f, aB = 0.f, aL = 0.f;
@@ -232,7 +234,7 @@ __device__ __forceinline__ void step(const ProbDev<float> &P, const Lane<C, TPP>
         St s;
         stage<C, TPP, false>(P, L, v, eps, su, sB, s, nullptr);
         if (rec) put(rec, st, s);
-        if (srec) srec[st] = make_float4(s.u, s.B, s.phi, s.D);
+        if (srec) srec[1 + st] = make_float2(s.phi, s.D);
         const float ku = rate_u(s), kB = rate_B(s);
         rk4_acc(st, ku, au);
         rk4_acc(st, kB, aB);
@@ -241,6 +243,7 @@ __device__ __forceinline__ void step(const ProbDev<float> &P, const Lane<C, TPP>
         su = fmaf(hs, ku, u);
         sB = fmaf(hs, kB, B);
     }
+    if (srec) srec[0] = make_float2(u, B);
     u = fmaf(h6, au, u);
     B = fmaf(h6, aB, B);
     dQ = __fmul_rn(h6, aL);
@@ -259,6 +262,23 @@ __device__ __forceinline__ float dot_w(const ProbDev<float> &P, const Lane<C, TP
         Acc<TPP> a;
 #pragma unroll
         for (int k = 0; k < Lane<C, TPP>::CL; ++k) a.fma_(k, L.w(P, k), x[k]);
+        return L.total(a.a0, a.a1);
+    }
+}
+// <w e, x> over the group's components (w e = w_i e_i, the products' weights
+// of the sign-folded adjoint below).
+template <int C, int TPP>
+__device__ __forceinline__ float dot_we(const ProbDev<float> &P, const Lane<C, TPP> &L, const float *x)
+{
+    if constexpr (TPP == 1) {
+        float2 a = splat2(0.f);
+#pragma unroll
+        for (int j = 0; j < C / 2; ++j) a = __ffma2_rn(pair2(P.rew, j), pair2(x, j), a);
+        return L.total(a.x, a.y);
+    } else {
+        Acc<TPP> a;
+#pragma unroll
+        for (int k = 0; k < Lane<C, TPP>::CL; ++k) a.fma_(k, L.we(P, k), x[k]);
         return L.total(a.a0, a.a1);
     }
 }
@@ -291,12 +311,12 @@ __device__ __forceinline__ float terminal(const ProbDev<float> &P, const Lane<C,
 
 // Functional G(v) (Hopf) from u0 = <w, x> and xv = <x, v>.  With ck != null
 // the step inputs (u_n, B_n) of every K-th step are stored there (the
-// adjoint's checkpoints); with sr != null the four stage records of every
-// step (sr[4 n + stage]).  B_N is returned in Bn.
+// adjoint's checkpoints); with sr != null every step's record (sr[5 n ..
+// 5 n + 4], see step()).  B_N is returned in Bn.
 template <int C, int TPP>
 __device__ __forceinline__ float functional(const ProbDev<float> &P, const Lane<C, TPP> &L, int kahan, float u0,
                                             float xv, const float *v, float t, int N, float2 *ck, int K, float &Bn,
-                                            float4 *sr = nullptr)
+                                            float2 *sr = nullptr)
 {
     if (N < 1 || N > MAX_N) {
         Bn = NAN;
@@ -310,7 +330,7 @@ __device__ __forceinline__ float functional(const ProbDev<float> &P, const Lane<
             if (++kk == K) kk = 0;
         }
         float dQ;
-        step<C, TPP>(P, L, v, eps, h, u, B, dQ, nullptr, sr ? sr + 4 * n : nullptr);
+        step<C, TPP>(P, L, v, eps, h, u, B, dQ, nullptr, sr ? sr + 5 * n : nullptr);
         add_q(kahan, dQ, Q, Qc);
     }
     Bn = B;
@@ -365,8 +385,11 @@ __device__ __forceinline__ float functional_gamma(const ProbDev<float> &P, const
 }
 
 // Vector-Jacobian product of one stage with scalar weights: gamma weight
-// a w, p weight with <weight_p, w> = Bw, quadrature weight bb.  Adds the
-// p-part to lp; returns the gamma-part's coefficient (dE/du) in R and
+// a w, p weight with <weight_p, w> = Bw, quadrature weight bb.  The p-part
+// is e_i r_i tt_i; with the signs e_i = +-1 folded into the adjoint state
+// (lp holds e_i lam_p,i, exactly, since a product with +-1 is exact and
+// rounding is symmetric) it adds r_i tt_i to lp, and its <w, .> is
+// <w e, r tt>.  Returns the gamma-part's coefficient (dE/du) in R and
 // <w, p-part> in Wr.  The stage's p and reciprocals are recomputed; the stage
 // input is made to depend on `after` (the previous product's result, finite
 // in any finite solve) so that this happens in order instead of being
@@ -393,11 +416,11 @@ __device__ __forceinline__ void vjp(const ProbDev<float> &P, const Lane<C, TPP> 
             const float2 q = __ffma2_rn(p, p, eps2);
             const float2 ri = make_float2(rsqrtf(q.x), rsqrtf(q.y));
             const float2 tt = __ffma2_rn(__fmul2_rn(mcea2, wk), __fmul2_rn(ri, ri), __fmul2_rn(kd2, p));
-            const float2 rp = __fmul2_rn(__fmul2_rn(pair2(P.re, j), ri), tt);
+            const float2 rp = __fmul2_rn(ri, tt);
             const float2 l = __fadd2_rn(pair2(lp, j), rp);
             lp[2 * j] = l.x;
             lp[2 * j + 1] = l.y;
-            w = __ffma2_rn(wk, rp, w);
+            w = __ffma2_rn(pair2(P.rew, j), rp, w);
         }
         Wr = L.total(w.x, w.y);
     } else {
@@ -408,9 +431,9 @@ __device__ __forceinline__ void vjp(const ProbDev<float> &P, const Lane<C, TPP> 
             const float p = fmaf(Bs, wk, v[k]);
             const float ri = rsqrtf(fmaf(p, p, eps));
             const float tt = fmaf(__fmul_rn(-cea, wk), __fmul_rn(ri, ri), __fmul_rn(kd, p));
-            const float rp = __fmul_rn(__fmul_rn(L.e(P, k), ri), tt);
+            const float rp = __fmul_rn(ri, tt);
             lp[k] = __fadd_rn(lp[k], rp);
-            w.fma_(k, wk, rp);
+            w.fma_(k, L.we(P, k), rp);
         }
         Wr = L.total(w.a0, w.a1);
     }
@@ -428,7 +451,7 @@ __device__ __forceinline__ void adjoint_step(const ProbDev<float> &P, const Lane
     const float h2 = 0.5f * h, h3 = h / 3.f, h6 = h / 6.f;
     float un = u, Bn = B, dQ;
     step<C, TPP>(P, L, v, eps, h, un, Bn, dQ, rec);
-    const float Lw = dot_w<C, TPP>(P, L, lp);
+    const float Lw = dot_we<C, TPP>(P, L, lp);
     float R = 0.f, W = 0.f, sumR = 0.f;
 #pragma unroll 1
     for (int j = 3; j >= 0; --j) {
@@ -442,30 +465,35 @@ __device__ __forceinline__ void adjoint_step(const ProbDev<float> &P, const Lane
     alpha = __fadd_rn(alpha, sumR);
 }
 
-// The stage scalars from a stored record (u, B, Phi, D): c and its
-// derivatives recomputed from u exactly as stage() computes them.
-__device__ __forceinline__ St from_rec(float4 r)
-{
-    float su, cu;
-    __sincosf(r.x, &su, &cu);
-    return St{r.x, r.y, fmaf(0.5f, su, 1.f), 0.5f * cu, -0.5f * su, r.z, r.w};
-}
-
-// adjoint_step with the step's four stage records taken from the forward
-// pass (sr[0..3]) instead of rebuilt: the same products in the same order on
-// the same stage values, so the same result bit for bit, without the
-// rebuild's four d-wide stage sums.
+// adjoint_step with the step's record from the forward pass (r[0] = (u_n,
+// B_n), r[1 + s] = (Phi, D) of stage s) instead of a rebuild: the stage
+// inputs are re-derived from (u_n, B_n) and the stored sums by the forward
+// step's own operations (c and its derivatives from sin/cos of u as in
+// stage()), so every stage product sees the same values and the result is
+// the rebuild's bit for bit, without the rebuild's four d-wide stage sums.
 template <int C, int TPP>
 __device__ __forceinline__ void adjoint_step_rec(const ProbDev<float> &P, const Lane<C, TPP> &L, const float *v,
-                                                 float eps, float h, const float4 *sr, float &alpha, float *lp)
+                                                 float eps, float h, const float2 *r, float &alpha, float *lp,
+                                                 float *rec)
 {
     const float h2 = 0.5f * h, h3 = h / 3.f, h6 = h / 6.f;
-    const float4 r0 = sr[0], r1 = sr[1], r2 = sr[2], r3 = sr[3];
-    const float Lw = dot_w<C, TPP>(P, L, lp);
+    const float u = r[0].x, B = r[0].y;
+    float su = u, sB = B;
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+        float sn, cs;
+        __sincosf(su, &sn, &cs);
+        const St s{su, sB, fmaf(0.5f, sn, 1.f), 0.5f * cs, -0.5f * sn, r[1 + st].x, r[1 + st].y};
+        put(rec, st, s);
+        const float hs = (st == 2) ? h : h2;
+        su = fmaf(hs, rate_u(s), u);
+        sB = fmaf(hs, rate_B(s), B);
+    }
+    const float Lw = dot_we<C, TPP>(P, L, lp);
     float R = 0.f, W = 0.f, sumR = 0.f;
 #pragma unroll 1
     for (int j = 3; j >= 0; --j) {
-        const St s = from_rec(j == 3 ? r3 : j == 2 ? r2 : j == 1 ? r1 : r0);
+        const St s = get(rec, j);
         const float wl = (j == 0 || j == 3) ? h6 : h3;
         const float wp = (j == 2) ? h : h2;
         vjp<C, TPP>(P, L, v, eps, s, fmaf(wl, alpha, __fmul_rn(wp, R)), fmaf(wl, Lw, __fmul_rn(wp, W)), wl, W, lp, R,
@@ -477,13 +505,14 @@ __device__ __forceinline__ void adjoint_step_rec(const ProbDev<float> &P, const 
 
 // Gradient of G with respect to v, less the -x of the Hopf terminal term:
 // gr gets lam_p(0) (the caller subtracts x).  Returns G.  K = 1: the forward
-// pass keeps every stage record in sr (4 N float4) and the reverse pass reads
-// them; K > 1: sr holds ceil(N/K) checkpoints (u_n, B_n) and each segment's
-// states are recomputed into seg (K states), each step's stages rebuilt.
-// Both give the same gradient bit for bit (thread-private scratch).
+// pass keeps every step's record in sr (5 N float2) and the reverse pass
+// reads them, the next step's while the current one runs; K > 1: sr holds
+// ceil(N/K) checkpoints (u_n, B_n) and each segment's states are recomputed
+// into seg (K states), each step's stages rebuilt.  Both give the same
+// gradient bit for bit (thread-private scratch).
 template <int C, int TPP>
 __device__ __forceinline__ float gradient(const ProbDev<float> &P, const Lane<C, TPP> &L, int kahan, int K, float u0,
-                                          float xv, const float *v, float t, int N, float *gr, float4 *sr,
+                                          float xv, const float *v, float t, int N, float *gr, float2 *sr,
                                           float2 *seg, float *rec)
 {
     if (N < 1 || N > MAX_N) {
@@ -493,13 +522,25 @@ __device__ __forceinline__ float gradient(const ProbDev<float> &P, const Lane<C,
     }
     const float eps = P.s_eps, h = t / (float)N;
     float Bn;
-    float2 *ck = (float2 *)sr;
+    float2 *ck = sr;
     const float F = functional<C, TPP>(P, L, kahan, u0, xv, v, t, N, K == 1 ? nullptr : ck, K, Bn,
                                        K == 1 ? sr : nullptr);
     terminal<C, TPP>(P, L, xv, v, Bn, gr);  // seed lam_p = grad g*(p_N), kept in gr
+#pragma unroll
+    for (int k = 0; k < Lane<C, TPP>::CL; ++k) gr[k] = __fmul_rn(L.e(P, k), gr[k]);  // sign-folded
     float alpha = 0.f;
     if (K == 1) {
-        for (int n = N - 1; n >= 0; --n) adjoint_step_rec<C, TPP>(P, L, v, eps, h, sr + 4 * n, alpha, gr);
+        float2 cur[5], nxt[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) cur[i] = sr[5 * (N - 1) + i];
+        for (int n = N - 1; n >= 0; --n) {
+            const int m = n > 0 ? n - 1 : 0;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) nxt[i] = sr[5 * m + i];
+            adjoint_step_rec<C, TPP>(P, L, v, eps, h, cur, alpha, gr, rec);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) cur[i] = nxt[i];
+        }
     } else {
         const int nseg = (N + K - 1) / K;
         for (int sg = nseg - 1; sg >= 0; --sg) {
@@ -516,6 +557,8 @@ __device__ __forceinline__ float gradient(const ProbDev<float> &P, const Lane<C,
                 adjoint_step<C, TPP>(P, L, v, eps, h, seg[n - n0].x, seg[n - n0].y, alpha, gr, rec);
         }
     }
+#pragma unroll
+    for (int k = 0; k < Lane<C, TPP>::CL; ++k) gr[k] = __fmul_rn(L.e(P, k), gr[k]);
     return F;
 }
 
@@ -571,7 +614,7 @@ template <int C>
 __global__ void __launch_bounds__(BLOCK, (min_blocks<C, 1>())) k_grad(RowArgs<float> a)
 {
     __shared__ float s_rec[4 * REC][BLOCK];
-    float4 sr[4 * MAX_N];
+    float2 sr[5 * MAX_N];
     float2 seg[MAX_SEG];
     float *rec = &s_rec[0][threadIdx.x];
     Lane<C, 1> L;
@@ -702,7 +745,7 @@ __global__ void __launch_bounds__(BLOCK, (min_blocks<C, TPP>())) k_desc(DescArgs
     const float fd_h = (float)a.S.fd_h;
     const bool central = (a.S.grad != HJ_GRAD_FD_FORWARD);
     const bool coarse = (MODE != DESC_CD) && a.phase == 1;
-    float4 sr[MODE == DESC_GD ? 4 * MAX_N : 1];
+    float2 sr[MODE == DESC_GD ? 5 * MAX_N : 1];
     float2 seg[MODE == DESC_GD ? MAX_SEG : 1];
     float *rec = &s_rec[0][tid];
     unsigned long long n_it = 0, n_f = 0, n_g = 0, n_rk = 0, n_adj = 0, n_pairs = 0, n_sumN = 0, n_cert = 0;
