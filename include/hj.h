@@ -374,8 +374,11 @@ hj_status hj_last_solve_info(hj_ctx *ctx, hj_solve_info *out);
  * any other); ck_interval = integrator steps between checkpoints of the
  * adjoint, in [1, 16] (0: automatic, the smallest interval whose checkpoint
  * storage fits a fixed per-thread budget; 1 for the one-pair-per-thread
- * kernels, whose checkpoints are 8 bytes).  Returns HJ_EUNSUPPORTED when no
- * kernel is built for the resulting components per thread.
+ * kernels, where interval 1 means the forward pass keeps every step's stage
+ * record (40 bytes) and the reverse pass reads it instead of rebuilding the
+ * step, and intervals > 1 keep (u, B) checkpoints and rebuild, with the same
+ * gradient bit for bit).  Returns HJ_EUNSUPPORTED when no kernel is built for
+ * the resulting components per thread.
  */
 hj_status hj_set_tuning(hj_ctx *ctx, int problem, int tpp, int ck_interval);
 

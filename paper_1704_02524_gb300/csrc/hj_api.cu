@@ -1150,7 +1150,10 @@ hj_status hj_guesses(hj_ctx *ctx, int64_t n, const int64_t *query_id, const int3
 // Auxiliary streams of the concurrent descent launches (created once).
 static hj_status ensure_aux(hj_ctx *ctx)
 {
-    const int want = std::min(ctx->np, 4);
+    // the tensor-core problems share the first stream; every other problem
+    // gets one of its own (up to 16), so that no problem's launches wait
+    // behind another's on a shared stream
+    const int want = std::min(ctx->np + 1, 17);
     if ((int)ctx->aux.size() >= want) return HJ_OK;
     if (!ctx->ev_fork) CU(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
     while ((int)ctx->aux.size() < want) {
