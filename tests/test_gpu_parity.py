@@ -637,6 +637,35 @@ def test_solve_mixed_families_and_dimensions_matches_oracle(hj):
     assert info["n_pairs"] >= w.n_pairs
 
 
+def test_mixed_nonconvex_rows_at_small_t_match_oracle_on_every_row(hj):
+    # the non-convex Hopf family inside the mixed batch where its answer is
+    # reproducible (t <= 0.5, d <= 32: the oracle certifies every such row
+    # and its phi stays put under 1e-7 changes of x), 20 rows per dimension
+    # beside rows of every other problem: checked on every row, no filter
+    from tests.helpers import oracle_opts_list
+    wl = W.c5_mixed(n_pairs=20000)
+    fam = np.array([wl.problems[int(i)].family for i in wl.problem_idx])
+    dd = np.array([wl.problems[int(i)].d for i in wl.problem_idx])
+    nc = np.flatnonzero((fam == W.FAM_SMOOTH_NONCONVEX) & (dd <= 32) & (wl.t <= 0.5))
+    ids = np.concatenate([nc[dd[nc] == d][:20] for d in (8, 16, 32)])
+    others = np.concatenate([np.flatnonzero(wl.problem_idx == p)[:6] for p in range(len(wl.problems))
+                             if wl.problems[p].family != W.FAM_SMOOTH_NONCONVEX])
+    w = wl.take(np.sort(np.concatenate([ids, others])))
+    ctx = hj.hj_create(w.problems, hj.opts_from_dict(w.solver, hj.HJ_PREC_FP32, 64), 0)
+    phi, v, st = hj.hj_solve(ctx, _t(w.x, torch.float32), _t(w.t, torch.float32), _t(w.n_steps, torch.int32),
+                             _t(w.problem_idx, torch.int32))
+    phi, st = phi.cpu().numpy(), st.cpu().numpy()
+    ctx.close()
+    ref = O.solve([oracle_problem(p) for p in w.problems], oracle_opts_list(w), w.x, w.t, w.n_steps,
+                  problem_idx=w.problem_idx)
+    rows = np.isin(np.sort(np.concatenate([ids, others])), ids)
+    assert rows.sum() == 60
+    err = rel_err(phi, ref["phi"])
+    assert np.all(err[rows] <= 1e-4), err[rows].max()
+    assert np.array_equal(st[rows] & 1, ref["status"][rows] & 1)
+    assert np.all(ref["status"][rows] & 1)
+
+
 def test_autotuned_mixed_solve_still_matches_oracle(hj):
     w = _mixed_sample()
     phi, st, ref, stable, info, chosen = _solve_mixed(hj, w, tune=True)
