@@ -262,6 +262,82 @@ struct LqScratch {
 // The adjoint reuses the FI of a stage for its vector-Jacobian product.
 // Speed c(gamma) = 1 + sin(u)/2, u = <w, gamma>, c' = cos(u)/2, c'' = -sin(u)/2.
 // ---------------------------------------------------------------------------
+// Elementwise vector operations over a lane's C components.  binary32 with
+// C even runs them as packed FP32x2 pairs (__ffma2_rn, __fmul2_rn,
+// __fadd2_rn: per component the rounding of the scalar fma, multiply and add
+// they replace); everything else, and callers that pass PACK = false, in
+// scalars.  (The linear-quadratic family's kernels keep scalars: their
+// register pressure is already high, and packing added spills that made the
+// d=100 descent slower, measured.)
+template <typename T, int C, bool PACK = true>
+struct Vec {
+    static constexpr bool packed = PACK && (sizeof(T) == 4) && (C % 2 == 0);
+    // out = a x + y
+    __device__ static __forceinline__ void axpy(T a, const T *x, const T *y, T *out)
+    {
+        if constexpr (packed) {
+            const float2 a2 = make_float2(a, a);
+#pragma unroll
+            for (int j = 0; j < C / 2; ++j) {
+                const float2 r = __ffma2_rn(a2, make_float2(x[2 * j], x[2 * j + 1]), make_float2(y[2 * j], y[2 * j + 1]));
+                out[2 * j] = r.x;
+                out[2 * j + 1] = r.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < C; ++k) out[k] = fma(a, x[k], y[k]);
+        }
+    }
+    // out = a x + b y (b y rounded first)
+    __device__ static __forceinline__ void axpby(T a, const T *x, T b, const T *y, T *out)
+    {
+        if constexpr (packed) {
+            const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+#pragma unroll
+            for (int j = 0; j < C / 2; ++j) {
+                const float2 by = __fmul2_rn(b2, make_float2(y[2 * j], y[2 * j + 1]));
+                const float2 r = __ffma2_rn(a2, make_float2(x[2 * j], x[2 * j + 1]), by);
+                out[2 * j] = r.x;
+                out[2 * j + 1] = r.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < C; ++k) out[k] = fma(a, x[k], b * y[k]);
+        }
+    }
+    // out = a x
+    __device__ static __forceinline__ void scale(T a, const T *x, T *out)
+    {
+        if constexpr (packed) {
+            const float2 a2 = make_float2(a, a);
+#pragma unroll
+            for (int j = 0; j < C / 2; ++j) {
+                const float2 r = __fmul2_rn(a2, make_float2(x[2 * j], x[2 * j + 1]));
+                out[2 * j] = r.x;
+                out[2 * j + 1] = r.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < C; ++k) out[k] = a * x[k];
+        }
+    }
+    // out = x + y
+    __device__ static __forceinline__ void add(const T *x, const T *y, T *out)
+    {
+        if constexpr (packed) {
+#pragma unroll
+            for (int j = 0; j < C / 2; ++j) {
+                const float2 r = __fadd2_rn(make_float2(x[2 * j], x[2 * j + 1]), make_float2(y[2 * j], y[2 * j + 1]));
+                out[2 * j] = r.x;
+                out[2 * j + 1] = r.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < C; ++k) out[k] = x[k] + y[k];
+        }
+    }
+};
+
 template <typename T, int C, int FAM, int PR>
 struct Family;
 
@@ -1082,41 +1158,35 @@ __device__ __forceinline__ void rk4_step(const Grp &g, const TP<T, C> &tp, T eps
         add_q(kahan, dQ, Q, Qc);
         return;
     }
+    using V = Vec<T, C, FAM != HJ_FAM_LINEAR_QUAD>;
 #pragma unroll
     for (int k = 0; k < C; ++k) {
         ag[k] = kg[k];
         ap[k] = kp[k];
-        zg[k] = fma(h2, kg[k], gam[k]);
-        zp[k] = fma(h2, kp[k], p[k]);
     }
+    V::axpy(h2, kg, gam, zg);
+    V::axpy(h2, kp, p, zp);
     aL = L;
     tp.st = s0 - h2;
     field<T, C, FAM, PR>(g, tp, eps, zg, zp, kg, kp, L);
-#pragma unroll
-    for (int k = 0; k < C; ++k) {
-        ag[k] = fma((T)2, kg[k], ag[k]);
-        ap[k] = fma((T)2, kp[k], ap[k]);
-        zg[k] = fma(h2, kg[k], gam[k]);
-        zp[k] = fma(h2, kp[k], p[k]);
-    }
+    V::axpy((T)2, kg, ag, ag);
+    V::axpy((T)2, kp, ap, ap);
+    V::axpy(h2, kg, gam, zg);
+    V::axpy(h2, kp, p, zp);
     aL = fma((T)2, L, aL);
     field<T, C, FAM, PR>(g, tp, eps, zg, zp, kg, kp, L);
-#pragma unroll
-    for (int k = 0; k < C; ++k) {
-        ag[k] = fma((T)2, kg[k], ag[k]);
-        ap[k] = fma((T)2, kp[k], ap[k]);
-        zg[k] = fma(h, kg[k], gam[k]);
-        zp[k] = fma(h, kp[k], p[k]);
-    }
+    V::axpy((T)2, kg, ag, ag);
+    V::axpy((T)2, kp, ap, ap);
+    V::axpy(h, kg, gam, zg);
+    V::axpy(h, kp, p, zp);
     aL = fma((T)2, L, aL);
     tp.st = s0 - h;
     field<T, C, FAM, PR>(g, tp, eps, zg, zp, kg, kp, L);
     const T h6 = h / (T)6;
-#pragma unroll
-    for (int k = 0; k < C; ++k) {
-        gam[k] = fma(h6, ag[k] + kg[k], gam[k]);
-        p[k] = fma(h6, ap[k] + kp[k], p[k]);
-    }
+    V::add(ag, kg, ag);
+    V::add(ap, kp, ap);
+    V::axpy(h6, ag, gam, gam);
+    V::axpy(h6, ap, p, p);
     aL += L;
     T dQ;
     if (!(quad & HJ_QUAD_RECT)) {
@@ -1200,54 +1270,54 @@ __device__ __forceinline__ void adjoint_step(const Grp &g, const TP<T, C> &tp, T
     const T h6 = h / (T)6, h3 = h / (T)3, h2 = (T)0.5 * h;
     // rebuild the stage inputs of the step from z_n, keeping each stage's FI
     // (each prepared at its stage's PDE time, s0, s0 - h/2, s0 - h/2, s0 - h)
+    using V = Vec<T, C, FAM != HJ_FAM_LINEAR_QUAD>;
     tp.st = s0;
     Fam::prep(g, tp, eps, zg, zp, f1);
     Fam::field_fi(tp, f1, eps, kg, kp, L);
-#pragma unroll
-    for (int k = 0; k < C; ++k) { sg[k] = fma(h2, kg[k], zg[k]); sp[k] = fma(h2, kp[k], zp[k]); }
+    V::axpy(h2, kg, zg, sg);
+    V::axpy(h2, kp, zp, sp);
     tp.st = s0 - h2;
     Fam::prep(g, tp, eps, sg, sp, f2);
     Fam::field_fi(tp, f2, eps, kg, kp, L);
-#pragma unroll
-    for (int k = 0; k < C; ++k) { sg[k] = fma(h2, kg[k], zg[k]); sp[k] = fma(h2, kp[k], zp[k]); }
+    V::axpy(h2, kg, zg, sg);
+    V::axpy(h2, kp, zp, sp);
     Fam::prep(g, tp, eps, sg, sp, f3);
     Fam::field_fi(tp, f3, eps, kg, kp, L);
-#pragma unroll
-    for (int k = 0; k < C; ++k) { sg[k] = fma(h, kg[k], zg[k]); sp[k] = fma(h, kp[k], zp[k]); }
+    V::axpy(h, kg, zg, sg);
+    V::axpy(h, kp, zp, sp);
     tp.st = s0 - h;
     Fam::prep(g, tp, eps, sg, sp, f4);
 
     T wg[C], wp[C], rg[C], rp[C], sumg[C], sump[C];
     // stage 4
-#pragma unroll
-    for (int k = 0; k < C; ++k) { wg[k] = h6 * lg[k]; wp[k] = h6 * lp[k]; }
+    V::scale(h6, lg, wg);
+    V::scale(h6, lp, wp);
     Fam::vjp_fi(g, tp, f4, eps, wg, wp, h6 * b, rg, rp);
 #pragma unroll
     for (int k = 0; k < C; ++k) {
-        sumg[k] = rg[k]; sump[k] = rp[k];
-        wg[k] = fma(h3, lg[k], h * rg[k]); wp[k] = fma(h3, lp[k], h * rp[k]);
+        sumg[k] = rg[k];
+        sump[k] = rp[k];
     }
+    V::axpby(h3, lg, h, rg, wg);
+    V::axpby(h3, lp, h, rp, wp);
     // stage 3
     Fam::vjp_fi(g, tp, f3, eps, wg, wp, h3 * b, rg, rp);
-#pragma unroll
-    for (int k = 0; k < C; ++k) {
-        sumg[k] += rg[k]; sump[k] += rp[k];
-        wg[k] = fma(h3, lg[k], h2 * rg[k]); wp[k] = fma(h3, lp[k], h2 * rp[k]);
-    }
+    V::add(sumg, rg, sumg);
+    V::add(sump, rp, sump);
+    V::axpby(h3, lg, h2, rg, wg);
+    V::axpby(h3, lp, h2, rp, wp);
     // stage 2
     Fam::vjp_fi(g, tp, f2, eps, wg, wp, h3 * b, rg, rp);
-#pragma unroll
-    for (int k = 0; k < C; ++k) {
-        sumg[k] += rg[k]; sump[k] += rp[k];
-        wg[k] = fma(h6, lg[k], h2 * rg[k]); wp[k] = fma(h6, lp[k], h2 * rp[k]);
-    }
+    V::add(sumg, rg, sumg);
+    V::add(sump, rp, sump);
+    V::axpby(h6, lg, h2, rg, wg);
+    V::axpby(h6, lp, h2, rp, wp);
     // stage 1
     Fam::vjp_fi(g, tp, f1, eps, wg, wp, h6 * b, rg, rp);
-#pragma unroll
-    for (int k = 0; k < C; ++k) {
-        lg[k] += sumg[k] + rg[k];
-        lp[k] += sump[k] + rp[k];
-    }
+    V::add(sumg, rg, sumg);
+    V::add(sump, rp, sump);
+    V::add(lg, sumg, lg);
+    V::add(lp, sump, lp);
 }
 
 // Checkpoint interval: the given K, or the smallest K whose checkpoint and
