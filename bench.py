@@ -86,7 +86,7 @@ L2_FLUSH_BYTES = 256 << 20
 # launch's traffic grows with the number of (query, start) pairs, so it is
 # scaled by queries / queries captured.  None: not captured for the current
 # kernel.
-TRAFFIC = {"smooth_nonconvex_d20_hopf": (32768, 17.949e9 + 38.362e9),
+TRAFFIC = {"smooth_nonconvex_d20_hopf": (32768, 17.906e9 + 38.355e9),
            "linear_quad_d64_lax": (4096, 28.598e9 + 42.637e9)}
 
 
