@@ -428,13 +428,15 @@ hj_status hj_autotune(hj_ctx *ctx, int64_t n_queries, const int32_t *problem_idx
  * would run on the tensor-core tile kernel (see hj_solve) runs here on the
  * lane-group kernels, whose results agree with it within the tile kernel's
  * BF16x3 rounding but not bit for bit; every other problem gets hj_solve's
- * results bit for bit.  A batch of more than 2^31 - 1 (query, start) pairs
- * returns HJ_EINVAL before any size arithmetic.  All of the
+ * results bit for bit.  A batch of more than 2^31 - 1 (query, trial) pairs
+ * (a query's trials: its starts plus, with reseeding on, the rest of its
+ * trial budget) returns HJ_EINVAL before any size arithmetic.  All of the
  * call's scratch lives in one static device array of
  * HJ_SOLVE_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps
  * for the life of the process; a call that needs more (about
- * n_queries * max_starts * (42 + ld * element size) bytes plus ~20 bytes per
- * query) returns HJ_EINVAL with the sizes in hj_last_error and enqueues
+ * n_queries * max_trials * (42 + ld * element size) bytes plus ~20 bytes per
+ * query, max_trials the largest per-query trial count of the context's
+ * problems) returns HJ_EINVAL with the sizes in hj_last_error and enqueues
  * nothing.  The first call on each device looks up the array's device
  * address with that device current; make that first call before any stream
  * capture starts.  Every call on a device shares the one array: calls that
